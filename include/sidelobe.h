@@ -1,0 +1,187 @@
+/*
+ * sidelobe.h -- C ABI of libsidelobe.so: the spin-harmonic sidelobe
+ * convolution of Galloway et al., "BeyondPlanck VIII: Sidelobe corrections"
+ * (arXiv:2201.03478), on one NVIDIA GB300 (sm_103a).
+ *
+ * The operation (Sect. 2.1).  For a real sky s (harmonic coefficients s_lm,
+ * Eq. convolution) and a real beam b (b_lk, Eq. breal), with the beam's
+ * boresight on +z and the pointing rotation R = Rz(phi) Ry(theta) Rz(psi),
+ *
+ *   c(theta, phi, psi) = sum_{l,m,k} s_lm conj(b_lk) d^l_{mk}(theta) e^{im phi} e^{ik psi}
+ *                                                         (Eq. totalconvolver)
+ *
+ * is computed in the paper's two steps: (1) for each beam order k = 0..kmax a
+ * spin-k synthesis gives the cube F_k(theta_r, phi_j) on iso-latitude rings
+ * (Eqs. c_m and S: F_k is the paper's  _{k}S  up to its sign convention for
+ * spin harmonics); (2) the cube is interpolated at each pointing and summed
+ * with e^{ik psi} phases using the conjugate pairs F_{-k} = conj(F_k)
+ * (Sect. 2.1, the pair formula before Eq. S):
+ *
+ *   c = Re S_0 + 2 sum_{k>=1} Re(e^{ik psi} S_k),  S_k = interpolated F_k.
+ *
+ * The paper leaves the interpolation open ("a wide range of interpolation
+ * schemes"); this library uses separable p-point Lagrange interpolation in
+ * theta (at the actual ring colatitudes) and phi (uniform, periodic), with
+ * p/2 ghost rows past each pole that hold (-1)^k F_k(ring, phi + pi).
+ *
+ * Polarised input (ncomp = 3, T/E/B) is the sum of three scalar
+ * convolutions: A_{k,lm} = sum_X s^X_lm conj(b^X_lk).
+ *
+ * Memory.  Every pointer argument of the compute calls is a DEVICE pointer
+ * on the plan's device; the caller owns those buffers.  The plan owns its
+ * own tables and scratch (allocated by sidelobe_plan_create, and for the
+ * pointing sort grown on demand by the first call with a larger n).
+ *
+ * Packing.
+ *   sky  : double [ncomp][nalm][2] (re, im), nalm = (lmax+1)(lmax+2)/2,
+ *          m-major: idx(l, m) = m(2 lmax + 1 - m)/2 + l, 0 <= m <= l.
+ *          Im of m = 0 entries is ignored.  s_{l,-m} = (-1)^m conj(s_lm).
+ *   beam : double [ncomp][kmax+1][lmax+1][2]; entries with l < k are
+ *          ignored; Im of k = 0 entries is ignored; b_{l,-k} = (-1)^k conj(b_lk).
+ *   maps : the cube, [nrings][nphi][kmax+1] complex, k fastest;
+ *          double2 in SL_FP64 plans, float2 in SL_FP32 plans.
+ *          phi_j = 2 pi j / nphi on every ring.
+ *   theta, phi, psi : double [n], radians; theta in [0, pi].
+ *   tod  : double [n].
+ *
+ * Execution.  All compute calls are asynchronous on the plan's stream and
+ * return after enqueuing.  Argument errors are reported synchronously;
+ * launch errors are reported by the call that launched; faults inside a
+ * kernel surface at the next synchronising call (sl_plan_sync).  A plan is
+ * not re-entrant: one host thread and one stream at a time.
+ *
+ * Errors.  Every call returns an sl_status; on anything but SL_OK,
+ * sl_last_error() gives a message (thread-local, valid until the next call
+ * from the same thread).  No call ever terminates the process.
+ */
+#ifndef SIDELOBE_H
+#define SIDELOBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sl_plan sl_plan;
+
+typedef enum {
+    SL_OK = 0,
+    SL_ERR_ARG = -1,          /* bad argument (null pointer, size, layout) */
+    SL_ERR_UNSUPPORTED = -2,  /* valid but not supported (e.g. nphi with a prime factor > 5) */
+    SL_ERR_NOMEM = -3,        /* device allocation failed */
+    SL_ERR_CUDA = -4,         /* CUDA runtime error (launch, copy, device fault) */
+    SL_ERR_TIMEOUT = -5       /* a bounded device-side wait expired */
+} sl_status;
+
+typedef enum {
+    SL_FP64 = 0,  /* everything in double precision */
+    SL_FP32 = 1   /* FP64 seeds, coefficient products, pointing->grid conversion
+                     and final TOD value; FP32 recurrence, contraction, ring FFT,
+                     maps and interpolation sums */
+} sl_precision;
+
+typedef struct {
+    int lmax;                  /* sky and beam band limit L >= 1 */
+    int kmax;                  /* beam azimuthal band limit K, 0 <= K <= min(L, 63) */
+    int ncomp;                 /* 1 (T) or 3 (T, E, B) */
+    int nrings;                /* R >= 4 */
+    const double *ring_theta;  /* HOST [nrings]: strictly ascending colatitudes in (0, pi),
+                                  symmetric: theta[R-1-r] == pi - theta[r] (to 1e-12);
+                                  copied at plan creation */
+    int nphi;                  /* Phi: even, >= 8, of the form 2^a 3^b 5^c, <= 8192 */
+    int interp_order;          /* p: 4 (0 selects 4) */
+    int precision;             /* sl_precision */
+    int device;                /* CUDA device ordinal */
+    void *stream;              /* cudaStream_t for all work; NULL = legacy default stream */
+} sl_plan_desc;
+
+/* Builds a plan: validates the description, uploads the ring geometry and
+ * computes on the device the FP64 recurrence seeds d^{l0}_{m,+-k}(theta_r),
+ * l0 = max(m, k), for every ring pair, m and k (Sect. 2.1: the spin-k
+ * transforms of Eq. S).  Synchronises the stream before returning.
+ * *out receives the plan (NULL on error).  Free with plan_destroy. */
+sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *desc);
+
+/* Step 1 of the two-step algorithm (Sect. 2.1): the cube
+ *   F_k(theta_r, phi_j) = sum_{l,m} A_{k,lm} d^l_{mk}(theta_r) e^{im phi_j},
+ *   A_{k,lm} = sum_X s^X_lm conj(b^X_lk),   k = 0..kmax,
+ * written to maps (layout above; fully overwritten).  sky and beam are device
+ * pointers in the packing above.  m is folded modulo nphi when 2 lmax + 1 >
+ * nphi, which is exact at the nodes. */
+sl_status synth_spin_maps(sl_plan *plan, const double *sky, const double *beam, void *maps);
+
+/* Step 2 (Sect. 2.1, conjugate pairs): for i < n,
+ *   tod[i] = Re S_0 + 2 sum_{k>=1} Re(e^{ik psi_i} S_k),
+ * S_k the p-point Lagrange interpolation of F_k at (theta_i, phi_i).
+ * The pointings are binned into grid tiles and sorted by a counting sort on
+ * the device first; tod is written in the caller's order.  n = 0 is a no-op.
+ * n < 2^31. */
+sl_status interp_tod(sl_plan *plan, const void *maps, const double *theta, const double *phi,
+                     const double *psi, int64_t n, double *tod);
+
+/* Adjoint of interp_tod o synth_spin_maps with respect to the packed real
+ * parameters of sky and beam (Re and Im of each stored entry; Im of m = 0 and
+ * k = 0 entries and beam entries with l < k are not parameters and get 0):
+ *   sky_grad  = d<c(sky, beam), tod>/d sky   (beam held fixed),
+ *   beam_grad = d<c(sky, beam), tod>/d beam  (sky held fixed),
+ * i.e. the gradients of sum_i tod_i c_i.  Shapes are those of sky and beam.
+ * accumulate != 0 adds to the output buffers instead of overwriting them.
+ * Either gradient pointer may be NULL to skip it. */
+sl_status adjoint_tod(sl_plan *plan, const double *theta, const double *phi, const double *psi,
+                      const double *tod, int64_t n, const double *sky, const double *beam,
+                      double *sky_grad, double *beam_grad, int accumulate);
+
+/* The two halves of adjoint_tod, for callers that keep the adjoint cube.
+ * adjoint_interp: maps_bar (maps layout, always double2) = transpose of the
+ * interpolation and phase sum applied to tod; overwritten.
+ * adjoint_synth: gradients from maps_bar (transpose of synth_spin_maps
+ * followed by the sky x beam products). */
+sl_status adjoint_interp(sl_plan *plan, const double *theta, const double *phi, const double *psi,
+                         const double *tod, int64_t n, double *maps_bar);
+sl_status adjoint_synth(sl_plan *plan, const double *maps_bar, const double *sky, const double *beam,
+                        double *sky_grad, double *beam_grad, int accumulate);
+
+/* Frees the plan and everything it owns (after synchronising its stream).
+ * NULL is a no-op. */
+void plan_destroy(sl_plan *plan);
+
+/* ---- plan utilities ---------------------------------------------------- */
+
+/* Sizes a caller needs to allocate buffers. */
+typedef struct {
+    int64_t nalm;          /* sky entries per component */
+    int64_t sky_doubles;   /* ncomp * nalm * 2 */
+    int64_t beam_doubles;  /* ncomp * (kmax+1) * (lmax+1) * 2 */
+    int64_t maps_bytes;    /* nrings * nphi * (kmax+1) * (16 or 8) */
+    int64_t scratch_bytes; /* device memory the plan holds right now */
+} sl_plan_sizes;
+sl_status sl_plan_get_sizes(const sl_plan *plan, sl_plan_sizes *out);
+
+/* Re-targets the plan to another stream of the same device. */
+sl_status sl_plan_set_stream(sl_plan *plan, void *stream);
+
+/* Synchronises the plan's stream; reports device faults as SL_ERR_CUDA. */
+sl_status sl_plan_sync(sl_plan *plan);
+
+/* Per-kernel timing.  While enabled, every launch is bracketed by CUDA events
+ * on the plan's stream.  sl_plan_kernel_stats fills, for up to max entries,
+ * the kernel name, the number of launches and the summed device milliseconds
+ * since the last reset (synchronises the stream).  Returns the number of
+ * distinct kernels in *count. */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} sl_kernel_stat;
+sl_status sl_plan_enable_timing(sl_plan *plan, int enable);
+sl_status sl_plan_kernel_stats(sl_plan *plan, sl_kernel_stat *out, int max, int *count, int reset);
+
+/* Thread-local message describing the last non-OK status of this thread. */
+const char *sl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIDELOBE_H */

@@ -1,0 +1,87 @@
+"""ctypes loader for libsidelobe.so (the C ABI declared in include/sidelobe.h).
+
+The library is built in-tree by ``paper_2201_03478_gb300._build.build()``.  There
+is no fallback: if the shared library is missing or fails to load, every entry
+point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+SL_OK, SL_ERR_ARG, SL_ERR_UNSUPPORTED, SL_ERR_NOMEM, SL_ERR_CUDA, SL_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+SL_FP64, SL_FP32 = 0, 1
+
+STATUS_NAMES = {0: "SL_OK", -1: "SL_ERR_ARG", -2: "SL_ERR_UNSUPPORTED", -3: "SL_ERR_NOMEM",
+                -4: "SL_ERR_CUDA", -5: "SL_ERR_TIMEOUT"}
+
+# Symbols include/sidelobe.h declares (checked by the host tests).
+EXPORTS = ["sidelobe_plan_create", "synth_spin_maps", "interp_tod", "adjoint_tod", "adjoint_interp",
+           "adjoint_synth", "plan_destroy", "sl_plan_get_sizes", "sl_plan_set_stream", "sl_plan_sync",
+           "sl_plan_enable_timing", "sl_plan_kernel_stats", "sl_last_error"]
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("lmax", ctypes.c_int), ("kmax", ctypes.c_int), ("ncomp", ctypes.c_int),
+                ("nrings", ctypes.c_int), ("ring_theta", ctypes.c_void_p), ("nphi", ctypes.c_int),
+                ("interp_order", ctypes.c_int), ("precision", ctypes.c_int), ("device", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class PlanSizes(ctypes.Structure):
+    _fields_ = [("nalm", ctypes.c_int64), ("sky_doubles", ctypes.c_int64), ("beam_doubles", ctypes.c_int64),
+                ("maps_bytes", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class SidelobeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Load (building first if stale) libsidelobe.so and declare the signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise OSError("libsidelobe.so not found at %s (run paper_2201_03478_gb300._build.build())" % path)
+    lib = ctypes.CDLL(path)
+    P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    sig = {
+        "sidelobe_plan_create": (I, [ctypes.POINTER(P), ctypes.POINTER(PlanDesc)]),
+        "synth_spin_maps": (I, [P, P, P, P]),
+        "interp_tod": (I, [P, P, P, P, P, I64, P]),
+        "adjoint_tod": (I, [P, P, P, P, P, I64, P, P, P, P, I]),
+        "adjoint_interp": (I, [P, P, P, P, P, I64, P]),
+        "adjoint_synth": (I, [P, P, P, P, P, P, I]),
+        "plan_destroy": (None, [P]),
+        "sl_plan_get_sizes": (I, [P, ctypes.POINTER(PlanSizes)]),
+        "sl_plan_set_stream": (I, [P, P]),
+        "sl_plan_sync": (I, [P]),
+        "sl_plan_enable_timing": (I, [P, I]),
+        "sl_plan_kernel_stats": (I, [P, ctypes.POINTER(KernelStat), I, ctypes.POINTER(I), I]),
+        "sl_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int) -> None:
+    if status != SL_OK:
+        msg = load().sl_last_error()
+        raise SidelobeError(status, msg.decode() if msg else "")

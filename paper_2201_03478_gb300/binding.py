@@ -1,0 +1,217 @@
+"""Python binding of the C ABI (include/sidelobe.h), argument marshalling only.
+
+PyTorch supplies device memory and the stream; every step of the computation
+runs in libsidelobe.so.  The functions keep the C names:
+
+    plan = sidelobe_plan_create(lmax, kmax, ring_theta, nphi, ncomp=1, precision="fp64")
+    synth_spin_maps(plan, sky, beam, maps=None)        -> maps  [R, nphi, K+1] complex
+    interp_tod(plan, maps, theta, phi, psi, tod=None)  -> tod   [n] float64
+    adjoint_tod(plan, theta, phi, psi, tod, sky, beam) -> (sky_grad, beam_grad)
+    plan_destroy(plan)
+
+``sky`` is a complex128 tensor [ncomp, nalm] (m-major packing), ``beam`` a
+complex128 tensor [ncomp, K+1, L+1]; both on the plan's device.  Gradients
+come back in the same layouts, as d/dRe + i d/dIm of sum_i tod_i c_i.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import SL_FP32, SL_FP64, check
+
+_PREC = {"fp64": SL_FP64, "fp32": SL_FP32, SL_FP64: SL_FP64, SL_FP32: SL_FP32}
+
+
+class Plan:
+    """Owns one sl_plan*.  Not thread-safe; all work goes to one CUDA stream."""
+
+    def __init__(self, ptr, lmax, kmax, ncomp, ring_theta, nphi, precision, device, stream):
+        self.ptr = ptr
+        self.lmax, self.kmax, self.ncomp = lmax, kmax, ncomp
+        self.ring_theta = np.asarray(ring_theta, dtype=np.float64)
+        self.nrings, self.nphi = self.ring_theta.size, nphi
+        self.precision, self.device = precision, device
+        self._stream = stream
+        self.nalm = (lmax + 1) * (lmax + 2) // 2
+
+    @property
+    def maps_dtype(self):
+        return torch.complex128 if self.precision == SL_FP64 else torch.complex64
+
+    def maps_shape(self):
+        return (self.nrings, self.nphi, self.kmax + 1)
+
+    def _sync_stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        if s != self._stream:
+            check(_lib.load().sl_plan_set_stream(self.ptr, ctypes.c_void_p(s)))
+            self._stream = s
+
+    def sizes(self):
+        out = _lib.PlanSizes()
+        check(_lib.load().sl_plan_get_sizes(self.ptr, ctypes.byref(out)))
+        return {f: getattr(out, f) for f, _ in out._fields_}
+
+    def enable_timing(self, on=True):
+        check(_lib.load().sl_plan_enable_timing(self.ptr, int(bool(on))))
+
+    def kernel_stats(self, reset=False):
+        arr = (_lib.KernelStat * 64)()
+        n = ctypes.c_int(0)
+        check(_lib.load().sl_plan_kernel_stats(self.ptr, arr, 64, ctypes.byref(n), int(bool(reset))))
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(min(n.value, 64))}
+
+    def sync(self):
+        check(_lib.load().sl_plan_sync(self.ptr))
+
+    def __del__(self):
+        try:
+            plan_destroy(self)
+        except Exception:
+            pass
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_tensor(x, dtype, device, name, shape=None):
+    if not isinstance(x, torch.Tensor):
+        raise TypeError("%s must be a torch tensor on cuda:%d" % (name, device))
+    if x.device.type != "cuda" or x.device.index != device:
+        raise ValueError("%s must live on cuda:%d (got %s)" % (name, device, x.device))
+    if x.dtype != dtype:
+        raise TypeError("%s must be %s (got %s)" % (name, dtype, x.dtype))
+    if not x.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(x.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(x.shape), tuple(shape)))
+    return x
+
+
+def sidelobe_plan_create(lmax, kmax, ring_theta, nphi, ncomp=1, precision="fp64", interp_order=4,
+                         device=None):
+    lib = _lib.load()
+    if device is None:
+        device = torch.cuda.current_device()
+    rt = np.ascontiguousarray(ring_theta, dtype=np.float64)
+    stream = torch.cuda.current_stream(device).cuda_stream
+    d = _lib.PlanDesc(lmax=int(lmax), kmax=int(kmax), ncomp=int(ncomp), nrings=int(rt.size),
+                      ring_theta=rt.ctypes.data_as(ctypes.c_void_p), nphi=int(nphi),
+                      interp_order=int(interp_order), precision=_PREC[precision], device=int(device),
+                      stream=ctypes.c_void_p(stream))
+    out = ctypes.c_void_p()
+    check(lib.sidelobe_plan_create(ctypes.byref(out), ctypes.byref(d)))
+    return Plan(out, int(lmax), int(kmax), int(ncomp), rt, int(nphi), _PREC[precision], int(device), stream)
+
+
+def plan_destroy(plan: Plan) -> None:
+    if plan is not None and plan.ptr:
+        _lib.load().plan_destroy(plan.ptr)
+        plan.ptr = None
+
+
+def _sky_beam(plan, sky, beam):
+    sky = _dev_tensor(sky, torch.complex128, plan.device, "sky", (plan.ncomp, plan.nalm))
+    beam = _dev_tensor(beam, torch.complex128, plan.device, "beam", (plan.ncomp, plan.kmax + 1, plan.lmax + 1))
+    return sky, beam
+
+
+def synth_spin_maps(plan: Plan, sky, beam, maps=None):
+    """Cube F_k(theta_r, phi_j), k = 0..kmax (Sect. 2.1, step 1)."""
+    sky, beam = _sky_beam(plan, sky, beam)
+    if maps is None:
+        maps = torch.empty(plan.maps_shape(), dtype=plan.maps_dtype, device=sky.device)
+    _dev_tensor(maps, plan.maps_dtype, plan.device, "maps", plan.maps_shape())
+    plan._sync_stream()
+    check(_lib.load().synth_spin_maps(plan.ptr, _ptr(sky), _ptr(beam), _ptr(maps)))
+    return maps
+
+
+def _ptg(plan, theta, phi, psi):
+    n = theta.numel()
+    for name, t in (("theta", theta), ("phi", phi), ("psi", psi)):
+        _dev_tensor(t, torch.float64, plan.device, name, (n,))
+    return n
+
+
+def interp_tod(plan: Plan, maps, theta, phi, psi, tod=None):
+    """TOD at the pointings (Sect. 2.1, step 2 with conjugate-pair phases)."""
+    _dev_tensor(maps, plan.maps_dtype, plan.device, "maps", plan.maps_shape())
+    n = _ptg(plan, theta, phi, psi)
+    if tod is None:
+        tod = torch.empty(n, dtype=torch.float64, device=theta.device)
+    _dev_tensor(tod, torch.float64, plan.device, "tod", (n,))
+    plan._sync_stream()
+    check(_lib.load().interp_tod(plan.ptr, _ptr(maps), _ptr(theta), _ptr(phi), _ptr(psi), n, _ptr(tod)))
+    return tod
+
+
+def adjoint_tod(plan: Plan, theta, phi, psi, tod, sky, beam, sky_grad=None, beam_grad=None,
+                accumulate=False, want_sky=True, want_beam=True):
+    """Gradients of sum_i tod_i c_i w.r.t. the packed sky and beam (d/dRe + i d/dIm)."""
+    sky, beam = _sky_beam(plan, sky, beam)
+    n = _ptg(plan, theta, phi, psi)
+    _dev_tensor(tod, torch.float64, plan.device, "tod", (n,))
+    if want_sky and sky_grad is None:
+        sky_grad = torch.zeros_like(sky)
+    if want_beam and beam_grad is None:
+        beam_grad = torch.zeros_like(beam)
+    if sky_grad is not None:
+        _dev_tensor(sky_grad, torch.complex128, plan.device, "sky_grad", tuple(sky.shape))
+    if beam_grad is not None:
+        _dev_tensor(beam_grad, torch.complex128, plan.device, "beam_grad", tuple(beam.shape))
+    plan._sync_stream()
+    check(_lib.load().adjoint_tod(plan.ptr, _ptr(theta), _ptr(phi), _ptr(psi), _ptr(tod), n, _ptr(sky),
+                                  _ptr(beam), _ptr(sky_grad) if sky_grad is not None else None,
+                                  _ptr(beam_grad) if beam_grad is not None else None, int(bool(accumulate))))
+    return sky_grad, beam_grad
+
+
+def adjoint_interp(plan: Plan, theta, phi, psi, tod, maps_bar=None):
+    """Transpose of interp_tod: the adjoint cube [R, nphi, K+1] complex128."""
+    n = _ptg(plan, theta, phi, psi)
+    _dev_tensor(tod, torch.float64, plan.device, "tod", (n,))
+    if maps_bar is None:
+        maps_bar = torch.empty(plan.maps_shape(), dtype=torch.complex128, device=theta.device)
+    _dev_tensor(maps_bar, torch.complex128, plan.device, "maps_bar", plan.maps_shape())
+    plan._sync_stream()
+    check(_lib.load().adjoint_interp(plan.ptr, _ptr(theta), _ptr(phi), _ptr(psi), _ptr(tod), n, _ptr(maps_bar)))
+    return maps_bar
+
+
+def adjoint_synth(plan: Plan, maps_bar, sky, beam, sky_grad=None, beam_grad=None, accumulate=False):
+    """Transpose of synth_spin_maps followed by the sky x beam products."""
+    sky, beam = _sky_beam(plan, sky, beam)
+    _dev_tensor(maps_bar, torch.complex128, plan.device, "maps_bar", plan.maps_shape())
+    if sky_grad is None:
+        sky_grad = torch.zeros_like(sky)
+    if beam_grad is None:
+        beam_grad = torch.zeros_like(beam)
+    plan._sync_stream()
+    check(_lib.load().adjoint_synth(plan.ptr, _ptr(maps_bar), _ptr(sky), _ptr(beam), _ptr(sky_grad),
+                                    _ptr(beam_grad), int(bool(accumulate))))
+    return sky_grad, beam_grad
+
+
+def tod_from_host(plan: Plan, sky, beam, theta, phi, psi):
+    """End-to-end call from host arrays: copies the inputs to the device (from
+    pinned memory when given pinned tensors), builds the cube, interpolates and
+    copies the TOD back.  Returns a host float64 tensor."""
+    dev = torch.device("cuda", plan.device)
+
+    def up(x, dtype):
+        t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x))
+        return t.to(device=dev, dtype=dtype, non_blocking=True)
+    sky_d, beam_d = up(sky, torch.complex128), up(beam, torch.complex128)
+    th, ph, ps = up(theta, torch.float64), up(phi, torch.float64), up(psi, torch.float64)
+    maps = synth_spin_maps(plan, sky_d, beam_d)
+    tod = interp_tod(plan, maps, th, ph, ps)
+    out = torch.empty(tod.shape, dtype=torch.float64, pin_memory=True)
+    out.copy_(tod, non_blocking=True)
+    torch.cuda.current_stream(plan.device).synchronize()
+    return out

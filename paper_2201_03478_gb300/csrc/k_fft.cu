@@ -1,0 +1,228 @@
+// k_fft.cu -- the phi direction of the cube (Sect. 2.1, step 1 of the
+// two-step algorithm: the synthesis along each ring) and its transpose.
+//
+// Synthesis (one CTA per (ring r, k)):
+//   H(q)  = sum_{m = q mod nphi, |m| <= L} G_k(r, m)     (exact alias folding)
+//   F_k(r, phi_j) = sum_q H(q) e^{+2 pi i q j / nphi}    (inverse DFT)
+// written to maps[r][j][k].
+// Transpose (one CTA per (ring r, k)):
+//   X(q) = sum_j Fbar_k(r, j) e^{-2 pi i q j / nphi},   Ghat_k(r, m) = X(m mod nphi).
+//
+// The DFT is a self-sorting (Stockham) mixed-radix FFT with radices 4, 2, 3, 5
+// entirely in shared memory, twiddles from a table e^{+2 pi i j/nphi} built in
+// long double on the host.  Each pass computes, for butterfly t in [0, N/R):
+//   kk = t mod Ns,  v_q = x[t + q N/R] w^{s q kk N/(Ns R)},  v = DFT_R(v),
+//   y[(t div Ns) Ns R + kk + q Ns] = v_q,  Ns <- Ns R.
+#include "sl_internal.cuh"
+
+namespace sl {
+
+template <typename T> struct CplxOf;
+template <> struct CplxOf<double> { using type = double2; };
+template <> struct CplxOf<float> { using type = float2; };
+
+template <typename C> __device__ __forceinline__ C mk(double x, double y);
+template <> __device__ __forceinline__ double2 mk<double2>(double x, double y) { return make_double2(x, y); }
+template <> __device__ __forceinline__ float2 mk<float2>(double x, double y) { return make_float2((float)x, (float)y); }
+
+template <typename C> __device__ __forceinline__ C add(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C sub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C> __device__ __forceinline__ C mulc(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+// multiply by -i (FWD) or +i (inverse)
+template <typename C, bool INV> __device__ __forceinline__ C rot(C a) {
+    C r;
+    if (INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+    return r;
+}
+template <typename C> __device__ __forceinline__ C scal(C a, double s) {
+    C r;
+    r.x = a.x * s;
+    r.y = a.y * s;
+    return r;
+}
+
+// cos/sin of 2 pi/3, 2 pi/5, 4 pi/5 (from their closed forms)
+constexpr double kS3 = 0.86602540378443864676;   // sqrt(3)/2
+constexpr double kC51 = 0.30901699437494742410;  // (sqrt(5)-1)/4
+constexpr double kS51 = 0.95105651629515357212;
+constexpr double kC52 = -0.80901699437494742410;
+constexpr double kS52 = 0.58778525229247312917;
+
+template <typename C, bool INV>
+__device__ __forceinline__ void dft_small(int R, C *v) {
+    if (R == 2) {
+        C a = v[0], b = v[1];
+        v[0] = add(a, b);
+        v[1] = sub(a, b);
+    } else if (R == 4) {
+        C s02 = add(v[0], v[2]), d02 = sub(v[0], v[2]);
+        C s13 = add(v[1], v[3]), d13 = rot<C, INV>(sub(v[1], v[3]));
+        v[0] = add(s02, s13);
+        v[2] = sub(s02, s13);
+        v[1] = add(d02, d13);
+        v[3] = sub(d02, d13);
+    } else if (R == 3) {
+        C t1 = add(v[1], v[2]);
+        C t2 = rot<C, INV>(scal(sub(v[1], v[2]), kS3));
+        C a = sub(v[0], scal(t1, 0.5));
+        v[0] = add(v[0], t1);
+        v[1] = add(a, t2);
+        v[2] = sub(a, t2);
+    } else {  // 5
+        C t1 = add(v[1], v[4]), t2 = add(v[2], v[3]);
+        C t3 = sub(v[1], v[4]), t4 = sub(v[2], v[3]);
+        C a1 = add(v[0], add(scal(t1, kC51), scal(t2, kC52)));
+        C a2 = add(v[0], add(scal(t1, kC52), scal(t2, kC51)));
+        C b1 = rot<C, INV>(add(scal(t3, kS51), scal(t4, kS52)));
+        C b2 = rot<C, INV>(sub(scal(t3, kS52), scal(t4, kS51)));
+        v[0] = add(v[0], add(t1, t2));
+        v[1] = add(a1, b1);
+        v[4] = sub(a1, b1);
+        v[2] = add(a2, b2);
+        v[3] = sub(a2, b2);
+    }
+}
+
+struct Radices {
+    int n;
+    int r[kMaxRadices];
+};
+
+template <typename C, bool INV, int R>
+__device__ __forceinline__ void fft_pass(const C *__restrict__ src, C *__restrict__ dst, int N, int Ns,
+                                         const C *__restrict__ tw) {
+    const int NR = N / R;
+    const int stride = N / (Ns * R);
+    for (int t = threadIdx.x; t < NR; t += blockDim.x) {
+        const int kk = t % Ns;
+        C v[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            C x = src[t + q * NR];
+            if (Ns > 1 && q > 0) {
+                C w = tw[kk * stride * q];
+                if (!INV) w.y = -w.y;
+                x = mulc(x, w);
+            }
+            v[q] = x;
+        }
+        dft_small<C, INV>(R, v);
+        const int base = (t / Ns) * Ns * R + kk;
+#pragma unroll
+        for (int q = 0; q < R; ++q) dst[base + q * Ns] = v[q];
+    }
+}
+
+// Transforms buf0 (length N) in shared memory, using buf1 as the second
+// buffer; returns the buffer holding the result.
+template <typename C, bool INV>
+__device__ C *fft_smem(C *buf0, C *buf1, int N, const Radices &rad, const C *__restrict__ tw) {
+    C *src = buf0, *dst = buf1;
+    int Ns = 1;
+    for (int pass = 0; pass < rad.n; ++pass) {
+        const int R = rad.r[pass];
+        switch (R) {
+            case 4: fft_pass<C, INV, 4>(src, dst, N, Ns, tw); break;
+            case 2: fft_pass<C, INV, 2>(src, dst, N, Ns, tw); break;
+            case 3: fft_pass<C, INV, 3>(src, dst, N, Ns, tw); break;
+            default: fft_pass<C, INV, 5>(src, dst, N, Ns, tw); break;
+        }
+        __syncthreads();
+        C *tmp = src;
+        src = dst;
+        dst = tmp;
+        Ns *= R;
+    }
+    return src;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ringfft_synth(int L, int K, int R, int N, Radices rad,
+                                                       const typename CplxOf<T>::type *__restrict__ G,
+                                                       const typename CplxOf<T>::type *__restrict__ tw,
+                                                       typename CplxOf<T>::type *__restrict__ maps) {
+    using C = typename CplxOf<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf0 = reinterpret_cast<C *>(smem_raw);
+    C *buf1 = buf0 + N;
+    const int k = blockIdx.x % (K + 1);
+    const int r = blockIdx.x / (K + 1);
+    const C *g = G + ((int64_t)k * R + r) * (2 * L + 1);
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+        // smallest m >= -L with m = q (mod N)
+        int m = q - N * ((q + L) / N);
+        C acc = mk<C>(0.0, 0.0);
+        for (; m <= L; m += N) acc = add(acc, g[m + L]);
+        buf0[q] = acc;
+    }
+    __syncthreads();
+    const C *res = fft_smem<C, true>(buf0, buf1, N, rad, tw);
+    C *out = maps + (int64_t)r * N * (K + 1) + k;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) out[(int64_t)j * (K + 1)] = res[j];
+}
+
+__global__ void __launch_bounds__(256) k_ringdft_adjoint(int L, int K, int R, int N, Radices rad,
+                                                         const double2 *__restrict__ fbar,
+                                                         const double2 *__restrict__ tw,
+                                                         double2 *__restrict__ Ghat) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *buf0 = reinterpret_cast<double2 *>(smem_raw);
+    double2 *buf1 = buf0 + N;
+    const int k = blockIdx.x % (K + 1);
+    const int r = blockIdx.x / (K + 1);
+    const double2 *in = fbar + (int64_t)r * N * (K + 1) + k;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) buf0[j] = in[(int64_t)j * (K + 1)];
+    __syncthreads();
+    const double2 *res = fft_smem<double2, false>(buf0, buf1, N, rad, tw);
+    double2 *g = Ghat + ((int64_t)k * R + r) * (2 * L + 1);
+    for (int m = -L + (int)threadIdx.x; m <= L; m += blockDim.x) {
+        int q = m % N;
+        if (q < 0) q += N;
+        g[m + L] = res[q];
+    }
+}
+
+static Radices radices_of(const sl_plan *p) {
+    Radices r;
+    r.n = p->nradix;
+    for (int i = 0; i < p->nradix; ++i) r.r[i] = p->radices[i];
+    return r;
+}
+
+sl_status launch_ringfft_synth(sl_plan *p, void *maps) {
+    const unsigned nblk = (unsigned)((p->K + 1) * p->R);
+    int slot;
+    if (p->precision == SL_FP64) {
+        const size_t sm = 2 * (size_t)p->nphi * sizeof(double2);
+        cudaFuncSetAttribute(k_ringfft_synth<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        slot = timing_begin(p, "ringfft_f64");
+        k_ringfft_synth<double><<<nblk, 256, sm, p->stream>>>(p->L, p->K, p->R, p->nphi, radices_of(p),
+                                                              (const double2 *)p->d_G, p->d_tw64, (double2 *)maps);
+    } else {
+        const size_t sm = 2 * (size_t)p->nphi * sizeof(float2);
+        cudaFuncSetAttribute(k_ringfft_synth<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        slot = timing_begin(p, "ringfft_f32");
+        k_ringfft_synth<float><<<nblk, 256, sm, p->stream>>>(p->L, p->K, p->R, p->nphi, radices_of(p),
+                                                             (const float2 *)p->d_G, p->d_tw32, (float2 *)maps);
+    }
+    timing_end(p, slot);
+    return cuda_check(cudaGetLastError(), "k_ringfft_synth launch");
+}
+
+sl_status launch_ringdft_adjoint(sl_plan *p, const double2 *fbar) {
+    const unsigned nblk = (unsigned)((p->K + 1) * p->R);
+    const size_t sm = 2 * (size_t)p->nphi * sizeof(double2);
+    cudaFuncSetAttribute(k_ringdft_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int slot = timing_begin(p, "ringdft_adj");
+    k_ringdft_adjoint<<<nblk, 256, sm, p->stream>>>(p->L, p->K, p->R, p->nphi, radices_of(p), fbar, p->d_tw64,
+                                                    p->d_Gadj);
+    timing_end(p, slot);
+    return cuda_check(cudaGetLastError(), "k_ringdft_adjoint launch");
+}
+
+}  // namespace sl

@@ -1,0 +1,371 @@
+// k_interp.cu -- step 2 of the two-step algorithm (Sect. 2.1): the cube is
+// evaluated at each pointing and summed over k with the conjugate-pair phases
+//
+//   c = Re S_0 + 2 sum_{k>=1} Re(e^{ik psi} S_k),   S_k = sum_{a,b} wt_a wp_b F_k(row a, col b),
+//
+// plus its transpose.  The paper leaves the interpolation scheme open; here it
+// is separable 4-point Lagrange: wt from the actual (extended) ring
+// colatitudes, wp for uniform phi nodes j-1..j+2 (periodic).  Stencil rows
+// beyond a pole are ghost rows: row -1-q is ring q and row R+q is ring R-1-q,
+// read at phi + pi with the factor (-1)^k (d^l_{mk}(-t) = (-1)^{m-k} d^l_{mk}(t)).
+//
+// Forward: one thread per sample, samples visited in tile-sorted order so that
+// neighbouring threads read neighbouring cube nodes.
+// Adjoint: one CTA per work item (<= kChunk samples of one tile); the tile's
+// cube nodes (with a 3-node halo) are accumulated in shared memory, each warp
+// owning a disjoint set of k so that no two threads update the same word, and
+// the tile is flushed to the global adjoint cube with atomic adds.
+#include "sl_internal.cuh"
+
+namespace sl {
+
+constexpr int kChunkA = 2048;   // must equal kChunk in k_sort.cu
+
+struct Stencil {
+    int off[16];       // element offsets (ring * nphi + col) * (K+1) of the 16 nodes
+    double w[16];      // wt_a * wp_b
+    unsigned ghost;    // bit a set if row a is a ghost row
+};
+
+__device__ __forceinline__ void make_stencil(const InterpGeom &g, double th, double ph, Stencil &st,
+                                             double &dth0, double &fph) {
+    const int i = locate_row(g, th);
+    double f;
+    const int j = locate_col(g, ph, f);
+    const double *te = g.ring_ext + g.half + i - 1;   // rows i-1 .. i+2
+    const double d0 = th - te[0], d1 = th - te[1], d2 = th - te[2], d3 = th - te[3];
+    const double *wd = g.wden + (size_t)(i + 1) * 4;
+    const double p01 = d0 * d1, p23 = d2 * d3;
+    const double wt[4] = {wd[0] * d1 * p23, wd[1] * d0 * p23, wd[2] * p01 * d3, wd[3] * p01 * d2};
+    const double a = f + 1.0, c = f - 1.0, d = f - 2.0;
+    const double cd = c * d, ab = a * f;
+    const double wp[4] = {-f * cd * (1.0 / 6.0), a * cd * 0.5, -ab * d * 0.5, ab * c * (1.0 / 6.0)};
+    const int K1 = g.K + 1;
+    st.ghost = 0;
+#pragma unroll
+    for (int ra = 0; ra < 4; ++ra) {
+        int row = i - 1 + ra, ring = row, shift = 0;
+        if (row < 0) { ring = -1 - row; shift = g.nphi / 2; st.ghost |= 1u << ra; }
+        else if (row >= g.R) { ring = 2 * g.R - 1 - row; shift = g.nphi / 2; st.ghost |= 1u << ra; }
+#pragma unroll
+        for (int cb = 0; cb < 4; ++cb) {
+            int col = j - 1 + cb + shift;
+            col = (col < 0) ? col + g.nphi : (col >= g.nphi ? col - g.nphi : col);
+            st.off[ra * 4 + cb] = (ring * g.nphi + col) * K1;
+            st.w[ra * 4 + cb] = wt[ra] * wp[cb];
+        }
+    }
+    dth0 = d0;
+    fph = f;
+}
+
+// ------------------------------------------------------------------ forward FP64
+__global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const double2 *__restrict__ maps,
+                                                    const double *__restrict__ theta, const double *__restrict__ phi,
+                                                    const double *__restrict__ psi, const unsigned *__restrict__ perm,
+                                                    int64_t n, double *__restrict__ tod) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned s = perm[t];
+        Stencil st;
+        double dd, ff;
+        make_stencil(g, theta[s], phi[s], st, dd, ff);
+        double sp, cp;
+        sincos(psi[s], &sp, &cp);
+        const double c2 = 2.0 * cp;
+        // cos(k psi), sin(k psi) by the Chebyshev three-term recurrence
+        double ck = 1.0, sk = 0.0, ckm = cp, skm = -sp;
+        double acc = 0.0;
+        for (int k = 0; k <= g.K; ++k) {
+            double sr = 0.0, si = 0.0;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const double2 v = __ldg(maps + st.off[q] + k);
+                sr = fma(st.w[q], v.x, sr);
+                si = fma(st.w[q], v.y, si);
+            }
+            if (k == 0) {
+                acc = sr;
+            } else {
+                acc = fma(2.0 * ck, sr, acc);
+                acc = fma(-2.0 * sk, si, acc);
+            }
+            const double cn = fma(c2, ck, -ckm), sn = fma(c2, sk, -skm);
+            ckm = ck;
+            skm = sk;
+            ck = cn;
+            sk = sn;
+            if (st.ghost) {   // (-1)^k on ghost rows: flip their weights between k and k+1
+#pragma unroll
+                for (int ra = 0; ra < 4; ++ra)
+                    if (st.ghost & (1u << ra))
+#pragma unroll
+                        for (int cb = 0; cb < 4; ++cb) st.w[ra * 4 + cb] = -st.w[ra * 4 + cb];
+            }
+        }
+        tod[s] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ forward FP32 maps
+// FP64: pointing -> (row, column, offsets), psi range reduction, final value.
+// FP32: weights (from FP64 offsets), the e^{ik psi} ladder and the stencil sums.
+__global__ void __launch_bounds__(256) k_interp_f32(const InterpGeom g, const float2 *__restrict__ maps,
+                                                    const double *__restrict__ theta, const double *__restrict__ phi,
+                                                    const double *__restrict__ psi, const unsigned *__restrict__ perm,
+                                                    int64_t n, double *__restrict__ tod) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned s = perm[t];
+        const double th = theta[s], ph = phi[s];
+        const int i = locate_row(g, th);
+        double fd;
+        const int j = locate_col(g, ph, fd);
+        const double *te = g.ring_ext + g.half + i - 1;
+        const float d0 = (float)(th - te[0]), d1 = (float)(th - te[1]), d2 = (float)(th - te[2]),
+                    d3 = (float)(th - te[3]);
+        const double *wd = g.wden + (size_t)(i + 1) * 4;
+        const float p01 = d0 * d1, p23 = d2 * d3;
+        const float wt[4] = {(float)wd[0] * d1 * p23, (float)wd[1] * d0 * p23, (float)wd[2] * p01 * d3,
+                             (float)wd[3] * p01 * d2};
+        const float f = (float)fd;
+        const float a = f + 1.f, c = f - 1.f, d = f - 2.f;
+        const float cd = c * d, ab = a * f;
+        const float wp[4] = {-f * cd * (1.f / 6.f), a * cd * 0.5f, -ab * d * 0.5f, ab * c * (1.f / 6.f)};
+        const int K1 = g.K + 1;
+        int off[16];
+        float w[16];
+        unsigned ghost = 0;
+#pragma unroll
+        for (int ra = 0; ra < 4; ++ra) {
+            int row = i - 1 + ra, ring = row, shift = 0;
+            if (row < 0) { ring = -1 - row; shift = g.nphi / 2; ghost |= 1u << ra; }
+            else if (row >= g.R) { ring = 2 * g.R - 1 - row; shift = g.nphi / 2; ghost |= 1u << ra; }
+#pragma unroll
+            for (int cb = 0; cb < 4; ++cb) {
+                int col = j - 1 + cb + shift;
+                col = (col < 0) ? col + g.nphi : (col >= g.nphi ? col - g.nphi : col);
+                off[ra * 4 + cb] = (ring * g.nphi + col) * K1;
+                w[ra * 4 + cb] = wt[ra] * wp[cb];
+            }
+        }
+        // psi reduced to [-pi, pi] in FP64, then an FP32 ladder z^k
+        const double ps = psi[s];
+        const float pr = (float)(ps - 6.283185307179586 * rint(ps * 0.15915494309189535));
+        float sz, cz;
+        sincosf(pr, &sz, &cz);
+        float zr = 1.f, zi = 0.f, acc1 = 0.f, acc0 = 0.f;
+        for (int k = 0; k <= g.K; ++k) {
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float2 v = __ldg(maps + off[q] + k);
+                sr = fmaf(w[q], v.x, sr);
+                si = fmaf(w[q], v.y, si);
+            }
+            if (k == 0) acc0 = sr;
+            else acc1 += zr * sr - zi * si;
+            const float nr = zr * cz - zi * sz, ni = zr * sz + zi * cz;
+            zr = nr;
+            zi = ni;
+            if (ghost) {
+#pragma unroll
+                for (int ra = 0; ra < 4; ++ra)
+                    if (ghost & (1u << ra))
+#pragma unroll
+                        for (int cb = 0; cb < 4; ++cb) w[ra * 4 + cb] = -w[ra * 4 + cb];
+            }
+        }
+        tod[s] = (double)acc0 + 2.0 * (double)acc1;
+    }
+}
+
+// ------------------------------------------------------------------ adjoint
+// maps_bar_k(node) += y wt_a wp_b sigma_{a,k} eps_k e^{-ik psi},  eps_0 = 1, eps_k = 2.
+struct AdjArgs {
+    InterpGeom g;
+    const double *theta, *phi, *psi, *y;
+    const unsigned *perm, *start, *chunk_off;
+    int ntiles;
+    double2 *fbar;
+};
+
+constexpr int kNB = 64;   // samples staged per batch
+
+__global__ void k_interp_adjoint(const AdjArgs A) {
+    const InterpGeom &g = A.g;
+    const int K1 = g.K + 1;
+    const int TC = g.tile_cols;
+    const int tw = TC + 3;                  // smem tile columns
+    const int th_rows = kTileRows + 3;      // smem tile rows
+    const int nnode = th_rows * tw;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *acc = reinterpret_cast<double2 *>(smem_raw);            // [nnode][K1]
+    double2 *P = acc + (size_t)nnode * K1;                            // [kNB][K1]
+    double *W = reinterpret_cast<double *>(P + (size_t)kNB * K1);     // [kNB][16]
+    int *LOC = reinterpret_cast<int *>(W + (size_t)kNB * 16);         // [kNB] node index of (row i-1, col j-1)
+
+    const unsigned nchunks = A.chunk_off[A.ntiles];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int q = lane & 15, kpar = lane >> 4;
+    const int qa = q >> 2, qb = q & 3;
+
+    for (int e = threadIdx.x; e < nnode * K1; e += blockDim.x) acc[e] = make_double2(0.0, 0.0);
+
+    for (unsigned v = blockIdx.x; v < nchunks; v += gridDim.x) {
+        // tile of this work item: largest t with chunk_off[t] <= v
+        int lo = 0, hi = A.ntiles - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (A.chunk_off[mid] <= v) lo = mid; else hi = mid - 1;
+        }
+        const int tile = lo;
+        const unsigned c = v - A.chunk_off[tile];
+        const unsigned s_beg = A.start[tile] + c * kChunkA;
+        const unsigned s_end = min(A.start[tile + 1], s_beg + kChunkA);
+        const int tr = tile / g.ntc, tcol = tile % g.ntc;
+        const int rowlo = tr * kTileRows - 2;   // stencil rows i-1..i+2, base row i >= tr*4-1
+        const int collo = tcol * TC - 1;
+        __syncthreads();
+        for (unsigned b0 = s_beg; b0 < s_end; b0 += kNB) {
+            const int nb = (int)min((unsigned)kNB, s_end - b0);
+            // phase A: per-sample weights, node location and phases
+            if ((int)threadIdx.x < nb) {
+                const unsigned s = A.perm[b0 + threadIdx.x];
+                const double th = A.theta[s];
+                const int i = locate_row(g, th);
+                double f;
+                const int j = locate_col(g, A.phi[s], f);
+                const double *te = g.ring_ext + g.half + i - 1;
+                const double d0 = th - te[0], d1 = th - te[1], d2 = th - te[2], d3 = th - te[3];
+                const double *wd = g.wden + (size_t)(i + 1) * 4;
+                const double p01 = d0 * d1, p23 = d2 * d3;
+                const double wt[4] = {wd[0] * d1 * p23, wd[1] * d0 * p23, wd[2] * p01 * d3, wd[3] * p01 * d2};
+                const double a = f + 1.0, cc = f - 1.0, d = f - 2.0;
+                const double cd = cc * d, ab = a * f;
+                const double wp[4] = {-f * cd * (1.0 / 6.0), a * cd * 0.5, -ab * d * 0.5, ab * cc * (1.0 / 6.0)};
+                double *ws = W + threadIdx.x * 16;
+#pragma unroll
+                for (int ra = 0; ra < 4; ++ra)
+#pragma unroll
+                    for (int cb = 0; cb < 4; ++cb) ws[ra * 4 + cb] = wt[ra] * wp[cb];
+                LOC[threadIdx.x] = (i - 1 - rowlo) * tw + (j - 1 - collo);
+                double sp, cp;
+                sincos(A.psi[s], &sp, &cp);
+                const double y = A.y[s], c2 = 2.0 * cp;
+                double ck = 1.0, sk = 0.0, ckm = cp, skm = -sp;
+                double2 *Ps = P + (size_t)threadIdx.x * K1;
+                for (int k = 0; k <= g.K; ++k) {
+                    const double sc = (k == 0) ? y : 2.0 * y;
+                    Ps[k] = make_double2(sc * ck, -sc * sk);     // eps_k y e^{-ik psi}
+                    const double cn = fma(c2, ck, -ckm), sn = fma(c2, sk, -skm);
+                    ckm = ck;
+                    skm = sk;
+                    ck = cn;
+                    sk = sn;
+                }
+            }
+            __syncthreads();
+            // phase B: warp w owns k-pairs w, w + nwarps, ...; lane = (node q, k parity)
+            for (int kp = warp; 2 * kp <= g.K; kp += nwarps) {
+                const int kk = 2 * kp + kpar;
+                const bool live = kk <= g.K;
+                for (int sidx = 0; sidx < nb; ++sidx) {
+                    if (live) {
+                        const int node = LOC[sidx] + qa * tw + qb;
+                        const double w = W[sidx * 16 + q];
+                        const double2 ph = P[(size_t)sidx * K1 + kk];
+                        double2 &dst = acc[(size_t)node * K1 + kk];
+                        double2 cur = dst;
+                        cur.x = fma(w, ph.x, cur.x);
+                        cur.y = fma(w, ph.y, cur.y);
+                        dst = cur;
+                    }
+                    // consecutive samples may share nodes: order this warp's updates
+                    __syncwarp(0xffffffffu);
+                }
+            }
+            __syncthreads();
+        }
+        // flush the tile (ghost rows fold onto their ring at phi + pi with (-1)^k)
+        for (int e = threadIdx.x; e < nnode * K1; e += blockDim.x) {
+            const double2 val = acc[e];
+            if (val.x == 0.0 && val.y == 0.0) continue;
+            acc[e] = make_double2(0.0, 0.0);
+            const int kk = e % K1;
+            const int node = e / K1;
+            const int row = rowlo + node / tw;
+            int col = collo + node % tw;
+            if (row < -2 || row > g.R + 1) continue;
+            int ring = row;
+            double sg = 1.0;
+            if (row < 0 || row >= g.R) {
+                ring = (row < 0) ? -1 - row : 2 * g.R - 1 - row;
+                col += g.nphi / 2;
+                if (kk & 1) sg = -1.0;
+            }
+            col %= g.nphi;
+            if (col < 0) col += g.nphi;
+            double2 *o = A.fbar + ((int64_t)ring * g.nphi + col) * K1 + kk;
+            atomicAdd(&o->x, sg * val.x);
+            atomicAdd(&o->y, sg * val.y);
+        }
+    }
+}
+
+static unsigned grid_for(int64_t n, int bs) {
+    int64_t b = (n + bs - 1) / bs;
+    const int64_t cap = 152 * 32;
+    return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+sl_status launch_interp(sl_plan *p, const void *maps, const double *theta, const double *phi,
+                        const double *psi, int64_t n, double *tod) {
+    int slot;
+    if (p->precision == SL_FP64) {
+        slot = timing_begin(p, "interp_f64");
+        k_interp_f64<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const double2 *)maps, theta, phi, psi,
+                                                             p->d_perm, n, tod);
+    } else {
+        slot = timing_begin(p, "interp_f32");
+        k_interp_f32<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const float2 *)maps, theta, phi, psi,
+                                                             p->d_perm, n, tod);
+    }
+    timing_end(p, slot);
+    return cuda_check(cudaGetLastError(), "k_interp launch");
+}
+
+sl_status launch_interp_adjoint(sl_plan *p, const double *theta, const double *phi, const double *psi,
+                                const double *tod, int64_t n, double2 *fbar) {
+    AdjArgs a;
+    a.g = p->geom;
+    a.theta = theta;
+    a.phi = phi;
+    a.psi = psi;
+    a.y = tod;
+    a.perm = p->d_perm;
+    a.start = p->d_hist;
+    a.chunk_off = p->d_chunk_off;
+    a.ntiles = p->ntiles;
+    a.fbar = fbar;
+    const int K1 = p->K + 1;
+    const int nnode = (kTileRows + 3) * (p->geom.tile_cols + 3);
+    const size_t sm = (size_t)nnode * K1 * sizeof(double2) + (size_t)kNB * K1 * sizeof(double2) +
+                      (size_t)kNB * 16 * sizeof(double) + (size_t)kNB * sizeof(int);
+    int nwarps = (K1 + 1) / 2;
+    if (nwarps < 2) nwarps = 2;
+    if (nwarps > 16) nwarps = 16;
+    cudaError_t e = cudaFuncSetAttribute(k_interp_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return cuda_check(e, "k_interp_adjoint smem attribute");
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_adjoint, 32 * nwarps, sm);
+    if (per_sm < 1) per_sm = 1;
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
+    int slot = timing_begin(p, "interp_adj");
+    k_interp_adjoint<<<(unsigned)(nsm * per_sm), 32 * nwarps, sm, p->stream>>>(a);
+    timing_end(p, slot);
+    (void)n;
+    return cuda_check(cudaGetLastError(), "k_interp_adjoint launch");
+}
+
+}  // namespace sl

@@ -1,0 +1,495 @@
+// plan.cu -- the C ABI of libsidelobe.so (include/sidelobe.h): argument
+// validation, plan geometry, scratch management, the call sequences of the
+// public entry points and per-kernel timing.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "sl_internal.cuh"
+
+namespace sl {
+
+static thread_local char g_err[512] = "";
+
+sl_status set_error(sl_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+sl_status cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return SL_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return set_error(SL_ERR_NOMEM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return set_error(SL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ timing
+int timing_begin(sl_plan *p, const char *name) {
+    if (!p->timing) return -1;
+    int idx = -1;
+    for (size_t i = 0; i < p->timers.size(); ++i)
+        if (p->timers[i].name == name) idx = (int)i;
+    if (idx < 0) {
+        p->timers.push_back(KernelTimer{name, 0, 0.0});
+        idx = (int)p->timers.size() - 1;
+    }
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return -1; }
+    cudaEventRecord(a, p->stream);
+    p->pending_ev.push_back(a);
+    p->pending_ev.push_back(b);
+    p->pending_idx.push_back(idx);
+    return (int)p->pending_idx.size() - 1;
+}
+
+void timing_end(sl_plan *p, int slot) {
+    if (slot < 0) return;
+    cudaEventRecord(p->pending_ev[2 * slot + 1], p->stream);
+}
+
+static void timing_flush(sl_plan *p) {
+    if (p->pending_idx.empty()) return;
+    cudaStreamSynchronize(p->stream);
+    for (size_t i = 0; i < p->pending_idx.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p->pending_ev[2 * i], p->pending_ev[2 * i + 1]) == cudaSuccess) {
+            p->timers[p->pending_idx[i]].launches += 1;
+            p->timers[p->pending_idx[i]].total_ms += ms;
+        }
+    }
+    for (cudaEvent_t e : p->pending_ev) cudaEventDestroy(e);
+    p->pending_ev.clear();
+    p->pending_idx.clear();
+}
+
+// ------------------------------------------------------------------ allocation
+static sl_status dalloc(sl_plan *p, void **ptr, size_t bytes, const char *what) {
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return set_error(SL_ERR_NOMEM, "cudaMalloc(%zu bytes) for %s failed: %s", bytes, what,
+                         cudaGetErrorString(e));
+    }
+    p->bytes_held += (int64_t)bytes;
+    return SL_OK;
+}
+
+template <typename T>
+static sl_status dalloc_t(sl_plan *p, T **ptr, size_t count, const char *what) {
+    void *v = nullptr;
+    sl_status st = dalloc(p, &v, count * sizeof(T), what);
+    *ptr = (T *)v;
+    return st;
+}
+
+static void dfree(void *ptr) {
+    if (ptr) cudaFree(ptr);
+}
+
+static sl_status ensure_sort_capacity(sl_plan *p, int64_t n) {
+    if (n <= p->sort_cap) return SL_OK;
+    cudaStreamSynchronize(p->stream);
+    dfree(p->d_keys);
+    dfree(p->d_perm);
+    p->bytes_held -= 2 * p->sort_cap * (int64_t)sizeof(unsigned);
+    p->d_keys = p->d_perm = nullptr;
+    p->sort_cap = 0;
+    sl_status st = dalloc_t(p, &p->d_keys, (size_t)n, "sort keys");
+    if (st != SL_OK) return st;
+    st = dalloc_t(p, &p->d_perm, (size_t)n, "sort permutation");
+    if (st != SL_OK) return st;
+    p->sort_cap = n;
+    return SL_OK;
+}
+
+static sl_status ensure_adjoint_scratch(sl_plan *p) {
+    sl_status st;
+    if (!p->d_Abar) {
+        st = dalloc_t(p, &p->d_Abar, (size_t)(p->K + 1) * (2 * p->L + 1) * (p->L + 1), "adjoint A");
+        if (st != SL_OK) return st;
+    }
+    if (!p->d_Gadj) {
+        if (p->precision == SL_FP64) {
+            p->d_Gadj = (double2 *)p->d_G;
+        } else {
+            st = dalloc_t(p, &p->d_Gadj, (size_t)(p->K + 1) * p->R * (2 * p->L + 1), "adjoint G");
+            if (st != SL_OK) return st;
+        }
+    }
+    return SL_OK;
+}
+
+static sl_status ensure_fbar(sl_plan *p) {
+    if (p->d_Fbar) return SL_OK;
+    return dalloc_t(p, &p->d_Fbar, (size_t)p->R * p->nphi * (p->K + 1), "adjoint cube");
+}
+
+// ------------------------------------------------------------------ validation
+static bool factor_235(int n, int *rad, int *nrad) {
+    int k = 0;
+    while (n % 4 == 0 && k < kMaxRadices) { rad[k++] = 4; n /= 4; }
+    while (n % 2 == 0 && k < kMaxRadices) { rad[k++] = 2; n /= 2; }
+    while (n % 3 == 0 && k < kMaxRadices) { rad[k++] = 3; n /= 3; }
+    while (n % 5 == 0 && k < kMaxRadices) { rad[k++] = 5; n /= 5; }
+    *nrad = k;
+    return n == 1;
+}
+
+static sl_status validate(const sl_plan_desc *d, int *rad, int *nrad) {
+    if (!d) return set_error(SL_ERR_ARG, "desc is NULL");
+    if (d->lmax < 1 || d->lmax > 16384) return set_error(SL_ERR_ARG, "lmax=%d outside [1, 16384]", d->lmax);
+    if (d->kmax < 0 || d->kmax > d->lmax || d->kmax > kMaxK)
+        return set_error(SL_ERR_ARG, "kmax=%d outside [0, min(lmax, %d)]", d->kmax, kMaxK);
+    if (d->ncomp != 1 && d->ncomp != 3) return set_error(SL_ERR_ARG, "ncomp=%d (must be 1 or 3)", d->ncomp);
+    int p = d->interp_order ? d->interp_order : 4;
+    if (p != 4) return set_error(SL_ERR_UNSUPPORTED, "interp_order=%d (only 4 is built)", d->interp_order);
+    if (d->nrings < 4 || d->nrings > 65536) return set_error(SL_ERR_ARG, "nrings=%d outside [4, 65536]", d->nrings);
+    if (!d->ring_theta) return set_error(SL_ERR_ARG, "ring_theta is NULL");
+    const double *t = d->ring_theta;
+    for (int r = 0; r < d->nrings; ++r) {
+        if (!(t[r] > 0.0 && t[r] < M_PI)) return set_error(SL_ERR_ARG, "ring_theta[%d]=%g not in (0, pi)", r, t[r]);
+        if (r > 0 && !(t[r] > t[r - 1])) return set_error(SL_ERR_ARG, "ring_theta not strictly ascending at %d", r);
+        double mir = M_PI - t[d->nrings - 1 - r];
+        if (fabs(mir - t[r]) > 1e-12) return set_error(SL_ERR_ARG, "ring_theta not N/S symmetric at ring %d", r);
+    }
+    if (d->nphi < 8 || d->nphi > kMaxNphi || (d->nphi & 1))
+        return set_error(SL_ERR_ARG, "nphi=%d must be even and in [8, %d]", d->nphi, kMaxNphi);
+    if (!factor_235(d->nphi, rad, nrad))
+        return set_error(SL_ERR_UNSUPPORTED, "nphi=%d has a prime factor > 5", d->nphi);
+    if (d->precision != SL_FP64 && d->precision != SL_FP32)
+        return set_error(SL_ERR_ARG, "precision=%d unknown", d->precision);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return set_error(SL_ERR_CUDA, "no CUDA device visible");
+    }
+    if (d->device < 0 || d->device >= ndev) return set_error(SL_ERR_ARG, "device=%d of %d", d->device, ndev);
+    return SL_OK;
+}
+
+}  // namespace sl
+
+using namespace sl;
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char *sl_last_error(void) { return g_err; }
+
+void plan_destroy(sl_plan *p) {
+    if (!p) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p->device);
+    cudaStreamSynchronize(p->stream);
+    for (cudaEvent_t e : p->pending_ev) cudaEventDestroy(e);
+    dfree(p->d_ring_theta);
+    dfree(p->d_xr);
+    dfree(p->d_y32);
+    dfree(p->d_ring_ext);
+    dfree(p->d_wden);
+    dfree(p->d_lut);
+    dfree(p->d_seed);
+    dfree(p->d_seed_e);
+    dfree(p->d_tw64);
+    dfree(p->d_tw32);
+    if (p->d_Gadj && (void *)p->d_Gadj != p->d_G) dfree(p->d_Gadj);
+    dfree(p->d_G);
+    dfree(p->d_Fbar);
+    dfree(p->d_Abar);
+    dfree(p->d_hist);
+    dfree(p->d_cursor);
+    dfree(p->d_chunk_off);
+    dfree(p->d_keys);
+    dfree(p->d_perm);
+    delete p;
+    cudaSetDevice(prev);
+}
+
+sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
+    if (!out) return set_error(SL_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int rad[kMaxRadices], nrad = 0;
+    sl_status st = validate(d, rad, &nrad);
+    if (st != SL_OK) return st;
+    st = cuda_check(cudaSetDevice(d->device), "cudaSetDevice");
+    if (st != SL_OK) return st;
+
+    sl_plan *p = new (std::nothrow) sl_plan();
+    if (!p) return set_error(SL_ERR_NOMEM, "host allocation of the plan failed");
+    p->L = d->lmax;
+    p->K = d->kmax;
+    p->ncomp = d->ncomp;
+    p->R = d->nrings;
+    p->nphi = d->nphi;
+    p->p = d->interp_order ? d->interp_order : 4;
+    p->precision = d->precision;
+    p->device = d->device;
+    p->stream = (cudaStream_t)d->stream;
+    p->npairs = (p->R + 1) / 2;
+    p->nalm = (int64_t)(p->L + 1) * (p->L + 2) / 2;
+    for (int i = 0; i < nrad; ++i) p->radices[i] = rad[i];
+    p->nradix = nrad;
+
+    const int R = p->R, L = p->L, K = p->K, half = p->p / 2, P = p->p;
+    const double *th = d->ring_theta;
+
+    // -------- geometry on the host in long double, then uploaded
+    std::vector<double> ring_ext(R + 2 * half), wden((size_t)(R + 1) * P), xr(p->npairs),
+        c2(p->npairs), s2(p->npairs), cs(p->npairs);
+    std::vector<float> y32(p->npairs);
+    for (int row = -half; row < R + half; ++row) {
+        double v;
+        if (row < 0) v = -th[-1 - row];
+        else if (row >= R) v = 2.0 * M_PI - th[2 * R - 1 - row];
+        else v = th[row];
+        ring_ext[row + half] = v;
+    }
+    for (int i = -1; i <= R - 1; ++i) {
+        for (int a = 0; a < P; ++a) {
+            long double ta = ring_ext[i - half + 1 + a + half], den = 1.0L;
+            for (int b = 0; b < P; ++b)
+                if (b != a) den *= ta - (long double)ring_ext[i - half + 1 + b + half];
+            wden[(size_t)(i + 1) * P + a] = (double)(1.0L / den);
+        }
+    }
+    for (int r = 0; r < p->npairs; ++r) {
+        long double t = th[r];
+        xr[r] = (double)cosl(t);
+        c2[r] = (double)cosl(t / 2);
+        s2[r] = (double)sinl(t / 2);
+        cs[r] = (double)(cosl(t / 2) * sinl(t / 2));
+        y32[r] = (float)(2.0L * sinl(t / 2) * sinl(t / 2));
+    }
+    int nlut = 4 * (R + 1);
+    std::vector<int> lut(nlut);
+    {
+        int i = -1;
+        for (int b = 0; b < nlut; ++b) {
+            double t0 = b * M_PI / nlut;
+            while (i < R - 1 && ring_ext[i + 1 + half] <= t0) ++i;
+            lut[b] = std::max(-1, i - 1);   // one row of margin against rounding of theta*scale
+        }
+    }
+    std::vector<double2> tw64(p->nphi);
+    std::vector<float2> tw32(p->nphi);
+    for (int j = 0; j < p->nphi; ++j) {
+        long double a = 2.0L * 3.14159265358979323846264338327950288L * j / p->nphi;
+        tw64[j] = make_double2((double)cosl(a), (double)sinl(a));
+        tw32[j] = make_float2((float)cosl(a), (float)sinl(a));
+    }
+
+    p->geom.R = R;
+    p->geom.nphi = p->nphi;
+    p->geom.K = K;
+    p->geom.p = P;
+    p->geom.half = half;
+    p->geom.nlut = nlut;
+    p->geom.lut_scale = nlut / M_PI;
+    p->geom.phi_scale = p->nphi / (2.0 * M_PI);
+    p->geom.tile_cols = (K <= 16) ? 32 : 16;
+    if (p->geom.tile_cols > p->nphi) p->geom.tile_cols = p->nphi;
+    p->geom.ntr = (R + 1 + kTileRows - 1) / kTileRows;
+    p->geom.ntc = (p->nphi + p->geom.tile_cols - 1) / p->geom.tile_cols;
+    p->ntiles = p->geom.ntr * p->geom.ntc;
+
+    double *d_c2 = nullptr, *d_s2 = nullptr, *d_cs = nullptr;
+#define TRY(x)                      \
+    do {                            \
+        st = (x);                   \
+        if (st != SL_OK) goto fail; \
+    } while (0)
+    TRY(dalloc_t(p, &p->d_ring_theta, R, "ring theta"));
+    TRY(dalloc_t(p, &p->d_xr, p->npairs, "ring cos"));
+    TRY(dalloc_t(p, &p->d_y32, p->npairs, "ring 1-cos"));
+    TRY(dalloc_t(p, &p->d_ring_ext, ring_ext.size(), "ring ext"));
+    TRY(dalloc_t(p, &p->d_wden, wden.size(), "lagrange denominators"));
+    TRY(dalloc_t(p, &p->d_lut, lut.size(), "ring lut"));
+    TRY(dalloc_t(p, &p->d_tw64, tw64.size(), "twiddles"));
+    TRY(dalloc_t(p, &p->d_tw32, tw32.size(), "twiddles"));
+    TRY(dalloc_t(p, &d_c2, p->npairs, "seed tmp"));
+    TRY(dalloc_t(p, &d_s2, p->npairs, "seed tmp"));
+    TRY(dalloc_t(p, &d_cs, p->npairs, "seed tmp"));
+    TRY(cuda_check(cudaMemcpy(p->d_ring_theta, th, R * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+    TRY(cuda_check(cudaMemcpy(p->d_xr, xr.data(), xr.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+    TRY(cuda_check(cudaMemcpy(p->d_y32, y32.data(), y32.size() * sizeof(float), cudaMemcpyHostToDevice), "upload"));
+    TRY(cuda_check(cudaMemcpy(p->d_ring_ext, ring_ext.data(), ring_ext.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+    TRY(cuda_check(cudaMemcpy(p->d_wden, wden.data(), wden.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+    TRY(cuda_check(cudaMemcpy(p->d_lut, lut.data(), lut.size() * sizeof(int), cudaMemcpyHostToDevice), "upload"));
+    TRY(cuda_check(cudaMemcpy(p->d_tw64, tw64.data(), tw64.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload"));
+    TRY(cuda_check(cudaMemcpy(p->d_tw32, tw32.data(), tw32.size() * sizeof(float2), cudaMemcpyHostToDevice), "upload"));
+    TRY(cuda_check(cudaMemcpy(d_c2, c2.data(), c2.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+    TRY(cuda_check(cudaMemcpy(d_s2, s2.data(), s2.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+    TRY(cuda_check(cudaMemcpy(d_cs, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+    p->geom.ring_ext = p->d_ring_ext;
+    p->geom.wden = p->d_wden;
+    p->geom.lut = p->d_lut;
+
+    {
+        size_t nseed = (size_t)(K + 1) * (L + 1) * p->npairs;
+        TRY(dalloc_t(p, &p->d_seed, nseed, "seeds"));
+        TRY(dalloc_t(p, &p->d_seed_e, nseed, "seed exponents"));
+    }
+    TRY(launch_seeds(p, d_c2, d_s2, d_cs));
+    {
+        size_t gel = (size_t)(K + 1) * R * (2 * L + 1);
+        p->G_bytes = gel * (p->precision == SL_FP64 ? sizeof(double2) : sizeof(float2));
+        TRY(dalloc(p, &p->d_G, p->G_bytes, "spin-Legendre scratch G"));
+    }
+    TRY(dalloc_t(p, &p->d_hist, p->ntiles + 1, "tile histogram"));
+    TRY(dalloc_t(p, &p->d_cursor, p->ntiles, "tile cursor"));
+    TRY(dalloc_t(p, &p->d_chunk_off, p->ntiles + 1, "tile chunks"));
+    TRY(cuda_check(cudaStreamSynchronize(p->stream), "plan seeds"));
+    dfree(d_c2);
+    dfree(d_s2);
+    dfree(d_cs);
+    p->bytes_held -= 3 * (int64_t)p->npairs * sizeof(double);
+    *out = p;
+    return SL_OK;
+fail:
+    cudaStreamSynchronize(p->stream);
+    dfree(d_c2);
+    dfree(d_s2);
+    dfree(d_cs);
+    {
+        char keep[512];
+        snprintf(keep, sizeof(keep), "%s", g_err);
+        plan_destroy(p);
+        snprintf(g_err, sizeof(g_err), "%s", keep);
+    }
+    return st;
+#undef TRY
+}
+
+static sl_status enter(sl_plan *p) {
+    if (!p) return set_error(SL_ERR_ARG, "plan is NULL");
+    return cuda_check(cudaSetDevice(p->device), "cudaSetDevice");
+}
+
+sl_status synth_spin_maps(sl_plan *p, const double *sky, const double *beam, void *maps) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if (!sky || !beam || !maps) return set_error(SL_ERR_ARG, "synth_spin_maps: NULL buffer");
+    st = launch_lcontract(p, sky, beam);
+    if (st != SL_OK) return st;
+    return launch_ringfft_synth(p, maps);
+}
+
+static sl_status check_ptg(const double *theta, const double *phi, const double *psi, int64_t n,
+                           const void *io, const char *who) {
+    if (n < 0 || n >= ((int64_t)1 << 31)) return set_error(SL_ERR_ARG, "%s: n=%lld outside [0, 2^31)", who, (long long)n);
+    if (n > 0 && (!theta || !phi || !psi || !io)) return set_error(SL_ERR_ARG, "%s: NULL buffer", who);
+    return SL_OK;
+}
+
+sl_status interp_tod(sl_plan *p, const void *maps, const double *theta, const double *phi,
+                     const double *psi, int64_t n, double *tod) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if ((st = check_ptg(theta, phi, psi, n, tod, "interp_tod")) != SL_OK) return st;
+    if (!maps) return set_error(SL_ERR_ARG, "interp_tod: maps is NULL");
+    if (n == 0) return SL_OK;
+    if ((st = ensure_sort_capacity(p, n)) != SL_OK) return st;
+    if ((st = launch_sort(p, theta, phi, n)) != SL_OK) return st;
+    return launch_interp(p, maps, theta, phi, psi, n, tod);
+}
+
+sl_status adjoint_interp(sl_plan *p, const double *theta, const double *phi, const double *psi,
+                         const double *tod, int64_t n, double *maps_bar) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if ((st = check_ptg(theta, phi, psi, n, tod, "adjoint_interp")) != SL_OK) return st;
+    if (!maps_bar) return set_error(SL_ERR_ARG, "adjoint_interp: maps_bar is NULL");
+    size_t bytes = (size_t)p->R * p->nphi * (p->K + 1) * sizeof(double2);
+    if ((st = cuda_check(cudaMemsetAsync(maps_bar, 0, bytes, p->stream), "memset maps_bar")) != SL_OK) return st;
+    if (n == 0) return SL_OK;
+    if ((st = ensure_sort_capacity(p, n)) != SL_OK) return st;
+    if ((st = launch_sort(p, theta, phi, n)) != SL_OK) return st;
+    return launch_interp_adjoint(p, theta, phi, psi, tod, n, (double2 *)maps_bar);
+}
+
+sl_status adjoint_synth(sl_plan *p, const double *maps_bar, const double *sky, const double *beam,
+                        double *sky_grad, double *beam_grad, int accumulate) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if (!maps_bar || !sky || !beam) return set_error(SL_ERR_ARG, "adjoint_synth: NULL buffer");
+    if (!sky_grad && !beam_grad) return SL_OK;
+    if ((st = ensure_adjoint_scratch(p)) != SL_OK) return st;
+    if ((st = launch_ringdft_adjoint(p, (const double2 *)maps_bar)) != SL_OK) return st;
+    if ((st = launch_lcontract_adjoint(p)) != SL_OK) return st;
+    return launch_grad(p, sky, beam, sky_grad, beam_grad, accumulate);
+}
+
+sl_status adjoint_tod(sl_plan *p, const double *theta, const double *phi, const double *psi,
+                      const double *tod, int64_t n, const double *sky, const double *beam,
+                      double *sky_grad, double *beam_grad, int accumulate) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if ((st = check_ptg(theta, phi, psi, n, tod, "adjoint_tod")) != SL_OK) return st;
+    if (!sky || !beam) return set_error(SL_ERR_ARG, "adjoint_tod: NULL sky/beam");
+    if ((st = ensure_fbar(p)) != SL_OK) return st;
+    if ((st = adjoint_interp(p, theta, phi, psi, tod, n, (double *)p->d_Fbar)) != SL_OK) return st;
+    return adjoint_synth(p, (const double *)p->d_Fbar, sky, beam, sky_grad, beam_grad, accumulate);
+}
+
+sl_status sl_plan_get_sizes(const sl_plan *p, sl_plan_sizes *o) {
+    if (!p || !o) return set_error(SL_ERR_ARG, "NULL argument");
+    o->nalm = p->nalm;
+    o->sky_doubles = (int64_t)p->ncomp * p->nalm * 2;
+    o->beam_doubles = (int64_t)p->ncomp * (p->K + 1) * (p->L + 1) * 2;
+    o->maps_bytes = (int64_t)p->R * p->nphi * (p->K + 1) * (p->precision == SL_FP64 ? 16 : 8);
+    o->scratch_bytes = p->bytes_held;
+    return SL_OK;
+}
+
+sl_status sl_plan_set_stream(sl_plan *p, void *stream) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    cudaStreamSynchronize(p->stream);
+    p->stream = (cudaStream_t)stream;
+    return SL_OK;
+}
+
+sl_status sl_plan_sync(sl_plan *p) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    return cuda_check(cudaStreamSynchronize(p->stream), "stream synchronize");
+}
+
+sl_status sl_plan_enable_timing(sl_plan *p, int enable) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    timing_flush(p);
+    p->timing = enable != 0;
+    return SL_OK;
+}
+
+sl_status sl_plan_kernel_stats(sl_plan *p, sl_kernel_stat *out, int max, int *count, int reset) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    timing_flush(p);
+    int n = (int)p->timers.size();
+    if (count) *count = n;
+    for (int i = 0; i < n && i < max && out; ++i) {
+        snprintf(out[i].name, sizeof(out[i].name), "%s", p->timers[i].name.c_str());
+        out[i].launches = p->timers[i].launches;
+        out[i].total_ms = p->timers[i].total_ms;
+    }
+    if (reset) p->timers.clear();
+    return cuda_check(cudaGetLastError(), "timing");
+}
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+// sl_internal.cuh -- plan layout, small device helpers and kernel launch
+// declarations shared by the translation units of libsidelobe.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sidelobe.h"
+
+namespace sl {
+
+// ---------------------------------------------------------------- constants
+constexpr int kMaxK = 63;        // beam azimuthal band limit supported
+constexpr int kMaxNphi = 8192;   // ring FFT length held in shared memory
+constexpr int kMaxRadices = 16;
+
+// Scaled FP64 Wigner values: value = mantissa * 2^(600 * e), e <= 0; a value
+// with e < 0 is below 2^-300 and contributes nothing.
+constexpr double kScaleUp = 0x1p600;
+constexpr double kScaleDn = 0x1p-600;
+constexpr double kScaleThr = 0x1p300;
+constexpr double kScaleLow = 0x1p-300;
+// FP32 recurrences use value = mantissa * 2^(64 e), rescaled above 2^32.
+constexpr float kScaleDn32 = 0x1p-64f;
+constexpr float kScaleThr32 = 0x1p32f;
+
+// Sort tiles: cells (base row i in [-1, R-1], base column j) grouped into
+// tiles of kTileRows x tile_cols cells.
+constexpr int kTileRows = 4;
+
+// ---------------------------------------------------------------- geometry
+// Everything the interpolation kernels need, passed by value.
+struct InterpGeom {
+    int R, nphi, K, p, half;      // half = p/2 ghost rows per pole
+    const double *ring_ext;       // [R + 2 half]: theta of rows -half .. R+half-1
+    const double *wden;           // [(R+1) * p]: 1 / prod_{b!=a}(theta_a - theta_b) per base row
+    const int *lut;               // [nlut]: base row for theta bin
+    int nlut;
+    double lut_scale;             // nlut / pi
+    double phi_scale;             // nphi / (2 pi)
+    int tile_cols, ntr, ntc;      // tile grid: ntr = ceil((R+1)/kTileRows), ntc = ceil(nphi/tile_cols)
+};
+
+struct KernelTimer {
+    std::string name;
+    int64_t launches = 0;
+    double total_ms = 0;
+};
+
+}  // namespace sl
+
+struct sl_plan {
+    int L, K, ncomp, R, nphi, p, precision, device;
+    cudaStream_t stream;
+    int npairs;            // ceil(R/2): north rings (equator ring pairs with itself)
+    int64_t nalm;
+
+    // geometry (device)
+    double *d_ring_theta = nullptr;   // [R]
+    double *d_xr = nullptr;           // [npairs] cos(theta) of north rings
+    float *d_y32 = nullptr;           // [npairs] 1 - cos(theta) = 2 sin^2(theta/2), FP32
+    double *d_ring_ext = nullptr;
+    double *d_wden = nullptr;
+    int *d_lut = nullptr;
+    int nlut = 0;
+    sl::InterpGeom geom;
+
+    // seeds: [K+1][L+1][npairs] (mantissa for +k, -k) and exponents
+    double2 *d_seed = nullptr;
+    int2 *d_seed_e = nullptr;
+
+    // ring FFT
+    double2 *d_tw64 = nullptr;        // [nphi] e^{+2 pi i j / nphi}
+    float2 *d_tw32 = nullptr;
+    int radices[sl::kMaxRadices];
+    int nradix = 0;
+
+    // scratch
+    void *d_G = nullptr;              // [K+1][R][2L+1] complex (precision of the plan; FP64 for adjoint)
+    size_t G_bytes = 0;
+    double2 *d_Gadj = nullptr;        // FP64 copy for FP32 plans (adjoint), else aliases d_G
+    double2 *d_Fbar = nullptr;        // [R][nphi][K+1] adjoint cube
+    double2 *d_Abar = nullptr;        // [K+1][2L+1][L+1]
+    // pointing sort
+    int ntiles = 0;
+    unsigned *d_hist = nullptr;       // [ntiles + 1]
+    unsigned *d_cursor = nullptr;     // [ntiles]
+    unsigned *d_chunk_off = nullptr;  // [ntiles + 1]
+    unsigned *d_keys = nullptr;       // [cap]
+    unsigned *d_perm = nullptr;       // [cap]
+    int64_t sort_cap = 0;
+
+    int64_t bytes_held = 0;
+
+    // timing
+    bool timing = false;
+    std::vector<sl::KernelTimer> timers;
+    std::vector<cudaEvent_t> pending_ev;     // pairs (start, stop)
+    std::vector<int> pending_idx;
+};
+
+namespace sl {
+
+// status helpers (plan.cu)
+sl_status set_error(sl_status st, const char *fmt, ...);
+sl_status cuda_check(cudaError_t e, const char *what);
+
+// timing (plan.cu): returns an index; call timing_end after the launch
+int timing_begin(sl_plan *p, const char *name);
+void timing_end(sl_plan *p, int idx);
+
+// launchers (one per translation unit)
+sl_status launch_seeds(sl_plan *p, const double *d_c2, const double *d_s2, const double *d_cs);
+sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam);
+sl_status launch_ringfft_synth(sl_plan *p, void *maps);
+sl_status launch_sort(sl_plan *p, const double *theta, const double *phi, int64_t n);
+sl_status launch_interp(sl_plan *p, const void *maps, const double *theta, const double *phi,
+                        const double *psi, int64_t n, double *tod);
+sl_status launch_interp_adjoint(sl_plan *p, const double *theta, const double *phi,
+                                const double *psi, const double *tod, int64_t n, double2 *fbar);
+sl_status launch_ringdft_adjoint(sl_plan *p, const double2 *fbar);
+sl_status launch_lcontract_adjoint(sl_plan *p);
+sl_status launch_grad(sl_plan *p, const double *sky, const double *beam, double *sky_grad,
+                      double *beam_grad, int accumulate);
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Locate the base row i in [-1, R-1] of the interpolation stencil: the largest
+// i with theta_ext(i) <= theta.  NaN maps to a valid row (result is NaN).
+__device__ __forceinline__ int locate_row(const InterpGeom &g, double theta) {
+    double tb = theta * g.lut_scale;
+    int b = (tb >= 0.0) ? ((tb < (double)(g.nlut - 1)) ? (int)tb : g.nlut - 1) : 0;
+    int i = __ldg(g.lut + b);
+    // ring_ext index of row r is r + half
+    while (i < g.R - 1 && __ldg(g.ring_ext + i + 1 + g.half) <= theta) ++i;
+    return i;
+}
+
+// phi -> base column j in [0, nphi) and fractional offset f in [0, 1).
+__device__ __forceinline__ int locate_col(const InterpGeom &g, double phi, double &f) {
+    double u = phi * g.phi_scale;
+    double n = (double)g.nphi;
+    u -= n * floor(u * (1.0 / n));
+    int j = (u >= 0.0) ? ((u < n) ? (int)u : g.nphi - 1) : 0;
+    if (j > g.nphi - 1) j = g.nphi - 1;
+    f = u - (double)j;
+    return j;
+}
+
+__device__ __forceinline__ unsigned tile_key(const InterpGeom &g, int i, int j) {
+    return (unsigned)((i + 1) / kTileRows) * (unsigned)g.ntc + (unsigned)(j / g.tile_cols);
+}
+
+}  // namespace sl

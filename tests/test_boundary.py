@@ -1,0 +1,87 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for sm_103a,
+loads, exports every function include/sidelobe.h declares, and rejects bad
+plan descriptions before touching a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2201_03478_gb300 import _lib
+    return _lib.load()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "sidelobe.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for must in ("sidelobe_plan_create", "synth_spin_maps", "interp_tod", "adjoint_tod", "plan_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2201_03478_gb300 import _lib
+    names = _declared_functions()
+    assert sorted(_lib.EXPORTS) == names
+    for n in names:
+        assert getattr(lib, n) is not None
+
+
+def _desc(**kw):
+    from paper_2201_03478_gb300 import _lib
+    rt = kw.pop("ring_theta", W.equiangular_ring_theta(16))
+    d = dict(lmax=16, kmax=2, ncomp=1, nrings=rt.size, nphi=32, interp_order=4, precision=0, device=0)
+    d.update(kw)
+    keep = np.ascontiguousarray(rt, dtype=np.float64)
+    return _lib.PlanDesc(ring_theta=keep.ctypes.data_as(ctypes.c_void_p), stream=None, **d), keep
+
+
+@pytest.mark.parametrize("bad,status", [
+    (dict(lmax=0), -1), (dict(kmax=17), -1), (dict(kmax=-1), -1), (dict(ncomp=2), -1),
+    (dict(nphi=31), -1), (dict(nphi=4), -1), (dict(nphi=14), -2), (dict(interp_order=6), -2),
+    (dict(precision=7), -1), (dict(nrings=3), -1),
+])
+def test_bad_descriptions_are_rejected(lib, bad, status):
+    d, keep = _desc(**bad)
+    out = ctypes.c_void_p()
+    st = lib.sidelobe_plan_create(ctypes.byref(out), ctypes.byref(d))
+    assert st == status
+    assert out.value is None
+    assert len(lib.sl_last_error()) > 0
+
+
+def test_asymmetric_or_unsorted_rings_are_rejected(lib):
+    rt = W.equiangular_ring_theta(16)
+    bad = rt.copy()
+    bad[2] += 1e-6
+    for r in (bad, rt[::-1].copy(), np.concatenate([[0.0], rt[1:]])):
+        d, keep = _desc(ring_theta=r)
+        out = ctypes.c_void_p()
+        assert lib.sidelobe_plan_create(ctypes.byref(out), ctypes.byref(d)) == -1
+
+
+def test_null_arguments(lib):
+    assert lib.sidelobe_plan_create(None, None) == -1
+    assert lib.synth_spin_maps(None, None, None, None) == -1
+    assert lib.interp_tod(None, None, None, None, None, 0, None) == -1
+    assert lib.adjoint_tod(None, None, None, None, None, 0, None, None, None, None, 0) == -1
+    lib.plan_destroy(None)
+
+
+def test_oracle_builds():
+    import oracle
+    assert os.path.exists(oracle.build())

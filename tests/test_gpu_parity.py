@@ -1,0 +1,191 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle,
+element by element on seeded inputs.
+
+Tolerances (relative L2 over the whole output, spec targets):
+  FP64 plans: 1e-10 (oracle and kernels take different but equally exact
+              routes: recurrence arrangement, FFT vs explicit DFT, sum order);
+  FP32 plans: 1e-5, with the measured error printed.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from tests.conftest import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sl():
+    import paper_2201_03478_gb300 as sl
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return sl
+
+
+def _dev(x, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def _case(L, K, rings, nphi, n, ncomp=1, seed=0, pointings="uniform"):
+    rng = np.random.default_rng(seed)
+    if ncomp == 1:
+        ell = np.arange(L + 1, dtype=float)
+        sky = W.sky_gaussian(L, [(ell + 1.0) ** -2], seed=seed)
+        beam = W.beam_gaussian_taper(L, K, max(4.0, L / 3.0), seed=seed + 1)
+    else:
+        sky = W.sky_polarised(L, seed=seed)
+        beam = W.beam_far_sidelobe(L, K, seed=seed + 1)
+    if pointings == "uniform":
+        th, ph, ps = W.pointings_uniform(n, seed=seed + 2)
+    else:
+        th, ph, ps = W.pointings_scan(n)
+    del rng
+    return dict(L=L, K=K, sky=sky, beam=beam, rt=rings, nphi=nphi, th=th, ph=ph, ps=ps)
+
+
+CASES = {
+    # the small configuration: Nside=32 HEALPix-like rings (odd: equator ring), 128 phi
+    "small_healpix": lambda: _case(64, 4, W.healpix_ring_theta(32), 128, 20000),
+    # several CTAs of rings (600 rings -> 300 pairs: two ring blocks, ragged), nphi = 90 = 2*3^2*5 < 2L+1
+    "ragged_mixed_radix": lambda: _case(40, 3, W.equiangular_ring_theta(600), 90, 5000, seed=3),
+    # polarised, K = 0 edge, power-of-two phi with folding at m = +-L
+    "polarised_k0": lambda: _case(24, 0, W.equiangular_ring_theta(24), 48, 3000, ncomp=3, seed=5),
+    # polarised, nphi = 50 (radix 5), K = L
+    "polarised_kmax_eq_lmax": lambda: _case(12, 12, W.healpix_ring_theta(4), 50, 3000, ncomp=3, seed=7),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request, oracle_lib):
+    c = CASES[request.param]()
+    c["name"] = request.param
+    c["cube"] = oracle_lib.cube(c["sky"], c["beam"], c["rt"], c["nphi"])
+    c["tod"] = oracle_lib.interp(c["cube"], c["rt"], c["th"], c["ph"], c["ps"])
+    return c
+
+
+def _plan(sl, c, precision="fp64"):
+    return sl.sidelobe_plan_create(c["L"], c["K"], c["rt"], c["nphi"], ncomp=c["sky"].shape[0],
+                                   precision=precision)
+
+
+def test_cube_fp64(sl, case):
+    plan = _plan(sl, case)
+    maps = sl.synth_spin_maps(plan, _dev(case["sky"]), _dev(case["beam"]))
+    got = maps.cpu().numpy()
+    err = rel_l2(got, case["cube"])
+    print(case["name"], "cube fp64 rel L2", err)
+    assert err < TOL64
+
+
+def test_interp_fp64_same_cube(sl, case):
+    """Interpolation alone: the GPU reads the oracle's cube."""
+    plan = _plan(sl, case)
+    tod = sl.interp_tod(plan, _dev(case["cube"]), _dev(case["th"]), _dev(case["ph"]), _dev(case["ps"]))
+    err = rel_l2(tod.cpu().numpy(), case["tod"])
+    print(case["name"], "interp fp64 rel L2", err)
+    assert err < 1e-12
+
+
+def test_tod_fp64(sl, case):
+    plan = _plan(sl, case)
+    maps = sl.synth_spin_maps(plan, _dev(case["sky"]), _dev(case["beam"]))
+    tod = sl.interp_tod(plan, maps, _dev(case["th"]), _dev(case["ph"]), _dev(case["ps"]))
+    err = rel_l2(tod.cpu().numpy(), case["tod"])
+    print(case["name"], "tod fp64 rel L2", err)
+    assert err < TOL64
+
+
+def test_tod_fp32(sl, case):
+    plan = _plan(sl, case, "fp32")
+    maps = sl.synth_spin_maps(plan, _dev(case["sky"]), _dev(case["beam"]))
+    assert maps.dtype == torch.complex64
+    err_c = rel_l2(maps.cpu().numpy().astype(np.complex128), case["cube"])
+    tod = sl.interp_tod(plan, maps, _dev(case["th"]), _dev(case["ph"]), _dev(case["ps"]))
+    err = rel_l2(tod.cpu().numpy(), case["tod"])
+    print(case["name"], "fp32: cube rel L2 %.2e, tod rel L2 %.2e" % (err_c, err))
+    assert err_c < TOL32 and err < TOL32
+
+
+def test_adjoint_interp_fp64(sl, case, oracle_lib):
+    plan = _plan(sl, case)
+    rng = np.random.default_rng(21)
+    y = rng.standard_normal(case["th"].size)
+    got = sl.adjoint_interp(plan, _dev(case["th"]), _dev(case["ph"]), _dev(case["ps"]), _dev(y)).cpu().numpy()
+    ref = oracle_lib.interp_adjoint(y, case["rt"], case["nphi"], case["K"], case["th"], case["ph"], case["ps"])
+    err = rel_l2(got, ref)
+    print(case["name"], "adjoint interp rel L2", err)
+    assert err < 1e-12
+
+
+def test_adjoint_synth_fp64(sl, case, oracle_lib):
+    """Transpose of the cube build + products, from the same adjoint cube."""
+    plan = _plan(sl, case)
+    rng = np.random.default_rng(22)
+    shp = (case["rt"].size, case["nphi"], case["K"] + 1)
+    fbar = rng.standard_normal(shp) + 1j * rng.standard_normal(shp)
+    gs, gb = sl.adjoint_synth(plan, _dev(fbar), _dev(case["sky"]), _dev(case["beam"]))
+    Gh = oracle_lib.cube_from_G_adjoint(fbar, case["L"])
+    Ab = oracle_lib.cube_G_adjoint(Gh, case["rt"])
+    rs, rb = oracle_lib.grad_products(Ab, case["sky"], case["beam"])
+    es, eb = rel_l2(gs.cpu().numpy(), rs), rel_l2(gb.cpu().numpy(), rb)
+    print(case["name"], "adjoint synth rel L2 sky %.2e beam %.2e" % (es, eb))
+    assert es < TOL64 and eb < TOL64
+
+
+def test_adjoint_tod_and_dot_product(sl, case, oracle_lib):
+    plan = _plan(sl, case)
+    rng = np.random.default_rng(23)
+    y = rng.standard_normal(case["th"].size)
+    sky, beam = _dev(case["sky"]), _dev(case["beam"])
+    th, ph, ps = _dev(case["th"]), _dev(case["ph"]), _dev(case["ps"])
+    gs, gb = sl.adjoint_tod(plan, th, ph, ps, _dev(y), sky, beam)
+    rs, rb = oracle_lib.adjoint_tod(y, case["sky"], case["beam"], case["rt"], case["nphi"], case["th"],
+                                    case["ph"], case["ps"])
+    assert rel_l2(gs.cpu().numpy(), rs) < TOL64
+    assert rel_l2(gb.cpu().numpy(), rb) < TOL64
+    # <A(s), y> is linear in s: <A s, y> = <s, A^T y> with the real inner product on packed params
+    tod = sl.interp_tod(plan, sl.synth_spin_maps(plan, sky, beam), th, ph, ps).cpu().numpy()
+    lhs = float(np.dot(tod, y))
+    s_np = case["sky"].copy()
+    rhs = float(np.sum(s_np.real * gs.cpu().numpy().real + s_np.imag * gs.cpu().numpy().imag))
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, np.linalg.norm(tod) * np.linalg.norm(y))
+    b_np = case["beam"]
+    rhs_b = float(np.sum(b_np.real * gb.cpu().numpy().real + b_np.imag * gb.cpu().numpy().imag))
+    assert abs(lhs - rhs_b) <= 1e-12 * max(1.0, np.linalg.norm(tod) * np.linalg.norm(y))
+
+
+def test_pointing_edge_cases(sl, oracle_lib):
+    """Exact poles, exact ring colatitudes, phi outside [0, 2 pi), large psi, n = 0."""
+    c = CASES["small_healpix"]()
+    rt = c["rt"]
+    th = np.array([0.0, math.pi, rt[0], rt[-1], rt[63], 1e-300, math.pi - 1e-15, 0.5 * rt[0], 1.0, 2.0])
+    ph = np.array([0.0, 2 * math.pi, -0.3, 7.5, 1e-17, 100.0, -100.0, 3.0, 2 * math.pi - 1e-16, 0.25])
+    ps = np.array([0.0, -1.0, 50.0, 1e3, 3.14, -7.0, 0.5, 2.0, 1.0, 6.2])
+    cube = oracle_lib.cube(c["sky"], c["beam"], rt, 128)
+    ref = oracle_lib.interp(cube, rt, th, ph, ps)
+    plan = _plan(sl, c)
+    got = sl.interp_tod(plan, _dev(cube), _dev(th), _dev(ph), _dev(ps)).cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    out = sl.interp_tod(plan, _dev(cube), e, e, e)
+    assert out.numel() == 0
+
+
+def test_errors_are_reported(sl):
+    c = CASES["small_healpix"]()
+    with pytest.raises(sl.SidelobeError, match="SL_ERR_ARG"):
+        sl.sidelobe_plan_create(64, 65, c["rt"], 128)
+    with pytest.raises(sl.SidelobeError, match="SL_ERR_UNSUPPORTED"):
+        sl.sidelobe_plan_create(64, 4, c["rt"], 14)       # 14 = 2 * 7
+    with pytest.raises(sl.SidelobeError, match="SL_ERR_ARG"):
+        sl.sidelobe_plan_create(64, 4, c["rt"][::-1].copy(), 128)
