@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark: TOD samples/s of the spin-harmonic sidelobe convolution
+(Galloway et al., BeyondPlanck VIII, Sect. 2.1) at LFI-like scale:
+polarised T/E/B sky and beam at lmax = 1024, kmax = 16, cube on 1024 x 2048
+rings, 1e8 synthetic scan pointings (32.5 Hz, 1 rpm, 85 deg opening angle).
+
+One step = the whole hot path on one batch: cube build (spin Legendre step +
+ring FFT, synth_spin_maps) and TOD evaluation (pointing sort + interpolation
+with e^{ik psi} phases, interp_tod), inputs resident in HBM.  Every launch in
+the step is a kernel of libsidelobe.so.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun): each rank builds the (replicated) cube and evaluates its
+own consecutive shard of the scan; no data-path collective (weak scaling).
+The reference arm (--impl reference) times the CPU FP64 oracle on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FSAMP = 32.5
+KERNELS_PER_STEP = 6   # lcontract, ringfft, bin, scan, scatter, interp
+L2_BYTES = 129 * 2 ** 20
+
+
+# ----------------------------------------------------------------------------- helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def shard_t0(rank: int, n: int, fsamp: float = FSAMP) -> float:
+    """Start time of rank's shard: ranks take consecutive stretches of one scan."""
+    return rank * n / fsamp
+
+
+def reduce_max(value: float, device=None) -> float:
+    """Max over ranks (identity without an initialised process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "power_w_max": float(max(power)), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# Peaks for ALU-bound kernels, from unit counts and the maximum SM clock:
+#   FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.2586 TFLOP/s (NVIDIA: 1.25)
+#   FP32: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz = 80.55 TFLOP/s
+PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def algorithmic_flops(L, K, R, n, p=4):
+    """Per-launch algorithmic work (dense triangular count):
+    spin Legendre step: (K+1) [4 R (L+1)^2 (complex x real MACs) + 3 R (L+1)(L+2)/2 (recurrence)];
+    interpolation: n [4 p^2 (K+1) + 10]."""
+    lcontract = (K + 1) * (4.0 * R * (L + 1) ** 2 + 3.0 * R * (L + 1) * (L + 2) / 2.0)
+    interp = n * (4.0 * p * p * (K + 1) + 10.0)
+    return lcontract, interp
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2201_03478_gb300 as sl
+    import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+
+    n = int(args.n)
+    cfg = W.config_lfi(with_pointings=False)
+    L, K = cfg["lmax"], cfg["kmax"]
+    rt, nphi = cfg["ring_theta"], cfg["nphi"]
+    R = rt.size
+    th, ph, ps = W.pointings_scan(n, t0=shard_t0(rank, n))
+    sky_h = torch.from_numpy(cfg["sky"])
+    beam_h = torch.from_numpy(cfg["beam"])
+    ptg_h = [torch.from_numpy(a) for a in (th, ph, ps)]
+    sky = sky_h.to(device)
+    beam = beam_h.to(device)
+    theta, phi, psi = (t.to(device) for t in ptg_h)
+
+    plan = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=3, precision=args.precision, device=local)
+    maps = torch.empty(plan.maps_shape(), dtype=plan.maps_dtype, device=device)
+    tod = torch.empty(n, dtype=torch.float64, device=device)
+
+    def step():
+        sl.synth_spin_maps(plan, sky, beam, maps)
+        sl.interp_tod(plan, maps, theta, phi, psi, tod)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if not bool(torch.isfinite(tod).all()):
+        raise RuntimeError("non-finite TOD")
+
+    stream = torch.cuda.current_stream(device)
+    plan.enable_timing(True)
+    plan.kernel_stats(reset=True)
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    barrier(device)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(device)
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop() if rank == 0 else None
+    stats = plan.kernel_stats(reset=True)
+    plan.enable_timing(False)
+    ms_total = reduce_max(ms_total, device)
+    ms_step = ms_total / args.steps
+    value = world * n * args.steps / (ms_total / 1e3)
+
+    # ---- roofline of the two big kernels (CUDA events around each launch, same stream)
+    fl_lc, fl_in = algorithmic_flops(L, K, R, n)
+    prec = args.precision
+    peak = PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS
+    roofs = {}
+    for name, fl in ((f"lcontract_{'f64' if prec == 'fp64' else 'f32'}", fl_lc),
+                     (f"interp_{'f64' if prec == 'fp64' else 'f32'}", fl_in)):
+        if name in stats and stats[name][0] > 0:
+            avg_ms = stats[name][1] / stats[name][0]
+            ach = fl / (avg_ms / 1e3) / 1e12
+            roofs[name] = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4),
+                           "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                           "traffic": TRAFFIC.get((name, prec)), "avg_ms": round(avg_ms, 4),
+                           "flops_per_launch": fl,
+                           "peak_note": "derived from unit counts x 2.07 GHz max SM clock"}
+    dominant = max(stats.items(), key=lambda kv: kv[1][1])[0] if stats else None
+    shares = {k: round(v[1] / max(1e-9, sum(x[1] for x in stats.values())), 4) for k, v in stats.items()}
+    launches = sum(v[0] for v in stats.values())
+
+    out = {
+        "metric": "TOD samples/s (cube build+interp) at lmax=1024,kmax=16; %roofline; vs GPU FP64",
+        "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "f32 (FP64 seeds/coords/final sum)",
+        "data": "synthetic (seeded T/E/B sky, far-sidelobe beam, satellite scan)",
+        "config": {"workload": "LFI-like: polarised T/E/B, lmax=1024, kmax=16, 1024 rings x 2048 phi, "
+                               "%d scan pointings per GPU (32.5 Hz, 1 rpm, 85 deg)" % n,
+                   "lmax": L, "kmax": K, "ncomp": 3, "nrings": R, "nphi": nphi, "interp_order": 4,
+                   "samples_per_gpu": n, "precision": prec, "parallelism": "replicated cube, sharded TOD",
+                   "l2": "inputs larger than L2 (pointings %.1f GB, cube %.2f GB)" % (24 * n / 1e9,
+                                                                                       plan.sizes()["maps_bytes"] / 1e9)},
+        "gpu_launches": int(launches),
+        "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in stats.items()},
+        "kernel_share": shares,
+        "dominant_kernel": dominant,
+        "roofline": roofs.get(dominant) if dominant in roofs else (next(iter(roofs.values())) if roofs else None),
+        "roofline_kernels": roofs,
+    }
+    if rank == 0:
+        out["clocks"] = clk
+
+    # ---- the other precision on the same box, compared with this run's TOD
+    if args.compare and rank == 0 and world == 1:
+        other = "fp32" if prec == "fp64" else "fp64"
+        p2 = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=3, precision=other, device=local)
+        maps2 = torch.empty(p2.maps_shape(), dtype=p2.maps_dtype, device=device)
+        tod2 = torch.empty(n, dtype=torch.float64, device=device)
+
+        def step2():
+            sl.synth_spin_maps(p2, sky, beam, maps2)
+            sl.interp_tod(p2, maps2, theta, phi, psi, tod2)
+        for _ in range(args.warmup):
+            step2()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step2()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms2 = e0.elapsed_time(e1) / args.steps
+        err = float(torch.linalg.vector_norm(tod2 - tod) / torch.linalg.vector_norm(tod))
+        out["other_precision"] = {"precision": other, "value": n / (ms2 / 1e3), "unit": "samples/s",
+                                  "ms_per_step": ms2, "tod_rel_l2_vs_%s" % prec: err}
+        del maps2, tod2, p2
+
+    # ---- end to end through the public API from pinned host buffers
+    if args.e2e_steps > 0:
+        pin = [t.pin_memory() for t in (sky_h, beam_h, *ptg_h)]
+        torch.cuda.synchronize()
+        res = sl.tod_from_host(plan, *pin)   # warm
+        barrier(device)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            res = sl.tod_from_host(plan, *pin)
+        dt = reduce_max(time.perf_counter() - t0, device)
+        h2d = sum(t.numel() * t.element_size() for t in pin)
+        out["e2e"] = {"value": world * n * args.e2e_steps / dt, "unit": "samples/s",
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(res.numel() * 8),
+                      "steps": args.e2e_steps}
+        del pin, res
+
+    if rank == 0 and world == 1 and args.cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, th, ph, ps, n, args)
+    elif rank == 0:
+        out["cpu_baseline"] = None
+    sl.plan_destroy(plan)
+    if rank == 0:
+        line = json.dumps(out)
+        print(line, flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                f.write(line + "\n")
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ncu-measured DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+# for the current kernels; filled from profiles/ summaries, None until measured.
+TRAFFIC = {}
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+def oracle_sample(cfg, th, ph, ps, n, ring_sample, samp_n):
+    """Time the CPU FP64 oracle on a bounded sample of one step and extrapolate:
+    spin Legendre step + DFT for `ring_sample` of the rings, interpolation of
+    `samp_n` of the n samples.  Returns (seconds per full step, detail)."""
+    import oracle
+    rt = cfg["ring_theta"]
+    R = rt.size
+    idx = np.linspace(0, R - 1, ring_sample).round().astype(int)
+    t0 = time.perf_counter()
+    G = oracle.cube_G(cfg["sky"], cfg["beam"], rt[idx])
+    oracle.cube_from_G(G, cfg["nphi"])
+    t_cube = time.perf_counter() - t0
+    cube = np.zeros((R, cfg["nphi"], cfg["kmax"] + 1), dtype=np.complex128)
+    t0 = time.perf_counter()
+    oracle.interp(cube, rt, th[:samp_n], ph[:samp_n], ps[:samp_n])
+    t_int = time.perf_counter() - t0
+    full = t_cube * R / ring_sample + t_int * n / samp_n
+    return full, {"cube_s": t_cube, "interp_s": t_int}
+
+
+def cpu_baseline(cfg, th, ph, ps, n, args):
+    rs, sn = args.cpu_rings, args.cpu_samples
+    full, det = oracle_sample(cfg, th, ph, ps, n, rs, sn)
+    return {"value": n / full, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "spin Legendre step + DFT on %d of %d rings, interpolation of %d of %d samples; "
+                      "extrapolated to one full step (%.1f s measured)"
+                      % (rs, cfg["ring_theta"].size, sn, n, det["cube_s"] + det["interp_s"])}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads as W
+    n = int(args.n)
+    cfg = W.config_lfi(with_pointings=False)
+    sn = args.cpu_samples
+    th, ph, ps = W.pointings_scan(sn)
+    for _ in range(args.warmup):
+        oracle_sample(cfg, th, ph, ps, n, 4, min(sn, 100000))
+    per = []
+    t_meas = 0.0
+    for _ in range(args.steps):
+        full, det = oracle_sample(cfg, th, ph, ps, n, args.ref_rings, sn)
+        per.append(full)
+        t_meas += det["cube_s"] + det["interp_s"]
+    full = float(np.mean(per))
+    value = world * n / full
+    out = {"impl": "reference", "metric": "TOD samples/s (cube build+interp) at lmax=1024,kmax=16; %roofline; vs GPU FP64",
+           "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": full * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic (seeded T/E/B sky, far-sidelobe beam, satellite scan)",
+           "config": {"workload": "LFI-like: polarised T/E/B, lmax=1024, kmax=16, 1024 rings x 2048 phi, "
+                                  "%d scan pointings per GPU" % n, "precision": "fp64"},
+           "cpu_baseline": {"value": value, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": "each step: oracle spin Legendre step + DFT on %d of 1024 rings and "
+                                      "interpolation of %d samples, extrapolated to a full step" % (args.ref_rings, sn)},
+           "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "measured_seconds": t_meas}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--n", type=float, default=1e8, help="pointings per GPU")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-compare", dest="compare", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-rings", type=int, default=96)
+    ap.add_argument("--cpu-samples", type=int, default=8_000_000)
+    ap.add_argument("--ref-rings", type=int, default=16)
+    ap.add_argument("--json-out", default=None)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, _ = dist_env()
+    if world != args.gpus:
+        print("note: WORLD_SIZE=%d, --gpus=%d; using WORLD_SIZE" % (world, args.gpus), file=sys.stderr)
+    if args.impl == "reference":
+        if args.cpu_samples > 2_000_000:
+            args.cpu_samples = 2_000_000
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()
