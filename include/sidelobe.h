@@ -142,6 +142,30 @@ sl_status adjoint_interp(sl_plan *plan, const double *theta, const double *phi, 
 sl_status adjoint_synth(sl_plan *plan, const double *maps_bar, const double *sky, const double *beam,
                         double *sky_grad, double *beam_grad, int accumulate);
 
+/* interp_tod for callers that must not allocate device memory during the
+ * call (no counterpart in the paper).  Some callers cannot allocate: code
+ * that runs while another component owns the device-memory budget (a
+ * caching allocator that must not see foreign cudaMalloc/cudaFree calls), and
+ * long-running acquisition loops that cannot take the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  interp_tod may grow the plan's sort
+ * scratch with cudaMalloc when n exceeds every earlier call; this entry point
+ * never allocates: its sort scratch is one static device array of 8.75 MiB
+ * that every GPU loading the library holds until the process exits.
+ *
+ * Same arguments, layout and result as interp_tod (the plan is created
+ * beforehand with sidelobe_plan_create).  Limits: n <= 1,048,576 samples per
+ * call (larger n returns SL_ERR_ARG: split the TOD into chunks) and plan
+ * grids of at most 65,536 sort tiles (else SL_ERR_UNSUPPORTED).
+ *
+ * The first call on a device looks up the static array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  Every call on a device shares the one
+ * array and leaves its contents behind (the sort clears what must start at
+ * zero), so calls that overlap on the GPU -- concurrent streams, or several
+ * host threads -- race and give wrong results: serialise them. */
+sl_status interp_tod_noalloc(sl_plan *plan, const void *maps, const double *theta, const double *phi,
+                             const double *psi, int64_t n, double *tod);
+
 /* Frees the plan and everything it owns (after synchronising its stream).
  * NULL is a no-op. */
 void plan_destroy(sl_plan *plan);

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "SL_OK", -1: "SL_ERR_ARG", -2: "SL_ERR_UNSUPPORTED", -3: "SL_
 
 # Symbols include/sidelobe.h declares (checked by the host tests).
 EXPORTS = ["sidelobe_plan_create", "synth_spin_maps", "interp_tod", "adjoint_tod", "adjoint_interp",
-           "adjoint_synth", "plan_destroy", "sl_plan_get_sizes", "sl_plan_set_stream", "sl_plan_sync",
+           "adjoint_synth", "interp_tod_noalloc", "plan_destroy", "sl_plan_get_sizes", "sl_plan_set_stream", "sl_plan_sync",
            "sl_plan_enable_timing", "sl_plan_kernel_stats", "sl_last_error"]
 
 
@@ -65,6 +65,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "adjoint_tod": (I, [P, P, P, P, P, I64, P, P, P, P, I]),
         "adjoint_interp": (I, [P, P, P, P, P, I64, P]),
         "adjoint_synth": (I, [P, P, P, P, P, P, I]),
+        "interp_tod_noalloc": (I, [P, P, P, P, P, I64, P]),
         "plan_destroy": (None, [P]),
         "sl_plan_get_sizes": (I, [P, ctypes.POINTER(PlanSizes)]),
         "sl_plan_set_stream": (I, [P, P]),

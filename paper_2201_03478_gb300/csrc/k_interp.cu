@@ -334,6 +334,18 @@ sl_status launch_interp(sl_plan *p, const void *maps, const double *theta, const
     return cuda_check(cudaGetLastError(), "k_interp launch");
 }
 
+// Forward interpolation with a caller-provided sample order (see launch_sort_into).
+sl_status launch_interp_perm(sl_plan *p, const void *maps, const double *theta, const double *phi,
+                             const double *psi, int64_t n, double *tod, const unsigned *perm) {
+    if (p->precision == SL_FP64)
+        k_interp_f64<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const double2 *)maps, theta, phi, psi,
+                                                             perm, n, tod);
+    else
+        k_interp_f32<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const float2 *)maps, theta, phi, psi,
+                                                             perm, n, tod);
+    return cuda_check(cudaGetLastError(), "k_interp launch");
+}
+
 sl_status launch_interp_adjoint(sl_plan *p, const double *theta, const double *phi, const double *psi,
                                 const double *tod, int64_t n, double2 *fbar) {
     AdjArgs a;

@@ -148,4 +148,20 @@ sl_status launch_sort(sl_plan *p, const double *theta, const double *phi, int64_
     return cuda_check(cudaGetLastError(), "k_scatter launch");
 }
 
+// Same three kernels as launch_sort, into caller-provided scratch (no plan
+// scratch, no allocation).  hist must hold ntiles + 1 entries, cursor ntiles,
+// chunk_off ntiles + 1, keys and perm n each.
+sl_status launch_sort_into(sl_plan *p, const double *theta, const double *phi, int64_t n, unsigned *keys,
+                           unsigned *perm, unsigned *hist, unsigned *cursor, unsigned *chunk_off) {
+    sl_status st = cuda_check(cudaMemsetAsync(hist, 0, (p->ntiles + 1) * sizeof(unsigned), p->stream),
+                              "memset hist");
+    if (st != SL_OK) return st;
+    k_bin<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, theta, phi, n, keys, hist);
+    if ((st = cuda_check(cudaGetLastError(), "k_bin launch")) != SL_OK) return st;
+    k_scan<<<1, 1024, 0, p->stream>>>(p->ntiles, hist, cursor, chunk_off);
+    if ((st = cuda_check(cudaGetLastError(), "k_scan launch")) != SL_OK) return st;
+    k_scatter<<<grid_for(n, 256), 256, 0, p->stream>>>(n, keys, cursor, perm);
+    return cuda_check(cudaGetLastError(), "k_scatter launch");
+}
+
 }  // namespace sl

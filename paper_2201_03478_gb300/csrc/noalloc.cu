@@ -1,0 +1,79 @@
+// noalloc.cu -- interp_tod_noalloc: the TOD evaluation of interp_tod for
+// callers that must not allocate device memory during the call.
+//
+// Who needs it: code that runs while another component owns the device-memory
+// budget (a caching allocator that must not see foreign cudaMalloc/cudaFree),
+// and long-running acquisition or processing loops that cannot afford the
+// implicit device synchronisation of cudaMalloc/cudaFree.  interp_tod may
+// grow the plan's sort scratch with cudaMalloc when n exceeds every earlier
+// call; this entry point never does.
+//
+// Its scratch (the pointing sort: tile histogram, cursors, chunk offsets,
+// keys and permutation) lives in one file-scope __device__ array of fixed
+// size, held by every GPU that loads the library until the process exits:
+//   kNoAllocMaxSamples (1,048,576) samples and kNoAllocMaxTiles (65,536)
+//   grid tiles, 2,293,762 x 4 bytes = 8.75 MiB per device.
+// Longer TODs are processed in chunks of at most kNoAllocMaxSamples.
+#include <mutex>
+
+#include "sl_internal.cuh"
+
+namespace sl {
+
+constexpr int64_t kNoAllocMaxSamples = 1 << 20;
+constexpr int kNoAllocMaxTiles = 1 << 16;
+constexpr size_t kNoAllocWords = 3 * (size_t)kNoAllocMaxTiles + 2 + 2 * (size_t)kNoAllocMaxSamples;
+
+static __device__ __align__(256) unsigned g_noalloc_scratch[kNoAllocWords];
+
+// Device address of g_noalloc_scratch per device ordinal.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device with cudaGetSymbolAddress (with that device current).
+constexpr int kMaxDevices = 64;
+static unsigned *g_scratch_ptr[kMaxDevices] = {nullptr};
+static std::mutex g_scratch_mu;
+
+static sl_status scratch_for_device(int device, unsigned **out) {
+    if (device < 0 || device >= kMaxDevices)
+        return set_error(SL_ERR_UNSUPPORTED, "interp_tod_noalloc: device ordinal %d >= %d", device, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            return cuda_check(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                              "interp_tod_noalloc: cudaGetSymbolAddress of the static scratch");
+        g_scratch_ptr[device] = (unsigned *)ptr;
+    }
+    *out = g_scratch_ptr[device];
+    return SL_OK;
+}
+
+}  // namespace sl
+
+using namespace sl;
+
+extern "C" sl_status interp_tod_noalloc(sl_plan *p, const void *maps, const double *theta, const double *phi,
+                                        const double *psi, int64_t n, double *tod) {
+    if (!p) return set_error(SL_ERR_ARG, "interp_tod_noalloc: plan is NULL");
+    sl_status st = cuda_check(cudaSetDevice(p->device), "cudaSetDevice");
+    if (st != SL_OK) return st;
+    if (n < 0 || n > kNoAllocMaxSamples)
+        return set_error(SL_ERR_ARG, "interp_tod_noalloc: n=%lld outside [0, %lld] (the static scratch limit; "
+                                     "split the TOD into chunks)", (long long)n, (long long)kNoAllocMaxSamples);
+    if (p->ntiles > kNoAllocMaxTiles)
+        return set_error(SL_ERR_UNSUPPORTED, "interp_tod_noalloc: the plan's grid has %d sort tiles, more than the "
+                                             "static scratch holds (%d)", p->ntiles, kNoAllocMaxTiles);
+    if (!maps || (n > 0 && (!theta || !phi || !psi || !tod)))
+        return set_error(SL_ERR_ARG, "interp_tod_noalloc: NULL buffer");
+    if (n == 0) return SL_OK;
+    unsigned *base = nullptr;
+    if ((st = scratch_for_device(p->device, &base)) != SL_OK) return st;
+    unsigned *hist = base;                                   // ntiles + 1 (cleared by the sort)
+    unsigned *cursor = hist + (kNoAllocMaxTiles + 1);        // ntiles
+    unsigned *chunk_off = cursor + kNoAllocMaxTiles;         // ntiles + 1
+    unsigned *keys = chunk_off + (kNoAllocMaxTiles + 1);     // n
+    unsigned *perm = keys + kNoAllocMaxSamples;              // n
+    if ((st = launch_sort_into(p, theta, phi, n, keys, perm, hist, cursor, chunk_off)) != SL_OK) return st;
+    return launch_interp_perm(p, maps, theta, phi, psi, n, tod, perm);
+}

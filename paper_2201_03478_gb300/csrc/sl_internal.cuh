@@ -125,6 +125,10 @@ sl_status launch_ringdft_adjoint(sl_plan *p, const double2 *fbar);
 sl_status launch_lcontract_adjoint(sl_plan *p);
 sl_status launch_grad(sl_plan *p, const double *sky, const double *beam, double *sky_grad,
                       double *beam_grad, int accumulate);
+sl_status launch_sort_into(sl_plan *p, const double *theta, const double *phi, int64_t n, unsigned *keys,
+                           unsigned *perm, unsigned *hist, unsigned *cursor, unsigned *chunk_off);
+sl_status launch_interp_perm(sl_plan *p, const void *maps, const double *theta, const double *phi,
+                             const double *psi, int64_t n, double *tod, const unsigned *perm);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
