@@ -162,6 +162,11 @@ def gpu_arm(args):
 
     n = int(args.n)
     cfg = W.config_lfi(with_pointings=False)
+    if args.lmax or args.nrings or args.nphi:   # smaller variants of the same workload (profiling)
+        Ls = args.lmax or cfg["lmax"]
+        cfg = dict(cfg, lmax=Ls, sky=W.sky_polarised(Ls, seed=0), beam=W.beam_far_sidelobe(Ls, cfg["kmax"], seed=1),
+                   ring_theta=W.equiangular_ring_theta(args.nrings or cfg["ring_theta"].size),
+                   nphi=args.nphi or cfg["nphi"])
     L, K = cfg["lmax"], cfg["kmax"]
     rt, nphi = cfg["ring_theta"], cfg["nphi"]
     R = rt.size
@@ -391,6 +396,9 @@ def main(argv=None):
     ap.add_argument("--cpu-samples", type=int, default=8_000_000)
     ap.add_argument("--ref-rings", type=int, default=16)
     ap.add_argument("--json-out", default=None)
+    ap.add_argument("--lmax", type=int, default=0, help="override lmax (smaller profiling variants)")
+    ap.add_argument("--nrings", type=int, default=0, help="override the number of equiangular rings")
+    ap.add_argument("--nphi", type=int, default=0, help="override phi samples per ring")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

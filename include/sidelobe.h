@@ -76,8 +76,9 @@ typedef enum {
 
 typedef enum {
     SL_FP64 = 0,  /* everything in double precision */
-    SL_FP32 = 1   /* FP64 seeds, coefficient products, pointing->grid conversion
-                     and final TOD value; FP32 recurrence, contraction, ring FFT,
+    SL_FP32 = 1   /* FP64 seeds and recurrence coefficients, pointing->grid
+                     conversion, psi reduction and final TOD value; FP32
+                     recurrence, sky x beam products, contraction, ring FFT,
                      maps and interpolation sums */
 } sl_precision;
 
@@ -149,11 +150,11 @@ sl_status adjoint_synth(sl_plan *plan, const double *maps_bar, const double *sky
  * long-running acquisition loops that cannot take the implicit device
  * synchronisation of cudaMalloc/cudaFree.  interp_tod may grow the plan's sort
  * scratch with cudaMalloc when n exceeds every earlier call; this entry point
- * never allocates: its sort scratch is one static device array of 8.75 MiB
+ * never allocates: its sort scratch is one static device array of 8.5 MiB
  * that every GPU loading the library holds until the process exits.
  *
  * Same arguments, layout and result as interp_tod (the plan is created
- * beforehand with sidelobe_plan_create).  Limits: n <= 1,048,576 samples per
+ * beforehand with sidelobe_plan_create).  Limits: n <= 262,144 samples per
  * call (larger n returns SL_ERR_ARG: split the TOD into chunks) and plan
  * grids of at most 65,536 sort tiles (else SL_ERR_UNSUPPORTED).
  *

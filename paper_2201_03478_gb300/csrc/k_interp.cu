@@ -9,66 +9,75 @@
 // beyond a pole are ghost rows: row -1-q is ring q and row R+q is ring R-1-q,
 // read at phi + pi with the factor (-1)^k (d^l_{mk}(-t) = (-1)^{m-k} d^l_{mk}(t)).
 //
-// Forward: one thread per sample, samples visited in tile-sorted order so that
-// neighbouring threads read neighbouring cube nodes.
+// The binning kernel has already turned each pointing into a stencil record
+// (cell (i, j), theta - theta(i-1), the phi fraction) in double precision.
+// Forward: one thread per sample in sorted order (samples of one cell are
+// adjacent, so the lanes of a warp read the same nodes).
 // Adjoint: one CTA per work item (<= kChunk samples of one tile); the tile's
-// cube nodes (with a 3-node halo) are accumulated in shared memory, each warp
+// nodes (with a 3-node halo) are accumulated in shared memory, each warp
 // owning a disjoint set of k so that no two threads update the same word, and
 // the tile is flushed to the global adjoint cube with atomic adds.
+#include <algorithm>
+
 #include "sl_internal.cuh"
 
 namespace sl {
 
 constexpr int kChunkA = 2048;   // must equal kChunk in k_sort.cu
 
-struct Stencil {
-    int off[16];       // element offsets (ring * nphi + col) * (K+1) of the 16 nodes
-    double w[16];      // wt_a * wp_b
-    unsigned ghost;    // bit a set if row a is a ghost row
-};
-
-__device__ __forceinline__ void make_stencil(const InterpGeom &g, double th, double ph, Stencil &st,
-                                             double &dth0, double &fph) {
-    const int i = locate_row(g, th);
-    double f;
-    const int j = locate_col(g, ph, f);
-    const double *te = g.ring_ext + g.half + i - 1;   // rows i-1 .. i+2
-    const double d0 = th - te[0], d1 = th - te[1], d2 = th - te[2], d3 = th - te[3];
+// 4-point Lagrange weights: theta rows from the record, phi nodes -1, 0, 1, 2.
+__device__ __forceinline__ void weights64(const InterpGeom &g, int i, double d0, double f, double wt[4],
+                                          double wp[4]) {
+    const double *of = g.offs64 + (size_t)(i + 1) * 4;
     const double *wd = g.wden + (size_t)(i + 1) * 4;
+    const double d1 = d0 - __ldg(of + 1), d2 = d0 - __ldg(of + 2), d3 = d0 - __ldg(of + 3);
     const double p01 = d0 * d1, p23 = d2 * d3;
-    const double wt[4] = {wd[0] * d1 * p23, wd[1] * d0 * p23, wd[2] * p01 * d3, wd[3] * p01 * d2};
+    wt[0] = __ldg(wd + 0) * d1 * p23;
+    wt[1] = __ldg(wd + 1) * d0 * p23;
+    wt[2] = __ldg(wd + 2) * p01 * d3;
+    wt[3] = __ldg(wd + 3) * p01 * d2;
     const double a = f + 1.0, c = f - 1.0, d = f - 2.0;
     const double cd = c * d, ab = a * f;
-    const double wp[4] = {-f * cd * (1.0 / 6.0), a * cd * 0.5, -ab * d * 0.5, ab * c * (1.0 / 6.0)};
+    wp[0] = -f * cd * (1.0 / 6.0);
+    wp[1] = a * cd * 0.5;
+    wp[2] = -ab * d * 0.5;
+    wp[3] = ab * c * (1.0 / 6.0);
+}
+
+// Element offsets of the 16 nodes and the ghost-row mask.
+__device__ __forceinline__ unsigned node_offsets(const InterpGeom &g, int i, int j, int off[16]) {
     const int K1 = g.K + 1;
-    st.ghost = 0;
+    unsigned ghost = 0;
 #pragma unroll
     for (int ra = 0; ra < 4; ++ra) {
         int row = i - 1 + ra, ring = row, shift = 0;
-        if (row < 0) { ring = -1 - row; shift = g.nphi / 2; st.ghost |= 1u << ra; }
-        else if (row >= g.R) { ring = 2 * g.R - 1 - row; shift = g.nphi / 2; st.ghost |= 1u << ra; }
+        if (row < 0) { ring = -1 - row; shift = g.nphi / 2; ghost |= 1u << ra; }
+        else if (row >= g.R) { ring = 2 * g.R - 1 - row; shift = g.nphi / 2; ghost |= 1u << ra; }
 #pragma unroll
         for (int cb = 0; cb < 4; ++cb) {
             int col = j - 1 + cb + shift;
             col = (col < 0) ? col + g.nphi : (col >= g.nphi ? col - g.nphi : col);
-            st.off[ra * 4 + cb] = (ring * g.nphi + col) * K1;
-            st.w[ra * 4 + cb] = wt[ra] * wp[cb];
+            off[ra * 4 + cb] = (ring * g.nphi + col) * K1;
         }
     }
-    dth0 = d0;
-    fph = f;
+    return ghost;
 }
 
 // ------------------------------------------------------------------ forward FP64
 __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const double2 *__restrict__ maps,
-                                                    const double *__restrict__ theta, const double *__restrict__ phi,
+                                                    const StencilRec64 *__restrict__ rec,
                                                     const double *__restrict__ psi, const unsigned *__restrict__ perm,
                                                     int64_t n, double *__restrict__ tod) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const unsigned s = perm[t];
-        Stencil st;
-        double dd, ff;
-        make_stencil(g, theta[s], phi[s], st, dd, ff);
+        const StencilRec64 r = rec[s];
+        const int i = (int)(r.cell / (unsigned)g.nphi) - 1, j = (int)(r.cell % (unsigned)g.nphi);
+        double wt[4], wp[4], w[16];
+        weights64(g, i, r.dth, r.fph, wt, wp);
+        int off[16];
+        const unsigned ghost = node_offsets(g, i, j, off);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) w[q] = wt[q >> 2] * wp[q & 3];
         double sp, cp;
         sincos(psi[s], &sp, &cp);
         const double c2 = 2.0 * cp;
@@ -79,9 +88,9 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const do
             double sr = 0.0, si = 0.0;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const double2 v = __ldg(maps + st.off[q] + k);
-                sr = fma(st.w[q], v.x, sr);
-                si = fma(st.w[q], v.y, si);
+                const double2 v = __ldg(maps + off[q] + k);
+                sr = fma(w[q], v.x, sr);
+                si = fma(w[q], v.y, si);
             }
             if (k == 0) {
                 acc = sr;
@@ -94,12 +103,12 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const do
             skm = sk;
             ck = cn;
             sk = sn;
-            if (st.ghost) {   // (-1)^k on ghost rows: flip their weights between k and k+1
+            if (ghost) {   // (-1)^k on ghost rows: flip their weights between k and k+1
 #pragma unroll
                 for (int ra = 0; ra < 4; ++ra)
-                    if (st.ghost & (1u << ra))
+                    if (ghost & (1u << ra))
 #pragma unroll
-                        for (int cb = 0; cb < 4; ++cb) st.w[ra * 4 + cb] = -st.w[ra * 4 + cb];
+                        for (int cb = 0; cb < 4; ++cb) w[ra * 4 + cb] = -w[ra * 4 + cb];
             }
         }
         tod[s] = acc;
@@ -107,51 +116,32 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const do
 }
 
 // ------------------------------------------------------------------ forward FP32 maps
-// FP64: pointing -> (row, column, offsets), psi range reduction, final value.
-// FP32: weights (from FP64 offsets), the e^{ik psi} ladder and the stencil sums.
+// FP64 only for the stored record (made by the binning kernel) and the final
+// value; weights, the e^{ik psi} ladder and the stencil sums in FP32.
 __global__ void __launch_bounds__(256) k_interp_f32(const InterpGeom g, const float2 *__restrict__ maps,
-                                                    const double *__restrict__ theta, const double *__restrict__ phi,
-                                                    const double *__restrict__ psi, const unsigned *__restrict__ perm,
-                                                    int64_t n, double *__restrict__ tod) {
+                                                    const StencilRec32 *__restrict__ rec,
+                                                    const unsigned *__restrict__ perm, int64_t n,
+                                                    double *__restrict__ tod) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const unsigned s = perm[t];
-        const double th = theta[s], ph = phi[s];
-        const int i = locate_row(g, th);
-        double fd;
-        const int j = locate_col(g, ph, fd);
-        const double *te = g.ring_ext + g.half + i - 1;
-        const float d0 = (float)(th - te[0]), d1 = (float)(th - te[1]), d2 = (float)(th - te[2]),
-                    d3 = (float)(th - te[3]);
-        const double *wd = g.wden + (size_t)(i + 1) * 4;
+        const StencilRec32 r = rec[s];
+        const int i = (int)(r.cell / (unsigned)g.nphi) - 1, j = (int)(r.cell % (unsigned)g.nphi);
+        const float4 of = __ldg(reinterpret_cast<const float4 *>(g.rowtab32) + 2 * (i + 1));
+        const float4 wd = __ldg(reinterpret_cast<const float4 *>(g.rowtab32) + 2 * (i + 1) + 1);
+        const float d0 = r.dth, d1 = d0 - of.y, d2 = d0 - of.z, d3 = d0 - of.w;
         const float p01 = d0 * d1, p23 = d2 * d3;
-        const float wt[4] = {(float)wd[0] * d1 * p23, (float)wd[1] * d0 * p23, (float)wd[2] * p01 * d3,
-                             (float)wd[3] * p01 * d2};
-        const float f = (float)fd;
+        const float wt[4] = {wd.x * d1 * p23, wd.y * d0 * p23, wd.z * p01 * d3, wd.w * p01 * d2};
+        const float f = r.fph;
         const float a = f + 1.f, c = f - 1.f, d = f - 2.f;
         const float cd = c * d, ab = a * f;
         const float wp[4] = {-f * cd * (1.f / 6.f), a * cd * 0.5f, -ab * d * 0.5f, ab * c * (1.f / 6.f)};
-        const int K1 = g.K + 1;
         int off[16];
         float w[16];
-        unsigned ghost = 0;
+        const unsigned ghost = node_offsets(g, i, j, off);
 #pragma unroll
-        for (int ra = 0; ra < 4; ++ra) {
-            int row = i - 1 + ra, ring = row, shift = 0;
-            if (row < 0) { ring = -1 - row; shift = g.nphi / 2; ghost |= 1u << ra; }
-            else if (row >= g.R) { ring = 2 * g.R - 1 - row; shift = g.nphi / 2; ghost |= 1u << ra; }
-#pragma unroll
-            for (int cb = 0; cb < 4; ++cb) {
-                int col = j - 1 + cb + shift;
-                col = (col < 0) ? col + g.nphi : (col >= g.nphi ? col - g.nphi : col);
-                off[ra * 4 + cb] = (ring * g.nphi + col) * K1;
-                w[ra * 4 + cb] = wt[ra] * wp[cb];
-            }
-        }
-        // psi reduced to [-pi, pi] in FP64, then an FP32 ladder z^k
-        const double ps = psi[s];
-        const float pr = (float)(ps - 6.283185307179586 * rint(ps * 0.15915494309189535));
+        for (int q = 0; q < 16; ++q) w[q] = wt[q >> 2] * wp[q & 3];
         float sz, cz;
-        sincosf(pr, &sz, &cz);
+        sincosf(r.psr, &sz, &cz);
         float zr = 1.f, zi = 0.f, acc1 = 0.f, acc0 = 0.f;
         for (int k = 0; k <= g.K; ++k) {
             float sr = 0.f, si = 0.f;
@@ -182,9 +172,10 @@ __global__ void __launch_bounds__(256) k_interp_f32(const InterpGeom g, const fl
 // maps_bar_k(node) += y wt_a wp_b sigma_{a,k} eps_k e^{-ik psi},  eps_0 = 1, eps_k = 2.
 struct AdjArgs {
     InterpGeom g;
-    const double *theta, *phi, *psi, *y;
+    const double *psi, *y;
+    const StencilRec64 *rec;
     const unsigned *perm, *start, *chunk_off;
-    int ntiles;
+    int ntiles, ncell;
     double2 *fbar;
 };
 
@@ -220,8 +211,8 @@ __global__ void k_interp_adjoint(const AdjArgs A) {
         }
         const int tile = lo;
         const unsigned c = v - A.chunk_off[tile];
-        const unsigned s_beg = A.start[tile] + c * kChunkA;
-        const unsigned s_end = min(A.start[tile + 1], s_beg + kChunkA);
+        const unsigned s_beg = A.start[(int64_t)tile * A.ncell] + c * kChunkA;
+        const unsigned s_end = min(A.start[(int64_t)(tile + 1) * A.ncell], s_beg + kChunkA);
         const int tr = tile / g.ntc, tcol = tile % g.ntc;
         const int rowlo = tr * kTileRows - 2;   // stencil rows i-1..i+2, base row i >= tr*4-1
         const int collo = tcol * TC - 1;
@@ -231,18 +222,10 @@ __global__ void k_interp_adjoint(const AdjArgs A) {
             // phase A: per-sample weights, node location and phases
             if ((int)threadIdx.x < nb) {
                 const unsigned s = A.perm[b0 + threadIdx.x];
-                const double th = A.theta[s];
-                const int i = locate_row(g, th);
-                double f;
-                const int j = locate_col(g, A.phi[s], f);
-                const double *te = g.ring_ext + g.half + i - 1;
-                const double d0 = th - te[0], d1 = th - te[1], d2 = th - te[2], d3 = th - te[3];
-                const double *wd = g.wden + (size_t)(i + 1) * 4;
-                const double p01 = d0 * d1, p23 = d2 * d3;
-                const double wt[4] = {wd[0] * d1 * p23, wd[1] * d0 * p23, wd[2] * p01 * d3, wd[3] * p01 * d2};
-                const double a = f + 1.0, cc = f - 1.0, d = f - 2.0;
-                const double cd = cc * d, ab = a * f;
-                const double wp[4] = {-f * cd * (1.0 / 6.0), a * cd * 0.5, -ab * d * 0.5, ab * cc * (1.0 / 6.0)};
+                const StencilRec64 r = A.rec[s];
+                const int i = (int)(r.cell / (unsigned)g.nphi) - 1, j = (int)(r.cell % (unsigned)g.nphi);
+                double wt[4], wp[4];
+                weights64(g, i, r.dth, r.fph, wt, wp);
                 double *ws = W + threadIdx.x * 16;
 #pragma unroll
                 for (int ra = 0; ra < 4; ++ra)
@@ -318,46 +301,34 @@ static unsigned grid_for(int64_t n, int bs) {
     return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
-sl_status launch_interp(sl_plan *p, const void *maps, const double *theta, const double *phi,
-                        const double *psi, int64_t n, double *tod) {
+sl_status launch_interp(sl_plan *p, const SortBufs &b, const void *maps, const double *psi, int64_t n,
+                        double *tod) {
     int slot;
     if (p->precision == SL_FP64) {
         slot = timing_begin(p, "interp_f64");
-        k_interp_f64<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const double2 *)maps, theta, phi, psi,
-                                                             p->d_perm, n, tod);
+        k_interp_f64<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const double2 *)maps,
+                                                             (const StencilRec64 *)b.rec, psi, b.perm, n, tod);
     } else {
         slot = timing_begin(p, "interp_f32");
-        k_interp_f32<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const float2 *)maps, theta, phi, psi,
-                                                             p->d_perm, n, tod);
+        k_interp_f32<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const float2 *)maps,
+                                                             (const StencilRec32 *)b.rec, b.perm, n, tod);
     }
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_interp launch");
 }
 
-// Forward interpolation with a caller-provided sample order (see launch_sort_into).
-sl_status launch_interp_perm(sl_plan *p, const void *maps, const double *theta, const double *phi,
-                             const double *psi, int64_t n, double *tod, const unsigned *perm) {
-    if (p->precision == SL_FP64)
-        k_interp_f64<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const double2 *)maps, theta, phi, psi,
-                                                             perm, n, tod);
-    else
-        k_interp_f32<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const float2 *)maps, theta, phi, psi,
-                                                             perm, n, tod);
-    return cuda_check(cudaGetLastError(), "k_interp launch");
-}
-
-sl_status launch_interp_adjoint(sl_plan *p, const double *theta, const double *phi, const double *psi,
-                                const double *tod, int64_t n, double2 *fbar) {
+sl_status launch_interp_adjoint(sl_plan *p, const SortBufs &b, int fine, const double *psi, const double *tod,
+                                int64_t n, double2 *fbar) {
     AdjArgs a;
     a.g = p->geom;
-    a.theta = theta;
-    a.phi = phi;
     a.psi = psi;
     a.y = tod;
-    a.perm = p->d_perm;
-    a.start = p->d_hist;
-    a.chunk_off = p->d_chunk_off;
+    a.rec = (const StencilRec64 *)b.rec;
+    a.perm = b.perm;
+    a.start = b.hist;
+    a.chunk_off = b.chunk_off;
     a.ntiles = p->ntiles;
+    a.ncell = fine ? kTileRows * p->geom.tile_cols : 1;
     a.fbar = fbar;
     const int K1 = p->K + 1;
     const int nnode = (kTileRows + 3) * (p->geom.tile_cols + 3);

@@ -6,328 +6,318 @@
 //
 // written to G[k][r][m + L].
 //
-// One CTA per (m >= 0, k, block of north rings); one thread per north ring r.
-// Each thread runs two l-recurrences, d^l_{m,+k}(theta_r) and d^l_{m,-k}(theta_r),
-// and from them produces four outputs through the reflection identities
+// Reflections.  Per north ring, two l-recurrences, d^l_{m,+k}(theta_r) and
+// d^l_{m,-k}(theta_r), give four outputs through
 //   d^l_{-m,k}(t)    = (-1)^{m+k} d^l_{m,-k}(t)
 //   d^l_{ m,k}(pi-t) = (-1)^{l+m} d^l_{m,-k}(t)
 //   d^l_{-m,k}(pi-t) = (-1)^{l-k} d^l_{m, k}(t)
 // and the sky's real-field relation s_{l,-m} = (-1)^m conj(s_lm):
-//   G(north, +m) =               sum_l A+_l d1_l
-//   G(south, +m) = (-1)^m        sum_l (-1)^l A+_l d2_l
-//   G(north, -m) = (-1)^k        sum_l A-_l d2_l
-//   G(south, -m) = (-1)^{m+k}    sum_l (-1)^l A-_l d1_l
-// with A+_l = sum_X s conj(b), A-_l = sum_X conj(s) conj(b), d1 = d_{m,+k},
-// d2 = d_{m,-k}.  The recurrence (in l, at fixed m, k):
-//   d^{l+1} = (alpha_l x - beta_l) d^l - gamma_l d^{l-1},   x = cos(theta),
-//   alpha_l = (2l+1)(l+1)/sqrt(((l+1)^2-m^2)((l+1)^2-k^2)),
-//   beta_l  = (2l+1) m k /(l sqrt(...)),  gamma_l = (l+1) sqrt((l^2-m^2)(l^2-k^2))/(l sqrt(...)),
-// (beta changes sign with k).  The CTA stages alpha, beta, gamma and the four
-// signed coefficients for a chunk of l in shared memory; every thread then
-// steps its two recurrences through the chunk.
+//   +k recurrence d1:  G(north, +m) = sum_l A+_l d1_l,
+//                      G(south, -m) = (-1)^{m+k} sum_l (-1)^l A-_l d1_l
+//   -k recurrence d2:  G(north, -m) = (-1)^k sum_l A-_l d2_l,
+//                      G(south, +m) = (-1)^m sum_l (-1)^l A+_l d2_l
+// with A+_l = sum_X s conj(b) and A-_l = sum_X conj(s) conj(b).
 //
-// FP64 plans: the recurrence and the sums in double.  FP32 plans: the
-// coefficients are formed in double and rounded; the recurrence runs in the
-// difference form  D_{l+1} = (c_l - alpha_l y) d_l + gamma_l D_l,
-// d_{l+1} = d_l + D_{l+1}, with y = 1 - cos(theta) and c_l = alpha_l -+ beta_l
-// - gamma_l - 1 formed in double, which keeps the FP32 recurrence accurate
-// near the pole, where cos(theta) alone carries too few bits.
+// Recurrence.  d^{l+1} = (a_l x - b_l) d^l - g_l d^{l-1} (x = cos theta; b
+// changes sign with k) runs on rescaled values y_l = d_l / c_l with
+// c_{l+1} = g_l c_{l-1}:  y_{l+1} = (a'_l x -+ b'_l) y_l - y_{l-1}, and c_l moves
+// into the sum coefficients.  a', b', c_l come from the plan table (k_rtab).
+// Each ring and sign starts at the plan's start state (k_advance): the first
+// l at which the value is significant; the evanescent part before it (about
+// 28% of the (ring, m, l) volume at lmax = 1024) is not run at all.
+//
+// FP64 plans: one thread per (north ring, sign of k): per l, 2 FP64 operations
+// for the recurrence and 4 for the two complex x real sums.  FP32 plans: one
+// thread per (two adjacent north rings, sign); the recurrence in the
+// difference form  D_{l+1} = (c'_l - a'_l y) y_l + D_l,  y_{l+1} = y_l + D_{l+1}
+// with y = 1 - cos(theta) and c' = a' -+ b' - 2 formed in double (keeps the
+// FP32 recurrence accurate near the pole, where cos theta alone carries too
+// few bits); sky x beam products from FP32 copies of sky and beam.
+// The CTA stages the coefficients of a chunk of l in shared memory (double
+// buffered in FP32); a thread steps only from its own start l.
+#include <algorithm>
+
 #include "sl_internal.cuh"
 
 namespace sl {
 
-constexpr int kLC = 64;     // l values staged per chunk
-constexpr int kNT = 256;    // threads (north rings) per CTA
+constexpr int kNT = 256;          // threads per CTA
+constexpr int kHalf = kNT / 2;    // threads per sign
+constexpr int kLC64 = 64;         // l values staged per chunk (FP64)
 
-struct __align__(32) Rec64 {
-    double a, b, g, pad;
+struct __align__(16) Coef64 {
+    double a, nb, pb, unused;     // a', -b', +b'
 };
 struct __align__(16) Acc64 {
-    double2 ap, am, sap, sam;
-};
-struct __align__(16) Rec32 {
-    float a, cp, cm, g;
-};
-struct __align__(16) Acc32 {
-    float2 ap, am, sap, sam;
+    double2 ap, sam, am, sap;     // +k uses (ap, sam), -k uses (am, sap)
 };
 
 struct LcArgs {
-    int L, K, ncomp, R, npairs, nchunk;
+    int L, K, ncomp, R, npairs, nchunk, ppt;  // ppt: ring pairs per thread
     int64_t nalm;
-    const double2 *sky, *beam;
+    const double2 *sky, *beam;       // FP64 inputs
+    const float2 *sky32, *beam32;    // FP32 copies (FP32 plans)
     const double *xr;
     const float *y32;
-    const double2 *seed;
-    const int2 *seed_e;
+    const int *ls;
+    const double2 *st64;
+    const float2 *st32;
+    const RTab64 *tab64;
+    const RTab32 *tab32;
     void *G;
 };
 
-// Recurrence coefficients of the step l -> l+1 and the signed A coefficients,
-// computed in double.
-__device__ __forceinline__ void make_coefs(const LcArgs &a, int m, int k, int l, double &al,
-                                           double &be, double &ga, double2 &ap, double2 &am) {
-    const double lp = l + 1.0, ll = (double)l, dm = (double)m, dk = (double)k;
-    const double A = (lp * lp - dm * dm) * (lp * lp - dk * dk);
-    const double ra = 1.0 / sqrt(A);
-    al = (2.0 * l + 1.0) * lp * ra;
-    if (l > 0) {
-        const double B = (ll * ll - dm * dm) * (ll * ll - dk * dk);
-        be = (2.0 * l + 1.0) * dm * dk * ra / ll;
-        ga = lp * sqrt(B) * ra / ll;
-    } else {
-        be = 0.0;
-        ga = 0.0;
-    }
-    ap = make_double2(0.0, 0.0);
-    am = make_double2(0.0, 0.0);
-    const int64_t moff = (int64_t)m * (2 * a.L + 1 - m) / 2;
-    for (int X = 0; X < a.ncomp; ++X) {
-        double2 s = a.sky[X * a.nalm + moff + l];
-        if (m == 0) s.y = 0.0;
-        double2 b = a.beam[((int64_t)X * (a.K + 1) + k) * (a.L + 1) + l];
-        if (k == 0) b.y = 0.0;
-        // s conj(b)
-        ap.x += s.x * b.x + s.y * b.y;
-        ap.y += s.y * b.x - s.x * b.y;
-        // conj(s) conj(b)
-        am.x += s.x * b.x - s.y * b.y;
-        am.y -= s.y * b.x + s.x * b.y;
-    }
-}
-
-__device__ __forceinline__ void block_mk(const LcArgs &a, int &m, int &k, int &pair) {
+__device__ __forceinline__ void block_mk(const LcArgs &a, int &m, int &k, int &pc) {
     int b = blockIdx.x;
-    const int pc = b % a.nchunk;
+    pc = b % a.nchunk;
     b /= a.nchunk;
     k = b % (a.K + 1);
     m = b / (a.K + 1);
-    pair = pc * kNT + threadIdx.x;
 }
 
+__device__ __forceinline__ int64_t start_index(const LcArgs &a, int k, int m, int neg, int pair) {
+    return (((int64_t)k * (a.L + 1) + m) * 2 + neg) * a.npairs + pair;
+}
+
+// Writes the two sums of one recurrence.  neg = 0 (+k): acc1 -> (north, +m),
+// acc2 -> (south, -m); neg = 1 (-k): acc1 -> (north, -m), acc2 -> (south, +m).
 template <typename C>
-__device__ __forceinline__ void write_out(const LcArgs &a, int m, int k, int pair, C NP, C SP, C NM, C SM) {
+__device__ __forceinline__ void write_two(const LcArgs &a, int m, int k, int pair, int neg, C acc1, C acc2) {
     C *G = reinterpret_cast<C *>(a.G);
     const int rn = pair, rs = a.R - 1 - pair;
     const int64_t row = 2 * (int64_t)a.L + 1;
     const int64_t base = (int64_t)k * a.R;
     const bool modd = m & 1, kodd = k & 1;
-    G[(base + rn) * row + a.L + m] = NP;
-    if (rs != rn) {
-        if (modd) { SP.x = -SP.x; SP.y = -SP.y; }
-        G[(base + rs) * row + a.L + m] = SP;
-    }
-    if (m > 0) {
-        if (kodd) { NM.x = -NM.x; NM.y = -NM.y; }
-        G[(base + rn) * row + a.L - m] = NM;
+    if (!neg) {
+        G[(base + rn) * row + a.L + m] = acc1;
+        if (m > 0 && rs != rn) {
+            if (modd != kodd) { acc2.x = -acc2.x; acc2.y = -acc2.y; }
+            G[(base + rs) * row + a.L - m] = acc2;
+        }
+    } else {
+        if (m > 0) {
+            if (kodd) { acc1.x = -acc1.x; acc1.y = -acc1.y; }
+            G[(base + rn) * row + a.L - m] = acc1;
+        }
         if (rs != rn) {
-            if (modd != kodd) { SM.x = -SM.x; SM.y = -SM.y; }
-            G[(base + rs) * row + a.L - m] = SM;
+            if (modd) { acc2.x = -acc2.x; acc2.y = -acc2.y; }
+            G[(base + rs) * row + a.L + m] = acc2;
         }
     }
+}
+
+// Smallest start l over the CTA (L + 1 when no thread has work).
+__device__ __forceinline__ int block_min(int v) {
+    __shared__ int s_min;
+    if (threadIdx.x == 0) s_min = 0x7fffffff;
+    __syncthreads();
+    atomicMin(&s_min, v);
+    __syncthreads();
+    return s_min;
 }
 
 // ------------------------------------------------------------------ FP64
 __global__ void __launch_bounds__(kNT) k_lcontract_f64(const LcArgs a) {
-    __shared__ Rec64 rc[kLC];
-    __shared__ Acc64 ac[kLC];
-    int m, k, pair;
-    block_mk(a, m, k, pair);
-    const int l0 = max(m, k);
+    __shared__ Coef64 rc[kLC64];
+    __shared__ Acc64 ac[kLC64];
+    int m, k, pc;
+    block_mk(a, m, k, pc);
+    const int neg = threadIdx.x >= kHalf;
+    const int pair = pc * kHalf + (threadIdx.x & (kHalf - 1));
     const bool active = pair < a.npairs;
+    const int64_t moff = (int64_t)m * (2 * a.L + 1 - m) / 2;
+    const RTab64 *tab = a.tab64 + (int64_t)k * a.nalm + moff;
 
-    double x = 0.0, d1 = 0.0, d1o = 0.0, d2 = 0.0, d2o = 0.0;
-    int e1 = 0, e2 = 0;
-    double2 NP = {0, 0}, SP = {0, 0}, NM = {0, 0}, SM = {0, 0};
+    double x = 0.0, y = 0.0, yo = 0.0;
+    int ls = a.L + 1;
     if (active) {
+        const int64_t si = start_index(a, k, m, neg, pair);
+        ls = a.ls[si];
+        const double2 s = a.st64[si];
+        yo = s.x;
+        y = s.y;
         x = a.xr[pair];
-        const int64_t si = ((int64_t)k * (a.L + 1) + m) * a.npairs + pair;
-        const double2 sv = a.seed[si];
-        const int2 se = a.seed_e[si];
-        d1 = sv.x;
-        e1 = se.x;
-        d2 = sv.y;
-        e2 = se.y;
     }
-    for (int c0 = l0; c0 <= a.L; c0 += kLC) {
-        const int nc = min(kLC, a.L - c0 + 1);
+    double2 acc1 = {0, 0}, acc2 = {0, 0};
+    const int lstart = block_min(ls);
+    // coefficient slots of this thread's sign
+    const int bofs = neg ? 2 : 1;     // index of -b' (for +k) or +b' (for -k) in Coef64
+    const int cofs = neg ? 2 : 0;     // first double2 of (ap, sam) or (am, sap) in Acc64
+    for (int c0 = lstart; c0 <= a.L; c0 += kLC64) {
+        const int nc = min(kLC64, a.L - c0 + 1);
         __syncthreads();
         for (int i = threadIdx.x; i < nc; i += kNT) {
             const int l = c0 + i;
-            double al, be, ga;
-            double2 ap, am;
-            make_coefs(a, m, k, l, al, be, ga, ap, am);
-            rc[i] = Rec64{al, be, ga, 0.0};
-            const double sg = (l & 1) ? -1.0 : 1.0;
-            ac[i] = Acc64{ap, am, make_double2(sg * ap.x, sg * ap.y), make_double2(sg * am.x, sg * am.y)};
+            const RTab64 t = tab[l];
+            rc[i] = Coef64{t.a, -t.b, t.b, 0.0};
+            double2 ap = {0.0, 0.0}, am = {0.0, 0.0};
+            for (int X = 0; X < a.ncomp; ++X) {
+                double2 s = a.sky[X * a.nalm + moff + l];
+                if (m == 0) s.y = 0.0;
+                double2 b = a.beam[((int64_t)X * (a.K + 1) + k) * (a.L + 1) + l];
+                if (k == 0) b.y = 0.0;
+                ap.x += s.x * b.x + s.y * b.y;      // s conj(b)
+                ap.y += s.y * b.x - s.x * b.y;
+                am.x += s.x * b.x - s.y * b.y;      // conj(s) conj(b)
+                am.y -= s.y * b.x + s.x * b.y;
+            }
+            const double c = t.c, sc = (l & 1) ? -c : c;
+            ac[i] = Acc64{make_double2(c * ap.x, c * ap.y), make_double2(sc * am.x, sc * am.y),
+                          make_double2(c * am.x, c * am.y), make_double2(sc * ap.x, sc * ap.y)};
         }
         __syncthreads();
-        if (!active) continue;
-        int i = 0;
-        // scaled phase: values below 2^-300 are carried with an exponent
-        for (; i < nc && (e1 < 0 || e2 < 0); ++i) {
-            const Rec64 r = rc[i];
-            const Acc64 c = ac[i];
-            if (e1 == 0) {
-                NP.x = fma(c.ap.x, d1, NP.x);
-                NP.y = fma(c.ap.y, d1, NP.y);
-                SM.x = fma(c.sam.x, d1, SM.x);
-                SM.y = fma(c.sam.y, d1, SM.y);
-            }
-            if (e2 == 0) {
-                NM.x = fma(c.am.x, d2, NM.x);
-                NM.y = fma(c.am.y, d2, NM.y);
-                SP.x = fma(c.sap.x, d2, SP.x);
-                SP.y = fma(c.sap.y, d2, SP.y);
-            }
-            const double n1 = fma(fma(r.a, x, -r.b), d1, -r.g * d1o);
-            const double n2 = fma(fma(r.a, x, r.b), d2, -r.g * d2o);
-            d1o = d1;
-            d1 = n1;
-            d2o = d2;
-            d2 = n2;
-            if (e1 < 0 && fabs(d1) > kScaleThr) {
-                d1 *= kScaleDn;
-                d1o *= kScaleDn;
-                ++e1;
-            }
-            if (e2 < 0 && fabs(d2) > kScaleThr) {
-                d2 *= kScaleDn;
-                d2o *= kScaleDn;
-                ++e2;
-            }
-        }
+        const int i0 = max(0, ls - c0);
+        const double *rcd = reinterpret_cast<const double *>(rc);
+        const double2 *acd = reinterpret_cast<const double2 *>(ac);
 #pragma unroll 4
-        for (; i < nc; ++i) {
-            const Rec64 r = rc[i];
-            const Acc64 c = ac[i];
-            NP.x = fma(c.ap.x, d1, NP.x);
-            NP.y = fma(c.ap.y, d1, NP.y);
-            SM.x = fma(c.sam.x, d1, SM.x);
-            SM.y = fma(c.sam.y, d1, SM.y);
-            NM.x = fma(c.am.x, d2, NM.x);
-            NM.y = fma(c.am.y, d2, NM.y);
-            SP.x = fma(c.sap.x, d2, SP.x);
-            SP.y = fma(c.sap.y, d2, SP.y);
-            const double n1 = fma(fma(r.a, x, -r.b), d1, -r.g * d1o);
-            const double n2 = fma(fma(r.a, x, r.b), d2, -r.g * d2o);
-            d1o = d1;
-            d1 = n1;
-            d2o = d2;
-            d2 = n2;
+        for (int i = i0; i < nc; ++i) {
+            const double ra = rcd[4 * i], rb = rcd[4 * i + bofs];
+            const double2 c1 = acd[4 * i + cofs], c2 = acd[4 * i + cofs + 1];
+            acc1.x = fma(c1.x, y, acc1.x);
+            acc1.y = fma(c1.y, y, acc1.y);
+            acc2.x = fma(c2.x, y, acc2.x);
+            acc2.y = fma(c2.y, y, acc2.y);
+            const double yn = fma(fma(ra, x, rb), y, -yo);
+            yo = y;
+            y = yn;
         }
     }
-    if (active) write_out<double2>(a, m, k, pair, NP, SP, NM, SM);
+    if (active) write_two<double2>(a, m, k, pair, neg, acc1, acc2);
 }
 
 // ------------------------------------------------------------------ FP32
-__device__ __forceinline__ void to_scaled32(double v, int e600, float &mant, int &e64) {
-    // value = v * 2^(600 e600) -> mant * 2^(64 e64), |mant| >= 2^-32 while e64 < 0
-    if (v == 0.0) {
-        mant = 0.f;
-        e64 = 0;
-        return;
+struct Stage32 {
+    RTab32 t;
+    float2 s[3], b[3];
+};
+
+__device__ __forceinline__ void stage_load(const LcArgs &a, const RTab32 *tab, int64_t moff, int m, int k, int l,
+                                           Stage32 &st) {
+    st.t = tab[l];
+#pragma unroll
+    for (int X = 0; X < 3; ++X) {
+        if (X < a.ncomp) {
+            st.s[X] = a.sky32[X * a.nalm + moff + l];
+            st.b[X] = a.beam32[((int64_t)X * (a.K + 1) + k) * (a.L + 1) + l];
+            if (m == 0) st.s[X].y = 0.f;
+            if (k == 0) st.b[X].y = 0.f;
+        } else {
+            st.s[X] = make_float2(0.f, 0.f);
+            st.b[X] = make_float2(0.f, 0.f);
+        }
     }
-    int ex;
-    const double f = frexp(v, &ex);       // v = f 2^ex, |f| in [0.5, 1)
-    long tot = (long)ex + 600L * e600;
-    int e = 0;
-    if (tot < -32) {
-        const long nsteps = (-32 - tot + 63) / 64;
-        tot += 64 * nsteps;
-        e = -(int)nsteps;
+}
+
+struct __align__(16) Acc32 {
+    float2 ap, sam, am, sap;
+};
+
+__device__ __forceinline__ void stage_store(const Stage32 &st, int l, float4 *rc, Acc32 *ac) {
+    float2 ap = {0.f, 0.f}, am = {0.f, 0.f};
+#pragma unroll
+    for (int X = 0; X < 3; ++X) {
+        const float2 s = st.s[X], b = st.b[X];
+        ap.x += s.x * b.x + s.y * b.y;      // s conj(b)
+        ap.y += s.y * b.x - s.x * b.y;
+        am.x += s.x * b.x - s.y * b.y;      // conj(s) conj(b)
+        am.y -= s.y * b.x + s.x * b.y;
     }
-    mant = (float)ldexp(f, (int)tot);
-    e64 = e;
+    const float c = st.t.c, sc = (l & 1) ? -c : c;
+    *rc = make_float4(st.t.a, st.t.cp, st.t.cm, 0.f);
+    *ac = Acc32{make_float2(c * ap.x, c * ap.y), make_float2(sc * am.x, sc * am.y),
+                make_float2(c * am.x, c * am.y), make_float2(sc * ap.x, sc * ap.y)};
+}
+
+struct Rec32 {
+    float yc, y, D;
+    int ls;
+    float2 acc1, acc2;
+};
+
+__device__ __forceinline__ void rec32_step(Rec32 &s, float ra, float rc_, float2 c1, float2 c2) {
+    s.acc1.x = fmaf(c1.x, s.y, s.acc1.x);
+    s.acc1.y = fmaf(c1.y, s.y, s.acc1.y);
+    s.acc2.x = fmaf(c2.x, s.y, s.acc2.x);
+    s.acc2.y = fmaf(c2.y, s.y, s.acc2.y);
+    s.D = fmaf(fmaf(-ra, s.yc, rc_), s.y, s.D);
+    s.y += s.D;
 }
 
 __global__ void __launch_bounds__(kNT) k_lcontract_f32(const LcArgs a) {
-    __shared__ Rec32 rc[kLC];
-    __shared__ Acc32 ac[kLC];
-    int m, k, pair;
-    block_mk(a, m, k, pair);
-    const int l0 = max(m, k);
-    const bool active = pair < a.npairs;
+    __shared__ float4 rc[2][kNT];   // a', c'+, c'-, unused
+    __shared__ Acc32 ac[2][kNT];
+    int m, k, pc;
+    block_mk(a, m, k, pc);
+    const int neg = threadIdx.x >= kHalf;
+    const int p0 = pc * (2 * kHalf) + 2 * (threadIdx.x & (kHalf - 1));
+    const int64_t moff = (int64_t)m * (2 * a.L + 1 - m) / 2;
+    const RTab32 *tab = a.tab32 + (int64_t)k * a.nalm + moff;
 
-    float y = 0.f, d1 = 0.f, D1 = 0.f, d2 = 0.f, D2 = 0.f;
-    int e1 = 0, e2 = 0;
-    float2 NP = {0, 0}, SP = {0, 0}, NM = {0, 0}, SM = {0, 0};
-    if (active) {
-        y = a.y32[pair];
-        const int64_t si = ((int64_t)k * (a.L + 1) + m) * a.npairs + pair;
-        const double2 sv = a.seed[si];
-        const int2 se = a.seed_e[si];
-        to_scaled32(sv.x, se.x, d1, e1);
-        to_scaled32(sv.y, se.y, d2, e2);
-        D1 = d1;   // d^{l0-1} = 0
-        D2 = d2;
+    Rec32 A, B;
+    A.ls = B.ls = a.L + 1;
+    A.acc1 = A.acc2 = B.acc1 = B.acc2 = make_float2(0.f, 0.f);
+    A.y = A.D = B.y = B.D = A.yc = B.yc = 0.f;
+    if (p0 < a.npairs) {
+        const int64_t si = start_index(a, k, m, neg, p0);
+        A.ls = a.ls[si];
+        const float2 s = a.st32[si];
+        A.y = s.x;
+        A.D = s.y;
+        A.yc = a.y32[p0];
     }
-    for (int c0 = l0; c0 <= a.L; c0 += kLC) {
-        const int nc = min(kLC, a.L - c0 + 1);
-        __syncthreads();
-        for (int i = threadIdx.x; i < nc; i += kNT) {
-            const int l = c0 + i;
-            double al, be, ga;
-            double2 ap, am;
-            make_coefs(a, m, k, l, al, be, ga, ap, am);
-            rc[i] = Rec32{(float)al, (float)(al - be - ga - 1.0), (float)(al + be - ga - 1.0), (float)ga};
-            const double sg = (l & 1) ? -1.0 : 1.0;
-            ac[i] = Acc32{make_float2((float)ap.x, (float)ap.y), make_float2((float)am.x, (float)am.y),
-                          make_float2((float)(sg * ap.x), (float)(sg * ap.y)),
-                          make_float2((float)(sg * am.x), (float)(sg * am.y))};
+    if (p0 + 1 < a.npairs) {
+        const int64_t si = start_index(a, k, m, neg, p0 + 1);
+        B.ls = a.ls[si];
+        const float2 s = a.st32[si];
+        B.y = s.x;
+        B.D = s.y;
+        B.yc = a.y32[p0 + 1];
+    }
+    const int lme = min(A.ls, B.ls);
+    const int lstart = block_min(lme);
+    const int cofs = neg ? 2 : 0;
+    Stage32 st;
+    {
+        const int l = lstart + (int)threadIdx.x;
+        if (l <= a.L) {
+            stage_load(a, tab, moff, m, k, l, st);
+            stage_store(st, l, &rc[0][threadIdx.x], &ac[0][threadIdx.x]);
         }
+    }
+    int buf = 0;
+    for (int c0 = lstart; c0 <= a.L; c0 += kNT, buf ^= 1) {
+        const int nc = min(kNT, a.L - c0 + 1);
+        const int ln = c0 + kNT + (int)threadIdx.x;   // this thread's l in the next chunk
+        const bool next = ln <= a.L;
+        if (next) stage_load(a, tab, moff, m, k, ln, st);
         __syncthreads();
-        if (!active) continue;
-        int i = 0;
-        for (; i < nc && (e1 < 0 || e2 < 0); ++i) {
-            const Rec32 r = rc[i];
-            const Acc32 c = ac[i];
-            if (e1 == 0) {
-                NP.x = fmaf(c.ap.x, d1, NP.x);
-                NP.y = fmaf(c.ap.y, d1, NP.y);
-                SM.x = fmaf(c.sam.x, d1, SM.x);
-                SM.y = fmaf(c.sam.y, d1, SM.y);
-            }
-            if (e2 == 0) {
-                NM.x = fmaf(c.am.x, d2, NM.x);
-                NM.y = fmaf(c.am.y, d2, NM.y);
-                SP.x = fmaf(c.sap.x, d2, SP.x);
-                SP.y = fmaf(c.sap.y, d2, SP.y);
-            }
-            D1 = fmaf(fmaf(-r.a, y, r.cp), d1, r.g * D1);
-            d1 += D1;
-            D2 = fmaf(fmaf(-r.a, y, r.cm), d2, r.g * D2);
-            d2 += D2;
-            if (e1 < 0 && fabsf(d1) > kScaleThr32) {
-                d1 *= kScaleDn32;
-                D1 *= kScaleDn32;
-                ++e1;
-            }
-            if (e2 < 0 && fabsf(d2) > kScaleThr32) {
-                d2 *= kScaleDn32;
-                D2 *= kScaleDn32;
-                ++e2;
-            }
+        const float *rcf = reinterpret_cast<const float *>(rc[buf]);
+        const float2 *acf = reinterpret_cast<const float2 *>(ac[buf]);
+        const int cidx = neg ? 2 : 1;    // c'- for -k, c'+ for +k
+        int i = max(0, lme - c0);
+        // until both rings have started
+        for (; i < nc && c0 + i < max(A.ls, B.ls); ++i) {
+            const float ra = rcf[4 * i], rcc = rcf[4 * i + cidx];
+            const float2 c1 = acf[4 * i + cofs], c2 = acf[4 * i + cofs + 1];
+            if (c0 + i >= A.ls) rec32_step(A, ra, rcc, c1, c2);
+            if (c0 + i >= B.ls) rec32_step(B, ra, rcc, c1, c2);
         }
-#pragma unroll 4
+#pragma unroll 2
         for (; i < nc; ++i) {
-            const Rec32 r = rc[i];
-            const Acc32 c = ac[i];
-            NP.x = fmaf(c.ap.x, d1, NP.x);
-            NP.y = fmaf(c.ap.y, d1, NP.y);
-            SM.x = fmaf(c.sam.x, d1, SM.x);
-            SM.y = fmaf(c.sam.y, d1, SM.y);
-            NM.x = fmaf(c.am.x, d2, NM.x);
-            NM.y = fmaf(c.am.y, d2, NM.y);
-            SP.x = fmaf(c.sap.x, d2, SP.x);
-            SP.y = fmaf(c.sap.y, d2, SP.y);
-            D1 = fmaf(fmaf(-r.a, y, r.cp), d1, r.g * D1);
-            d1 += D1;
-            D2 = fmaf(fmaf(-r.a, y, r.cm), d2, r.g * D2);
-            d2 += D2;
+            const float ra = rcf[4 * i], rcc = rcf[4 * i + cidx];
+            const float2 c1 = acf[4 * i + cofs], c2 = acf[4 * i + cofs + 1];
+            rec32_step(A, ra, rcc, c1, c2);
+            rec32_step(B, ra, rcc, c1, c2);
         }
+        if (next) stage_store(st, ln, &rc[buf ^ 1][threadIdx.x], &ac[buf ^ 1][threadIdx.x]);
     }
-    if (active) write_out<float2>(a, m, k, pair, NP, SP, NM, SM);
+    if (p0 < a.npairs) write_two<float2>(a, m, k, p0, neg, A.acc1, A.acc2);
+    if (p0 + 1 < a.npairs) write_two<float2>(a, m, k, p0 + 1, neg, B.acc1, B.acc2);
+}
+
+__global__ void k_to_f32(const double2 *__restrict__ in, float2 *__restrict__ out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
 
 sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
@@ -337,14 +327,20 @@ sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
     a.ncomp = p->ncomp;
     a.R = p->R;
     a.npairs = p->npairs;
-    a.nchunk = (p->npairs + kNT - 1) / kNT;
+    a.ppt = (p->precision == SL_FP64) ? 1 : 2;
+    a.nchunk = (p->npairs + a.ppt * kHalf - 1) / (a.ppt * kHalf);
     a.nalm = p->nalm;
     a.sky = (const double2 *)sky;
     a.beam = (const double2 *)beam;
+    a.sky32 = p->d_sky32;
+    a.beam32 = p->d_beam32;
     a.xr = p->d_xr;
     a.y32 = p->d_y32;
-    a.seed = p->d_seed;
-    a.seed_e = p->d_seed_e;
+    a.ls = p->d_ls;
+    a.st64 = p->d_st64;
+    a.st32 = p->d_st32;
+    a.tab64 = p->d_tab64;
+    a.tab32 = p->d_tab32;
     a.G = p->d_G;
     const int64_t nblk = (int64_t)(p->L + 1) * (p->K + 1) * a.nchunk;
     if (nblk > 0x7fffffff) return set_error(SL_ERR_UNSUPPORTED, "grid too large");
@@ -353,6 +349,11 @@ sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
         slot = timing_begin(p, "lcontract_f64");
         k_lcontract_f64<<<(unsigned)nblk, kNT, 0, p->stream>>>(a);
     } else {
+        const int64_t ns = (int64_t)p->ncomp * p->nalm, nb = (int64_t)p->ncomp * (p->K + 1) * (p->L + 1);
+        k_to_f32<<<(unsigned)std::min<int64_t>((ns + 255) / 256, 4096), 256, 0, p->stream>>>(
+            (const double2 *)sky, p->d_sky32, ns);
+        k_to_f32<<<(unsigned)std::min<int64_t>((nb + 255) / 256, 4096), 256, 0, p->stream>>>(
+            (const double2 *)beam, p->d_beam32, nb);
         slot = timing_begin(p, "lcontract_f32");
         k_lcontract_f32<<<(unsigned)nblk, kNT, 0, p->stream>>>(a);
     }

@@ -1,32 +1,55 @@
 // k_sort.cu -- binning of the pointings before interpolation (the cube is read
 // through p x p stencils, Sect. 2.1 interpolation step): a counting sort of
-// the samples by grid tile.  A sample's cell is (base row i, base column j) of
-// its stencil; tiles group kTileRows x tile_cols cells.
+// the samples by grid cell, plus a per-sample stencil record.
 //
-//   k_bin:      key[s] = tile(i, j), histogram of keys (warp-aggregated atomics)
-//   k_scan:     exclusive prefix sum -> tile start offsets (and cursor copy),
-//               plus per-tile chunk offsets used by the adjoint scatter
-//   k_scatter:  perm[cursor[key]++] = s  (order within a tile is unspecified)
+// A sample's cell is (base row i, base column j) of its stencil.  Cells are
+// grouped into tiles of kTileRows x tile_cols; the sort key is either the tile
+// (coarse) or the cell in tile-major order (fine), so that both orders list
+// each tile's samples contiguously.  With fine keys the samples of one cell
+// are adjacent and neighbouring threads read the same cube nodes.
+//
+//   k_bin:        pointing -> (i, j) in double; key; record {theta - theta(i-1),
+//                 phi fraction, [reduced psi], cell}; key histogram
+//   k_scan_local / k_scan1 / k_scan_add:  exclusive prefix sum of the histogram
+//                 -> first position of every key (and a cursor copy)
+//   k_scatter:    perm[cursor[key]++] = s   (order within a key unspecified)
+//   k_tile_chunks: work items of at most kChunk samples per tile (adjoint)
 #include "sl_internal.cuh"
 
 namespace sl {
 
-constexpr int kChunk = 2048;   // adjoint work item: at most this many samples of one tile
+constexpr int kChunk = 2048;        // adjoint work item: at most this many samples of one tile
+constexpr int kScanBlock = 4096;    // keys per CTA of k_scan_local (1024 threads x 4)
 
-__global__ void __launch_bounds__(256) k_bin(const InterpGeom g, const double *__restrict__ theta,
-                                             const double *__restrict__ phi, int64_t n,
-                                             unsigned *__restrict__ keys, unsigned *__restrict__ hist) {
+template <bool REC64>
+__global__ void __launch_bounds__(256) k_bin(const InterpGeom g, int fine, const double *__restrict__ theta,
+                                             const double *__restrict__ phi, const double *__restrict__ psi,
+                                             int64_t n, unsigned *__restrict__ keys, void *__restrict__ rec,
+                                             unsigned *__restrict__ hist) {
     const unsigned lane = threadIdx.x & 31;
     for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x; s0 < n; s0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = s0 + threadIdx.x;
         const bool ok = s < n;
         unsigned key = 0xffffffffu;
         if (ok) {
-            const int i = locate_row(g, theta[s]);
+            const double th = theta[s];
+            const int i = locate_row(g, th);
             double f;
             const int j = locate_col(g, phi[s], f);
-            key = tile_key(g, i, j);
+            const int tr = (i + 1) / kTileRows, li = (i + 1) - tr * kTileRows;
+            const int tc = j / g.tile_cols, lj = j - tc * g.tile_cols;
+            const unsigned tile = (unsigned)tr * (unsigned)g.ntc + (unsigned)tc;
+            key = fine ? tile * (unsigned)(kTileRows * g.tile_cols) + (unsigned)(li * g.tile_cols + lj) : tile;
             keys[s] = key;
+            const double dth = th - __ldg(g.ring_ext + g.half + i - 1);
+            const unsigned cell = (unsigned)(i + 1) * (unsigned)g.nphi + (unsigned)j;
+            if (REC64) {
+                reinterpret_cast<StencilRec64 *>(rec)[s] = StencilRec64{dth, f, cell, 0u};
+            } else {
+                const double ps = psi[s];
+                const float pr = (float)(ps - 6.283185307179586 * rint(ps * 0.15915494309189535));
+                reinterpret_cast<StencilRec32 *>(rec)[s] = StencilRec32{(float)dth, (float)f, pr, cell};
+            }
         }
         const unsigned act = __ballot_sync(0xffffffffu, ok);
         if (ok) {
@@ -37,71 +60,78 @@ __global__ void __launch_bounds__(256) k_bin(const InterpGeom g, const double *_
     }
 }
 
-// Single CTA: exclusive scan of hist[0..ntiles) into start (hist, in place,
-// with hist[ntiles] = n), cursor = start, chunk_off = prefix of ceil(cnt/kChunk).
-__global__ void __launch_bounds__(1024) k_scan(int ntiles, unsigned *__restrict__ hist,
-                                               unsigned *__restrict__ cursor,
-                                               unsigned *__restrict__ chunk_off) {
-    __shared__ unsigned s_tot[32], s_ch[32];
-    __shared__ unsigned carry_tot, carry_ch;
-    if (threadIdx.x == 0) {
-        carry_tot = 0;
-        carry_ch = 0;
-    }
-    __syncthreads();
+// Block-wide exclusive scan of 1024 values (one per thread); returns the total.
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned &excl) {
+    __shared__ unsigned s_w[32];
+    __shared__ unsigned s_tot;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < ntiles; base += 1024) {
-        const int t = base + threadIdx.x;
-        const unsigned c = (t < ntiles) ? hist[t] : 0u;
-        const unsigned ch = (c + kChunk - 1) / kChunk;
-        unsigned a = c, b = ch;
+    unsigned a = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, a, o);
+        if ((int)lane >= o) a += y;
+    }
+    if (lane == 31) s_w[warp] = a;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned w = s_w[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned ya = __shfl_up_sync(0xffffffffu, a, o);
-            const unsigned yb = __shfl_up_sync(0xffffffffu, b, o);
-            if ((int)lane >= o) {
-                a += ya;
-                b += yb;
-            }
+            const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+            if ((int)lane >= o) w += y;
         }
-        if (lane == 31) {
-            s_tot[warp] = a;
-            s_ch[warp] = b;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            unsigned wa = s_tot[lane], wb = s_ch[lane];
+        s_w[lane] = w;
+        if (lane == 31) s_tot = w;
+    }
+    __syncthreads();
+    excl = (warp ? s_w[warp - 1] : 0u) + a - v;
+    const unsigned tot = s_tot;
+    __syncthreads();
+    return tot;
+}
+
+// Per CTA: exclusive scan of data[b*4096 .. +4096) in place, block total to bsum[b].
+__global__ void __launch_bounds__(1024) k_scan_local(int64_t n, unsigned *__restrict__ data,
+                                                      unsigned *__restrict__ bsum) {
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + 4 * threadIdx.x;
+    unsigned v[4], t = 0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned ya = __shfl_up_sync(0xffffffffu, wa, o);
-                const unsigned yb = __shfl_up_sync(0xffffffffu, wb, o);
-                if ((int)lane >= o) {
-                    wa += ya;
-                    wb += yb;
-                }
-            }
-            s_tot[lane] = wa;
-            s_ch[lane] = wb;
-        }
-        __syncthreads();
-        const unsigned pre_a = (warp ? s_tot[warp - 1] : 0u) + a - c + carry_tot;
-        const unsigned pre_b = (warp ? s_ch[warp - 1] : 0u) + b - ch + carry_ch;
-        if (t < ntiles) {
-            hist[t] = pre_a;
-            cursor[t] = pre_a;
-            chunk_off[t] = pre_b;
-        }
-        __syncthreads();
-        if (threadIdx.x == 1023) {
-            carry_tot = pre_a + c;
-            carry_ch = pre_b + ch;
-        }
-        __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+        v[q] = (base + q < n) ? data[base + q] : 0u;
+        t += v[q];
     }
-    if (threadIdx.x == 0) {
-        hist[ntiles] = carry_tot;
-        chunk_off[ntiles] = carry_ch;
+    unsigned ex;
+    const unsigned tot = block_exclusive_scan(t, ex);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (base + q < n) data[base + q] = ex;
+        ex += v[q];
     }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// Single CTA: exclusive scan of data[0..n) in place; data[n] = total.
+__global__ void __launch_bounds__(1024) k_scan1(int n, unsigned *__restrict__ data) {
+    unsigned carry = 0;
+    for (int base = 0; base < n; base += 1024) {
+        const int t = base + threadIdx.x;
+        const unsigned v = (t < n) ? data[t] : 0u;
+        unsigned ex;
+        const unsigned tot = block_exclusive_scan(v, ex);
+        if (t < n) data[t] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) data[n] = carry;
+}
+
+__global__ void k_scan_add(int64_t n, unsigned *__restrict__ data, const unsigned *__restrict__ bsum,
+                           unsigned *__restrict__ cursor, unsigned total_slot_from_bsum) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned v = data[i] + bsum[i / kScanBlock];
+        data[i] = v;
+        cursor[i] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) data[n] = bsum[total_slot_from_bsum];
 }
 
 __global__ void __launch_bounds__(256) k_scatter(int64_t n, const unsigned *__restrict__ keys,
@@ -124,44 +154,57 @@ __global__ void __launch_bounds__(256) k_scatter(int64_t n, const unsigned *__re
     }
 }
 
+// chunk_off[t] = ceil(#samples of tile t / kChunk); scanned by k_scan1 afterwards.
+__global__ void k_tile_chunks(int ntiles, int ncell, const unsigned *__restrict__ start,
+                              unsigned *__restrict__ chunk_off) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const unsigned c = start[(int64_t)(t + 1) * ncell] - start[(int64_t)t * ncell];
+    chunk_off[t] = (c + kChunk - 1) / kChunk;
+}
+
 static unsigned grid_for(int64_t n, int bs) {
     int64_t b = (n + bs - 1) / bs;
     const int64_t cap = 152 * 16;
     return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
-sl_status launch_sort(sl_plan *p, const double *theta, const double *phi, int64_t n) {
-    sl_status st = cuda_check(cudaMemsetAsync(p->d_hist, 0, (p->ntiles + 1) * sizeof(unsigned), p->stream),
-                              "memset hist");
+int64_t sort_nkeys(const sl_plan *p, int fine) {
+    return fine ? (int64_t)p->ntiles * kTileRows * p->geom.tile_cols : (int64_t)p->ntiles;
+}
+
+int64_t sort_nbsum(int64_t nkeys) { return (nkeys + kScanBlock - 1) / kScanBlock; }
+
+sl_status launch_sort_into(sl_plan *p, const SortBufs &b, const double *theta, const double *phi,
+                           const double *psi, int64_t n, int fine, int rec64, int with_chunks) {
+    const int64_t nkeys = sort_nkeys(p, fine), nb = sort_nbsum(nkeys);
+    const int ncell = fine ? kTileRows * p->geom.tile_cols : 1;
+    sl_status st = cuda_check(cudaMemsetAsync(b.hist, 0, (nkeys + 1) * sizeof(unsigned), p->stream), "memset hist");
     if (st != SL_OK) return st;
     int slot = timing_begin(p, "bin");
-    k_bin<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, theta, phi, n, p->d_keys, p->d_hist);
+    if (rec64)
+        k_bin<true><<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, fine, theta, phi, psi, n, b.keys, b.rec, b.hist);
+    else
+        k_bin<false><<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, fine, theta, phi, psi, n, b.keys, b.rec, b.hist);
     timing_end(p, slot);
     if ((st = cuda_check(cudaGetLastError(), "k_bin launch")) != SL_OK) return st;
     slot = timing_begin(p, "scan");
-    k_scan<<<1, 1024, 0, p->stream>>>(p->ntiles, p->d_hist, p->d_cursor, p->d_chunk_off);
+    k_scan_local<<<(unsigned)nb, 1024, 0, p->stream>>>(nkeys, b.hist, b.bsum);
+    k_scan1<<<1, 1024, 0, p->stream>>>((int)nb, b.bsum);
+    k_scan_add<<<(unsigned)std::min<int64_t>((nkeys + 255) / 256, 152 * 16), 256, 0, p->stream>>>(
+        nkeys, b.hist, b.bsum, b.cursor, (unsigned)nb);
     timing_end(p, slot);
     if ((st = cuda_check(cudaGetLastError(), "k_scan launch")) != SL_OK) return st;
     slot = timing_begin(p, "scatter");
-    k_scatter<<<grid_for(n, 256), 256, 0, p->stream>>>(n, p->d_keys, p->d_cursor, p->d_perm);
+    k_scatter<<<grid_for(n, 256), 256, 0, p->stream>>>(n, b.keys, b.cursor, b.perm);
     timing_end(p, slot);
-    return cuda_check(cudaGetLastError(), "k_scatter launch");
-}
-
-// Same three kernels as launch_sort, into caller-provided scratch (no plan
-// scratch, no allocation).  hist must hold ntiles + 1 entries, cursor ntiles,
-// chunk_off ntiles + 1, keys and perm n each.
-sl_status launch_sort_into(sl_plan *p, const double *theta, const double *phi, int64_t n, unsigned *keys,
-                           unsigned *perm, unsigned *hist, unsigned *cursor, unsigned *chunk_off) {
-    sl_status st = cuda_check(cudaMemsetAsync(hist, 0, (p->ntiles + 1) * sizeof(unsigned), p->stream),
-                              "memset hist");
-    if (st != SL_OK) return st;
-    k_bin<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, theta, phi, n, keys, hist);
-    if ((st = cuda_check(cudaGetLastError(), "k_bin launch")) != SL_OK) return st;
-    k_scan<<<1, 1024, 0, p->stream>>>(p->ntiles, hist, cursor, chunk_off);
-    if ((st = cuda_check(cudaGetLastError(), "k_scan launch")) != SL_OK) return st;
-    k_scatter<<<grid_for(n, 256), 256, 0, p->stream>>>(n, keys, cursor, perm);
-    return cuda_check(cudaGetLastError(), "k_scatter launch");
+    if ((st = cuda_check(cudaGetLastError(), "k_scatter launch")) != SL_OK) return st;
+    if (with_chunks) {
+        k_tile_chunks<<<(p->ntiles + 255) / 256, 256, 0, p->stream>>>(p->ntiles, ncell, b.hist, b.chunk_off);
+        k_scan1<<<1, 1024, 0, p->stream>>>(p->ntiles, b.chunk_off);
+        st = cuda_check(cudaGetLastError(), "k_tile_chunks launch");
+    }
+    return st;
 }
 
 }  // namespace sl

@@ -8,21 +8,27 @@
 // grow the plan's sort scratch with cudaMalloc when n exceeds every earlier
 // call; this entry point never does.
 //
-// Its scratch (the pointing sort: tile histogram, cursors, chunk offsets,
-// keys and permutation) lives in one file-scope __device__ array of fixed
-// size, held by every GPU that loads the library until the process exits:
-//   kNoAllocMaxSamples (1,048,576) samples and kNoAllocMaxTiles (65,536)
-//   grid tiles, 2,293,762 x 4 bytes = 8.75 MiB per device.
-// Longer TODs are processed in chunks of at most kNoAllocMaxSamples.
+// Its scratch (the pointing sort: per-sample stencil records, keys and
+// permutation, the tile histogram and cursors) lives in one file-scope
+// __device__ array of fixed size, held by every GPU that loads the library
+// until the process exits:
+//   kNoAllocMaxSamples (262,144) samples and kNoAllocMaxTiles (65,536) grid
+//   tiles, 8.5 MiB per device.
+// Longer TODs are processed in chunks of at most kNoAllocMaxSamples.  The sort
+// here keys samples by tile (not by cell), which keeps the histogram small.
 #include <mutex>
 
 #include "sl_internal.cuh"
 
 namespace sl {
 
-constexpr int64_t kNoAllocMaxSamples = 1 << 20;
+constexpr int64_t kNoAllocMaxSamples = 1 << 18;
 constexpr int kNoAllocMaxTiles = 1 << 16;
-constexpr size_t kNoAllocWords = 3 * (size_t)kNoAllocMaxTiles + 2 + 2 * (size_t)kNoAllocMaxSamples;
+// words (4 bytes): records (24 bytes each), keys, permutation, histogram, cursor, block sums
+constexpr size_t kRecWords = (size_t)kNoAllocMaxSamples * (sizeof(StencilRec64) / 4);
+constexpr size_t kBsumWords = (size_t)kNoAllocMaxTiles / 4096 + 2;
+constexpr size_t kNoAllocWords =
+    kRecWords + 2 * (size_t)kNoAllocMaxSamples + (kNoAllocMaxTiles + 1) + kNoAllocMaxTiles + kBsumWords;
 
 static __device__ __align__(256) unsigned g_noalloc_scratch[kNoAllocWords];
 
@@ -69,11 +75,15 @@ extern "C" sl_status interp_tod_noalloc(sl_plan *p, const void *maps, const doub
     if (n == 0) return SL_OK;
     unsigned *base = nullptr;
     if ((st = scratch_for_device(p->device, &base)) != SL_OK) return st;
-    unsigned *hist = base;                                   // ntiles + 1 (cleared by the sort)
-    unsigned *cursor = hist + (kNoAllocMaxTiles + 1);        // ntiles
-    unsigned *chunk_off = cursor + kNoAllocMaxTiles;         // ntiles + 1
-    unsigned *keys = chunk_off + (kNoAllocMaxTiles + 1);     // n
-    unsigned *perm = keys + kNoAllocMaxSamples;              // n
-    if ((st = launch_sort_into(p, theta, phi, n, keys, perm, hist, cursor, chunk_off)) != SL_OK) return st;
-    return launch_interp_perm(p, maps, theta, phi, psi, n, tod, perm);
+    SortBufs b;
+    b.rec = base;                                          // 256-byte aligned records
+    b.keys = base + kRecWords;
+    b.perm = b.keys + kNoAllocMaxSamples;
+    b.hist = b.perm + kNoAllocMaxSamples;                  // cleared by the sort before use
+    b.cursor = b.hist + (kNoAllocMaxTiles + 1);
+    b.bsum = b.cursor + kNoAllocMaxTiles;
+    b.chunk_off = nullptr;                                 // not needed by the forward path
+    const int rec64 = p->precision == SL_FP64;
+    if ((st = launch_sort_into(p, b, theta, phi, psi, n, 0, rec64, 0)) != SL_OK) return st;
+    return launch_interp(p, b, maps, psi, n, tod);
 }

@@ -102,14 +102,18 @@ static void dfree(void *ptr) {
 static sl_status ensure_sort_capacity(sl_plan *p, int64_t n) {
     if (n <= p->sort_cap) return SL_OK;
     cudaStreamSynchronize(p->stream);
-    dfree(p->d_keys);
-    dfree(p->d_perm);
-    p->bytes_held -= 2 * p->sort_cap * (int64_t)sizeof(unsigned);
-    p->d_keys = p->d_perm = nullptr;
+    dfree(p->sort.keys);
+    dfree(p->sort.perm);
+    dfree(p->sort.rec);
+    p->bytes_held -= p->sort_cap * (int64_t)(2 * sizeof(unsigned) + sizeof(StencilRec64));
+    p->sort.keys = p->sort.perm = nullptr;
+    p->sort.rec = nullptr;
     p->sort_cap = 0;
-    sl_status st = dalloc_t(p, &p->d_keys, (size_t)n, "sort keys");
+    sl_status st = dalloc_t(p, &p->sort.keys, (size_t)n, "sort keys");
     if (st != SL_OK) return st;
-    st = dalloc_t(p, &p->d_perm, (size_t)n, "sort permutation");
+    st = dalloc_t(p, &p->sort.perm, (size_t)n, "sort permutation");
+    if (st != SL_OK) return st;
+    st = dalloc(p, &p->sort.rec, (size_t)n * sizeof(StencilRec64), "stencil records");
     if (st != SL_OK) return st;
     p->sort_cap = n;
     return SL_OK;
@@ -204,17 +208,28 @@ void plan_destroy(sl_plan *p) {
     dfree(p->d_lut);
     dfree(p->d_seed);
     dfree(p->d_seed_e);
+    dfree(p->d_tab64);
+    dfree(p->d_tab32);
+    dfree(p->d_ls);
+    dfree(p->d_st64);
+    dfree(p->d_st32);
+    dfree(p->d_sky32);
+    dfree(p->d_beam32);
     dfree(p->d_tw64);
     dfree(p->d_tw32);
     if (p->d_Gadj && (void *)p->d_Gadj != p->d_G) dfree(p->d_Gadj);
     dfree(p->d_G);
     dfree(p->d_Fbar);
     dfree(p->d_Abar);
-    dfree(p->d_hist);
-    dfree(p->d_cursor);
-    dfree(p->d_chunk_off);
-    dfree(p->d_keys);
-    dfree(p->d_perm);
+    dfree(p->d_offs64);
+    dfree(p->d_rowtab32);
+    dfree(p->sort.hist);
+    dfree(p->sort.cursor);
+    dfree(p->sort.bsum);
+    dfree(p->sort.chunk_off);
+    dfree(p->sort.keys);
+    dfree(p->sort.perm);
+    dfree(p->sort.rec);
     delete p;
     cudaSetDevice(prev);
 }
@@ -264,6 +279,19 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
             for (int b = 0; b < P; ++b)
                 if (b != a) den *= ta - (long double)ring_ext[i - half + 1 + b + half];
             wden[(size_t)(i + 1) * P + a] = (double)(1.0L / den);
+        }
+    }
+    // per base row: theta(i-1+a) - theta(i-1) (double) and, for FP32 plans, the
+    // same offsets followed by wden in float
+    std::vector<double> offs64((size_t)(R + 1) * 4);
+    std::vector<float> rowtab32((size_t)(R + 1) * 8);
+    for (int i = -1; i <= R - 1; ++i) {
+        const double t0 = ring_ext[i - 1 + half];
+        for (int a = 0; a < 4; ++a) {
+            const double o = (double)((long double)ring_ext[i - 1 + a + half] - (long double)t0);
+            offs64[(size_t)(i + 1) * 4 + a] = o;
+            rowtab32[(size_t)(i + 1) * 8 + a] = (float)o;
+            rowtab32[(size_t)(i + 1) * 8 + 4 + a] = (float)wden[(size_t)(i + 1) * P + a];
         }
     }
     for (int r = 0; r < p->npairs; ++r) {
@@ -334,9 +362,15 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     TRY(cuda_check(cudaMemcpy(d_c2, c2.data(), c2.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
     TRY(cuda_check(cudaMemcpy(d_s2, s2.data(), s2.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
     TRY(cuda_check(cudaMemcpy(d_cs, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+    TRY(dalloc_t(p, &p->d_offs64, offs64.size(), "row offsets"));
+    TRY(dalloc_t(p, &p->d_rowtab32, rowtab32.size(), "row table"));
+    TRY(cuda_check(cudaMemcpy(p->d_offs64, offs64.data(), offs64.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+    TRY(cuda_check(cudaMemcpy(p->d_rowtab32, rowtab32.data(), rowtab32.size() * sizeof(float), cudaMemcpyHostToDevice), "upload"));
     p->geom.ring_ext = p->d_ring_ext;
     p->geom.wden = p->d_wden;
     p->geom.lut = p->d_lut;
+    p->geom.offs64 = p->d_offs64;
+    p->geom.rowtab32 = p->d_rowtab32;
 
     {
         size_t nseed = (size_t)(K + 1) * (L + 1) * p->npairs;
@@ -344,14 +378,38 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
         TRY(dalloc_t(p, &p->d_seed_e, nseed, "seed exponents"));
     }
     TRY(launch_seeds(p, d_c2, d_s2, d_cs));
+    // the FP64 table drives the plan-time advance in both precisions; FP32 plans
+    // keep only its float form
+    TRY(dalloc_t(p, &p->d_tab64, (size_t)(K + 1) * p->nalm, "recurrence table"));
+    if (p->precision == SL_FP32) {
+        TRY(dalloc_t(p, &p->d_tab32, (size_t)(K + 1) * p->nalm, "recurrence table"));
+        TRY(dalloc_t(p, &p->d_sky32, (size_t)p->ncomp * p->nalm, "FP32 sky"));
+        TRY(dalloc_t(p, &p->d_beam32, (size_t)p->ncomp * (K + 1) * (L + 1), "FP32 beam"));
+    }
+    TRY(launch_rtab(p));
+    {
+        const size_t nst = (size_t)(K + 1) * (L + 1) * 2 * p->npairs;
+        TRY(dalloc_t(p, &p->d_ls, nst, "start l"));
+        if (p->precision == SL_FP64) TRY(dalloc_t(p, &p->d_st64, nst, "start states"));
+        else TRY(dalloc_t(p, &p->d_st32, nst, "start states"));
+    }
+    TRY(launch_advance(p, p->precision == SL_FP64 ? 0x1p-64 : 0x1p-30));
+    if (p->precision == SL_FP32) {
+        TRY(cuda_check(cudaStreamSynchronize(p->stream), "plan advance"));
+        dfree(p->d_tab64);
+        p->d_tab64 = nullptr;
+        p->bytes_held -= (int64_t)(K + 1) * p->nalm * (int64_t)sizeof(RTab64);
+    }
     {
         size_t gel = (size_t)(K + 1) * R * (2 * L + 1);
         p->G_bytes = gel * (p->precision == SL_FP64 ? sizeof(double2) : sizeof(float2));
         TRY(dalloc(p, &p->d_G, p->G_bytes, "spin-Legendre scratch G"));
     }
-    TRY(dalloc_t(p, &p->d_hist, p->ntiles + 1, "tile histogram"));
-    TRY(dalloc_t(p, &p->d_cursor, p->ntiles, "tile cursor"));
-    TRY(dalloc_t(p, &p->d_chunk_off, p->ntiles + 1, "tile chunks"));
+    p->nkeys = sort_nkeys(p, 1);
+    TRY(dalloc_t(p, &p->sort.hist, (size_t)p->nkeys + 1, "cell histogram"));
+    TRY(dalloc_t(p, &p->sort.cursor, (size_t)p->nkeys, "cell cursor"));
+    TRY(dalloc_t(p, &p->sort.bsum, (size_t)sort_nbsum(p->nkeys) + 2, "scan block sums"));
+    TRY(dalloc_t(p, &p->sort.chunk_off, (size_t)p->ntiles + 1, "tile chunks"));
     TRY(cuda_check(cudaStreamSynchronize(p->stream), "plan seeds"));
     dfree(d_c2);
     dfree(d_s2);
@@ -403,8 +461,9 @@ sl_status interp_tod(sl_plan *p, const void *maps, const double *theta, const do
     if (!maps) return set_error(SL_ERR_ARG, "interp_tod: maps is NULL");
     if (n == 0) return SL_OK;
     if ((st = ensure_sort_capacity(p, n)) != SL_OK) return st;
-    if ((st = launch_sort(p, theta, phi, n)) != SL_OK) return st;
-    return launch_interp(p, maps, theta, phi, psi, n, tod);
+    const int rec64 = p->precision == SL_FP64;
+    if ((st = launch_sort_into(p, p->sort, theta, phi, psi, n, 1, rec64, 0)) != SL_OK) return st;
+    return launch_interp(p, p->sort, maps, psi, n, tod);
 }
 
 sl_status adjoint_interp(sl_plan *p, const double *theta, const double *phi, const double *psi,
@@ -417,8 +476,8 @@ sl_status adjoint_interp(sl_plan *p, const double *theta, const double *phi, con
     if ((st = cuda_check(cudaMemsetAsync(maps_bar, 0, bytes, p->stream), "memset maps_bar")) != SL_OK) return st;
     if (n == 0) return SL_OK;
     if ((st = ensure_sort_capacity(p, n)) != SL_OK) return st;
-    if ((st = launch_sort(p, theta, phi, n)) != SL_OK) return st;
-    return launch_interp_adjoint(p, theta, phi, psi, tod, n, (double2 *)maps_bar);
+    if ((st = launch_sort_into(p, p->sort, theta, phi, psi, n, 1, 1, 1)) != SL_OK) return st;
+    return launch_interp_adjoint(p, p->sort, 1, psi, tod, n, (double2 *)maps_bar);
 }
 
 sl_status adjoint_synth(sl_plan *p, const double *maps_bar, const double *sky, const double *beam,

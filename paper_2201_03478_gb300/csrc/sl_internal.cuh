@@ -42,6 +42,41 @@ struct InterpGeom {
     double lut_scale;             // nlut / pi
     double phi_scale;             // nphi / (2 pi)
     int tile_cols, ntr, ntc;      // tile grid: ntr = ceil((R+1)/kTileRows), ntc = ceil(nphi/tile_cols)
+    const double *offs64;         // [(R+1) * 4]: theta(i-1+a) - theta(i-1) per base row i
+    const float *rowtab32;        // [(R+1) * 8]: the same offsets, then wden, in float
+};
+
+// Per-sample stencil record written by the binning kernel: the colatitude
+// offset from the stencil's first row, the phi fraction in [0, 1), and the
+// cell (i+1) * nphi + j; FP32 plans also keep psi reduced to [-pi, pi].
+struct StencilRec64 {
+    double dth, fph;
+    unsigned cell, pad;
+};
+struct __align__(16) StencilRec32 {
+    float dth, fph, psr;
+    unsigned cell;
+};
+
+// Device buffers of one pointing sort.
+struct SortBufs {
+    unsigned *keys;       // [n]
+    unsigned *perm;       // [n]
+    void *rec;            // [n] StencilRec64 or StencilRec32
+    unsigned *hist;       // [nkeys + 1]: key counts, then first position of each key
+    unsigned *cursor;     // [nkeys]
+    unsigned *bsum;       // [nkeys / 4096 + 2]
+    unsigned *chunk_off;  // [ntiles + 1]
+};
+
+// Rescaled l-recurrence coefficients per (k, m, l), stored at
+// [k][m(2L+1-m)/2 + l] (the sky's packing): y_{l+1} = (a x -+ b) y_l - y_{l-1},
+// d_l = c y_l.  FP32 plans keep c'+- = a -+ b - 2 for the difference form.
+struct __align__(32) RTab64 {
+    double a, b, c, unused;
+};
+struct __align__(16) RTab32 {
+    float a, cp, cm, c;
 };
 
 struct KernelTimer {
@@ -64,6 +99,8 @@ struct sl_plan {
     float *d_y32 = nullptr;           // [npairs] 1 - cos(theta) = 2 sin^2(theta/2), FP32
     double *d_ring_ext = nullptr;
     double *d_wden = nullptr;
+    double *d_offs64 = nullptr;
+    float *d_rowtab32 = nullptr;
     int *d_lut = nullptr;
     int nlut = 0;
     sl::InterpGeom geom;
@@ -71,6 +108,17 @@ struct sl_plan {
     // seeds: [K+1][L+1][npairs] (mantissa for +k, -k) and exponents
     double2 *d_seed = nullptr;
     int2 *d_seed_e = nullptr;
+    // rescaled recurrence tables [K+1][nalm] (one of the two, by precision)
+    sl::RTab64 *d_tab64 = nullptr;
+    sl::RTab32 *d_tab32 = nullptr;
+    // per-call start states [K+1][L+1][2 signs][npairs]: first significant l and
+    // the recurrence state there (FP64 plans: st64, FP32 plans: st32)
+    int *d_ls = nullptr;
+    double2 *d_st64 = nullptr;
+    float2 *d_st32 = nullptr;
+    // FP32 copies of sky and beam (FP32 plans)
+    float2 *d_sky32 = nullptr;
+    float2 *d_beam32 = nullptr;
 
     // ring FFT
     double2 *d_tw64 = nullptr;        // [nphi] e^{+2 pi i j / nphi}
@@ -84,13 +132,10 @@ struct sl_plan {
     double2 *d_Gadj = nullptr;        // FP64 copy for FP32 plans (adjoint), else aliases d_G
     double2 *d_Fbar = nullptr;        // [R][nphi][K+1] adjoint cube
     double2 *d_Abar = nullptr;        // [K+1][2L+1][L+1]
-    // pointing sort
+    // pointing sort (fine cell keys; per-sample scratch grown on demand)
     int ntiles = 0;
-    unsigned *d_hist = nullptr;       // [ntiles + 1]
-    unsigned *d_cursor = nullptr;     // [ntiles]
-    unsigned *d_chunk_off = nullptr;  // [ntiles + 1]
-    unsigned *d_keys = nullptr;       // [cap]
-    unsigned *d_perm = nullptr;       // [cap]
+    int64_t nkeys = 0;
+    sl::SortBufs sort = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int64_t sort_cap = 0;
 
     int64_t bytes_held = 0;
@@ -114,21 +159,26 @@ void timing_end(sl_plan *p, int idx);
 
 // launchers (one per translation unit)
 sl_status launch_seeds(sl_plan *p, const double *d_c2, const double *d_s2, const double *d_cs);
+sl_status launch_rtab(sl_plan *p);
+sl_status launch_advance(sl_plan *p, double thr);
 sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam);
 sl_status launch_ringfft_synth(sl_plan *p, void *maps);
-sl_status launch_sort(sl_plan *p, const double *theta, const double *phi, int64_t n);
-sl_status launch_interp(sl_plan *p, const void *maps, const double *theta, const double *phi,
-                        const double *psi, int64_t n, double *tod);
-sl_status launch_interp_adjoint(sl_plan *p, const double *theta, const double *phi,
-                                const double *psi, const double *tod, int64_t n, double2 *fbar);
+// Sort of n pointings into b: fine (cell) or coarse (tile) keys, FP64 or FP32
+// stencil records; with_chunks also builds the adjoint's per-tile work items.
+int64_t sort_nkeys(const sl_plan *p, int fine);
+int64_t sort_nbsum(int64_t nkeys);
+sl_status launch_sort_into(sl_plan *p, const SortBufs &b, const double *theta, const double *phi,
+                           const double *psi, int64_t n, int fine, int rec64, int with_chunks);
+// Forward interpolation over a sort (records in the plan's precision).
+sl_status launch_interp(sl_plan *p, const SortBufs &b, const void *maps, const double *psi, int64_t n,
+                        double *tod);
+// Adjoint scatter over a sort made with rec64 = 1, with_chunks = 1.
+sl_status launch_interp_adjoint(sl_plan *p, const SortBufs &b, int fine, const double *psi, const double *tod,
+                                int64_t n, double2 *fbar);
 sl_status launch_ringdft_adjoint(sl_plan *p, const double2 *fbar);
 sl_status launch_lcontract_adjoint(sl_plan *p);
 sl_status launch_grad(sl_plan *p, const double *sky, const double *beam, double *sky_grad,
                       double *beam_grad, int accumulate);
-sl_status launch_sort_into(sl_plan *p, const double *theta, const double *phi, int64_t n, unsigned *keys,
-                           unsigned *perm, unsigned *hist, unsigned *cursor, unsigned *chunk_off);
-sl_status launch_interp_perm(sl_plan *p, const void *maps, const double *theta, const double *phi,
-                             const double *psi, int64_t n, double *tod, const unsigned *perm);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -159,10 +209,6 @@ __device__ __forceinline__ int locate_col(const InterpGeom &g, double phi, doubl
     if (j > g.nphi - 1) j = g.nphi - 1;
     f = u - (double)j;
     return j;
-}
-
-__device__ __forceinline__ unsigned tile_key(const InterpGeom &g, int i, int j) {
-    return (unsigned)((i + 1) / kTileRows) * (unsigned)g.ntc + (unsigned)(j / g.tile_cols);
 }
 
 }  // namespace sl

@@ -61,6 +61,10 @@ CASES = {
     "polarised_k0": lambda: _case(24, 0, W.equiangular_ring_theta(24), 48, 3000, ncomp=3, seed=5),
     # polarised, nphi = 50 (radix 5), K = L
     "polarised_kmax_eq_lmax": lambda: _case(12, 12, W.healpix_ring_theta(4), 50, 3000, ncomp=3, seed=7),
+    # larger band limit on equiangular rings: deep polar evanescent zones (recurrence
+    # start states well past l0), nphi = 400 = 2^4 5^2 < 2L+1, scan pointings
+    "medium_polar_scan": lambda: _case(200, 6, W.equiangular_ring_theta(200), 400, 20000, seed=9,
+                                       pointings="scan"),
 }
 
 

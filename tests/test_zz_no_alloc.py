@@ -45,7 +45,7 @@ def test_interp_tod_noalloc_matches_interp_tod():
         assert err < 1e-12, (n, err)
 
     # sizes beyond the static scratch are rejected before any launch
-    big = (1 << 20) + 1
+    big = (1 << 18) + 1
     st = lib.interp_tod_noalloc(plan.ptr, P(maps), P(th), P(ph), P(ps), big, P(got))
     assert st == _lib.SL_ERR_ARG
     assert b"static scratch" in lib.sl_last_error()
