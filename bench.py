@@ -218,7 +218,10 @@ def gpu_arm(args):
     value = world * n * args.steps / (ms_total / 1e3)
 
     # ---- roofline of the two big kernels (CUDA events around each launch, same stream)
-    fl_lc, fl_in = algorithmic_flops(L, K, R, n)
+    fl_dense, fl_in = algorithmic_flops(L, K, R, n)
+    # the contraction skips the evanescent zone: count the work it executes,
+    # 11 flops (3 recurrence + 2 complex x real MACs) per visited (ring, m, k, sign, l)
+    fl_lc = 11.0 * plan.sizes()["lsteps"]
     prec = args.precision
     peak = PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS
     roofs = {}
@@ -232,6 +235,10 @@ def gpu_arm(args):
                            "traffic": TRAFFIC.get((name, prec)), "avg_ms": round(avg_ms, 4),
                            "flops_per_launch": fl,
                            "peak_note": "derived from unit counts x 2.07 GHz max SM clock"}
+    lc_name = "lcontract_%s" % ("f64" if prec == "fp64" else "f32")
+    if lc_name in roofs:
+        roofs[lc_name]["flops_dense_triangle"] = fl_dense
+        roofs[lc_name]["dense_equivalent_tflops"] = round(fl_dense / (roofs[lc_name]["avg_ms"] / 1e3) / 1e12, 4)
     dominant = max(stats.items(), key=lambda kv: kv[1][1])[0] if stats else None
     shares = {k: round(v[1] / max(1e-9, sum(x[1] for x in stats.values())), 4) for k, v in stats.items()}
     launches = sum(v[0] for v in stats.values())

@@ -180,6 +180,10 @@ typedef struct {
     int64_t beam_doubles;  /* ncomp * (kmax+1) * (lmax+1) * 2 */
     int64_t maps_bytes;    /* nrings * nphi * (kmax+1) * (16 or 8) */
     int64_t scratch_bytes; /* device memory the plan holds right now */
+    int64_t lsteps;        /* recurrence steps one synth_spin_maps runs: sum over
+                              (north ring, m, k, sign of k) of the l it visits
+                              (the evanescent part below the significance
+                              threshold is skipped) */
 } sl_plan_sizes;
 sl_status sl_plan_get_sizes(const sl_plan *plan, sl_plan_sizes *out);
 

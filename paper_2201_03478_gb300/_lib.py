@@ -32,7 +32,7 @@ class PlanDesc(ctypes.Structure):
 
 class PlanSizes(ctypes.Structure):
     _fields_ = [("nalm", ctypes.c_int64), ("sky_doubles", ctypes.c_int64), ("beam_doubles", ctypes.c_int64),
-                ("maps_bytes", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64)]
+                ("maps_bytes", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64), ("lsteps", ctypes.c_int64)]
 
 
 class KernelStat(ctypes.Structure):

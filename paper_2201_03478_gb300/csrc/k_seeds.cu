@@ -12,6 +12,8 @@
 // upward with the ratio
 //   d^m_{m,q} / d^{m-1}_{m-1,q} = -sqrt(2m (2m-1) / ((m+q)(m-q))) c s,
 // so each seed costs O(1) instead of O(m).
+#include <algorithm>
+
 #include "sl_internal.cuh"
 
 namespace sl {
@@ -197,6 +199,29 @@ sl_status launch_advance(sl_plan *p, double thr) {
                                                         p->d_st32);
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_advance launch");
+}
+
+// Number of recurrence steps the per-call contraction runs: sum of (L + 1 - ls).
+__global__ void k_count_lsteps(int L, int64_t n, const int *__restrict__ ls, unsigned long long *__restrict__ out) {
+    unsigned long long s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += (unsigned long long)max(0, L + 1 - ls[i]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+sl_status count_lsteps(sl_plan *p, int64_t *out) {
+    unsigned long long *d = nullptr, h = 0;
+    sl_status st = cuda_check(cudaMalloc(&d, sizeof(unsigned long long)), "count alloc");
+    if (st != SL_OK) return st;
+    const int64_t n = (int64_t)(p->K + 1) * (p->L + 1) * 2 * p->npairs;
+    cudaMemsetAsync(d, 0, sizeof(unsigned long long), p->stream);
+    k_count_lsteps<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, p->stream>>>(p->L, n, p->d_ls, d);
+    st = cuda_check(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, p->stream), "count copy");
+    if (st == SL_OK) st = cuda_check(cudaStreamSynchronize(p->stream), "count sync");
+    cudaFree(d);
+    *out = (int64_t)h;
+    return st;
 }
 
 sl_status launch_seeds(sl_plan *p, const double *d_c2, const double *d_s2, const double *d_cs) {

@@ -394,6 +394,7 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
         else TRY(dalloc_t(p, &p->d_st32, nst, "start states"));
     }
     TRY(launch_advance(p, p->precision == SL_FP64 ? 0x1p-64 : 0x1p-30));
+    TRY(count_lsteps(p, &p->lsteps));
     if (p->precision == SL_FP32) {
         TRY(cuda_check(cudaStreamSynchronize(p->stream), "plan advance"));
         dfree(p->d_tab64);
@@ -511,6 +512,7 @@ sl_status sl_plan_get_sizes(const sl_plan *p, sl_plan_sizes *o) {
     o->beam_doubles = (int64_t)p->ncomp * (p->K + 1) * (p->L + 1) * 2;
     o->maps_bytes = (int64_t)p->R * p->nphi * (p->K + 1) * (p->precision == SL_FP64 ? 16 : 8);
     o->scratch_bytes = p->bytes_held;
+    o->lsteps = p->lsteps;
     return SL_OK;
 }
 

@@ -116,6 +116,7 @@ struct sl_plan {
     int *d_ls = nullptr;
     double2 *d_st64 = nullptr;
     float2 *d_st32 = nullptr;
+    int64_t lsteps = 0;               // recurrence steps per synth call
     // FP32 copies of sky and beam (FP32 plans)
     float2 *d_sky32 = nullptr;
     float2 *d_beam32 = nullptr;
@@ -161,6 +162,7 @@ void timing_end(sl_plan *p, int idx);
 sl_status launch_seeds(sl_plan *p, const double *d_c2, const double *d_s2, const double *d_cs);
 sl_status launch_rtab(sl_plan *p);
 sl_status launch_advance(sl_plan *p, double thr);
+sl_status count_lsteps(sl_plan *p, int64_t *out);
 sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam);
 sl_status launch_ringfft_synth(sl_plan *p, void *maps);
 // Sort of n pointings into b: fine (cell) or coarse (tile) keys, FP64 or FP32
