@@ -80,11 +80,22 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const do
         for (int q = 0; q < 16; ++q) w[q] = wt[q >> 2] * wp[q & 3];
         double sp, cp;
         sincos(psi[s], &sp, &cp);
-        const double c2 = 2.0 * cp;
-        // cos(k psi), sin(k psi) by the Chebyshev three-term recurrence
-        double ck = 1.0, sk = 0.0, ckm = cp, skm = -sp;
+        // k = 0: only Re S_0 enters the TOD
         double acc = 0.0;
-        for (int k = 0; k <= g.K; ++k) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc = fma(w[q], __ldg(maps + off[q]).x, acc);
+        // C_k = 2 cos(k psi), S_k = 2 sin(k psi) by the Chebyshev three-term
+        // recurrence X_{k+1} = (2 cos psi) X_k - X_{k-1}
+        const double c1 = 2.0 * cp;
+        double Ck = c1, Sk = 2.0 * sp, Ckm = 2.0, Skm = 0.0;
+        for (int k = 1; k <= g.K; ++k) {
+            if (ghost) {   // (-1)^k on ghost rows: flip their weights between k-1 and k
+#pragma unroll
+                for (int ra = 0; ra < 4; ++ra)
+                    if (ghost & (1u << ra))
+#pragma unroll
+                        for (int cb = 0; cb < 4; ++cb) w[ra * 4 + cb] = -w[ra * 4 + cb];
+            }
             double sr = 0.0, si = 0.0;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
@@ -92,24 +103,13 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const do
                 sr = fma(w[q], v.x, sr);
                 si = fma(w[q], v.y, si);
             }
-            if (k == 0) {
-                acc = sr;
-            } else {
-                acc = fma(2.0 * ck, sr, acc);
-                acc = fma(-2.0 * sk, si, acc);
-            }
-            const double cn = fma(c2, ck, -ckm), sn = fma(c2, sk, -skm);
-            ckm = ck;
-            skm = sk;
-            ck = cn;
-            sk = sn;
-            if (ghost) {   // (-1)^k on ghost rows: flip their weights between k and k+1
-#pragma unroll
-                for (int ra = 0; ra < 4; ++ra)
-                    if (ghost & (1u << ra))
-#pragma unroll
-                        for (int cb = 0; cb < 4; ++cb) w[ra * 4 + cb] = -w[ra * 4 + cb];
-            }
+            acc = fma(Ck, sr, acc);
+            acc = fma(-Sk, si, acc);
+            const double cn = fma(c1, Ck, -Ckm), sn = fma(c1, Sk, -Skm);
+            Ckm = Ck;
+            Skm = Sk;
+            Ck = cn;
+            Sk = sn;
         }
         tod[s] = acc;
     }
@@ -118,13 +118,24 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const do
 // ------------------------------------------------------------------ forward FP32 maps
 // FP64 only for the stored record (made by the binning kernel) and the final
 // value; weights, the e^{ik psi} ladder and the stencil sums in FP32.
-__global__ void __launch_bounds__(256) k_interp_f32(const InterpGeom g, const float2 *__restrict__ maps,
+__global__ void __launch_bounds__(256, 3) k_interp_f32(const InterpGeom g, const float2 *__restrict__ maps,
                                                     const StencilRec32 *__restrict__ rec,
                                                     const unsigned *__restrict__ perm, int64_t n,
                                                     double *__restrict__ tod) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned s = perm[t];
-        const StencilRec32 r = rec[s];
+    // software pipeline over this thread's samples: the permutation entry two
+    // samples ahead and the record one sample ahead are in flight while the
+    // current sample is evaluated
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned s_next = (t < n) ? perm[t] : 0u;
+    unsigned s_next2 = (t + stride < n) ? perm[t + stride] : 0u;
+    StencilRec32 r_next = (t < n) ? rec[s_next] : StencilRec32{0.f, 0.f, 0.f, 0u};
+    for (; t < n; t += stride) {
+        const unsigned s = s_next;
+        const StencilRec32 r = r_next;
+        s_next = s_next2;
+        if (t + stride < n) r_next = rec[s_next];
+        if (t + 2 * stride < n) s_next2 = perm[t + 2 * stride];
         const int i = (int)(r.cell / (unsigned)g.nphi) - 1, j = (int)(r.cell % (unsigned)g.nphi);
         const float4 of = __ldg(reinterpret_cast<const float4 *>(g.rowtab32) + 2 * (i + 1));
         const float4 wd = __ldg(reinterpret_cast<const float4 *>(g.rowtab32) + 2 * (i + 1) + 1);
@@ -142,27 +153,37 @@ __global__ void __launch_bounds__(256) k_interp_f32(const InterpGeom g, const fl
         for (int q = 0; q < 16; ++q) w[q] = wt[q >> 2] * wp[q & 3];
         float sz, cz;
         sincosf(r.psr, &sz, &cz);
-        float zr = 1.f, zi = 0.f, acc1 = 0.f, acc0 = 0.f;
-        for (int k = 0; k <= g.K; ++k) {
-            float sr = 0.f, si = 0.f;
+        // k = 0: only Re S_0 enters the TOD (two independent chains)
+        float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const float2 v = __ldg(maps + off[q] + k);
-                sr = fmaf(w[q], v.x, sr);
-                si = fmaf(w[q], v.y, si);
-            }
-            if (k == 0) acc0 = sr;
-            else acc1 += zr * sr - zi * si;
-            const float nr = zr * cz - zi * sz, ni = zr * sz + zi * cz;
-            zr = nr;
-            zi = ni;
-            if (ghost) {
+        for (int q = 0; q < 8; ++q) {
+            a0 = fmaf(w[q], __ldg(maps + off[q]).x, a0);
+            a1 = fmaf(w[q + 8], __ldg(maps + off[q + 8]).x, a1);
+        }
+        const float acc0 = a0 + a1;
+        float zr = cz, zi = sz, acc1 = 0.f;
+        for (int k = 1; k <= g.K; ++k) {
+            if (ghost) {   // (-1)^k on ghost rows
 #pragma unroll
                 for (int ra = 0; ra < 4; ++ra)
                     if (ghost & (1u << ra))
 #pragma unroll
                         for (int cb = 0; cb < 4; ++cb) w[ra * 4 + cb] = -w[ra * 4 + cb];
             }
+            float sr0 = 0.f, si0 = 0.f, sr1 = 0.f, si1 = 0.f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float2 v0 = __ldg(maps + off[q] + k), v1 = __ldg(maps + off[q + 8] + k);
+                sr0 = fmaf(w[q], v0.x, sr0);
+                si0 = fmaf(w[q], v0.y, si0);
+                sr1 = fmaf(w[q + 8], v1.x, sr1);
+                si1 = fmaf(w[q + 8], v1.y, si1);
+            }
+            const float sr = sr0 + sr1, si = si0 + si1;
+            acc1 = fmaf(zr, sr, fmaf(-zi, si, acc1));
+            const float nr = zr * cz - zi * sz, ni = zr * sz + zi * cz;
+            zr = nr;
+            zi = ni;
         }
         tod[s] = (double)acc0 + 2.0 * (double)acc1;
     }

@@ -46,8 +46,9 @@ __global__ void __launch_bounds__(256) k_bin(const InterpGeom g, int fine, const
             if (REC64) {
                 reinterpret_cast<StencilRec64 *>(rec)[s] = StencilRec64{dth, f, cell, 0u};
             } else {
-                const double ps = psi[s];
-                const float pr = (float)(ps - 6.283185307179586 * rint(ps * 0.15915494309189535));
+                double ps = psi[s];
+                if (!(fabs(ps) <= 3.141592653589793)) ps -= 6.283185307179586 * rint(ps * 0.15915494309189535);
+                const float pr = (float)ps;
                 reinterpret_cast<StencilRec32 *>(rec)[s] = StencilRec32{(float)dth, (float)f, pr, cell};
             }
         }

@@ -194,8 +194,9 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 // Locate the base row i in [-1, R-1] of the interpolation stencil: the largest
 // i with theta_ext(i) <= theta.  NaN maps to a valid row (result is NaN).
 __device__ __forceinline__ int locate_row(const InterpGeom &g, double theta) {
-    double tb = theta * g.lut_scale;
-    int b = (tb >= 0.0) ? ((tb < (double)(g.nlut - 1)) ? (int)tb : g.nlut - 1) : 0;
+    // the conversion saturates (NaN gives 0); the bin is clamped in integers
+    int b = __double2int_rz(theta * g.lut_scale);
+    b = min(max(b, 0), g.nlut - 1);
     int i = __ldg(g.lut + b);
     // ring_ext index of row r is r + half
     while (i < g.R - 1 && __ldg(g.ring_ext + i + 1 + g.half) <= theta) ++i;
@@ -205,10 +206,10 @@ __device__ __forceinline__ int locate_row(const InterpGeom &g, double theta) {
 // phi -> base column j in [0, nphi) and fractional offset f in [0, 1).
 __device__ __forceinline__ int locate_col(const InterpGeom &g, double phi, double &f) {
     double u = phi * g.phi_scale;
-    double n = (double)g.nphi;
-    u -= n * floor(u * (1.0 / n));
-    int j = (u >= 0.0) ? ((u < n) ? (int)u : g.nphi - 1) : 0;
-    if (j > g.nphi - 1) j = g.nphi - 1;
+    const double n = (double)g.nphi;
+    if (!(u >= 0.0 && u < n)) u -= n * floor(u * (1.0 / n));   // phi outside [0, 2 pi)
+    int j = __double2int_rz(u);
+    j = min(max(j, 0), g.nphi - 1);
     f = u - (double)j;
     return j;
 }
