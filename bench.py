@@ -265,6 +265,29 @@ def gpu_arm(args):
     if rank == 0:
         out["clocks"] = clk
 
+    # ---- adjoint (gradients of sum_i y_i c_i w.r.t. sky and beam) on the same pointings
+    if args.adjoint_steps > 0:
+        gs = torch.zeros_like(sky)
+        gb = torch.zeros_like(beam)
+        y = tod.clone()
+        sl.adjoint_tod(plan, theta, phi, psi, y, sky, beam, gs, gb)          # warm (allocates scratch)
+        torch.cuda.synchronize()
+        plan.enable_timing(True)
+        plan.kernel_stats(reset=True)
+        barrier(device)
+        e0.record(stream)
+        for _ in range(args.adjoint_steps):
+            sl.adjoint_tod(plan, theta, phi, psi, y, sky, beam, gs, gb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_adj = reduce_max(e0.elapsed_time(e1), device) / args.adjoint_steps
+        st_adj = plan.kernel_stats(reset=True)
+        plan.enable_timing(False)
+        out["adjoint"] = {"value": world * n / (ms_adj / 1e3), "unit": "samples/s", "ms_per_step": ms_adj,
+                          "steps": args.adjoint_steps, "precision": "fp64",
+                          "kernel_ms_per_step": {k: round(v[1] / args.adjoint_steps, 4) for k, v in st_adj.items()}}
+        del gs, gb, y
+
     # ---- the other precision on the same box, compared with this run's TOD
     if args.compare and rank == 0 and world == 1:
         other = "fp32" if prec == "fp64" else "fp64"
@@ -397,6 +420,7 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--n", type=float, default=1e8, help="pointings per GPU")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--adjoint-steps", type=int, default=3, help="timed adjoint_tod calls (0: skip)")
     ap.add_argument("--no-compare", dest="compare", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-rings", type=int, default=96)

@@ -150,7 +150,7 @@ sl_status adjoint_synth(sl_plan *plan, const double *maps_bar, const double *sky
  * long-running acquisition loops that cannot take the implicit device
  * synchronisation of cudaMalloc/cudaFree.  interp_tod may grow the plan's sort
  * scratch with cudaMalloc when n exceeds every earlier call; this entry point
- * never allocates: its sort scratch is one static device array of 8.5 MiB
+ * never allocates: its sort scratch is one static device array of 8.75 MiB
  * that every GPU loading the library holds until the process exits.
  *
  * Same arguments, layout and result as interp_tod (the plan is created

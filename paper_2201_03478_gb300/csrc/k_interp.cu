@@ -189,6 +189,125 @@ __global__ void __launch_bounds__(256, 3) k_interp_f32(const InterpGeom g, const
     }
 }
 
+// ------------------------------------------------------------------ forward FP32, tile-staged
+// One CTA per work item (<= kChunkA sorted samples of one tile).  The tile's
+// stencil nodes -- rows tr*4-2 .. tr*4+4 and columns tc*TC-1 .. tc*TC+TC+1,
+// every k -- are staged into shared memory with coalesced loads (each tile row
+// is one or two contiguous spans of the cube); ghost rows are folded in while
+// staging (ring at phi + pi, factor (-1)^k), and k is padded to an even count
+// so that a pair of k is one 128-bit load.  Samples are then evaluated from
+// shared memory; the lanes of a warp mostly share one cell (broadcast reads).
+struct TiledArgs {
+    InterpGeom g;
+    const float2 *maps;
+    const StencilRec32 *rec;
+    const unsigned *perm, *start, *chunk_off;
+    int ntiles, ncell;
+    double *tod;
+};
+
+__device__ __forceinline__ int find_tile(const unsigned *chunk_off, int ntiles, unsigned v) {
+    int lo = 0, hi = ntiles - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (chunk_off[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
+    const InterpGeom &g = A.g;
+    const int K1 = g.K + 1, Kp = (K1 + 1) & ~1;
+    const int TC = g.tile_cols, tw = TC + 3, nrow = kTileRows + 3;
+    const int rowspan = tw * K1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *node = reinterpret_cast<float2 *>(smem_raw);   // [nrow][tw][Kp]
+    const unsigned nchunks = A.chunk_off[A.ntiles];
+    int staged_tile = -1;
+    for (unsigned v = blockIdx.x; v < nchunks; v += gridDim.x) {
+        const int tile = find_tile(A.chunk_off, A.ntiles, v);
+        const unsigned c = v - A.chunk_off[tile];
+        const unsigned s_beg = A.start[(int64_t)tile * A.ncell] + c * kChunkA;
+        const unsigned s_end = min(A.start[(int64_t)(tile + 1) * A.ncell], s_beg + kChunkA);
+        const int tr = tile / g.ntc, tcol = tile % g.ntc;
+        const int rowlo = tr * kTileRows - 2, collo = tcol * TC - 1;
+        if (tile != staged_tile) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < nrow * rowspan; e += blockDim.x) {
+                const int r = e / rowspan, x = e - r * rowspan;
+                const int cc = x / K1, k = x - cc * K1;
+                const int row = rowlo + r;
+                float2 val = make_float2(0.f, 0.f);
+                if (row >= -2 && row <= g.R + 1) {
+                    int ring = row, col = collo + cc;
+                    bool flip = false;
+                    if (row < 0 || row >= g.R) {
+                        ring = (row < 0) ? -1 - row : 2 * g.R - 1 - row;
+                        col += g.nphi / 2;
+                        flip = k & 1;
+                    }
+                    col %= g.nphi;
+                    if (col < 0) col += g.nphi;
+                    val = __ldg(A.maps + ((int64_t)ring * g.nphi + col) * K1 + k);
+                    if (flip) { val.x = -val.x; val.y = -val.y; }
+                }
+                node[(r * tw + cc) * Kp + k] = val;
+            }
+            if (Kp != K1)
+                for (int e = threadIdx.x; e < nrow * tw; e += blockDim.x) node[e * Kp + K1] = make_float2(0.f, 0.f);
+            __syncthreads();
+            staged_tile = tile;
+        }
+        for (unsigned t = s_beg + threadIdx.x; t < s_end; t += blockDim.x) {
+            const unsigned s = A.perm[t];
+            const StencilRec32 r = A.rec[s];
+            const int i = (int)(r.cell / (unsigned)g.nphi) - 1, j = (int)(r.cell % (unsigned)g.nphi);
+            const float4 of = __ldg(reinterpret_cast<const float4 *>(g.rowtab32) + 2 * (i + 1));
+            const float4 wd = __ldg(reinterpret_cast<const float4 *>(g.rowtab32) + 2 * (i + 1) + 1);
+            const float d0 = r.dth, d1 = d0 - of.y, d2 = d0 - of.z, d3 = d0 - of.w;
+            const float p01 = d0 * d1, p23 = d2 * d3;
+            const float wt[4] = {wd.x * d1 * p23, wd.y * d0 * p23, wd.z * p01 * d3, wd.w * p01 * d2};
+            const float f = r.fph;
+            const float a = f + 1.f, cm = f - 1.f, d = f - 2.f;
+            const float cd = cm * d, ab = a * f;
+            const float wp[4] = {-f * cd * (1.f / 6.f), a * cd * 0.5f, -ab * d * 0.5f, ab * cm * (1.f / 6.f)};
+            float w[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) w[q] = wt[q >> 2] * wp[q & 3];
+            const float2 *nb = node + ((i - 1 - rowlo) * tw + (j - 1 - collo)) * Kp;
+            float sz, cz;
+            sincosf(r.psr, &sz, &cz);
+            // z^k for the pair (k, k+1), starting at (1, z)
+            float z0r = 1.f, z0i = 0.f, z1r = cz, z1i = sz;
+            const float z2r = cz * cz - sz * sz, z2i = 2.f * cz * sz;
+            float acc0 = 0.f, acc1 = 0.f;
+            for (int k = 0; k < K1; k += 2) {
+                float sr0 = 0.f, si0 = 0.f, sr1 = 0.f, si1 = 0.f;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const float4 v = *reinterpret_cast<const float4 *>(nb + ((q >> 2) * tw + (q & 3)) * Kp + k);
+                    sr0 = fmaf(w[q], v.x, sr0);
+                    si0 = fmaf(w[q], v.y, si0);
+                    sr1 = fmaf(w[q], v.z, sr1);
+                    si1 = fmaf(w[q], v.w, si1);
+                }
+                if (k == 0) acc0 = sr0;
+                else acc1 = fmaf(z0r, sr0, fmaf(-z0i, si0, acc1));
+                acc1 = fmaf(z1r, sr1, fmaf(-z1i, si1, acc1));   // padding slot holds zeros
+                const float n0r = z0r * z2r - z0i * z2i, n0i = z0r * z2i + z0i * z2r;
+                const float n1r = z1r * z2r - z1i * z2i, n1i = z1r * z2i + z1i * z2r;
+                z0r = n0r; z0i = n0i; z1r = n1r; z1i = n1i;
+            }
+            A.tod[s] = (double)acc0 + 2.0 * (double)acc1;
+        }
+    }
+}
+
+size_t interp_f32_tiled_smem(const sl_plan *p) {
+    const int K1 = p->K + 1, Kp = (K1 + 1) & ~1;
+    return (size_t)(kTileRows + 3) * (p->geom.tile_cols + 3) * Kp * sizeof(float2);
+}
+
 // ------------------------------------------------------------------ adjoint
 // maps_bar_k(node) += y wt_a wp_b sigma_{a,k} eps_k e^{-ik psi},  eps_0 = 1, eps_k = 2.
 struct AdjArgs {
@@ -322,13 +441,33 @@ static unsigned grid_for(int64_t n, int bs) {
     return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
-sl_status launch_interp(sl_plan *p, const SortBufs &b, const void *maps, const double *psi, int64_t n,
+sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *maps, const double *psi, int64_t n,
                         double *tod) {
     int slot;
     if (p->precision == SL_FP64) {
         slot = timing_begin(p, "interp_f64");
         k_interp_f64<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const double2 *)maps,
                                                              (const StencilRec64 *)b.rec, psi, b.perm, n, tod);
+    } else if (b.chunk_off) {
+        TiledArgs a;
+        a.g = p->geom;
+        a.maps = (const float2 *)maps;
+        a.rec = (const StencilRec32 *)b.rec;
+        a.perm = b.perm;
+        a.start = b.hist;
+        a.chunk_off = b.chunk_off;
+        a.ntiles = p->ntiles;
+        a.ncell = fine ? kTileRows * p->geom.tile_cols : 1;
+        a.tod = tod;
+        const size_t sm = interp_f32_tiled_smem(p);
+        cudaError_t e = cudaFuncSetAttribute(k_interp_f32_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return cuda_check(e, "k_interp_f32_tiled smem attribute");
+        int per_sm = 1, nsm = 152;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_f32_tiled, 256, sm);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
+        if (per_sm < 1) per_sm = 1;
+        slot = timing_begin(p, "interp_f32");
+        k_interp_f32_tiled<<<(unsigned)(nsm * per_sm), 256, sm, p->stream>>>(a);
     } else {
         slot = timing_begin(p, "interp_f32");
         k_interp_f32<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const float2 *)maps,

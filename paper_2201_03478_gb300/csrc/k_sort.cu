@@ -34,8 +34,9 @@ __global__ void __launch_bounds__(256) k_bin(const InterpGeom g, int fine, const
         if (ok) {
             const double th = theta[s];
             const int i = locate_row(g, th);
-            double f;
-            const int j = locate_col(g, phi[s], f);
+            unsigned long long fr;
+            int sh;
+            const int j = locate_col_bits(g, phi[s], fr, sh);
             const int tr = (i + 1) / kTileRows, li = (i + 1) - tr * kTileRows;
             const int tc = j / g.tile_cols, lj = j - tc * g.tile_cols;
             const unsigned tile = (unsigned)tr * (unsigned)g.ntc + (unsigned)tc;
@@ -44,12 +45,14 @@ __global__ void __launch_bounds__(256) k_bin(const InterpGeom g, int fine, const
             const double dth = th - __ldg(g.ring_ext + g.half + i - 1);
             const unsigned cell = (unsigned)(i + 1) * (unsigned)g.nphi + (unsigned)j;
             if (REC64) {
-                reinterpret_cast<StencilRec64 *>(rec)[s] = StencilRec64{dth, f, cell, 0u};
+                reinterpret_cast<StencilRec64 *>(rec)[s] = StencilRec64{dth, frac_bits_d(fr, sh), cell, 0u};
             } else {
                 double ps = psi[s];
-                if (!(fabs(ps) <= 3.141592653589793)) ps -= 6.283185307179586 * rint(ps * 0.15915494309189535);
-                const float pr = (float)ps;
-                reinterpret_cast<StencilRec32 *>(rec)[s] = StencilRec32{(float)dth, (float)f, pr, cell};
+                // |psi| <= pi compared on the bit pattern; larger |psi| reduced in FP64
+                const long long pb = __double_as_longlong(ps) & 0x7fffffffffffffffll;
+                if (pb > 0x400921fb54442d18ll) ps -= 6.283185307179586 * rint(ps * 0.15915494309189535);
+                reinterpret_cast<StencilRec32 *>(rec)[s] =
+                    StencilRec32{d2f_bits(dth), frac_bits_f(fr, sh), d2f_bits(ps), cell};
             }
         }
         const unsigned act = __ballot_sync(0xffffffffu, ok);

@@ -13,7 +13,7 @@
 // __device__ array of fixed size, held by every GPU that loads the library
 // until the process exits:
 //   kNoAllocMaxSamples (262,144) samples and kNoAllocMaxTiles (65,536) grid
-//   tiles, 8.5 MiB per device.
+//   tiles, 8.75 MiB per device.
 // Longer TODs are processed in chunks of at most kNoAllocMaxSamples.  The sort
 // here keys samples by tile (not by cell), which keeps the histogram small.
 #include <mutex>
@@ -27,8 +27,8 @@ constexpr int kNoAllocMaxTiles = 1 << 16;
 // words (4 bytes): records (24 bytes each), keys, permutation, histogram, cursor, block sums
 constexpr size_t kRecWords = (size_t)kNoAllocMaxSamples * (sizeof(StencilRec64) / 4);
 constexpr size_t kBsumWords = (size_t)kNoAllocMaxTiles / 4096 + 2;
-constexpr size_t kNoAllocWords =
-    kRecWords + 2 * (size_t)kNoAllocMaxSamples + (kNoAllocMaxTiles + 1) + kNoAllocMaxTiles + kBsumWords;
+constexpr size_t kNoAllocWords = kRecWords + 2 * (size_t)kNoAllocMaxSamples + (kNoAllocMaxTiles + 1) +
+                                  kNoAllocMaxTiles + kBsumWords + (kNoAllocMaxTiles + 1);
 
 static __device__ __align__(256) unsigned g_noalloc_scratch[kNoAllocWords];
 
@@ -82,8 +82,8 @@ extern "C" sl_status interp_tod_noalloc(sl_plan *p, const void *maps, const doub
     b.hist = b.perm + kNoAllocMaxSamples;                  // cleared by the sort before use
     b.cursor = b.hist + (kNoAllocMaxTiles + 1);
     b.bsum = b.cursor + kNoAllocMaxTiles;
-    b.chunk_off = nullptr;                                 // not needed by the forward path
     const int rec64 = p->precision == SL_FP64;
-    if ((st = launch_sort_into(p, b, theta, phi, psi, n, 0, rec64, 0)) != SL_OK) return st;
-    return launch_interp(p, b, maps, psi, n, tod);
+    b.chunk_off = rec64 ? nullptr : b.bsum + kBsumWords;  // FP32 plans: tile work items
+    if ((st = launch_sort_into(p, b, theta, phi, psi, n, 0, rec64, !rec64)) != SL_OK) return st;
+    return launch_interp(p, b, 0, maps, psi, n, tod);
 }

@@ -327,6 +327,7 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     p->geom.half = half;
     p->geom.nlut = nlut;
     p->geom.lut_scale = nlut / M_PI;
+    p->geom.lut_scale_f = (float)(nlut / M_PI);
     p->geom.phi_scale = p->nphi / (2.0 * M_PI);
     p->geom.tile_cols = (K <= 16) ? 32 : 16;
     if (p->geom.tile_cols > p->nphi) p->geom.tile_cols = p->nphi;
@@ -463,8 +464,11 @@ sl_status interp_tod(sl_plan *p, const void *maps, const double *theta, const do
     if (n == 0) return SL_OK;
     if ((st = ensure_sort_capacity(p, n)) != SL_OK) return st;
     const int rec64 = p->precision == SL_FP64;
-    if ((st = launch_sort_into(p, p->sort, theta, phi, psi, n, 1, rec64, 0)) != SL_OK) return st;
-    return launch_interp(p, p->sort, maps, psi, n, tod);
+    // FP32 plans interpolate tile by tile from shared memory (needs the work items)
+    SortBufs b = p->sort;
+    if (rec64) b.chunk_off = nullptr;
+    if ((st = launch_sort_into(p, b, theta, phi, psi, n, 1, rec64, !rec64)) != SL_OK) return st;
+    return launch_interp(p, b, 1, maps, psi, n, tod);
 }
 
 sl_status adjoint_interp(sl_plan *p, const double *theta, const double *phi, const double *psi,

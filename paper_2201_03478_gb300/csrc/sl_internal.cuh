@@ -40,6 +40,7 @@ struct InterpGeom {
     const int *lut;               // [nlut]: base row for theta bin
     int nlut;
     double lut_scale;             // nlut / pi
+    float lut_scale_f;            // the same, in float
     double phi_scale;             // nphi / (2 pi)
     int tile_cols, ntr, ntc;      // tile grid: ntr = ceil((R+1)/kTileRows), ntc = ceil(nphi/tile_cols)
     const double *offs64;         // [(R+1) * 4]: theta(i-1+a) - theta(i-1) per base row i
@@ -171,9 +172,11 @@ int64_t sort_nkeys(const sl_plan *p, int fine);
 int64_t sort_nbsum(int64_t nkeys);
 sl_status launch_sort_into(sl_plan *p, const SortBufs &b, const double *theta, const double *phi,
                            const double *psi, int64_t n, int fine, int rec64, int with_chunks);
-// Forward interpolation over a sort (records in the plan's precision).
-sl_status launch_interp(sl_plan *p, const SortBufs &b, const void *maps, const double *psi, int64_t n,
+// Forward interpolation over a sort (records in the plan's precision).  FP32
+// plans use the tile-staged kernel when the sort built work items (chunk_off).
+sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *maps, const double *psi, int64_t n,
                         double *tod);
+size_t interp_f32_tiled_smem(const sl_plan *p);
 // Adjoint scatter over a sort made with rec64 = 1, with_chunks = 1.
 sl_status launch_interp_adjoint(sl_plan *p, const SortBufs &b, int fine, const double *psi, const double *tod,
                                 int64_t n, double2 *fbar);
@@ -191,26 +194,81 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
+// ---- conversions on the integer pipes.  GB300 runs FP64 at 1/64 of FP32, and
+// FP64 conversions and compares occupy that pipe; the binning kernel does
+// these steps on the bit patterns instead (exact, except the rounding noted).
+
+// double -> float, round half away from zero on the magnitude; values below
+// the float normal range give +-0, above it +-inf (NaN stays NaN).
+__device__ __forceinline__ float d2f_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const unsigned long long t = b & 0x7fffffffffffffffull;
+    if (t > 0x7ff0000000000000ull) return __int_as_float(0x7fc00000);           // NaN
+    const long long fb = (long long)((t + (1ull << 28)) >> 29) - ((long long)(1023 - 127) << 23);
+    if (fb < (1ll << 23)) return __int_as_float((int)sign);                     // underflow, 0
+    if (fb >= (255ll << 23)) return __int_as_float((int)(sign | 0x7f800000u));  // overflow, inf
+    return __int_as_float((int)(sign | (unsigned)fb));
+}
+
+// fr * 2^-sh (0 <= fr < 2^sh, sh <= 52) as a double (exact) and a float (truncated).
+__device__ __forceinline__ double frac_bits_d(unsigned long long fr, int sh) {
+    if (fr == 0) return 0.0;
+    const int p = 63 - __clzll((long long)fr);                 // leading one, p < sh
+    const unsigned long long m = (fr << (52 - p)) & ((1ull << 52) - 1);
+    return __longlong_as_double((long long)(((unsigned long long)(p - sh + 1023) << 52) | m));
+}
+__device__ __forceinline__ float frac_bits_f(unsigned long long fr, int sh) {
+    if (fr == 0) return 0.f;
+    const int p = 63 - __clzll((long long)fr);
+    if (p - sh + 127 <= 0) return 0.f;
+    const unsigned long long m = (p >= 23) ? (fr >> (p - 23)) : (fr << (23 - p));
+    return __int_as_float((int)(((unsigned)(p - sh + 127) << 23) | ((unsigned)m & 0x7fffffu)));
+}
+
 // Locate the base row i in [-1, R-1] of the interpolation stencil: the largest
-// i with theta_ext(i) <= theta.  NaN maps to a valid row (result is NaN).
+// i with theta_ext(i) <= theta.  The look-up bin comes from a float copy of
+// theta (the table keeps one row of margin); the final compares are exact:
+// for non-negative doubles the bit patterns order like the values, a negative
+// theta stays at row -1 and NaN ends on a valid row (the result is NaN).
 __device__ __forceinline__ int locate_row(const InterpGeom &g, double theta) {
-    // the conversion saturates (NaN gives 0); the bin is clamped in integers
-    int b = __double2int_rz(theta * g.lut_scale);
+    int b = __float2int_rz(d2f_bits(theta) * g.lut_scale_f);
     b = min(max(b, 0), g.nlut - 1);
     int i = __ldg(g.lut + b);
-    // ring_ext index of row r is r + half
-    while (i < g.R - 1 && __ldg(g.ring_ext + i + 1 + g.half) <= theta) ++i;
+    const long long tb = __double_as_longlong(theta);
+    // ring_ext index of row r is r + half (rows >= 0 are positive colatitudes)
+    while (i < g.R - 1 && __double_as_longlong(__ldg(g.ring_ext + i + 1 + g.half)) <= tb) ++i;
     return i;
 }
 
-// phi -> base column j in [0, nphi) and fractional offset f in [0, 1).
-__device__ __forceinline__ int locate_col(const InterpGeom &g, double phi, double &f) {
+// phi -> base column j in [0, nphi) and fraction u - j in [0, 1), u = phi nphi / (2 pi):
+// one FP64 multiply; floor and fraction from the bits of u (exact).  phi outside
+// [0, 2 pi) is first reduced in FP64.
+__device__ __forceinline__ int locate_col_bits(const InterpGeom &g, double phi, unsigned long long &fr, int &sh) {
     double u = phi * g.phi_scale;
     const double n = (double)g.nphi;
-    if (!(u >= 0.0 && u < n)) u -= n * floor(u * (1.0 / n));   // phi outside [0, 2 pi)
-    int j = __double2int_rz(u);
-    j = min(max(j, 0), g.nphi - 1);
-    f = u - (double)j;
+    if (!(u >= 0.0 && u < n)) u -= n * floor(u * (1.0 / n));   // rare; also maps NaN to NaN
+    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    const unsigned long long M = (b & ((1ull << 52) - 1)) | (1ull << 52);   // u = M 2^(e-52)
+    if (e > 30) { fr = 0; sh = 1; return 0; }          // NaN or out of range: column 0
+    if (e < 0) {                                       // u < 1: j = 0, fraction u (exact)
+        if (e < -126) { fr = 0; sh = 1; } else { fr = M; sh = 52 - e; }
+        return 0;
+    }
+    sh = 52 - e;
+    int j = (int)(M >> sh);
+    fr = M & ((1ull << sh) - 1);
+    if (j > g.nphi - 1) { j = g.nphi - 1; fr = (1ull << sh) - 1; }
+    return j;
+}
+
+// phi -> base column j and fraction f (double).
+__device__ __forceinline__ int locate_col(const InterpGeom &g, double phi, double &f) {
+    unsigned long long fr;
+    int sh;
+    const int j = locate_col_bits(g, phi, fr, sh);
+    f = frac_bits_d(fr, sh);
     return j;
 }
 
