@@ -3,16 +3,19 @@
 // with respect to the sky s_lm and the beam b_lk).
 //
 // Contraction transpose (real inner product Re<x, y>):
-//   Abar_{k,l,m} = sum_r d^l_{mk}(theta_r) Ghat_k(r, m),   m in [-L, L],
-// organised like the forward kernel: one CTA per (m >= 0, k, 256 north rings),
-// two recurrences per thread, the four reflections folded into
-//   Abar_{+m} = sum_pairs [d1 Ghat(N,+m) + (-1)^{l+m} d2 Ghat(S,+m)]
-//   Abar_{-m} = sum_pairs [(-1)^{m+k} d2 Ghat(N,-m) + (-1)^{l-k} d1 Ghat(S,-m)]
-// Every l needs a sum over the CTA's rings: a 4-value warp reduce-scatter by
-// shuffles, a cross-warp sum in shared memory per chunk of l, and one atomic
-// add per (l, value) into Abar (zeroed first).  All warps step l together;
-// a warp keeps checking the scaled representation until all its lanes have
-// reached normal range.
+//   Abar_{k,l,m} = sum_r d^l_{mk}(theta_r) Ghat_k(r, m),   m in [-L, L].
+// With the reflections of the forward step, per north ring pair (d1 = d_{m,+k},
+// d2 = d_{m,-k}, s_l = (-1)^l):
+//   Abar_{+m}(l) = c_l sum_pairs [y1 Ghat(N,+m) + s_l y2 (-1)^m Ghat(S,+m)]
+//   Abar_{-m}(l) = c_l sum_pairs [y2 (-1)^{m+k} Ghat(N,-m) + s_l y1 (-1)^k Ghat(S,-m)]
+// where d = c y are the rescaled recurrence values of the forward kernel, run
+// from the same FP64 start states (the evanescent zone is skipped).
+// One CTA per (m >= 0, k, 128 ring pairs), one thread per (ring pair, sign of
+// k).  Per chunk of 32 l: every thread steps its recurrence and writes y to
+// shared memory (0 before its start l); then each of the 256 threads forms
+// one of the 8 real dot products of one l over the CTA's 128 pairs.  The
+// (l, value) results are combined with c_l and s_l and added atomically into
+// Abar (zeroed first; the CTAs of other ring blocks add to the same entries).
 //
 // Products (A_{k,lm} = sum_X s^X_lm conj(b^X_lk), extended to m < 0 by
 // s_{l,-m} = (-1)^m conj(s_lm)); g = d/dRe + i d/dIm:
@@ -23,159 +26,151 @@
 
 namespace sl {
 
-constexpr int kNTA = 256;
-constexpr int kLCA = 32;
-
-struct __align__(32) RecA {
-    double x, y, z, w;   // alpha, beta, gamma, unused
-};
+constexpr int kNTA = 256;          // threads per CTA
+constexpr int kPA = kNTA / 2;      // ring pairs per CTA
+constexpr int kLCA = 32;           // l per chunk (kLCA * 8 dot products = kNTA threads)
+constexpr int kWS = kPA + 1;       // padded row of the y tile (bank spread)
 
 struct LcAdjArgs {
     int L, K, R, npairs, nchunk;
+    int64_t nalm;
     const double *xr;
-    const double2 *seed;
-    const int2 *seed_e;
+    const int *ls;
+    const double2 *st64;
+    const RTab64 *tab;
     const double2 *Ghat;   // [K+1][R][2L+1]
     double2 *Abar;         // [K+1][2L+1][L+1]
 };
 
-__device__ __forceinline__ void rec_coefs(int m, int k, int l, double &al, double &be, double &ga) {
-    const double lp = l + 1.0, ll = (double)l, dm = (double)m, dk = (double)k;
-    const double ra = 1.0 / sqrt((lp * lp - dm * dm) * (lp * lp - dk * dk));
-    al = (2.0 * l + 1.0) * lp * ra;
-    if (l > 0) {
-        be = (2.0 * l + 1.0) * dm * dk * ra / ll;
-        ga = lp * sqrt((ll * ll - dm * dm) * (ll * ll - dk * dk)) * ra / ll;
-    } else {
-        be = 0.0;
-        ga = 0.0;
-    }
-}
+struct AdjSmem {
+    double W[kLCA][2][kWS];        // y values [l][sign][pair]
+    double Gv[8][kWS];             // dot-product partners [dot][pair]
+    double dots[kLCA][8];
+    double2 rc[kLCA];              // a', b'
+    double cl[kLCA];               // c_l
+};
 
 __global__ void __launch_bounds__(kNTA) k_lcontract_adj(const LcAdjArgs a) {
-    __shared__ RecA rc[kLCA];                       // alpha, beta, gamma
-    __shared__ double red[kNTA / 32][kLCA][4];      // per-warp sums
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AdjSmem &S = *reinterpret_cast<AdjSmem *>(smem_raw);
+    auto &W = S.W;
+    auto &Gv = S.Gv;
+    auto &dots = S.dots;
+    auto &rc = S.rc;
+    auto &cl = S.cl;
     int b = blockIdx.x;
     const int pc = b % a.nchunk;
     b /= a.nchunk;
-    const int k = b % (a.K + 1);
-    const int m = b / (a.K + 1);
-    const int pair = pc * kNTA + threadIdx.x;
-    const int l0 = max(m, k);
+    const int k = b % (a.K + 1), m = b / (a.K + 1);
+    const int neg = threadIdx.x >= kPA;
+    const int lp = threadIdx.x & (kPA - 1);
+    const int pair = pc * kPA + lp;
     const bool active = pair < a.npairs;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t moff = (int64_t)m * (2 * a.L + 1 - m) / 2;
+    const RTab64 *tab = a.tab + (int64_t)k * a.nalm + moff;
 
-    double x = 0.0, d1 = 0.0, d1o = 0.0, d2 = 0.0, d2o = 0.0;
-    int e1 = 0, e2 = 0;
-    double2 gnp = {0, 0}, gsp = {0, 0}, gnm = {0, 0}, gsm = {0, 0};
-    if (active) {
-        x = a.xr[pair];
-        const int64_t si = ((int64_t)k * (a.L + 1) + m) * a.npairs + pair;
-        const double2 sv = a.seed[si];
-        const int2 se = a.seed_e[si];
-        d1 = sv.x;
-        e1 = se.x;
-        d2 = sv.y;
-        e2 = se.y;
-        const int rn = pair, rs = a.R - 1 - pair;
-        const int64_t row = 2 * (int64_t)a.L + 1;
-        const double2 *Gk = a.Ghat + (int64_t)k * a.R * row;
-        const double sm_ = (m & 1) ? -1.0 : 1.0, sk = (k & 1) ? -1.0 : 1.0;
-        gnp = Gk[rn * row + a.L + m];
-        if (rs != rn) {
-            const double2 v = Gk[rs * row + a.L + m];
-            gsp = make_double2(sm_ * v.x, sm_ * v.y);
-        }
-        if (m > 0) {
-            const double2 v = Gk[rn * row + a.L - m];
-            gnm = make_double2(sm_ * sk * v.x, sm_ * sk * v.y);
-            if (rs != rn) {
-                const double2 w = Gk[rs * row + a.L - m];
-                gsm = make_double2(sk * w.x, sk * w.y);
+    double x = 0.0, y = 0.0, yo = 0.0;
+    int ls = a.L + 1;
+    // dot partners: 0/1 W+ . Ghat(N,+m); 2/3 W- . (-1)^m Ghat(S,+m);
+    //               4/5 W- . (-1)^{m+k} Ghat(N,-m); 6/7 W+ . (-1)^k Ghat(S,-m)
+    {
+        double2 g0 = {0, 0}, g1 = {0, 0};
+        if (active) {
+            const int64_t si = (((int64_t)k * (a.L + 1) + m) * 2 + neg) * a.npairs + pair;
+            ls = a.ls[si];
+            yo = a.st64[si].x;
+            y = a.st64[si].y;
+            x = a.xr[pair];
+            const int rn = pair, rs = a.R - 1 - pair;
+            const int64_t row = 2 * (int64_t)a.L + 1;
+            const double2 *Gk = a.Ghat + (int64_t)k * a.R * row;
+            const double sm_ = (m & 1) ? -1.0 : 1.0, sk = (k & 1) ? -1.0 : 1.0;
+            if (!neg) {
+                g0 = Gk[rn * row + a.L + m];
+                if (m > 0 && rs != rn) {
+                    const double2 v = Gk[rs * row + a.L - m];
+                    g1 = make_double2(sk * v.x, sk * v.y);
+                }
+            } else {
+                if (rs != rn) {
+                    const double2 v = Gk[rs * row + a.L + m];
+                    g0 = make_double2(sm_ * v.x, sm_ * v.y);
+                }
+                if (m > 0) {
+                    const double2 v = Gk[rn * row + a.L - m];
+                    g1 = make_double2(sm_ * sk * v.x, sm_ * sk * v.y);
+                }
             }
         }
+        const int d0 = neg ? 2 : 0, d1 = neg ? 4 : 6;
+        Gv[d0][lp] = g0.x;
+        Gv[d0 + 1][lp] = g0.y;
+        Gv[d1][lp] = g1.x;
+        Gv[d1 + 1][lp] = g1.y;
     }
-    bool slow = __any_sync(0xffffffffu, e1 < 0 || e2 < 0);
+    // smallest start l over the CTA
+    __shared__ int s_min;
+    if (threadIdx.x == 0) s_min = 0x7fffffff;
+    __syncthreads();
+    atomicMin(&s_min, ls);
+    __syncthreads();
+    const int lstart = s_min;
+    const double sb = neg ? 1.0 : -1.0;
+    const int dl = threadIdx.x >> 3, dq = threadIdx.x & 7;     // this thread's (l, dot) in phase 2
+    const int wsg = (dq == 0 || dq == 1 || dq == 6 || dq == 7) ? 0 : 1;   // W+ or W-
     double2 *Ap = a.Abar + ((int64_t)k * (2 * a.L + 1) + a.L + m) * (a.L + 1);
     double2 *Am = a.Abar + ((int64_t)k * (2 * a.L + 1) + a.L - m) * (a.L + 1);
 
-    for (int c0 = l0; c0 <= a.L; c0 += kLCA) {
+    for (int c0 = lstart; c0 <= a.L; c0 += kLCA) {
         const int nc = min(kLCA, a.L - c0 + 1);
         __syncthreads();
-        for (int i = threadIdx.x; i < nc; i += kNTA) {
-            double al, be, ga;
-            rec_coefs(m, k, c0 + i, al, be, ga);
-            rc[i] = RecA{al, be, ga, 0.0};
+        if (threadIdx.x < nc) {
+            const RTab64 t = tab[c0 + threadIdx.x];
+            rc[threadIdx.x] = make_double2(t.a, t.b);
+            cl[threadIdx.x] = t.c;
         }
         __syncthreads();
+        // phase 1: recurrence values of this (pair, sign) for the chunk
         for (int i = 0; i < nc; ++i) {
             const int l = c0 + i;
-            const RecA r = rc[i];
-            double u1, u2;   // d1, d2 as they contribute (0 while scaled)
-            if (slow) {
-                u1 = (e1 == 0) ? d1 : 0.0;
-                u2 = (e2 == 0) ? d2 : 0.0;
-            } else {
-                u1 = d1;
-                u2 = d2;
+            double v = 0.0;
+            if (l >= ls) {
+                v = y;
+                const double2 r = rc[i];
+                const double yn = fma(fma(r.x, x, sb * r.y), y, -yo);
+                yo = y;
+                y = yn;
             }
-            double v0, v1, v2, v3;   // Abar_{+m} (re, im), Abar_{-m} (re, im)
-            if (l & 1) {
-                v0 = fma(-u2, gsp.x, u1 * gnp.x);
-                v1 = fma(-u2, gsp.y, u1 * gnp.y);
-                v2 = fma(-u1, gsm.x, u2 * gnm.x);
-                v3 = fma(-u1, gsm.y, u2 * gnm.y);
-            } else {
-                v0 = fma(u2, gsp.x, u1 * gnp.x);
-                v1 = fma(u2, gsp.y, u1 * gnp.y);
-                v2 = fma(u1, gsm.x, u2 * gnm.x);
-                v3 = fma(u1, gsm.y, u2 * gnm.y);
+            W[i][neg][lp] = v;
+        }
+        for (int i = nc; i < kLCA; ++i) W[i][neg][lp] = 0.0;
+        __syncthreads();
+        // phase 2: dot product (dl, dq) over the CTA's pairs
+        {
+            const double *wr = W[dl][wsg];
+            const double *gr = Gv[dq];
+            double s0 = 0.0, s1 = 0.0;
+#pragma unroll 8
+            for (int q = 0; q < kPA; q += 2) {
+                s0 = fma(wr[q], gr[q], s0);
+                s1 = fma(wr[q + 1], gr[q + 1], s1);
             }
-            // reduce-scatter over the warp: lane 0 -> v0, 8 -> v1, 16 -> v2, 24 -> v3
-            {
-                const bool hi = lane & 16;
-                const double s0 = hi ? v0 : v2, s1 = hi ? v1 : v3;
-                const double k0 = hi ? v2 : v0, k1 = hi ? v3 : v1;
-                const double t0 = k0 + __shfl_xor_sync(0xffffffffu, s0, 16);
-                const double t1 = k1 + __shfl_xor_sync(0xffffffffu, s1, 16);
-                const bool b8 = lane & 8;
-                double w = (b8 ? t1 : t0) + __shfl_xor_sync(0xffffffffu, b8 ? t0 : t1, 8);
-                w += __shfl_xor_sync(0xffffffffu, w, 4);
-                w += __shfl_xor_sync(0xffffffffu, w, 2);
-                w += __shfl_xor_sync(0xffffffffu, w, 1);
-                if ((lane & 7) == 0) red[warp][i][lane >> 3] = w;
-            }
-            // advance both recurrences
-            const double n1 = fma(fma(r.x, x, -r.y), d1, -r.z * d1o);
-            const double n2 = fma(fma(r.x, x, r.y), d2, -r.z * d2o);
-            d1o = d1;
-            d1 = n1;
-            d2o = d2;
-            d2 = n2;
-            if (slow) {
-                if (e1 < 0 && fabs(d1) > kScaleThr) {
-                    d1 *= kScaleDn;
-                    d1o *= kScaleDn;
-                    ++e1;
-                }
-                if (e2 < 0 && fabs(d2) > kScaleThr) {
-                    d2 *= kScaleDn;
-                    d2o *= kScaleDn;
-                    ++e2;
-                }
-                slow = __any_sync(0xffffffffu, e1 < 0 || e2 < 0);
-            }
+            dots[dl][dq] = s0 + s1;
         }
         __syncthreads();
-        // cross-warp sums, one atomic per (l, value)
-        for (int t = threadIdx.x; t < nc * 4; t += kNTA) {
-            const int i = t >> 2, c = t & 3;
-            if (m == 0 && c >= 2) continue;
-            double s = 0.0;
-#pragma unroll
-            for (int w = 0; w < kNTA / 32; ++w) s += red[w][i][c];
-            double *dst = (c < 2) ? &Ap[c0 + i].x : &Am[c0 + i].x;
-            atomicAdd(dst + (c & 1), s);
+        // combine: Abar+ = c (D01 + s D23), Abar- = c (D45 + s D67)
+        if (threadIdx.x < 4 * nc) {
+            const int i = threadIdx.x >> 2, comp = threadIdx.x & 3;
+            const int l = c0 + i;
+            const double s = (l & 1) ? -1.0 : 1.0;
+            const double c = cl[i];
+            if (comp < 2) {
+                const double v = c * (dots[i][comp] + s * dots[i][2 + comp]);
+                atomicAdd(&Ap[l].x + comp, v);
+            } else if (m > 0) {
+                const double v = c * (dots[i][2 + comp] + s * dots[i][4 + comp]);
+                atomicAdd(&Am[l].x + (comp - 2), v);
+            }
         }
     }
 }
@@ -186,10 +181,12 @@ sl_status launch_lcontract_adjoint(sl_plan *p) {
     a.K = p->K;
     a.R = p->R;
     a.npairs = p->npairs;
-    a.nchunk = (p->npairs + kNTA - 1) / kNTA;
+    a.nchunk = (p->npairs + kPA - 1) / kPA;
+    a.nalm = p->nalm;
     a.xr = p->d_xr;
-    a.seed = p->d_seed;
-    a.seed_e = p->d_seed_e;
+    a.ls = p->d_ls_adj;
+    a.st64 = p->d_st64_adj;
+    a.tab = p->d_tab64;
     a.Ghat = p->d_Gadj;
     a.Abar = p->d_Abar;
     sl_status st = cuda_check(cudaMemsetAsync(p->d_Abar, 0,
@@ -198,8 +195,12 @@ sl_status launch_lcontract_adjoint(sl_plan *p) {
                               "memset Abar");
     if (st != SL_OK) return st;
     const int64_t nblk = (int64_t)(p->L + 1) * (p->K + 1) * a.nchunk;
+    const size_t sm = sizeof(AdjSmem);
+    if ((st = cuda_check(cudaFuncSetAttribute(k_lcontract_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                         "k_lcontract_adj smem attribute")) != SL_OK)
+        return st;
     int slot = timing_begin(p, "lcontract_adj");
-    k_lcontract_adj<<<(unsigned)nblk, kNTA, 0, p->stream>>>(a);
+    k_lcontract_adj<<<(unsigned)nblk, kNTA, sm, p->stream>>>(a);
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_lcontract_adj launch");
 }

@@ -190,13 +190,12 @@ __global__ void __launch_bounds__(kAdvNT) k_advance(int L, int K, int npairs, in
     if (st32) st32[o] = make_float2((float)y, (float)(y - yo));
 }
 
-sl_status launch_advance(sl_plan *p, double thr) {
+sl_status launch_advance(sl_plan *p, double thr, int *ls, double2 *st64, float2 *st32) {
     const int nchunk = (p->npairs + kAdvNT / 2 - 1) / (kAdvNT / 2);
     const int64_t nblk = (int64_t)(p->L + 1) * (p->K + 1) * nchunk;
     int slot = timing_begin(p, "advance");
     k_advance<<<(unsigned)nblk, kAdvNT, 0, p->stream>>>(p->L, p->K, p->npairs, nchunk, p->nalm, thr, p->d_xr,
-                                                        p->d_seed, p->d_seed_e, p->d_tab64, p->d_ls, p->d_st64,
-                                                        p->d_st32);
+                                                        p->d_seed, p->d_seed_e, p->d_tab64, ls, st64, st32);
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_advance launch");
 }

@@ -133,6 +133,19 @@ static sl_status ensure_adjoint_scratch(sl_plan *p) {
             if (st != SL_OK) return st;
         }
     }
+    // the adjoint contraction runs in FP64: FP32 plans build the FP64 table and
+    // start states (threshold 2^-64) on first use
+    if (p->precision == SL_FP64) {
+        p->d_ls_adj = p->d_ls;
+        p->d_st64_adj = p->d_st64;
+    } else if (!p->d_st64_adj) {
+        const size_t nst = (size_t)(p->K + 1) * (p->L + 1) * 2 * p->npairs;
+        if ((st = dalloc_t(p, &p->d_tab64, (size_t)(p->K + 1) * p->nalm, "recurrence table")) != SL_OK) return st;
+        if ((st = launch_rtab(p)) != SL_OK) return st;
+        if ((st = dalloc_t(p, &p->d_ls_adj, nst, "adjoint start l")) != SL_OK) return st;
+        if ((st = dalloc_t(p, &p->d_st64_adj, nst, "adjoint start states")) != SL_OK) return st;
+        if ((st = launch_advance(p, 0x1p-64, p->d_ls_adj, p->d_st64_adj, nullptr)) != SL_OK) return st;
+    }
     return SL_OK;
 }
 
@@ -210,6 +223,8 @@ void plan_destroy(sl_plan *p) {
     dfree(p->d_seed_e);
     dfree(p->d_tab64);
     dfree(p->d_tab32);
+    if (p->d_ls_adj && p->d_ls_adj != p->d_ls) dfree(p->d_ls_adj);
+    if (p->d_st64_adj && p->d_st64_adj != p->d_st64) dfree(p->d_st64_adj);
     dfree(p->d_ls);
     dfree(p->d_st64);
     dfree(p->d_st32);
@@ -394,7 +409,7 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
         if (p->precision == SL_FP64) TRY(dalloc_t(p, &p->d_st64, nst, "start states"));
         else TRY(dalloc_t(p, &p->d_st32, nst, "start states"));
     }
-    TRY(launch_advance(p, p->precision == SL_FP64 ? 0x1p-64 : 0x1p-30));
+    TRY(launch_advance(p, p->precision == SL_FP64 ? 0x1p-64 : 0x1p-30, p->d_ls, p->d_st64, p->d_st32));
     TRY(count_lsteps(p, &p->lsteps));
     if (p->precision == SL_FP32) {
         TRY(cuda_check(cudaStreamSynchronize(p->stream), "plan advance"));

@@ -118,6 +118,9 @@ struct sl_plan {
     double2 *d_st64 = nullptr;
     float2 *d_st32 = nullptr;
     int64_t lsteps = 0;               // recurrence steps per synth call
+    // FP64 start states of the adjoint contraction (alias the above in FP64 plans)
+    int *d_ls_adj = nullptr;
+    double2 *d_st64_adj = nullptr;
     // FP32 copies of sky and beam (FP32 plans)
     float2 *d_sky32 = nullptr;
     float2 *d_beam32 = nullptr;
@@ -162,7 +165,7 @@ void timing_end(sl_plan *p, int idx);
 // launchers (one per translation unit)
 sl_status launch_seeds(sl_plan *p, const double *d_c2, const double *d_s2, const double *d_cs);
 sl_status launch_rtab(sl_plan *p);
-sl_status launch_advance(sl_plan *p, double thr);
+sl_status launch_advance(sl_plan *p, double thr, int *ls, double2 *st64, float2 *st32);
 sl_status count_lsteps(sl_plan *p, int64_t *out);
 sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam);
 sl_status launch_ringfft_synth(sl_plan *p, void *maps);
