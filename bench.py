@@ -315,12 +315,13 @@ def gpu_arm(args):
     # ---- end to end through the public API from pinned host buffers
     if args.e2e_steps > 0:
         pin = [t.pin_memory() for t in (sky_h, beam_h, *ptg_h)]
+        res = torch.empty(n, dtype=torch.float64, pin_memory=True)   # reused TOD buffer
         torch.cuda.synchronize()
-        res = sl.tod_from_host(plan, *pin)   # warm
+        sl.tod_from_host(plan, *pin, out=res)   # warm
         barrier(device)
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            res = sl.tod_from_host(plan, *pin)
+            sl.tod_from_host(plan, *pin, out=res)
         dt = reduce_max(time.perf_counter() - t0, device)
         h2d = sum(t.numel() * t.element_size() for t in pin)
         out["e2e"] = {"value": world * n * args.e2e_steps / dt, "unit": "samples/s",
@@ -344,8 +345,13 @@ def gpu_arm(args):
 
 
 # ncu-measured DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
-# for the current kernels; filled from profiles/ summaries, None until measured.
-TRAFFIC = {}
+# at full size for the current kernels (profiles/traffic_lfi_full_size.txt).
+TRAFFIC = {
+    ("lcontract_f64", "fp64"): 695.9e6 + 535.9e6,
+    ("interp_f64", "fp64"): 14959.2e6 + 1821.2e6,
+    ("lcontract_f32", "fp32"): 391.9e6 + 253.6e6,
+    ("interp_f32", "fp32"): 10506.0e6 + 2472.8e6,
+}
 
 
 # ----------------------------------------------------------------------------- CPU oracle timing
