@@ -19,8 +19,7 @@
  *
  *   c = Re S_0 + 2 sum_{k>=1} Re(e^{ik psi} S_k),  S_k = interpolated F_k.
  *
- * The paper leaves the interpolation open ("a wide range of interpolation
- * schemes"); this library uses separable p-point Lagrange interpolation in
+ * The paper does not fix the interpolation scheme; this library uses separable p-point Lagrange interpolation in
  * theta (at the actual ring colatitudes) and phi (uniform, periodic), with
  * p/2 ghost rows past each pole that hold (-1)^k F_k(ring, phi + pi).
  *
@@ -86,7 +85,7 @@ typedef struct {
     int lmax;                  /* sky and beam band limit L >= 1 */
     int kmax;                  /* beam azimuthal band limit K, 0 <= K <= min(L, 63) */
     int ncomp;                 /* 1 (T) or 3 (T, E, B) */
-    int nrings;                /* R >= 4 */
+    int nrings;                /* R in [4, 65534] */
     const double *ring_theta;  /* HOST [nrings]: strictly ascending colatitudes in (0, pi),
                                   symmetric: theta[R-1-r] == pi - theta[r] (to 1e-12);
                                   copied at plan creation */

@@ -248,9 +248,8 @@ void or_cube_G_adjoint(int L, int K, int nrings, const double *ring_theta,
 }
 
 /* ---------------------------------------------------------------------------
- * Interpolation of the cube at pointings (Sect. 2.1: "a wide range of
- * interpolation schemes may be employed"; reading: separable p-point
- * Lagrange).  Rows are the p rings around theta on the ring list extended
+ * Interpolation of the cube at pointings (Sect. 2.1 leaves the scheme to
+ * the implementer; reading: separable p-point Lagrange).  Rows are the p rings around theta on the ring list extended
  * past the poles: row -1-q is ring q at colatitude -theta_q, row R+q is ring
  * R-1-q at colatitude 2 pi - theta_{R-1-q}; a ghost row holds
  * (-1)^k F_k(ring, phi + pi), because d^l_{mk}(-t) = (-1)^{m-k} d^l_{mk}(t).

@@ -11,8 +11,9 @@
 //
 // The binning kernel has already turned each pointing into a stencil record
 // (cell (i, j), theta - theta(i-1), the phi fraction) in double precision.
-// Forward: one thread per sample in sorted order (samples of one cell are
-// adjacent, so the lanes of a warp read the same nodes).
+// Forward FP64: one thread per sample in sorted order (samples of one cell are
+// adjacent, so the lanes of a warp read the same nodes).  Forward FP32: one CTA
+// per work item, the tile's nodes staged in shared memory first.
 // Adjoint: one CTA per work item (<= kChunk samples of one tile); the tile's
 // nodes (with a 3-node halo) are accumulated in shared memory, each warp
 // owning a disjoint set of k so that no two threads update the same word, and
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const do
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const unsigned s = perm[t];
         const StencilRec64 r = rec[s];
-        const int i = (int)(r.cell / (unsigned)g.nphi) - 1, j = (int)(r.cell % (unsigned)g.nphi);
+        const int i = (int)(r.cell >> 16) - 1, j = (int)(r.cell & 0xffffu);
         double wt[4], wp[4], w[16];
         weights64(g, i, r.dth, r.fph, wt, wp);
         int off[16];
@@ -112,80 +113,6 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const do
             Sk = sn;
         }
         tod[s] = acc;
-    }
-}
-
-// ------------------------------------------------------------------ forward FP32 maps
-// FP64 only for the stored record (made by the binning kernel) and the final
-// value; weights, the e^{ik psi} ladder and the stencil sums in FP32.
-__global__ void __launch_bounds__(256, 3) k_interp_f32(const InterpGeom g, const float2 *__restrict__ maps,
-                                                    const StencilRec32 *__restrict__ rec,
-                                                    const unsigned *__restrict__ perm, int64_t n,
-                                                    double *__restrict__ tod) {
-    // software pipeline over this thread's samples: the permutation entry two
-    // samples ahead and the record one sample ahead are in flight while the
-    // current sample is evaluated
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned s_next = (t < n) ? perm[t] : 0u;
-    unsigned s_next2 = (t + stride < n) ? perm[t + stride] : 0u;
-    StencilRec32 r_next = (t < n) ? rec[s_next] : StencilRec32{0.f, 0.f, 0.f, 0u};
-    for (; t < n; t += stride) {
-        const unsigned s = s_next;
-        const StencilRec32 r = r_next;
-        s_next = s_next2;
-        if (t + stride < n) r_next = rec[s_next];
-        if (t + 2 * stride < n) s_next2 = perm[t + 2 * stride];
-        const int i = (int)(r.cell / (unsigned)g.nphi) - 1, j = (int)(r.cell % (unsigned)g.nphi);
-        const float4 of = __ldg(reinterpret_cast<const float4 *>(g.rowtab32) + 2 * (i + 1));
-        const float4 wd = __ldg(reinterpret_cast<const float4 *>(g.rowtab32) + 2 * (i + 1) + 1);
-        const float d0 = r.dth, d1 = d0 - of.y, d2 = d0 - of.z, d3 = d0 - of.w;
-        const float p01 = d0 * d1, p23 = d2 * d3;
-        const float wt[4] = {wd.x * d1 * p23, wd.y * d0 * p23, wd.z * p01 * d3, wd.w * p01 * d2};
-        const float f = r.fph;
-        const float a = f + 1.f, c = f - 1.f, d = f - 2.f;
-        const float cd = c * d, ab = a * f;
-        const float wp[4] = {-f * cd * (1.f / 6.f), a * cd * 0.5f, -ab * d * 0.5f, ab * c * (1.f / 6.f)};
-        int off[16];
-        float w[16];
-        const unsigned ghost = node_offsets(g, i, j, off);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) w[q] = wt[q >> 2] * wp[q & 3];
-        float sz, cz;
-        sincosf(r.psr, &sz, &cz);
-        // k = 0: only Re S_0 enters the TOD (two independent chains)
-        float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            a0 = fmaf(w[q], __ldg(maps + off[q]).x, a0);
-            a1 = fmaf(w[q + 8], __ldg(maps + off[q + 8]).x, a1);
-        }
-        const float acc0 = a0 + a1;
-        float zr = cz, zi = sz, acc1 = 0.f;
-        for (int k = 1; k <= g.K; ++k) {
-            if (ghost) {   // (-1)^k on ghost rows
-#pragma unroll
-                for (int ra = 0; ra < 4; ++ra)
-                    if (ghost & (1u << ra))
-#pragma unroll
-                        for (int cb = 0; cb < 4; ++cb) w[ra * 4 + cb] = -w[ra * 4 + cb];
-            }
-            float sr0 = 0.f, si0 = 0.f, sr1 = 0.f, si1 = 0.f;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float2 v0 = __ldg(maps + off[q] + k), v1 = __ldg(maps + off[q + 8] + k);
-                sr0 = fmaf(w[q], v0.x, sr0);
-                si0 = fmaf(w[q], v0.y, si0);
-                sr1 = fmaf(w[q + 8], v1.x, sr1);
-                si1 = fmaf(w[q + 8], v1.y, si1);
-            }
-            const float sr = sr0 + sr1, si = si0 + si1;
-            acc1 = fmaf(zr, sr, fmaf(-zi, si, acc1));
-            const float nr = zr * cz - zi * sz, ni = zr * sz + zi * cz;
-            zr = nr;
-            zi = ni;
-        }
-        tod[s] = (double)acc0 + 2.0 * (double)acc1;
     }
 }
 
@@ -261,7 +188,7 @@ __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
         for (unsigned t = s_beg + threadIdx.x; t < s_end; t += blockDim.x) {
             const unsigned s = A.perm[t];
             const StencilRec32 r = A.rec[s];
-            const int i = (int)(r.cell / (unsigned)g.nphi) - 1, j = (int)(r.cell % (unsigned)g.nphi);
+            const int i = (int)(r.cell >> 16) - 1, j = (int)(r.cell & 0xffffu);
             const float4 of = __ldg(reinterpret_cast<const float4 *>(g.rowtab32) + 2 * (i + 1));
             const float4 wd = __ldg(reinterpret_cast<const float4 *>(g.rowtab32) + 2 * (i + 1) + 1);
             const float d0 = r.dth, d1 = d0 - of.y, d2 = d0 - of.z, d3 = d0 - of.w;
@@ -363,7 +290,7 @@ __global__ void k_interp_adjoint(const AdjArgs A) {
             if ((int)threadIdx.x < nb) {
                 const unsigned s = A.perm[b0 + threadIdx.x];
                 const StencilRec64 r = A.rec[s];
-                const int i = (int)(r.cell / (unsigned)g.nphi) - 1, j = (int)(r.cell % (unsigned)g.nphi);
+                const int i = (int)(r.cell >> 16) - 1, j = (int)(r.cell & 0xffffu);
                 double wt[4], wp[4];
                 weights64(g, i, r.dth, r.fph, wt, wp);
                 double *ws = W + threadIdx.x * 16;
@@ -448,7 +375,8 @@ sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *map
         slot = timing_begin(p, "interp_f64");
         k_interp_f64<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const double2 *)maps,
                                                              (const StencilRec64 *)b.rec, psi, b.perm, n, tod);
-    } else if (b.chunk_off) {
+    } else {
+        if (!b.chunk_off) return set_error(SL_ERR_ARG, "FP32 interpolation needs the per-tile work list");
         TiledArgs a;
         a.g = p->geom;
         a.maps = (const float2 *)maps;
@@ -468,10 +396,6 @@ sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *map
         if (per_sm < 1) per_sm = 1;
         slot = timing_begin(p, "interp_f32");
         k_interp_f32_tiled<<<(unsigned)(nsm * per_sm), 256, sm, p->stream>>>(a);
-    } else {
-        slot = timing_begin(p, "interp_f32");
-        k_interp_f32<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const float2 *)maps,
-                                                             (const StencilRec32 *)b.rec, b.perm, n, tod);
     }
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_interp launch");

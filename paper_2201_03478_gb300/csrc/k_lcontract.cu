@@ -291,21 +291,23 @@ __global__ void __launch_bounds__(kNT) k_lcontract_f32(const LcArgs a) {
         const bool next = ln <= a.L;
         if (next) stage_load(a, tab, moff, m, k, ln, st);
         __syncthreads();
-        const float *rcf = reinterpret_cast<const float *>(rc[buf]);
-        const float2 *acf = reinterpret_cast<const float2 *>(ac[buf]);
-        const int cidx = neg ? 2 : 1;    // c'- for -k, c'+ for +k
+        const float4 *rcv = rc[buf];
+        // (c1, c2) = (ap, sam) for +k, (am, sap) for -k: one 16-byte load each step
+        const float4 *acv = reinterpret_cast<const float4 *>(ac[buf]) + (cofs >> 1);
         int i = max(0, lme - c0);
         // until both rings have started
         for (; i < nc && c0 + i < max(A.ls, B.ls); ++i) {
-            const float ra = rcf[4 * i], rcc = rcf[4 * i + cidx];
-            const float2 c1 = acf[4 * i + cofs], c2 = acf[4 * i + cofs + 1];
+            const float4 r = rcv[i], cc = acv[2 * i];
+            const float ra = r.x, rcc = neg ? r.z : r.y;    // c'- for -k, c'+ for +k
+            const float2 c1 = make_float2(cc.x, cc.y), c2 = make_float2(cc.z, cc.w);
             if (c0 + i >= A.ls) rec32_step(A, ra, rcc, c1, c2);
             if (c0 + i >= B.ls) rec32_step(B, ra, rcc, c1, c2);
         }
 #pragma unroll 2
         for (; i < nc; ++i) {
-            const float ra = rcf[4 * i], rcc = rcf[4 * i + cidx];
-            const float2 c1 = acf[4 * i + cofs], c2 = acf[4 * i + cofs + 1];
+            const float4 r = rcv[i], cc = acv[2 * i];
+            const float ra = r.x, rcc = neg ? r.z : r.y;    // c'- for -k, c'+ for +k
+            const float2 c1 = make_float2(cc.x, cc.y), c2 = make_float2(cc.z, cc.w);
             rec32_step(A, ra, rcc, c1, c2);
             rec32_step(B, ra, rcc, c1, c2);
         }

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256) k_bin(const InterpGeom g, int fine, const
             key = fine ? tile * (unsigned)(kTileRows * g.tile_cols) + (unsigned)(li * g.tile_cols + lj) : tile;
             keys[s] = key;
             const double dth = th - __ldg(g.ring_ext + g.half + i - 1);
-            const unsigned cell = (unsigned)(i + 1) * (unsigned)g.nphi + (unsigned)j;
+            const unsigned cell = ((unsigned)(i + 1) << 16) | (unsigned)j;
             if (REC64) {
                 reinterpret_cast<StencilRec64 *>(rec)[s] = StencilRec64{dth, frac_bits_d(fr, sh), cell, 0u};
             } else {

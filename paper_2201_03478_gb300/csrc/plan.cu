@@ -173,7 +173,7 @@ static sl_status validate(const sl_plan_desc *d, int *rad, int *nrad) {
     if (d->ncomp != 1 && d->ncomp != 3) return set_error(SL_ERR_ARG, "ncomp=%d (must be 1 or 3)", d->ncomp);
     int p = d->interp_order ? d->interp_order : 4;
     if (p != 4) return set_error(SL_ERR_UNSUPPORTED, "interp_order=%d (only 4 is built)", d->interp_order);
-    if (d->nrings < 4 || d->nrings > 65536) return set_error(SL_ERR_ARG, "nrings=%d outside [4, 65536]", d->nrings);
+    if (d->nrings < 4 || d->nrings > 65534) return set_error(SL_ERR_ARG, "nrings=%d outside [4, 65534]", d->nrings);
     if (!d->ring_theta) return set_error(SL_ERR_ARG, "ring_theta is NULL");
     const double *t = d->ring_theta;
     for (int r = 0; r < d->nrings; ++r) {

@@ -49,7 +49,7 @@ struct InterpGeom {
 
 // Per-sample stencil record written by the binning kernel: the colatitude
 // offset from the stencil's first row, the phi fraction in [0, 1), and the
-// cell (i+1) * nphi + j; FP32 plans also keep psi reduced to [-pi, pi].
+// cell ((i+1) << 16) | j; FP32 plans also keep psi reduced to [-pi, pi].
 struct StencilRec64 {
     double dth, fph;
     unsigned cell, pad;
