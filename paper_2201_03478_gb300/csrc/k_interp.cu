@@ -119,11 +119,13 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const do
 // ------------------------------------------------------------------ forward FP32, tile-staged
 // One CTA per work item (<= kChunkA sorted samples of one tile).  The tile's
 // stencil nodes -- rows tr*4-2 .. tr*4+4 and columns tc*TC-1 .. tc*TC+TC+1,
-// every k -- are staged into shared memory with coalesced loads (each tile row
-// is one or two contiguous spans of the cube); ghost rows are folded in while
-// staging (ring at phi + pi, factor (-1)^k), and k is padded to an even count
-// so that a pair of k is one 128-bit load.  Samples are then evaluated from
-// shared memory; the lanes of a warp mostly share one cell (broadcast reads).
+// every k -- are staged into shared memory with coalesced loads (consecutive
+// threads read consecutive k of one node); ghost rows are folded in while
+// staging (ring at phi + pi, factor (-1)^k).  Shared layout [k pair][row][col]
+// of float4 (F_k, F_k+1), k padded to an even count: the 16 stencil nodes of a
+// sample sit at compile-time offsets from its first node, and one k pair is
+// one 128-bit load.  Samples are then evaluated from shared memory; the lanes
+// of a warp mostly share one cell (broadcast reads).
 struct TiledArgs {
     InterpGeom g;
     const float2 *maps;
@@ -142,13 +144,16 @@ __device__ __forceinline__ int find_tile(const unsigned *chunk_off, int ntiles, 
     return lo;
 }
 
+template <int TC>
 __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
+    constexpr int TW = TC + 3, NR = kTileRows + 3, NN = NR * TW;   // staged nodes per k pair
     const InterpGeom &g = A.g;
-    const int K1 = g.K + 1, Kp = (K1 + 1) & ~1;
-    const int TC = g.tile_cols, tw = TC + 3, nrow = kTileRows + 3;
-    const int rowspan = tw * K1;
+    const int K1 = g.K + 1, KH = (K1 + 1) >> 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *node = reinterpret_cast<float2 *>(smem_raw);   // [nrow][tw][Kp]
+    float4 *node = reinterpret_cast<float4 *>(smem_raw);   // [KH][NR][TW]
+    // staging walk: element e = node * KH + kp, advanced by blockDim.x per step
+    const int e_step_n = (int)blockDim.x / KH, e_step_k = (int)blockDim.x - e_step_n * KH;
+    const int e0_n = (int)threadIdx.x / KH, e0_k = (int)threadIdx.x - e0_n * KH;
     const unsigned nchunks = A.chunk_off[A.ntiles];
     int staged_tile = -1;
     for (unsigned v = blockIdx.x; v < nchunks; v += gridDim.x) {
@@ -156,32 +161,37 @@ __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
         const unsigned c = v - A.chunk_off[tile];
         const unsigned s_beg = A.start[(int64_t)tile * A.ncell] + c * kChunkA;
         const unsigned s_end = min(A.start[(int64_t)(tile + 1) * A.ncell], s_beg + kChunkA);
-        const int tr = tile / g.ntc, tcol = tile % g.ntc;
+        const int tr = tile / g.ntc, tcol = tile - tr * g.ntc;
         const int rowlo = tr * kTileRows - 2, collo = tcol * TC - 1;
         if (tile != staged_tile) {
             __syncthreads();
-            for (int e = threadIdx.x; e < nrow * rowspan; e += blockDim.x) {
-                const int r = e / rowspan, x = e - r * rowspan;
-                const int cc = x / K1, k = x - cc * K1;
-                const int row = rowlo + r;
-                float2 val = make_float2(0.f, 0.f);
+            for (int nd = e0_n, kp = e0_k; nd < NN;) {
+                const int r = nd / TW, cc = nd - r * TW;
+                const int row = rowlo + r, k = 2 * kp;
+                float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (row >= -2 && row <= g.R + 1) {
                     int ring = row, col = collo + cc;
                     bool flip = false;
                     if (row < 0 || row >= g.R) {
                         ring = (row < 0) ? -1 - row : 2 * g.R - 1 - row;
-                        col += g.nphi / 2;
-                        flip = k & 1;
+                        col += g.nphi >> 1;
                     }
-                    col %= g.nphi;
+                    // col in [-1, 1.5 nphi + TC + 2): at most two wraps
                     if (col < 0) col += g.nphi;
-                    val = __ldg(A.maps + ((int64_t)ring * g.nphi + col) * K1 + k);
-                    if (flip) { val.x = -val.x; val.y = -val.y; }
+                    if (col >= g.nphi) col -= g.nphi;
+                    if (col >= g.nphi) col -= g.nphi;
+                    flip = ring != row;
+                    const float2 *src = A.maps + ((int64_t)ring * g.nphi + col) * K1 + k;
+                    const float2 v0 = __ldg(src);
+                    const float2 v1 = (k + 1 < K1) ? __ldg(src + 1) : make_float2(0.f, 0.f);
+                    // ghost rows: (-1)^k, i.e. the odd member of the pair flips
+                    val = flip ? make_float4(v0.x, v0.y, -v1.x, -v1.y) : make_float4(v0.x, v0.y, v1.x, v1.y);
                 }
-                node[(r * tw + cc) * Kp + k] = val;
+                node[kp * NN + nd] = val;
+                nd += e_step_n;
+                kp += e_step_k;
+                if (kp >= KH) { kp -= KH; ++nd; }
             }
-            if (Kp != K1)
-                for (int e = threadIdx.x; e < nrow * tw; e += blockDim.x) node[e * Kp + K1] = make_float2(0.f, 0.f);
             __syncthreads();
             staged_tile = tile;
         }
@@ -201,24 +211,24 @@ __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
             float w[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) w[q] = wt[q >> 2] * wp[q & 3];
-            const float2 *nb = node + ((i - 1 - rowlo) * tw + (j - 1 - collo)) * Kp;
+            const float4 *nb = node + (i - 1 - rowlo) * TW + (j - 1 - collo);
             float sz, cz;
             sincosf(r.psr, &sz, &cz);
             // z^k for the pair (k, k+1), starting at (1, z)
             float z0r = 1.f, z0i = 0.f, z1r = cz, z1i = sz;
             const float z2r = cz * cz - sz * sz, z2i = 2.f * cz * sz;
             float acc0 = 0.f, acc1 = 0.f;
-            for (int k = 0; k < K1; k += 2) {
+            for (int kp = 0; kp < KH; ++kp, nb += NN) {
                 float sr0 = 0.f, si0 = 0.f, sr1 = 0.f, si1 = 0.f;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const float4 v = *reinterpret_cast<const float4 *>(nb + ((q >> 2) * tw + (q & 3)) * Kp + k);
+                    const float4 v = nb[(q >> 2) * TW + (q & 3)];
                     sr0 = fmaf(w[q], v.x, sr0);
                     si0 = fmaf(w[q], v.y, si0);
                     sr1 = fmaf(w[q], v.z, sr1);
                     si1 = fmaf(w[q], v.w, si1);
                 }
-                if (k == 0) acc0 = sr0;
+                if (kp == 0) acc0 = sr0;
                 else acc1 = fmaf(z0r, sr0, fmaf(-z0i, si0, acc1));
                 acc1 = fmaf(z1r, sr1, fmaf(-z1i, si1, acc1));   // padding slot holds zeros
                 const float n0r = z0r * z2r - z0i * z2i, n0i = z0r * z2i + z0i * z2r;
@@ -231,8 +241,8 @@ __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
 }
 
 size_t interp_f32_tiled_smem(const sl_plan *p) {
-    const int K1 = p->K + 1, Kp = (K1 + 1) & ~1;
-    return (size_t)(kTileRows + 3) * (p->geom.tile_cols + 3) * Kp * sizeof(float2);
+    const int KH = (p->K + 2) / 2;
+    return (size_t)(kTileRows + 3) * (p->geom.tile_cols + 3) * KH * sizeof(float4);
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -388,14 +398,21 @@ sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *map
         a.ncell = fine ? kTileRows * p->geom.tile_cols : 1;
         a.tod = tod;
         const size_t sm = interp_f32_tiled_smem(p);
-        cudaError_t e = cudaFuncSetAttribute(k_interp_f32_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        void (*kern)(const TiledArgs);
+        switch (p->geom.tile_cols) {
+            case 32: kern = k_interp_f32_tiled<32>; break;
+            case 16: kern = k_interp_f32_tiled<16>; break;
+            case 8: kern = k_interp_f32_tiled<8>; break;
+            default: return set_error(SL_ERR_UNSUPPORTED, "tile width %d", p->geom.tile_cols);
+        }
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return cuda_check(e, "k_interp_f32_tiled smem attribute");
         int per_sm = 1, nsm = 152;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_f32_tiled, 256, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
         if (per_sm < 1) per_sm = 1;
         slot = timing_begin(p, "interp_f32");
-        k_interp_f32_tiled<<<(unsigned)(nsm * per_sm), 256, sm, p->stream>>>(a);
+        kern<<<(unsigned)(nsm * per_sm), 256, sm, p->stream>>>(a);
     }
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_interp launch");

@@ -36,23 +36,35 @@ __global__ void __launch_bounds__(256) k_bin(const InterpGeom g, int fine, const
             const int i = locate_row(g, th);
             unsigned long long fr;
             int sh;
-            const int j = locate_col_bits(g, phi[s], fr, sh);
+            const int j = locate_col_fix(g, phi[s], fr, sh);
             const int tr = (i + 1) / kTileRows, li = (i + 1) - tr * kTileRows;
             const int tc = j / g.tile_cols, lj = j - tc * g.tile_cols;
             const unsigned tile = (unsigned)tr * (unsigned)g.ntc + (unsigned)tc;
             key = fine ? tile * (unsigned)(kTileRows * g.tile_cols) + (unsigned)(li * g.tile_cols + lj) : tile;
             keys[s] = key;
-            const double dth = th - __ldg(g.ring_ext + g.half + i - 1);
+            // theta - theta(i-1) in 2^-60 fixed point (exact for theta >= 2^-8)
+            long long tf = 0;
+            const bool tfix = to_fix<60>(th, tf);
+            const long long dfix = tf - __ldg(g.ring_fix + g.half + i - 1);
             const unsigned cell = ((unsigned)(i + 1) << 16) | (unsigned)j;
             if (REC64) {
+                const double dth = tfix ? fix_to_d<60>(dfix) : th - __ldg(g.ring_ext + g.half + i - 1);
                 reinterpret_cast<StencilRec64 *>(rec)[s] = StencilRec64{dth, frac_bits_d(fr, sh), cell, 0u};
             } else {
-                double ps = psi[s];
-                // |psi| <= pi compared on the bit pattern; larger |psi| reduced in FP64
-                const long long pb = __double_as_longlong(ps) & 0x7fffffffffffffffll;
-                if (pb > 0x400921fb54442d18ll) ps -= 6.283185307179586 * rint(ps * 0.15915494309189535);
-                reinterpret_cast<StencilRec32 *>(rec)[s] =
-                    StencilRec32{d2f_bits(dth), frac_bits_f(fr, sh), d2f_bits(ps), cell};
+                const float dth = tfix ? fix_to_f<60>(dfix) : d2f_bits(th - __ldg(g.ring_ext + g.half + i - 1));
+                // psi reduced to [-pi, pi] in 2^-59 fixed point; |psi| >= 8 (and NaN) in FP64
+                const double ps = psi[s];
+                long long pf;
+                float psr;
+                if (to_fix<59>(ps, pf)) {
+                    constexpr long long kPi59 = 1811004864519280711ll, k2Pi59 = 3622009729038561421ll;
+                    if (pf > kPi59) pf -= k2Pi59;
+                    else if (pf < -kPi59) pf += k2Pi59;
+                    psr = fix_to_f<59>(pf);
+                } else {
+                    psr = d2f_bits(ps - 6.283185307179586 * rint(ps * 0.15915494309189535));
+                }
+                reinterpret_cast<StencilRec32 *>(rec)[s] = StencilRec32{dth, frac_bits_f(fr, sh), psr, cell};
             }
         }
         const unsigned act = __ballot_sync(0xffffffffu, ok);

@@ -217,6 +217,7 @@ void plan_destroy(sl_plan *p) {
     dfree(p->d_xr);
     dfree(p->d_y32);
     dfree(p->d_ring_ext);
+    dfree(p->d_ring_fix);
     dfree(p->d_wden);
     dfree(p->d_lut);
     dfree(p->d_seed);
@@ -344,8 +345,11 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     p->geom.lut_scale = nlut / M_PI;
     p->geom.lut_scale_f = (float)(nlut / M_PI);
     p->geom.phi_scale = p->nphi / (2.0 * M_PI);
+    p->geom.phi_fix = (unsigned long long)llroundl(
+        ldexpl((long double)p->nphi / (2.0L * 3.14159265358979323846264338327950288L), 52));
+    // tile width: 32 columns (16 when kmax > 16), at most nphi; one of 8, 16, 32
     p->geom.tile_cols = (K <= 16) ? 32 : 16;
-    if (p->geom.tile_cols > p->nphi) p->geom.tile_cols = p->nphi;
+    while (p->geom.tile_cols > p->nphi) p->geom.tile_cols >>= 1;
     p->geom.ntr = (R + 1 + kTileRows - 1) / kTileRows;
     p->geom.ntc = (p->nphi + p->geom.tile_cols - 1) / p->geom.tile_cols;
     p->ntiles = p->geom.ntr * p->geom.ntc;
@@ -371,6 +375,13 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     TRY(cuda_check(cudaMemcpy(p->d_xr, xr.data(), xr.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
     TRY(cuda_check(cudaMemcpy(p->d_y32, y32.data(), y32.size() * sizeof(float), cudaMemcpyHostToDevice), "upload"));
     TRY(cuda_check(cudaMemcpy(p->d_ring_ext, ring_ext.data(), ring_ext.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+    {
+        std::vector<long long> ring_fix(ring_ext.size());
+        for (size_t q = 0; q < ring_ext.size(); ++q) ring_fix[q] = llroundl(ldexpl((long double)ring_ext[q], 60));
+        TRY(dalloc_t(p, &p->d_ring_fix, ring_fix.size(), "ring fixed point"));
+        TRY(cuda_check(cudaMemcpy(p->d_ring_fix, ring_fix.data(), ring_fix.size() * sizeof(long long),
+                                  cudaMemcpyHostToDevice), "upload"));
+    }
     TRY(cuda_check(cudaMemcpy(p->d_wden, wden.data(), wden.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
     TRY(cuda_check(cudaMemcpy(p->d_lut, lut.data(), lut.size() * sizeof(int), cudaMemcpyHostToDevice), "upload"));
     TRY(cuda_check(cudaMemcpy(p->d_tw64, tw64.data(), tw64.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload"));
@@ -383,6 +394,7 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     TRY(cuda_check(cudaMemcpy(p->d_offs64, offs64.data(), offs64.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
     TRY(cuda_check(cudaMemcpy(p->d_rowtab32, rowtab32.data(), rowtab32.size() * sizeof(float), cudaMemcpyHostToDevice), "upload"));
     p->geom.ring_ext = p->d_ring_ext;
+    p->geom.ring_fix = p->d_ring_fix;
     p->geom.wden = p->d_wden;
     p->geom.lut = p->d_lut;
     p->geom.offs64 = p->d_offs64;

@@ -36,12 +36,14 @@ constexpr int kTileRows = 4;
 struct InterpGeom {
     int R, nphi, K, p, half;      // half = p/2 ghost rows per pole
     const double *ring_ext;       // [R + 2 half]: theta of rows -half .. R+half-1
+    const long long *ring_fix;    // the same colatitudes in fixed point, round(theta 2^60)
     const double *wden;           // [(R+1) * p]: 1 / prod_{b!=a}(theta_a - theta_b) per base row
     const int *lut;               // [nlut]: base row for theta bin
     int nlut;
     double lut_scale;             // nlut / pi
     float lut_scale_f;            // the same, in float
     double phi_scale;             // nphi / (2 pi)
+    unsigned long long phi_fix;   // round(nphi / (2 pi) 2^52)
     int tile_cols, ntr, ntc;      // tile grid: ntr = ceil((R+1)/kTileRows), ntc = ceil(nphi/tile_cols)
     const double *offs64;         // [(R+1) * 4]: theta(i-1+a) - theta(i-1) per base row i
     const float *rowtab32;        // [(R+1) * 8]: the same offsets, then wden, in float
@@ -99,6 +101,7 @@ struct sl_plan {
     double *d_xr = nullptr;           // [npairs] cos(theta) of north rings
     float *d_y32 = nullptr;           // [npairs] 1 - cos(theta) = 2 sin^2(theta/2), FP32
     double *d_ring_ext = nullptr;
+    long long *d_ring_fix = nullptr;
     double *d_wden = nullptr;
     double *d_offs64 = nullptr;
     float *d_rowtab32 = nullptr;
@@ -264,6 +267,73 @@ __device__ __forceinline__ int locate_col_bits(const InterpGeom &g, double phi, 
     fr = M & ((1ull << sh) - 1);
     if (j > g.nphi - 1) { j = g.nphi - 1; fr = (1ull << sh) - 1; }
     return j;
+}
+
+// ---- coordinate arithmetic on the integer pipes ---------------------------
+// On this GPU the FP64 unit runs at 1/64 of the FP32 rate, so the per-sample
+// conversions of the binning kernel are done in 64-bit fixed point instead.
+
+// x 2^S truncated toward zero, if |x| < 2^(62-S) (else false: NaN, inf, too
+// large).  Exact when the last mantissa bit of x is worth at least 2^-S.
+template <int S>
+__device__ __forceinline__ bool to_fix(double x, long long &v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    if (e > 61 - S) return false;
+    const unsigned long long M = (b & ((1ull << 52) - 1)) | (1ull << 52);   // x = M 2^(e-52)
+    const int sh = e + S - 52;
+    const unsigned long long a = (sh >= 0) ? (M << sh) : (sh > -64 ? (M >> -sh) : 0ull);
+    v = (b >> 63) ? -(long long)a : (long long)a;
+    return true;
+}
+
+// v 2^-S rounded to the nearest double / float (|v| < 2^63).
+template <int S>
+__device__ __forceinline__ double fix_to_d(long long v) {
+    if (v == 0) return 0.0;
+    const unsigned long long sgn = (v < 0) ? (1ull << 63) : 0ull;
+    const unsigned long long a = (v < 0) ? (unsigned long long)(-v) : (unsigned long long)v;
+    const int p = 63 - __clzll((long long)a);
+    const unsigned long long m = (p > 52) ? ((a + (1ull << (p - 53))) >> (p - 52)) : (a << (52 - p));
+    // m in [2^52, 2^53]; a carry into 2^53 moves into the exponent field
+    return __longlong_as_double(
+        (long long)(sgn | ((((unsigned long long)(p - S + 1023)) << 52) + (m - (1ull << 52)))));
+}
+template <int S>
+__device__ __forceinline__ float fix_to_f(long long v) {
+    if (v == 0) return 0.f;
+    const unsigned sgn = (v < 0) ? 0x80000000u : 0u;
+    const unsigned long long a = (v < 0) ? (unsigned long long)(-v) : (unsigned long long)v;
+    const int p = 63 - __clzll((long long)a);
+    const int E = p - S + 127;
+    if (E <= 0) return __int_as_float((int)sgn);     // below the normal range: 0
+    const unsigned long long m = (p > 23) ? ((a + (1ull << (p - 24))) >> (p - 23)) : (a << (23 - p));
+    return __int_as_float((int)(sgn | (((unsigned)E << 23) + (unsigned)(m - (1ull << 23)))));
+}
+
+// phi -> base column j in [0, nphi) and fraction fr 2^-53 in [0, 1): u = phi
+// nphi / (2 pi) as the 128-bit product of phi's mantissa and phi_fix.  Falls
+// back to locate_col_bits for |phi| < 2^-20, |phi| >= 16, NaN and inf.
+__device__ __forceinline__ int locate_col_fix(const InterpGeom &g, double phi, unsigned long long &fr, int &sh) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(phi);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    if (e < -20 || e > 3) return locate_col_bits(g, phi, fr, sh);
+    const unsigned long long M = (b & ((1ull << 52) - 1)) | (1ull << 52);
+    unsigned long long lo = M * g.phi_fix, hi = __umul64hi(M, g.phi_fix);
+    if (b >> 63) {                       // negate the 128-bit product
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    // u = (hi:lo) 2^(e-104): integer part hi >> t, fraction bits [t, t+64), t = 40 - e in [37, 60]
+    const int t = 40 - e;
+    long long j = (long long)hi >> t;
+    fr = ((lo >> t) | (hi << (64 - t))) >> 11;
+    sh = 53;
+    if ((unsigned long long)j >= (unsigned long long)g.nphi) {
+        j %= g.nphi;
+        if (j < 0) j += g.nphi;
+    }
+    return (int)j;
 }
 
 // phi -> base column j and fraction f (double).
