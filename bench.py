@@ -161,16 +161,21 @@ def gpu_arm(args):
         dist.init_process_group("nccl")
 
     n = int(args.n)
-    cfg = W.config_lfi(with_pointings=False)
+    highres = args.workload == "highres"
+    cfg = W.config_highres(with_pointings=False) if highres else W.config_lfi(with_pointings=False)
     if args.lmax or args.nrings or args.nphi:   # smaller variants of the same workload (profiling)
         Ls = args.lmax or cfg["lmax"]
         cfg = dict(cfg, lmax=Ls, sky=W.sky_polarised(Ls, seed=0), beam=W.beam_far_sidelobe(Ls, cfg["kmax"], seed=1),
                    ring_theta=W.equiangular_ring_theta(args.nrings or cfg["ring_theta"].size),
                    nphi=args.nphi or cfg["nphi"])
     L, K = cfg["lmax"], cfg["kmax"]
+    ncomp = cfg["sky"].shape[0]
     rt, nphi = cfg["ring_theta"], cfg["nphi"]
     R = rt.size
-    th, ph, ps = W.pointings_scan(n, t0=shard_t0(rank, n))
+    if highres:
+        th, ph, ps = W.pointings_uniform(n, seed=2 + rank)
+    else:
+        th, ph, ps = W.pointings_scan(n, t0=shard_t0(rank, n))
     sky_h = torch.from_numpy(cfg["sky"])
     beam_h = torch.from_numpy(cfg["beam"])
     ptg_h = [torch.from_numpy(a) for a in (th, ph, ps)]
@@ -178,7 +183,7 @@ def gpu_arm(args):
     beam = beam_h.to(device)
     theta, phi, psi = (t.to(device) for t in ptg_h)
 
-    plan = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=3, precision=args.precision, device=local)
+    plan = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=ncomp, precision=args.precision, device=local)
     maps = torch.empty(plan.maps_shape(), dtype=plan.maps_dtype, device=device)
     tod = torch.empty(n, dtype=torch.float64, device=device)
 
@@ -232,7 +237,8 @@ def gpu_arm(args):
             ach = fl / (avg_ms / 1e3) / 1e12
             roofs[name] = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4),
                            "unit": "TFLOP/s", "frac": round(ach / peak, 4),
-                           "traffic": TRAFFIC.get((name, prec)), "avg_ms": round(avg_ms, 4),
+                           "traffic": None if highres else TRAFFIC.get((name, prec)),
+                           "avg_ms": round(avg_ms, 4),
                            "flops_per_launch": fl,
                            "peak_note": "derived from unit counts x 2.07 GHz max SM clock"}
     lc_name = "lcontract_%s" % ("f64" if prec == "fp64" else "f32")
@@ -243,15 +249,24 @@ def gpu_arm(args):
     shares = {k: round(v[1] / max(1e-9, sum(x[1] for x in stats.values())), 4) for k, v in stats.items()}
     launches = sum(v[0] for v in stats.values())
 
+    if highres:
+        metric = "TOD samples/s (cube build+interp) at lmax=%d,kmax=%d; %%roofline; vs GPU FP64" % (L, K)
+        data = "synthetic (seeded Gaussian sky, Gaussian-taper beam, uniform pointings)"
+        workload = ("precision variant: unpolarised, lmax=%d, kmax=%d, %d rings x %d phi, %d uniform pointings "
+                    "per GPU" % (L, K, R, nphi, n))
+    else:
+        metric = "TOD samples/s (cube build+interp) at lmax=1024,kmax=16; %roofline; vs GPU FP64"
+        data = "synthetic (seeded T/E/B sky, far-sidelobe beam, satellite scan)"
+        workload = ("LFI-like: polarised T/E/B, lmax=%d, kmax=%d, %d rings x %d phi, "
+                    "%d scan pointings per GPU (32.5 Hz, 1 rpm, 85 deg)" % (L, K, R, nphi, n))
     out = {
-        "metric": "TOD samples/s (cube build+interp) at lmax=1024,kmax=16; %roofline; vs GPU FP64",
+        "metric": metric,
         "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == "fp64" else "f32 (FP64 seeds/coords/final sum)",
-        "data": "synthetic (seeded T/E/B sky, far-sidelobe beam, satellite scan)",
-        "config": {"workload": "LFI-like: polarised T/E/B, lmax=1024, kmax=16, 1024 rings x 2048 phi, "
-                               "%d scan pointings per GPU (32.5 Hz, 1 rpm, 85 deg)" % n,
-                   "lmax": L, "kmax": K, "ncomp": 3, "nrings": R, "nphi": nphi, "interp_order": 4,
+        "data": data,
+        "config": {"workload": workload,
+                   "lmax": L, "kmax": K, "ncomp": ncomp, "nrings": R, "nphi": nphi, "interp_order": 4,
                    "samples_per_gpu": n, "precision": prec, "parallelism": "replicated cube, sharded TOD",
                    "l2": "inputs larger than L2 (pointings %.1f GB, cube %.2f GB)" % (24 * n / 1e9,
                                                                                        plan.sizes()["maps_bytes"] / 1e9)},
@@ -291,7 +306,7 @@ def gpu_arm(args):
     # ---- the other precision on the same box, compared with this run's TOD
     if args.compare and rank == 0 and world == 1:
         other = "fp32" if prec == "fp64" else "fp64"
-        p2 = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=3, precision=other, device=local)
+        p2 = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=ncomp, precision=other, device=local)
         maps2 = torch.empty(p2.maps_shape(), dtype=p2.maps_dtype, device=device)
         tod2 = torch.empty(n, dtype=torch.float64, device=device)
 
@@ -390,9 +405,10 @@ def reference_arm(args):
         return
     import workloads as W
     n = int(args.n)
-    cfg = W.config_lfi(with_pointings=False)
+    highres = args.workload == "highres"
+    cfg = W.config_highres(with_pointings=False) if highres else W.config_lfi(with_pointings=False)
     sn = args.cpu_samples
-    th, ph, ps = W.pointings_scan(sn)
+    th, ph, ps = W.pointings_uniform(sn, seed=2) if highres else W.pointings_scan(sn)
     for _ in range(args.warmup):
         oracle_sample(cfg, th, ph, ps, n, 4, min(sn, 100000))
     per = []
@@ -403,15 +419,26 @@ def reference_arm(args):
         t_meas += det["cube_s"] + det["interp_s"]
     full = float(np.mean(per))
     value = world * n / full
-    out = {"impl": "reference", "metric": "TOD samples/s (cube build+interp) at lmax=1024,kmax=16; %roofline; vs GPU FP64",
+    L, K, R = cfg["lmax"], cfg["kmax"], cfg["ring_theta"].size
+    if highres:
+        metric = "TOD samples/s (cube build+interp) at lmax=%d,kmax=%d; %%roofline; vs GPU FP64" % (L, K)
+        data = "synthetic (seeded Gaussian sky, Gaussian-taper beam, uniform pointings)"
+        workload = ("precision variant: unpolarised, lmax=%d, kmax=%d, %d rings x %d phi, %d uniform pointings "
+                    "per GPU" % (L, K, R, cfg["nphi"], n))
+    else:
+        metric = "TOD samples/s (cube build+interp) at lmax=1024,kmax=16; %roofline; vs GPU FP64"
+        data = "synthetic (seeded T/E/B sky, far-sidelobe beam, satellite scan)"
+        workload = ("LFI-like: polarised T/E/B, lmax=%d, kmax=%d, %d rings x %d phi, "
+                    "%d scan pointings per GPU (32.5 Hz, 1 rpm, 85 deg)" % (L, K, R, cfg["nphi"], n))
+    out = {"impl": "reference", "metric": metric,
            "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": full * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64", "data": "synthetic (seeded T/E/B sky, far-sidelobe beam, satellite scan)",
-           "config": {"workload": "LFI-like: polarised T/E/B, lmax=1024, kmax=16, 1024 rings x 2048 phi, "
-                                  "%d scan pointings per GPU" % n, "precision": "fp64"},
+           "dtype": "f64", "data": data,
+           "config": {"workload": workload, "precision": "fp64"},
            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": "each step: oracle spin Legendre step + DFT on %d of 1024 rings and "
-                                      "interpolation of %d samples, extrapolated to a full step" % (args.ref_rings, sn)},
+                            "sample": "each step: oracle spin Legendre step + DFT on %d of %d rings and "
+                                      "interpolation of %d samples, extrapolated to a full step"
+                                      % (args.ref_rings, R, sn)},
            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "measured_seconds": t_meas}
     print(json.dumps(out), flush=True)
@@ -424,7 +451,10 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
-    ap.add_argument("--n", type=float, default=1e8, help="pointings per GPU")
+    ap.add_argument("--workload", choices=["lfi", "highres"], default="lfi",
+                    help="lfi: T/E/B, lmax 1024, kmax 16, scan (the headline); "
+                         "highres: lmax 2048, kmax 32, 2048 x 4096 rings, uniform pointings (precision variant)")
+    ap.add_argument("--n", type=float, default=0, help="pointings per GPU (default 1e8; 2e8 for highres)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--adjoint-steps", type=int, default=3, help="timed adjoint_tod calls (0: skip)")
     ap.add_argument("--no-compare", dest="compare", action="store_false")
@@ -437,6 +467,8 @@ def main(argv=None):
     ap.add_argument("--nrings", type=int, default=0, help="override the number of equiangular rings")
     ap.add_argument("--nphi", type=int, default=0, help="override phi samples per ring")
     args = ap.parse_args(argv)
+    if not args.n:
+        args.n = 2e8 if args.workload == "highres" else 1e8
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world, _ = dist_env()

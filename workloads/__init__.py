@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "nalm", "alm_index", "healpix_ring_theta", "equiangular_ring_theta",
     "sky_gaussian", "sky_polarised", "beam_gaussian_taper", "beam_far_sidelobe",
-    "pointings_uniform", "pointings_scan", "config_small", "config_lfi",
+    "pointings_uniform", "pointings_scan", "config_small", "config_lfi", "config_highres",
 ]
 
 
@@ -206,4 +206,18 @@ def config_lfi(n: int = 100_000_000, with_pointings: bool = True):
              ring_theta=equiangular_ring_theta(1024), nphi=2048)
     if with_pointings:
         d["theta"], d["phi"], d["psi"] = pointings_scan(n)
+    return d
+
+
+def config_highres(n: int = 200_000_000, with_pointings: bool = True):
+    """Precision-variant scale: the small case's generators (unpolarised sky with
+    C_l = (l+1)^-2, Gaussian-taper beam with sigma_l = 20 and 0.5^k) at
+    lmax=2048, kmax=32; 2048 equiangular rings x 4096 phi; uniform pointings."""
+    lmax, kmax = 2048, 32
+    ell = np.arange(lmax + 1, dtype=np.float64)
+    d = dict(lmax=lmax, kmax=kmax, sky=sky_gaussian(lmax, [(ell + 1.0) ** -2], seed=0),
+             beam=beam_gaussian_taper(lmax, kmax, 20.0, seed=1),
+             ring_theta=equiangular_ring_theta(2048), nphi=4096)
+    if with_pointings:
+        d["theta"], d["phi"], d["psi"] = pointings_uniform(n, seed=2)
     return d
