@@ -359,6 +359,91 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def detectors_arm(args):
+    """Many detectors (uneven lmax, kmax, grids and sample counts) in one CUDA
+    graph (sl_batch_*), timed against the same detectors called one by one."""
+    import torch
+
+    import paper_2201_03478_gb300 as sl
+    import workloads as W
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dets = W.config_detectors(ndet=args.ndet)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    items = []
+    for d in dets:
+        plan = sl.sidelobe_plan_create(d["lmax"], d["kmax"], d["ring_theta"], d["nphi"], ncomp=3,
+                                       precision=args.precision, device=local)
+        items.append(dict(plan=plan, sky=dev(d["sky"]), beam=dev(d["beam"]),
+                          maps=torch.empty(plan.maps_shape(), dtype=plan.maps_dtype, device=device),
+                          theta=dev(d["theta"]), phi=dev(d["phi"]), psi=dev(d["psi"]),
+                          tod=torch.empty(d["n"], dtype=torch.float64, device=device)))
+        del d["theta"], d["phi"], d["psi"]
+    ntot = sum(d["n"] for d in dets)
+    stream = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def serial():
+        for it in items:
+            sl.synth_spin_maps(it["plan"], it["sky"], it["beam"], it["maps"])
+            sl.interp_tod(it["plan"], it["maps"], it["theta"], it["phi"], it["psi"], it["tod"])
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_serial = timed(serial)
+    ref = [it["tod"].clone() for it in items]
+    t0 = time.perf_counter()
+    batch = sl.sl_batch_create(items, autotune=args.autotune)
+    t_create = time.perf_counter() - t0
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms = timed(batch.run)
+    clk = clocks.stop()
+    identical = all(bool(torch.equal(it["tod"], r)) for it, r in zip(items, ref))
+    info = batch.info()
+    out = {
+        "metric": "TOD samples/s (cube build+interp), %d detectors of uneven lmax/kmax in one CUDA graph" % len(dets),
+        "value": ntot / (ms / 1e3), "unit": "samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32 (FP64 seeds/coords/final sum)",
+        "data": "synthetic (T/E/B sky truncated per detector, per-detector far-sidelobe beams, offset scans)",
+        "config": {"workload": "multi-detector batch: %d detectors, lmax in {256..1500}, kmax in {4..24}, "
+                               "%d samples in total" % (len(dets), ntot),
+                   "detectors": [{"lmax": d["lmax"], "kmax": d["kmax"], "n": d["n"],
+                                  "tile_cols": it["plan"].sizes()["tile_cols"]} for d, it in zip(dets, items)],
+                   "precision": args.precision, "autotune": bool(args.autotune),
+                   "l2": "inputs larger than L2 (pointings %.1f GB)" % (24 * ntot / 1e9)},
+        "serial": {"value": ntot / (ms_serial / 1e3), "ms_per_step": ms_serial,
+                   "note": "the same detectors called one after another on one stream"},
+        "graph": {"nstreams": info["nstreams"], "kernel_nodes": info["kernel_nodes"],
+                  "graph_nodes": info["graph_nodes"], "create_s": t_create, "tuned_ms": info["tuned_ms"],
+                  "tuner_serial_ms": info["serial_ms"]},
+        "tod_identical_to_serial": identical,
+        "gpu_launches": info["kernel_nodes"],
+        "clocks": clk,
+    }
+    sl.sl_batch_destroy(batch)
+    line = json.dumps(out)
+    print(line, flush=True)
+    if args.json_out:
+        with open(args.json_out, "w") as f:
+            f.write(line + "\n")
+
+
 # ncu-measured DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
 # at full size for the current kernels (profiles/traffic_lfi_full_size.txt).
 TRAFFIC = {
@@ -451,9 +536,12 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
-    ap.add_argument("--workload", choices=["lfi", "highres"], default="lfi",
+    ap.add_argument("--workload", choices=["lfi", "highres", "detectors"], default="lfi",
                     help="lfi: T/E/B, lmax 1024, kmax 16, scan (the headline); "
-                         "highres: lmax 2048, kmax 32, 2048 x 4096 rings, uniform pointings (precision variant)")
+                         "highres: lmax 2048, kmax 32, 2048 x 4096 rings, uniform pointings (precision variant); "
+                         "detectors: 22 detectors of uneven lmax/kmax in one CUDA graph (batch variant)")
+    ap.add_argument("--ndet", type=int, default=22, help="detectors of the batch workload")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--n", type=float, default=0, help="pointings per GPU (default 1e8; 2e8 for highres)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--adjoint-steps", type=int, default=3, help="timed adjoint_tod calls (0: skip)")
@@ -478,6 +566,8 @@ def main(argv=None):
         if args.cpu_samples > 2_000_000:
             args.cpu_samples = 2_000_000
         reference_arm(args)
+    elif args.workload == "detectors":
+        detectors_arm(args)
     else:
         gpu_arm(args)
 

@@ -183,11 +183,27 @@ typedef struct {
                               (north ring, m, k, sign of k) of the l it visits
                               (the evanescent part below the significance
                               threshold is skipped) */
+    int64_t tile_cols;     /* phi columns per sort tile (the tile is 4 rows high) */
 } sl_plan_sizes;
 sl_status sl_plan_get_sizes(const sl_plan *plan, sl_plan_sizes *out);
 
-/* Re-targets the plan to another stream of the same device. */
+/* Re-targets the plan to another stream of the same device (synchronises the
+ * old stream first). */
 sl_status sl_plan_set_stream(sl_plan *plan, void *stream);
+
+/* Grows the plan's pointing-sort scratch to hold n samples now, so that later
+ * interp_tod / adjoint calls with at most n samples allocate nothing.
+ * n in [0, 2^31).  SL_ERR_ARG while a batch graph holds the plan and n exceeds
+ * the current capacity. */
+sl_status sl_plan_reserve(sl_plan *plan, int64_t n);
+
+/* Sets the width (phi columns: 8, 16 or 32, at most nphi) of the sort tiles,
+ * the unit of the FP32 interpolation's shared-memory staging and of the
+ * adjoint's.  Results do not depend on it; speed does (see sl_batch_create's
+ * autotuner).  Reallocates the per-tile tables: SL_ERR_ARG while a batch graph
+ * holds the plan; SL_ERR_UNSUPPORTED when the staged tile would not fit in
+ * shared memory. */
+sl_status sl_plan_set_tile_cols(sl_plan *plan, int tile_cols);
 
 /* Synchronises the plan's stream; reports device faults as SL_ERR_CUDA. */
 sl_status sl_plan_sync(sl_plan *plan);
@@ -204,6 +220,55 @@ typedef struct {
 } sl_kernel_stat;
 sl_status sl_plan_enable_timing(sl_plan *plan, int enable);
 sl_status sl_plan_kernel_stats(sl_plan *plan, sl_kernel_stat *out, int max, int *count, int reset);
+
+/* ---- batches of detectors ------------------------------------------------
+ *
+ * A batch runs the whole forward path (synth_spin_maps + interp_tod) of many
+ * detectors -- each with its own plan (lmax, kmax, grid, precision), sky,
+ * beam and pointing stream -- as one CUDA graph (no counterpart in the paper,
+ * which convolves one detector at a time).  Detectors are spread over a few
+ * streams inside the graph so that small ones overlap; one graph launch
+ * replaces the per-detector launches.
+ *
+ * sl_batch_create validates the items, reserves each plan's sort scratch for
+ * its n, optionally autotunes (flags & SL_BATCH_AUTOTUNE: per detector the
+ * tile width among 8, 16, 32 by timing interp_tod on its own pointings; then
+ * the number of streams among 1, 2, 4, 8 by timing graph replays), and
+ * captures the graph on `stream`.  It runs the path while tuning, so the
+ * items' inputs must be valid by then.  The graph holds the items' pointers:
+ * later runs read whatever those buffers hold, and the plans may not grow or
+ * re-tile their scratch until the batch is destroyed (such calls return
+ * SL_ERR_ARG).  Every item needs its own plan; plans must be on one device.
+ * The plans' streams are left as they were.
+ *
+ * sl_batch_run enqueues one replay on the batch's stream (asynchronous). */
+typedef struct sl_batch sl_batch;
+
+typedef struct {
+    sl_plan *plan;
+    const double *sky, *beam;             /* device, the plan's packing */
+    void *maps;                           /* device, the plan's maps layout (written) */
+    const double *theta, *phi, *psi;      /* device [n] */
+    int64_t n;
+    double *tod;                          /* device [n] (written) */
+} sl_batch_item;
+
+enum { SL_BATCH_AUTOTUNE = 1 };
+
+typedef struct {
+    int nitems;
+    int nstreams;             /* streams the graph spreads the detectors over */
+    double tuned_ms;          /* replay time measured for that choice (0 without autotuning) */
+    double serial_ms;         /* the same detectors one after another on one stream, no graph
+                                 (measured while autotuning; 0 otherwise) */
+    int kernel_nodes;         /* kernel launches one run of the graph makes */
+    int graph_nodes;          /* all nodes of the graph (kernels, memsets, events) */
+} sl_batch_info;
+
+sl_status sl_batch_create(sl_batch **out, const sl_batch_item *items, int nitems, void *stream, int flags);
+sl_status sl_batch_run(sl_batch *batch);
+sl_status sl_batch_get_info(const sl_batch *batch, sl_batch_info *info);
+void sl_batch_destroy(sl_batch *batch);
 
 /* Thread-local message describing the last non-OK status of this thread. */
 const char *sl_last_error(void);

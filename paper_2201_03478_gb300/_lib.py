@@ -20,7 +20,9 @@ STATUS_NAMES = {0: "SL_OK", -1: "SL_ERR_ARG", -2: "SL_ERR_UNSUPPORTED", -3: "SL_
 # Symbols include/sidelobe.h declares (checked by the host tests).
 EXPORTS = ["sidelobe_plan_create", "synth_spin_maps", "interp_tod", "adjoint_tod", "adjoint_interp",
            "adjoint_synth", "interp_tod_noalloc", "plan_destroy", "sl_plan_get_sizes", "sl_plan_set_stream", "sl_plan_sync",
-           "sl_plan_enable_timing", "sl_plan_kernel_stats", "sl_last_error"]
+           "sl_plan_enable_timing", "sl_plan_kernel_stats", "sl_plan_reserve", "sl_plan_set_tile_cols",
+           "sl_batch_create", "sl_batch_run", "sl_batch_get_info", "sl_batch_destroy", "sl_last_error"]
+SL_BATCH_AUTOTUNE = 1
 
 
 class PlanDesc(ctypes.Structure):
@@ -32,7 +34,19 @@ class PlanDesc(ctypes.Structure):
 
 class PlanSizes(ctypes.Structure):
     _fields_ = [("nalm", ctypes.c_int64), ("sky_doubles", ctypes.c_int64), ("beam_doubles", ctypes.c_int64),
-                ("maps_bytes", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64), ("lsteps", ctypes.c_int64)]
+                ("maps_bytes", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64), ("lsteps", ctypes.c_int64),
+                ("tile_cols", ctypes.c_int64)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("sky", ctypes.c_void_p), ("beam", ctypes.c_void_p),
+                ("maps", ctypes.c_void_p), ("theta", ctypes.c_void_p), ("phi", ctypes.c_void_p),
+                ("psi", ctypes.c_void_p), ("n", ctypes.c_int64), ("tod", ctypes.c_void_p)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("nitems", ctypes.c_int), ("nstreams", ctypes.c_int), ("tuned_ms", ctypes.c_double),
+                ("serial_ms", ctypes.c_double), ("kernel_nodes", ctypes.c_int), ("graph_nodes", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -72,6 +86,12 @@ def load(build: bool = True) -> ctypes.CDLL:
         "sl_plan_sync": (I, [P]),
         "sl_plan_enable_timing": (I, [P, I]),
         "sl_plan_kernel_stats": (I, [P, ctypes.POINTER(KernelStat), I, ctypes.POINTER(I), I]),
+        "sl_plan_reserve": (I, [P, I64]),
+        "sl_plan_set_tile_cols": (I, [P, I]),
+        "sl_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(BatchItem), I, P, I]),
+        "sl_batch_run": (I, [P]),
+        "sl_batch_get_info": (I, [P, ctypes.POINTER(BatchInfo)]),
+        "sl_batch_destroy": (None, [P]),
         "sl_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():

@@ -68,6 +68,14 @@ class Plan:
     def sync(self):
         check(_lib.load().sl_plan_sync(self.ptr))
 
+    def reserve(self, n):
+        """Grow the pointing-sort scratch to n samples now (sl_plan_reserve)."""
+        check(_lib.load().sl_plan_reserve(self.ptr, int(n)))
+
+    def set_tile_cols(self, tile_cols):
+        """Sort-tile width in phi columns: 8, 16 or 32 (sl_plan_set_tile_cols)."""
+        check(_lib.load().sl_plan_set_tile_cols(self.ptr, int(tile_cols)))
+
     def __del__(self):
         try:
             plan_destroy(self)
@@ -247,3 +255,64 @@ def tod_from_host(plan: Plan, sky, beam, theta, phi, psi, chunks: int = 8, out=N
             out[a:b].copy_(tod[a:b], non_blocking=True)
     down_s.synchronize()      # every piece of the TOD is on the host
     return out
+
+
+class Batch:
+    """Owns one sl_batch*: the forward path of several detectors as one CUDA
+    graph.  Holds references to every item's tensors and plan, whose buffers
+    the graph reads and writes on each run."""
+
+    def __init__(self, ptr, items, device):
+        self.ptr = ptr
+        self.items = items
+        self.device = device
+
+    def run(self):
+        check(_lib.load().sl_batch_run(self.ptr))
+
+    def info(self):
+        out = _lib.BatchInfo()
+        check(_lib.load().sl_batch_get_info(self.ptr, ctypes.byref(out)))
+        return {f: getattr(out, f) for f, _ in out._fields_}
+
+    def __del__(self):
+        try:
+            sl_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def sl_batch_create(items, autotune: bool = False) -> Batch:
+    """items: sequence of dicts with keys plan, sky, beam, maps, theta, phi, psi, tod
+    (device tensors in the layouts of synth_spin_maps and interp_tod, one plan per
+    item).  Captured on the current torch stream of the first plan's device."""
+    lib = _lib.load()
+    items = [dict(it) for it in items]
+    if not items:
+        raise ValueError("a batch needs at least one item")
+    device = items[0]["plan"].device
+    arr = (_lib.BatchItem * len(items))()
+    for i, it in enumerate(items):
+        plan = it["plan"]
+        sky, beam = _sky_beam(plan, it["sky"], it["beam"])
+        _dev_tensor(it["maps"], plan.maps_dtype, plan.device, "maps", plan.maps_shape())
+        n = _ptg(plan, it["theta"], it["phi"], it["psi"])
+        _dev_tensor(it["tod"], torch.float64, plan.device, "tod", (n,))
+        arr[i] = _lib.BatchItem(plan=plan.ptr, sky=_ptr(sky), beam=_ptr(beam), maps=_ptr(it["maps"]),
+                                theta=_ptr(it["theta"]), phi=_ptr(it["phi"]), psi=_ptr(it["psi"]), n=n,
+                                tod=_ptr(it["tod"]))
+    stream = torch.cuda.current_stream(device).cuda_stream
+    out = ctypes.c_void_p()
+    check(lib.sl_batch_create(ctypes.byref(out), arr, len(items), ctypes.c_void_p(stream),
+                              _lib.SL_BATCH_AUTOTUNE if autotune else 0))
+    return Batch(out, items, device)
+
+
+def sl_batch_run(batch: Batch) -> None:
+    batch.run()
+
+
+def sl_batch_destroy(batch: Batch) -> None:
+    if batch is not None and batch.ptr:
+        _lib.load().sl_batch_destroy(batch.ptr)
+        batch.ptr = None

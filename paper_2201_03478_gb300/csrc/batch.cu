@@ -1,0 +1,342 @@
+// batch.cu -- the forward path of many detectors as one CUDA graph.
+//
+// A detector is a plan (its own lmax, kmax, ring grid, precision) with its own
+// sky, beam, cube buffer and pointing stream.  The batch captures, once, the
+// synth_spin_maps + interp_tod calls of every detector into a CUDA graph whose
+// branches are spread over a few streams (longest-processing-time-first
+// assignment), so that small detectors overlap and one graph launch replaces
+// every per-detector launch.  Optionally it tunes first: each detector's sort
+// tile width (8, 16 or 32 columns) by timing its own interpolation, then the
+// number of branches (1, 2, 4, 8) by timing replays.
+//
+// This layer is host code on top of the plan API; it only adds the plans'
+// batch_refs lock, which stops a plan from reallocating scratch that a graph
+// still points into.
+#include <algorithm>
+#include <vector>
+
+#include "sl_internal.cuh"
+
+struct sl_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;       // where the graph is captured and replayed
+    bool own_stream = false;
+    std::vector<sl_batch_item> items;
+    std::vector<double> cost;            // per item: measured ms (autotune) or a flop estimate
+    std::vector<cudaStream_t> branches;  // capture-only streams
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> joins;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int nstreams = 0;
+    double tuned_ms = 0.0, serial_ms = 0.0;
+    bool locked = false;
+};
+
+namespace sl {
+
+static void destroy_graph(cudaGraph_t &g, cudaGraphExec_t &e) {
+    if (e) cudaGraphExecDestroy(e);
+    if (g) cudaGraphDestroy(g);
+    e = nullptr;
+    g = nullptr;
+}
+
+// One detector's forward path on its plan's current stream.
+static sl_status run_item(const sl_batch_item &it) {
+    sl_status st = synth_spin_maps(it.plan, it.sky, it.beam, it.maps);
+    if (st != SL_OK) return st;
+    return interp_tod(it.plan, it.maps, it.theta, it.phi, it.psi, it.n, it.tod);
+}
+
+// Moves every plan to stream s (synchronising the old streams), or back to
+// the saved streams when s == nullptr and saved is given.
+static sl_status move_plans(sl_batch *b, const std::vector<cudaStream_t> *assign_streams,
+                            const std::vector<cudaStream_t> *saved) {
+    for (size_t i = 0; i < b->items.size(); ++i) {
+        cudaStream_t s = saved ? (*saved)[i] : (*assign_streams)[i];
+        sl_status st = sl_plan_set_stream(b->items[i].plan, (void *)s);
+        if (st != SL_OK) return st;
+    }
+    return SL_OK;
+}
+
+// Longest processing time first over nbr branches.
+static std::vector<int> assign_branches(const sl_batch *b, int nbr) {
+    const int n = (int)b->items.size();
+    std::vector<int> order(n), br(n, 0);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->cost[x] > b->cost[y]; });
+    std::vector<double> load(nbr, 0.0);
+    for (int i : order) {
+        int best = 0;
+        for (int s = 1; s < nbr; ++s)
+            if (load[s] < load[best]) best = s;
+        br[i] = best;
+        load[best] += b->cost[i];
+    }
+    return br;
+}
+
+// Captures the batch with nbr branches into (graph, exec).
+static sl_status capture(sl_batch *b, int nbr, cudaGraph_t *graph, cudaGraphExec_t *exec) {
+    *graph = nullptr;
+    *exec = nullptr;
+    const int n = (int)b->items.size();
+    const std::vector<int> br = assign_branches(b, nbr);
+    std::vector<cudaStream_t> saved(n), target(n);
+    std::vector<bool> timing(n);
+    for (int i = 0; i < n; ++i) {
+        saved[i] = b->items[i].plan->stream;
+        target[i] = b->branches[br[i]];
+        timing[i] = b->items[i].plan->timing;
+    }
+    sl_status st = move_plans(b, &target, nullptr);
+    if (st != SL_OK) {
+        move_plans(b, nullptr, &saved);
+        return st;
+    }
+    for (int i = 0; i < n; ++i) b->items[i].plan->timing = false;   // no event records inside the graph
+    st = cuda_check(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (st == SL_OK) {
+        sl_status cst = cuda_check(cudaEventRecord(b->fork, b->stream), "fork");
+        for (int s = 0; s < nbr && cst == SL_OK; ++s)
+            cst = cuda_check(cudaStreamWaitEvent(b->branches[s], b->fork, 0), "fork wait");
+        for (int i = 0; i < n && cst == SL_OK; ++i) cst = run_item(b->items[i]);
+        for (int s = 0; s < nbr && cst == SL_OK; ++s) {
+            cst = cuda_check(cudaEventRecord(b->joins[s], b->branches[s]), "join");
+            if (cst == SL_OK) cst = cuda_check(cudaStreamWaitEvent(b->stream, b->joins[s], 0), "join wait");
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (cst == SL_OK) cst = cuda_check(e, "end capture");
+        if (cst == SL_OK) cst = cuda_check(cudaGraphInstantiate(exec, g, 0), "graph instantiate");
+        if (cst != SL_OK) {
+            if (*exec) cudaGraphExecDestroy(*exec);
+            if (g) cudaGraphDestroy(g);
+            *exec = nullptr;
+            g = nullptr;
+            cudaGetLastError();
+        }
+        *graph = g;
+        st = cst;
+    }
+    for (int i = 0; i < n; ++i) b->items[i].plan->timing = timing[i];
+    const sl_status rst = move_plans(b, nullptr, &saved);
+    return st != SL_OK ? st : rst;
+}
+
+// Milliseconds of `reps` replays of exec on the batch stream (after one warm replay).
+static sl_status time_replays(sl_batch *b, cudaGraphExec_t exec, int reps, double *ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sl_status st = cuda_check(cudaEventCreate(&e0), "event");
+    if (st == SL_OK) st = cuda_check(cudaEventCreate(&e1), "event");
+    if (st == SL_OK) st = cuda_check(cudaGraphLaunch(exec, b->stream), "graph launch");
+    if (st == SL_OK) st = cuda_check(cudaEventRecord(e0, b->stream), "event");
+    for (int r = 0; r < reps && st == SL_OK; ++r) st = cuda_check(cudaGraphLaunch(exec, b->stream), "graph launch");
+    if (st == SL_OK) st = cuda_check(cudaEventRecord(e1, b->stream), "event");
+    if (st == SL_OK) st = cuda_check(cudaEventSynchronize(e1), "event sync");
+    float t = 0.f;
+    if (st == SL_OK) st = cuda_check(cudaEventElapsedTime(&t, e0, e1), "elapsed");
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    *ms = (double)t / reps;
+    return st;
+}
+
+// Milliseconds of fn() enqueued on the batch stream (plans moved there by the caller).
+template <typename F>
+static sl_status time_on_stream(sl_batch *b, F fn, double *ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sl_status st = cuda_check(cudaEventCreate(&e0), "event");
+    if (st == SL_OK) st = cuda_check(cudaEventCreate(&e1), "event");
+    if (st == SL_OK) st = cuda_check(cudaEventRecord(e0, b->stream), "event");
+    if (st == SL_OK) st = fn();
+    if (st == SL_OK) st = cuda_check(cudaEventRecord(e1, b->stream), "event");
+    if (st == SL_OK) st = cuda_check(cudaEventSynchronize(e1), "event sync");
+    float t = 0.f;
+    if (st == SL_OK) st = cuda_check(cudaEventElapsedTime(&t, e0, e1), "elapsed");
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    *ms = (double)t;
+    return st;
+}
+
+// Per detector: the fastest tile width for its own pointings, and its cost;
+// then the serial time of the whole batch.
+static sl_status autotune_items(sl_batch *b) {
+    const int n = (int)b->items.size();
+    for (int i = 0; i < n; ++i) {
+        const sl_batch_item &it = b->items[i];
+        double t_syn = 0.0;
+        sl_status st = time_on_stream(b, [&] { return synth_spin_maps(it.plan, it.sky, it.beam, it.maps); }, &t_syn);
+        if (st != SL_OK) return st;
+        int best_tc = it.plan->geom.tile_cols;
+        double best = -1.0;
+        for (int tc : {8, 16, 32}) {
+            if (sl_plan_set_tile_cols(it.plan, tc) != SL_OK) continue;   // not valid for this grid
+            auto interp = [&] { return interp_tod(it.plan, it.maps, it.theta, it.phi, it.psi, it.n, it.tod); };
+            double t = 0.0;
+            if ((st = time_on_stream(b, interp, &t)) != SL_OK) return st;   // warm
+            if ((st = time_on_stream(b, interp, &t)) != SL_OK) return st;
+            if (best < 0.0 || t < best) {
+                best = t;
+                best_tc = tc;
+            }
+        }
+        if ((st = sl_plan_set_tile_cols(it.plan, best_tc)) != SL_OK) return st;
+        b->cost[i] = t_syn + std::max(best, 0.0);
+    }
+    return time_on_stream(b, [&] {
+        for (const sl_batch_item &it : b->items) {
+            sl_status s = run_item(it);
+            if (s != SL_OK) return s;
+        }
+        return SL_OK;
+    }, &b->serial_ms);
+}
+
+static void release(sl_batch *b) {
+    if (b->locked)
+        for (const sl_batch_item &it : b->items) --it.plan->batch_refs;
+    b->locked = false;
+    destroy_graph(b->graph, b->exec);
+    for (cudaStream_t s : b->branches) cudaStreamDestroy(s);
+    b->branches.clear();
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+    b->joins.clear();
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+}  // namespace sl
+
+using namespace sl;
+
+extern "C" {
+
+sl_status sl_batch_create(sl_batch **out, const sl_batch_item *items, int nitems, void *stream, int flags) {
+    if (!out) return set_error(SL_ERR_ARG, "sl_batch_create: out is NULL");
+    *out = nullptr;
+    if (!items || nitems < 1) return set_error(SL_ERR_ARG, "sl_batch_create: no items");
+    for (int i = 0; i < nitems; ++i) {
+        const sl_batch_item &it = items[i];
+        if (!it.plan) return set_error(SL_ERR_ARG, "sl_batch_create: item %d has no plan", i);
+        if (it.plan->device != items[0].plan->device)
+            return set_error(SL_ERR_ARG, "sl_batch_create: item %d is on device %d, item 0 on %d", i,
+                             it.plan->device, items[0].plan->device);
+        for (int j = 0; j < i; ++j)
+            if (items[j].plan == it.plan)
+                return set_error(SL_ERR_ARG, "sl_batch_create: items %d and %d share a plan", j, i);
+        if (!it.sky || !it.beam || !it.maps) return set_error(SL_ERR_ARG, "sl_batch_create: item %d: NULL buffer", i);
+        if (it.n < 0 || it.n >= ((int64_t)1 << 31))
+            return set_error(SL_ERR_ARG, "sl_batch_create: item %d: n=%lld outside [0, 2^31)", i, (long long)it.n);
+        if (it.n > 0 && (!it.theta || !it.phi || !it.psi || !it.tod))
+            return set_error(SL_ERR_ARG, "sl_batch_create: item %d: NULL pointing or TOD buffer", i);
+    }
+    sl_batch *b = new (std::nothrow) sl_batch();
+    if (!b) return set_error(SL_ERR_NOMEM, "sl_batch_create: host allocation");
+    b->device = items[0].plan->device;
+    b->items.assign(items, items + nitems);
+    b->cost.assign(nitems, 0.0);
+    sl_status st = cuda_check(cudaSetDevice(b->device), "cudaSetDevice");
+    if (st == SL_OK && stream) {
+        b->stream = (cudaStream_t)stream;
+    } else if (st == SL_OK) {   // the legacy stream cannot be captured: a blocking stream of our own
+        st = cuda_check(cudaStreamCreate(&b->stream), "batch stream");
+        b->own_stream = st == SL_OK;
+    }
+    const int max_branches = std::min(8, nitems);
+    for (int s = 0; s < max_branches && st == SL_OK; ++s) {
+        cudaStream_t bs = nullptr;
+        st = cuda_check(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking), "branch stream");
+        if (st == SL_OK) b->branches.push_back(bs);
+        cudaEvent_t ev = nullptr;
+        if (st == SL_OK) st = cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "join event");
+        if (st == SL_OK) b->joins.push_back(ev);
+    }
+    if (st == SL_OK) st = cuda_check(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "fork event");
+    for (int i = 0; i < nitems && st == SL_OK; ++i) st = sl_plan_reserve(b->items[i].plan, b->items[i].n);
+    for (int i = 0; i < nitems && st == SL_OK; ++i) {   // flop estimate (FP64 at 1/64 of the FP32 rate)
+        const sl_plan *p = b->items[i].plan;
+        const double w = p->precision == SL_FP64 ? 64.0 : 1.0;
+        b->cost[i] = w * (11.0 * (double)p->lsteps + 4.0 * 16.0 * (p->K + 1) * (double)b->items[i].n);
+    }
+    if (st == SL_OK && (flags & SL_BATCH_AUTOTUNE)) {
+        std::vector<cudaStream_t> saved(nitems), here(nitems, b->stream);
+        for (int i = 0; i < nitems; ++i) saved[i] = b->items[i].plan->stream;
+        st = move_plans(b, &here, nullptr);
+        if (st == SL_OK) st = autotune_items(b);
+        const sl_status rst = move_plans(b, nullptr, &saved);
+        if (st == SL_OK) st = rst;
+        for (int nbr = 1; nbr <= max_branches && st == SL_OK; nbr *= 2) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t e = nullptr;
+            double ms = 0.0;
+            st = capture(b, nbr, &g, &e);
+            if (st == SL_OK) st = time_replays(b, e, 2, &ms);
+            if (st == SL_OK && (b->nstreams == 0 || ms < b->tuned_ms)) {
+                destroy_graph(b->graph, b->exec);
+                b->graph = g;
+                b->exec = e;
+                b->nstreams = nbr;
+                b->tuned_ms = ms;
+            } else {
+                destroy_graph(g, e);
+            }
+        }
+    } else if (st == SL_OK) {
+        b->nstreams = std::min(4, max_branches);
+        st = capture(b, b->nstreams, &b->graph, &b->exec);
+    }
+    if (st == SL_OK) {
+        for (const sl_batch_item &it : b->items) ++it.plan->batch_refs;
+        b->locked = true;
+        *out = b;
+        return SL_OK;
+    }
+    release(b);
+    delete b;
+    return st;
+}
+
+sl_status sl_batch_run(sl_batch *b) {
+    if (!b || !b->exec) return set_error(SL_ERR_ARG, "sl_batch_run: no batch");
+    sl_status st = cuda_check(cudaSetDevice(b->device), "cudaSetDevice");
+    if (st != SL_OK) return st;
+    return cuda_check(cudaGraphLaunch(b->exec, b->stream), "sl_batch_run: graph launch");
+}
+
+sl_status sl_batch_get_info(const sl_batch *b, sl_batch_info *info) {
+    if (!b || !info) return set_error(SL_ERR_ARG, "sl_batch_get_info: NULL argument");
+    info->nitems = (int)b->items.size();
+    info->nstreams = b->nstreams;
+    info->tuned_ms = b->tuned_ms;
+    info->serial_ms = b->serial_ms;
+    info->kernel_nodes = info->graph_nodes = 0;
+    size_t count = 0;
+    sl_status st = cuda_check(cudaGraphGetNodes(b->graph, nullptr, &count), "graph nodes");
+    if (st != SL_OK) return st;
+    std::vector<cudaGraphNode_t> nodes(count);
+    if (count && (st = cuda_check(cudaGraphGetNodes(b->graph, nodes.data(), &count), "graph nodes")) != SL_OK)
+        return st;
+    info->graph_nodes = (int)count;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++info->kernel_nodes;
+    }
+    return SL_OK;
+}
+
+void sl_batch_destroy(sl_batch *b) {
+    if (!b) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    release(b);
+    delete b;
+    cudaSetDevice(prev);
+}
+
+}  // extern "C"

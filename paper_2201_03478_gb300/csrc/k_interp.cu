@@ -240,10 +240,12 @@ __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
     }
 }
 
-size_t interp_f32_tiled_smem(const sl_plan *p) {
+size_t interp_f32_tiled_smem_tc(const sl_plan *p, int tc) {
     const int KH = (p->K + 2) / 2;
-    return (size_t)(kTileRows + 3) * (p->geom.tile_cols + 3) * KH * sizeof(float4);
+    return (size_t)(kTileRows + 3) * (tc + 3) * KH * sizeof(float4);
 }
+
+size_t interp_f32_tiled_smem(const sl_plan *p) { return interp_f32_tiled_smem_tc(p, p->geom.tile_cols); }
 
 // ------------------------------------------------------------------ adjoint
 // maps_bar_k(node) += y wt_a wp_b sigma_{a,k} eps_k e^{-ik psi},  eps_0 = 1, eps_k = 2.
@@ -418,6 +420,13 @@ sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *map
     return cuda_check(cudaGetLastError(), "k_interp launch");
 }
 
+size_t interp_adjoint_smem_tc(const sl_plan *p, int tc) {
+    const int K1 = p->K + 1;
+    const int nnode = (kTileRows + 3) * (tc + 3);
+    return (size_t)nnode * K1 * sizeof(double2) + (size_t)kNB * K1 * sizeof(double2) +
+           (size_t)kNB * 16 * sizeof(double) + (size_t)kNB * sizeof(int);
+}
+
 sl_status launch_interp_adjoint(sl_plan *p, const SortBufs &b, int fine, const double *psi, const double *tod,
                                 int64_t n, double2 *fbar) {
     AdjArgs a;
@@ -432,9 +441,7 @@ sl_status launch_interp_adjoint(sl_plan *p, const SortBufs &b, int fine, const d
     a.ncell = fine ? kTileRows * p->geom.tile_cols : 1;
     a.fbar = fbar;
     const int K1 = p->K + 1;
-    const int nnode = (kTileRows + 3) * (p->geom.tile_cols + 3);
-    const size_t sm = (size_t)nnode * K1 * sizeof(double2) + (size_t)kNB * K1 * sizeof(double2) +
-                      (size_t)kNB * 16 * sizeof(double) + (size_t)kNB * sizeof(int);
+    const size_t sm = interp_adjoint_smem_tc(p, p->geom.tile_cols);
     int nwarps = (K1 + 1) / 2;
     if (nwarps < 2) nwarps = 2;
     if (nwarps > 16) nwarps = 16;

@@ -101,6 +101,10 @@ static void dfree(void *ptr) {
 
 static sl_status ensure_sort_capacity(sl_plan *p, int64_t n) {
     if (n <= p->sort_cap) return SL_OK;
+    if (p->batch_refs > 0)
+        return set_error(SL_ERR_ARG, "n=%lld exceeds the sort scratch (%lld samples) of a plan that a batch graph "
+                                     "holds; reserve the capacity before the batch is created",
+                         (long long)n, (long long)p->sort_cap);
     cudaStreamSynchronize(p->stream);
     dfree(p->sort.keys);
     dfree(p->sort.perm);
@@ -117,6 +121,33 @@ static sl_status ensure_sort_capacity(sl_plan *p, int64_t n) {
     if (st != SL_OK) return st;
     p->sort_cap = n;
     return SL_OK;
+}
+
+// Per-key tables of the sort (their size follows the tile grid).
+static sl_status alloc_sort_tables(sl_plan *p) {
+    p->nkeys = sort_nkeys(p, 1);
+    sl_status st = dalloc_t(p, &p->sort.hist, (size_t)p->nkeys + 1, "cell histogram");
+    if (st == SL_OK) st = dalloc_t(p, &p->sort.cursor, (size_t)p->nkeys, "cell cursor");
+    if (st == SL_OK) st = dalloc_t(p, &p->sort.bsum, (size_t)sort_nbsum(p->nkeys) + 2, "scan block sums");
+    if (st == SL_OK) st = dalloc_t(p, &p->sort.chunk_off, (size_t)p->ntiles + 1, "tile chunks");
+    return st;
+}
+
+static void free_sort_tables(sl_plan *p) {
+    dfree(p->sort.hist);
+    dfree(p->sort.cursor);
+    dfree(p->sort.bsum);
+    dfree(p->sort.chunk_off);
+    p->sort.hist = p->sort.cursor = p->sort.bsum = p->sort.chunk_off = nullptr;
+    p->bytes_held -= (int64_t)sizeof(unsigned) * ((p->nkeys + 1) + p->nkeys + (sort_nbsum(p->nkeys) + 2) +
+                                                  (p->ntiles + 1));
+}
+
+static void set_tile_grid(sl_plan *p, int tc) {
+    p->geom.tile_cols = tc;
+    p->geom.ntr = (p->R + 1 + kTileRows - 1) / kTileRows;
+    p->geom.ntc = (p->nphi + tc - 1) / tc;
+    p->ntiles = p->geom.ntr * p->geom.ntc;
 }
 
 static sl_status ensure_adjoint_scratch(sl_plan *p) {
@@ -347,12 +378,11 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     p->geom.phi_scale = p->nphi / (2.0 * M_PI);
     p->geom.phi_fix = (unsigned long long)llroundl(
         ldexpl((long double)p->nphi / (2.0L * 3.14159265358979323846264338327950288L), 52));
-    // tile width: 32 columns (16 when kmax > 16), at most nphi; one of 8, 16, 32
-    p->geom.tile_cols = (K <= 16) ? 32 : 16;
-    while (p->geom.tile_cols > p->nphi) p->geom.tile_cols >>= 1;
-    p->geom.ntr = (R + 1 + kTileRows - 1) / kTileRows;
-    p->geom.ntc = (p->nphi + p->geom.tile_cols - 1) / p->geom.tile_cols;
-    p->ntiles = p->geom.ntr * p->geom.ntc;
+    {   // tile width: 32 columns (16 when kmax > 16), at most nphi; one of 8, 16, 32
+        int tc = (K <= 16) ? 32 : 16;
+        while (tc > p->nphi) tc >>= 1;
+        set_tile_grid(p, tc);
+    }
 
     double *d_c2 = nullptr, *d_s2 = nullptr, *d_cs = nullptr;
 #define TRY(x)                      \
@@ -434,11 +464,7 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
         p->G_bytes = gel * (p->precision == SL_FP64 ? sizeof(double2) : sizeof(float2));
         TRY(dalloc(p, &p->d_G, p->G_bytes, "spin-Legendre scratch G"));
     }
-    p->nkeys = sort_nkeys(p, 1);
-    TRY(dalloc_t(p, &p->sort.hist, (size_t)p->nkeys + 1, "cell histogram"));
-    TRY(dalloc_t(p, &p->sort.cursor, (size_t)p->nkeys, "cell cursor"));
-    TRY(dalloc_t(p, &p->sort.bsum, (size_t)sort_nbsum(p->nkeys) + 2, "scan block sums"));
-    TRY(dalloc_t(p, &p->sort.chunk_off, (size_t)p->ntiles + 1, "tile chunks"));
+    TRY(alloc_sort_tables(p));
     TRY(cuda_check(cudaStreamSynchronize(p->stream), "plan seeds"));
     dfree(d_c2);
     dfree(d_s2);
@@ -544,7 +570,34 @@ sl_status sl_plan_get_sizes(const sl_plan *p, sl_plan_sizes *o) {
     o->maps_bytes = (int64_t)p->R * p->nphi * (p->K + 1) * (p->precision == SL_FP64 ? 16 : 8);
     o->scratch_bytes = p->bytes_held;
     o->lsteps = p->lsteps;
+    o->tile_cols = p->geom.tile_cols;
     return SL_OK;
+}
+
+sl_status sl_plan_reserve(sl_plan *p, int64_t n) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if (n < 0 || n >= ((int64_t)1 << 31)) return set_error(SL_ERR_ARG, "sl_plan_reserve: n=%lld outside [0, 2^31)", (long long)n);
+    return ensure_sort_capacity(p, n);
+}
+
+sl_status sl_plan_set_tile_cols(sl_plan *p, int tc) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if (tc != 8 && tc != 16 && tc != 32) return set_error(SL_ERR_ARG, "tile width %d is not 8, 16 or 32", tc);
+    if (tc > p->nphi) return set_error(SL_ERR_ARG, "tile width %d exceeds nphi=%d", tc, p->nphi);
+    if (tc == p->geom.tile_cols) return SL_OK;
+    int dev_smem = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    const size_t need = std::max(interp_f32_tiled_smem_tc(p, tc), interp_adjoint_smem_tc(p, tc));
+    if (dev_smem > 0 && need > (size_t)dev_smem)
+        return set_error(SL_ERR_UNSUPPORTED, "tile width %d needs %zu bytes of shared memory (device: %d)", tc,
+                         need, dev_smem);
+    if (p->batch_refs > 0) return set_error(SL_ERR_ARG, "the plan is held by a batch graph");
+    if ((st = cuda_check(cudaStreamSynchronize(p->stream), "stream synchronize")) != SL_OK) return st;
+    free_sort_tables(p);
+    set_tile_grid(p, tc);
+    return alloc_sort_tables(p);
 }
 
 sl_status sl_plan_set_stream(sl_plan *p, void *stream) {

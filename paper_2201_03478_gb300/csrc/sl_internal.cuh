@@ -147,6 +147,9 @@ struct sl_plan {
     int64_t sort_cap = 0;
 
     int64_t bytes_held = 0;
+    // number of captured batch graphs that hold pointers into this plan's
+    // scratch: while > 0 nothing may be reallocated (the graphs would dangle)
+    int batch_refs = 0;
 
     // timing
     bool timing = false;
@@ -183,6 +186,9 @@ sl_status launch_sort_into(sl_plan *p, const SortBufs &b, const double *theta, c
 sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *maps, const double *psi, int64_t n,
                         double *tod);
 size_t interp_f32_tiled_smem(const sl_plan *p);
+// Dynamic shared memory of the two tile-staged kernels for tile width tc.
+size_t interp_f32_tiled_smem_tc(const sl_plan *p, int tc);
+size_t interp_adjoint_smem_tc(const sl_plan *p, int tc);
 // Adjoint scatter over a sort made with rec64 = 1, with_chunks = 1.
 sl_status launch_interp_adjoint(sl_plan *p, const SortBufs &b, int fine, const double *psi, const double *tod,
                                 int64_t n, double2 *fbar);

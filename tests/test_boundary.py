@@ -80,6 +80,24 @@ def test_null_arguments(lib):
     assert lib.interp_tod(None, None, None, None, None, 0, None) == -1
     assert lib.adjoint_tod(None, None, None, None, None, 0, None, None, None, None, 0) == -1
     lib.plan_destroy(None)
+    assert lib.sl_plan_reserve(None, 10) == -1
+    assert lib.sl_plan_set_tile_cols(None, 16) == -1
+
+
+def test_batch_arguments_are_checked_before_any_device_call(lib):
+    from paper_2201_03478_gb300 import _lib
+    out = ctypes.c_void_p()
+    assert lib.sl_batch_create(None, None, 0, None, 0) == -1
+    assert lib.sl_batch_create(ctypes.byref(out), None, 1, None, 0) == -1
+    items = (_lib.BatchItem * 2)()
+    assert lib.sl_batch_create(ctypes.byref(out), items, 0, None, 0) == -1
+    assert lib.sl_batch_create(ctypes.byref(out), items, 2, None, 0) == -1        # no plan
+    assert b"no plan" in lib.sl_last_error()
+    assert not out.value
+    assert lib.sl_batch_run(None) == -1
+    info = _lib.BatchInfo()
+    assert lib.sl_batch_get_info(None, ctypes.byref(info)) == -1
+    lib.sl_batch_destroy(None)
 
 
 def test_oracle_builds():

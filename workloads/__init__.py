@@ -27,6 +27,7 @@ __all__ = [
     "nalm", "alm_index", "healpix_ring_theta", "equiangular_ring_theta",
     "sky_gaussian", "sky_polarised", "beam_gaussian_taper", "beam_far_sidelobe",
     "pointings_uniform", "pointings_scan", "config_small", "config_lfi", "config_highres",
+    "truncate_alm", "rotation_about", "config_detectors",
 ]
 
 
@@ -150,12 +151,13 @@ def pointings_uniform(n: int, seed: int = 2):
 
 def pointings_scan(n: int, fsamp: float = 32.5, spin_rpm: float = 1.0,
                    opening_deg: float = 85.0, psi_offset: float = 0.0,
-                   t0: float = 0.0, chunk: int = 1 << 22):
+                   t0: float = 0.0, chunk: int = 1 << 22, offset=None):
     """Synthetic satellite scan: spin axis in the ecliptic plane at longitude
     2 pi t / (365.25 d), boresight at ``opening_deg`` from the spin axis,
     spinning at ``spin_rpm``; the beam x-axis points along the scan direction.
     (theta, phi, psi) are the zyz Euler angles of the beam-to-sky rotation
-    R = [x_beam, y_beam, boresight]."""
+    R = [x_beam, y_beam, boresight].  ``offset`` (a 3x3 rotation) moves the
+    detector within the focal plane: R -> R @ offset."""
     th = np.empty(n)
     ph = np.empty(n)
     ps = np.empty(n)
@@ -178,6 +180,15 @@ def pointings_scan(n: int, fsamp: float = 32.5, spin_rpm: float = 1.0,
         xz = -sw
         # y = n cross x
         yz = nx * xy - ny * xx
+        if offset is not None:
+            Q = np.asarray(offset, dtype=np.float64)
+            yx = ny * xz - nz * xy
+            yy = nz * xx - nx * xz
+            cols = []
+            for j in range(3):     # column j of R @ Q = sum_i R[:, i] Q[i, j]
+                cols.append(tuple(Q[0, j] * a + Q[1, j] * b + Q[2, j] * c
+                                  for a, b, c in ((xx, yx, nx), (xy, yy, ny), (xz, yz, nz))))
+            (xx, xy, xz), (_, _, yz), (nx, ny, nz) = cols
         th[s:e] = np.arccos(np.clip(nz, -1.0, 1.0))
         ph[s:e] = np.mod(np.arctan2(ny, nx), 2.0 * math.pi)
         ps[s:e] = np.mod(np.arctan2(yz, -xz) + psi_offset, 2.0 * math.pi)
@@ -221,3 +232,44 @@ def config_highres(n: int = 200_000_000, with_pointings: bool = True):
     if with_pointings:
         d["theta"], d["phi"], d["psi"] = pointings_uniform(n, seed=2)
     return d
+
+
+def truncate_alm(alm: np.ndarray, lmax: int, lnew: int) -> np.ndarray:
+    """The packed coefficients [..., nalm(lmax)] restricted to l <= lnew."""
+    idx = np.concatenate([alm_index(lmax, np.arange(m, lnew + 1), m) for m in range(lnew + 1)])
+    return np.ascontiguousarray(alm[..., idx])
+
+
+def rotation_about(axis, angle: float) -> np.ndarray:
+    """Rotation matrix by ``angle`` about the unit vector ``axis`` (Rodrigues)."""
+    a = np.asarray(axis, dtype=np.float64)
+    a = a / np.linalg.norm(a)
+    K = np.array([[0.0, -a[2], a[1]], [a[2], 0.0, -a[0]], [-a[1], a[0], 0.0]])
+    return np.eye(3) + math.sin(angle) * K + (1.0 - math.cos(angle)) * (K @ K)
+
+
+def config_detectors(ndet: int = 22, sky_lmax: int = 1500, seed: int = 3, with_pointings: bool = True):
+    """Many detectors with uneven band limits sharing one polarised sky:
+    detector d has lmax = (256, 512, 768, 1024, 1500)[d mod 5] and
+    kmax = (4, 8, 12, 16, 24)[3d mod 5], its own far-sidelobe beam (seed 100+d),
+    lmax_d equiangular rings x 2 lmax_d phi, a scan of n_d samples (log-uniform
+    in [1e6, 5e7]) seen through a random 0-5 degree focal-plane offset and a
+    psi offset uniform in [0, 2 pi).  The sky is the T/E/B sky at sky_lmax
+    truncated to each lmax_d."""
+    rng = np.random.default_rng(seed)
+    sky = sky_polarised(sky_lmax, seed=0)
+    dets = []
+    for d in range(ndet):
+        L = (256, 512, 768, 1024, 1500)[d % 5]
+        K = (4, 8, 12, 16, 24)[(3 * d) % 5]
+        n = int(round(math.exp(rng.uniform(math.log(1e6), math.log(5e7)))))
+        axis = rng.standard_normal(3)
+        offset = rotation_about(axis, math.radians(rng.uniform(0.0, 5.0)))
+        psi_off = rng.uniform(0.0, 2.0 * math.pi)
+        det = dict(lmax=L, kmax=K, sky=truncate_alm(sky, sky_lmax, L),
+                   beam=beam_far_sidelobe(L, K, seed=100 + d), ring_theta=equiangular_ring_theta(L),
+                   nphi=2 * L, n=n, offset=offset, psi_offset=psi_off)
+        if with_pointings:
+            det["theta"], det["phi"], det["psi"] = pointings_scan(n, psi_offset=psi_off, offset=offset)
+        dets.append(det)
+    return dets
