@@ -184,6 +184,8 @@ def gpu_arm(args):
     theta, phi, psi = (t.to(device) for t in ptg_h)
 
     plan = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=ncomp, precision=args.precision, device=local)
+    if args.tile_cols:
+        plan.set_tile_cols(args.tile_cols)
     maps = torch.empty(plan.maps_shape(), dtype=plan.maps_dtype, device=device)
     tod = torch.empty(n, dtype=torch.float64, device=device)
 
@@ -267,6 +269,7 @@ def gpu_arm(args):
         "data": data,
         "config": {"workload": workload,
                    "lmax": L, "kmax": K, "ncomp": ncomp, "nrings": R, "nphi": nphi, "interp_order": 4,
+                   "tile_cols": plan.sizes()["tile_cols"],
                    "samples_per_gpu": n, "precision": prec, "parallelism": "replicated cube, sharded TOD",
                    "l2": "inputs larger than L2 (pointings %.1f GB, cube %.2f GB)" % (24 * n / 1e9,
                                                                                        plan.sizes()["maps_bytes"] / 1e9)},
@@ -541,6 +544,7 @@ def main(argv=None):
                          "highres: lmax 2048, kmax 32, 2048 x 4096 rings, uniform pointings (precision variant); "
                          "detectors: 22 detectors of uneven lmax/kmax in one CUDA graph (batch variant)")
     ap.add_argument("--ndet", type=int, default=22, help="detectors of the batch workload")
+    ap.add_argument("--tile-cols", type=int, default=0, help="sort-tile width (8, 16, 32; 0: the plan's default)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--n", type=float, default=0, help="pointings per GPU (default 1e8; 2e8 for highres)")
     ap.add_argument("--e2e-steps", type=int, default=3)
