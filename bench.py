@@ -135,6 +135,18 @@ def measured_peaks():
 #   FP32: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz = 80.55 TFLOP/s
 PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+DTYPE = {"fp64": "f64", "fp32": "f32 (FP64 seeds/coords/final sum)",
+         "df64": "f32x2 double-float contraction and interpolation (FP64 seeds/tables/FFT/coords)"}
+PEAK_FP32_TINST = 152 * 128 * 2.07e9 / 1e12          # FP32-pipe instructions per second (x 1e12)
+
+
+def df_interp_inst(K, p=4):
+    """FP32 instructions the double-float interpolation executes per sample
+    (counted from k_interp_df.cu): a double-float multiply-accumulate is 12
+    instructions (product with its FMA error terms, two_sum, two adds); per
+    k >= 1 there are 2 p^2 of them, 2 for the phase and a double-float
+    Chebyshev step for cos and sin (36); k = 0 has p^2; the weights take ~320."""
+    return 12 * p * p + K * (12 * 2 * p * p + 6 + 24 + 36) + 320
 
 
 def algorithmic_flops(L, K, R, n, p=4):
@@ -230,20 +242,23 @@ def gpu_arm(args):
     # 11 flops (3 recurrence + 2 complex x real MACs) per visited (ring, m, k, sign, l)
     fl_lc = 11.0 * plan.sizes()["lsteps"]
     prec = args.precision
-    peak = PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS
+    suffix = {"fp64": "f64", "fp32": "f32", "df64": "df"}[prec]
     roofs = {}
-    for name, fl in ((f"lcontract_{'f64' if prec == 'fp64' else 'f32'}", fl_lc),
-                     (f"interp_{'f64' if prec == 'fp64' else 'f32'}", fl_in)):
+    lc_name = "lcontract_f64" if prec == "df64" else "lcontract_" + suffix
+    kernels = [(lc_name, fl_lc, PEAK_FP64_TFLOPS if prec != "fp32" else PEAK_FP32_TFLOPS, "TFLOP/s"),
+               ("interp_" + suffix, fl_in if prec != "df64" else float(n) * df_interp_inst(K),
+                PEAK_FP32_TINST if prec == "df64" else (PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS),
+                "Tinst/s" if prec == "df64" else "TFLOP/s")]
+    for name, fl, peak, unit in kernels:
         if name in stats and stats[name][0] > 0:
             avg_ms = stats[name][1] / stats[name][0]
             ach = fl / (avg_ms / 1e3) / 1e12
             roofs[name] = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4),
-                           "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                           "unit": unit, "frac": round(ach / peak, 4),
                            "traffic": None if highres else TRAFFIC.get((name, prec)),
                            "avg_ms": round(avg_ms, 4),
-                           "flops_per_launch": fl,
+                           ("flops_per_launch" if unit == "TFLOP/s" else "fp32_inst_per_launch"): fl,
                            "peak_note": "derived from unit counts x 2.07 GHz max SM clock"}
-    lc_name = "lcontract_%s" % ("f64" if prec == "fp64" else "f32")
     if lc_name in roofs:
         roofs[lc_name]["flops_dense_triangle"] = fl_dense
         roofs[lc_name]["dense_equivalent_tflops"] = round(fl_dense / (roofs[lc_name]["avg_ms"] / 1e3) / 1e12, 4)
@@ -265,7 +280,7 @@ def gpu_arm(args):
         "metric": metric,
         "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == "fp64" else "f32 (FP64 seeds/coords/final sum)",
+        "dtype": DTYPE[prec],
         "data": data,
         "config": {"workload": workload,
                    "lmax": L, "kmax": K, "ncomp": ncomp, "nrings": R, "nphi": nphi, "interp_order": 4,
@@ -306,9 +321,10 @@ def gpu_arm(args):
                           "kernel_ms_per_step": {k: round(v[1] / args.adjoint_steps, 4) for k, v in st_adj.items()}}
         del gs, gb, y
 
-    # ---- the other precision on the same box, compared with this run's TOD
-    if args.compare and rank == 0 and world == 1:
-        other = "fp32" if prec == "fp64" else "fp64"
+    # ---- the other precisions on the same box, compared with this run's TOD
+    others = [q for q in ("fp64", "df64", "fp32") if q != prec] if (args.compare and rank == 0 and world == 1) else []
+    out["other_precisions"] = []
+    for other in others:
         p2 = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=ncomp, precision=other, device=local)
         maps2 = torch.empty(p2.maps_shape(), dtype=p2.maps_dtype, device=device)
         tod2 = torch.empty(n, dtype=torch.float64, device=device)
@@ -326,8 +342,8 @@ def gpu_arm(args):
         torch.cuda.synchronize()
         ms2 = e0.elapsed_time(e1) / args.steps
         err = float(torch.linalg.vector_norm(tod2 - tod) / torch.linalg.vector_norm(tod))
-        out["other_precision"] = {"precision": other, "value": n / (ms2 / 1e3), "unit": "samples/s",
-                                  "ms_per_step": ms2, "tod_rel_l2_vs_%s" % prec: err}
+        out["other_precisions"].append({"precision": other, "value": n / (ms2 / 1e3), "unit": "samples/s",
+                                        "ms_per_step": ms2, "tod_rel_l2_vs_%s" % prec: err})
         del maps2, tod2, p2
 
     # ---- end to end through the public API from pinned host buffers
@@ -422,7 +438,7 @@ def detectors_arm(args):
         "metric": "TOD samples/s (cube build+interp), %d detectors of uneven lmax/kmax in one CUDA graph" % len(dets),
         "value": ntot / (ms / 1e3), "unit": "samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32 (FP64 seeds/coords/final sum)",
+        "dtype": DTYPE[args.precision],
         "data": "synthetic (T/E/B sky truncated per detector, per-detector far-sidelobe beams, offset scans)",
         "config": {"workload": "multi-detector batch: %d detectors, lmax in {256..1500}, kmax in {4..24}, "
                                "%d samples in total" % (len(dets), ntot),
@@ -538,7 +554,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "df64"], default="fp64")
     ap.add_argument("--workload", choices=["lfi", "highres", "detectors"], default="lfi",
                     help="lfi: T/E/B, lmax 1024, kmax 16, scan (the headline); "
                          "highres: lmax 2048, kmax 32, 2048 x 4096 rings, uniform pointings (precision variant); "

@@ -75,10 +75,15 @@ typedef enum {
 
 typedef enum {
     SL_FP64 = 0,  /* everything in double precision */
-    SL_FP32 = 1   /* FP64 seeds and recurrence coefficients, pointing->grid
+    SL_FP32 = 1,  /* FP64 seeds and recurrence coefficients, pointing->grid
                      conversion, psi reduction and final TOD value; FP32
                      recurrence, sky x beam products, contraction, ring FFT,
                      maps and interpolation sums */
+    SL_DF64 = 4   /* FP64-class results from the FP32 pipes: the layouts,
+                     tables, FFT and coordinates of SL_FP64 (maps are double2),
+                     with the l-contraction and the interpolation sums run in
+                     double-float arithmetic (pairs of floats, ~48-bit
+                     significands).  The adjoint runs in FP64. */
 } sl_precision;
 
 typedef struct {

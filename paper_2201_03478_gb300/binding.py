@@ -21,9 +21,9 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import SL_FP32, SL_FP64, check
+from ._lib import SL_DF64, SL_FP32, SL_FP64, check
 
-_PREC = {"fp64": SL_FP64, "fp32": SL_FP32, SL_FP64: SL_FP64, SL_FP32: SL_FP32}
+_PREC = {"fp64": SL_FP64, "fp32": SL_FP32, "df64": SL_DF64, SL_FP64: SL_FP64, SL_FP32: SL_FP32, SL_DF64: SL_DF64}
 
 
 class Plan:
@@ -40,7 +40,7 @@ class Plan:
 
     @property
     def maps_dtype(self):
-        return torch.complex128 if self.precision == SL_FP64 else torch.complex64
+        return torch.complex64 if self.precision == SL_FP32 else torch.complex128
 
     def maps_shape(self):
         return (self.nrings, self.nphi, self.kmax + 1)

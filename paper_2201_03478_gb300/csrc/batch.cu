@@ -259,7 +259,7 @@ sl_status sl_batch_create(sl_batch **out, const sl_batch_item *items, int nitems
     for (int i = 0; i < nitems && st == SL_OK; ++i) st = sl_plan_reserve(b->items[i].plan, b->items[i].n);
     for (int i = 0; i < nitems && st == SL_OK; ++i) {   // flop estimate (FP64 at 1/64 of the FP32 rate)
         const sl_plan *p = b->items[i].plan;
-        const double w = p->precision == SL_FP64 ? 64.0 : 1.0;
+        const double w = p->precision == SL_FP64 ? 64.0 : (p->precision == SL_DF64 ? 12.0 : 1.0);
         b->cost[i] = w * (11.0 * (double)p->lsteps + 4.0 * 16.0 * (p->K + 1) * (double)b->items[i].n);
     }
     if (st == SL_OK && (flags & SL_BATCH_AUTOTUNE)) {

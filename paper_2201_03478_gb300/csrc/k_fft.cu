@@ -197,7 +197,7 @@ static Radices radices_of(const sl_plan *p) {
 sl_status launch_ringfft_synth(sl_plan *p, void *maps) {
     const unsigned nblk = (unsigned)((p->K + 1) * p->R);
     int slot;
-    if (p->precision == SL_FP64) {
+    if (plan_wide(p->precision)) {
         const size_t sm = 2 * (size_t)p->nphi * sizeof(double2);
         cudaFuncSetAttribute(k_ringfft_synth<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         slot = timing_begin(p, "ringfft_f64");

@@ -24,7 +24,7 @@
 
 namespace sl {
 
-constexpr int kChunkA = 2048;   // must equal kChunk in k_sort.cu
+constexpr int kChunkA = kWorkChunk;
 
 // 4-point Lagrange weights: theta rows from the record, phi nodes -1, 0, 1, 2.
 __device__ __forceinline__ void weights64(const InterpGeom &g, int i, double d0, double f, double wt[4],
@@ -134,15 +134,6 @@ struct TiledArgs {
     int ntiles, ncell;
     double *tod;
 };
-
-__device__ __forceinline__ int find_tile(const unsigned *chunk_off, int ntiles, unsigned v) {
-    int lo = 0, hi = ntiles - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (chunk_off[mid] <= v) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
 
 template <int TC>
 __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
@@ -383,6 +374,7 @@ static unsigned grid_for(int64_t n, int bs) {
 sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *maps, const double *psi, int64_t n,
                         double *tod) {
     int slot;
+    if (p->precision == SL_DF64) return launch_interp_df(p, b, fine, maps, psi, n, tod);
     if (p->precision == SL_FP64) {
         slot = timing_begin(p, "interp_f64");
         k_interp_f64<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const double2 *)maps,

@@ -329,7 +329,7 @@ sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
     a.ncomp = p->ncomp;
     a.R = p->R;
     a.npairs = p->npairs;
-    a.ppt = (p->precision == SL_FP64) ? 1 : 2;
+    a.ppt = plan_wide(p->precision) ? 1 : 2;
     a.nchunk = (p->npairs + a.ppt * kHalf - 1) / (a.ppt * kHalf);
     a.nalm = p->nalm;
     a.sky = (const double2 *)sky;
@@ -347,7 +347,7 @@ sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
     const int64_t nblk = (int64_t)(p->L + 1) * (p->K + 1) * a.nchunk;
     if (nblk > 0x7fffffff) return set_error(SL_ERR_UNSUPPORTED, "grid too large");
     int slot;
-    if (p->precision == SL_FP64) {
+    if (plan_wide(p->precision)) {
         slot = timing_begin(p, "lcontract_f64");
         k_lcontract_f64<<<(unsigned)nblk, kNT, 0, p->stream>>>(a);
     } else {

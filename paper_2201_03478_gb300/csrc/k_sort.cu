@@ -18,7 +18,7 @@
 
 namespace sl {
 
-constexpr int kChunk = 2048;        // adjoint work item: at most this many samples of one tile
+constexpr int kChunk = kWorkChunk;
 constexpr int kScanBlock = 4096;    // keys per CTA of k_scan_local (1024 threads x 4)
 
 template <bool REC64>

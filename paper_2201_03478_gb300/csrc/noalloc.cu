@@ -82,8 +82,8 @@ extern "C" sl_status interp_tod_noalloc(sl_plan *p, const void *maps, const doub
     b.hist = b.perm + kNoAllocMaxSamples;                  // cleared by the sort before use
     b.cursor = b.hist + (kNoAllocMaxTiles + 1);
     b.bsum = b.cursor + kNoAllocMaxTiles;
-    const int rec64 = p->precision == SL_FP64;
-    b.chunk_off = rec64 ? nullptr : b.bsum + kBsumWords;  // FP32 plans: tile work items
+    const int rec64 = plan_wide(p->precision);
+    b.chunk_off = p->precision == SL_FP64 ? nullptr : b.bsum + kBsumWords;  // tile-staged kernels: work items
     if ((st = launch_sort_into(p, b, theta, phi, psi, n, 0, rec64, !rec64)) != SL_OK) return st;
     return launch_interp(p, b, 0, maps, psi, n, tod);
 }

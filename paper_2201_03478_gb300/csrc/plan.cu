@@ -157,7 +157,7 @@ static sl_status ensure_adjoint_scratch(sl_plan *p) {
         if (st != SL_OK) return st;
     }
     if (!p->d_Gadj) {
-        if (p->precision == SL_FP64) {
+        if (plan_wide(p->precision)) {
             p->d_Gadj = (double2 *)p->d_G;
         } else {
             st = dalloc_t(p, &p->d_Gadj, (size_t)(p->K + 1) * p->R * (2 * p->L + 1), "adjoint G");
@@ -166,7 +166,7 @@ static sl_status ensure_adjoint_scratch(sl_plan *p) {
     }
     // the adjoint contraction runs in FP64: FP32 plans build the FP64 table and
     // start states (threshold 2^-64) on first use
-    if (p->precision == SL_FP64) {
+    if (plan_wide(p->precision)) {
         p->d_ls_adj = p->d_ls;
         p->d_st64_adj = p->d_st64;
     } else if (!p->d_st64_adj) {
@@ -217,7 +217,7 @@ static sl_status validate(const sl_plan_desc *d, int *rad, int *nrad) {
         return set_error(SL_ERR_ARG, "nphi=%d must be even and in [8, %d]", d->nphi, kMaxNphi);
     if (!factor_235(d->nphi, rad, nrad))
         return set_error(SL_ERR_UNSUPPORTED, "nphi=%d has a prime factor > 5", d->nphi);
-    if (d->precision != SL_FP64 && d->precision != SL_FP32)
+    if (d->precision != SL_FP64 && d->precision != SL_FP32 && d->precision != SL_DF64)
         return set_error(SL_ERR_ARG, "precision=%d unknown", d->precision);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -270,6 +270,7 @@ void plan_destroy(sl_plan *p) {
     dfree(p->d_Abar);
     dfree(p->d_offs64);
     dfree(p->d_rowtab32);
+    dfree(p->d_rowtab_df);
     dfree(p->sort.hist);
     dfree(p->sort.cursor);
     dfree(p->sort.bsum);
@@ -332,6 +333,11 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     // same offsets followed by wden in float
     std::vector<double> offs64((size_t)(R + 1) * 4);
     std::vector<float> rowtab32((size_t)(R + 1) * 8);
+    std::vector<float2> rowtab_df((size_t)(R + 1) * 8);
+    auto split = [](long double v) {
+        const float h = (float)v;
+        return make_float2(h, (float)(v - (long double)h));
+    };
     for (int i = -1; i <= R - 1; ++i) {
         const double t0 = ring_ext[i - 1 + half];
         for (int a = 0; a < 4; ++a) {
@@ -339,6 +345,8 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
             offs64[(size_t)(i + 1) * 4 + a] = o;
             rowtab32[(size_t)(i + 1) * 8 + a] = (float)o;
             rowtab32[(size_t)(i + 1) * 8 + 4 + a] = (float)wden[(size_t)(i + 1) * P + a];
+            rowtab_df[(size_t)(i + 1) * 8 + a] = split(o);
+            rowtab_df[(size_t)(i + 1) * 8 + 4 + a] = split(wden[(size_t)(i + 1) * P + a]);
         }
     }
     for (int r = 0; r < p->npairs; ++r) {
@@ -421,6 +429,9 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     TRY(cuda_check(cudaMemcpy(d_cs, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
     TRY(dalloc_t(p, &p->d_offs64, offs64.size(), "row offsets"));
     TRY(dalloc_t(p, &p->d_rowtab32, rowtab32.size(), "row table"));
+    TRY(dalloc_t(p, &p->d_rowtab_df, rowtab_df.size(), "row table"));
+    TRY(cuda_check(cudaMemcpy(p->d_rowtab_df, rowtab_df.data(), rowtab_df.size() * sizeof(float2),
+                              cudaMemcpyHostToDevice), "upload"));
     TRY(cuda_check(cudaMemcpy(p->d_offs64, offs64.data(), offs64.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
     TRY(cuda_check(cudaMemcpy(p->d_rowtab32, rowtab32.data(), rowtab32.size() * sizeof(float), cudaMemcpyHostToDevice), "upload"));
     p->geom.ring_ext = p->d_ring_ext;
@@ -429,6 +440,7 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     p->geom.lut = p->d_lut;
     p->geom.offs64 = p->d_offs64;
     p->geom.rowtab32 = p->d_rowtab32;
+    p->geom.rowtab_df = p->d_rowtab_df;
 
     {
         size_t nseed = (size_t)(K + 1) * (L + 1) * p->npairs;
@@ -448,10 +460,10 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     {
         const size_t nst = (size_t)(K + 1) * (L + 1) * 2 * p->npairs;
         TRY(dalloc_t(p, &p->d_ls, nst, "start l"));
-        if (p->precision == SL_FP64) TRY(dalloc_t(p, &p->d_st64, nst, "start states"));
+        if (plan_wide(p->precision)) TRY(dalloc_t(p, &p->d_st64, nst, "start states"));
         else TRY(dalloc_t(p, &p->d_st32, nst, "start states"));
     }
-    TRY(launch_advance(p, p->precision == SL_FP64 ? 0x1p-64 : 0x1p-30, p->d_ls, p->d_st64, p->d_st32));
+    TRY(launch_advance(p, plan_wide(p->precision) ? 0x1p-64 : 0x1p-30, p->d_ls, p->d_st64, p->d_st32));
     TRY(count_lsteps(p, &p->lsteps));
     if (p->precision == SL_FP32) {
         TRY(cuda_check(cudaStreamSynchronize(p->stream), "plan advance"));
@@ -461,7 +473,7 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     }
     {
         size_t gel = (size_t)(K + 1) * R * (2 * L + 1);
-        p->G_bytes = gel * (p->precision == SL_FP64 ? sizeof(double2) : sizeof(float2));
+        p->G_bytes = gel * (plan_wide(p->precision) ? sizeof(double2) : sizeof(float2));
         TRY(dalloc(p, &p->d_G, p->G_bytes, "spin-Legendre scratch G"));
     }
     TRY(alloc_sort_tables(p));
@@ -516,11 +528,12 @@ sl_status interp_tod(sl_plan *p, const void *maps, const double *theta, const do
     if (!maps) return set_error(SL_ERR_ARG, "interp_tod: maps is NULL");
     if (n == 0) return SL_OK;
     if ((st = ensure_sort_capacity(p, n)) != SL_OK) return st;
-    const int rec64 = p->precision == SL_FP64;
-    // FP32 plans interpolate tile by tile from shared memory (needs the work items)
+    const int rec64 = plan_wide(p->precision);
+    // FP32 and DF64 plans interpolate tile by tile from shared memory (needs the work items)
     SortBufs b = p->sort;
-    if (rec64) b.chunk_off = nullptr;
-    if ((st = launch_sort_into(p, b, theta, phi, psi, n, 1, rec64, !rec64)) != SL_OK) return st;
+    const int chunks = p->precision != SL_FP64;
+    if (!chunks) b.chunk_off = nullptr;
+    if ((st = launch_sort_into(p, b, theta, phi, psi, n, 1, rec64, chunks)) != SL_OK) return st;
     return launch_interp(p, b, 1, maps, psi, n, tod);
 }
 
@@ -567,7 +580,7 @@ sl_status sl_plan_get_sizes(const sl_plan *p, sl_plan_sizes *o) {
     o->nalm = p->nalm;
     o->sky_doubles = (int64_t)p->ncomp * p->nalm * 2;
     o->beam_doubles = (int64_t)p->ncomp * (p->K + 1) * (p->L + 1) * 2;
-    o->maps_bytes = (int64_t)p->R * p->nphi * (p->K + 1) * (p->precision == SL_FP64 ? 16 : 8);
+    o->maps_bytes = (int64_t)p->R * p->nphi * (p->K + 1) * (plan_wide(p->precision) ? 16 : 8);
     o->scratch_bytes = p->bytes_held;
     o->lsteps = p->lsteps;
     o->tile_cols = p->geom.tile_cols;
@@ -589,7 +602,8 @@ sl_status sl_plan_set_tile_cols(sl_plan *p, int tc) {
     if (tc == p->geom.tile_cols) return SL_OK;
     int dev_smem = 0;
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
-    const size_t need = std::max(interp_f32_tiled_smem_tc(p, tc), interp_adjoint_smem_tc(p, tc));
+    const size_t need = std::max(std::max(interp_f32_tiled_smem_tc(p, tc), interp_adjoint_smem_tc(p, tc)),
+                                 p->precision == SL_DF64 ? interp_df_tiled_smem_tc(p, tc) : (size_t)0);
     if (dev_smem > 0 && need > (size_t)dev_smem)
         return set_error(SL_ERR_UNSUPPORTED, "tile width %d needs %zu bytes of shared memory (device: %d)", tc,
                          need, dev_smem);

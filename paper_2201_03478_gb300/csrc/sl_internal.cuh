@@ -30,6 +30,11 @@ constexpr float kScaleThr32 = 0x1p32f;
 // Sort tiles: cells (base row i in [-1, R-1], base column j) grouped into
 // tiles of kTileRows x tile_cols cells.
 constexpr int kTileRows = 4;
+// Work item of the tile-staged kernels: at most this many sorted samples of one tile.
+constexpr int kWorkChunk = 2048;
+
+// SL_FP64 and SL_DF64 plans share every FP64 layout (G, cube, records, tables).
+inline bool plan_wide(int precision) { return precision != SL_FP32; }
 
 // ---------------------------------------------------------------- geometry
 // Everything the interpolation kernels need, passed by value.
@@ -47,7 +52,18 @@ struct InterpGeom {
     int tile_cols, ntr, ntc;      // tile grid: ntr = ceil((R+1)/kTileRows), ntc = ceil(nphi/tile_cols)
     const double *offs64;         // [(R+1) * 4]: theta(i-1+a) - theta(i-1) per base row i
     const float *rowtab32;        // [(R+1) * 8]: the same offsets, then wden, in float
+    const float2 *rowtab_df;      // [(R+1) * 8]: the same, as double-float (hi, lo)
 };
+
+// Work item v -> its tile: the last t with chunk_off[t] <= v.
+__device__ __forceinline__ int find_tile(const unsigned *chunk_off, int ntiles, unsigned v) {
+    int lo = 0, hi = ntiles - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (chunk_off[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 // Per-sample stencil record written by the binning kernel: the colatitude
 // offset from the stencil's first row, the phi fraction in [0, 1), and the
@@ -105,6 +121,7 @@ struct sl_plan {
     double *d_wden = nullptr;
     double *d_offs64 = nullptr;
     float *d_rowtab32 = nullptr;
+    float2 *d_rowtab_df = nullptr;
     int *d_lut = nullptr;
     int nlut = 0;
     sl::InterpGeom geom;
@@ -189,6 +206,11 @@ size_t interp_f32_tiled_smem(const sl_plan *p);
 // Dynamic shared memory of the two tile-staged kernels for tile width tc.
 size_t interp_f32_tiled_smem_tc(const sl_plan *p, int tc);
 size_t interp_adjoint_smem_tc(const sl_plan *p, int tc);
+// Double-float interpolation (SL_DF64 plans; k_interp_df.cu), over a sort made
+// with rec64 = 1 and with_chunks = 1.
+sl_status launch_interp_df(sl_plan *p, const SortBufs &b, int fine, const void *maps, const double *psi, int64_t n,
+                           double *tod);
+size_t interp_df_tiled_smem_tc(const sl_plan *p, int tc);
 // Adjoint scatter over a sort made with rec64 = 1, with_chunks = 1.
 sl_status launch_interp_adjoint(sl_plan *p, const SortBufs &b, int fine, const double *psi, const double *tod,
                                 int64_t n, double2 *fbar);

@@ -19,7 +19,7 @@ def lfi(oracle_lib):
     cfg = W.config_lfi(n=100_000_000)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     out = {"cfg": cfg}
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "df64"):
         plan = sl.sidelobe_plan_create(cfg["lmax"], cfg["kmax"], cfg["ring_theta"], cfg["nphi"], ncomp=3,
                                        precision=prec)
         maps = sl.synth_spin_maps(plan, dev(cfg["sky"]), dev(cfg["beam"]))
@@ -41,7 +41,7 @@ def test_fullsize_cube_rings(lfi, oracle_lib):
     rt = cfg["ring_theta"]
     G = oracle_lib.cube_G(cfg["sky"], cfg["beam"], rt[RINGS])
     ref = oracle_lib.cube_from_G(G, cfg["nphi"])            # [len(RINGS), nphi, K+1]
-    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5)):
+    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5), ("df64", 1e-10)):
         got = lfi[prec][0][RINGS].astype(np.complex128)
         err = rel_l2(got, ref)
         print("full-size cube rings %s rel L2 %.2e" % (prec, err))
@@ -68,7 +68,7 @@ def test_fullsize_tod_samples(lfi, oracle_lib):
     cube = np.zeros((R, nphi, cfg["kmax"] + 1), dtype=np.complex128)
     cube[rows] = part
     ref = oracle_lib.interp(cube, rt, th, ph, ps)
-    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5)):
+    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5), ("df64", 1e-10)):
         got = lfi[prec][1][idx]
         err = rel_l2(got, ref)
         print("full-size TOD samples %s rel L2 %.2e" % (prec, err))
@@ -78,4 +78,9 @@ def test_fullsize_tod_samples(lfi, oracle_lib):
     assert np.isfinite(t64).all() and np.isfinite(t32).all()
     err = rel_l2(t32, t64)
     print("full-size TOD fp32 vs fp64 rel L2 %.2e" % err)
+    td = lfi["df64"][1]
+    assert np.isfinite(td).all()
+    err_d = rel_l2(td, t64)
+    print("full-size TOD df64 vs fp64 rel L2 %.2e" % err_d)
+    assert err_d < 1e-10
     assert err < 1e-5

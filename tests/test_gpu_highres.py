@@ -25,7 +25,7 @@ def highres():
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     out = {"cfg": cfg}
     th, ph, ps = dev(cfg["theta"]), dev(cfg["phi"]), dev(cfg["psi"])
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "df64"):
         plan = sl.sidelobe_plan_create(cfg["lmax"], cfg["kmax"], cfg["ring_theta"], cfg["nphi"], ncomp=1,
                                        precision=prec)
         maps = sl.synth_spin_maps(plan, dev(cfg["sky"]), dev(cfg["beam"]))
@@ -61,7 +61,7 @@ def test_highres_precision_modes_vs_oracle(highres, oracle_lib):
     rt, nphi = cfg["ring_theta"], cfg["nphi"]
     subsets = _band_subset(cfg)
     assert sum(s.size for s in subsets) >= 900_000
-    refs, got = [], {"fp64": [], "fp32": []}
+    refs, got = [], {"fp64": [], "fp32": [], "df64": []}
     for (a, b), idx in zip(BANDS, subsets):
         band = rt[a:b + 1]
         cube = oracle_lib.cube_from_G(oracle_lib.cube_G(cfg["sky"], cfg["beam"], band), nphi)
@@ -69,7 +69,7 @@ def test_highres_precision_modes_vs_oracle(highres, oracle_lib):
         for prec in got:
             got[prec].append(highres[prec][idx])
     ref = np.concatenate(refs)
-    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5)):
+    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5), ("df64", 1e-10)):
         g = np.concatenate(got[prec])
         err = rel_l2(g, ref)
         print("lmax=2048 kmax=32: %s TOD on %d-sample subset, rel L2 vs oracle %.2e, max|err|/rms %.2e"

@@ -4,6 +4,7 @@ element by element on seeded inputs.
 Tolerances (relative L2 over the whole output, spec targets):
   FP64 plans: 1e-10 (oracle and kernels take different but equally exact
               routes: recurrence arrangement, FFT vs explicit DFT, sum order);
+  DF64 plans (double-float contraction and interpolation): the FP64 target, 1e-10;
   FP32 plans: 1e-5, with the measured error printed.
 """
 import math
@@ -120,6 +121,26 @@ def test_tod_fp32(sl, case):
     assert err_c < TOL32 and err < TOL32
 
 
+def test_cube_and_tod_df64(sl, case):
+    plan = _plan(sl, case, "df64")
+    maps = sl.synth_spin_maps(plan, _dev(case["sky"]), _dev(case["beam"]))
+    assert maps.dtype == torch.complex128
+    err_c = rel_l2(maps.cpu().numpy(), case["cube"])
+    tod = sl.interp_tod(plan, maps, _dev(case["th"]), _dev(case["ph"]), _dev(case["ps"]))
+    err = rel_l2(tod.cpu().numpy(), case["tod"])
+    print(case["name"], "df64: cube rel L2 %.2e, tod rel L2 %.2e" % (err_c, err))
+    assert err_c < TOL64 and err < TOL64
+
+
+def test_interp_df64_same_cube(sl, case):
+    """Double-float interpolation alone, reading the oracle's cube."""
+    plan = _plan(sl, case, "df64")
+    tod = sl.interp_tod(plan, _dev(case["cube"]), _dev(case["th"]), _dev(case["ph"]), _dev(case["ps"]))
+    err = rel_l2(tod.cpu().numpy(), case["tod"])
+    print(case["name"], "interp df64 rel L2", err)
+    assert err < 1e-12
+
+
 def test_adjoint_interp_fp64(sl, case, oracle_lib):
     plan = _plan(sl, case)
     rng = np.random.default_rng(21)
@@ -183,6 +204,35 @@ def test_pointing_edge_cases(sl, oracle_lib):
     e = torch.empty(0, dtype=torch.float64, device="cuda")
     out = sl.interp_tod(plan, _dev(cube), e, e, e)
     assert out.numel() == 0
+
+
+def test_pointing_edge_cases_df64(sl, oracle_lib):
+    """The double-float interpolation at the poles (ghost rows), on ring
+    colatitudes, with phi outside [0, 2 pi) and large psi."""
+    c = CASES["small_healpix"]()
+    rt = c["rt"]
+    th = np.array([0.0, math.pi, rt[0], rt[-1], rt[63], 1e-300, math.pi - 1e-15, 0.5 * rt[0], 1.0, 2.0])
+    ph = np.array([0.0, 2 * math.pi, -0.3, 7.5, 1e-17, 100.0, -100.0, 3.0, 2 * math.pi - 1e-16, 0.25])
+    ps = np.array([0.0, -1.0, 50.0, 1e3, 3.14, -7.0, 0.5, 2.0, 1.0, 6.2])
+    cube = oracle_lib.cube(c["sky"], c["beam"], rt, 128)
+    ref = oracle_lib.interp(cube, rt, th, ph, ps)
+    plan = _plan(sl, c, "df64")
+    got = sl.interp_tod(plan, _dev(cube), _dev(th), _dev(ph), _dev(ps)).cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_df64_adjoint_is_the_fp64_adjoint(sl):
+    """DF64 plans share the FP64 plans' tables and run the FP64 adjoint (equal up
+    to the order of the atomic additions into the adjoint cube)."""
+    c = CASES["small_healpix"]()
+    y = _dev(np.random.default_rng(4).standard_normal(c["th"].size))
+    outs = []
+    for prec in ("fp64", "df64"):
+        plan = _plan(sl, c, prec)
+        gs, gb = sl.adjoint_tod(plan, _dev(c["th"]), _dev(c["ph"]), _dev(c["ps"]), y, _dev(c["sky"]),
+                                _dev(c["beam"]))
+        outs.append((gs.cpu().numpy(), gb.cpu().numpy()))
+    assert rel_l2(outs[1][0], outs[0][0]) < 1e-13 and rel_l2(outs[1][1], outs[0][1]) < 1e-13
 
 
 def test_tod_from_host_pipeline(sl):
