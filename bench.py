@@ -140,6 +140,12 @@ DTYPE = {"fp64": "f64", "fp32": "f32 (FP64 seeds/coords/final sum)",
 PEAK_FP32_TINST = 152 * 128 * 2.07e9 / 1e12          # FP32-pipe instructions per second (x 1e12)
 
 
+# FP32 instructions per recurrence step of the double-float contraction
+# (k_lcontract.cu): four double-float multiply-accumulates (12 each), the
+# double-float a' x -+ b' (product 7 + sum 11) and the step (product 7 + sum 11).
+DF_LC_INST_PER_STEP = 4 * 12 + 7 + 11 + 7 + 11
+
+
 def df_interp_inst(K, p=4):
     """FP32 instructions the double-float interpolation executes per sample
     (counted from k_interp_df.cu): a double-float multiply-accumulate is 12
@@ -244,8 +250,10 @@ def gpu_arm(args):
     prec = args.precision
     suffix = {"fp64": "f64", "fp32": "f32", "df64": "df"}[prec]
     roofs = {}
-    lc_name = "lcontract_f64" if prec == "df64" else "lcontract_" + suffix
-    kernels = [(lc_name, fl_lc, PEAK_FP64_TFLOPS if prec != "fp32" else PEAK_FP32_TFLOPS, "TFLOP/s"),
+    lc_name = "lcontract_" + suffix
+    kernels = [(lc_name, fl_lc if prec != "df64" else DF_LC_INST_PER_STEP * float(plan.sizes()["lsteps"]),
+                {"fp64": PEAK_FP64_TFLOPS, "fp32": PEAK_FP32_TFLOPS, "df64": PEAK_FP32_TINST}[prec],
+                "Tinst/s" if prec == "df64" else "TFLOP/s"),
                ("interp_" + suffix, fl_in if prec != "df64" else float(n) * df_interp_inst(K),
                 PEAK_FP32_TINST if prec == "df64" else (PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS),
                 "Tinst/s" if prec == "df64" else "TFLOP/s")]

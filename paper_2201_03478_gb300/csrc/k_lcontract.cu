@@ -33,10 +33,15 @@
 // with y = 1 - cos(theta) and c' = a' -+ b' - 2 formed in double (keeps the
 // FP32 recurrence accurate near the pole, where cos theta alone carries too
 // few bits); sky x beam products from FP32 copies of sky and beam.
+// DF64 plans: the FP64 plan's layout and start states, with the recurrence
+// and the sums in double-float arithmetic (df.cuh): per l, two double-float
+// products and two sums for the recurrence and four double-float
+// multiply-accumulates, all on the FP32 pipes.
 // The CTA stages the coefficients of a chunk of l in shared memory (double
 // buffered in FP32); a thread steps only from its own start l.
 #include <algorithm>
 
+#include "df.cuh"
 #include "sl_internal.cuh"
 
 namespace sl {
@@ -317,6 +322,97 @@ __global__ void __launch_bounds__(kNT) k_lcontract_f32(const LcArgs a) {
     if (p0 + 1 < a.npairs) write_two<float2>(a, m, k, p0 + 1, neg, B.acc1, B.acc2);
 }
 
+// ------------------------------------------------------------------ DF64
+// Per l, staged: a' and b' as double-float, then (ap, sam, am, sap), each
+// complex as (Re hi, Re lo, Im hi, Im lo).
+struct __align__(16) CoefDF {
+    float4 ab;
+    float4 c[4];
+};
+
+__device__ __forceinline__ float4 df4(double2 v) {
+    const dfl re = df_from_d(v.x), im = df_from_d(v.y);
+    return make_float4(re.h, re.l, im.h, im.l);
+}
+
+__global__ void __launch_bounds__(kNT) k_lcontract_df(const LcArgs a) {
+    __shared__ CoefDF cf[kLC64];
+    int m, k, pc;
+    block_mk(a, m, k, pc);
+    const int neg = threadIdx.x >= kHalf;
+    const int pair = pc * kHalf + (threadIdx.x & (kHalf - 1));
+    const bool active = pair < a.npairs;
+    const int64_t moff = (int64_t)m * (2 * a.L + 1 - m) / 2;
+    const RTab64 *tab = a.tab64 + (int64_t)k * a.nalm + moff;
+
+    dfl x = {0.f, 0.f}, y = {0.f, 0.f}, yo = {0.f, 0.f};
+    int ls = a.L + 1;
+    if (active) {
+        const int64_t si = start_index(a, k, m, neg, pair);
+        ls = a.ls[si];
+        const double2 s = a.st64[si];
+        yo = df_from_d(s.x);
+        y = df_from_d(s.y);
+        x = df_from_d(a.xr[pair]);
+    }
+    dacc a1r, a1i, a2r, a2i;
+    dacc_zero(a1r);
+    dacc_zero(a1i);
+    dacc_zero(a2r);
+    dacc_zero(a2i);
+    const int lstart = block_min(ls);
+    const int cofs = neg ? 2 : 0;      // (ap, sam) for +k, (am, sap) for -k
+    const float bsg = neg ? 1.f : -1.f;  // -b' for +k, +b' for -k
+    for (int c0 = lstart; c0 <= a.L; c0 += kLC64) {
+        const int nc = min(kLC64, a.L - c0 + 1);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nc; i += kNT) {
+            const int l = c0 + i;
+            const RTab64 t = tab[l];
+            double2 ap = {0.0, 0.0}, am = {0.0, 0.0};
+            for (int X = 0; X < a.ncomp; ++X) {
+                double2 s = a.sky[X * a.nalm + moff + l];
+                if (m == 0) s.y = 0.0;
+                double2 b = a.beam[((int64_t)X * (a.K + 1) + k) * (a.L + 1) + l];
+                if (k == 0) b.y = 0.0;
+                ap.x += s.x * b.x + s.y * b.y;      // s conj(b)
+                ap.y += s.y * b.x - s.x * b.y;
+                am.x += s.x * b.x - s.y * b.y;      // conj(s) conj(b)
+                am.y -= s.y * b.x + s.x * b.y;
+            }
+            const double c = t.c, sc = (l & 1) ? -c : c;
+            const dfl ra = df_from_d(t.a), rb = df_from_d(t.b);
+            CoefDF v;
+            v.ab = make_float4(ra.h, ra.l, rb.h, rb.l);
+            v.c[0] = df4(make_double2(c * ap.x, c * ap.y));
+            v.c[1] = df4(make_double2(sc * am.x, sc * am.y));
+            v.c[2] = df4(make_double2(c * am.x, c * am.y));
+            v.c[3] = df4(make_double2(sc * ap.x, sc * ap.y));
+            cf[i] = v;
+        }
+        __syncthreads();
+        const int i0 = max(0, ls - c0);
+#pragma unroll 2
+        for (int i = i0; i < nc; ++i) {
+            const float4 ab = cf[i].ab, c1 = cf[i].c[cofs], c2 = cf[i].c[cofs + 1];
+            dacc_mac(a1r, dfl{c1.x, c1.y}, y);
+            dacc_mac(a1i, dfl{c1.z, c1.w}, y);
+            dacc_mac(a2r, dfl{c2.x, c2.y}, y);
+            dacc_mac(a2i, dfl{c2.z, c2.w}, y);
+            // y_{l+1} = (a' x -+ b') y_l - y_{l-1}
+            const dfl tt = df_add(df_mul(dfl{ab.x, ab.y}, x), dfl{bsg * ab.z, bsg * ab.w});
+            const dfl yn = df_sub(df_mul(tt, y), yo);
+            yo = y;
+            y = yn;
+        }
+    }
+    if (active) {
+        const double2 acc1 = make_double2(df_to_d(dacc_get(a1r)), df_to_d(dacc_get(a1i)));
+        const double2 acc2 = make_double2(df_to_d(dacc_get(a2r)), df_to_d(dacc_get(a2i)));
+        write_two<double2>(a, m, k, pair, neg, acc1, acc2);
+    }
+}
+
 __global__ void k_to_f32(const double2 *__restrict__ in, float2 *__restrict__ out, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = make_float2((float)in[i].x, (float)in[i].y);
@@ -347,7 +443,10 @@ sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
     const int64_t nblk = (int64_t)(p->L + 1) * (p->K + 1) * a.nchunk;
     if (nblk > 0x7fffffff) return set_error(SL_ERR_UNSUPPORTED, "grid too large");
     int slot;
-    if (plan_wide(p->precision)) {
+    if (p->precision == SL_DF64) {
+        slot = timing_begin(p, "lcontract_df");
+        k_lcontract_df<<<(unsigned)nblk, kNT, 0, p->stream>>>(a);
+    } else if (p->precision == SL_FP64) {
         slot = timing_begin(p, "lcontract_f64");
         k_lcontract_f64<<<(unsigned)nblk, kNT, 0, p->stream>>>(a);
     } else {
