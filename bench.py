@@ -350,8 +350,9 @@ def gpu_arm(args):
         torch.cuda.synchronize()
         ms2 = e0.elapsed_time(e1) / args.steps
         err = float(torch.linalg.vector_norm(tod2 - tod) / torch.linalg.vector_norm(tod))
-        out["other_precisions"].append({"precision": other, "value": n / (ms2 / 1e3), "unit": "samples/s",
-                                        "ms_per_step": ms2, "tod_rel_l2_vs_%s" % prec: err})
+        out["other_precisions"].append({"precision": other, "dtype": DTYPE[other], "value": n / (ms2 / 1e3),
+                                        "unit": "samples/s", "ms_per_step": ms2,
+                                        "rate_vs_%s" % prec: ms_step / ms2, "tod_rel_l2_vs_%s" % prec: err})
         del maps2, tod2, p2
 
     # ---- end to end through the public API from pinned host buffers
