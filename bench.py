@@ -141,18 +141,19 @@ PEAK_FP32_TINST = 152 * 128 * 2.07e9 / 1e12          # FP32-pipe instructions pe
 
 
 # FP32 instructions per recurrence step of the double-float contraction
-# (k_lcontract.cu): four double-float multiply-accumulates (12 each), the
-# double-float a' x -+ b' (product 7 + sum 11) and the step (product 7 + sum 11).
-DF_LC_INST_PER_STEP = 4 * 12 + 7 + 11 + 7 + 11
+# (k_lcontract.cu): four double-float multiply-accumulates (12 each) and two
+# fused double-float a b + c (15 each: a' x -+ b', then t y_l - y_{l-1}).
+DF_LC_INST_PER_STEP = 4 * 12 + 2 * 15
 
 
 def df_interp_inst(K, p=4):
     """FP32 instructions the double-float interpolation executes per sample
     (counted from k_interp_df.cu): a double-float multiply-accumulate is 12
     instructions (product with its FMA error terms, two_sum, two adds); per
-    k >= 1 there are 2 p^2 of them, 2 for the phase and a double-float
-    Chebyshev step for cos and sin (36); k = 0 has p^2; the weights take ~320."""
-    return 12 * p * p + K * (12 * 2 * p * p + 6 + 24 + 36) + 320
+    k >= 1 there are 2 p^2 of them, 2 for the phase, two normalisations (6)
+    and a fused double-float Chebyshev step for cos and sin (2 x 15); k = 0
+    has p^2; the weights take ~320."""
+    return 12 * p * p + K * (12 * 2 * p * p + 6 + 24 + 30) + 320
 
 
 def algorithmic_flops(L, K, R, n, p=4):

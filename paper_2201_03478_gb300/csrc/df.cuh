@@ -61,8 +61,20 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
     return r;
 }
 
-// a b + c
-__device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) { return df_add(df_mul(a, b), c); }
+// a b + c with one normalisation: the product's high part and c's high part
+// meet in two_sum, every term of order 2^-24 relative goes to the low part.
+__device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    float s, e2;
+    two_sum(p, c.h, s, e2);
+    e = __fadd_rn(e, __fadd_rn(e2, c.l));
+    dfl r;
+    fast_two_sum(s, e, r.h, r.l);
+    return r;
+}
 
 // Accumulator for long sums of products: the high parts are summed with
 // two_sum (exact), everything of order 2^-24 relative goes to lo; normalise

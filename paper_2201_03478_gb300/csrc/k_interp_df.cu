@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) k_interp_df_tiled(const DfArgs A) {
                 }
                 dacc_mac(acc, Ck, dacc_get(sr));
                 dacc_mac(acc, df_neg(Sk), dacc_get(si));
-                const dfl cn = df_sub(df_mul(c1, Ck), Ckm), sn = df_sub(df_mul(c1, Sk), Skm);
+                const dfl cn = df_fma(c1, Ck, df_neg(Ckm)), sn = df_fma(c1, Sk, df_neg(Skm));
                 Ckm = Ck;
                 Skm = Sk;
                 Ck = cn;

@@ -335,33 +335,65 @@ __device__ __forceinline__ float4 df4(double2 v) {
     return make_float4(re.h, re.l, im.h, im.l);
 }
 
+// One recurrence (ring pair, sign) of the double-float kernel.
+struct RecDF {
+    dfl x, y, yo;
+    dacc a1r, a1i, a2r, a2i;
+    int ls;
+};
+
+__device__ __forceinline__ void rec_df_start(const LcArgs &a, int k, int m, int neg, int pair, RecDF &r) {
+    r.x = r.y = r.yo = dfl{0.f, 0.f};
+    dacc_zero(r.a1r);
+    dacc_zero(r.a1i);
+    dacc_zero(r.a2r);
+    dacc_zero(r.a2i);
+    r.ls = a.L + 1;
+    if (pair < a.npairs) {
+        const int64_t si = start_index(a, k, m, neg, pair);
+        r.ls = a.ls[si];
+        const double2 s = a.st64[si];
+        r.yo = df_from_d(s.x);
+        r.y = df_from_d(s.y);
+        r.x = df_from_d(a.xr[pair]);
+    }
+}
+
+// accumulate with y_l, then y_{l+1} = (a' x -+ b') y_l - y_{l-1}
+__device__ __forceinline__ void rec_df_step(RecDF &r, dfl ra, dfl rb, float4 c1, float4 c2) {
+    dacc_mac(r.a1r, dfl{c1.x, c1.y}, r.y);
+    dacc_mac(r.a1i, dfl{c1.z, c1.w}, r.y);
+    dacc_mac(r.a2r, dfl{c2.x, c2.y}, r.y);
+    dacc_mac(r.a2i, dfl{c2.z, c2.w}, r.y);
+    const dfl t = df_fma(ra, r.x, rb);
+    const dfl yn = df_fma(t, r.y, df_neg(r.yo));
+    r.yo = r.y;
+    r.y = yn;
+}
+
+__device__ __forceinline__ void rec_df_write(const LcArgs &a, int m, int k, int pair, int neg, const RecDF &r) {
+    if (pair >= a.npairs) return;
+    const double2 acc1 = make_double2(df_to_d(dacc_get(r.a1r)), df_to_d(dacc_get(r.a1i)));
+    const double2 acc2 = make_double2(df_to_d(dacc_get(r.a2r)), df_to_d(dacc_get(r.a2i)));
+    write_two<double2>(a, m, k, pair, neg, acc1, acc2);
+}
+
+// Two adjacent ring pairs per thread (they share every coefficient load).
 __global__ void __launch_bounds__(kNT) k_lcontract_df(const LcArgs a) {
     __shared__ CoefDF cf[kLC64];
     int m, k, pc;
     block_mk(a, m, k, pc);
     const int neg = threadIdx.x >= kHalf;
-    const int pair = pc * kHalf + (threadIdx.x & (kHalf - 1));
-    const bool active = pair < a.npairs;
+    const int p0 = pc * (2 * kHalf) + 2 * (threadIdx.x & (kHalf - 1));
     const int64_t moff = (int64_t)m * (2 * a.L + 1 - m) / 2;
     const RTab64 *tab = a.tab64 + (int64_t)k * a.nalm + moff;
 
-    dfl x = {0.f, 0.f}, y = {0.f, 0.f}, yo = {0.f, 0.f};
-    int ls = a.L + 1;
-    if (active) {
-        const int64_t si = start_index(a, k, m, neg, pair);
-        ls = a.ls[si];
-        const double2 s = a.st64[si];
-        yo = df_from_d(s.x);
-        y = df_from_d(s.y);
-        x = df_from_d(a.xr[pair]);
-    }
-    dacc a1r, a1i, a2r, a2i;
-    dacc_zero(a1r);
-    dacc_zero(a1i);
-    dacc_zero(a2r);
-    dacc_zero(a2i);
-    const int lstart = block_min(ls);
-    const int cofs = neg ? 2 : 0;      // (ap, sam) for +k, (am, sap) for -k
+    RecDF A, B;
+    rec_df_start(a, k, m, neg, p0, A);
+    rec_df_start(a, k, m, neg, p0 + 1, B);
+    const int lme = min(A.ls, B.ls), lmx = max(A.ls, B.ls);
+    const int lstart = block_min(lme);
+    const int cofs = neg ? 2 : 0;        // (ap, sam) for +k, (am, sap) for -k
     const float bsg = neg ? 1.f : -1.f;  // -b' for +k, +b' for -k
     for (int c0 = lstart; c0 <= a.L; c0 += kLC64) {
         const int nc = min(kLC64, a.L - c0 + 1);
@@ -391,26 +423,24 @@ __global__ void __launch_bounds__(kNT) k_lcontract_df(const LcArgs a) {
             cf[i] = v;
         }
         __syncthreads();
-        const int i0 = max(0, ls - c0);
-#pragma unroll 2
-        for (int i = i0; i < nc; ++i) {
+        int i = max(0, lme - c0);
+        // until both recurrences have started
+        for (; i < nc && c0 + i < lmx; ++i) {
             const float4 ab = cf[i].ab, c1 = cf[i].c[cofs], c2 = cf[i].c[cofs + 1];
-            dacc_mac(a1r, dfl{c1.x, c1.y}, y);
-            dacc_mac(a1i, dfl{c1.z, c1.w}, y);
-            dacc_mac(a2r, dfl{c2.x, c2.y}, y);
-            dacc_mac(a2i, dfl{c2.z, c2.w}, y);
-            // y_{l+1} = (a' x -+ b') y_l - y_{l-1}
-            const dfl tt = df_add(df_mul(dfl{ab.x, ab.y}, x), dfl{bsg * ab.z, bsg * ab.w});
-            const dfl yn = df_sub(df_mul(tt, y), yo);
-            yo = y;
-            y = yn;
+            const dfl ra = dfl{ab.x, ab.y}, rb = dfl{bsg * ab.z, bsg * ab.w};
+            if (c0 + i >= A.ls) rec_df_step(A, ra, rb, c1, c2);
+            if (c0 + i >= B.ls) rec_df_step(B, ra, rb, c1, c2);
+        }
+#pragma unroll 2
+        for (; i < nc; ++i) {
+            const float4 ab = cf[i].ab, c1 = cf[i].c[cofs], c2 = cf[i].c[cofs + 1];
+            const dfl ra = dfl{ab.x, ab.y}, rb = dfl{bsg * ab.z, bsg * ab.w};
+            rec_df_step(A, ra, rb, c1, c2);
+            rec_df_step(B, ra, rb, c1, c2);
         }
     }
-    if (active) {
-        const double2 acc1 = make_double2(df_to_d(dacc_get(a1r)), df_to_d(dacc_get(a1i)));
-        const double2 acc2 = make_double2(df_to_d(dacc_get(a2r)), df_to_d(dacc_get(a2i)));
-        write_two<double2>(a, m, k, pair, neg, acc1, acc2);
-    }
+    rec_df_write(a, m, k, p0, neg, A);
+    rec_df_write(a, m, k, p0 + 1, neg, B);
 }
 
 __global__ void k_to_f32(const double2 *__restrict__ in, float2 *__restrict__ out, int64_t n) {
@@ -425,7 +455,7 @@ sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
     a.ncomp = p->ncomp;
     a.R = p->R;
     a.npairs = p->npairs;
-    a.ppt = plan_wide(p->precision) ? 1 : 2;
+    a.ppt = (p->precision == SL_FP64) ? 1 : 2;
     a.nchunk = (p->npairs + a.ppt * kHalf - 1) / (a.ppt * kHalf);
     a.nalm = p->nalm;
     a.sky = (const double2 *)sky;
