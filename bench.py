@@ -474,12 +474,12 @@ def detectors_arm(args):
 
 
 # ncu-measured DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
-# at full size for the current kernels (profiles/traffic_lfi_full_size.txt).
+# at full size for the current kernels (profiles/launches_lfi_*.txt).
 TRAFFIC = {
-    ("lcontract_f64", "fp64"): 695.9e6 + 535.9e6,
-    ("interp_f64", "fp64"): 14959.2e6 + 1821.2e6,
-    ("lcontract_f32", "fp32"): 391.9e6 + 253.6e6,
-    ("interp_f32", "fp32"): 10506.0e6 + 2472.8e6,
+    ("lcontract_f64", "fp64"): 695.3e6 + 535.0e6,
+    ("interp_f64", "fp64"): 14800.6e6 + 1861.2e6,
+    ("lcontract_f32", "fp32"): 394.3e6 + 254.7e6,
+    ("interp_f32", "fp32"): 10122.3e6 + 2399.5e6,
 }
 
 
