@@ -19,9 +19,10 @@
  *
  *   c = Re S_0 + 2 sum_{k>=1} Re(e^{ik psi} S_k),  S_k = interpolated F_k.
  *
- * The paper does not fix the interpolation scheme; this library uses separable p-point Lagrange interpolation in
- * theta (at the actual ring colatitudes) and phi (uniform, periodic), with
- * p/2 ghost rows past each pole that hold (-1)^k F_k(ring, phi + pi).
+ * The paper does not fix the interpolation scheme; this library uses
+ * separable p-point Lagrange interpolation in theta (at the actual ring
+ * colatitudes) and phi (uniform, periodic), p = 2, 4 or 6, with p/2 ghost
+ * rows past each pole that hold (-1)^k F_k(ring, phi + pi).
  *
  * Polarised input (ncomp = 3, T/E/B) is the sum of three scalar
  * convolutions: A_{k,lm} = sum_X s^X_lm conj(b^X_lk).
@@ -95,7 +96,7 @@ typedef struct {
                                   symmetric: theta[R-1-r] == pi - theta[r] (to 1e-12);
                                   copied at plan creation */
     int nphi;                  /* Phi: even, >= 8, of the form 2^a 3^b 5^c, <= 8192 */
-    int interp_order;          /* p: 4 (0 selects 4) */
+    int interp_order;          /* p: 2, 4 or 6 points per axis (0 selects 4) */
     int precision;             /* sl_precision */
     int device;                /* CUDA device ordinal */
     void *stream;              /* cudaStream_t for all work; NULL = legacy default stream */

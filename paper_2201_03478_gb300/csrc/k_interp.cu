@@ -26,45 +26,52 @@ namespace sl {
 
 constexpr int kChunkA = kWorkChunk;
 
-// 4-point Lagrange weights: theta rows from the record, phi nodes -1, 0, 1, 2.
-__device__ __forceinline__ void weights64(const InterpGeom &g, int i, double d0, double f, double wt[4],
-                                          double wp[4]) {
-    const double *of = g.offs64 + (size_t)(i + 1) * 4;
-    const double *wd = g.wden + (size_t)(i + 1) * 4;
-    const double d1 = d0 - __ldg(of + 1), d2 = d0 - __ldg(of + 2), d3 = d0 - __ldg(of + 3);
-    const double p01 = d0 * d1, p23 = d2 * d3;
-    wt[0] = __ldg(wd + 0) * d1 * p23;
-    wt[1] = __ldg(wd + 1) * d0 * p23;
-    wt[2] = __ldg(wd + 2) * p01 * d3;
-    wt[3] = __ldg(wd + 3) * p01 * d2;
-    const double a = f + 1.0, c = f - 1.0, d = f - 2.0;
-    const double cd = c * d, ab = a * f;
-    wp[0] = -f * cd * (1.0 / 6.0);
-    wp[1] = a * cd * 0.5;
-    wp[2] = -ab * d * 0.5;
-    wp[3] = ab * c * (1.0 / 6.0);
+// p-point weights of a sample: theta rows from the record and the plan's row
+// table, phi nodes -p/2+1 .. p/2.
+template <int P>
+__device__ __forceinline__ void weights64(const InterpGeom &g, int i, double d0, double f, double wt[P],
+                                          double wp[P]) {
+    double o[P], wd[P];
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+        o[a] = __ldg(g.offs64 + (size_t)(i + 1) * P + a);
+        wd[a] = __ldg(g.wden + (size_t)(i + 1) * P + a);
+    }
+    lagrange_theta<P>(d0, o, wd, wt);
+    lagrange_phi<P>(f, wp);
 }
 
-// Element offsets of the 16 nodes and the ghost-row mask.
-__device__ __forceinline__ unsigned node_offsets(const InterpGeom &g, int i, int j, int off[16]) {
+// Element offsets of the stencil's rows (ring * nphi * K1) and columns (col * K1)
+// -- a node is row + column -- and the mask of ghost rows (beyond a pole: the
+// ring at phi + pi).
+template <int P>
+__device__ __forceinline__ unsigned stencil_offsets(const InterpGeom &g, int i, int j, int roff[P], int coff[P],
+                                                    int coff_g[P]) {
     const int K1 = g.K + 1;
     unsigned ghost = 0;
 #pragma unroll
-    for (int ra = 0; ra < 4; ++ra) {
-        int row = i - 1 + ra, ring = row, shift = 0;
-        if (row < 0) { ring = -1 - row; shift = g.nphi / 2; ghost |= 1u << ra; }
-        else if (row >= g.R) { ring = 2 * g.R - 1 - row; shift = g.nphi / 2; ghost |= 1u << ra; }
+    for (int a = 0; a < P; ++a) {
+        const int row = i - P / 2 + 1 + a;
+        int ring = row;
+        if (row < 0) { ring = -1 - row; ghost |= 1u << a; }
+        else if (row >= g.R) { ring = 2 * g.R - 1 - row; ghost |= 1u << a; }
+        roff[a] = ring * g.nphi * K1;
+    }
 #pragma unroll
-        for (int cb = 0; cb < 4; ++cb) {
-            int col = j - 1 + cb + shift;
-            col = (col < 0) ? col + g.nphi : (col >= g.nphi ? col - g.nphi : col);
-            off[ra * 4 + cb] = (ring * g.nphi + col) * K1;
-        }
+    for (int b = 0; b < P; ++b) {
+        int col = j - P / 2 + 1 + b;
+        col = (col < 0) ? col + g.nphi : (col >= g.nphi ? col - g.nphi : col);
+        coff[b] = col * K1;
+        int cg = col + g.nphi / 2;
+        cg = (cg >= g.nphi) ? cg - g.nphi : cg;
+        coff_g[b] = cg * K1;
     }
     return ghost;
 }
 
 // ------------------------------------------------------------------ forward FP64
+// One thread per sample: combined weights w_a w_b per node, read through L1.
+template <int P>
 __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const double2 *__restrict__ maps,
                                                     const StencilRec64 *__restrict__ rec,
                                                     const double *__restrict__ psi, const unsigned *__restrict__ perm,
@@ -73,18 +80,26 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const do
         const unsigned s = perm[t];
         const StencilRec64 r = rec[s];
         const int i = (int)(r.cell >> 16) - 1, j = (int)(r.cell & 0xffffu);
-        double wt[4], wp[4], w[16];
-        weights64(g, i, r.dth, r.fph, wt, wp);
-        int off[16];
-        const unsigned ghost = node_offsets(g, i, j, off);
+        double wt[P], wp[P];
+        weights64<P>(g, i, r.dth, r.fph, wt, wp);
+        int roff[P], coff[P], coffg[P];
+        const unsigned ghost = stencil_offsets<P>(g, i, j, roff, coff, coffg);
+        // node offsets and combined weights (ghost rows read the ring at phi + pi)
+        int off[P * P];
+        double w[P * P];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) w[q] = wt[q >> 2] * wp[q & 3];
+        for (int a = 0; a < P; ++a)
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                off[a * P + b] = roff[a] + (((ghost >> a) & 1u) ? coffg[b] : coff[b]);
+                w[a * P + b] = wt[a] * wp[b];
+            }
         double sp, cp;
         sincos(psi[s], &sp, &cp);
         // k = 0: only Re S_0 enters the TOD
         double acc = 0.0;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc = fma(w[q], __ldg(maps + off[q]).x, acc);
+        for (int q = 0; q < P * P; ++q) acc = fma(w[q], __ldg(maps + off[q]).x, acc);
         // C_k = 2 cos(k psi), S_k = 2 sin(k psi) by the Chebyshev three-term
         // recurrence X_{k+1} = (2 cos psi) X_k - X_{k-1}
         const double c1 = 2.0 * cp;
@@ -92,14 +107,14 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const do
         for (int k = 1; k <= g.K; ++k) {
             if (ghost) {   // (-1)^k on ghost rows: flip their weights between k-1 and k
 #pragma unroll
-                for (int ra = 0; ra < 4; ++ra)
-                    if (ghost & (1u << ra))
+                for (int a = 0; a < P; ++a)
+                    if (ghost & (1u << a))
 #pragma unroll
-                        for (int cb = 0; cb < 4; ++cb) w[ra * 4 + cb] = -w[ra * 4 + cb];
+                        for (int b = 0; b < P; ++b) w[a * P + b] = -w[a * P + b];
             }
             double sr = 0.0, si = 0.0;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
+            for (int q = 0; q < P * P; ++q) {
                 const double2 v = __ldg(maps + off[q] + k);
                 sr = fma(w[q], v.x, sr);
                 si = fma(w[q], v.y, si);
@@ -135,9 +150,9 @@ struct TiledArgs {
     double *tod;
 };
 
-template <int TC>
+template <int TC, int P>
 __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
-    constexpr int TW = TC + 3, NR = kTileRows + 3, NN = NR * TW;   // staged nodes per k pair
+    constexpr int TW = TC + P - 1, NR = kTileRows + P - 1, NN = NR * TW;   // staged nodes per k pair
     const InterpGeom &g = A.g;
     const int K1 = g.K + 1, KH = (K1 + 1) >> 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -153,14 +168,14 @@ __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
         const unsigned s_beg = A.start[(int64_t)tile * A.ncell] + c * kChunkA;
         const unsigned s_end = min(A.start[(int64_t)(tile + 1) * A.ncell], s_beg + kChunkA);
         const int tr = tile / g.ntc, tcol = tile - tr * g.ntc;
-        const int rowlo = tr * kTileRows - 2, collo = tcol * TC - 1;
+        const int rowlo = tr * kTileRows - P / 2, collo = tcol * TC - P / 2 + 1;
         if (tile != staged_tile) {
             __syncthreads();
             for (int nd = e0_n, kp = e0_k; nd < NN;) {
                 const int r = nd / TW, cc = nd - r * TW;
                 const int row = rowlo + r, k = 2 * kp;
                 float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (row >= -2 && row <= g.R + 1) {
+                if (row >= -P / 2 && row <= g.R - 1 + P / 2) {
                     int ring = row, col = collo + cc;
                     bool flip = false;
                     if (row < 0 || row >= g.R) {
@@ -190,19 +205,18 @@ __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
             const unsigned s = A.perm[t];
             const StencilRec32 r = A.rec[s];
             const int i = (int)(r.cell >> 16) - 1, j = (int)(r.cell & 0xffffu);
-            const float4 of = __ldg(reinterpret_cast<const float4 *>(g.rowtab32) + 2 * (i + 1));
-            const float4 wd = __ldg(reinterpret_cast<const float4 *>(g.rowtab32) + 2 * (i + 1) + 1);
-            const float d0 = r.dth, d1 = d0 - of.y, d2 = d0 - of.z, d3 = d0 - of.w;
-            const float p01 = d0 * d1, p23 = d2 * d3;
-            const float wt[4] = {wd.x * d1 * p23, wd.y * d0 * p23, wd.z * p01 * d3, wd.w * p01 * d2};
-            const float f = r.fph;
-            const float a = f + 1.f, cm = f - 1.f, d = f - 2.f;
-            const float cd = cm * d, ab = a * f;
-            const float wp[4] = {-f * cd * (1.f / 6.f), a * cd * 0.5f, -ab * d * 0.5f, ab * cm * (1.f / 6.f)};
-            float w[16];
+            float o[P], wd[P], wt[P], wp[P];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) w[q] = wt[q >> 2] * wp[q & 3];
-            const float4 *nb = node + (i - 1 - rowlo) * TW + (j - 1 - collo);
+            for (int a = 0; a < P; ++a) {
+                o[a] = __ldg(g.rowtab32 + (size_t)(i + 1) * 2 * P + a);
+                wd[a] = __ldg(g.rowtab32 + (size_t)(i + 1) * 2 * P + P + a);
+            }
+            lagrange_theta<P>(r.dth, o, wd, wt);
+            lagrange_phi<P>(r.fph, wp);
+            float w[P * P];
+#pragma unroll
+            for (int q = 0; q < P * P; ++q) w[q] = wt[q / P] * wp[q % P];
+            const float4 *nb = node + (i - P / 2 + 1 - rowlo) * TW + (j - P / 2 + 1 - collo);
             float sz, cz;
             sincosf(r.psr, &sz, &cz);
             // z^k for the pair (k, k+1), starting at (1, z)
@@ -212,8 +226,8 @@ __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
             for (int kp = 0; kp < KH; ++kp, nb += NN) {
                 float sr0 = 0.f, si0 = 0.f, sr1 = 0.f, si1 = 0.f;
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float4 v = nb[(q >> 2) * TW + (q & 3)];
+                for (int q = 0; q < P * P; ++q) {
+                    const float4 v = nb[(q / P) * TW + (q % P)];
                     sr0 = fmaf(w[q], v.x, sr0);
                     si0 = fmaf(w[q], v.y, si0);
                     sr1 = fmaf(w[q], v.z, sr1);
@@ -233,7 +247,7 @@ __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
 
 size_t interp_f32_tiled_smem_tc(const sl_plan *p, int tc) {
     const int KH = (p->K + 2) / 2;
-    return (size_t)(kTileRows + 3) * (tc + 3) * KH * sizeof(float4);
+    return (size_t)(kTileRows + p->p - 1) * (tc + p->p - 1) * KH * sizeof(float4);
 }
 
 size_t interp_f32_tiled_smem(const sl_plan *p) { return interp_f32_tiled_smem_tc(p, p->geom.tile_cols); }
@@ -251,24 +265,24 @@ struct AdjArgs {
 
 constexpr int kNB = 64;   // samples staged per batch
 
+template <int P>
 __global__ void k_interp_adjoint(const AdjArgs A) {
+    constexpr int NQ = P * P;               // stencil nodes
     const InterpGeom &g = A.g;
     const int K1 = g.K + 1;
     const int TC = g.tile_cols;
-    const int tw = TC + 3;                  // smem tile columns
-    const int th_rows = kTileRows + 3;      // smem tile rows
+    const int tw = TC + P - 1;              // smem tile columns
+    const int th_rows = kTileRows + P - 1;  // smem tile rows
     const int nnode = th_rows * tw;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *acc = reinterpret_cast<double2 *>(smem_raw);            // [nnode][K1]
-    double2 *P = acc + (size_t)nnode * K1;                            // [kNB][K1]
-    double *W = reinterpret_cast<double *>(P + (size_t)kNB * K1);     // [kNB][16]
-    int *LOC = reinterpret_cast<int *>(W + (size_t)kNB * 16);         // [kNB] node index of (row i-1, col j-1)
+    double2 *PH = acc + (size_t)nnode * K1;                           // [kNB][K1]
+    double *W = reinterpret_cast<double *>(PH + (size_t)kNB * K1);    // [kNB][NQ]
+    int *LOC = reinterpret_cast<int *>(W + (size_t)kNB * NQ);         // [kNB] node index of the first stencil node
 
     const unsigned nchunks = A.chunk_off[A.ntiles];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    const int q = lane & 15, kpar = lane >> 4;
-    const int qa = q >> 2, qb = q & 3;
 
     for (int e = threadIdx.x; e < nnode * K1; e += blockDim.x) acc[e] = make_double2(0.0, 0.0);
 
@@ -284,8 +298,8 @@ __global__ void k_interp_adjoint(const AdjArgs A) {
         const unsigned s_beg = A.start[(int64_t)tile * A.ncell] + c * kChunkA;
         const unsigned s_end = min(A.start[(int64_t)(tile + 1) * A.ncell], s_beg + kChunkA);
         const int tr = tile / g.ntc, tcol = tile % g.ntc;
-        const int rowlo = tr * kTileRows - 2;   // stencil rows i-1..i+2, base row i >= tr*4-1
-        const int collo = tcol * TC - 1;
+        const int rowlo = tr * kTileRows - P / 2;   // stencil rows i-P/2+1 .., base row i >= tr*4-1
+        const int collo = tcol * TC - P / 2 + 1;
         __syncthreads();
         for (unsigned b0 = s_beg; b0 < s_end; b0 += kNB) {
             const int nb = (int)min((unsigned)kNB, s_end - b0);
@@ -294,19 +308,19 @@ __global__ void k_interp_adjoint(const AdjArgs A) {
                 const unsigned s = A.perm[b0 + threadIdx.x];
                 const StencilRec64 r = A.rec[s];
                 const int i = (int)(r.cell >> 16) - 1, j = (int)(r.cell & 0xffffu);
-                double wt[4], wp[4];
-                weights64(g, i, r.dth, r.fph, wt, wp);
-                double *ws = W + threadIdx.x * 16;
+                double wt[P], wp[P];
+                weights64<P>(g, i, r.dth, r.fph, wt, wp);
+                double *ws = W + threadIdx.x * NQ;
 #pragma unroll
-                for (int ra = 0; ra < 4; ++ra)
+                for (int ra = 0; ra < P; ++ra)
 #pragma unroll
-                    for (int cb = 0; cb < 4; ++cb) ws[ra * 4 + cb] = wt[ra] * wp[cb];
-                LOC[threadIdx.x] = (i - 1 - rowlo) * tw + (j - 1 - collo);
+                    for (int cb = 0; cb < P; ++cb) ws[ra * P + cb] = wt[ra] * wp[cb];
+                LOC[threadIdx.x] = (i - P / 2 + 1 - rowlo) * tw + (j - P / 2 + 1 - collo);
                 double sp, cp;
                 sincos(A.psi[s], &sp, &cp);
                 const double y = A.y[s], c2 = 2.0 * cp;
                 double ck = 1.0, sk = 0.0, ckm = cp, skm = -sp;
-                double2 *Ps = P + (size_t)threadIdx.x * K1;
+                double2 *Ps = PH + (size_t)threadIdx.x * K1;
                 for (int k = 0; k <= g.K; ++k) {
                     const double sc = (k == 0) ? y : 2.0 * y;
                     Ps[k] = make_double2(sc * ck, -sc * sk);     // eps_k y e^{-ik psi}
@@ -318,20 +332,23 @@ __global__ void k_interp_adjoint(const AdjArgs A) {
                 }
             }
             __syncthreads();
-            // phase B: warp w owns k-pairs w, w + nwarps, ...; lane = (node q, k parity)
+            // phase B: warp w owns k-pairs w, w + nwarps, ...; a lane handles the
+            // entries (node q, k parity) = lane, lane + 32, ... of the 2 P^2
             for (int kp = warp; 2 * kp <= g.K; kp += nwarps) {
-                const int kk = 2 * kp + kpar;
-                const bool live = kk <= g.K;
                 for (int sidx = 0; sidx < nb; ++sidx) {
-                    if (live) {
-                        const int node = LOC[sidx] + qa * tw + qb;
-                        const double w = W[sidx * 16 + q];
-                        const double2 ph = P[(size_t)sidx * K1 + kk];
-                        double2 &dst = acc[(size_t)node * K1 + kk];
-                        double2 cur = dst;
-                        cur.x = fma(w, ph.x, cur.x);
-                        cur.y = fma(w, ph.y, cur.y);
-                        dst = cur;
+#pragma unroll
+                    for (int e = lane; e < 2 * NQ; e += 32) {
+                        const int q = e % NQ, kk = 2 * kp + e / NQ;
+                        if (kk <= g.K) {
+                            const int node = LOC[sidx] + (q / P) * tw + (q % P);
+                            const double w = W[sidx * NQ + q];
+                            const double2 ph = PH[(size_t)sidx * K1 + kk];
+                            double2 &dst = acc[(size_t)node * K1 + kk];
+                            double2 cur = dst;
+                            cur.x = fma(w, ph.x, cur.x);
+                            cur.y = fma(w, ph.y, cur.y);
+                            dst = cur;
+                        }
                     }
                     // consecutive samples may share nodes: order this warp's updates
                     __syncwarp(0xffffffffu);
@@ -348,7 +365,7 @@ __global__ void k_interp_adjoint(const AdjArgs A) {
             const int node = e / K1;
             const int row = rowlo + node / tw;
             int col = collo + node % tw;
-            if (row < -2 || row > g.R + 1) continue;
+            if (row < -P / 2 || row > g.R - 1 + P / 2) continue;
             int ring = row;
             double sg = 1.0;
             if (row < 0 || row >= g.R) {
@@ -376,9 +393,17 @@ sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *map
     int slot;
     if (p->precision == SL_DF64) return launch_interp_df(p, b, fine, maps, psi, n, tod);
     if (p->precision == SL_FP64) {
+        void (*kern)(const InterpGeom, const double2 *, const StencilRec64 *, const double *, const unsigned *,
+                     int64_t, double *);
+        switch (p->p) {
+            case 2: kern = k_interp_f64<2>; break;
+            case 4: kern = k_interp_f64<4>; break;
+            case 6: kern = k_interp_f64<6>; break;
+            default: return set_error(SL_ERR_UNSUPPORTED, "interp_order %d", p->p);
+        }
         slot = timing_begin(p, "interp_f64");
-        k_interp_f64<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const double2 *)maps,
-                                                             (const StencilRec64 *)b.rec, psi, b.perm, n, tod);
+        kern<<<grid_for(n, 256), 256, 0, p->stream>>>(p->geom, (const double2 *)maps, (const StencilRec64 *)b.rec,
+                                                       psi, b.perm, n, tod);
     } else {
         if (!b.chunk_off) return set_error(SL_ERR_ARG, "FP32 interpolation needs the per-tile work list");
         TiledArgs a;
@@ -392,13 +417,14 @@ sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *map
         a.ncell = fine ? kTileRows * p->geom.tile_cols : 1;
         a.tod = tod;
         const size_t sm = interp_f32_tiled_smem(p);
-        void (*kern)(const TiledArgs);
-        switch (p->geom.tile_cols) {
-            case 32: kern = k_interp_f32_tiled<32>; break;
-            case 16: kern = k_interp_f32_tiled<16>; break;
-            case 8: kern = k_interp_f32_tiled<8>; break;
-            default: return set_error(SL_ERR_UNSUPPORTED, "tile width %d", p->geom.tile_cols);
-        }
+        void (*kern)(const TiledArgs) = nullptr;
+#define SL_TILED(TCV, PV) \
+    if (p->geom.tile_cols == TCV && p->p == PV) kern = k_interp_f32_tiled<TCV, PV>;
+        SL_TILED(32, 4) SL_TILED(16, 4) SL_TILED(8, 4)
+        SL_TILED(32, 2) SL_TILED(16, 2) SL_TILED(8, 2)
+        SL_TILED(32, 6) SL_TILED(16, 6) SL_TILED(8, 6)
+#undef SL_TILED
+        if (!kern) return set_error(SL_ERR_UNSUPPORTED, "tile width %d, interp_order %d", p->geom.tile_cols, p->p);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return cuda_check(e, "k_interp_f32_tiled smem attribute");
         int per_sm = 1, nsm = 152;
@@ -413,10 +439,10 @@ sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *map
 }
 
 size_t interp_adjoint_smem_tc(const sl_plan *p, int tc) {
-    const int K1 = p->K + 1;
-    const int nnode = (kTileRows + 3) * (tc + 3);
+    const int K1 = p->K + 1, P = p->p;
+    const int nnode = (kTileRows + P - 1) * (tc + P - 1);
     return (size_t)nnode * K1 * sizeof(double2) + (size_t)kNB * K1 * sizeof(double2) +
-           (size_t)kNB * 16 * sizeof(double) + (size_t)kNB * sizeof(int);
+           (size_t)kNB * P * P * sizeof(double) + (size_t)kNB * sizeof(int);
 }
 
 sl_status launch_interp_adjoint(sl_plan *p, const SortBufs &b, int fine, const double *psi, const double *tod,
@@ -437,15 +463,22 @@ sl_status launch_interp_adjoint(sl_plan *p, const SortBufs &b, int fine, const d
     int nwarps = (K1 + 1) / 2;
     if (nwarps < 2) nwarps = 2;
     if (nwarps > 16) nwarps = 16;
-    cudaError_t e = cudaFuncSetAttribute(k_interp_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    void (*kern)(const AdjArgs);
+    switch (p->p) {
+        case 2: kern = k_interp_adjoint<2>; break;
+        case 4: kern = k_interp_adjoint<4>; break;
+        case 6: kern = k_interp_adjoint<6>; break;
+        default: return set_error(SL_ERR_UNSUPPORTED, "interp_order %d", p->p);
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return cuda_check(e, "k_interp_adjoint smem attribute");
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_adjoint, 32 * nwarps, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * nwarps, sm);
     if (per_sm < 1) per_sm = 1;
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
     int slot = timing_begin(p, "interp_adj");
-    k_interp_adjoint<<<(unsigned)(nsm * per_sm), 32 * nwarps, sm, p->stream>>>(a);
+    kern<<<(unsigned)(nsm * per_sm), 32 * nwarps, sm, p->stream>>>(a);
     timing_end(p, slot);
     (void)n;
     return cuda_check(cudaGetLastError(), "k_interp_adjoint launch");

@@ -32,9 +32,39 @@ __device__ __forceinline__ dfl df_ld(const float2 *p) {
     return dfl{v.x, v.y};
 }
 
-template <int TC>
+// p-point Lagrange weights in double-float (the same prefix / suffix products
+// as lagrange_theta and lagrange_phi).
+template <int P>
+__device__ __forceinline__ void weights_df(const float2 *rt, dfl d0, dfl f, dfl wt[P], dfl wp[P]) {
+    dfl d[P], pre[P + 1], suf[P + 1];
+    const dfl one = df_make(1.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < P; ++a) d[a] = (a == 0) ? d0 : df_sub(d0, df_ld(rt + a));
+    pre[0] = one;
+    suf[P] = one;
+#pragma unroll
+    for (int a = 0; a < P; ++a) pre[a + 1] = df_mul(pre[a], d[a]);
+#pragma unroll
+    for (int a = P - 1; a >= 0; --a) suf[a] = df_mul(suf[a + 1], d[a]);
+#pragma unroll
+    for (int a = 0; a < P; ++a) wt[a] = df_mul(df_ld(rt + P + a), df_mul(pre[a], suf[a + 1]));
+#pragma unroll
+    for (int b = 0; b < P; ++b) d[b] = df_sub(f, df_make((float)(b - P / 2 + 1), 0.f));
+#pragma unroll
+    for (int b = 0; b < P; ++b) pre[b + 1] = df_mul(pre[b], d[b]);
+#pragma unroll
+    for (int b = P - 1; b >= 0; --b) suf[b] = df_mul(suf[b + 1], d[b]);
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+        const double inv = uniform_inv_den<P>(b);
+        const float ih = (float)inv;
+        wp[b] = df_mul(df_mul(pre[b], suf[b + 1]), df_make(ih, (float)(inv - (double)ih)));
+    }
+}
+
+template <int TC, int P>
 __global__ void __launch_bounds__(256) k_interp_df_tiled(const DfArgs A) {
-    constexpr int TW = TC + 3, NR = kTileRows + 3, NN = NR * TW;
+    constexpr int TW = TC + P - 1, NR = kTileRows + P - 1, NN = NR * TW;
     const InterpGeom &g = A.g;
     const int K1 = g.K + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -49,7 +79,7 @@ __global__ void __launch_bounds__(256) k_interp_df_tiled(const DfArgs A) {
         const unsigned s_beg = A.start[(int64_t)tile * A.ncell] + c * kWorkChunk;
         const unsigned s_end = min(A.start[(int64_t)(tile + 1) * A.ncell], s_beg + kWorkChunk);
         const int tr = tile / g.ntc, tcol = tile - tr * g.ntc;
-        const int rowlo = tr * kTileRows - 2, collo = tcol * TC - 1;
+        const int rowlo = tr * kTileRows - P / 2, collo = tcol * TC - P / 2 + 1;
         if (tile != staged_tile) {
             __syncthreads();
             // element e = node * K1 + k, walked with blockDim.x steps
@@ -57,7 +87,7 @@ __global__ void __launch_bounds__(256) k_interp_df_tiled(const DfArgs A) {
                 const int r = nd / TW, cc = nd - r * TW;
                 const int row = rowlo + r;
                 float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (row >= -2 && row <= g.R + 1) {
+                if (row >= -P / 2 && row <= g.R - 1 + P / 2) {
                     int ring = row, col = collo + cc;
                     if (row < 0 || row >= g.R) {
                         ring = (row < 0) ? -1 - row : 2 * g.R - 1 - row;
@@ -86,23 +116,13 @@ __global__ void __launch_bounds__(256) k_interp_df_tiled(const DfArgs A) {
             double sp, cp;
             sincos(__ldg(A.psi + s), &sp, &cp);
             // Lagrange weights in double-float
-            const float2 *rt = g.rowtab_df + (size_t)(i + 1) * 8;
-            const dfl d0 = df_from_d(r.dth), f = df_from_d(r.fph);
-            const dfl d1 = df_sub(d0, df_ld(rt + 1)), d2 = df_sub(d0, df_ld(rt + 2)), d3 = df_sub(d0, df_ld(rt + 3));
-            const dfl p01 = df_mul(d0, d1), p23 = df_mul(d2, d3);
-            const dfl wt[4] = {df_mul(df_ld(rt + 4), df_mul(d1, p23)), df_mul(df_ld(rt + 5), df_mul(d0, p23)),
-                               df_mul(df_ld(rt + 6), df_mul(p01, d3)), df_mul(df_ld(rt + 7), df_mul(p01, d2))};
-            const dfl one = df_make(1.f, 0.f), two = df_make(2.f, 0.f);
-            const dfl a = df_add(f, one), cm = df_sub(f, one), d = df_sub(f, two);
-            const dfl cd = df_mul(cm, d), ab = df_mul(a, f);
-            // 1/6 and 1/2 as double-float: 1/6 = h + l exactly to 2^-48
-            const dfl sixth = df_make(0.16666667163372039795f, -4.9670538793103396892e-09f);
-            const dfl wp[4] = {df_neg(df_mul(df_mul(f, cd), sixth)), df_mul(df_mul(a, cd), df_make(0.5f, 0.f)),
-                               df_neg(df_mul(df_mul(ab, d), df_make(0.5f, 0.f))), df_mul(df_mul(ab, cm), sixth)};
-            dfl w[16];
+            dfl wt[P], wp[P];
+            weights_df<P>(g.rowtab_df + (size_t)(i + 1) * 2 * P, df_from_d(r.dth), df_from_d(r.fph), wt, wp);
+            dfl w[P * P];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) w[q] = df_mul(wt[q >> 2], wp[q & 3]);
-            const float4 *nb = node + (i - 1 - rowlo) * TW + (j - 1 - collo);
+            for (int q = 0; q < P * P; ++q) w[q] = df_mul(wt[q / P], wp[q % P]);
+            const float4 *nb = node + (i - P / 2 + 1 - rowlo) * TW + (j - P / 2 + 1 - collo);
+            const dfl two = df_make(2.f, 0.f);
             // C_k = 2 cos(k psi), S_k = 2 sin(k psi): X_{k+1} = (2 cos psi) X_k - X_{k-1}
             const dfl c1 = df_from_d(2.0 * cp);
             dfl Ck = c1, Sk = df_from_d(2.0 * sp), Ckm = two, Skm = df_make(0.f, 0.f);
@@ -111,8 +131,8 @@ __global__ void __launch_bounds__(256) k_interp_df_tiled(const DfArgs A) {
                 dacc sr;
                 dacc_zero(sr);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float4 v4 = nb[(q >> 2) * TW + (q & 3)];
+                for (int q = 0; q < P * P; ++q) {
+                    const float4 v4 = nb[(q / P) * TW + (q % P)];
                     dacc_mac(sr, w[q], dfl{v4.x, v4.y});
                 }
                 acc = sr;
@@ -123,8 +143,8 @@ __global__ void __launch_bounds__(256) k_interp_df_tiled(const DfArgs A) {
                 dacc_zero(sr);
                 dacc_zero(si);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float4 v4 = nb[(q >> 2) * TW + (q & 3)];
+                for (int q = 0; q < P * P; ++q) {
+                    const float4 v4 = nb[(q / P) * TW + (q % P)];
                     dacc_mac(sr, w[q], dfl{v4.x, v4.y});
                     dacc_mac(si, w[q], dfl{v4.z, v4.w});
                 }
@@ -142,7 +162,7 @@ __global__ void __launch_bounds__(256) k_interp_df_tiled(const DfArgs A) {
 }
 
 size_t interp_df_tiled_smem_tc(const sl_plan *p, int tc) {
-    return (size_t)(kTileRows + 3) * (tc + 3) * (p->K + 1) * sizeof(float4);
+    return (size_t)(kTileRows + p->p - 1) * (tc + p->p - 1) * (p->K + 1) * sizeof(float4);
 }
 
 sl_status launch_interp_df(sl_plan *p, const SortBufs &b, int fine, const void *maps, const double *psi, int64_t n,
@@ -160,13 +180,14 @@ sl_status launch_interp_df(sl_plan *p, const SortBufs &b, int fine, const void *
     a.ncell = fine ? kTileRows * p->geom.tile_cols : 1;
     a.tod = tod;
     const size_t sm = interp_df_tiled_smem_tc(p, p->geom.tile_cols);
-    void (*kern)(const DfArgs);
-    switch (p->geom.tile_cols) {
-        case 32: kern = k_interp_df_tiled<32>; break;
-        case 16: kern = k_interp_df_tiled<16>; break;
-        case 8: kern = k_interp_df_tiled<8>; break;
-        default: return set_error(SL_ERR_UNSUPPORTED, "tile width %d", p->geom.tile_cols);
-    }
+    void (*kern)(const DfArgs) = nullptr;
+#define SL_TILED(TCV, PV) \
+    if (p->geom.tile_cols == TCV && p->p == PV) kern = k_interp_df_tiled<TCV, PV>;
+    SL_TILED(32, 4) SL_TILED(16, 4) SL_TILED(8, 4)
+    SL_TILED(32, 2) SL_TILED(16, 2) SL_TILED(8, 2)
+    SL_TILED(32, 6) SL_TILED(16, 6) SL_TILED(8, 6)
+#undef SL_TILED
+    if (!kern) return set_error(SL_ERR_UNSUPPORTED, "tile width %d, interp_order %d", p->geom.tile_cols, p->p);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return cuda_check(e, "k_interp_df_tiled smem attribute");
     int per_sm = 1, nsm = 152;

@@ -42,16 +42,17 @@ __global__ void __launch_bounds__(256) k_bin(const InterpGeom g, int fine, const
             const unsigned tile = (unsigned)tr * (unsigned)g.ntc + (unsigned)tc;
             key = fine ? tile * (unsigned)(kTileRows * g.tile_cols) + (unsigned)(li * g.tile_cols + lj) : tile;
             keys[s] = key;
-            // theta - theta(i-1) in 2^-60 fixed point (exact for theta >= 2^-8)
+            // theta - theta(i0), i0 = i - p/2 + 1 the first stencil row (index i0 + half = i + 1),
+            // in 2^-60 fixed point (exact for theta >= 2^-8)
             long long tf = 0;
             const bool tfix = to_fix<60>(th, tf);
-            const long long dfix = tf - __ldg(g.ring_fix + g.half + i - 1);
+            const long long dfix = tf - __ldg(g.ring_fix + i + 1);
             const unsigned cell = ((unsigned)(i + 1) << 16) | (unsigned)j;
             if (REC64) {
-                const double dth = tfix ? fix_to_d<60>(dfix) : th - __ldg(g.ring_ext + g.half + i - 1);
+                const double dth = tfix ? fix_to_d<60>(dfix) : th - __ldg(g.ring_ext + i + 1);
                 reinterpret_cast<StencilRec64 *>(rec)[s] = StencilRec64{dth, frac_bits_d(fr, sh), cell, 0u};
             } else {
-                const float dth = tfix ? fix_to_f<60>(dfix) : d2f_bits(th - __ldg(g.ring_ext + g.half + i - 1));
+                const float dth = tfix ? fix_to_f<60>(dfix) : d2f_bits(th - __ldg(g.ring_ext + i + 1));
                 // psi reduced to [-pi, pi] in 2^-59 fixed point; |psi| >= 8 (and NaN) in FP64
                 const double ps = psi[s];
                 long long pf;

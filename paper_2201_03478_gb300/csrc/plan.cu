@@ -143,6 +143,15 @@ static void free_sort_tables(sl_plan *p) {
                                                   (p->ntiles + 1));
 }
 
+// Shared memory the tile-staged kernels need at tile width tc.
+static size_t tile_smem_need(const sl_plan *p, int tc) {
+    size_t need = interp_adjoint_smem_tc(p, tc);
+    if (p->precision == SL_FP32) need = std::max(need, interp_f32_tiled_smem_tc(p, tc));
+    if (p->precision == SL_DF64) need = std::max(need, interp_df_tiled_smem_tc(p, tc));
+    return need;
+}
+constexpr size_t kSmemOptin = 232448;   // 227 KB of dynamic shared memory per CTA (sm_100 family)
+
 static void set_tile_grid(sl_plan *p, int tc) {
     p->geom.tile_cols = tc;
     p->geom.ntr = (p->R + 1 + kTileRows - 1) / kTileRows;
@@ -203,7 +212,8 @@ static sl_status validate(const sl_plan_desc *d, int *rad, int *nrad) {
         return set_error(SL_ERR_ARG, "kmax=%d outside [0, min(lmax, %d)]", d->kmax, kMaxK);
     if (d->ncomp != 1 && d->ncomp != 3) return set_error(SL_ERR_ARG, "ncomp=%d (must be 1 or 3)", d->ncomp);
     int p = d->interp_order ? d->interp_order : 4;
-    if (p != 4) return set_error(SL_ERR_UNSUPPORTED, "interp_order=%d (only 4 is built)", d->interp_order);
+    if (p < 2 || (p & 1)) return set_error(SL_ERR_ARG, "interp_order=%d (must be even, >= 2)", d->interp_order);
+    if (p > 6) return set_error(SL_ERR_UNSUPPORTED, "interp_order=%d (2, 4 and 6 are built)", d->interp_order);
     if (d->nrings < 4 || d->nrings > 65534) return set_error(SL_ERR_ARG, "nrings=%d outside [4, 65534]", d->nrings);
     if (!d->ring_theta) return set_error(SL_ERR_ARG, "ring_theta is NULL");
     const double *t = d->ring_theta;
@@ -329,24 +339,24 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
             wden[(size_t)(i + 1) * P + a] = (double)(1.0L / den);
         }
     }
-    // per base row: theta(i-1+a) - theta(i-1) (double) and, for FP32 plans, the
-    // same offsets followed by wden in float
-    std::vector<double> offs64((size_t)(R + 1) * 4);
-    std::vector<float> rowtab32((size_t)(R + 1) * 8);
-    std::vector<float2> rowtab_df((size_t)(R + 1) * 8);
+    // per base row i: theta(i0+a) - theta(i0), i0 = i - p/2 + 1 (double) and the
+    // same offsets followed by wden in float and in double-float
+    std::vector<double> offs64((size_t)(R + 1) * P);
+    std::vector<float> rowtab32((size_t)(R + 1) * 2 * P);
+    std::vector<float2> rowtab_df((size_t)(R + 1) * 2 * P);
     auto split = [](long double v) {
         const float h = (float)v;
         return make_float2(h, (float)(v - (long double)h));
     };
     for (int i = -1; i <= R - 1; ++i) {
-        const double t0 = ring_ext[i - 1 + half];
-        for (int a = 0; a < 4; ++a) {
-            const double o = (double)((long double)ring_ext[i - 1 + a + half] - (long double)t0);
-            offs64[(size_t)(i + 1) * 4 + a] = o;
-            rowtab32[(size_t)(i + 1) * 8 + a] = (float)o;
-            rowtab32[(size_t)(i + 1) * 8 + 4 + a] = (float)wden[(size_t)(i + 1) * P + a];
-            rowtab_df[(size_t)(i + 1) * 8 + a] = split(o);
-            rowtab_df[(size_t)(i + 1) * 8 + 4 + a] = split(wden[(size_t)(i + 1) * P + a]);
+        const double t0 = ring_ext[i + 1];            // row i0 = i - half + 1 sits at index i0 + half
+        for (int a = 0; a < P; ++a) {
+            const double o = (double)((long double)ring_ext[i + 1 + a] - (long double)t0);
+            offs64[(size_t)(i + 1) * P + a] = o;
+            rowtab32[(size_t)(i + 1) * 2 * P + a] = (float)o;
+            rowtab32[(size_t)(i + 1) * 2 * P + P + a] = (float)wden[(size_t)(i + 1) * P + a];
+            rowtab_df[(size_t)(i + 1) * 2 * P + a] = split(o);
+            rowtab_df[(size_t)(i + 1) * 2 * P + P + a] = split(wden[(size_t)(i + 1) * P + a]);
         }
     }
     for (int r = 0; r < p->npairs; ++r) {
@@ -386,11 +396,6 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     p->geom.phi_scale = p->nphi / (2.0 * M_PI);
     p->geom.phi_fix = (unsigned long long)llroundl(
         ldexpl((long double)p->nphi / (2.0L * 3.14159265358979323846264338327950288L), 52));
-    {   // tile width: 32 columns (16 when kmax > 16), at most nphi; one of 8, 16, 32
-        int tc = (K <= 16) ? 32 : 16;
-        while (tc > p->nphi) tc >>= 1;
-        set_tile_grid(p, tc);
-    }
 
     double *d_c2 = nullptr, *d_s2 = nullptr, *d_cs = nullptr;
 #define TRY(x)                      \
@@ -398,6 +403,16 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
         st = (x);                   \
         if (st != SL_OK) goto fail; \
     } while (0)
+    {   // tile width: 32 columns (16 when kmax > 16), at most nphi and within the
+        // shared memory of the tile-staged kernels; one of 8, 16, 32
+        int tc = (K <= 16) ? 32 : 16;
+        while (tc > 8 && (tc > p->nphi || tile_smem_need(p, tc) > kSmemOptin)) tc >>= 1;
+        if (tile_smem_need(p, tc) > kSmemOptin) {
+            st = set_error(SL_ERR_UNSUPPORTED, "kmax=%d with interp_order=%d: a sort tile exceeds shared memory", K, P);
+            goto fail;
+        }
+        set_tile_grid(p, tc);
+    }
     TRY(dalloc_t(p, &p->d_ring_theta, R, "ring theta"));
     TRY(dalloc_t(p, &p->d_xr, p->npairs, "ring cos"));
     TRY(dalloc_t(p, &p->d_y32, p->npairs, "ring 1-cos"));
@@ -602,8 +617,7 @@ sl_status sl_plan_set_tile_cols(sl_plan *p, int tc) {
     if (tc == p->geom.tile_cols) return SL_OK;
     int dev_smem = 0;
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
-    const size_t need = std::max(std::max(interp_f32_tiled_smem_tc(p, tc), interp_adjoint_smem_tc(p, tc)),
-                                 p->precision == SL_DF64 ? interp_df_tiled_smem_tc(p, tc) : (size_t)0);
+    const size_t need = tile_smem_need(p, tc);
     if (dev_smem > 0 && need > (size_t)dev_smem)
         return set_error(SL_ERR_UNSUPPORTED, "tile width %d needs %zu bytes of shared memory (device: %d)", tc,
                          need, dev_smem);

@@ -50,10 +50,54 @@ struct InterpGeom {
     double phi_scale;             // nphi / (2 pi)
     unsigned long long phi_fix;   // round(nphi / (2 pi) 2^52)
     int tile_cols, ntr, ntc;      // tile grid: ntr = ceil((R+1)/kTileRows), ntc = ceil(nphi/tile_cols)
-    const double *offs64;         // [(R+1) * 4]: theta(i-1+a) - theta(i-1) per base row i
-    const float *rowtab32;        // [(R+1) * 8]: the same offsets, then wden, in float
-    const float2 *rowtab_df;      // [(R+1) * 8]: the same, as double-float (hi, lo)
+    const double *offs64;         // [(R+1) * p]: theta(i0+a) - theta(i0), i0 = i - p/2 + 1, per base row i
+    const float *rowtab32;        // [(R+1) * 2p]: the same offsets, then wden, in float
+    const float2 *rowtab_df;      // [(R+1) * 2p]: the same, as double-float (hi, lo)
 };
+
+// p-point Lagrange weights (separable interpolation, any even p).  theta:
+// nodes at offsets o[a] from the first stencil row (o[0] = 0), 1/prod(o_a - o_b)
+// in wd; d0 = theta - theta(first row).  phi: uniform nodes x_b = b - p/2 + 1
+// around the base column, f the fraction in [0, 1).  Products of all but one
+// factor through prefix and suffix products.
+template <int P, typename T>
+__device__ __forceinline__ void lagrange_theta(T d0, const T *o, const T *wd, T wt[P]) {
+    T d[P], pre[P + 1], suf[P + 1];
+#pragma unroll
+    for (int a = 0; a < P; ++a) d[a] = (a == 0) ? d0 : d0 - o[a];
+    pre[0] = T(1);
+    suf[P] = T(1);
+#pragma unroll
+    for (int a = 0; a < P; ++a) pre[a + 1] = pre[a] * d[a];
+#pragma unroll
+    for (int a = P - 1; a >= 0; --a) suf[a] = suf[a + 1] * d[a];
+#pragma unroll
+    for (int a = 0; a < P; ++a) wt[a] = wd[a] * (pre[a] * suf[a + 1]);
+}
+
+// 1 / prod_{c != b} (b - c) for uniform nodes: (-1)^(P-1-b) / (b! (P-1-b)!).
+template <int P>
+__host__ __device__ constexpr double uniform_inv_den(int b) {
+    double f = 1.0;
+    for (int c = 0; c < P; ++c)
+        if (c != b) f *= (double)(b - c);
+    return 1.0 / f;
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void lagrange_phi(T f, T wp[P]) {
+    T d[P], pre[P + 1], suf[P + 1];
+#pragma unroll
+    for (int b = 0; b < P; ++b) d[b] = f - T(b - P / 2 + 1);
+    pre[0] = T(1);
+    suf[P] = T(1);
+#pragma unroll
+    for (int b = 0; b < P; ++b) pre[b + 1] = pre[b] * d[b];
+#pragma unroll
+    for (int b = P - 1; b >= 0; --b) suf[b] = suf[b + 1] * d[b];
+#pragma unroll
+    for (int b = 0; b < P; ++b) wp[b] = (pre[b] * suf[b + 1]) * T(uniform_inv_den<P>(b));
+}
 
 // Work item v -> its tile: the last t with chunk_off[t] <= v.
 __device__ __forceinline__ int find_tile(const unsigned *chunk_off, int ntiles, unsigned v) {

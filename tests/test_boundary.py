@@ -52,7 +52,8 @@ def _desc(**kw):
 
 @pytest.mark.parametrize("bad,status", [
     (dict(lmax=0), -1), (dict(kmax=17), -1), (dict(kmax=-1), -1), (dict(ncomp=2), -1),
-    (dict(nphi=31), -1), (dict(nphi=4), -1), (dict(nphi=14), -2), (dict(interp_order=6), -2),
+    (dict(nphi=31), -1), (dict(nphi=4), -1), (dict(nphi=14), -2), (dict(interp_order=8), -2),
+    (dict(interp_order=3), -1), (dict(interp_order=-2), -1),
     (dict(precision=7), -1), (dict(nrings=3), -1),
 ])
 def test_bad_descriptions_are_rejected(lib, bad, status):

@@ -235,6 +235,50 @@ def test_df64_adjoint_is_the_fp64_adjoint(sl):
     assert rel_l2(outs[1][0], outs[0][0]) < 1e-13 and rel_l2(outs[1][1], outs[0][1]) < 1e-13
 
 
+@pytest.fixture(scope="module")
+def order_case(oracle_lib):
+    """Small configuration plus pointings at and near the poles, on rings and
+    with phi outside [0, 2 pi): ghost rows p/2 deep at both poles."""
+    c = CASES["small_healpix"]()
+    rt = c["rt"]
+    extra_th = np.array([0.0, math.pi, rt[0], rt[1], rt[2], rt[-1], 1e-9, math.pi - 1e-9, 0.5 * rt[0], rt[63]])
+    extra_ph = np.array([0.1, 6.0, -0.3, 7.5, 2 * math.pi - 1e-16, 100.0, 0.0, 3.0, 1.0, 0.25])
+    extra_ps = np.linspace(-3.0, 40.0, extra_th.size)
+    c["th"] = np.concatenate([c["th"], extra_th])
+    c["ph"] = np.concatenate([c["ph"], extra_ph])
+    c["ps"] = np.concatenate([c["ps"], extra_ps])
+    c["cube"] = oracle_lib.cube(c["sky"], c["beam"], rt, c["nphi"])
+    return c
+
+
+@pytest.mark.parametrize("p", [2, 6])
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("df64", TOL64), ("fp32", TOL32)])
+def test_interp_order_2_and_6(sl, oracle_lib, order_case, p, prec, tol):
+    c = order_case
+    ref = oracle_lib.interp(c["cube"], c["rt"], c["th"], c["ph"], c["ps"], p=p)
+    plan = sl.sidelobe_plan_create(c["L"], c["K"], c["rt"], c["nphi"], ncomp=1, precision=prec, interp_order=p)
+    maps = sl.synth_spin_maps(plan, _dev(c["sky"]), _dev(c["beam"]))
+    tod = sl.interp_tod(plan, maps, _dev(c["th"]), _dev(c["ph"]), _dev(c["ps"])).cpu().numpy()
+    err = rel_l2(tod, ref)
+    print("p=%d %s tod rel L2 %.2e" % (p, prec, err))
+    assert err < tol
+    if prec != "fp32":      # interpolation alone, on the oracle's cube
+        got = sl.interp_tod(plan, _dev(c["cube"]), _dev(c["th"]), _dev(c["ph"]), _dev(c["ps"])).cpu().numpy()
+        assert rel_l2(got, ref) < 1e-12
+
+
+@pytest.mark.parametrize("p", [2, 6])
+def test_adjoint_interp_order_2_and_6(sl, oracle_lib, order_case, p):
+    c = order_case
+    y = np.random.default_rng(8).standard_normal(c["th"].size)
+    ref = oracle_lib.interp_adjoint(y, c["rt"], c["nphi"], c["K"], c["th"], c["ph"], c["ps"], p=p)
+    plan = sl.sidelobe_plan_create(c["L"], c["K"], c["rt"], c["nphi"], ncomp=1, interp_order=p)
+    got = sl.adjoint_interp(plan, _dev(c["th"]), _dev(c["ph"]), _dev(c["ps"]), _dev(y)).cpu().numpy()
+    err = rel_l2(got, ref)
+    print("p=%d adjoint interp rel L2 %.2e" % (p, err))
+    assert err < 1e-12
+
+
 def test_tod_from_host_pipeline(sl):
     """The host-buffer end-to-end call (chunked upload / interpolation / download)
     gives the device path's TOD, for several chunk counts including ragged ones."""
