@@ -473,6 +473,99 @@ def detectors_arm(args):
             f.write(line + "\n")
 
 
+def multisky_arm(args):
+    """Cube builds of many skies sharing one beam (FP32 plan, LFI-like sizes):
+    synth_spin_maps_multi (tensor-core contraction) against the same skies one
+    by one through synth_spin_maps (CUDA-core contraction)."""
+    import torch
+
+    import paper_2201_03478_gb300 as sl
+    import workloads as W
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    cfg = W.config_lfi(with_pointings=False)
+    if args.lmax or args.nrings or args.nphi:   # smaller variants of the same workload (profiling)
+        Ls = args.lmax or cfg["lmax"]
+        cfg = dict(cfg, lmax=Ls, beam=W.beam_far_sidelobe(Ls, cfg["kmax"], seed=1),
+                   ring_theta=W.equiangular_ring_theta(args.nrings or cfg["ring_theta"].size),
+                   nphi=args.nphi or cfg["nphi"])
+    L, K, rt, nphi = cfg["lmax"], cfg["kmax"], cfg["ring_theta"], cfg["nphi"]
+    nsky = args.nsky
+    skies = torch.from_numpy(np.stack([W.sky_polarised(L, seed=s) for s in range(nsky)])).to(device)
+    beam = torch.from_numpy(cfg["beam"]).to(device)
+    plan = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=3, precision="fp32", device=local)
+    maps = torch.empty((nsky,) + plan.maps_shape(), dtype=torch.complex64, device=device)
+    one = torch.empty(plan.maps_shape(), dtype=torch.complex64, device=device)
+    stream = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    def singles():
+        for s in range(nsky):
+            sl.synth_spin_maps(plan, skies[s], beam, one)
+
+    ms_single = timed(singles)
+    plan.enable_timing(True)
+    plan.kernel_stats(reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms_multi = timed(lambda: sl.synth_spin_maps_multi(plan, skies, beam, maps))
+    clk = clocks.stop()
+    stats = plan.kernel_stats(reset=True)
+    plan.enable_timing(False)
+    plan.sync()
+    errs = []
+    for s in (0, nsky - 1):
+        sl.synth_spin_maps(plan, skies[s], beam, one)
+        errs.append(float(torch.linalg.vector_norm(maps[s] - one) / torch.linalg.vector_norm(one)))
+    mma = stats.get("lcontract_mma", (1, 0.0))
+    mma_ms = mma[1] / max(1, mma[0])
+    # dense tile work the tensor cores execute per launch: three TF32 products of
+    # (128 rows x N columns x 32 l) per CTA chunk; counted from the plan's recurrence volume
+    nsg = min(32, nsky)
+    nsg = (nsg + 3) // 4 * 4
+    n_cols = 4 * nsg * ((nsky + nsg - 1) // nsg)
+    mma_flops = 3 * 2.0 * float(plan.sizes()["lsteps"]) * n_cols
+    out = {
+        "metric": "sky cubes/s (lmax=1024, kmax=16, T/E/B, 1024x2048), %d skies sharing one beam" % nsky,
+        "value": nsky / (ms_multi / 1e3), "unit": "cubes/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_multi, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (3xTF32 tensor-core contraction, FP32 accumulation)",
+        "data": "synthetic (seeded T/E/B skies, far-sidelobe beam)",
+        "config": {"workload": "multi-sky cube build, %d skies" % nsky, "lmax": L, "kmax": K, "nrings": rt.size,
+                   "nphi": nphi, "precision": "fp32"},
+        "single_sky_path": {"value": nsky / (ms_single / 1e3), "ms_per_step": ms_single,
+                            "note": "synth_spin_maps once per sky (CUDA-core contraction)"},
+        "speedup_vs_single_sky_path": ms_single / ms_multi,
+        "cube_rel_l2_vs_single_sky_path": errs,
+        "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in stats.items()},
+        "tensor": {"kernel": "k_lcontract_mma", "avg_ms": mma_ms,
+                   "tf32_flops_per_launch": mma_flops,
+                   "achieved_tflops": mma_flops / (mma_ms / 1e3) / 1e12 if mma_ms > 0 else None,
+                   "note": "dense TF32 work of the visited (ring, m, k, sign, l) volume; the zero rows of "
+                           "not-yet-started rings inside a chunk are executed too"},
+        "gpu_launches": int(sum(v[0] for v in stats.values()) / args.steps),
+        "clocks": clk,
+    }
+    sl.plan_destroy(plan)
+    print(json.dumps(out), flush=True)
+
+
 # ncu-measured DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
 # at full size for the current kernels (profiles/launches_lfi_*.txt).
 TRAFFIC = {
@@ -565,11 +658,12 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["fp64", "fp32", "df64"], default="fp64")
-    ap.add_argument("--workload", choices=["lfi", "highres", "detectors"], default="lfi",
+    ap.add_argument("--workload", choices=["lfi", "highres", "detectors", "multisky"], default="lfi",
                     help="lfi: T/E/B, lmax 1024, kmax 16, scan (the headline); "
                          "highres: lmax 2048, kmax 32, 2048 x 4096 rings, uniform pointings (precision variant); "
                          "detectors: 22 detectors of uneven lmax/kmax in one CUDA graph (batch variant)")
     ap.add_argument("--ndet", type=int, default=22, help="detectors of the batch workload")
+    ap.add_argument("--nsky", type=int, default=32, help="skies of the multi-sky workload")
     ap.add_argument("--tile-cols", type=int, default=0, help="sort-tile width (8, 16, 32; 0: the plan's default)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--n", type=float, default=0, help="pointings per GPU (default 1e8; 2e8 for highres)")
@@ -598,6 +692,8 @@ def main(argv=None):
         reference_arm(args)
     elif args.workload == "detectors":
         detectors_arm(args)
+    elif args.workload == "multisky":
+        multisky_arm(args)
     else:
         gpu_arm(args)
 

@@ -117,6 +117,23 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *desc);
  * nphi, which is exact at the nodes. */
 sl_status synth_spin_maps(sl_plan *plan, const double *sky, const double *beam, void *maps);
 
+/* Step 1 for many skies sharing one beam (no counterpart in the paper, which
+ * convolves one sky at a time; sampling sky posteriors convolves many sky
+ * realisations with one beam): for s < nsky, maps[s] is what synth_spin_maps
+ * gives for sky[s] and beam.  FP32 plans only (else SL_ERR_UNSUPPORTED): the
+ * l-contraction of all skies runs per (m, k) as one tensor-core tile product
+ * (tcgen05; the rescaled Wigner values and the sky x beam columns are split
+ * into TF32 high and low parts, three products, FP32 accumulation in tensor
+ * memory), with the accuracy of the FP32 path.
+ *   sky  : device double [nsky][ncomp][nalm][2], the packing above per sky;
+ *   beam : device, the packing above (shared by every sky);
+ *   maps : device float2 [nsky][nrings][nphi][kmax+1], fully overwritten.
+ * The plan grows scratch for FP32 skies and per-sky G on the first call with a
+ * larger nsky (8 (ncomp nalm + (kmax+1) nrings (2 lmax+1)) bytes per sky).  A
+ * bounded wait inside the kernel that expires is reported as SL_ERR_TIMEOUT
+ * by the next sl_plan_sync. */
+sl_status synth_spin_maps_multi(sl_plan *plan, int nsky, const double *sky, const double *beam, void *maps);
+
 /* Step 2 (Sect. 2.1, conjugate pairs): for i < n,
  *   tod[i] = Re S_0 + 2 sum_{k>=1} Re(e^{ik psi_i} S_k),
  * S_k the p-point Lagrange interpolation of F_k at (theta_i, phi_i).

@@ -21,7 +21,8 @@ STATUS_NAMES = {0: "SL_OK", -1: "SL_ERR_ARG", -2: "SL_ERR_UNSUPPORTED", -3: "SL_
 EXPORTS = ["sidelobe_plan_create", "synth_spin_maps", "interp_tod", "adjoint_tod", "adjoint_interp",
            "adjoint_synth", "interp_tod_noalloc", "plan_destroy", "sl_plan_get_sizes", "sl_plan_set_stream", "sl_plan_sync",
            "sl_plan_enable_timing", "sl_plan_kernel_stats", "sl_plan_reserve", "sl_plan_set_tile_cols",
-           "sl_batch_create", "sl_batch_run", "sl_batch_get_info", "sl_batch_destroy", "sl_last_error"]
+           "sl_batch_create", "sl_batch_run", "sl_batch_get_info", "sl_batch_destroy", "synth_spin_maps_multi",
+           "sl_last_error"]
 SL_BATCH_AUTOTUNE = 1
 
 
@@ -75,6 +76,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     sig = {
         "sidelobe_plan_create": (I, [ctypes.POINTER(P), ctypes.POINTER(PlanDesc)]),
         "synth_spin_maps": (I, [P, P, P, P]),
+        "synth_spin_maps_multi": (I, [P, I, P, P, P]),
         "interp_tod": (I, [P, P, P, P, P, I64, P]),
         "adjoint_tod": (I, [P, P, P, P, P, I64, P, P, P, P, I]),
         "adjoint_interp": (I, [P, P, P, P, P, I64, P]),

@@ -140,6 +140,26 @@ def synth_spin_maps(plan: Plan, sky, beam, maps=None):
     return maps
 
 
+def synth_spin_maps_multi(plan: Plan, sky, beam, maps=None):
+    """Cubes of several skies that share one beam (FP32 plans; the l-contraction
+    runs on the tensor cores).  sky: complex128 [nsky, ncomp, nalm]; returns
+    complex64 maps [nsky, R, nphi, K+1]."""
+    if plan.precision != SL_FP32:
+        raise ValueError("synth_spin_maps_multi needs an FP32 plan")
+    if not isinstance(sky, torch.Tensor) or sky.dim() != 3:
+        raise ValueError("sky must be a [nsky, ncomp, nalm] tensor")
+    nsky = sky.shape[0]
+    _dev_tensor(sky, torch.complex128, plan.device, "sky", (nsky, plan.ncomp, plan.nalm))
+    beam = _dev_tensor(beam, torch.complex128, plan.device, "beam", (plan.ncomp, plan.kmax + 1, plan.lmax + 1))
+    shape = (nsky,) + plan.maps_shape()
+    if maps is None:
+        maps = torch.empty(shape, dtype=torch.complex64, device=sky.device)
+    _dev_tensor(maps, torch.complex64, plan.device, "maps", shape)
+    plan._sync_stream()
+    check(_lib.load().synth_spin_maps_multi(plan.ptr, int(nsky), _ptr(sky), _ptr(beam), _ptr(maps)))
+    return maps
+
+
 def _ptg(plan, theta, phi, psi):
     n = theta.numel()
     for name, t in (("theta", theta), ("phi", phi), ("psi", psi)):

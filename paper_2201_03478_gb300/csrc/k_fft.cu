@@ -152,6 +152,9 @@ __global__ void __launch_bounds__(256) k_ringfft_synth(int L, int K, int R, int 
     C *buf1 = buf0 + N;
     const int k = blockIdx.x % (K + 1);
     const int r = blockIdx.x / (K + 1);
+    // blockIdx.y: sky of a multi-sky build (consecutive G and cube blocks)
+    G += (int64_t)blockIdx.y * (K + 1) * R * (2 * L + 1);
+    maps += (int64_t)blockIdx.y * R * N * (K + 1);
     const C *g = G + ((int64_t)k * R + r) * (2 * L + 1);
     for (int q = threadIdx.x; q < N; q += blockDim.x) {
         // smallest m >= -L with m = q (mod N)
@@ -194,25 +197,27 @@ static Radices radices_of(const sl_plan *p) {
     return r;
 }
 
-sl_status launch_ringfft_synth(sl_plan *p, void *maps) {
-    const unsigned nblk = (unsigned)((p->K + 1) * p->R);
+sl_status launch_ringfft_synth_from(sl_plan *p, const void *G, int nsky, void *maps) {
+    const dim3 nblk((unsigned)((p->K + 1) * p->R), (unsigned)nsky);
     int slot;
     if (plan_wide(p->precision)) {
         const size_t sm = 2 * (size_t)p->nphi * sizeof(double2);
         cudaFuncSetAttribute(k_ringfft_synth<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         slot = timing_begin(p, "ringfft_f64");
         k_ringfft_synth<double><<<nblk, 256, sm, p->stream>>>(p->L, p->K, p->R, p->nphi, radices_of(p),
-                                                              (const double2 *)p->d_G, p->d_tw64, (double2 *)maps);
+                                                              (const double2 *)G, p->d_tw64, (double2 *)maps);
     } else {
         const size_t sm = 2 * (size_t)p->nphi * sizeof(float2);
         cudaFuncSetAttribute(k_ringfft_synth<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         slot = timing_begin(p, "ringfft_f32");
         k_ringfft_synth<float><<<nblk, 256, sm, p->stream>>>(p->L, p->K, p->R, p->nphi, radices_of(p),
-                                                             (const float2 *)p->d_G, p->d_tw32, (float2 *)maps);
+                                                             (const float2 *)G, p->d_tw32, (float2 *)maps);
     }
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_ringfft_synth launch");
 }
+
+sl_status launch_ringfft_synth(sl_plan *p, void *maps) { return launch_ringfft_synth_from(p, p->d_G, 1, maps); }
 
 sl_status launch_ringdft_adjoint(sl_plan *p, const double2 *fbar) {
     const unsigned nblk = (unsigned)((p->K + 1) * p->R);

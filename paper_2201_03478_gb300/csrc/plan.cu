@@ -280,6 +280,9 @@ void plan_destroy(sl_plan *p) {
     dfree(p->d_Abar);
     dfree(p->d_offs64);
     dfree(p->d_rowtab32);
+    dfree(p->d_skym32);
+    dfree(p->d_Gm);
+    dfree(p->d_err);
     dfree(p->d_rowtab_df);
     dfree(p->sort.hist);
     dfree(p->sort.cursor);
@@ -639,7 +642,47 @@ sl_status sl_plan_set_stream(sl_plan *p, void *stream) {
 sl_status sl_plan_sync(sl_plan *p) {
     sl_status st = enter(p);
     if (st != SL_OK) return st;
-    return cuda_check(cudaStreamSynchronize(p->stream), "stream synchronize");
+    if ((st = cuda_check(cudaStreamSynchronize(p->stream), "stream synchronize")) != SL_OK) return st;
+    if (p->d_err) {
+        int flag = 0;
+        if ((st = cuda_check(cudaMemcpy(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag")) != SL_OK)
+            return st;
+        if (flag) {
+            cudaMemset(p->d_err, 0, sizeof(int));
+            return set_error(SL_ERR_TIMEOUT, "a bounded wait of the tensor-core contraction expired");
+        }
+    }
+    return SL_OK;
+}
+
+sl_status synth_spin_maps_multi(sl_plan *p, int nsky, const double *sky, const double *beam, void *maps) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if (p->precision != SL_FP32)
+        return set_error(SL_ERR_UNSUPPORTED, "synth_spin_maps_multi: FP32 plans only (the tensor-core path)");
+    if (nsky < 1) return set_error(SL_ERR_ARG, "synth_spin_maps_multi: nsky=%d < 1", nsky);
+    if (!sky || !beam || !maps) return set_error(SL_ERR_ARG, "synth_spin_maps_multi: NULL buffer");
+    if (nsky > p->msky_cap) {
+        if (p->batch_refs > 0) return set_error(SL_ERR_ARG, "synth_spin_maps_multi: the plan is held by a batch graph");
+        cudaStreamSynchronize(p->stream);
+        const int64_t gsky = (int64_t)(p->K + 1) * p->R * (2 * p->L + 1);
+        if (p->msky_cap > 0)
+            p->bytes_held -= (int64_t)p->msky_cap * (int64_t)sizeof(float2) * (p->ncomp * p->nalm + gsky);
+        dfree(p->d_skym32);
+        dfree(p->d_Gm);
+        p->d_skym32 = nullptr;
+        p->d_Gm = nullptr;
+        p->msky_cap = 0;
+        if ((st = dalloc_t(p, &p->d_skym32, (size_t)nsky * p->ncomp * p->nalm, "FP32 skies")) != SL_OK) return st;
+        if ((st = dalloc_t(p, &p->d_Gm, (size_t)nsky * gsky, "multi-sky G")) != SL_OK) return st;
+        p->msky_cap = nsky;
+    }
+    if (!p->d_err) {
+        if ((st = dalloc_t(p, &p->d_err, 1, "error flag")) != SL_OK) return st;
+        if ((st = cuda_check(cudaMemset(p->d_err, 0, sizeof(int)), "error flag")) != SL_OK) return st;
+    }
+    if ((st = launch_lcontract_mma(p, nsky, sky, beam, p->d_skym32, p->d_Gm, p->d_err)) != SL_OK) return st;
+    return launch_ringfft_synth_from(p, p->d_Gm, nsky, maps);
 }
 
 sl_status sl_plan_enable_timing(sl_plan *p, int enable) {

@@ -208,6 +208,12 @@ struct sl_plan {
     int64_t sort_cap = 0;
 
     int64_t bytes_held = 0;
+    // multi-sky builds (FP32 plans): FP32 skies, per-sky G, and the device flag of
+    // the tensor-core kernel's bounded waits; grown on demand
+    float2 *d_skym32 = nullptr;
+    float2 *d_Gm = nullptr;
+    int *d_err = nullptr;
+    int msky_cap = 0;
     // number of captured batch graphs that hold pointers into this plan's
     // scratch: while > 0 nothing may be reallocated (the graphs would dangle)
     int batch_refs = 0;
@@ -236,6 +242,12 @@ sl_status launch_advance(sl_plan *p, double thr, int *ls, double2 *st64, float2 
 sl_status count_lsteps(sl_plan *p, int64_t *out);
 sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam);
 sl_status launch_ringfft_synth(sl_plan *p, void *maps);
+// nsky cubes from nsky consecutive G blocks (gridDim.y = nsky)
+sl_status launch_ringfft_synth_from(sl_plan *p, const void *G, int nsky, void *maps);
+// Multi-sky spin Legendre step on the tensor cores (k_multisky.cu), FP32 plans.
+sl_status launch_lcontract_mma(sl_plan *p, int nsky, const double *sky, const double *beam, float2 *sky32,
+                               float2 *G, int *err);
+int lcontract_mma_group(int nsky);
 // Sort of n pointings into b: fine (cell) or coarse (tile) keys, FP64 or FP32
 // stencil records; with_chunks also builds the adjoint's per-tile work items.
 int64_t sort_nkeys(const sl_plan *p, int fine);
