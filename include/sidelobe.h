@@ -228,8 +228,15 @@ sl_status sl_plan_reserve(sl_plan *plan, int64_t n);
  * shared memory. */
 sl_status sl_plan_set_tile_cols(sl_plan *plan, int tile_cols);
 
-/* Synchronises the plan's stream; reports device faults as SL_ERR_CUDA. */
+/* Synchronises the plan's stream; reports device faults as SL_ERR_CUDA and an
+ * expired bounded wait inside a kernel (synth_spin_maps_multi) as
+ * SL_ERR_TIMEOUT (the flag is then cleared; the context stays usable). */
 sl_status sl_plan_sync(sl_plan *plan);
+
+/* Failure-detection self-test: enqueues a kernel whose bounded wait (50 ms) on
+ * a barrier that nothing signals must expire and raise the plan's error flag,
+ * so that the next sl_plan_sync returns SL_ERR_TIMEOUT. */
+sl_status sl_plan_selftest_timeout(sl_plan *plan);
 
 /* Per-kernel timing.  While enabled, every launch is bracketed by CUDA events
  * on the plan's stream.  sl_plan_kernel_stats fills, for up to max entries,

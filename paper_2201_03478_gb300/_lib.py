@@ -22,7 +22,7 @@ EXPORTS = ["sidelobe_plan_create", "synth_spin_maps", "interp_tod", "adjoint_tod
            "adjoint_synth", "interp_tod_noalloc", "plan_destroy", "sl_plan_get_sizes", "sl_plan_set_stream", "sl_plan_sync",
            "sl_plan_enable_timing", "sl_plan_kernel_stats", "sl_plan_reserve", "sl_plan_set_tile_cols",
            "sl_batch_create", "sl_batch_run", "sl_batch_get_info", "sl_batch_destroy", "synth_spin_maps_multi",
-           "sl_last_error"]
+           "sl_plan_selftest_timeout", "sl_last_error"]
 SL_BATCH_AUTOTUNE = 1
 
 
@@ -86,6 +86,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "sl_plan_get_sizes": (I, [P, ctypes.POINTER(PlanSizes)]),
         "sl_plan_set_stream": (I, [P, P]),
         "sl_plan_sync": (I, [P]),
+        "sl_plan_selftest_timeout": (I, [P]),
         "sl_plan_enable_timing": (I, [P, I]),
         "sl_plan_kernel_stats": (I, [P, ctypes.POINTER(KernelStat), I, ctypes.POINTER(I), I]),
         "sl_plan_reserve": (I, [P, I64]),

@@ -33,7 +33,7 @@ namespace sl {
 constexpr int kMsRows = 128;      // ring pairs per CTA (MMA M)
 constexpr int kMsLC = 32;         // l per chunk
 constexpr int kMsThreads = 256;
-constexpr long kMsSpin = 1L << 24;   // bound of every mbarrier wait (try_wait iterations)
+constexpr unsigned long long kMsWaitNs = 1000000000ull;   // bound of every mbarrier wait: 1 s
 
 struct MsArgs {
     int L, K, ncomp, R, npairs, nrc;     // nrc: ring chunks of 128 pairs
@@ -65,13 +65,24 @@ __device__ __forceinline__ uint32_t ms_idesc(int m, int n) {
 // float index of element (row, k) of a [rows][32] tile in that layout
 __device__ __forceinline__ int ms_sw(int row, int k) { return row * 32 + ((((k >> 2) ^ (row & 7))) << 2) + (k & 3); }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    uint32_t done = 0;
-    for (long it = 0; it < kMsSpin && !done; ++it)
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the completion of the mbarrier phase of the given parity, for at
+// most limit_ns of wall time; false when the limit expired.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns = kMsWaitNs) {
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+        uint32_t done;
         asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, q;\n\t}"
                      : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-    return done != 0;
+        if (done) return true;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
 }
 
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
@@ -363,6 +374,20 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_lcontract_mma(const MsArgs a)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(ncols) : "memory");
+}
+
+// Failure-detection self-test: a wait on an mbarrier that nothing signals
+// must expire and raise the error flag (the context stays usable).
+__global__ void k_wait_probe(int *err, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar)) : "memory");
+    if (!mbar_wait(smem_u32(&bar), 0, limit_ns)) atomicExch(err, 1);
+}
+
+sl_status launch_wait_probe(sl_plan *p, int *err) {
+    k_wait_probe<<<1, 32, 0, p->stream>>>(err, 50000000ull);
+    return cuda_check(cudaGetLastError(), "k_wait_probe launch");
 }
 
 __global__ void k_to_f32_ms(const double2 *__restrict__ in, float2 *__restrict__ out, int64_t n) {

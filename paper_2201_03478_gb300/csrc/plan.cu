@@ -655,6 +655,16 @@ sl_status sl_plan_sync(sl_plan *p) {
     return SL_OK;
 }
 
+sl_status sl_plan_selftest_timeout(sl_plan *p) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if (!p->d_err) {
+        if ((st = dalloc_t(p, &p->d_err, 1, "error flag")) != SL_OK) return st;
+        if ((st = cuda_check(cudaMemset(p->d_err, 0, sizeof(int)), "error flag")) != SL_OK) return st;
+    }
+    return launch_wait_probe(p, p->d_err);
+}
+
 sl_status synth_spin_maps_multi(sl_plan *p, int nsky, const double *sky, const double *beam, void *maps) {
     sl_status st = enter(p);
     if (st != SL_OK) return st;

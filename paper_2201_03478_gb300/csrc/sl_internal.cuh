@@ -248,6 +248,7 @@ sl_status launch_ringfft_synth_from(sl_plan *p, const void *G, int nsky, void *m
 sl_status launch_lcontract_mma(sl_plan *p, int nsky, const double *sky, const double *beam, float2 *sky32,
                                float2 *G, int *err);
 int lcontract_mma_group(int nsky);
+sl_status launch_wait_probe(sl_plan *p, int *err);
 // Sort of n pointings into b: fine (cell) or coarse (tile) keys, FP64 or FP32
 // stencil records; with_chunks also builds the adjoint's per-tile work items.
 int64_t sort_nkeys(const sl_plan *p, int fine);

@@ -63,3 +63,22 @@ def test_multisky_rejects_fp64_plans():
     from paper_2201_03478_gb300 import _lib
     st = _lib.load().synth_spin_maps_multi(plan.ptr, 2, sky.data_ptr(), beam.data_ptr(), sky.data_ptr())
     assert st == -2
+
+
+def test_bounded_wait_expires_and_is_reported():
+    """A device-side wait that nothing satisfies gives up after its bound, raises
+    the plan's flag and is reported as SL_ERR_TIMEOUT; the context stays usable."""
+    import paper_2201_03478_gb300 as sl
+    from paper_2201_03478_gb300 import _lib
+    L, K, rt, nphi, ncomp, nsky = CASES["small_healpix_5"]
+    plan = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=1, precision="fp32")
+    lib = _lib.load()
+    assert lib.sl_plan_selftest_timeout(plan.ptr) == 0
+    assert lib.sl_plan_sync(plan.ptr) == -5
+    assert b"bounded wait" in lib.sl_last_error()
+    assert lib.sl_plan_sync(plan.ptr) == 0           # the flag was cleared
+    skies = torch.from_numpy(_skies(L, 1, 2, 7)).cuda()
+    beam = torch.from_numpy(W.beam_gaussian_taper(L, K, 20.0, seed=3)).cuda()
+    maps = sl.synth_spin_maps_multi(plan, skies, beam)
+    plan.sync()
+    assert torch.isfinite(torch.view_as_real(maps)).all()
