@@ -12,15 +12,18 @@
 // product is a matrix-vector product; with many skies it is a dense tile
 // product and runs on tcgen05:
 //
-//   * CTA = (m, k, sign, 128 ring pairs, group of up to 64 skies), M = 128,
-//     N = 4 x skies, K = l in chunks of 32 (one 128-byte swizzle row of TF32);
+//   * CTA = (m, k, sign, 128 ring pairs, group of up to 32 skies), M = 128,
+//     N = 4 x skies, K = l in chunks of 32;
 //   * W and V are split into TF32 high and low parts and multiplied as
 //     hi x hi + hi x lo + lo x hi (three MMAs, FP32 accumulation in tensor
 //     memory): ~2^-21 relative per product, the accuracy of the FP32 path;
-//   * both operands live in shared memory, K-major with the 128-byte swizzle,
-//     double buffered: while the MMAs of one chunk run, the CTA generates the
-//     next chunk's W rows and V columns, from coefficients, sky and beam values
-//     that cp.async copies have staged in shared memory two chunks ahead;
+//   * W lives in tensor memory: the thread that owns ring pair r runs its
+//     recurrence and writes its row (TMEM lane r) with tcgen05.st; V lives in
+//     shared memory, K-major with the 128-byte swizzle, built by all warps
+//     from coalesced sky and beam loads; both double buffered, so that while
+//     the MMAs of one chunk run the CTA builds the next chunk; the chunk's
+//     recurrence coefficients are staged by cp.async one chunk ahead;
+//   * 256 TMEM columns and 33 KB of shared memory per CTA: two CTAs per SM;
 //   * one thread issues the MMAs and commits them to an mbarrier per buffer;
 //     every wait is bounded and sets an error flag (the CTA then stops,
 //     waits for its MMAs with a bound and frees its tensor memory).
@@ -85,37 +88,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
     }
 }
 
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(smem_u32(dst)), "l"(src) : "memory");
-}
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int NPEND>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(NPEND) : "memory"); }
-
-// Staged inputs of one chunk: sky [nsg][ncomp][32], beam [ncomp][32], coefficients [32].
-struct MsStage {
-    float2 *sky, *beam;
-    RTab32 *tab;
-};
-
-// The sky tile's rows (sky, X) are consecutive rows of the [nsky][ncomp][nalm]
-// array: warp w copies rows w, w + 8, ..., lane = l - c0.
-__device__ __forceinline__ void ms_prefetch(const MsArgs &a, const MsStage &st, const float2 *sky_rows,
-                                            int row_limit, const float2 *beam_k, const RTab32 *tab, int c0) {
-    const int lane = threadIdx.x & 31, l = c0 + lane;
-    if (l <= a.L) {
-        const int rows = a.nsg * a.ncomp;
-        for (int r = threadIdx.x >> 5; r < rows; r += kMsThreads / 32)
-            if (r < row_limit) cp_async8(st.sky + r * 32 + lane, sky_rows + (int64_t)r * a.nalm + l);
-        const int X = threadIdx.x >> 5;
-        if (X < a.ncomp) cp_async8(st.beam + X * 32 + lane, beam_k + (int64_t)X * (a.K + 1) * (a.L + 1) + l);
-        if (threadIdx.x < 32) cp_async16(st.tab + lane, tab + l);
-    }
-    cp_async_commit();
-}
 
 // TF32 split: hi keeps the 19 bits the tensor core reads, lo = x - hi (exact)
 __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
@@ -146,9 +124,15 @@ __device__ __forceinline__ void ms_write_two(const MsArgs &a, float2 *G, int m, 
     }
 }
 
-__global__ void __launch_bounds__(kMsThreads, 1) k_lcontract_mma(const MsArgs a) {
+// TMEM columns of one CTA: the accumulator D in [0, N), the W operand (TF32
+// high and low parts, two buffers of 32 columns each) from column 128.
+constexpr int kMsTmemCols = 256;
+constexpr int kMsAcol = 128;
+
+__global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a) {
     extern __shared__ unsigned char ms_raw[];
     __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(16) RTab32 tabs[2][kMsLC];   // this and the next chunk's coefficients
     __shared__ uint32_t tmem_base;
     __shared__ int s_lmin, s_fail;
 
@@ -166,20 +150,12 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_lcontract_mma(const MsArgs a)
     const int64_t moff = (int64_t)m * (2 * a.L + 1 - m) / 2;
     const RTab32 *tab = a.tab32 + (int64_t)k * a.nalm + moff;
 
-    // operand buffers, 1024-byte aligned: per buffer A_hi, A_lo [128][32], B_hi, B_lo [N][32]
+    // V operand buffers in shared memory, 1024-byte aligned: per buffer B_hi, B_lo [N][32]
     const uint32_t raw = smem_u32(ms_raw);
     float *base = reinterpret_cast<float *>(ms_raw + ((1024u - (raw & 1023u)) & 1023u));
-    const int afl = kMsRows * kMsLC, bfl = N * kMsLC;
-    float *buf[2] = {base, base + 2 * afl + 2 * bfl};
-    float2 *const stage0 = reinterpret_cast<float2 *>(base + 4 * afl + 4 * bfl);
-    const int nsky_el = a.nsg * a.ncomp * 32, nbeam_el = a.ncomp * 32;
-    const int stage_el = nsky_el + nbeam_el + 64;   // 32 RTab32 = 64 float2
-    auto stage_of = [&](int q) {
-        float2 *sp = stage0 + q * stage_el;
-        return MsStage{sp, sp + nsky_el, reinterpret_cast<RTab32 *>(sp + nsky_el + nbeam_el)};
-    };
+    const int bfl = N * kMsLC;
 
-    // this thread's recurrence (threads 0..127 own the rows)
+    // this thread's recurrence (threads 0..127 own the rows = TMEM lanes)
     const int pair = rc * kMsRows + tid;
     float y = 0.f, D = 0.f, yc = 0.f;
     int ls = a.L + 1;
@@ -209,11 +185,9 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_lcontract_mma(const MsArgs a)
         return;
     }
     const int nchunks = (a.L - lstart + kMsLC) / kMsLC;
-    int ncols = 32;
-    while (ncols < N) ncols <<= 1;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&tmem_base)), "r"(ncols) : "memory");
+                     :: "r"(smem_u32(&tmem_base)), "r"(kMsTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
@@ -221,96 +195,120 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_lcontract_mma(const MsArgs a)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (tid < kMsLC && lstart + tid <= a.L) cp_async16(&tabs[0][tid], tab + lstart + tid);
+    cp_async_commit();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
     const uint32_t idesc = ms_idesc(kMsRows, N);
+    const float2 *beam_k = a.beam + (int64_t)k * (a.L + 1);
+    const int lmin = max(m, k);
 
     int issued = -1;    // last chunk whose MMAs were committed
-    const float2 *sky_rows = a.sky + (int64_t)s_first * a.ncomp * a.nalm + moff;
-    const int row_limit = min(a.nsg, a.nsky - s_first) * a.ncomp;
-    const float2 *beam_k = a.beam + (int64_t)k * (a.L + 1);
-    ms_prefetch(a, stage_of(0), sky_rows, row_limit, beam_k, tab, lstart);
-    ms_prefetch(a, stage_of(1), sky_rows, row_limit, beam_k, tab, lstart + kMsLC);
     for (int c = 0; c < nchunks; ++c) {
         const int bi = c & 1;
-        // stage chunk c + 2 (its stage was last read by chunk c - 1, before the
-        // barrier that preceded that chunk's MMAs; past lmax the group is empty),
-        // then wait for chunk c's copies (two newer groups may stay in flight)
-        ms_prefetch(a, stage_of((c + 2) % 3), sky_rows, row_limit, beam_k, tab, lstart + (c + 2) * kMsLC);
-        cp_async_wait<2>();
+        const int c0 = lstart + c * kMsLC;
+        // the next chunk's coefficients (their buffer was last read by chunk c - 1)
+        if (tid < kMsLC && c0 + kMsLC + tid <= a.L) cp_async16(&tabs[bi ^ 1][tid], tab + c0 + kMsLC + tid);
+        cp_async_commit();
+        cp_async_wait<1>();
         if (c >= 2 && !mbar_wait(smem_u32(&mbar[bi]), ((c - 2) >> 1) & 1)) s_fail = 1;
         __syncthreads();
         if (s_fail) break;
-        float *Ah = buf[bi], *Al = Ah + afl, *Bh = Al + afl, *Bl = Bh + bfl;
-        const MsStage st = stage_of(c % 3);
-        const int c0 = lstart + c * kMsLC;
+        const RTab32 *tb = tabs[bi];
         if (tid < kMsRows) {
-            // W row: y_l for l in [c0, c0 + 32), zero before the ring's start
-            float w[kMsLC];
+            // W row in tensor memory: y_l for l in [c0, c0 + 32), zero before the ring's start
+            uint32_t hv[kMsLC], lv[kMsLC];
 #pragma unroll
             for (int i = 0; i < kMsLC; ++i) {
                 const int l = c0 + i;
                 float v = 0.f;
                 if (l >= ls && l <= a.L) {
                     v = y;
-                    const RTab32 t = st.tab[i];
+                    const RTab32 t = tb[i];
                     D = fmaf(fmaf(-t.a, yc, neg ? t.cm : t.cp), y, D);
                     y += D;
                 }
-                w[i] = v;
+                float h, lo;
+                tf32_split(v, h, lo);
+                hv[i] = __float_as_uint(h);
+                lv[i] = __float_as_uint(lo);
             }
-#pragma unroll
-            for (int q = 0; q < kMsLC / 4; ++q) {
-                float4 h, lo;
-                tf32_split(w[4 * q + 0], h.x, lo.x);
-                tf32_split(w[4 * q + 1], h.y, lo.y);
-                tf32_split(w[4 * q + 2], h.z, lo.z);
-                tf32_split(w[4 * q + 3], h.w, lo.w);
-                *reinterpret_cast<float4 *>(Ah + ms_sw(tid, 4 * q)) = h;
-                *reinterpret_cast<float4 *>(Al + ms_sw(tid, 4 * q)) = lo;
-            }
+            const uint32_t arow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kMsAcol + bi * 64);
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+                         "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                         "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+                         :: "r"(arow), "r"(hv[0]), "r"(hv[1]), "r"(hv[2]), "r"(hv[3]), "r"(hv[4]), "r"(hv[5]),
+                            "r"(hv[6]), "r"(hv[7]), "r"(hv[8]), "r"(hv[9]), "r"(hv[10]), "r"(hv[11]), "r"(hv[12]),
+                            "r"(hv[13]), "r"(hv[14]), "r"(hv[15]), "r"(hv[16]), "r"(hv[17]), "r"(hv[18]),
+                            "r"(hv[19]), "r"(hv[20]), "r"(hv[21]), "r"(hv[22]), "r"(hv[23]), "r"(hv[24]),
+                            "r"(hv[25]), "r"(hv[26]), "r"(hv[27]), "r"(hv[28]), "r"(hv[29]), "r"(hv[30]),
+                            "r"(hv[31]) : "memory");
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+                         "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                         "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+                         :: "r"(arow + 32), "r"(lv[0]), "r"(lv[1]), "r"(lv[2]), "r"(lv[3]), "r"(lv[4]), "r"(lv[5]),
+                            "r"(lv[6]), "r"(lv[7]), "r"(lv[8]), "r"(lv[9]), "r"(lv[10]), "r"(lv[11]), "r"(lv[12]),
+                            "r"(lv[13]), "r"(lv[14]), "r"(lv[15]), "r"(lv[16]), "r"(lv[17]), "r"(lv[18]),
+                            "r"(lv[19]), "r"(lv[20]), "r"(lv[21]), "r"(lv[22]), "r"(lv[23]), "r"(lv[24]),
+                            "r"(lv[25]), "r"(lv[26]), "r"(lv[27]), "r"(lv[28]), "r"(lv[29]), "r"(lv[30]),
+                            "r"(lv[31]) : "memory");
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         }
-        // V columns: item (sky s, four consecutive l), the four values of this sign each
-        const int lmin = max(m, k);
-        for (int e = tid; e < a.nsg * (kMsLC / 4); e += kMsThreads) {
-            const int s = e >> 3, q = e & 7;
-            float v[4][4];
+        // V columns: lane = l - c0, warp w builds skies w, w + 8, ...; reads coalesced over l
+        {
+            float *Bh = base + bi * 2 * bfl, *Bl = Bh + bfl;
+            const int i = lane, l = c0 + i;
+            const bool live = l <= a.L && l >= lmin;
+            float2 bv[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            float cl = 0.f;
+            if (live) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = 4 * q + u, l = c0 + i;
-                v[0][u] = v[1][u] = v[2][u] = v[3][u] = 0.f;
-                if (l <= a.L && s_first + s < a.nsky && l >= lmin) {
-                    float2 ap = {0.f, 0.f}, am = {0.f, 0.f};
-                    for (int X = 0; X < a.ncomp; ++X) {
-                        float2 sv = st.sky[(s * a.ncomp + X) * 32 + i];
-                        if (m == 0) sv.y = 0.f;
-                        float2 bv = st.beam[X * 32 + i];
-                        if (k == 0) bv.y = 0.f;
-                        ap.x += sv.x * bv.x + sv.y * bv.y;      // s conj(b)
-                        ap.y += sv.y * bv.x - sv.x * bv.y;
-                        am.x += sv.x * bv.x - sv.y * bv.y;      // conj(s) conj(b)
-                        am.y -= sv.y * bv.x + sv.x * bv.y;
+                for (int X = 0; X < 3; ++X)
+                    if (X < a.ncomp) {
+                        bv[X] = __ldg(beam_k + (int64_t)X * (a.K + 1) * (a.L + 1) + l);
+                        if (k == 0) bv[X].y = 0.f;
                     }
-                    const float cl = st.tab[i].c, sc = (l & 1) ? -cl : cl;
-                    const float2 p1 = neg ? am : ap, p2 = neg ? ap : am;
-                    v[0][u] = cl * p1.x;
-                    v[1][u] = cl * p1.y;
-                    v[2][u] = sc * p2.x;
-                    v[3][u] = sc * p2.y;
-                }
+                cl = tb[i].c;
             }
+            const float sc = (l & 1) ? -cl : cl;
+            const int ch = i >> 2, lo4 = i & 3;
+            for (int s = warp; s < a.nsg; s += kMsThreads / 32) {
+                const int sky = s_first + s;
+                float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+                if (live && sky < a.nsky) {
+                    const float2 *sp = a.sky + (int64_t)sky * a.ncomp * a.nalm + moff + l;
+                    float2 sv[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int row = 4 * s + j, off = row * 32 + ((q ^ (row & 7)) << 2);
-                float4 h, lo;
-                tf32_split(v[j][0], h.x, lo.x);
-                tf32_split(v[j][1], h.y, lo.y);
-                tf32_split(v[j][2], h.z, lo.z);
-                tf32_split(v[j][3], h.w, lo.w);
-                *reinterpret_cast<float4 *>(Bh + off) = h;
-                *reinterpret_cast<float4 *>(Bl + off) = lo;
+                    for (int X = 0; X < 3; ++X)
+                        if (X < a.ncomp) sv[X] = __ldg(sp + (int64_t)X * a.nalm);
+                    float2 ap = {0.f, 0.f}, am = {0.f, 0.f};
+#pragma unroll
+                    for (int X = 0; X < 3; ++X) {
+                        float2 s2 = sv[X];
+                        if (m == 0) s2.y = 0.f;
+                        const float2 b2 = bv[X];
+                        ap.x += s2.x * b2.x + s2.y * b2.y;      // s conj(b)
+                        ap.y += s2.y * b2.x - s2.x * b2.y;
+                        am.x += s2.x * b2.x - s2.y * b2.y;      // conj(s) conj(b)
+                        am.y -= s2.y * b2.x + s2.x * b2.y;
+                    }
+                    const float2 p1 = neg ? am : ap, p2 = neg ? ap : am;
+                    v0 = cl * p1.x;
+                    v1 = cl * p1.y;
+                    v2 = sc * p2.x;
+                    v3 = sc * p2.y;
+                }
+                const float vv[4] = {v0, v1, v2, v3};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int row = 4 * s + j, off = row * 32 + ((ch ^ (row & 7)) << 2) + lo4;
+                    float h, lo;
+                    tf32_split(vv[j], h, lo);
+                    Bh[off] = h;
+                    Bl[off] = lo;
+                }
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -318,20 +316,20 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_lcontract_mma(const MsArgs a)
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0) {
-            const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
+            const float *Bh = base + bi * 2 * bfl, *Bl = Bh + bfl;
+            const uint32_t bh = smem_u32(Bh), bl = smem_u32(Bl);
+            const uint32_t ahi = tmem + (uint32_t)(kMsAcol + bi * 64), alo = ahi + 32;
 #pragma unroll
             for (int kk = 0; kk < kMsLC / 8; ++kk) {
-                const uint32_t off = kk * 32;   // 8 TF32 along K
-                const uint64_t dah = ms_sdesc(ah + off), dal = ms_sdesc(al + off);
-                const uint64_t dbh = ms_sdesc(bh + off), dbl = ms_sdesc(bl + off);
+                const uint64_t dbh = ms_sdesc(bh + kk * 32), dbl = ms_sdesc(bl + kk * 32);
                 const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
                 asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-                             :: "r"(tmem), "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0) : "memory");
-                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
-                             :: "r"(tmem), "l"(dah), "l"(dbl), "r"(idesc) : "memory");
-                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
-                             :: "r"(tmem), "l"(dal), "l"(dbh), "r"(idesc) : "memory");
+                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}"
+                             :: "r"(tmem), "r"(ahi + kk * 8), "l"(dbh), "r"(idesc), "r"(acc0) : "memory");
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;"
+                             :: "r"(tmem), "r"(ahi + kk * 8), "l"(dbl), "r"(idesc) : "memory");
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;"
+                             :: "r"(tmem), "r"(alo + kk * 8), "l"(dbh), "r"(idesc) : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(smem_u32(&mbar[bi])) : "memory");
@@ -373,7 +371,8 @@ __global__ void __launch_bounds__(kMsThreads, 1) k_lcontract_mma(const MsArgs a)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(ncols) : "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kMsTmemCols) : "memory");
 }
 
 // Failure-detection self-test: a wait on an mbarrier that nothing signals
@@ -396,9 +395,8 @@ __global__ void k_to_f32_ms(const double2 *__restrict__ in, float2 *__restrict__
 }
 
 size_t lcontract_mma_smem(int nsg, int ncomp) {
-    const size_t ops = 2 * (2 * (size_t)kMsRows * kMsLC + 2 * (size_t)4 * nsg * kMsLC) * 4;
-    const size_t stage = 3 * ((size_t)nsg * ncomp * 32 + (size_t)ncomp * 32 + 64) * sizeof(float2);
-    return ops + stage + 1024;
+    (void)ncomp;
+    return 2 * 2 * (size_t)4 * nsg * kMsLC * sizeof(float) + 1024;   // B_hi, B_lo, two buffers
 }
 
 int lcontract_mma_group(int nsky) {
