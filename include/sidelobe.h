@@ -95,7 +95,7 @@ typedef struct {
     const double *ring_theta;  /* HOST [nrings]: strictly ascending colatitudes in (0, pi),
                                   symmetric: theta[R-1-r] == pi - theta[r] (to 1e-12);
                                   copied at plan creation */
-    int nphi;                  /* Phi: even, >= 8, of the form 2^a 3^b 5^c, <= 8192 */
+    int nphi;                  /* Phi: even, >= 8, of the form 2^a 3^b 5^c, <= 7200 */
     int interp_order;          /* p: 2, 4 or 6 points per axis (0 selects 4) */
     int precision;             /* sl_precision */
     int device;                /* CUDA device ordinal */

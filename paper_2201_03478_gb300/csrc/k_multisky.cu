@@ -274,19 +274,29 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a)
             }
             const float sc = (l & 1) ? -cl : cl;
             const int ch = i >> 2, lo4 = i & 3;
-            for (int s = warp; s < a.nsg; s += kMsThreads / 32) {
+            // all of this thread's sky values first (up to 4 skies x 3 components in flight)
+            constexpr int kSpw = 32 / (kMsThreads / 32);     // skies per warp at most
+            float2 sv[kSpw][3];
+#pragma unroll
+            for (int t = 0; t < kSpw; ++t) {
+                const int sky = s_first + warp + 8 * t;
+                const bool ok = live && warp + 8 * t < a.nsg && sky < a.nsky;
+                const float2 *sp = a.sky + (int64_t)sky * a.ncomp * a.nalm + moff + l;
+#pragma unroll
+                for (int X = 0; X < 3; ++X)
+                    sv[t][X] = (ok && X < a.ncomp) ? __ldg(sp + (int64_t)X * a.nalm) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int t = 0; t < kSpw; ++t) {
+                const int s = warp + 8 * t;
+                if (s >= a.nsg) break;
                 const int sky = s_first + s;
                 float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
                 if (live && sky < a.nsky) {
-                    const float2 *sp = a.sky + (int64_t)sky * a.ncomp * a.nalm + moff + l;
-                    float2 sv[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll
-                    for (int X = 0; X < 3; ++X)
-                        if (X < a.ncomp) sv[X] = __ldg(sp + (int64_t)X * a.nalm);
                     float2 ap = {0.f, 0.f}, am = {0.f, 0.f};
 #pragma unroll
                     for (int X = 0; X < 3; ++X) {
-                        float2 s2 = sv[X];
+                        float2 s2 = sv[t][X];
                         if (m == 0) s2.y = 0.f;
                         const float2 b2 = bv[X];
                         ap.x += s2.x * b2.x + s2.y * b2.y;      // s conj(b)

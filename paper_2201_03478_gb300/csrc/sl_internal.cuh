@@ -14,7 +14,9 @@ namespace sl {
 
 // ---------------------------------------------------------------- constants
 constexpr int kMaxK = 63;        // beam azimuthal band limit supported
-constexpr int kMaxNphi = 8192;   // ring FFT length held in shared memory
+// ring FFT length held in shared memory: two double-complex buffers of nphi
+// (the FP64 synthesis and every plan's adjoint DFT) within 227 KB
+constexpr int kMaxNphi = 7200;
 constexpr int kMaxRadices = 16;
 
 // Scaled FP64 Wigner values: value = mantissa * 2^(600 * e), e <= 0; a value
