@@ -326,7 +326,7 @@ def gpu_arm(args):
         st_adj = plan.kernel_stats(reset=True)
         plan.enable_timing(False)
         out["adjoint"] = {"value": world * n / (ms_adj / 1e3), "unit": "samples/s", "ms_per_step": ms_adj,
-                          "steps": args.adjoint_steps, "precision": "fp64",
+                          "steps": args.adjoint_steps, "precision": "df64" if prec == "df64" else "fp64",
                           "kernel_ms_per_step": {k: round(v[1] / args.adjoint_steps, 4) for k, v in st_adj.items()}}
         del gs, gb, y
 

@@ -22,6 +22,7 @@
 //   sky,  m > 0: sum_k [b_lk Abar_{k,l,m} + (-1)^m conj(b_lk) conj(Abar_{k,l,-m})]
 //   sky,  m = 0: sum_k Re(b_lk Abar_{k,l,0})
 //   beam:        sum_{m=-l..l} s_lm conj(Abar_{k,lm})   (Re only for k = 0; 0 for l < k)
+#include "df.cuh"
 #include "sl_internal.cuh"
 
 namespace sl {
@@ -175,6 +176,139 @@ __global__ void __launch_bounds__(kNTA) k_lcontract_adj(const LcAdjArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ DF64
+// The same transpose for SL_DF64 plans: the recurrence and the dot products in
+// double-float arithmetic (df.cuh), the c_l, s_l combination and the atomic
+// additions into Abar in double.
+struct AdjSmemDF {
+    float2 W[kLCA][2][kWS];        // y values [l][sign][pair], double-float
+    float2 Gv[8][kWS];
+    double dots[kLCA][8];
+    float4 rc[kLCA];               // a', b' as double-float
+    double cl[kLCA];
+};
+
+__global__ void __launch_bounds__(kNTA) k_lcontract_adj_df(const LcAdjArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AdjSmemDF &S = *reinterpret_cast<AdjSmemDF *>(smem_raw);
+    int b = blockIdx.x;
+    const int pc = b % a.nchunk;
+    b /= a.nchunk;
+    const int k = b % (a.K + 1), m = b / (a.K + 1);
+    const int neg = threadIdx.x >= kPA;
+    const int lp = threadIdx.x & (kPA - 1);
+    const int pair = pc * kPA + lp;
+    const bool active = pair < a.npairs;
+    const int64_t moff = (int64_t)m * (2 * a.L + 1 - m) / 2;
+    const RTab64 *tab = a.tab + (int64_t)k * a.nalm + moff;
+
+    dfl x = {0.f, 0.f}, y = {0.f, 0.f}, yo = {0.f, 0.f};
+    int ls = a.L + 1;
+    {
+        double2 g0 = {0, 0}, g1 = {0, 0};
+        if (active) {
+            const int64_t si = (((int64_t)k * (a.L + 1) + m) * 2 + neg) * a.npairs + pair;
+            ls = a.ls[si];
+            yo = df_from_d(a.st64[si].x);
+            y = df_from_d(a.st64[si].y);
+            x = df_from_d(a.xr[pair]);
+            const int rn = pair, rs = a.R - 1 - pair;
+            const int64_t row = 2 * (int64_t)a.L + 1;
+            const double2 *Gk = a.Ghat + (int64_t)k * a.R * row;
+            const double sm_ = (m & 1) ? -1.0 : 1.0, sk = (k & 1) ? -1.0 : 1.0;
+            if (!neg) {
+                g0 = Gk[rn * row + a.L + m];
+                if (m > 0 && rs != rn) {
+                    const double2 v = Gk[rs * row + a.L - m];
+                    g1 = make_double2(sk * v.x, sk * v.y);
+                }
+            } else {
+                if (rs != rn) {
+                    const double2 v = Gk[rs * row + a.L + m];
+                    g0 = make_double2(sm_ * v.x, sm_ * v.y);
+                }
+                if (m > 0) {
+                    const double2 v = Gk[rn * row + a.L - m];
+                    g1 = make_double2(sm_ * sk * v.x, sm_ * sk * v.y);
+                }
+            }
+        }
+        const int d0 = neg ? 2 : 0, d1 = neg ? 4 : 6;
+        const dfl a0 = df_from_d(g0.x), a1 = df_from_d(g0.y), b0 = df_from_d(g1.x), b1 = df_from_d(g1.y);
+        S.Gv[d0][lp] = make_float2(a0.h, a0.l);
+        S.Gv[d0 + 1][lp] = make_float2(a1.h, a1.l);
+        S.Gv[d1][lp] = make_float2(b0.h, b0.l);
+        S.Gv[d1 + 1][lp] = make_float2(b1.h, b1.l);
+    }
+    __shared__ int s_min;
+    if (threadIdx.x == 0) s_min = 0x7fffffff;
+    __syncthreads();
+    atomicMin(&s_min, ls);
+    __syncthreads();
+    const int lstart = s_min;
+    const float sb = neg ? 1.f : -1.f;
+    const int dl = threadIdx.x >> 3, dq = threadIdx.x & 7;
+    const int wsg = (dq == 0 || dq == 1 || dq == 6 || dq == 7) ? 0 : 1;
+    double2 *Ap = a.Abar + ((int64_t)k * (2 * a.L + 1) + a.L + m) * (a.L + 1);
+    double2 *Am = a.Abar + ((int64_t)k * (2 * a.L + 1) + a.L - m) * (a.L + 1);
+
+    for (int c0 = lstart; c0 <= a.L; c0 += kLCA) {
+        const int nc = min(kLCA, a.L - c0 + 1);
+        __syncthreads();
+        if (threadIdx.x < nc) {
+            const RTab64 t = tab[c0 + threadIdx.x];
+            const dfl ra = df_from_d(t.a), rb = df_from_d(t.b);
+            S.rc[threadIdx.x] = make_float4(ra.h, ra.l, rb.h, rb.l);
+            S.cl[threadIdx.x] = t.c;
+        }
+        __syncthreads();
+        for (int i = 0; i < nc; ++i) {
+            const int l = c0 + i;
+            float2 v = make_float2(0.f, 0.f);
+            if (l >= ls) {
+                v = make_float2(y.h, y.l);
+                const float4 r = S.rc[i];
+                const dfl t = df_fma(dfl{r.x, r.y}, x, dfl{sb * r.z, sb * r.w});
+                const dfl yn = df_fma(t, y, df_neg(yo));
+                yo = y;
+                y = yn;
+            }
+            S.W[i][neg][lp] = v;
+        }
+        for (int i = nc; i < kLCA; ++i) S.W[i][neg][lp] = make_float2(0.f, 0.f);
+        __syncthreads();
+        {
+            const float2 *wr = S.W[dl][wsg];
+            const float2 *gr = S.Gv[dq];
+            dacc s0, s1;
+            dacc_zero(s0);
+            dacc_zero(s1);
+#pragma unroll 4
+            for (int q = 0; q < kPA; q += 2) {
+                const float2 w0 = wr[q], g0 = gr[q], w1 = wr[q + 1], g1 = gr[q + 1];
+                dacc_mac(s0, dfl{w0.x, w0.y}, dfl{g0.x, g0.y});
+                dacc_mac(s1, dfl{w1.x, w1.y}, dfl{g1.x, g1.y});
+            }
+            dacc_add(s0, dacc_get(s1));
+            S.dots[dl][dq] = df_to_d(dacc_get(s0));
+        }
+        __syncthreads();
+        if (threadIdx.x < 4 * nc) {
+            const int i = threadIdx.x >> 2, comp = threadIdx.x & 3;
+            const int l = c0 + i;
+            const double s = (l & 1) ? -1.0 : 1.0;
+            const double c = S.cl[i];
+            if (comp < 2) {
+                const double v = c * (S.dots[i][comp] + s * S.dots[i][2 + comp]);
+                atomicAdd(&Ap[l].x + comp, v);
+            } else if (m > 0) {
+                const double v = c * (S.dots[i][2 + comp] + s * S.dots[i][4 + comp]);
+                atomicAdd(&Am[l].x + (comp - 2), v);
+            }
+        }
+    }
+}
+
 sl_status launch_lcontract_adjoint(sl_plan *p) {
     LcAdjArgs a;
     a.L = p->L;
@@ -195,12 +329,14 @@ sl_status launch_lcontract_adjoint(sl_plan *p) {
                               "memset Abar");
     if (st != SL_OK) return st;
     const int64_t nblk = (int64_t)(p->L + 1) * (p->K + 1) * a.nchunk;
-    const size_t sm = sizeof(AdjSmem);
-    if ((st = cuda_check(cudaFuncSetAttribute(k_lcontract_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+    const bool df = p->precision == SL_DF64;
+    const size_t sm = df ? sizeof(AdjSmemDF) : sizeof(AdjSmem);
+    void (*kern)(const LcAdjArgs) = df ? k_lcontract_adj_df : k_lcontract_adj;
+    if ((st = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                          "k_lcontract_adj smem attribute")) != SL_OK)
         return st;
-    int slot = timing_begin(p, "lcontract_adj");
-    k_lcontract_adj<<<(unsigned)nblk, kNTA, sm, p->stream>>>(a);
+    int slot = timing_begin(p, df ? "lcontract_adj_df" : "lcontract_adj");
+    kern<<<(unsigned)nblk, kNTA, sm, p->stream>>>(a);
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_lcontract_adj launch");
 }

@@ -333,25 +333,48 @@ __global__ void k_interp_adjoint(const AdjArgs A) {
             }
             __syncthreads();
             // phase B: warp w owns k-pairs w, w + nwarps, ...; a lane handles the
-            // entries (node q, k parity) = lane, lane + 32, ... of the 2 P^2
+            // entries (node q, k parity) = lane, lane + 32, ... of the 2 P^2.
+            // Samples are in cell order, so consecutive samples mostly share
+            // their stencil: a lane sums in registers while the cell stays
+            // the same and adds to the shared tile when it changes.
+            constexpr int NE = (2 * NQ + 31) / 32;
             for (int kp = warp; 2 * kp <= g.K; kp += nwarps) {
-                for (int sidx = 0; sidx < nb; ++sidx) {
+                double2 racc[NE];
 #pragma unroll
-                    for (int e = lane; e < 2 * NQ; e += 32) {
+                for (int t = 0; t < NE; ++t) racc[t] = make_double2(0.0, 0.0);
+                int cur_loc = nb > 0 ? LOC[0] : 0;
+                for (int sidx = 0; sidx <= nb; ++sidx) {
+                    const int loc = (sidx < nb) ? LOC[sidx] : -1;
+                    if (loc != cur_loc) {       // warp-uniform: flush the previous cell's sums
+#pragma unroll
+                        for (int t = 0; t < NE; ++t) {
+                            const int e = lane + 32 * t;
+                            const int q = e % NQ, kk = 2 * kp + e / NQ;
+                            if (e < 2 * NQ && kk <= g.K) {
+                                double2 &dst = acc[(size_t)(cur_loc + (q / P) * tw + (q % P)) * K1 + kk];
+                                double2 c = dst;
+                                c.x += racc[t].x;
+                                c.y += racc[t].y;
+                                dst = c;
+                            }
+                            racc[t] = make_double2(0.0, 0.0);
+                        }
+                        // the next cell's stencil may overlap: order this warp's updates
+                        __syncwarp(0xffffffffu);
+                        cur_loc = loc;
+                    }
+                    if (sidx == nb) break;
+#pragma unroll
+                    for (int t = 0; t < NE; ++t) {
+                        const int e = lane + 32 * t;
                         const int q = e % NQ, kk = 2 * kp + e / NQ;
-                        if (kk <= g.K) {
-                            const int node = LOC[sidx] + (q / P) * tw + (q % P);
+                        if (e < 2 * NQ && kk <= g.K) {
                             const double w = W[sidx * NQ + q];
                             const double2 ph = PH[(size_t)sidx * K1 + kk];
-                            double2 &dst = acc[(size_t)node * K1 + kk];
-                            double2 cur = dst;
-                            cur.x = fma(w, ph.x, cur.x);
-                            cur.y = fma(w, ph.y, cur.y);
-                            dst = cur;
+                            racc[t].x = fma(w, ph.x, racc[t].x);
+                            racc[t].y = fma(w, ph.y, racc[t].y);
                         }
                     }
-                    // consecutive samples may share nodes: order this warp's updates
-                    __syncwarp(0xffffffffu);
                 }
             }
             __syncthreads();
@@ -447,6 +470,7 @@ size_t interp_adjoint_smem_tc(const sl_plan *p, int tc) {
 
 sl_status launch_interp_adjoint(sl_plan *p, const SortBufs &b, int fine, const double *psi, const double *tod,
                                 int64_t n, double2 *fbar) {
+    if (p->precision == SL_DF64) return launch_interp_adjoint_df(p, b, fine, psi, tod, fbar);
     AdjArgs a;
     a.g = p->geom;
     a.psi = psi;

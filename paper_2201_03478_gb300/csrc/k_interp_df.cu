@@ -24,7 +24,8 @@ struct DfArgs {
     const double *psi;
     const unsigned *perm, *start, *chunk_off;
     int ntiles, ncell;
-    double *tod;
+    double *tod;       // forward: written; adjoint: the input TOD
+    double2 *fbar;     // adjoint cube (adjoint only)
 };
 
 __device__ __forceinline__ dfl df_ld(const float2 *p) {
@@ -161,6 +162,196 @@ __global__ void __launch_bounds__(256) k_interp_df_tiled(const DfArgs A) {
     }
 }
 
+// ------------------------------------------------------------------ adjoint
+// The transpose of the interpolation for SL_DF64 plans: the FP64 kernel's tile
+// scatter with the weights, the phases and the shared-memory accumulation in
+// double-float (each accumulator an unnormalised high/low pair); the tile is
+// flushed to the double adjoint cube with atomic additions.
+constexpr int kNBD = 64;   // samples staged per batch
+
+template <int P>
+__global__ void k_interp_adjoint_df(const DfArgs A) {
+    constexpr int NQ = P * P;
+    const InterpGeom &g = A.g;
+    const int K1 = g.K + 1;
+    const int TC = g.tile_cols;
+    const int tw = TC + P - 1, th_rows = kTileRows + P - 1, nnode = th_rows * tw;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *acc = reinterpret_cast<float4 *>(smem_raw);               // [nnode][K1] (Re h, Re l, Im h, Im l)
+    float4 *PH = acc + (size_t)nnode * K1;                            // [kNBD][K1]
+    float2 *W = reinterpret_cast<float2 *>(PH + (size_t)kNBD * K1);   // [kNBD][NQ]
+    int *LOC = reinterpret_cast<int *>(W + (size_t)kNBD * NQ);        // [kNBD]
+
+    const unsigned nchunks = A.chunk_off[A.ntiles];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    for (int e = threadIdx.x; e < nnode * K1; e += blockDim.x) acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    for (unsigned v = blockIdx.x; v < nchunks; v += gridDim.x) {
+        const int tile = find_tile(A.chunk_off, A.ntiles, v);
+        const unsigned c = v - A.chunk_off[tile];
+        const unsigned s_beg = A.start[(int64_t)tile * A.ncell] + c * kWorkChunk;
+        const unsigned s_end = min(A.start[(int64_t)(tile + 1) * A.ncell], s_beg + kWorkChunk);
+        const int tr = tile / g.ntc, tcol = tile % g.ntc;
+        const int rowlo = tr * kTileRows - P / 2, collo = tcol * TC - P / 2 + 1;
+        __syncthreads();
+        for (unsigned b0 = s_beg; b0 < s_end; b0 += kNBD) {
+            const int nb = (int)min((unsigned)kNBD, s_end - b0);
+            // phase A: per-sample weights, node location and phases eps_k y e^{-ik psi}
+            if ((int)threadIdx.x < nb) {
+                const unsigned s = A.perm[b0 + threadIdx.x];
+                const StencilRec64 r = A.rec[s];
+                const int i = (int)(r.cell >> 16) - 1, j = (int)(r.cell & 0xffffu);
+                dfl wt[P], wp[P];
+                weights_df<P>(g.rowtab_df + (size_t)(i + 1) * 2 * P, df_from_d(r.dth), df_from_d(r.fph), wt, wp);
+                float2 *ws = W + threadIdx.x * NQ;
+#pragma unroll
+                for (int ra = 0; ra < P; ++ra)
+#pragma unroll
+                    for (int cb = 0; cb < P; ++cb) {
+                        const dfl w = df_mul(wt[ra], wp[cb]);
+                        ws[ra * P + cb] = make_float2(w.h, w.l);
+                    }
+                LOC[threadIdx.x] = (i - P / 2 + 1 - rowlo) * tw + (j - P / 2 + 1 - collo);
+                double sp, cp;
+                sincos(__ldg(A.psi + s), &sp, &cp);
+                const double yv = A.tod[s];
+                const dfl y1 = df_from_d(yv), y2 = df_from_d(2.0 * yv), c2 = df_from_d(2.0 * cp);
+                dfl ck = df_make(1.f, 0.f), sk = df_make(0.f, 0.f), ckm = df_from_d(cp), skm = df_from_d(-sp);
+                float4 *Ps = PH + (size_t)threadIdx.x * K1;
+                for (int k = 0; k <= g.K; ++k) {
+                    const dfl sc = (k == 0) ? y1 : y2;
+                    const dfl re = df_mul(sc, ck), im = df_neg(df_mul(sc, sk));
+                    Ps[k] = make_float4(re.h, re.l, im.h, im.l);
+                    const dfl cn = df_fma(c2, ck, df_neg(ckm)), sn = df_fma(c2, sk, df_neg(skm));
+                    ckm = ck;
+                    skm = sk;
+                    ck = cn;
+                    sk = sn;
+                }
+            }
+            __syncthreads();
+            // phase B: warp w owns k-pairs w, w + nwarps, ...; lanes over (node, k
+            // parity); register sums while the cell stays the same (cell order),
+            // added to the shared tile when it changes
+            constexpr int NE = (2 * NQ + 31) / 32;
+            for (int kp = warp; 2 * kp <= g.K; kp += nwarps) {
+                dacc rr[NE], ri[NE];
+#pragma unroll
+                for (int t = 0; t < NE; ++t) {
+                    dacc_zero(rr[t]);
+                    dacc_zero(ri[t]);
+                }
+                int cur_loc = nb > 0 ? LOC[0] : 0;
+                for (int sidx = 0; sidx <= nb; ++sidx) {
+                    const int loc = (sidx < nb) ? LOC[sidx] : -1;
+                    if (loc != cur_loc) {       // warp-uniform
+#pragma unroll
+                        for (int t = 0; t < NE; ++t) {
+                            const int e = lane + 32 * t;
+                            const int q = e % NQ, kk = 2 * kp + e / NQ;
+                            if (e < 2 * NQ && kk <= g.K) {
+                                float4 &dst = acc[(size_t)(cur_loc + (q / P) * tw + (q % P)) * K1 + kk];
+                                const float4 c = dst;
+                                dacc sr{c.x, c.y}, si{c.z, c.w};
+                                dacc_add(sr, dacc_get(rr[t]));
+                                dacc_add(si, dacc_get(ri[t]));
+                                dst = make_float4(sr.h, sr.l, si.h, si.l);
+                            }
+                            dacc_zero(rr[t]);
+                            dacc_zero(ri[t]);
+                        }
+                        __syncwarp(0xffffffffu);
+                        cur_loc = loc;
+                    }
+                    if (sidx == nb) break;
+#pragma unroll
+                    for (int t = 0; t < NE; ++t) {
+                        const int e = lane + 32 * t;
+                        const int q = e % NQ, kk = 2 * kp + e / NQ;
+                        if (e < 2 * NQ && kk <= g.K) {
+                            const float2 w = W[sidx * NQ + q];
+                            const float4 ph = PH[(size_t)sidx * K1 + kk];
+                            dacc_mac(rr[t], dfl{w.x, w.y}, dfl{ph.x, ph.y});
+                            dacc_mac(ri[t], dfl{w.x, w.y}, dfl{ph.z, ph.w});
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // flush the tile (ghost rows fold onto their ring at phi + pi with (-1)^k)
+        for (int e = threadIdx.x; e < nnode * K1; e += blockDim.x) {
+            const float4 val = acc[e];
+            if (val.x == 0.f && val.y == 0.f && val.z == 0.f && val.w == 0.f) continue;
+            acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int kk = e % K1;
+            const int node = e / K1;
+            const int row = rowlo + node / tw;
+            int col = collo + node % tw;
+            if (row < -P / 2 || row > g.R - 1 + P / 2) continue;
+            int ring = row;
+            double sg = 1.0;
+            if (row < 0 || row >= g.R) {
+                ring = (row < 0) ? -1 - row : 2 * g.R - 1 - row;
+                col += g.nphi / 2;
+                if (kk & 1) sg = -1.0;
+            }
+            col %= g.nphi;
+            if (col < 0) col += g.nphi;
+            double2 *o = A.fbar + ((int64_t)ring * g.nphi + col) * K1 + kk;
+            atomicAdd(&o->x, sg * ((double)val.x + (double)val.y));
+            atomicAdd(&o->y, sg * ((double)val.z + (double)val.w));
+        }
+    }
+}
+
+size_t interp_adjoint_df_smem_tc(const sl_plan *p, int tc) {
+    const int K1 = p->K + 1, P = p->p;
+    const int nnode = (kTileRows + P - 1) * (tc + P - 1);
+    return (size_t)nnode * K1 * sizeof(float4) + (size_t)kNBD * K1 * sizeof(float4) +
+           (size_t)kNBD * P * P * sizeof(float2) + (size_t)kNBD * sizeof(int);
+}
+
+sl_status launch_interp_adjoint_df(sl_plan *p, const SortBufs &b, int fine, const double *psi, const double *tod,
+                                   double2 *fbar) {
+    if (!b.chunk_off) return set_error(SL_ERR_ARG, "adjoint interpolation needs the per-tile work list");
+    DfArgs a;
+    a.g = p->geom;
+    a.maps = nullptr;
+    a.rec = (const StencilRec64 *)b.rec;
+    a.psi = psi;
+    a.perm = b.perm;
+    a.start = b.hist;
+    a.chunk_off = b.chunk_off;
+    a.ntiles = p->ntiles;
+    a.ncell = fine ? kTileRows * p->geom.tile_cols : 1;
+    a.tod = const_cast<double *>(tod);   // read only here
+    a.fbar = fbar;
+    const int K1 = p->K + 1;
+    const size_t sm = interp_adjoint_df_smem_tc(p, p->geom.tile_cols);
+    int nwarps = (K1 + 1) / 2;
+    if (nwarps < 2) nwarps = 2;
+    if (nwarps > 16) nwarps = 16;
+    void (*kern)(const DfArgs);
+    switch (p->p) {
+        case 2: kern = k_interp_adjoint_df<2>; break;
+        case 4: kern = k_interp_adjoint_df<4>; break;
+        case 6: kern = k_interp_adjoint_df<6>; break;
+        default: return set_error(SL_ERR_UNSUPPORTED, "interp_order %d", p->p);
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return cuda_check(e, "k_interp_adjoint_df smem attribute");
+    int per_sm = 1, nsm = 152;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * nwarps, sm);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
+    if (per_sm < 1) per_sm = 1;
+    const int slot = timing_begin(p, "interp_adj_df");
+    kern<<<(unsigned)(nsm * per_sm), 32 * nwarps, sm, p->stream>>>(a);
+    timing_end(p, slot);
+    return cuda_check(cudaGetLastError(), "k_interp_adjoint_df launch");
+}
+
 size_t interp_df_tiled_smem_tc(const sl_plan *p, int tc) {
     return (size_t)(kTileRows + p->p - 1) * (tc + p->p - 1) * (p->K + 1) * sizeof(float4);
 }
@@ -179,6 +370,7 @@ sl_status launch_interp_df(sl_plan *p, const SortBufs &b, int fine, const void *
     a.ntiles = p->ntiles;
     a.ncell = fine ? kTileRows * p->geom.tile_cols : 1;
     a.tod = tod;
+    a.fbar = nullptr;
     const size_t sm = interp_df_tiled_smem_tc(p, p->geom.tile_cols);
     void (*kern)(const DfArgs) = nullptr;
 #define SL_TILED(TCV, PV) \

@@ -147,7 +147,8 @@ static void free_sort_tables(sl_plan *p) {
 static size_t tile_smem_need(const sl_plan *p, int tc) {
     size_t need = interp_adjoint_smem_tc(p, tc);
     if (p->precision == SL_FP32) need = std::max(need, interp_f32_tiled_smem_tc(p, tc));
-    if (p->precision == SL_DF64) need = std::max(need, interp_df_tiled_smem_tc(p, tc));
+    if (p->precision == SL_DF64)
+        need = std::max(need, std::max(interp_df_tiled_smem_tc(p, tc), interp_adjoint_df_smem_tc(p, tc)));
     return need;
 }
 constexpr size_t kSmemOptin = 232448;   // 227 KB of dynamic shared memory per CTA (sm_100 family)

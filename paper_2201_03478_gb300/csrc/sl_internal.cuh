@@ -270,6 +270,9 @@ size_t interp_adjoint_smem_tc(const sl_plan *p, int tc);
 sl_status launch_interp_df(sl_plan *p, const SortBufs &b, int fine, const void *maps, const double *psi, int64_t n,
                            double *tod);
 size_t interp_df_tiled_smem_tc(const sl_plan *p, int tc);
+sl_status launch_interp_adjoint_df(sl_plan *p, const SortBufs &b, int fine, const double *psi, const double *tod,
+                                   double2 *fbar);
+size_t interp_adjoint_df_smem_tc(const sl_plan *p, int tc);
 // Adjoint scatter over a sort made with rec64 = 1, with_chunks = 1.
 sl_status launch_interp_adjoint(sl_plan *p, const SortBufs &b, int fine, const double *psi, const double *tod,
                                 int64_t n, double2 *fbar);

@@ -141,20 +141,22 @@ def test_interp_df64_same_cube(sl, case):
     assert err < 1e-12
 
 
-def test_adjoint_interp_fp64(sl, case, oracle_lib):
-    plan = _plan(sl, case)
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_adjoint_interp(sl, case, oracle_lib, prec):
+    plan = _plan(sl, case, prec)
     rng = np.random.default_rng(21)
     y = rng.standard_normal(case["th"].size)
     got = sl.adjoint_interp(plan, _dev(case["th"]), _dev(case["ph"]), _dev(case["ps"]), _dev(y)).cpu().numpy()
     ref = oracle_lib.interp_adjoint(y, case["rt"], case["nphi"], case["K"], case["th"], case["ph"], case["ps"])
     err = rel_l2(got, ref)
-    print(case["name"], "adjoint interp rel L2", err)
+    print(case["name"], prec, "adjoint interp rel L2", err)
     assert err < 1e-12
 
 
-def test_adjoint_synth_fp64(sl, case, oracle_lib):
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_adjoint_synth(sl, case, oracle_lib, prec):
     """Transpose of the cube build + products, from the same adjoint cube."""
-    plan = _plan(sl, case)
+    plan = _plan(sl, case, prec)
     rng = np.random.default_rng(22)
     shp = (case["rt"].size, case["nphi"], case["K"] + 1)
     fbar = rng.standard_normal(shp) + 1j * rng.standard_normal(shp)
@@ -163,12 +165,13 @@ def test_adjoint_synth_fp64(sl, case, oracle_lib):
     Ab = oracle_lib.cube_G_adjoint(Gh, case["rt"])
     rs, rb = oracle_lib.grad_products(Ab, case["sky"], case["beam"])
     es, eb = rel_l2(gs.cpu().numpy(), rs), rel_l2(gb.cpu().numpy(), rb)
-    print(case["name"], "adjoint synth rel L2 sky %.2e beam %.2e" % (es, eb))
+    print(case["name"], prec, "adjoint synth rel L2 sky %.2e beam %.2e" % (es, eb))
     assert es < TOL64 and eb < TOL64
 
 
-def test_adjoint_tod_and_dot_product(sl, case, oracle_lib):
-    plan = _plan(sl, case)
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_adjoint_tod_and_dot_product(sl, case, oracle_lib, prec):
+    plan = _plan(sl, case, prec)
     rng = np.random.default_rng(23)
     y = rng.standard_normal(case["th"].size)
     sky, beam = _dev(case["sky"]), _dev(case["beam"])
@@ -183,10 +186,12 @@ def test_adjoint_tod_and_dot_product(sl, case, oracle_lib):
     lhs = float(np.dot(tod, y))
     s_np = case["sky"].copy()
     rhs = float(np.sum(s_np.real * gs.cpu().numpy().real + s_np.imag * gs.cpu().numpy().imag))
-    assert abs(lhs - rhs) <= 1e-12 * max(1.0, np.linalg.norm(tod) * np.linalg.norm(y))
+    # DF64: forward and adjoint each carry ~1e-14 of double-float rounding
+    dot_tol = 1e-12 if prec == "fp64" else 1e-11
+    assert abs(lhs - rhs) <= dot_tol * max(1.0, np.linalg.norm(tod) * np.linalg.norm(y))
     b_np = case["beam"]
     rhs_b = float(np.sum(b_np.real * gb.cpu().numpy().real + b_np.imag * gb.cpu().numpy().imag))
-    assert abs(lhs - rhs_b) <= 1e-12 * max(1.0, np.linalg.norm(tod) * np.linalg.norm(y))
+    assert abs(lhs - rhs_b) <= dot_tol * max(1.0, np.linalg.norm(tod) * np.linalg.norm(y))
 
 
 def test_pointing_edge_cases(sl, oracle_lib):
@@ -221,9 +226,9 @@ def test_pointing_edge_cases_df64(sl, oracle_lib):
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
 
 
-def test_df64_adjoint_is_the_fp64_adjoint(sl):
-    """DF64 plans share the FP64 plans' tables and run the FP64 adjoint (equal up
-    to the order of the atomic additions into the adjoint cube)."""
+def test_df64_adjoint_matches_fp64_adjoint(sl):
+    """The double-float adjoint (interpolation transpose and contraction
+    transpose in double-float) against the FP64 adjoint on the same inputs."""
     c = CASES["small_healpix"]()
     y = _dev(np.random.default_rng(4).standard_normal(c["th"].size))
     outs = []
@@ -232,7 +237,9 @@ def test_df64_adjoint_is_the_fp64_adjoint(sl):
         gs, gb = sl.adjoint_tod(plan, _dev(c["th"]), _dev(c["ph"]), _dev(c["ps"]), y, _dev(c["sky"]),
                                 _dev(c["beam"]))
         outs.append((gs.cpu().numpy(), gb.cpu().numpy()))
-    assert rel_l2(outs[1][0], outs[0][0]) < 1e-13 and rel_l2(outs[1][1], outs[0][1]) < 1e-13
+    es, eb = rel_l2(outs[1][0], outs[0][0]), rel_l2(outs[1][1], outs[0][1])
+    print("df64 vs fp64 adjoint: sky %.2e beam %.2e" % (es, eb))
+    assert es < 1e-11 and eb < 1e-11
 
 
 @pytest.fixture(scope="module")
@@ -268,14 +275,15 @@ def test_interp_order_2_and_6(sl, oracle_lib, order_case, p, prec, tol):
 
 
 @pytest.mark.parametrize("p", [2, 6])
-def test_adjoint_interp_order_2_and_6(sl, oracle_lib, order_case, p):
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_adjoint_interp_order_2_and_6(sl, oracle_lib, order_case, p, prec):
     c = order_case
     y = np.random.default_rng(8).standard_normal(c["th"].size)
     ref = oracle_lib.interp_adjoint(y, c["rt"], c["nphi"], c["K"], c["th"], c["ph"], c["ps"], p=p)
-    plan = sl.sidelobe_plan_create(c["L"], c["K"], c["rt"], c["nphi"], ncomp=1, interp_order=p)
+    plan = sl.sidelobe_plan_create(c["L"], c["K"], c["rt"], c["nphi"], ncomp=1, interp_order=p, precision=prec)
     got = sl.adjoint_interp(plan, _dev(c["th"]), _dev(c["ph"]), _dev(c["ps"]), _dev(y)).cpu().numpy()
     err = rel_l2(got, ref)
-    print("p=%d adjoint interp rel L2 %.2e" % (p, err))
+    print("p=%d %s adjoint interp rel L2 %.2e" % (p, prec, err))
     assert err < 1e-12
 
 
