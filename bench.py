@@ -135,8 +135,11 @@ def measured_peaks():
 #   FP32: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz = 80.55 TFLOP/s
 PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# TF32 tensor peak: the measured bf16 burst (MEASURED_PEAKS.json) x the nominal TF32 / BF16 ratio (1.1 / 2.25)
+PEAK_TF32_TFLOPS = measured_peaks().get("bf16_tflops", 1900.0) * 1.1 / 2.25
 DTYPE = {"fp64": "f64", "fp32": "f32 (FP64 seeds/coords/final sum)",
-         "df64": "f32x2 double-float contraction and interpolation (FP64 seeds/tables/FFT/coords)"}
+         "df64": "f32x2 double-float contraction and interpolation (FP64 seeds/tables/FFT/coords)",
+         "tf32x3": "f32 with a 3xTF32 tensor-core contraction (FP64 seeds/coords/final sum)"}
 PEAK_FP32_TINST = 152 * 128 * 2.07e9 / 1e12          # FP32-pipe instructions per second (x 1e12)
 
 
@@ -249,11 +252,16 @@ def gpu_arm(args):
     # 11 flops (3 recurrence + 2 complex x real MACs) per visited (ring, m, k, sign, l)
     fl_lc = 11.0 * plan.sizes()["lsteps"]
     prec = args.precision
-    suffix = {"fp64": "f64", "fp32": "f32", "df64": "df"}[prec]
+    suffix = {"fp64": "f64", "fp32": "f32", "df64": "df", "tf32x3": "f32"}[prec]
     roofs = {}
-    lc_name = "lcontract_" + suffix
-    kernels = [(lc_name, fl_lc if prec != "df64" else DF_LC_INST_PER_STEP * float(plan.sizes()["lsteps"]),
-                {"fp64": PEAK_FP64_TFLOPS, "fp32": PEAK_FP32_TFLOPS, "df64": PEAK_FP32_TINST}[prec],
+    lc_name = "lcontract_mma" if prec == "tf32x3" else "lcontract_" + suffix
+    lsteps = float(plan.sizes()["lsteps"])
+    lc_work = {"fp64": fl_lc, "fp32": fl_lc, "df64": DF_LC_INST_PER_STEP * lsteps,
+               # tensor work executed: 3 TF32 products x 2 flops x 16 columns (4 used, one sky)
+               "tf32x3": 3 * 2.0 * 16 * lsteps}[prec]
+    kernels = [(lc_name, lc_work,
+                {"fp64": PEAK_FP64_TFLOPS, "fp32": PEAK_FP32_TFLOPS, "df64": PEAK_FP32_TINST,
+                 "tf32x3": PEAK_TF32_TFLOPS}[prec],
                 "Tinst/s" if prec == "df64" else "TFLOP/s"),
                ("interp_" + suffix, fl_in if prec != "df64" else float(n) * df_interp_inst(K),
                 PEAK_FP32_TINST if prec == "df64" else (PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS),
@@ -262,12 +270,15 @@ def gpu_arm(args):
         if name in stats and stats[name][0] > 0:
             avg_ms = stats[name][1] / stats[name][0]
             ach = fl / (avg_ms / 1e3) / 1e12
-            roofs[name] = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4),
+            roofs[name] = {"bound": "tensor" if name == "lcontract_mma" else "alu", "achieved": round(ach, 4),
+                           "peak": round(peak, 4),
                            "unit": unit, "frac": round(ach / peak, 4),
                            "traffic": None if highres else TRAFFIC.get((name, prec)),
                            "avg_ms": round(avg_ms, 4),
                            ("flops_per_launch" if unit == "TFLOP/s" else "fp32_inst_per_launch"): fl,
-                           "peak_note": "derived from unit counts x 2.07 GHz max SM clock"}
+                           "peak_note": ("measured bf16 burst x nominal TF32/BF16 ratio (of measured)"
+                                         if name == "lcontract_mma" else
+                                         "derived from unit counts x 2.07 GHz max SM clock")}
     if lc_name in roofs:
         roofs[lc_name]["flops_dense_triangle"] = fl_dense
         roofs[lc_name]["dense_equivalent_tflops"] = round(fl_dense / (roofs[lc_name]["avg_ms"] / 1e3) / 1e12, 4)
@@ -331,7 +342,7 @@ def gpu_arm(args):
         del gs, gb, y
 
     # ---- the other precisions on the same box, compared with this run's TOD
-    others = [q for q in ("fp64", "df64", "fp32") if q != prec] if (args.compare and rank == 0 and world == 1) else []
+    others = [q for q in ("fp64", "df64", "fp32", "tf32x3") if q != prec] if (args.compare and rank == 0 and world == 1) else []
     out["other_precisions"] = []
     for other in others:
         p2 = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=ncomp, precision=other, device=local)
@@ -659,7 +670,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--precision", choices=["fp64", "fp32", "df64"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "df64", "tf32x3"], default="fp64")
     ap.add_argument("--workload", choices=["lfi", "highres", "detectors", "multisky"], default="lfi",
                     help="lfi: T/E/B, lmax 1024, kmax 16, scan (the headline); "
                          "highres: lmax 2048, kmax 32, 2048 x 4096 rings, uniform pointings (precision variant); "

@@ -80,6 +80,11 @@ typedef enum {
                      conversion, psi reduction and final TOD value; FP32
                      recurrence, sky x beam products, contraction, ring FFT,
                      maps and interpolation sums */
+    SL_TF32X3 = 2, /* SL_FP32 with the l-contraction on the tensor cores
+                     (tcgen05, the FP32 recurrence values and the sky x beam
+                     columns split into TF32 high and low parts, three
+                     products, FP32 accumulation; the multi-sky kernel with
+                     one sky) */
     SL_DF64 = 4   /* FP64-class results from the FP32 pipes: the layouts,
                      tables, FFT and coordinates of SL_FP64 (maps are double2),
                      with the l-contraction and the interpolation sums run in

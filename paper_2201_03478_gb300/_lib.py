@@ -12,7 +12,7 @@ import os
 from . import _build
 
 SL_OK, SL_ERR_ARG, SL_ERR_UNSUPPORTED, SL_ERR_NOMEM, SL_ERR_CUDA, SL_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
-SL_FP64, SL_FP32, SL_DF64 = 0, 1, 4
+SL_FP64, SL_FP32, SL_TF32X3, SL_DF64 = 0, 1, 2, 4
 
 STATUS_NAMES = {0: "SL_OK", -1: "SL_ERR_ARG", -2: "SL_ERR_UNSUPPORTED", -3: "SL_ERR_NOMEM",
                 -4: "SL_ERR_CUDA", -5: "SL_ERR_TIMEOUT"}

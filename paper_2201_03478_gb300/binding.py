@@ -21,9 +21,10 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import SL_DF64, SL_FP32, SL_FP64, check
+from ._lib import SL_DF64, SL_FP32, SL_FP64, SL_TF32X3, check
 
-_PREC = {"fp64": SL_FP64, "fp32": SL_FP32, "df64": SL_DF64, SL_FP64: SL_FP64, SL_FP32: SL_FP32, SL_DF64: SL_DF64}
+_PREC = {"fp64": SL_FP64, "fp32": SL_FP32, "df64": SL_DF64, "tf32x3": SL_TF32X3,
+         SL_FP64: SL_FP64, SL_FP32: SL_FP32, SL_DF64: SL_DF64, SL_TF32X3: SL_TF32X3}
 
 
 class Plan:
@@ -40,7 +41,7 @@ class Plan:
 
     @property
     def maps_dtype(self):
-        return torch.complex64 if self.precision == SL_FP32 else torch.complex128
+        return torch.complex64 if self.precision in (SL_FP32, SL_TF32X3) else torch.complex128
 
     def maps_shape(self):
         return (self.nrings, self.nphi, self.kmax + 1)
@@ -144,7 +145,7 @@ def synth_spin_maps_multi(plan: Plan, sky, beam, maps=None):
     """Cubes of several skies that share one beam (FP32 plans; the l-contraction
     runs on the tensor cores).  sky: complex128 [nsky, ncomp, nalm]; returns
     complex64 maps [nsky, R, nphi, K+1]."""
-    if plan.precision != SL_FP32:
+    if plan.precision not in (SL_FP32, SL_TF32X3):
         raise ValueError("synth_spin_maps_multi needs an FP32 plan")
     if not isinstance(sky, torch.Tensor) or sky.dim() != 3:
         raise ValueError("sky must be a [nsky, ncomp, nalm] tensor")

@@ -449,6 +449,8 @@ __global__ void k_to_f32(const double2 *__restrict__ in, float2 *__restrict__ ou
 }
 
 sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
+    if (p->precision == SL_TF32X3)   // one sky on the tensor cores
+        return launch_lcontract_mma(p, 1, sky, beam, p->d_sky32, (float2 *)p->d_G, p->d_err);
     LcArgs a;
     a.L = p->L;
     a.K = p->K;

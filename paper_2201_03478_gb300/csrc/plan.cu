@@ -146,7 +146,7 @@ static void free_sort_tables(sl_plan *p) {
 // Shared memory the tile-staged kernels need at tile width tc.
 static size_t tile_smem_need(const sl_plan *p, int tc) {
     size_t need = interp_adjoint_smem_tc(p, tc);
-    if (p->precision == SL_FP32) need = std::max(need, interp_f32_tiled_smem_tc(p, tc));
+    if (plan_fp32(p->precision)) need = std::max(need, interp_f32_tiled_smem_tc(p, tc));
     if (p->precision == SL_DF64)
         need = std::max(need, std::max(interp_df_tiled_smem_tc(p, tc), interp_adjoint_df_smem_tc(p, tc)));
     return need;
@@ -228,7 +228,7 @@ static sl_status validate(const sl_plan_desc *d, int *rad, int *nrad) {
         return set_error(SL_ERR_ARG, "nphi=%d must be even and in [8, %d]", d->nphi, kMaxNphi);
     if (!factor_235(d->nphi, rad, nrad))
         return set_error(SL_ERR_UNSUPPORTED, "nphi=%d has a prime factor > 5", d->nphi);
-    if (d->precision != SL_FP64 && d->precision != SL_FP32 && d->precision != SL_DF64)
+    if (d->precision != SL_FP64 && d->precision != SL_FP32 && d->precision != SL_DF64 && d->precision != SL_TF32X3)
         return set_error(SL_ERR_ARG, "precision=%d unknown", d->precision);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -470,7 +470,7 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     // the FP64 table drives the plan-time advance in both precisions; FP32 plans
     // keep only its float form
     TRY(dalloc_t(p, &p->d_tab64, (size_t)(K + 1) * p->nalm, "recurrence table"));
-    if (p->precision == SL_FP32) {
+    if (plan_fp32(p->precision)) {
         TRY(dalloc_t(p, &p->d_tab32, (size_t)(K + 1) * p->nalm, "recurrence table"));
         TRY(dalloc_t(p, &p->d_sky32, (size_t)p->ncomp * p->nalm, "FP32 sky"));
         TRY(dalloc_t(p, &p->d_beam32, (size_t)p->ncomp * (K + 1) * (L + 1), "FP32 beam"));
@@ -484,7 +484,7 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     }
     TRY(launch_advance(p, plan_wide(p->precision) ? 0x1p-64 : 0x1p-30, p->d_ls, p->d_st64, p->d_st32));
     TRY(count_lsteps(p, &p->lsteps));
-    if (p->precision == SL_FP32) {
+    if (plan_fp32(p->precision)) {
         TRY(cuda_check(cudaStreamSynchronize(p->stream), "plan advance"));
         dfree(p->d_tab64);
         p->d_tab64 = nullptr;
@@ -496,6 +496,10 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
         TRY(dalloc(p, &p->d_G, p->G_bytes, "spin-Legendre scratch G"));
     }
     TRY(alloc_sort_tables(p));
+    if (p->precision == SL_TF32X3) {   // device flag of the tensor-core kernel's bounded waits
+        TRY(dalloc_t(p, &p->d_err, 1, "error flag"));
+        TRY(cuda_check(cudaMemset(p->d_err, 0, sizeof(int)), "error flag"));
+    }
     TRY(cuda_check(cudaStreamSynchronize(p->stream), "plan seeds"));
     dfree(d_c2);
     dfree(d_s2);
@@ -669,7 +673,7 @@ sl_status sl_plan_selftest_timeout(sl_plan *p) {
 sl_status synth_spin_maps_multi(sl_plan *p, int nsky, const double *sky, const double *beam, void *maps) {
     sl_status st = enter(p);
     if (st != SL_OK) return st;
-    if (p->precision != SL_FP32)
+    if (!plan_fp32(p->precision))
         return set_error(SL_ERR_UNSUPPORTED, "synth_spin_maps_multi: FP32 plans only (the tensor-core path)");
     if (nsky < 1) return set_error(SL_ERR_ARG, "synth_spin_maps_multi: nsky=%d < 1", nsky);
     if (!sky || !beam || !maps) return set_error(SL_ERR_ARG, "synth_spin_maps_multi: NULL buffer");

@@ -35,8 +35,10 @@ constexpr int kTileRows = 4;
 // Work item of the tile-staged kernels: at most this many sorted samples of one tile.
 constexpr int kWorkChunk = 2048;
 
-// SL_FP64 and SL_DF64 plans share every FP64 layout (G, cube, records, tables).
-inline bool plan_wide(int precision) { return precision != SL_FP32; }
+// SL_FP32 and SL_TF32X3 plans share every FP32 layout; SL_FP64 and SL_DF64
+// plans share every FP64 layout (G, cube, records, tables).
+inline bool plan_fp32(int precision) { return precision == SL_FP32 || precision == SL_TF32X3; }
+inline bool plan_wide(int precision) { return !plan_fp32(precision); }
 
 // ---------------------------------------------------------------- geometry
 // Everything the interpolation kernels need, passed by value.

@@ -132,6 +132,19 @@ def test_cube_and_tod_df64(sl, case):
     assert err_c < TOL64 and err < TOL64
 
 
+def test_cube_and_tod_tf32x3(sl, case):
+    """FP32 plan with the contraction on the tensor cores (3xTF32, one sky)."""
+    plan = _plan(sl, case, "tf32x3")
+    maps = sl.synth_spin_maps(plan, _dev(case["sky"]), _dev(case["beam"]))
+    plan.sync()
+    assert maps.dtype == torch.complex64
+    err_c = rel_l2(maps.cpu().numpy().astype(np.complex128), case["cube"])
+    tod = sl.interp_tod(plan, maps, _dev(case["th"]), _dev(case["ph"]), _dev(case["ps"]))
+    err = rel_l2(tod.cpu().numpy(), case["tod"])
+    print(case["name"], "tf32x3: cube rel L2 %.2e, tod rel L2 %.2e" % (err_c, err))
+    assert err_c < TOL32 and err < TOL32
+
+
 def test_interp_df64_same_cube(sl, case):
     """Double-float interpolation alone, reading the oracle's cube."""
     plan = _plan(sl, case, "df64")
