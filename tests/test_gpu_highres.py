@@ -1,6 +1,7 @@
 """Precision variant at lmax = 2048, kmax = 32 (2048 x 4096 equiangular rings,
-2e8 uniform pointings): the error of each precision mode against the oracle on
-a subset of about 1e6 samples, and FP32 against FP64 over the whole TOD.
+2e8 uniform pointings): the error of each precision mode (FP64, FP32, DF64 and
+the 3xTF32 tensor-core contraction) against the oracle on a subset of about 1e6
+samples, and FP32 against FP64 over the whole TOD.
 
 The oracle synthesises only the rings of three bands (polar, mid-latitude,
 equatorial); the subset is every pointing whose 4 x 4 stencil lies inside a
@@ -25,7 +26,7 @@ def highres():
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     out = {"cfg": cfg}
     th, ph, ps = dev(cfg["theta"]), dev(cfg["phi"]), dev(cfg["psi"])
-    for prec in ("fp64", "fp32", "df64"):
+    for prec in ("fp64", "fp32", "df64", "tf32x3"):
         plan = sl.sidelobe_plan_create(cfg["lmax"], cfg["kmax"], cfg["ring_theta"], cfg["nphi"], ncomp=1,
                                        precision=prec)
         maps = sl.synth_spin_maps(plan, dev(cfg["sky"]), dev(cfg["beam"]))
@@ -61,7 +62,7 @@ def test_highres_precision_modes_vs_oracle(highres, oracle_lib):
     rt, nphi = cfg["ring_theta"], cfg["nphi"]
     subsets = _band_subset(cfg)
     assert sum(s.size for s in subsets) >= 900_000
-    refs, got = [], {"fp64": [], "fp32": [], "df64": []}
+    refs, got = [], {"fp64": [], "fp32": [], "df64": [], "tf32x3": []}
     for (a, b), idx in zip(BANDS, subsets):
         band = rt[a:b + 1]
         cube = oracle_lib.cube_from_G(oracle_lib.cube_G(cfg["sky"], cfg["beam"], band), nphi)
@@ -69,7 +70,7 @@ def test_highres_precision_modes_vs_oracle(highres, oracle_lib):
         for prec in got:
             got[prec].append(highres[prec][idx])
     ref = np.concatenate(refs)
-    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5), ("df64", 1e-10)):
+    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5), ("df64", 1e-10), ("tf32x3", 1e-5)):
         g = np.concatenate(got[prec])
         err = rel_l2(g, ref)
         print("lmax=2048 kmax=32: %s TOD on %d-sample subset, rel L2 vs oracle %.2e, max|err|/rms %.2e"
