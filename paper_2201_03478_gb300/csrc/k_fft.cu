@@ -2,7 +2,8 @@
 // two-step algorithm: the synthesis along each ring) and its transpose.
 //
 // Synthesis (one CTA per (ring r, k)):
-//   H(q)  = sum_{m = q mod nphi, |m| <= L} G_k(r, m)     (exact alias folding)
+//   H(q)  = sum_{m = q mod nphi, |m| <= L} G_k(r, m)     (exact alias folding,
+//           G stored [k][m + L][r])
 //   F_k(r, phi_j) = sum_q H(q) e^{+2 pi i q j / nphi}    (inverse DFT)
 // written to maps[r][j][k].
 // Transpose (one CTA per (ring r, k)):
@@ -141,6 +142,8 @@ __device__ C *fft_smem(C *buf0, C *buf1, int N, const Radices &rad, const C *__r
     return src;
 }
 
+constexpr int kRingGroup = 4;   // rings per sector of an FP32 G row
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_ringfft_synth(int L, int K, int R, int N, Radices rad,
                                                        const typename CplxOf<T>::type *__restrict__ G,
@@ -150,17 +153,24 @@ __global__ void __launch_bounds__(256) k_ringfft_synth(int L, int K, int R, int 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf0 = reinterpret_cast<C *>(smem_raw);
     C *buf1 = buf0 + N;
-    const int k = blockIdx.x % (K + 1);
-    const int r = blockIdx.x / (K + 1);
+    // CTA order: kRingGroup consecutive rings fastest, then k, then the ring
+    // group, so that the rings sharing a sector of G (ring index fastest) and the
+    // k values sharing a sector of the cube ([r][j][k]) run close together
+    int b = blockIdx.x;
+    const int rlo = b % kRingGroup;
+    b /= kRingGroup;
+    const int k = b % (K + 1);
+    const int r = (b / (K + 1)) * kRingGroup + rlo;
+    if (r >= R) return;
     // blockIdx.y: sky of a multi-sky build (consecutive G and cube blocks)
     G += (int64_t)blockIdx.y * (K + 1) * R * (2 * L + 1);
     maps += (int64_t)blockIdx.y * R * N * (K + 1);
-    const C *g = G + ((int64_t)k * R + r) * (2 * L + 1);
+    const C *g = G + (int64_t)k * (2 * L + 1) * R + r;
     for (int q = threadIdx.x; q < N; q += blockDim.x) {
         // smallest m >= -L with m = q (mod N)
         int m = q - N * ((q + L) / N);
         C acc = mk<C>(0.0, 0.0);
-        for (; m <= L; m += N) acc = add(acc, g[m + L]);
+        for (; m <= L; m += N) acc = add(acc, g[(int64_t)(m + L) * R]);
         buf0[q] = acc;
     }
     __syncthreads();
@@ -198,7 +208,8 @@ static Radices radices_of(const sl_plan *p) {
 }
 
 sl_status launch_ringfft_synth_from(sl_plan *p, const void *G, int nsky, void *maps) {
-    const dim3 nblk((unsigned)((p->K + 1) * p->R), (unsigned)nsky);
+    const int ngrp = (p->R + kRingGroup - 1) / kRingGroup;
+    const dim3 nblk((unsigned)(ngrp * kRingGroup * (p->K + 1)), (unsigned)nsky);
     int slot;
     if (plan_wide(p->precision)) {
         const size_t sm = 2 * (size_t)p->nphi * sizeof(double2);

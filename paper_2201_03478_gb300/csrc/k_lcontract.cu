@@ -4,7 +4,8 @@
 //   G_k(r, m) = sum_{l >= max(|m|, k)} A_{k,lm} d^l_{mk}(theta_r),
 //   A_{k,lm}  = sum_X s^X_lm conj(b^X_lk),      m in [-L, L], k in [0, K],
 //
-// written to G[k][r][m + L].
+// written to G[k][m + L][r]: the ring index is fastest, so that the threads of a
+// CTA (consecutive ring pairs at one m) write contiguous runs.
 //
 // Reflections.  Per north ring, two l-recurrences, d^l_{m,+k}(theta_r) and
 // d^l_{m,-k}(theta_r), give four outputs through
@@ -90,23 +91,24 @@ template <typename C>
 __device__ __forceinline__ void write_two(const LcArgs &a, int m, int k, int pair, int neg, C acc1, C acc2) {
     C *G = reinterpret_cast<C *>(a.G);
     const int rn = pair, rs = a.R - 1 - pair;
-    const int64_t row = 2 * (int64_t)a.L + 1;
-    const int64_t base = (int64_t)k * a.R;
+    // rows (k, L + m) and (k, L - m) of G
+    C *gp = G + ((int64_t)k * (2 * a.L + 1) + a.L + m) * a.R;
+    C *gm = G + ((int64_t)k * (2 * a.L + 1) + a.L - m) * a.R;
     const bool modd = m & 1, kodd = k & 1;
     if (!neg) {
-        G[(base + rn) * row + a.L + m] = acc1;
+        gp[rn] = acc1;
         if (m > 0 && rs != rn) {
             if (modd != kodd) { acc2.x = -acc2.x; acc2.y = -acc2.y; }
-            G[(base + rs) * row + a.L - m] = acc2;
+            gm[rs] = acc2;
         }
     } else {
         if (m > 0) {
             if (kodd) { acc1.x = -acc1.x; acc1.y = -acc1.y; }
-            G[(base + rn) * row + a.L - m] = acc1;
+            gm[rn] = acc1;
         }
         if (rs != rn) {
             if (modd) { acc2.x = -acc2.x; acc2.y = -acc2.y; }
-            G[(base + rs) * row + a.L + m] = acc2;
+            gp[rs] = acc2;
         }
     }
 }

@@ -35,7 +35,7 @@ namespace sl {
 
 constexpr int kMsRows = 128;      // ring pairs per CTA (MMA M)
 constexpr int kMsLC = 32;         // l per chunk
-constexpr int kMsThreads = 256;
+constexpr int kMsThreads = 288;   // 4 W-producer warps, 4 V-producer warps, 1 MMA warp
 constexpr unsigned long long kMsWaitNs = 1000000000ull;   // bound of every mbarrier wait: 1 s
 
 struct MsArgs {
@@ -91,6 +91,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(dst)), "l"(src) : "memory");
 }
+// 8-byte copy; with ok == false nothing is read and the destination is zero-filled
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" :: "r"(smem_u32(dst)), "l"(src), "r"(ok ? 8 : 0)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int NPEND>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(NPEND) : "memory"); }
@@ -104,22 +109,24 @@ __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
 __device__ __forceinline__ void ms_write_two(const MsArgs &a, float2 *G, int m, int k, int pair, int neg, float2 acc1,
                                              float2 acc2) {
     const int rn = pair, rs = a.R - 1 - pair;
-    const int64_t row = 2 * (int64_t)a.L + 1, base = (int64_t)k * a.R;
+    // G[k][L +- m][r]: consecutive rows (ring pairs) of the CTA write contiguous runs
+    float2 *gp = G + ((int64_t)k * (2 * a.L + 1) + a.L + m) * a.R;
+    float2 *gm = G + ((int64_t)k * (2 * a.L + 1) + a.L - m) * a.R;
     const bool modd = m & 1, kodd = k & 1;
     if (!neg) {
-        G[(base + rn) * row + a.L + m] = acc1;
+        gp[rn] = acc1;
         if (m > 0 && rs != rn) {
             if (modd != kodd) { acc2.x = -acc2.x; acc2.y = -acc2.y; }
-            G[(base + rs) * row + a.L - m] = acc2;
+            gm[rs] = acc2;
         }
     } else {
         if (m > 0) {
             if (kodd) { acc1.x = -acc1.x; acc1.y = -acc1.y; }
-            G[(base + rn) * row + a.L - m] = acc1;
+            gm[rn] = acc1;
         }
         if (rs != rn) {
             if (modd) { acc2.x = -acc2.x; acc2.y = -acc2.y; }
-            G[(base + rs) * row + a.L + m] = acc2;
+            gp[rs] = acc2;
         }
     }
 }
@@ -128,13 +135,30 @@ __device__ __forceinline__ void ms_write_two(const MsArgs &a, float2 *G, int m, 
 // high and low parts, two buffers of 32 columns each) from column 128.
 constexpr int kMsTmemCols = 256;
 constexpr int kMsAcol = 128;
+constexpr int kMsNB = 2;            // operand buffers (chunks in flight)
+constexpr int kMsNS = 3;            // staging slots of the sky values (work units in flight)
+constexpr int kMsSlots = 12;        // float2 per V thread and unit: 4 skies x 3 components
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
+}
+
+// Roles (warp-specialized; no CTA-wide barrier inside the chunk loop):
+//   warps 0-3  W producers: thread = ring pair = TMEM lane; per chunk the 32
+//              recurrence steps, TF32 split, tcgen05.st into A buffer b;
+//              arrive on full_a[b];
+//   warps 4-7  V producers: lane = l - c0, warp over skies; sky x beam
+//              columns into the swizzled B buffer b; arrive on full_b[b];
+//   warp 8     MMA issuer (lane 0): waits full_a[b] and full_b[b], issues the
+//              12 MMAs of the chunk, commits them to empty[b];
+// the producers wait on empty[b] before refilling buffer b.  After the last
+// chunk the W warps wait for its commit and read the accumulator.
 __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a) {
     extern __shared__ unsigned char ms_raw[];
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ __align__(16) RTab32 tabs[2][kMsLC];   // this and the next chunk's coefficients
+    __shared__ __align__(8) uint64_t full_a[kMsNB], full_b[kMsNB], empty[kMsNB];
     __shared__ uint32_t tmem_base;
     __shared__ int s_lmin, s_fail;
+    volatile int *fail = &s_fail;   // set by any role whose bounded wait ran out
 
     int b = blockIdx.x;
     const int grp = b % a.ngroups;
@@ -155,7 +179,7 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a)
     float *base = reinterpret_cast<float *>(ms_raw + ((1024u - (raw & 1023u)) & 1023u));
     const int bfl = N * kMsLC;
 
-    // this thread's recurrence (threads 0..127 own the rows = TMEM lanes)
+    // W threads' recurrences (threads 0..127 own the rows = TMEM lanes)
     const int pair = rc * kMsRows + tid;
     float y = 0.f, D = 0.f, yc = 0.f;
     int ls = a.L + 1;
@@ -191,43 +215,40 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])) : "memory");
+        for (int q = 0; q < kMsNB; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&full_a[q])), "r"(kMsRows) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&full_b[q])), "r"(kMsRows) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[q])) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (tid < kMsLC && lstart + tid <= a.L) cp_async16(&tabs[0][tid], tab + lstart + tid);
-    cp_async_commit();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = ms_idesc(kMsRows, N);
-    const float2 *beam_k = a.beam + (int64_t)k * (a.L + 1);
-    const int lmin = max(m, k);
 
-    int issued = -1;    // last chunk whose MMAs were committed
-    for (int c = 0; c < nchunks; ++c) {
-        const int bi = c & 1;
-        const int c0 = lstart + c * kMsLC;
-        // the next chunk's coefficients (their buffer was last read by chunk c - 1)
-        if (tid < kMsLC && c0 + kMsLC + tid <= a.L) cp_async16(&tabs[bi ^ 1][tid], tab + c0 + kMsLC + tid);
-        cp_async_commit();
-        cp_async_wait<1>();
-        if (c >= 2 && !mbar_wait(smem_u32(&mbar[bi]), ((c - 2) >> 1) & 1)) s_fail = 1;
-        __syncthreads();
-        if (s_fail) break;
-        const RTab32 *tb = tabs[bi];
-        if (tid < kMsRows) {
-            // W row in tensor memory: y_l for l in [c0, c0 + 32), zero before the ring's start
+    if (warp < 4) {
+        // ---------------------------------------------------------------- W producers
+        // this warp's lane i holds the coefficients of l = c0 + i (prefetched one chunk ahead)
+        RTab32 tcur = {0.f, 0.f, 0.f, 0.f}, tnext = {0.f, 0.f, 0.f, 0.f};
+        if (lstart + lane <= a.L) tcur = tab[lstart + lane];
+        for (int c = 0; c < nchunks; ++c) {
+            const int bi = c % kMsNB;
+            const int c0 = lstart + c * kMsLC;
+            if (c + 1 < nchunks && c0 + kMsLC + lane <= a.L) tnext = tab[c0 + kMsLC + lane];
+            if (c >= kMsNB && !mbar_wait(smem_u32(&empty[bi]), ((c - kMsNB) / kMsNB) & 1)) *fail = 1;
+            if (*fail) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             uint32_t hv[kMsLC], lv[kMsLC];
 #pragma unroll
             for (int i = 0; i < kMsLC; ++i) {
                 const int l = c0 + i;
+                const float ta = __shfl_sync(0xffffffffu, tcur.a, i);
+                const float tc = __shfl_sync(0xffffffffu, neg ? tcur.cm : tcur.cp, i);
                 float v = 0.f;
                 if (l >= ls && l <= a.L) {
                     v = y;
-                    const RTab32 t = tb[i];
-                    D = fmaf(fmaf(-t.a, yc, neg ? t.cm : t.cp), y, D);
+                    D = fmaf(fmaf(-ta, yc, tc), y, D);
                     y += D;
                 }
                 float h, lo;
@@ -255,77 +276,119 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a)
                             "r"(lv[25]), "r"(lv[26]), "r"(lv[27]), "r"(lv[28]), "r"(lv[29]), "r"(lv[30]),
                             "r"(lv[31]) : "memory");
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(smem_u32(&full_a[bi]));
+            tcur = tnext;
         }
-        // V columns: lane = l - c0, warp w builds skies w, w + 8, ...; reads coalesced over l
-        {
-            float *Bh = base + bi * 2 * bfl, *Bl = Bh + bfl;
-            const int i = lane, l = c0 + i;
-            const bool live = l <= a.L && l >= lmin;
-            float2 bv[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-            float cl = 0.f;
-            if (live) {
+    } else if (warp < 8) {
+        // ---------------------------------------------------------------- V producers
+        // Work unit u = (chunk c, pass j): skies s = vw + 4t + 16j (t < 4) at l = c0 + lane.
+        // Their T/E/B values travel by cp.async into a 3-deep staging ring, two units
+        // ahead of the one being built; each thread reads back only its own slots.
+        const int vw = warp - 4, tv = tid - 128;
+        const float2 *beam_k = a.beam + (int64_t)k * (a.L + 1);
+        const int lmin = max(m, k);
+        const int i = lane, ch = i >> 2, lo4 = i & 3;
+        const int npass = (a.nsg + 15) >> 4, nunits = nchunks * npass;
+        float2 *stage = reinterpret_cast<float2 *>(base + 2 * kMsNB * bfl);
+        auto issue = [&](int u) {   // copies of unit u (every slot written: zero-filled where unused)
+            if (u < nunits) {
+                const int c = u / npass, j = u - c * npass, l = lstart + c * kMsLC + i;
+                const bool live = l <= a.L && l >= lmin;
+                float2 *dst = stage + (int64_t)(u % kMsNS) * kMsSlots * 128 + tv;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int s = vw + 4 * t + 16 * j, sky = s_first + s;
+#pragma unroll
+                    for (int X = 0; X < 3; ++X) {
+                        const bool ok = live && s < a.nsg && sky < a.nsky && X < a.ncomp;
+                        const float2 *src = ok ? a.sky + ((int64_t)sky * a.ncomp + X) * a.nalm + moff + l : a.sky;
+                        cp_async8(dst + (t * 3 + X) * 128, src, ok);
+                    }
+                }
+            }
+            cp_async_commit();
+        };
+        issue(0);
+        issue(1);
+        // beam and c_l of the next chunk are prefetched into registers
+        float2 bn[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        float cn = 0.f;
+        auto beam_of = [&](int c) {
+            const int l = lstart + c * kMsLC + i;
+            bn[0] = bn[1] = bn[2] = make_float2(0.f, 0.f);
+            cn = 0.f;
+            if (c < nchunks && l <= a.L && l >= lmin) {
 #pragma unroll
                 for (int X = 0; X < 3; ++X)
                     if (X < a.ncomp) {
-                        bv[X] = __ldg(beam_k + (int64_t)X * (a.K + 1) * (a.L + 1) + l);
-                        if (k == 0) bv[X].y = 0.f;
+                        bn[X] = __ldg(beam_k + (int64_t)X * (a.K + 1) * (a.L + 1) + l);
+                        if (k == 0) bn[X].y = 0.f;
                     }
-                cl = tb[i].c;
+                cn = __ldg(&tab[l].c);
             }
-            const float sc = (l & 1) ? -cl : cl;
-            const int ch = i >> 2, lo4 = i & 3;
-            // all of this thread's sky values first (up to 4 skies x 3 components in flight)
-            constexpr int kSpw = 32 / (kMsThreads / 32);     // skies per warp at most
-            float2 sv[kSpw][3];
+        };
+        beam_of(0);
+        float2 bv[3];
+        float cl = 0.f, sc = 0.f;
+        for (int u = 0; u < nunits; ++u) {
+            const int c = u / npass, j = u - c * npass, bi = c % kMsNB;
+            issue(u + 2);
+            cp_async_wait<2>();
+            if (j == 0) {
+                const int l = lstart + c * kMsLC + i;
 #pragma unroll
-            for (int t = 0; t < kSpw; ++t) {
-                const int sky = s_first + warp + 8 * t;
-                const bool ok = live && warp + 8 * t < a.nsg && sky < a.nsky;
-                const float2 *sp = a.sky + (int64_t)sky * a.ncomp * a.nalm + moff + l;
-#pragma unroll
-                for (int X = 0; X < 3; ++X)
-                    sv[t][X] = (ok && X < a.ncomp) ? __ldg(sp + (int64_t)X * a.nalm) : make_float2(0.f, 0.f);
+                for (int X = 0; X < 3; ++X) bv[X] = bn[X];
+                cl = cn;
+                sc = (l & 1) ? -cl : cl;
+                beam_of(c + 1);
+                if (c >= kMsNB && !mbar_wait(smem_u32(&empty[bi]), ((c - kMsNB) / kMsNB) & 1)) *fail = 1;
             }
+            if (*fail) break;
+            float *Bh = base + bi * 2 * bfl, *Bl = Bh + bfl;
+            const float2 *src = stage + (int64_t)(u % kMsNS) * kMsSlots * 128 + tv;
 #pragma unroll
-            for (int t = 0; t < kSpw; ++t) {
-                const int s = warp + 8 * t;
+            for (int t = 0; t < 4; ++t) {
+                const int s = vw + 4 * t + 16 * j;
                 if (s >= a.nsg) break;
-                const int sky = s_first + s;
-                float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-                if (live && sky < a.nsky) {
-                    float2 ap = {0.f, 0.f}, am = {0.f, 0.f};
+                float2 ap = {0.f, 0.f}, am = {0.f, 0.f};
 #pragma unroll
-                    for (int X = 0; X < 3; ++X) {
-                        float2 s2 = sv[t][X];
-                        if (m == 0) s2.y = 0.f;
-                        const float2 b2 = bv[X];
-                        ap.x += s2.x * b2.x + s2.y * b2.y;      // s conj(b)
-                        ap.y += s2.y * b2.x - s2.x * b2.y;
-                        am.x += s2.x * b2.x - s2.y * b2.y;      // conj(s) conj(b)
-                        am.y -= s2.y * b2.x + s2.x * b2.y;
-                    }
-                    const float2 p1 = neg ? am : ap, p2 = neg ? ap : am;
-                    v0 = cl * p1.x;
-                    v1 = cl * p1.y;
-                    v2 = sc * p2.x;
-                    v3 = sc * p2.y;
+                for (int X = 0; X < 3; ++X) {
+                    float2 s2 = src[(t * 3 + X) * 128];
+                    if (m == 0) s2.y = 0.f;
+                    const float2 b2 = bv[X];
+                    ap.x += s2.x * b2.x + s2.y * b2.y;      // s conj(b)
+                    ap.y += s2.y * b2.x - s2.x * b2.y;
+                    am.x += s2.x * b2.x - s2.y * b2.y;      // conj(s) conj(b)
+                    am.y -= s2.y * b2.x + s2.x * b2.y;
                 }
-                const float vv[4] = {v0, v1, v2, v3};
+                const float2 p1 = neg ? am : ap, p2 = neg ? ap : am;
+                const float vv[4] = {cl * p1.x, cl * p1.y, sc * p2.x, sc * p2.y};
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int row = 4 * s + j, off = row * 32 + ((ch ^ (row & 7)) << 2) + lo4;
+                for (int q = 0; q < 4; ++q) {
+                    const int row = 4 * s + q, off = row * 32 + ((ch ^ (row & 7)) << 2) + lo4;
                     float h, lo;
-                    tf32_split(vv[j], h, lo);
+                    tf32_split(vv[q], h, lo);
                     Bh[off] = h;
                     Bl[off] = lo;
                 }
             }
+            if (j == npass - 1) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(smem_u32(&full_b[bi]));
+            }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
+        cp_async_wait<0>();
+    } else if (lane == 0) {
+        // ---------------------------------------------------------------- MMA issuer
+        const uint32_t idesc = ms_idesc(kMsRows, N);
+        int issued = -1;   // last chunk whose MMAs were committed
+        for (int c = 0; c < nchunks; ++c) {
+            const int bi = c % kMsNB;
+            const uint32_t par = (c / kMsNB) & 1;
+            if (!mbar_wait(smem_u32(&full_a[bi]), par) || !mbar_wait(smem_u32(&full_b[bi]), par)) *fail = 1;
+            if (*fail) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const float *Bh = base + bi * 2 * bfl, *Bl = Bh + bfl;
             const uint32_t bh = smem_u32(Bh), bl = smem_u32(Bl);
             const uint32_t ahi = tmem + (uint32_t)(kMsAcol + bi * 64), alo = ahi + 32;
@@ -342,38 +405,43 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a)
                              :: "r"(tmem), "r"(alo + kk * 8), "l"(dbh), "r"(idesc) : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(&mbar[bi])) : "memory");
+                         :: "r"(smem_u32(&empty[bi])) : "memory");
+            issued = c;
         }
-        issued = c;
+        // MMAs still in flight (a failed wait elsewhere) must end before the dealloc
+        if (*fail && issued >= 0) mbar_wait(smem_u32(&empty[issued % kMsNB]), (issued / kMsNB) & 1);
     }
-    cp_async_wait<0>();   // no copy into shared memory outlives the loop
-    // every committed MMA has finished once the last commit has arrived
-    bool ok = !s_fail;
-    if (issued >= 0 && !mbar_wait(smem_u32(&mbar[issued & 1]), (issued >> 1) & 1)) ok = false;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!ok) {
-        if (tid == 0) atomicExch(a.err, 1);
-    } else if (warp < 4) {
-        // epilogue: lanes 32w..32w+31 are rows (ring pairs); 16 columns = 4 skies per load
-        const int row = warp * 32 + lane, pr = rc * kMsRows + row;
-        for (int cg = 0; cg < N / 16; ++cg) {
-            uint32_t r[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cg * 16);
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-                           "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                         : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (pr < a.npairs) {
+
+    // the last chunk's commit means every MMA of the CTA has finished
+    bool ok = true;
+    if (warp < 4) {
+        const int cl_ = nchunks - 1;
+        ok = !*fail && mbar_wait(smem_u32(&empty[cl_ % kMsNB]), (cl_ / kMsNB) & 1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) {
+            if (lane == 0) atomicExch(a.err, 1);
+        } else {
+            // epilogue: lanes 32w..32w+31 are rows (ring pairs); 16 columns = 4 skies per load
+            const int row = warp * 32 + lane, pr = rc * kMsRows + row;
+            for (int cg = 0; cg < N / 16; ++cg) {
+                uint32_t r[16];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cg * 16);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                               "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (pr < a.npairs) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int sky = s_first + cg * 4 + q;
-                    if (sky < a.nsky)
-                        ms_write_two(a, a.G + (int64_t)sky * a.gsky, m, k, pr, neg,
-                                     make_float2(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1])),
-                                     make_float2(__uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3])));
+                    for (int q = 0; q < 4; ++q) {
+                        const int sky = s_first + cg * 4 + q;
+                        if (sky < a.nsky)
+                            ms_write_two(a, a.G + (int64_t)sky * a.gsky, m, k, pr, neg,
+                                         make_float2(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1])),
+                                         make_float2(__uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3])));
+                    }
                 }
             }
         }
@@ -406,7 +474,9 @@ __global__ void k_to_f32_ms(const double2 *__restrict__ in, float2 *__restrict__
 
 size_t lcontract_mma_smem(int nsg, int ncomp) {
     (void)ncomp;
-    return 2 * 2 * (size_t)4 * nsg * kMsLC * sizeof(float) + 1024;   // B_hi, B_lo, two buffers
+    // B_hi, B_lo (two buffers), the sky staging ring, alignment slack
+    return 2 * kMsNB * (size_t)4 * nsg * kMsLC * sizeof(float) + (size_t)kMsNS * kMsSlots * 128 * sizeof(float2) +
+           1024;
 }
 
 int lcontract_mma_group(int nsky) {

@@ -200,7 +200,7 @@ struct sl_plan {
     int nradix = 0;
 
     // scratch
-    void *d_G = nullptr;              // [K+1][R][2L+1] complex (precision of the plan; FP64 for adjoint)
+    void *d_G = nullptr;              // [K+1][2L+1][R] complex, ring index fastest (precision of the plan)
     size_t G_bytes = 0;
     double2 *d_Gadj = nullptr;        // FP64 copy for FP32 plans (adjoint), else aliases d_G
     double2 *d_Fbar = nullptr;        // [R][nphi][K+1] adjoint cube
