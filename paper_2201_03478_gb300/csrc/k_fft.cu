@@ -91,7 +91,7 @@ __device__ __forceinline__ void dft_small(int R, C *v) {
 
 struct Radices {
     int n;
-    int r[kMaxRadices];
+    unsigned long long code;   // radix of pass i in bits [3i, 3i + 3)
 };
 
 template <typename C, bool INV, int R>
@@ -99,21 +99,28 @@ __device__ __forceinline__ void fft_pass(const C *__restrict__ src, C *__restric
                                          const C *__restrict__ tw) {
     const int NR = N / R;
     const int stride = N / (Ns * R);
+    // Ns = R_0 R_1 ... of the passes done; shifts and masks when it is a power of two
+    const bool p2 = (Ns & (Ns - 1)) == 0;
+    const int lg = __ffs(Ns) - 1;
     for (int t = threadIdx.x; t < NR; t += blockDim.x) {
-        const int kk = t % Ns;
+        const int kk = p2 ? (t & (Ns - 1)) : t % Ns;
+        const int blk = p2 ? (t >> lg) : t / Ns;
         C v[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-            C x = src[t + q * NR];
-            if (Ns > 1 && q > 0) {
-                C w = tw[kk * stride * q];
-                if (!INV) w.y = -w.y;
-                x = mulc(x, w);
+        for (int q = 0; q < R; ++q) v[q] = src[t + q * NR];
+        if (Ns > 1) {
+            // one table read per butterfly: w^2 .. w^(R-1) as products of w
+            C w = tw[kk * stride];
+            if (!INV) w.y = -w.y;
+            C wq = w;
+#pragma unroll
+            for (int q = 1; q < R; ++q) {
+                v[q] = mulc(v[q], wq);
+                if (q + 1 < R) wq = mulc(wq, w);
             }
-            v[q] = x;
         }
         dft_small<C, INV>(R, v);
-        const int base = (t / Ns) * Ns * R + kk;
+        const int base = blk * Ns * R + kk;
 #pragma unroll
         for (int q = 0; q < R; ++q) dst[base + q * Ns] = v[q];
     }
@@ -126,7 +133,7 @@ __device__ C *fft_smem(C *buf0, C *buf1, int N, const Radices &rad, const C *__r
     C *src = buf0, *dst = buf1;
     int Ns = 1;
     for (int pass = 0; pass < rad.n; ++pass) {
-        const int R = rad.r[pass];
+        const int R = (int)((rad.code >> (3 * pass)) & 7);
         switch (R) {
             case 4: fft_pass<C, INV, 4>(src, dst, N, Ns, tw); break;
             case 2: fft_pass<C, INV, 2>(src, dst, N, Ns, tw); break;
@@ -166,12 +173,28 @@ __global__ void __launch_bounds__(256) k_ringfft_synth(int L, int K, int R, int 
     G += (int64_t)blockIdx.y * (K + 1) * R * (2 * L + 1);
     maps += (int64_t)blockIdx.y * R * N * (K + 1);
     const C *g = G + (int64_t)k * (2 * L + 1) * R + r;
-    for (int q = threadIdx.x; q < N; q += blockDim.x) {
-        // smallest m >= -L with m = q (mod N)
-        int m = q - N * ((q + L) / N);
-        C acc = mk<C>(0.0, 0.0);
-        for (; m <= L; m += N) acc = add(acc, g[(int64_t)(m + L) * R]);
-        buf0[q] = acc;
+    // the first alias of kGather values of q per thread is loaded before any is used
+    constexpr int kGather = 8;
+    const bool p2n = (N & (N - 1)) == 0;
+    const int lgn = __ffs(N) - 1;
+    for (int q0 = threadIdx.x; q0 < N; q0 += kGather * blockDim.x) {
+        C v[kGather];
+#pragma unroll
+        for (int i = 0; i < kGather; ++i) {
+            const int q = q0 + i * (int)blockDim.x;
+            const int m = q - N * (p2n ? (q + L) >> lgn : (q + L) / N);   // smallest m >= -L, m = q (mod N)
+            v[i] = (q < N && m <= L) ? g[(int64_t)(m + L) * R] : mk<C>(0.0, 0.0);
+        }
+#pragma unroll
+        for (int i = 0; i < kGather; ++i) {
+            const int q = q0 + i * (int)blockDim.x;
+            if (q < N) {
+                C acc = v[i];
+                for (int m = q - N * (p2n ? (q + L) >> lgn : (q + L) / N) + N; m <= L; m += N)
+                    acc = add(acc, g[(int64_t)(m + L) * R]);
+                buf0[q] = acc;
+            }
+        }
     }
     __syncthreads();
     const C *res = fft_smem<C, true>(buf0, buf1, N, rad, tw);
@@ -203,7 +226,8 @@ __global__ void __launch_bounds__(256) k_ringdft_adjoint(int L, int K, int R, in
 static Radices radices_of(const sl_plan *p) {
     Radices r;
     r.n = p->nradix;
-    for (int i = 0; i < p->nradix; ++i) r.r[i] = p->radices[i];
+    r.code = 0;
+    for (int i = 0; i < p->nradix; ++i) r.code |= (unsigned long long)p->radices[i] << (3 * i);
     return r;
 }
 
