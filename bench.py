@@ -590,6 +590,228 @@ TRAFFIC = {
 
 
 # ----------------------------------------------------------------------------- CPU oracle timing
+ORB_SUBSAMPLE = 20
+# FP64 flops k_orb_nodes executes per node (DADD + DMUL + 2 DFMA from an ncu op
+# count of one launch, divided by the nodes): the three library sincos and the
+# rotation and quadratic form of Eq. dipole_fast.
+ORB_NODE_FLOPS = 152     # 65 DFMA + 22 DMUL per node (ncu op counts, 1e7-sample case)
+
+
+def orbital_inputs(n, rank):
+    import workloads as W
+    cfg = W.config_orbital(n=n, with_pointings=False)
+    th, ph, ps = W.pointings_scan(n, t0=shard_t0(rank, n))
+    return cfg, th, ph, ps
+
+
+def orbital_bytes(starts, n, s):
+    """Algorithmic DRAM bytes of k_orb_eval: the 8-byte TOD write per sample, the
+    node value and second derivative (16 B) per node, and the pointing (24 B) of
+    each remainder sample evaluated exactly."""
+    lens = np.diff(starts)
+    nodes = np.where(lens > 0, (lens - 1) // s + 1, 0)
+    rem = np.maximum(lens - 1 - s * (nodes - 1), 0) * (lens > 0)
+    return 8.0 * n + 16.0 * nodes.sum() + 24.0 * rem.sum(), int(nodes.sum()), int(rem.sum())
+
+
+def orbital_arm(args):
+    """Orbital dipole and quadrupole through the 4pi beam (Sect. 4): the rotation at
+    every 20th sample of each pointing period, a natural cubic spline in between,
+    the remainder exact; the exact per-sample GPU evaluation and the CPU oracle
+    are timed beside it."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2201_03478_gb300 as sl
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    n = int(args.n)
+    s = ORB_SUBSAMPLE
+    cfg, th, ph, ps = orbital_inputs(n, rank)
+    starts, beta = cfg["period_start"], cfg["beta"]
+    T0 = cfg["T0"]
+    q = sl.quad_factor(cfg["nu"], T0)
+    plan = sl.sidelobe_plan_create(cfg["lmax"], cfg["kmax"], cfg["ring_theta"], cfg["nphi"], ncomp=3,
+                                   precision="fp64", device=local)
+    ptg_h = [torch.from_numpy(a) for a in (th, ph, ps)]
+    theta, phi, psi = (t.to(device) for t in ptg_h)
+    beam = torch.from_numpy(cfg["beam"]).to(device)
+    tod = torch.empty(n, dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+
+    def step(sub=s):
+        sl.orbital_dipole_tod(plan, beam, T0, q, theta, phi, psi, starts, beta, subsample=sub, tod=tod)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if not bool(torch.isfinite(tod).all()):
+        raise RuntimeError("non-finite orbital TOD")
+    plan.enable_timing(True)
+    plan.kernel_stats(reset=True)
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    barrier(device)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(device)
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop() if rank == 0 else None
+    stats = plan.kernel_stats(reset=True)
+    plan.enable_timing(False)
+    ms_total = reduce_max(ms_total, device)
+    ms_step = ms_total / args.steps
+    value = world * n * args.steps / (ms_total / 1e3)
+    ref_tod = tod.clone()
+
+    # the exact per-sample evaluation (s = 1) on the GPU
+    ex_steps = max(1, min(args.steps, 3))
+    step(1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(ex_steps):
+        step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_exact = reduce_max(e0.elapsed_time(e1), device) / ex_steps
+    exact_err = float(torch.max(torch.abs(ref_tod - tod)) / torch.max(torch.abs(tod)))
+
+    bytes_eval, nnodes, nrem = orbital_bytes(starts, n, s)
+    roofs = {}
+    peaks = measured_peaks()
+    if "orb_eval" in stats and stats["orb_eval"][0] > 0:
+        # binding roof: FP64 (one DMUL + three DFMA per spline sample, the node flops per
+        # remainder sample) ahead of HBM (the algorithmic bytes above)
+        avg = stats["orb_eval"][1] / stats["orb_eval"][0]
+        fl = 7.0 * (n - nrem) + ORB_NODE_FLOPS * nrem
+        ach = fl / (avg / 1e3) / 1e12
+        hbm = bytes_eval / (avg / 1e3) / 1e9
+        roofs["orb_eval"] = {"bound": "alu", "achieved": round(ach, 4), "peak": round(PEAK_FP64_TFLOPS, 4),
+                             "unit": "TFLOP/s", "frac": round(ach / PEAK_FP64_TFLOPS, 4),
+                             "traffic": TRAFFIC.get(("orb_eval", "fp64")), "avg_ms": round(avg, 4),
+                             "flops_per_launch": fl, "bytes_per_launch": bytes_eval,
+                             "hbm_achieved_gbs": round(hbm, 1), "hbm_frac": round(hbm / peaks["hbm_gbs"], 4),
+                             "peak_note": "FP64 pipe: unit counts x 2.07 GHz max SM clock; HBM: measured copy "
+                                          "bandwidth (of measured)"}
+    if ORB_NODE_FLOPS and "orb_nodes" in stats and stats["orb_nodes"][0] > 0:
+        avg = stats["orb_nodes"][1] / stats["orb_nodes"][0]
+        fl = ORB_NODE_FLOPS * nnodes
+        ach = fl / (avg / 1e3) / 1e12
+        roofs["orb_nodes"] = {"bound": "alu", "achieved": round(ach, 4), "peak": round(PEAK_FP64_TFLOPS, 4),
+                              "unit": "TFLOP/s", "frac": round(ach / PEAK_FP64_TFLOPS, 4),
+                              "traffic": TRAFFIC.get(("orb_nodes", "fp64")), "avg_ms": round(avg, 4),
+                              "flops_per_launch": fl,
+                              "peak_note": "FP64 pipe: unit counts x 2.07 GHz max SM clock; flops per node are "
+                                           "the FP64 operations the kernel executes (rotation with its three "
+                                           "sincos, and the quadratic form)"}
+    dominant = max(stats.items(), key=lambda kv: kv[1][1])[0] if stats else None
+    out = {
+        "metric": "orbital dipole TOD samples/s (4pi beam; rotation every %dth sample + natural spline)" % s,
+        "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (LFI-like far-sidelobe beam, satellite scan, Earth-orbit velocities)",
+        "config": {"workload": "orbital dipole + quadrupole through the 4pi beam: %d scan samples per GPU in %d "
+                               "pointing periods of 40-70 min, rotation every %d samples" % (n, starts.size - 1, s),
+                   "subsample": s, "nodes": nnodes, "remainder_samples": nrem,
+                   "l2": "inputs larger than L2 (3 x 8 B x n pointings)"},
+        "roofline": roofs.get(dominant) if dominant in roofs else None,
+        "roofline_all": roofs,
+        "dominant_kernel": dominant,
+        "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in stats.items()},
+        "exact_gpu": {"value": world * n / (ms_exact / 1e3), "ms_per_step": ms_exact,
+                      "note": "every sample rotated exactly (subsample = 1)"},
+        "vs_gpu_exact": ms_exact / ms_step,
+        "spline_vs_exact_max_rel": exact_err,
+        "gpu_launches": int(sum(v[0] for v in stats.values()) / args.steps) + 1,   # + the moments kernel
+        "clocks": clk,
+    }
+    # ---- end to end through the public API from pinned host buffers
+    if args.e2e_steps > 0:
+        pin = [t.pin_memory() for t in ptg_h]
+        res = torch.empty(n, dtype=torch.float64, pin_memory=True)
+
+        def e2e():
+            for d, h in zip((theta, phi, psi), pin):
+                d.copy_(h, non_blocking=True)
+            step()
+            res.copy_(tod, non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e()
+        barrier(device)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e()
+        dt = reduce_max(time.perf_counter() - t0, device)
+        out["e2e"] = {"value": world * n * args.e2e_steps / dt, "unit": "samples/s",
+                      "h2d_bytes_per_step": int(sum(t.numel() * 8 for t in pin)), "d2h_bytes_per_step": int(n * 8),
+                      "steps": args.e2e_steps}
+        del pin, res
+    if rank == 0 and world == 1 and args.cpu_baseline:
+        out["cpu_baseline"] = orbital_cpu(cfg, th, ph, ps, s, 3)
+    elif rank == 0:
+        out["cpu_baseline"] = None
+    sl.plan_destroy(plan)
+    if rank == 0:
+        line = json.dumps(out)
+        print(line, flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                f.write(line + "\n")
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def orbital_cpu(cfg, th, ph, ps, s, nper_sample):
+    """The oracle (numpy, one thread) on the first whole pointing periods."""
+    from oracle import orbital as orb
+    starts, beta = cfg["period_start"], cfg["beta"]
+    e = int(starts[nper_sample])
+    S = orb.moments(cfg["beam"][0])
+    q = orb.quad_factor(cfg["nu"], cfg["T0"])
+    t0 = time.perf_counter()
+    orb.dipole_subsampled(S, cfg["T0"], q, th[:e], ph[:e], ps[:e], starts[:nper_sample + 1], beta[:nper_sample], s)
+    dt = time.perf_counter() - t0
+    return {"value": e / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": "the first %d pointing periods (%d samples), subsample %d, %.1f s" % (nper_sample, e, s, dt)}
+
+
+def orbital_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    n = int(args.n)
+    cfg, th, ph, ps = orbital_inputs(n, 0)
+    for _ in range(args.warmup):
+        orbital_cpu(cfg, th, ph, ps, ORB_SUBSAMPLE, 1)
+    per = [orbital_cpu(cfg, th, ph, ps, ORB_SUBSAMPLE, 3) for _ in range(args.steps)]
+    value = float(np.mean([p["value"] for p in per]))
+    out = {"impl": "reference",
+           "metric": "orbital dipole TOD samples/s (4pi beam; rotation every %dth sample + natural spline)"
+                     % ORB_SUBSAMPLE,
+           "value": world * value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": n / value * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (LFI-like far-sidelobe beam, satellite scan, Earth-orbit velocities)",
+           "config": {"workload": "orbital dipole + quadrupole through the 4pi beam: %d scan samples per GPU, "
+                                  "rotation every %d samples" % (n, ORB_SUBSAMPLE), "subsample": ORB_SUBSAMPLE},
+           "cpu_baseline": dict(per[-1], value=value),
+           "e2e": {"value": world * value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
 def oracle_sample(cfg, th, ph, ps, n, ring_sample, samp_n):
     """Time the CPU FP64 oracle on a bounded sample of one step and extrapolate:
     spin Legendre step + DFT for `ring_sample` of the rings, interpolation of
@@ -671,10 +893,12 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["fp64", "fp32", "df64", "tf32x3"], default="fp64")
-    ap.add_argument("--workload", choices=["lfi", "highres", "detectors", "multisky"], default="lfi",
+    ap.add_argument("--workload", choices=["lfi", "highres", "detectors", "multisky", "orbital"], default="lfi",
                     help="lfi: T/E/B, lmax 1024, kmax 16, scan (the headline); "
                          "highres: lmax 2048, kmax 32, 2048 x 4096 rings, uniform pointings (precision variant); "
-                         "detectors: 22 detectors of uneven lmax/kmax in one CUDA graph (batch variant)")
+                         "detectors: 22 detectors of uneven lmax/kmax in one CUDA graph (batch variant); "
+                         "multisky: cubes of many skies with one beam (tensor cores); "
+                         "orbital: orbital dipole through the 4pi beam")
     ap.add_argument("--ndet", type=int, default=22, help="detectors of the batch workload")
     ap.add_argument("--nsky", type=int, default=32, help="skies of the multi-sky workload")
     ap.add_argument("--tile-cols", type=int, default=0, help="sort-tile width (8, 16, 32; 0: the plan's default)")
@@ -699,10 +923,14 @@ def main(argv=None):
     rank, world, _ = dist_env()
     if world != args.gpus:
         print("note: WORLD_SIZE=%d, --gpus=%d; using WORLD_SIZE" % (world, args.gpus), file=sys.stderr)
-    if args.impl == "reference":
+    if args.impl == "reference" and args.workload == "orbital":
+        orbital_reference(args)
+    elif args.impl == "reference":
         if args.cpu_samples > 2_000_000:
             args.cpu_samples = 2_000_000
         reference_arm(args)
+    elif args.workload == "orbital":
+        orbital_arm(args)
     elif args.workload == "detectors":
         detectors_arm(args)
     elif args.workload == "multisky":

@@ -194,6 +194,46 @@ sl_status adjoint_synth(sl_plan *plan, const double *maps_bar, const double *sky
 sl_status interp_tod_noalloc(sl_plan *plan, const void *maps, const double *theta, const double *phi,
                              const double *psi, int64_t n, double *tod);
 
+/* ---------------------------------------------------------------------------
+ * Orbital dipole and quadrupole through the full 4pi beam (Sect. 4, Eqs.
+ * dipole_simple, dipole and dipole_fast).  The satellite velocity beta = v/c
+ * (one 3-vector per pointing period, in the frame of the pointings) gives the
+ * sky signal D(n) = T0 [beta.n + q (beta.n)^2]; seen through the beam it is
+ *
+ *   D~ = T0 [ S_x b'_x + S_y b'_y + S_z b'_z + q ( S_xx b'_x^2 + S_yy b'_y^2
+ *             + S_zz b'_z^2 + 2 S_xy b'_x b'_y + 2 S_xz b'_x b'_z + 2 S_yz b'_y b'_z ) ],
+ *
+ * b' = R^T beta with R = Rz(phi) Ry(theta) Rz(psi) (the rotation of the
+ * convolution above), S_v = int v B dOmega the moments of the temperature beam
+ * B = sum b_lk Y_lk in its own frame (boresight +z); only l <= 2 enters.
+ *
+ * sl_orbital_moments: the nine moments {S_x, S_y, S_z, S_xx, S_yy, S_zz, S_xy,
+ *   S_xz, S_yz} of the beam (DEVICE, the plan's beam layout; component 0 is
+ *   the temperature beam) into S (HOST, 9 doubles).  Synchronises the stream.
+ *
+ * orbital_dipole_tod: the TOD D~ for n samples (theta, phi, psi: DEVICE, n
+ *   doubles; tod: DEVICE, n doubles, overwritten or, with accumulate != 0,
+ *   added to).  The samples form nper consecutive pointing periods:
+ *   period_start (HOST, nper + 1 int64, 0 = period_start[0] <= ... <=
+ *   period_start[nper] = n) and beta (HOST, [nper][3] doubles).  T0 [K] and q
+ *   (the quadrupole factor (a/2)(e^a + 1)/(e^a - 1), a = h nu / (k_B T0)) scale
+ *   the result.  subsample = s: within each period the rotation is evaluated at
+ *   local samples 0, s, 2s, ... only, a natural cubic spline through those node
+ *   values gives the samples between them, and the samples after the last node
+ *   (the remainder that s does not divide) are evaluated exactly (the paper's
+ *   acceleration, s = 20 there); s = 1 evaluates every sample exactly.
+ *   1 <= s <= 65536; a period holds fewer than 2^31 samples.  The period
+ *   tables go through a pinned staging buffer of the plan into device scratch
+ *   (both grown on demand; growth synchronises the stream); the call returns
+ *   once the previous call's upload has left the staging buffer.  Errors:
+ *   SL_ERR_ARG for NULL buffers, n < 0, s out of range, non-finite T0, q or
+ *   beta, or period_start not running from 0 to n; SL_ERR_NOMEM if the
+ *   scratch cannot grow. */
+sl_status sl_orbital_moments(sl_plan *plan, const double *beam, double *S);
+sl_status orbital_dipole_tod(sl_plan *plan, const double *beam, double T0, double q, const double *theta,
+                             const double *phi, const double *psi, int64_t n, const int64_t *period_start,
+                             const double *beta, int64_t nper, int subsample, double *tod, int accumulate);
+
 /* Frees the plan and everything it owns (after synchronising its stream).
  * NULL is a no-op. */
 void plan_destroy(sl_plan *plan);

@@ -16,6 +16,7 @@ come back in the same layouts, as d/dRe + i d/dIm of sum_i tod_i c_i.
 from __future__ import annotations
 
 import ctypes
+import math
 
 import numpy as np
 import torch
@@ -177,6 +178,48 @@ def interp_tod(plan: Plan, maps, theta, phi, psi, tod=None):
     _dev_tensor(tod, torch.float64, plan.device, "tod", (n,))
     plan._sync_stream()
     check(_lib.load().interp_tod(plan.ptr, _ptr(maps), _ptr(theta), _ptr(phi), _ptr(psi), n, _ptr(tod)))
+    return tod
+
+
+def quad_factor(nu_hz: float, T0: float) -> float:
+    """The quadrupole factor of the orbital dipole: (a/2)(e^a + 1)/(e^a - 1) with
+    a = h nu / (k_B T0) (h, k_B exact SI values)."""
+    a = 6.62607015e-34 * nu_hz / (1.380649e-23 * T0)
+    return 0.5 * a * (math.exp(a) + 1.0) / math.expm1(a)
+
+
+def orbital_moments(plan: Plan, beam):
+    """The nine moments [S_x, S_y, S_z, S_xx, S_yy, S_zz, S_xy, S_xz, S_yz] of the
+    temperature beam (component 0 of the plan's beam layout), as numpy float64."""
+    beam = _dev_tensor(beam, torch.complex128, plan.device, "beam", (plan.ncomp, plan.kmax + 1, plan.lmax + 1))
+    S = np.zeros(9, dtype=np.float64)
+    plan._sync_stream()
+    check(_lib.load().sl_orbital_moments(plan.ptr, _ptr(beam), S.ctypes.data_as(ctypes.c_void_p)))
+    return S
+
+
+def orbital_dipole_tod(plan: Plan, beam, T0, q, theta, phi, psi, period_start, beta, subsample=20, tod=None,
+                       accumulate=False):
+    """Orbital dipole and quadrupole through the 4pi beam (Sect. 4, Eq. dipole_fast).
+
+    period_start: nper + 1 sample offsets (host, 0 ... n); beta: [nper, 3] velocity / c
+    per pointing period (host); subsample: rotation at every s-th sample of a period,
+    natural cubic spline in between, the remainder exact (s = 1: exact everywhere)."""
+    beam = _dev_tensor(beam, torch.complex128, plan.device, "beam", (plan.ncomp, plan.kmax + 1, plan.lmax + 1))
+    n = _ptg(plan, theta, phi, psi)
+    starts = np.ascontiguousarray(np.asarray(period_start, dtype=np.int64))
+    bet = np.ascontiguousarray(np.asarray(beta, dtype=np.float64).reshape(-1, 3))
+    nper = starts.size - 1
+    if nper < 1 or bet.shape[0] != nper:
+        raise ValueError("period_start must have nper + 1 entries and beta nper rows")
+    if tod is None:
+        tod = torch.empty(n, dtype=torch.float64, device=theta.device)
+    _dev_tensor(tod, torch.float64, plan.device, "tod", (n,))
+    plan._sync_stream()
+    check(_lib.load().orbital_dipole_tod(plan.ptr, _ptr(beam), float(T0), float(q), _ptr(theta), _ptr(phi),
+                                         _ptr(psi), n, starts.ctypes.data_as(ctypes.c_void_p),
+                                         bet.ctypes.data_as(ctypes.c_void_p), nper, int(subsample), _ptr(tod),
+                                         1 if accumulate else 0))
     return tod
 
 

@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
+#include <vector>
 #include <new>
 
 #include "sl_internal.cuh"
@@ -284,6 +286,9 @@ void plan_destroy(sl_plan *p) {
     dfree(p->d_skym32);
     dfree(p->d_Gm);
     dfree(p->d_err);
+    dfree(p->d_orb);
+    if (p->h_orb) cudaFreeHost(p->h_orb);
+    if (p->orb_ev) cudaEventDestroy(p->orb_ev);
     dfree(p->d_rowtab_df);
     dfree(p->sort.hist);
     dfree(p->sort.cursor);
@@ -698,6 +703,134 @@ sl_status synth_spin_maps_multi(sl_plan *p, int nsky, const double *sky, const d
     }
     if ((st = launch_lcontract_mma(p, nsky, sky, beam, p->d_skym32, p->d_Gm, p->d_err)) != SL_OK) return st;
     return launch_ringfft_synth_from(p, p->d_Gm, nsky, maps);
+}
+
+// ------------------------------------------------------------------ orbital dipole
+static sl_status orb_scratch(sl_plan *p, size_t bytes) {
+    if (bytes <= p->orb_bytes) return SL_OK;
+    cudaStreamSynchronize(p->stream);
+    if (p->d_orb) {
+        dfree(p->d_orb);
+        p->bytes_held -= (int64_t)p->orb_bytes;
+    }
+    p->d_orb = nullptr;
+    p->orb_bytes = 0;
+    sl_status st = dalloc(p, (void **)&p->d_orb, bytes, "orbital dipole scratch");
+    if (st == SL_OK) p->orb_bytes = bytes;
+    return st;
+}
+
+constexpr size_t kOrbS = 16;   // doubles reserved for the moments at the start of the scratch
+
+sl_status sl_orbital_moments(sl_plan *p, const double *beam, double *S) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if (!beam || !S) return set_error(SL_ERR_ARG, "sl_orbital_moments: NULL buffer");
+    if ((st = orb_scratch(p, kOrbS * sizeof(double))) != SL_OK) return st;
+    if ((st = launch_orb_moments(p, beam, p->d_orb)) != SL_OK) return st;
+    if ((st = cuda_check(cudaMemcpyAsync(S, p->d_orb, 9 * sizeof(double), cudaMemcpyDeviceToHost, p->stream),
+                         "moments copy")) != SL_OK)
+        return st;
+    return cuda_check(cudaStreamSynchronize(p->stream), "stream synchronize");
+}
+
+sl_status orbital_dipole_tod(sl_plan *p, const double *beam, double T0, double q, const double *theta,
+                             const double *phi, const double *psi, int64_t n, const int64_t *period_start,
+                             const double *beta, int64_t nper, int subsample, double *tod, int accumulate) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if (n < 0) return set_error(SL_ERR_ARG, "orbital_dipole_tod: n=%lld < 0", (long long)n);
+    if (subsample < 1 || subsample > (1 << 16))
+        return set_error(SL_ERR_ARG, "orbital_dipole_tod: subsample=%d outside [1, 65536]", subsample);
+    if (!std::isfinite(T0) || !std::isfinite(q)) return set_error(SL_ERR_ARG, "orbital_dipole_tod: T0, q not finite");
+    if (n == 0) return SL_OK;
+    if (!beam || !theta || !phi || !psi || !tod || !period_start || !beta)
+        return set_error(SL_ERR_ARG, "orbital_dipole_tod: NULL buffer");
+    if (nper < 1 || period_start[0] != 0 || period_start[nper] != n)
+        return set_error(SL_ERR_ARG, "orbital_dipole_tod: period_start must run from 0 to n over nper >= 1 periods");
+    // the pinned staging buffer is reused: wait until the previous upload has left it
+    if (p->orb_ev && (st = cuda_check(cudaEventSynchronize(p->orb_ev), "orbital staging")) != SL_OK) return st;
+    // host tables: [start | noff] as int64, then beta [nper][3], the elimination
+    // pivots c_j = 1 / (4 - c_{j-1}) (c_0 = 0) and the spline weights of the
+    // positions r = 0 .. s between two nodes (B = r/s, A = 1 - B)
+    constexpr int kPiv = 40;
+    const size_t nw = 4 * ((size_t)subsample + 1);
+    // layout [weights | pivots | start | noff | beta]: the weights (read as 32-byte
+    // vectors) first, at a 32-byte aligned offset of the scratch
+    const size_t tab_bytes = (nw + kPiv + 2 * (size_t)(nper + 1) + 3 * (size_t)nper) * sizeof(int64_t);
+    if (tab_bytes > p->h_orb_bytes) {
+        if (p->h_orb) cudaFreeHost(p->h_orb);
+        p->h_orb = nullptr;
+        p->h_orb_bytes = 0;
+        if (cudaHostAlloc(&p->h_orb, tab_bytes, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            p->h_orb = nullptr;
+            return set_error(SL_ERR_NOMEM, "orbital_dipole_tod: pinned staging of %zu bytes", tab_bytes);
+        }
+        p->h_orb_bytes = tab_bytes;
+    }
+    if (!p->orb_ev && (st = cuda_check(cudaEventCreateWithFlags(&p->orb_ev, cudaEventDisableTiming),
+                                       "orbital event")) != SL_OK)
+        return st;
+    double *wt = reinterpret_cast<double *>(p->h_orb), *piv = wt + nw;
+    int64_t *start = reinterpret_cast<int64_t *>(piv + kPiv), *noff = start + (nper + 1);
+    double *bet = reinterpret_cast<double *>(noff + (nper + 1));
+    piv[0] = 0.0;
+    for (int j = 1; j < kPiv; ++j) piv[j] = 1.0 / (4.0 - piv[j - 1]);
+    const double sd = (double)subsample, h2 = sd * sd / 6.0;
+    for (int r = 0; r <= subsample; ++r) {
+        const double B = (double)r / sd, A = 1.0 - B;
+        wt[4 * r + 0] = A;
+        wt[4 * r + 1] = B;
+        wt[4 * r + 2] = (A * A * A - A) * h2;
+        wt[4 * r + 3] = (B * B * B - B) * h2;
+    }
+    noff[0] = 0;
+    for (int64_t k = 0; k < nper; ++k) {
+        const int64_t np = period_start[k + 1] - period_start[k];
+        if (np < 0) return set_error(SL_ERR_ARG, "orbital_dipole_tod: period_start decreases at period %lld", (long long)k);
+        if (np >= ((int64_t)1 << 31))
+            return set_error(SL_ERR_ARG, "orbital_dipole_tod: period %lld has 2^31 samples or more", (long long)k);
+        start[k] = period_start[k];
+        noff[k + 1] = noff[k] + (subsample > 1 && np > 0 ? (np - 1) / subsample + 1 : 0);
+        for (int c = 0; c < 3; ++c) {
+            bet[3 * k + c] = beta[3 * k + c];
+            if (!std::isfinite(beta[3 * k + c])) return set_error(SL_ERR_ARG, "orbital_dipole_tod: beta not finite");
+        }
+    }
+    start[nper] = n;
+    const int64_t nnodes = noff[nper];
+    const size_t need = kOrbS * sizeof(double) + tab_bytes + 2 * (size_t)nnodes * sizeof(double);
+    if ((st = orb_scratch(p, need)) != SL_OK) return st;
+    char *base = reinterpret_cast<char *>(p->d_orb);
+    int64_t *d_tab = reinterpret_cast<int64_t *>(base + kOrbS * sizeof(double));
+    double *d_nodes = reinterpret_cast<double *>(base + kOrbS * sizeof(double) + tab_bytes);
+    if ((st = cuda_check(cudaMemcpyAsync(d_tab, p->h_orb, tab_bytes, cudaMemcpyHostToDevice, p->stream),
+                         "orbital tables")) != SL_OK)
+        return st;
+    if ((st = cuda_check(cudaEventRecord(p->orb_ev, p->stream), "orbital event")) != SL_OK) return st;
+    if ((st = launch_orb_moments(p, beam, p->d_orb)) != SL_OK) return st;
+    OrbLaunch o;
+    o.theta = theta;
+    o.phi = phi;
+    o.psi = psi;
+    o.w = reinterpret_cast<const double *>(d_tab);
+    o.piv = o.w + nw;
+    o.start = d_tab + nw + kPiv;
+    o.noff = o.start + (nper + 1);
+    o.beta = reinterpret_cast<const double *>(o.noff + (nper + 1));
+    o.S = p->d_orb;
+    o.T0 = T0;
+    o.q = q;
+    o.n = n;
+    o.nper = nper;
+    o.nnodes = nnodes;
+    o.s = subsample;
+    o.y = d_nodes;
+    o.M2 = d_nodes + nnodes;
+    o.tod = tod;
+    o.accumulate = accumulate != 0;
+    return launch_orbital(p, o);
 }
 
 sl_status sl_plan_enable_timing(sl_plan *p, int enable) {

@@ -218,6 +218,12 @@ struct sl_plan {
     float2 *d_Gm = nullptr;
     int *d_err = nullptr;
     int msky_cap = 0;
+    // orbital dipole (grown on demand): moments, period tables, spline nodes
+    double *d_orb = nullptr;
+    size_t orb_bytes = 0;
+    void *h_orb = nullptr;              // pinned staging of the period tables
+    size_t h_orb_bytes = 0;
+    cudaEvent_t orb_ev = nullptr;       // recorded after the last table upload
     // number of captured batch graphs that hold pointers into this plan's
     // scratch: while > 0 nothing may be reallocated (the graphs would dangle)
     int batch_refs = 0;
@@ -238,6 +244,22 @@ sl_status cuda_check(cudaError_t e, const char *what);
 // timing (plan.cu): returns an index; call timing_end after the launch
 int timing_begin(sl_plan *p, const char *name);
 void timing_end(sl_plan *p, int idx);
+
+// orbital dipole (k_orbital.cu): device pointers of one call
+struct OrbLaunch {
+    const double *theta, *phi, *psi;
+    const int64_t *start, *noff;
+    const double *beta, *S;
+    const double *piv;       // elimination pivots c_1 .. c_39 (c_0 = 0), the last one the limit
+    const double *w;         // [s][4] spline weights per position between nodes
+    double T0, q;
+    int64_t n, nper, nnodes;
+    int s;
+    double *y, *M2, *tod;
+    int accumulate;
+};
+sl_status launch_orb_moments(sl_plan *p, const double *beam, double *S);
+sl_status launch_orbital(sl_plan *p, const OrbLaunch &o);
 
 // launchers (one per translation unit)
 sl_status launch_seeds(sl_plan *p, const double *d_c2, const double *d_s2, const double *d_cs);

@@ -83,6 +83,8 @@ def test_null_arguments(lib):
     lib.plan_destroy(None)
     assert lib.sl_plan_reserve(None, 10) == -1
     assert lib.sl_plan_set_tile_cols(None, 16) == -1
+    assert lib.sl_orbital_moments(None, None, None) == -1
+    assert lib.orbital_dipole_tod(None, None, 2.7255, 1.0, None, None, None, 0, None, None, 0, 20, None, 0) == -1
 
 
 def test_batch_arguments_are_checked_before_any_device_call(lib):

@@ -273,3 +273,41 @@ def config_detectors(ndet: int = 22, sky_lmax: int = 1500, seed: int = 3, with_p
             det["theta"], det["phi"], det["psi"] = pointings_scan(n, psi_offset=psi_off, offset=offset)
         dets.append(det)
     return dets
+
+
+def pointing_periods(n: int, fsamp: float = 32.5, minutes=(40.0, 70.0), seed: int = 4) -> np.ndarray:
+    """Offsets (nper + 1 int64, 0 ... n) of consecutive pointing periods whose
+    lengths are uniform in ``minutes`` at ``fsamp`` Hz (the last one truncated)."""
+    rng = np.random.default_rng(seed)
+    lo, hi = (int(round(m * 60.0 * fsamp)) for m in minutes)
+    starts = [0]
+    while starts[-1] < n:
+        starts.append(min(n, starts[-1] + int(rng.integers(lo, hi + 1))))
+    return np.asarray(starts, dtype=np.int64)
+
+
+def orbital_velocity(starts: np.ndarray, fsamp: float = 32.5, seed: int = 5) -> np.ndarray:
+    """beta = v / c per pointing period [nper, 3] (ecliptic frame of the scan):
+    the Earth's orbital velocity (29.78 km/s along the orbit, longitude 2 pi t /
+    (365.25 d) at mid-period) plus a 0.3 km/s Gaussian jitter per component."""
+    rng = np.random.default_rng(seed)
+    c = 299792458.0
+    tmid = 0.5 * (starts[:-1] + starts[1:]) / fsamp
+    lam = 2.0 * math.pi * tmid / (365.25 * 86400.0)
+    v = 29.78e3 * np.stack([-np.sin(lam), np.cos(lam), np.zeros_like(lam)], -1)
+    v += rng.standard_normal(v.shape) * 0.3e3
+    return v / c
+
+
+def config_orbital(n: int = 100_000_000, with_pointings: bool = True):
+    """Orbital dipole through the 4pi beam: the LFI-like beam (lmax=1024, kmax=16,
+    T/E/B; the temperature beam's l <= 2 coefficients enter), the 32.5 Hz scan,
+    40-70 minute pointing periods, Earth-orbit velocities, T0 = 2.7255 K and a
+    70 GHz channel."""
+    d = dict(lmax=1024, kmax=16, beam=beam_far_sidelobe(1024, 16, seed=1),
+             ring_theta=equiangular_ring_theta(1024), nphi=2048, T0=2.7255, nu=70e9)
+    d["period_start"] = pointing_periods(n)
+    d["beta"] = orbital_velocity(d["period_start"])
+    if with_pointings:
+        d["theta"], d["phi"], d["psi"] = pointings_scan(n)
+    return d
