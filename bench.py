@@ -590,6 +590,126 @@ TRAFFIC = {
 
 
 # ----------------------------------------------------------------------------- CPU oracle timing
+def psigrid_arm(args):
+    """Step 2 as the paper states it: the transform over k to a psi grid and
+    Lagrange interpolation in theta, phi and psi, against the exact phase sum
+    (same plan, cube and pointings)."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2201_03478_gb300 as sl
+    import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    n = int(args.n)
+    cfg = W.config_lfi(with_pointings=False)
+    L, K, rt, nphi = cfg["lmax"], cfg["kmax"], cfg["ring_theta"], cfg["nphi"]
+    npsi = args.npsi or 2 * K + 2
+    th, ph, ps = W.pointings_scan(n, t0=shard_t0(rank, n))
+    ptg_h = [torch.from_numpy(a) for a in (th, ph, ps)]
+    theta, phi, psi = (t.to(device) for t in ptg_h)
+    sky = torch.from_numpy(cfg["sky"]).to(device)
+    beam = torch.from_numpy(cfg["beam"]).to(device)
+    plan = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=3, precision=args.precision, device=local)
+    maps = torch.empty(plan.maps_shape(), dtype=plan.maps_dtype, device=device)
+    rdt = torch.float64 if plan.maps_dtype == torch.complex128 else torch.float32
+    cube_psi = torch.empty((rt.size, nphi, npsi), dtype=rdt, device=device)
+    tod = torch.empty(n, dtype=torch.float64, device=device)
+    tod_x = torch.empty(n, dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+
+    def step():
+        sl.synth_spin_maps(plan, sky, beam, maps)
+        sl.synth_psi_cube(plan, maps, npsi, cube_psi)
+        sl.interp_tod_psi(plan, cube_psi, theta, phi, psi, tod)
+
+    def step_exact():
+        sl.synth_spin_maps(plan, sky, beam, maps)
+        sl.interp_tod(plan, maps, theta, phi, psi, tod_x)
+
+    def timed(fn, steps, stats_on=False):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        if stats_on:
+            plan.enable_timing(True)
+            plan.kernel_stats(reset=True)
+        barrier(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return reduce_max(e0.elapsed_time(e1), device) / steps
+
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    ms_step = timed(step, args.steps, stats_on=True)
+    clk = clocks.stop() if rank == 0 else None
+    stats = plan.kernel_stats(reset=True)
+    plan.enable_timing(False)
+    ms_exact = timed(step_exact, max(1, min(args.steps, 3)))
+    err = float(torch.linalg.vector_norm(tod - tod_x) / torch.linalg.vector_norm(tod_x))
+    prec = args.precision
+    wide = prec in ("fp64", "df64")
+    P = 4
+    roofs = {}
+    nm = "interp_psi_f64" if wide else "interp_psi_f32"
+    peak = PEAK_FP64_TFLOPS if wide else PEAK_FP32_TFLOPS
+    if nm in stats and stats[nm][0] > 0:
+        # p^3 weighted terms, the p^2 and p partial sums and weight products: 2 (p^3 + p^2 + p) flops a sample
+        fl = 2.0 * (P ** 3 + P ** 2 + P) * n
+        avg = stats[nm][1] / stats[nm][0]
+        ach = fl / (avg / 1e3) / 1e12
+        roofs[nm] = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                     "frac": round(ach / peak, 4), "traffic": None, "avg_ms": round(avg, 4), "flops_per_launch": fl,
+                     "peak_note": "unit counts x 2.07 GHz max SM clock"}
+    nc = "psi_cube_f64" if wide else "psi_cube_f32"
+    if nc in stats and stats[nc][0] > 0:
+        fl = 4.0 * rt.size * nphi * npsi * (K + 1)
+        avg = stats[nc][1] / stats[nc][0]
+        ach = fl / (avg / 1e3) / 1e12
+        roofs[nc] = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                     "frac": round(ach / peak, 4), "traffic": None, "avg_ms": round(avg, 4), "flops_per_launch": fl,
+                     "peak_note": "unit counts x 2.07 GHz max SM clock"}
+    dominant = max(stats.items(), key=lambda kv: kv[1][1])[0] if stats else None
+    out = {
+        "metric": "TOD samples/s via the psi-grid cube (cube build + psi transform + 3-D interp) at "
+                  "lmax=%d,kmax=%d; vs exact phase sum" % (L, K),
+        "value": world * n / (ms_step / 1e3), "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE.get(prec, prec),
+        "data": "synthetic (seeded T/E/B sky, far-sidelobe beam, satellite scan)",
+        "config": {"workload": "psi-grid variant: LFI-like T/E/B, lmax=%d, kmax=%d, %d rings x %d phi, npsi=%d, "
+                               "%d scan pointings per GPU" % (L, K, rt.size, nphi, npsi, n),
+                   "npsi": npsi, "precision": prec, "l2": "inputs larger than L2"},
+        "roofline": roofs.get(dominant), "roofline_all": roofs, "dominant_kernel": dominant,
+        "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in stats.items()},
+        "exact_phase_sum": {"value": world * n / (ms_exact / 1e3), "ms_per_step": ms_exact},
+        "speedup_vs_exact_phase_sum": ms_exact / ms_step,
+        "tod_rel_l2_vs_exact_phase_sum": err,
+        "gpu_launches": int(sum(v[0] for v in stats.values()) / args.steps),
+        "clocks": clk,
+        "cpu_baseline": None,
+    }
+    sl.plan_destroy(plan)
+    if rank == 0:
+        line = json.dumps(out)
+        print(line, flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                f.write(line + "\n")
+    if world > 1:
+        dist.destroy_process_group()
+
+
 ORB_SUBSAMPLE = 20
 # FP64 flops k_orb_nodes executes per node (DADD + DMUL + 2 DFMA from an ncu op
 # count of one launch, divided by the nodes): the three library sincos and the
@@ -893,14 +1013,17 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["fp64", "fp32", "df64", "tf32x3"], default="fp64")
-    ap.add_argument("--workload", choices=["lfi", "highres", "detectors", "multisky", "orbital"], default="lfi",
+    ap.add_argument("--workload", choices=["lfi", "highres", "detectors", "multisky", "orbital", "psigrid"],
+                    default="lfi",
                     help="lfi: T/E/B, lmax 1024, kmax 16, scan (the headline); "
                          "highres: lmax 2048, kmax 32, 2048 x 4096 rings, uniform pointings (precision variant); "
                          "detectors: 22 detectors of uneven lmax/kmax in one CUDA graph (batch variant); "
                          "multisky: cubes of many skies with one beam (tensor cores); "
-                         "orbital: orbital dipole through the 4pi beam")
+                         "orbital: orbital dipole through the 4pi beam; "
+                         "psigrid: step 2 through a psi-grid cube, against the exact phase sum")
     ap.add_argument("--ndet", type=int, default=22, help="detectors of the batch workload")
     ap.add_argument("--nsky", type=int, default=32, help="skies of the multi-sky workload")
+    ap.add_argument("--npsi", type=int, default=0, help="psi grid of the psigrid workload (0: 2 kmax + 2)")
     ap.add_argument("--tile-cols", type=int, default=0, help="sort-tile width (8, 16, 32; 0: the plan's default)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--n", type=float, default=0, help="pointings per GPU (default 1e8; 2e8 for highres)")
@@ -931,6 +1054,8 @@ def main(argv=None):
         reference_arm(args)
     elif args.workload == "orbital":
         orbital_arm(args)
+    elif args.workload == "psigrid":
+        psigrid_arm(args)
     elif args.workload == "detectors":
         detectors_arm(args)
     elif args.workload == "multisky":

@@ -195,6 +195,28 @@ sl_status interp_tod_noalloc(sl_plan *plan, const void *maps, const double *thet
                              const double *psi, int64_t n, double *tod);
 
 /* ---------------------------------------------------------------------------
+ * psi-grid variant of step 2 (Sect. 2.1: the Fourier transform over the beam
+ * order that turns c(theta, phi, k) into c(theta, phi, psi), Eq. c_m).
+ *
+ * synth_psi_cube: from the cube maps (DEVICE, [nrings][nphi][kmax+1] complex,
+ *   the plan's precision) to the real cube (DEVICE, [nrings][nphi][npsi]; double
+ *   for FP64 and DF64 plans, float for FP32 and TF32X3 plans)
+ *     c(r, j, n) = Re F_0 + 2 sum_{k=1}^{kmax} Re(e^{ik psi_n} F_k(r, j)),
+ *     psi_n = 2 pi n / npsi.
+ * interp_tod_psi: the TOD (DEVICE, n doubles) at the pointings from that cube:
+ *   p-point Lagrange in theta and phi as interp_tod, times p-point Lagrange on
+ *   the periodic psi grid (p = the plan's interp_order); ghost rows past a pole
+ *   read the ring at phi + pi and psi + pi.  Sums in the plan's precision.
+ * npsi: even, >= 2 kmax + 2, >= p, <= 8192.  At grid angles psi = psi_n the
+ * result is the exact phase sum of interp_tod; between them it carries the psi
+ * interpolation error (smaller as npsi grows).  Errors: SL_ERR_ARG (NULL
+ * buffers, npsi out of range), SL_ERR_UNSUPPORTED (nrings nphi npsi >= 2^31).
+ * Like interp_tod, interp_tod_psi uses the plan's sort scratch. */
+sl_status synth_psi_cube(sl_plan *plan, const void *maps, int npsi, void *cube_psi);
+sl_status interp_tod_psi(sl_plan *plan, const void *cube_psi, int npsi, const double *theta, const double *phi,
+                         const double *psi, int64_t n, double *tod);
+
+/* ---------------------------------------------------------------------------
  * Orbital dipole and quadrupole through the full 4pi beam (Sect. 4, Eqs.
  * dipole_simple, dipole and dipole_fast).  The satellite velocity beta = v/c
  * (one 3-vector per pointing period, in the frame of the pointings) gives the

@@ -22,7 +22,8 @@ EXPORTS = ["sidelobe_plan_create", "synth_spin_maps", "interp_tod", "adjoint_tod
            "adjoint_synth", "interp_tod_noalloc", "plan_destroy", "sl_plan_get_sizes", "sl_plan_set_stream", "sl_plan_sync",
            "sl_plan_enable_timing", "sl_plan_kernel_stats", "sl_plan_reserve", "sl_plan_set_tile_cols",
            "sl_batch_create", "sl_batch_run", "sl_batch_get_info", "sl_batch_destroy", "synth_spin_maps_multi",
-           "sl_plan_selftest_timeout", "sl_orbital_moments", "orbital_dipole_tod", "sl_last_error"]
+           "sl_plan_selftest_timeout", "sl_orbital_moments", "orbital_dipole_tod", "synth_psi_cube", "interp_tod_psi",
+           "sl_last_error"]
 SL_BATCH_AUTOTUNE = 1
 
 
@@ -96,6 +97,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         "sl_batch_get_info": (I, [P, ctypes.POINTER(BatchInfo)]),
         "sl_batch_destroy": (None, [P]),
         "sl_orbital_moments": (I, [P, P, P]),
+        "synth_psi_cube": (I, [P, P, I, P]),
+        "interp_tod_psi": (I, [P, P, I, P, P, P, I64, P]),
         "orbital_dipole_tod": (I, [P, P, ctypes.c_double, ctypes.c_double, P, P, P, I64, P, P, I64, I, P, I]),
         "sl_last_error": (ctypes.c_char_p, []),
     }

@@ -181,6 +181,38 @@ def interp_tod(plan: Plan, maps, theta, phi, psi, tod=None):
     return tod
 
 
+def synth_psi_cube(plan: Plan, maps, npsi: int, cube_psi=None):
+    """psi-grid cube c(theta_r, phi_j, psi_n), psi_n = 2 pi n / npsi, from the spin
+    cube (Sect. 2.1, step 2): float64 [R, nphi, npsi] for FP64/DF64 plans, float32
+    for FP32 plans."""
+    _dev_tensor(maps, plan.maps_dtype, plan.device, "maps", plan.maps_shape())
+    rdt = torch.float64 if plan.maps_dtype == torch.complex128 else torch.float32
+    shape = (plan.nrings, plan.nphi, int(npsi))
+    if cube_psi is None:
+        cube_psi = torch.empty(shape, dtype=rdt, device=maps.device)
+    _dev_tensor(cube_psi, rdt, plan.device, "cube_psi", shape)
+    plan._sync_stream()
+    check(_lib.load().synth_psi_cube(plan.ptr, _ptr(maps), int(npsi), _ptr(cube_psi)))
+    return cube_psi
+
+
+def interp_tod_psi(plan: Plan, cube_psi, theta, phi, psi, tod=None):
+    """TOD from the psi-grid cube: Lagrange in theta, phi and psi (plan's order)."""
+    if cube_psi.dim() != 3:
+        raise ValueError("cube_psi must be [nrings, nphi, npsi]")
+    npsi = cube_psi.shape[2]
+    rdt = torch.float64 if plan.maps_dtype == torch.complex128 else torch.float32
+    _dev_tensor(cube_psi, rdt, plan.device, "cube_psi", (plan.nrings, plan.nphi, npsi))
+    n = _ptg(plan, theta, phi, psi)
+    if tod is None:
+        tod = torch.empty(n, dtype=torch.float64, device=theta.device)
+    _dev_tensor(tod, torch.float64, plan.device, "tod", (n,))
+    plan._sync_stream()
+    check(_lib.load().interp_tod_psi(plan.ptr, _ptr(cube_psi), int(npsi), _ptr(theta), _ptr(phi), _ptr(psi), n,
+                                     _ptr(tod)))
+    return tod
+
+
 def quad_factor(nu_hz: float, T0: float) -> float:
     """The quadrupole factor of the orbital dipole: (a/2)(e^a + 1)/(e^a - 1) with
     a = h nu / (k_B T0) (h, k_B exact SI values)."""

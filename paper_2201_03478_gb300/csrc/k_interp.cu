@@ -26,49 +26,6 @@ namespace sl {
 
 constexpr int kChunkA = kWorkChunk;
 
-// p-point weights of a sample: theta rows from the record and the plan's row
-// table, phi nodes -p/2+1 .. p/2.
-template <int P>
-__device__ __forceinline__ void weights64(const InterpGeom &g, int i, double d0, double f, double wt[P],
-                                          double wp[P]) {
-    double o[P], wd[P];
-#pragma unroll
-    for (int a = 0; a < P; ++a) {
-        o[a] = __ldg(g.offs64 + (size_t)(i + 1) * P + a);
-        wd[a] = __ldg(g.wden + (size_t)(i + 1) * P + a);
-    }
-    lagrange_theta<P>(d0, o, wd, wt);
-    lagrange_phi<P>(f, wp);
-}
-
-// Element offsets of the stencil's rows (ring * nphi * K1) and columns (col * K1)
-// -- a node is row + column -- and the mask of ghost rows (beyond a pole: the
-// ring at phi + pi).
-template <int P>
-__device__ __forceinline__ unsigned stencil_offsets(const InterpGeom &g, int i, int j, int roff[P], int coff[P],
-                                                    int coff_g[P]) {
-    const int K1 = g.K + 1;
-    unsigned ghost = 0;
-#pragma unroll
-    for (int a = 0; a < P; ++a) {
-        const int row = i - P / 2 + 1 + a;
-        int ring = row;
-        if (row < 0) { ring = -1 - row; ghost |= 1u << a; }
-        else if (row >= g.R) { ring = 2 * g.R - 1 - row; ghost |= 1u << a; }
-        roff[a] = ring * g.nphi * K1;
-    }
-#pragma unroll
-    for (int b = 0; b < P; ++b) {
-        int col = j - P / 2 + 1 + b;
-        col = (col < 0) ? col + g.nphi : (col >= g.nphi ? col - g.nphi : col);
-        coff[b] = col * K1;
-        int cg = col + g.nphi / 2;
-        cg = (cg >= g.nphi) ? cg - g.nphi : cg;
-        coff_g[b] = cg * K1;
-    }
-    return ghost;
-}
-
 // ------------------------------------------------------------------ forward FP64
 // One thread per sample: combined weights w_a w_b per node, read through L1.
 template <int P>

@@ -287,6 +287,7 @@ void plan_destroy(sl_plan *p) {
     dfree(p->d_Gm);
     dfree(p->d_err);
     dfree(p->d_orb);
+    dfree(p->d_psitab);
     if (p->h_orb) cudaFreeHost(p->h_orb);
     if (p->orb_ev) cudaEventDestroy(p->orb_ev);
     dfree(p->d_rowtab_df);
@@ -831,6 +832,76 @@ sl_status orbital_dipole_tod(sl_plan *p, const double *beam, double T0, double q
     o.tod = tod;
     o.accumulate = accumulate != 0;
     return launch_orbital(p, o);
+}
+
+// ------------------------------------------------------------------ psi-grid variant
+static sl_status check_npsi(const sl_plan *p, int npsi, const char *who) {
+    if (npsi < 2 * p->K + 2 || npsi < p->p || (npsi & 1) || npsi > 8192)
+        return set_error(SL_ERR_ARG, "%s: npsi=%d must be even, >= 2 kmax + 2 = %d, >= the interpolation order "
+                                     "and <= 8192", who, npsi, 2 * p->K + 2);
+    if ((int64_t)p->R * p->nphi * npsi >= ((int64_t)1 << 31))
+        return set_error(SL_ERR_UNSUPPORTED, "%s: nrings * nphi * npsi >= 2^31", who);
+    if (psi_cube_smem_bytes(p, npsi) > (size_t)kSmemOptin)
+        return set_error(SL_ERR_UNSUPPORTED, "%s: npsi=%d too large for the phase table in shared memory", who, npsi);
+    return SL_OK;
+}
+
+sl_status synth_psi_cube(sl_plan *p, const void *maps, int npsi, void *cube_psi) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if (!maps || !cube_psi) return set_error(SL_ERR_ARG, "synth_psi_cube: NULL buffer");
+    if ((st = check_npsi(p, npsi, "synth_psi_cube")) != SL_OK) return st;
+    const bool wide = plan_wide(p->precision);
+    if (p->psitab_n != npsi) {
+        if (p->batch_refs > 0) return set_error(SL_ERR_ARG, "synth_psi_cube: the plan is held by a batch graph");
+        cudaStreamSynchronize(p->stream);
+        const int K1 = p->K + 1;
+        const size_t elem = wide ? sizeof(double2) : sizeof(float2);
+        if (p->d_psitab) {
+            dfree(p->d_psitab);
+            p->bytes_held -= (int64_t)K1 * p->psitab_n * (int64_t)elem;
+        }
+        p->d_psitab = nullptr;
+        p->psitab_n = 0;
+        if ((st = dalloc(p, &p->d_psitab, (size_t)K1 * npsi * elem, "psi phase table")) != SL_OK) return st;
+        // [k][n]: (w_k cos(2 pi k n / npsi), -w_k sin(2 pi k n / npsi)), w_0 = 1, w_k = 2; exact integer phase
+        std::vector<double> t64(2 * (size_t)K1 * npsi);
+        const long double two_pi = 6.283185307179586476925286766559L;
+        for (int k = 0; k < K1; ++k)
+            for (int n = 0; n < npsi; ++n) {
+                const long double a = two_pi * (long double)(((int64_t)k * n) % npsi) / (long double)npsi;
+                const long double w = k == 0 ? 1.0L : 2.0L;
+                t64[2 * ((size_t)k * npsi + n)] = (double)(w * cosl(a));
+                t64[2 * ((size_t)k * npsi + n) + 1] = (double)(-w * sinl(a));
+            }
+        if (wide) {
+            st = cuda_check(cudaMemcpy(p->d_psitab, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice),
+                            "psi table upload");
+        } else {
+            std::vector<float> t32(t64.size());
+            for (size_t i = 0; i < t64.size(); ++i) t32[i] = (float)t64[i];
+            st = cuda_check(cudaMemcpy(p->d_psitab, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice),
+                            "psi table upload");
+        }
+        if (st != SL_OK) return st;
+        p->psitab_n = npsi;
+    }
+    return launch_psi_cube(p, maps, npsi, p->d_psitab, cube_psi);
+}
+
+sl_status interp_tod_psi(sl_plan *p, const void *cube_psi, int npsi, const double *theta, const double *phi,
+                         const double *psi, int64_t n, double *tod) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if ((st = check_ptg(theta, phi, psi, n, tod, "interp_tod_psi")) != SL_OK) return st;
+    if (!cube_psi) return set_error(SL_ERR_ARG, "interp_tod_psi: cube_psi is NULL");
+    if ((st = check_npsi(p, npsi, "interp_tod_psi")) != SL_OK) return st;
+    if (n == 0) return SL_OK;
+    if ((st = ensure_sort_capacity(p, n)) != SL_OK) return st;
+    SortBufs b = p->sort;
+    b.chunk_off = nullptr;
+    if ((st = launch_sort_into(p, b, theta, phi, psi, n, 1, 1, 0)) != SL_OK) return st;
+    return launch_interp_psi(p, b, cube_psi, npsi, psi, n, tod);
 }
 
 sl_status sl_plan_enable_timing(sl_plan *p, int enable) {

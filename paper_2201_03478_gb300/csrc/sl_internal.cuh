@@ -103,6 +103,49 @@ __device__ __forceinline__ void lagrange_phi(T f, T wp[P]) {
     for (int b = 0; b < P; ++b) wp[b] = (pre[b] * suf[b + 1]) * T(uniform_inv_den<P>(b));
 }
 
+// p-point weights of a sample: theta rows from the record and the plan's row
+// table, phi nodes -p/2+1 .. p/2.
+template <int P>
+__device__ __forceinline__ void weights64(const InterpGeom &g, int i, double d0, double f, double wt[P],
+                                          double wp[P]) {
+    double o[P], wd[P];
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+        o[a] = __ldg(g.offs64 + (size_t)(i + 1) * P + a);
+        wd[a] = __ldg(g.wden + (size_t)(i + 1) * P + a);
+    }
+    lagrange_theta<P>(d0, o, wd, wt);
+    lagrange_phi<P>(f, wp);
+}
+
+// Element offsets of the stencil's rows (ring * nphi * K1) and columns (col * K1)
+// -- a node is row + column -- and the mask of ghost rows (beyond a pole: the
+// ring at phi + pi).
+template <int P>
+__device__ __forceinline__ unsigned stencil_offsets(const InterpGeom &g, int i, int j, int roff[P], int coff[P],
+                                                    int coff_g[P]) {
+    const int K1 = g.K + 1;
+    unsigned ghost = 0;
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+        const int row = i - P / 2 + 1 + a;
+        int ring = row;
+        if (row < 0) { ring = -1 - row; ghost |= 1u << a; }
+        else if (row >= g.R) { ring = 2 * g.R - 1 - row; ghost |= 1u << a; }
+        roff[a] = ring * g.nphi * K1;
+    }
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+        int col = j - P / 2 + 1 + b;
+        col = (col < 0) ? col + g.nphi : (col >= g.nphi ? col - g.nphi : col);
+        coff[b] = col * K1;
+        int cg = col + g.nphi / 2;
+        cg = (cg >= g.nphi) ? cg - g.nphi : cg;
+        coff_g[b] = cg * K1;
+    }
+    return ghost;
+}
+
 // Work item v -> its tile: the last t with chunk_off[t] <= v.
 __device__ __forceinline__ int find_tile(const unsigned *chunk_off, int ntiles, unsigned v) {
     int lo = 0, hi = ntiles - 1;
@@ -221,6 +264,9 @@ struct sl_plan {
     // orbital dipole (grown on demand): moments, period tables, spline nodes
     double *d_orb = nullptr;
     size_t orb_bytes = 0;
+    // psi-grid variant: phase table [K+1][npsi] of the current npsi
+    void *d_psitab = nullptr;
+    int psitab_n = 0;
     void *h_orb = nullptr;              // pinned staging of the period tables
     size_t h_orb_bytes = 0;
     cudaEvent_t orb_ev = nullptr;       // recorded after the last table upload
@@ -259,6 +305,11 @@ struct OrbLaunch {
     int accumulate;
 };
 sl_status launch_orb_moments(sl_plan *p, const double *beam, double *S);
+// psi-grid variant (k_psigrid.cu)
+size_t psi_cube_smem_bytes(const sl_plan *p, int npsi);
+sl_status launch_psi_cube(sl_plan *p, const void *maps, int npsi, const void *tab, void *out);
+sl_status launch_interp_psi(sl_plan *p, const SortBufs &b, const void *cube, int npsi, const double *psi, int64_t n,
+                            double *tod);
 sl_status launch_orbital(sl_plan *p, const OrbLaunch &o);
 
 // launchers (one per translation unit)
