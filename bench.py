@@ -580,12 +580,12 @@ def multisky_arm(args):
 # ncu-measured DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
 # at full size for the current kernels (profiles/launches_lfi_*.txt).
 TRAFFIC = {
-    ("lcontract_f64", "fp64"): 694.8e6 + 534.9e6,
-    ("interp_f64", "fp64"): 14803.8e6 + 1805.8e6,
-    ("lcontract_f32", "fp32"): 394.3e6 + 254.8e6,
-    ("interp_f32", "fp32"): 7304.9e6 + 2038.2e6,
-    ("lcontract_df", "df64"): 697.1e6 + 538.1e6,
-    ("interp_df", "df64"): 22906.8e6 + 2736.0e6,
+    ("lcontract_f64", "fp64"): 674.1e6 + 516.7e6,
+    ("interp_f64", "fp64"): 14801.7e6 + 1813.7e6,
+    ("lcontract_f32", "fp32"): 370.5e6 + 231.6e6,
+    ("interp_f32", "fp32"): 7297.4e6 + 2036.5e6,
+    ("lcontract_df", "df64"): 672.8e6 + 511.4e6,
+    ("interp_df", "df64"): 22844.9e6 + 2732.1e6,
 }
 
 
