@@ -29,6 +29,9 @@
 //     waits for its MMAs with a bound and frees its tensor memory).
 #include <algorithm>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "sl_internal.cuh"
 
 namespace sl {
@@ -42,7 +45,8 @@ struct MsArgs {
     int L, K, ncomp, R, npairs, nrc;     // nrc: ring chunks of 128 pairs
     int nsky, nsg, ngroups;              // skies, skies per CTA (multiple of 4), groups
     int64_t nalm;
-    const float2 *sky;                   // [nsky][ncomp][nalm], FP32 copy
+    const float2 *sky;                   // [nsky][ncomp][salm], FP32 copy (rows padded to an even length)
+    int64_t salm;                        // sky row stride: nalm rounded up to even (16-byte rows)
     const float2 *beam;                  // [ncomp][K+1][L+1], FP32 copy
     const float *y32;                    // [npairs] 1 - cos theta
     const int *ls;                       // [K+1][L+1][2][npairs] first significant l
@@ -136,8 +140,9 @@ __device__ __forceinline__ void ms_write_two(const MsArgs &a, float2 *G, int m, 
 constexpr int kMsTmemCols = 256;
 constexpr int kMsAcol = 128;
 constexpr int kMsNB = 2;            // operand buffers (chunks in flight)
-constexpr int kMsNS = 3;            // staging slots of the sky values (work units in flight)
-constexpr int kMsSlots = 12;        // float2 per V thread and unit: 4 skies x 3 components
+constexpr int kMsNS = 3;            // staging slots of the sky values per V warp (work units in flight)
+constexpr int kMsBoxX = 68;         // floats per TMA row: 34 float2 = 32 l plus the alignment slack
+constexpr int kMsStageF = 832;      // floats per staging slot: [4 skies][<= 3 components][68], 128-byte multiple
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
@@ -153,9 +158,11 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 //              12 MMAs of the chunk, commits them to empty[b];
 // the producers wait on empty[b] before refilling buffer b.  After the last
 // chunk the W warps wait for its commit and read the accumulator.
-__global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a) {
+__global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
+                                                                  const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ unsigned char ms_raw[];
     __shared__ __align__(8) uint64_t full_a[kMsNB], full_b[kMsNB], empty[kMsNB];
+    __shared__ __align__(8) uint64_t stg_bar[4][kMsNS];    // TMA arrivals of each V warp's staging slots
     __shared__ uint32_t tmem_base;
     __shared__ int s_lmin, s_fail;
     volatile int *fail = &s_fail;   // set by any role whose bounded wait ran out
@@ -215,6 +222,9 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
+        for (int q = 0; q < 4 * kMsNS; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&stg_bar[q / kMsNS][q % kMsNS]))
+                         : "memory");
         for (int q = 0; q < kMsNB; ++q) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&full_a[q])), "r"(kMsRows) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&full_b[q])), "r"(kMsRows) : "memory");
@@ -282,32 +292,34 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a)
         }
     } else if (warp < 8) {
         // ---------------------------------------------------------------- V producers
-        // Work unit u = (chunk c, pass j): skies s = vw + 4t + 16j (t < 4) at l = c0 + lane.
-        // Their T/E/B values travel by cp.async into a 3-deep staging ring, two units
-        // ahead of the one being built; each thread reads back only its own slots.
-        const int vw = warp - 4, tv = tid - 128;
+        // Work unit u = (chunk c, pass j): the 4 consecutive skies 4 vw + 16 j .. + 3 at
+        // l = c0 + lane.  Lane 0 brings their T/E/B rows m, l = c0 .. c0 + 31 (from an even
+        // alm index: the tensor map's rows start on 16 bytes) into this warp's staging slot
+        // u mod 3 with one TMA tensor load, two units ahead of the unit being built.
+        const int vw = warp - 4;
         const float2 *beam_k = a.beam + (int64_t)k * (a.L + 1);
         const int lmin = max(m, k);
         const int i = lane, ch = i >> 2, lo4 = i & 3;
         const int npass = (a.nsg + 15) >> 4, nunits = nchunks * npass;
-        float2 *stage = reinterpret_cast<float2 *>(base + 2 * kMsNB * bfl);
-        auto issue = [&](int u) {   // copies of unit u (every slot written: zero-filled where unused)
-            if (u < nunits) {
-                const int c = u / npass, j = u - c * npass, l = lstart + c * kMsLC + i;
-                const bool live = l <= a.L && l >= lmin;
-                float2 *dst = stage + (int64_t)(u % kMsNS) * kMsSlots * 128 + tv;
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int s = vw + 4 * t + 16 * j, sky = s_first + s;
-#pragma unroll
-                    for (int X = 0; X < 3; ++X) {
-                        const bool ok = live && s < a.nsg && sky < a.nsky && X < a.ncomp;
-                        const float2 *src = ok ? a.sky + ((int64_t)sky * a.ncomp + X) * a.nalm + moff + l : a.sky;
-                        cp_async8(dst + (t * 3 + X) * 128, src, ok);
-                    }
-                }
-            }
-            cp_async_commit();
+        // this warp's passes j < na hold skies (4 vw + 16 j < nsg); its staged units are
+        // numbered ui = c na + j, slot ui mod 3, and issued two units ahead
+        const int na = min(npass, max(0, (a.nsg - 4 * vw + 15) >> 4)), nact = nchunks * na;
+        float *stage = base + 2 * kMsNB * bfl + vw * kMsNS * kMsStageF;
+        const uint32_t tx_bytes = (uint32_t)(kMsBoxX * a.ncomp * 4 * sizeof(float));
+        auto issue = [&](int ui) {
+            if (lane != 0 || ui >= nact) return;
+            const int c = ui / na, j = ui - c * na, s0 = 4 * vw + 16 * j;
+            const int64_t x0 = moff + lstart + (int64_t)c * kMsLC;    // alm index of l = c0
+            const int xf = (int)((x0 & ~(int64_t)1) * 2);              // in floats, a multiple of 4
+            const uint32_t bar = smem_u32(&stg_bar[vw][ui % kMsNS]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(tx_bytes)
+                         : "memory");
+            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                         "[%0], [%1, {%2, %3, %4}], [%5];"
+                         :: "r"(smem_u32(stage + (ui % kMsNS) * kMsStageF)), "l"(&tmap), "r"(xf), "r"(0),
+                            "r"(s_first + s0), "r"(bar)
+                         : "memory");
         };
         issue(0);
         issue(1);
@@ -331,10 +343,9 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a)
         beam_of(0);
         float2 bv[3];
         float cl = 0.f, sc = 0.f;
+        int ui_done = 0;                  // staged units consumed
         for (int u = 0; u < nunits; ++u) {
-            const int c = u / npass, j = u - c * npass, bi = c % kMsNB;
-            issue(u + 2);
-            cp_async_wait<2>();
+            const int c = u / npass, j = u - c * npass, bi = c % kMsNB, s0 = 4 * vw + 16 * j;
             if (j == 0) {
                 const int l = lstart + c * kMsLC + i;
 #pragma unroll
@@ -345,40 +356,54 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a)
                 if (c >= kMsNB && !mbar_wait(smem_u32(&empty[bi]), ((c - kMsNB) / kMsNB) & 1)) *fail = 1;
             }
             if (*fail) break;
-            float *Bh = base + bi * 2 * bfl, *Bl = Bh + bfl;
-            const float2 *src = stage + (int64_t)(u % kMsNS) * kMsSlots * 128 + tv;
+            if (j < na) {
+                const int ui = c * na + j;
+                __syncwarp();             // slot (ui + 2) mod 3 was last read in unit ui - 1
+                issue(ui + 2);
+                if (!mbar_wait(smem_u32(&stg_bar[vw][ui % kMsNS]), (ui / kMsNS) & 1)) *fail = 1;
+                if (*fail) break;
+                float *Bh = base + bi * 2 * bfl, *Bl = Bh + bfl;
+                // this lane's l sits at float2 (x0 & 1) + lane of each staged row
+                const int64_t x0 = moff + lstart + (int64_t)c * kMsLC;
+                const float *src = stage + (ui % kMsNS) * kMsStageF + 2 * ((int)(x0 & 1) + i);
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int s = vw + 4 * t + 16 * j;
-                if (s >= a.nsg) break;
-                float2 ap = {0.f, 0.f}, am = {0.f, 0.f};
+                for (int t = 0; t < 4; ++t) {
+                    const int s = s0 + t;
+                    float2 ap = {0.f, 0.f}, am = {0.f, 0.f};
 #pragma unroll
-                for (int X = 0; X < 3; ++X) {
-                    float2 s2 = src[(t * 3 + X) * 128];
-                    if (m == 0) s2.y = 0.f;
-                    const float2 b2 = bv[X];
-                    ap.x += s2.x * b2.x + s2.y * b2.y;      // s conj(b)
-                    ap.y += s2.y * b2.x - s2.x * b2.y;
-                    am.x += s2.x * b2.x - s2.y * b2.y;      // conj(s) conj(b)
-                    am.y -= s2.y * b2.x + s2.x * b2.y;
+                    for (int X = 0; X < 3; ++X) {
+                        if (X >= a.ncomp) break;
+                        float2 s2 = *reinterpret_cast<const float2 *>(src + (t * a.ncomp + X) * kMsBoxX);
+                        if (m == 0) s2.y = 0.f;
+                        const float2 b2 = bv[X];
+                        ap.x += s2.x * b2.x + s2.y * b2.y;      // s conj(b)
+                        ap.y += s2.y * b2.x - s2.x * b2.y;
+                        am.x += s2.x * b2.x - s2.y * b2.y;      // conj(s) conj(b)
+                        am.y -= s2.y * b2.x + s2.x * b2.y;
+                    }
+                    const float2 p1 = neg ? am : ap, p2 = neg ? ap : am;
+                    const float vv[4] = {cl * p1.x, cl * p1.y, sc * p2.x, sc * p2.y};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int row = 4 * s + q, off = row * 32 + ((ch ^ (row & 7)) << 2) + lo4;
+                        float h, lo;
+                        tf32_split(vv[q], h, lo);
+                        Bh[off] = h;
+                        Bl[off] = lo;
+                    }
                 }
-                const float2 p1 = neg ? am : ap, p2 = neg ? ap : am;
-                const float vv[4] = {cl * p1.x, cl * p1.y, sc * p2.x, sc * p2.y};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int row = 4 * s + q, off = row * 32 + ((ch ^ (row & 7)) << 2) + lo4;
-                    float h, lo;
-                    tf32_split(vv[q], h, lo);
-                    Bh[off] = h;
-                    Bl[off] = lo;
-                }
+                ui_done = ui + 1;
             }
             if (j == npass - 1) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(smem_u32(&full_b[bi]));
             }
         }
-        cp_async_wait<0>();
+        // after a failed wait: the TMA loads still in flight land (bounded) before the
+        // CTA's shared memory is released
+        if (*fail && lane == 0)
+            for (int ui = ui_done; ui < min(ui_done + kMsNS, nact); ++ui)
+                mbar_wait(smem_u32(&stg_bar[vw][ui % kMsNS]), (ui / kMsNS) & 1, 1000000ull);
     } else if (lane == 0) {
         // ---------------------------------------------------------------- MMA issuer
         const uint32_t idesc = ms_idesc(kMsRows, N);
@@ -472,11 +497,44 @@ __global__ void k_to_f32_ms(const double2 *__restrict__ in, float2 *__restrict__
         out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
 
+// [nrows][nalm] complex128 -> [nrows][salm] complex64, the padding zeroed
+__global__ void k_to_f32_rows(const double2 *__restrict__ in, float2 *__restrict__ out, int64_t nrows, int64_t nalm,
+                              int64_t salm) {
+    const int64_t n = nrows * salm;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / salm, c = i - r * salm;
+        const double2 v = c < nalm ? in[r * nalm + c] : make_double2(0.0, 0.0);
+        out[i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// The 3-D tensor map over the FP32 skies: x = floats of a row (2 salm), y = component,
+// z = sky; boxes of 68 floats x ncomp x 4 skies, zero fill outside.
+static sl_status sky_tensor_map(CUtensorMap *tm, const float2 *sky32, int64_t salm, int ncomp, int nsky) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return set_error(SL_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)(2 * salm), (cuuint64_t)ncomp, (cuuint64_t)nsky};
+    const cuuint64_t strides[2] = {(cuuint64_t)(2 * salm * sizeof(float)), (cuuint64_t)(2 * salm * ncomp * sizeof(float))};
+    const cuuint32_t box[3] = {(cuuint32_t)kMsBoxX, (cuuint32_t)ncomp, 4u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)sky32, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(SL_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return SL_OK;
+}
+
 size_t lcontract_mma_smem(int nsg, int ncomp) {
     (void)ncomp;
-    // B_hi, B_lo (two buffers), the sky staging ring, alignment slack
-    return 2 * kMsNB * (size_t)4 * nsg * kMsLC * sizeof(float) + (size_t)kMsNS * kMsSlots * 128 * sizeof(float2) +
-           1024;
+    // B_hi, B_lo (two buffers), the four V warps' staging slots, alignment slack
+    return 2 * kMsNB * (size_t)4 * nsg * kMsLC * sizeof(float) + (size_t)4 * kMsNS * kMsStageF * sizeof(float) + 1024;
 }
 
 int lcontract_mma_group(int nsky) {
@@ -486,9 +544,10 @@ int lcontract_mma_group(int nsky) {
 
 sl_status launch_lcontract_mma(sl_plan *p, int nsky, const double *sky, const double *beam, float2 *sky32,
                                float2 *G, int *err) {
-    const int64_t ns = (int64_t)nsky * p->ncomp * p->nalm, nb = (int64_t)p->ncomp * (p->K + 1) * (p->L + 1);
-    k_to_f32_ms<<<(unsigned)std::min<int64_t>((ns + 255) / 256, 8192), 256, 0, p->stream>>>((const double2 *)sky,
-                                                                                             sky32, ns);
+    const int64_t salm = sky_row_stride(p->nalm);
+    const int64_t nrows = (int64_t)nsky * p->ncomp, nb = (int64_t)p->ncomp * (p->K + 1) * (p->L + 1);
+    k_to_f32_rows<<<(unsigned)std::min<int64_t>((nrows * salm + 255) / 256, 8192), 256, 0, p->stream>>>(
+        (const double2 *)sky, sky32, nrows, p->nalm, salm);
     k_to_f32_ms<<<(unsigned)std::min<int64_t>((nb + 255) / 256, 4096), 256, 0, p->stream>>>((const double2 *)beam,
                                                                                              p->d_beam32, nb);
     MsArgs a;
@@ -503,6 +562,10 @@ sl_status launch_lcontract_mma(sl_plan *p, int nsky, const double *sky, const do
     a.ngroups = (nsky + a.nsg - 1) / a.nsg;
     a.nalm = p->nalm;
     a.sky = sky32;
+    a.salm = salm;
+    CUtensorMap tmap;
+    sl_status st = sky_tensor_map(&tmap, sky32, salm, p->ncomp, nsky);
+    if (st != SL_OK) return st;
     a.beam = p->d_beam32;
     a.y32 = p->d_y32;
     a.ls = p->d_ls;
@@ -517,7 +580,7 @@ sl_status launch_lcontract_mma(sl_plan *p, int nsky, const double *sky, const do
     cudaError_t e = cudaFuncSetAttribute(k_lcontract_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return cuda_check(e, "k_lcontract_mma smem attribute");
     const int slot = timing_begin(p, "lcontract_mma");
-    k_lcontract_mma<<<(unsigned)nblk, kMsThreads, sm, p->stream>>>(a);
+    k_lcontract_mma<<<(unsigned)nblk, kMsThreads, sm, p->stream>>>(a, tmap);
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_lcontract_mma launch");
 }

@@ -94,7 +94,7 @@ struct OrbArgs {
     const double *beta;       // [nper][3]
     const double *S;          // [9]
     const double *piv;        // [kOrbPivots] c_j (c_0 = 0); c_j = piv[kOrbPivots - 1] beyond
-    const double4 *w;         // [s] spline weights (w0, w1, w2, w3) of r = 0 .. s - 1
+    const double4_32a *w;     // [s + 1] spline weights (w0, w1, w2, w3) of r = 0 .. s
     double T0, q;
     int64_t n, nper, nnodes;
     int s;
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(256) k_orb_eval(const OrbArgs a) {
                 val = a.y[g0];
             } else {
                 const unsigned j = jt < M - 1 ? jt : M - 2;
-                const double4 w = a.w[t - j * su];             // r = t - j s (s at the last node)
+                const double4_32a w = a.w[t - j * su];             // r = t - j s (s at the last node)
                 const double *yy = a.y + g0 + j, *mm = a.M2 + g0 + j;
                 val = w.x * yy[0] + w.y * yy[1] + w.z * mm[0] + w.w * mm[1];
             }
@@ -265,7 +265,7 @@ sl_status launch_orbital(sl_plan *p, const OrbLaunch &o) {
     a.beta = o.beta;
     a.S = o.S;
     a.piv = o.piv;
-    a.w = reinterpret_cast<const double4 *>(o.w);
+    a.w = reinterpret_cast<const double4_32a *>(o.w);
     a.T0 = o.T0;
     a.q = o.q;
     a.n = o.n;

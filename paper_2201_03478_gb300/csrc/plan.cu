@@ -478,7 +478,7 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     TRY(dalloc_t(p, &p->d_tab64, (size_t)(K + 1) * p->nalm, "recurrence table"));
     if (plan_fp32(p->precision)) {
         TRY(dalloc_t(p, &p->d_tab32, (size_t)(K + 1) * p->nalm, "recurrence table"));
-        TRY(dalloc_t(p, &p->d_sky32, (size_t)p->ncomp * p->nalm, "FP32 sky"));
+        TRY(dalloc_t(p, &p->d_sky32, (size_t)p->ncomp * sky_row_stride(p->nalm), "FP32 sky"));
         TRY(dalloc_t(p, &p->d_beam32, (size_t)p->ncomp * (K + 1) * (L + 1), "FP32 beam"));
     }
     TRY(launch_rtab(p));
@@ -688,13 +688,14 @@ sl_status synth_spin_maps_multi(sl_plan *p, int nsky, const double *sky, const d
         cudaStreamSynchronize(p->stream);
         const int64_t gsky = (int64_t)(p->K + 1) * p->R * (2 * p->L + 1);
         if (p->msky_cap > 0)
-            p->bytes_held -= (int64_t)p->msky_cap * (int64_t)sizeof(float2) * (p->ncomp * p->nalm + gsky);
+            p->bytes_held -= (int64_t)p->msky_cap * (int64_t)sizeof(float2) * (p->ncomp * sky_row_stride(p->nalm) + gsky);
         dfree(p->d_skym32);
         dfree(p->d_Gm);
         p->d_skym32 = nullptr;
         p->d_Gm = nullptr;
         p->msky_cap = 0;
-        if ((st = dalloc_t(p, &p->d_skym32, (size_t)nsky * p->ncomp * p->nalm, "FP32 skies")) != SL_OK) return st;
+        if ((st = dalloc_t(p, &p->d_skym32, (size_t)nsky * p->ncomp * sky_row_stride(p->nalm), "FP32 skies")) != SL_OK)
+            return st;
         if ((st = dalloc_t(p, &p->d_Gm, (size_t)nsky * gsky, "multi-sky G")) != SL_OK) return st;
         p->msky_cap = nsky;
     }

@@ -291,6 +291,10 @@ sl_status cuda_check(cudaError_t e, const char *what);
 int timing_begin(sl_plan *p, const char *name);
 void timing_end(sl_plan *p, int idx);
 
+// row stride (complex elements) of the FP32 sky copies: nalm rounded up to even, so that
+// every row starts on 16 bytes (the tensor-core contraction loads them with TMA)
+inline int64_t sky_row_stride(int64_t nalm) { return (nalm + 1) & ~(int64_t)1; }
+
 // orbital dipole (k_orbital.cu): device pointers of one call
 struct OrbLaunch {
     const double *theta, *phi, *psi;
