@@ -94,13 +94,15 @@ typedef enum {
 
 typedef struct {
     int lmax;                  /* sky and beam band limit L >= 1 */
-    int kmax;                  /* beam azimuthal band limit K, 0 <= K <= min(L, 63) */
+    int kmax;                  /* beam azimuthal band limit K, 0 <= K <= min(L, 128) */
     int ncomp;                 /* 1 (T) or 3 (T, E, B) */
     int nrings;                /* R in [4, 65534] */
     const double *ring_theta;  /* HOST [nrings]: strictly ascending colatitudes in (0, pi),
                                   symmetric: theta[R-1-r] == pi - theta[r] (to 1e-12);
                                   copied at plan creation */
-    int nphi;                  /* Phi: even, >= 8, of the form 2^a 3^b 5^c, <= 7200 */
+    int nphi;                  /* Phi: even, >= 8, of the form 2^a 3^b 5^c, <= 16384; rings longer
+                                  than one CTA's shared memory run on a cluster of 2-8 CTAs;
+                                  nrings * nphi * (kmax + 1) < 2^31 */
     int interp_order;          /* p: 2, 4 or 6 points per axis (0 selects 4) */
     int precision;             /* sl_precision */
     int device;                /* CUDA device ordinal */

@@ -220,7 +220,8 @@ struct AdjArgs {
     double2 *fbar;
 };
 
-constexpr int kNB = 64;   // samples staged per batch
+constexpr int kNB = 64;   // samples staged per batch (32 when kmax + 1 > 64, to fit shared memory)
+__host__ __device__ __forceinline__ int kNB_of(int K1) { return K1 > 64 ? kNB / 2 : kNB; }
 
 template <int P>
 __global__ void k_interp_adjoint(const AdjArgs A) {
@@ -234,8 +235,8 @@ __global__ void k_interp_adjoint(const AdjArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *acc = reinterpret_cast<double2 *>(smem_raw);            // [nnode][K1]
     double2 *PH = acc + (size_t)nnode * K1;                           // [kNB][K1]
-    double *W = reinterpret_cast<double *>(PH + (size_t)kNB * K1);    // [kNB][NQ]
-    int *LOC = reinterpret_cast<int *>(W + (size_t)kNB * NQ);         // [kNB] node index of the first stencil node
+    double *W = reinterpret_cast<double *>(PH + (size_t)kNB_of(K1) * K1);    // [kNB][NQ]
+    int *LOC = reinterpret_cast<int *>(W + (size_t)kNB_of(K1) * NQ);         // [kNB] node index of the first stencil node
 
     const unsigned nchunks = A.chunk_off[A.ntiles];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -258,8 +259,8 @@ __global__ void k_interp_adjoint(const AdjArgs A) {
         const int rowlo = tr * kTileRows - P / 2;   // stencil rows i-P/2+1 .., base row i >= tr*4-1
         const int collo = tcol * TC - P / 2 + 1;
         __syncthreads();
-        for (unsigned b0 = s_beg; b0 < s_end; b0 += kNB) {
-            const int nb = (int)min((unsigned)kNB, s_end - b0);
+        for (unsigned b0 = s_beg; b0 < s_end; b0 += (unsigned)kNB_of(K1)) {
+            const int nb = (int)min((unsigned)kNB_of(K1), s_end - b0);
             // phase A: per-sample weights, node location and phases
             if ((int)threadIdx.x < nb) {
                 const unsigned s = A.perm[b0 + threadIdx.x];
@@ -421,8 +422,8 @@ sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *map
 size_t interp_adjoint_smem_tc(const sl_plan *p, int tc) {
     const int K1 = p->K + 1, P = p->p;
     const int nnode = (kTileRows + P - 1) * (tc + P - 1);
-    return (size_t)nnode * K1 * sizeof(double2) + (size_t)kNB * K1 * sizeof(double2) +
-           (size_t)kNB * P * P * sizeof(double) + (size_t)kNB * sizeof(int);
+    return (size_t)nnode * K1 * sizeof(double2) + (size_t)kNB_of(K1) * K1 * sizeof(double2) +
+           (size_t)kNB_of(K1) * P * P * sizeof(double) + (size_t)kNB_of(K1) * sizeof(int);
 }
 
 sl_status launch_interp_adjoint(sl_plan *p, const SortBufs &b, int fine, const double *psi, const double *tod,

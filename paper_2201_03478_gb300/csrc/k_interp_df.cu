@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(256) k_interp_df_tiled(const DfArgs A) {
 // scatter with the weights, the phases and the shared-memory accumulation in
 // double-float (each accumulator an unnormalised high/low pair); the tile is
 // flushed to the double adjoint cube with atomic additions.
-constexpr int kNBD = 64;   // samples staged per batch
+constexpr int kNBD = 64;   // samples staged per batch (32 when kmax + 1 > 64, to fit shared memory)
+__host__ __device__ __forceinline__ int kNBD_of(int K1) { return K1 > 64 ? kNBD / 2 : kNBD; }
 
 template <int P>
 __global__ void k_interp_adjoint_df(const DfArgs A) {
@@ -179,8 +180,8 @@ __global__ void k_interp_adjoint_df(const DfArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *acc = reinterpret_cast<float4 *>(smem_raw);               // [nnode][K1] (Re h, Re l, Im h, Im l)
     float4 *PH = acc + (size_t)nnode * K1;                            // [kNBD][K1]
-    float2 *W = reinterpret_cast<float2 *>(PH + (size_t)kNBD * K1);   // [kNBD][NQ]
-    int *LOC = reinterpret_cast<int *>(W + (size_t)kNBD * NQ);        // [kNBD]
+    float2 *W = reinterpret_cast<float2 *>(PH + (size_t)kNBD_of(K1) * K1);   // [kNBD][NQ]
+    int *LOC = reinterpret_cast<int *>(W + (size_t)kNBD_of(K1) * NQ);        // [kNBD]
 
     const unsigned nchunks = A.chunk_off[A.ntiles];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -195,8 +196,8 @@ __global__ void k_interp_adjoint_df(const DfArgs A) {
         const int tr = tile / g.ntc, tcol = tile % g.ntc;
         const int rowlo = tr * kTileRows - P / 2, collo = tcol * TC - P / 2 + 1;
         __syncthreads();
-        for (unsigned b0 = s_beg; b0 < s_end; b0 += kNBD) {
-            const int nb = (int)min((unsigned)kNBD, s_end - b0);
+        for (unsigned b0 = s_beg; b0 < s_end; b0 += (unsigned)kNBD_of(K1)) {
+            const int nb = (int)min((unsigned)kNBD_of(K1), s_end - b0);
             // phase A: per-sample weights, node location and phases eps_k y e^{-ik psi}
             if ((int)threadIdx.x < nb) {
                 const unsigned s = A.perm[b0 + threadIdx.x];
@@ -309,8 +310,8 @@ __global__ void k_interp_adjoint_df(const DfArgs A) {
 size_t interp_adjoint_df_smem_tc(const sl_plan *p, int tc) {
     const int K1 = p->K + 1, P = p->p;
     const int nnode = (kTileRows + P - 1) * (tc + P - 1);
-    return (size_t)nnode * K1 * sizeof(float4) + (size_t)kNBD * K1 * sizeof(float4) +
-           (size_t)kNBD * P * P * sizeof(float2) + (size_t)kNBD * sizeof(int);
+    return (size_t)nnode * K1 * sizeof(float4) + (size_t)kNBD_of(K1) * K1 * sizeof(float4) +
+           (size_t)kNBD_of(K1) * P * P * sizeof(float2) + (size_t)kNBD_of(K1) * sizeof(int);
 }
 
 sl_status launch_interp_adjoint_df(sl_plan *p, const SortBufs &b, int fine, const double *psi, const double *tod,

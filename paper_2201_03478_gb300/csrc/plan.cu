@@ -230,6 +230,8 @@ static sl_status validate(const sl_plan_desc *d, int *rad, int *nrad) {
         return set_error(SL_ERR_ARG, "nphi=%d must be even and in [8, %d]", d->nphi, kMaxNphi);
     if (!factor_235(d->nphi, rad, nrad))
         return set_error(SL_ERR_UNSUPPORTED, "nphi=%d has a prime factor > 5", d->nphi);
+    if ((int64_t)d->nrings * d->nphi * (d->kmax + 1) >= ((int64_t)1 << 31))
+        return set_error(SL_ERR_UNSUPPORTED, "nrings * nphi * (kmax + 1) >= 2^31 (cube element offsets are 32-bit)");
     if (d->precision != SL_FP64 && d->precision != SL_FP32 && d->precision != SL_DF64 && d->precision != SL_TF32X3)
         return set_error(SL_ERR_ARG, "precision=%d unknown", d->precision);
     int ndev = 0;
@@ -404,8 +406,9 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     p->geom.lut_scale = nlut / M_PI;
     p->geom.lut_scale_f = (float)(nlut / M_PI);
     p->geom.phi_scale = p->nphi / (2.0 * M_PI);
-    p->geom.phi_fix = (unsigned long long)llroundl(
-        ldexpl((long double)p->nphi / (2.0L * 3.14159265358979323846264338327950288L), 52));
+    // round(nphi / (2 pi) 2^52) < 2^64 for nphi <= 16384 (the rounding stays unsigned)
+    p->geom.phi_fix = (unsigned long long)(
+        ldexpl((long double)p->nphi / (2.0L * 3.14159265358979323846264338327950288L), 52) + 0.5L);
 
     double *d_c2 = nullptr, *d_s2 = nullptr, *d_cs = nullptr;
 #define TRY(x)                      \

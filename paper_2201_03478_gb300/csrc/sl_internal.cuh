@@ -13,10 +13,13 @@
 namespace sl {
 
 // ---------------------------------------------------------------- constants
-constexpr int kMaxK = 63;        // beam azimuthal band limit supported
+constexpr int kMaxK = 128;       // beam azimuthal band limit supported
 // ring FFT length held in shared memory: two double-complex buffers of nphi
 // (the FP64 synthesis and every plan's adjoint DFT) within 227 KB
-constexpr int kMaxNphi = 7200;
+// longest ring: the binning's fixed-point phi scale round(nphi / (2 pi) 2^52) fits 64 bits
+// up to here; rings longer than one CTA's shared memory use a cluster FFT
+constexpr int kMaxNphi = 16384;
+constexpr int kFftSmemMax = 232448;    // dynamic shared memory per CTA (227 KB)
 constexpr int kMaxRadices = 16;
 
 // Scaled FP64 Wigner values: value = mantissa * 2^(600 * e), e <= 0; a value
@@ -325,6 +328,8 @@ sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam);
 sl_status launch_ringfft_synth(sl_plan *p, void *maps);
 // nsky cubes from nsky consecutive G blocks (gridDim.y = nsky)
 sl_status launch_ringfft_synth_from(sl_plan *p, const void *G, int nsky, void *maps);
+// CTAs per cluster of the ring FFT (1: one CTA per ring; 0: unsupported nphi)
+int ring_fft_cluster_size(const sl_plan *p);
 // Multi-sky spin Legendre step on the tensor cores (k_multisky.cu), FP32 plans.
 sl_status launch_lcontract_mma(sl_plan *p, int nsky, const double *sky, const double *beam, float2 *sky32,
                                float2 *G, int *err);

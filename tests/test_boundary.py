@@ -54,7 +54,7 @@ def _desc(**kw):
     (dict(lmax=0), -1), (dict(kmax=17), -1), (dict(kmax=-1), -1), (dict(ncomp=2), -1),
     (dict(nphi=31), -1), (dict(nphi=4), -1), (dict(nphi=14), -2), (dict(interp_order=8), -2),
     (dict(interp_order=3), -1), (dict(interp_order=-2), -1),
-    (dict(precision=7), -1), (dict(nrings=3), -1),
+    (dict(precision=7), -1), (dict(nrings=3), -1), (dict(nphi=20000), -1), (dict(lmax=200, kmax=129), -1),
 ])
 def test_bad_descriptions_are_rejected(lib, bad, status):
     d, keep = _desc(**bad)
