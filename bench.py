@@ -710,6 +710,92 @@ def psigrid_arm(args):
         dist.destroy_process_group()
 
 
+SWEEP = [(256, 0), (256, 10), (512, 0), (512, 10), (1024, 0), (1024, 10), (2048, 0), (2048, 10), (4096, 0),
+         (4096, 10), (8192, 0), (8192, 10), (512, 100)]
+
+
+def sweep_arm(args):
+    """Cube-build runtime against lmax (the paper's Fig. speed): random sky, an
+    elliptical-Gaussian-like beam with kmax (the paper's m_max) 0 or 10, lmax 256 ... 8192
+    on lmax equiangular rings x 2 lmax phi, plus the stored sidelobe models' lmax 512 /
+    kmax 100.  Each point: plan creation, then synth_spin_maps timed on the device."""
+    import torch
+
+    import paper_2201_03478_gb300 as sl
+    import workloads as W
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(device)
+    precs = [x for x in args.sweep_precisions.split(",") if x]
+    points = []
+    for L, K in SWEEP:
+        if L > args.sweep_max:
+            continue
+        R, nphi = L, 2 * L
+        rt = W.equiangular_ring_theta(R)
+        ell = np.arange(L + 1, dtype=np.float64)
+        sky = torch.from_numpy(W.sky_gaussian(L, [(ell + 1.0) ** -2], seed=0)).to(device)
+        beam = torch.from_numpy(W.beam_elliptical(L, K)).to(device)
+        for prec in precs:
+            t0 = time.perf_counter()
+            plan = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=1, precision=prec, device=local)
+            torch.cuda.synchronize()
+            t_plan = time.perf_counter() - t0
+            maps = torch.empty(plan.maps_shape(), dtype=plan.maps_dtype, device=device)
+            steps = 3 if L <= 2048 else 1
+            sl.synth_spin_maps(plan, sky, beam, maps)
+            torch.cuda.synchronize()
+            plan.enable_timing(True)
+            plan.kernel_stats(reset=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                sl.synth_spin_maps(plan, sky, beam, maps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            stats = plan.kernel_stats(reset=True)
+            plan.enable_timing(False)
+            lsteps = float(plan.sizes()["lsteps"])
+            dense = 4.0 * R * (L + 1) ** 2 * (K + 1) + 3.0 * R * (L + 1) * (L + 2) / 2 * (K + 1)
+            lc = [v for k, v in stats.items() if k.startswith("lcontract")]
+            lc_ms = lc[0][1] / max(1, lc[0][0]) if lc else None
+            pt = {"lmax": L, "kmax": K, "nrings": R, "nphi": nphi, "precision": prec, "ms": round(ms, 3),
+                  "plan_s": round(t_plan, 2), "dense_flops": dense, "executed_flops": 11.0 * lsteps,
+                  "kernel_ms": {k: round(v[1] / steps, 3) for k, v in stats.items()}}
+            if lc_ms and prec in ("fp64", "fp32"):
+                peak = PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS
+                pt["lcontract_frac_of_peak"] = round(11.0 * lsteps / (lc_ms / 1e3) / 1e12 / peak, 4)
+            points.append(pt)
+            print("sweep lmax=%d kmax=%d %s: %.2f ms (plan %.1f s)" % (L, K, prec, ms, t_plan), file=sys.stderr,
+                  flush=True)
+            sl.plan_destroy(plan)
+            del maps
+            torch.cuda.empty_cache()
+        del sky, beam
+        torch.cuda.empty_cache()
+    head = [p for p in points if p["precision"] == precs[0]]
+    top = max(head, key=lambda p: (p["lmax"], p["kmax"])) if head else None
+    out = {"metric": "cube build time (synth_spin_maps) against lmax, kmax 0 and 10 (Fig. speed sweep)",
+           "value": top["ms"] if top else None, "unit": "ms", "n_gpus": 1, "steps": None, "warmup": 1,
+           "ms_per_step": top["ms"] if top else None, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": precs[0],
+           "data": "synthetic (seeded Gaussian sky C_l=(l+1)^-2, elliptical-Gaussian-like beam)",
+           "config": {"workload": "runtime sweep: lmax %s, kmax {0, 10} and (512, 100); lmax rings x 2 lmax phi"
+                                  % sorted({p["lmax"] for p in points}),
+                      "value_point": {"lmax": top["lmax"], "kmax": top["kmax"]} if top else None},
+           "sweep": points, "cpu_baseline": None, "gpu_launches": None}
+    line = json.dumps(out)
+    print(line, flush=True)
+    if args.json_out:
+        with open(args.json_out, "w") as f:
+            f.write(line + "\n")
+
+
 ORB_SUBSAMPLE = 20
 # FP64 flops k_orb_nodes executes per node (DADD + DMUL + 2 DFMA from an ncu op
 # count of one launch, divided by the nodes): the three library sincos and the
@@ -1013,17 +1099,20 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["fp64", "fp32", "df64", "tf32x3"], default="fp64")
-    ap.add_argument("--workload", choices=["lfi", "highres", "detectors", "multisky", "orbital", "psigrid"],
+    ap.add_argument("--workload", choices=["lfi", "highres", "detectors", "multisky", "orbital", "psigrid", "sweep"],
                     default="lfi",
                     help="lfi: T/E/B, lmax 1024, kmax 16, scan (the headline); "
                          "highres: lmax 2048, kmax 32, 2048 x 4096 rings, uniform pointings (precision variant); "
                          "detectors: 22 detectors of uneven lmax/kmax in one CUDA graph (batch variant); "
                          "multisky: cubes of many skies with one beam (tensor cores); "
                          "orbital: orbital dipole through the 4pi beam; "
-                         "psigrid: step 2 through a psi-grid cube, against the exact phase sum")
+                         "psigrid: step 2 through a psi-grid cube, against the exact phase sum; "
+                         "sweep: cube-build runtime against lmax (Fig. speed)")
     ap.add_argument("--ndet", type=int, default=22, help="detectors of the batch workload")
     ap.add_argument("--nsky", type=int, default=32, help="skies of the multi-sky workload")
     ap.add_argument("--npsi", type=int, default=0, help="psi grid of the psigrid workload (0: 2 kmax + 2)")
+    ap.add_argument("--sweep-max", type=int, default=8192, help="largest lmax of the sweep workload")
+    ap.add_argument("--sweep-precisions", default="fp64,fp32,df64", help="plans of the sweep workload")
     ap.add_argument("--tile-cols", type=int, default=0, help="sort-tile width (8, 16, 32; 0: the plan's default)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--n", type=float, default=0, help="pointings per GPU (default 1e8; 2e8 for highres)")
@@ -1056,6 +1145,8 @@ def main(argv=None):
         orbital_arm(args)
     elif args.workload == "psigrid":
         psigrid_arm(args)
+    elif args.workload == "sweep":
+        sweep_arm(args)
     elif args.workload == "detectors":
         detectors_arm(args)
     elif args.workload == "multisky":

@@ -311,3 +311,24 @@ def config_orbital(n: int = 100_000_000, with_pointings: bool = True):
     if with_pointings:
         d["theta"], d["phi"], d["psi"] = pointings_scan(n)
     return d
+
+
+def beam_elliptical(lmax: int, kmax: int, sigma_l: float = 0.0, ellipticity: float = 0.3) -> np.ndarray:
+    """Elliptical-Gaussian-like beam [1][kmax+1][lmax+1] (boresight on +z): the
+    Gaussian envelope sqrt((2l+1)/4pi) exp(-l(l+1) s^2/2) times, for even k, the
+    ratio of modified Bessel functions I_{k/2}(x)/I_0(x) with x = l(l+1) s^2 e/4
+    (odd k vanish for a beam symmetric under a half turn); s = 1.5/lmax unless
+    sigma_l is given.  A timing stand-in with the shape and k structure of an
+    elliptical beam."""
+    from scipy.special import ive
+    s = sigma_l if sigma_l > 0 else 1.5 / lmax
+    ell = np.arange(lmax + 1, dtype=np.float64)
+    ll = ell * (ell + 1.0)
+    env = np.sqrt((2 * ell + 1) / (4 * math.pi)) * np.exp(-0.5 * ll * s * s)
+    x = ll * s * s * ellipticity / 4.0
+    b = np.zeros((1, kmax + 1, lmax + 1), dtype=np.complex128)
+    i0 = ive(0, x)
+    for k in range(0, kmax + 1, 2):
+        b[0, k] = env * ive(k // 2, x) / i0
+        b[0, k, :k] = 0.0
+    return b
