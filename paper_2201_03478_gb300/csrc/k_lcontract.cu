@@ -49,6 +49,7 @@ namespace sl {
 
 constexpr int kNT = 256;          // threads per CTA
 constexpr int kHalf = kNT / 2;    // threads per sign
+constexpr int kF32Pairs = 4;      // ring pairs per thread of the FP32 contraction
 constexpr int kLC64 = 64;         // l values staged per chunk (FP64)
 
 struct __align__(16) Coef64 {
@@ -250,37 +251,37 @@ __device__ __forceinline__ void rec32_step(Rec32 &s, float ra, float rc_, float2
     s.y += s.D;
 }
 
+// PPT ring pairs per thread (consecutive pairs): each staged coefficient load
+// feeds PPT recurrence steps.
+template <int PPT>
 __global__ void __launch_bounds__(kNT) k_lcontract_f32(const LcArgs a) {
     __shared__ float4 rc[2][kNT];   // a', c'+, c'-, unused
     __shared__ Acc32 ac[2][kNT];
     int m, k, pc;
     block_mk(a, m, k, pc);
     const int neg = threadIdx.x >= kHalf;
-    const int p0 = pc * (2 * kHalf) + 2 * (threadIdx.x & (kHalf - 1));
+    const int p0 = pc * (PPT * kHalf) + PPT * (threadIdx.x & (kHalf - 1));
     const int64_t moff = (int64_t)m * (2 * a.L + 1 - m) / 2;
     const RTab32 *tab = a.tab32 + (int64_t)k * a.nalm + moff;
 
-    Rec32 A, B;
-    A.ls = B.ls = a.L + 1;
-    A.acc1 = A.acc2 = B.acc1 = B.acc2 = make_float2(0.f, 0.f);
-    A.y = A.D = B.y = B.D = A.yc = B.yc = 0.f;
-    if (p0 < a.npairs) {
-        const int64_t si = start_index(a, k, m, neg, p0);
-        A.ls = a.ls[si];
-        const float2 s = a.st32[si];
-        A.y = s.x;
-        A.D = s.y;
-        A.yc = a.y32[p0];
+    Rec32 S[PPT];
+    int lme = a.L + 1, lmx = 0;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        S[q].ls = a.L + 1;
+        S[q].acc1 = S[q].acc2 = make_float2(0.f, 0.f);
+        S[q].y = S[q].D = S[q].yc = 0.f;
+        if (p0 + q < a.npairs) {
+            const int64_t si = start_index(a, k, m, neg, p0 + q);
+            S[q].ls = a.ls[si];
+            const float2 st2 = a.st32[si];
+            S[q].y = st2.x;
+            S[q].D = st2.y;
+            S[q].yc = a.y32[p0 + q];
+        }
+        lme = min(lme, S[q].ls);
+        lmx = max(lmx, S[q].ls);
     }
-    if (p0 + 1 < a.npairs) {
-        const int64_t si = start_index(a, k, m, neg, p0 + 1);
-        B.ls = a.ls[si];
-        const float2 s = a.st32[si];
-        B.y = s.x;
-        B.D = s.y;
-        B.yc = a.y32[p0 + 1];
-    }
-    const int lme = min(A.ls, B.ls);
     const int lstart = block_min(lme);
     const int cofs = neg ? 2 : 0;
     Stage32 st;
@@ -302,26 +303,28 @@ __global__ void __launch_bounds__(kNT) k_lcontract_f32(const LcArgs a) {
         // (c1, c2) = (ap, sam) for +k, (am, sap) for -k: one 16-byte load each step
         const float4 *acv = reinterpret_cast<const float4 *>(ac[buf]) + (cofs >> 1);
         int i = max(0, lme - c0);
-        // until both rings have started
-        for (; i < nc && c0 + i < max(A.ls, B.ls); ++i) {
+        // until every ring of the thread has started
+        for (; i < nc && c0 + i < lmx; ++i) {
             const float4 r = rcv[i], cc = acv[2 * i];
             const float ra = r.x, rcc = neg ? r.z : r.y;    // c'- for -k, c'+ for +k
             const float2 c1 = make_float2(cc.x, cc.y), c2 = make_float2(cc.z, cc.w);
-            if (c0 + i >= A.ls) rec32_step(A, ra, rcc, c1, c2);
-            if (c0 + i >= B.ls) rec32_step(B, ra, rcc, c1, c2);
+#pragma unroll
+            for (int q = 0; q < PPT; ++q)
+                if (c0 + i >= S[q].ls) rec32_step(S[q], ra, rcc, c1, c2);
         }
 #pragma unroll 2
         for (; i < nc; ++i) {
             const float4 r = rcv[i], cc = acv[2 * i];
             const float ra = r.x, rcc = neg ? r.z : r.y;    // c'- for -k, c'+ for +k
             const float2 c1 = make_float2(cc.x, cc.y), c2 = make_float2(cc.z, cc.w);
-            rec32_step(A, ra, rcc, c1, c2);
-            rec32_step(B, ra, rcc, c1, c2);
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) rec32_step(S[q], ra, rcc, c1, c2);
         }
         if (next) stage_store(st, ln, &rc[buf ^ 1][threadIdx.x], &ac[buf ^ 1][threadIdx.x]);
     }
-    if (p0 < a.npairs) write_two<float2>(a, m, k, p0, neg, A.acc1, A.acc2);
-    if (p0 + 1 < a.npairs) write_two<float2>(a, m, k, p0 + 1, neg, B.acc1, B.acc2);
+#pragma unroll
+    for (int q = 0; q < PPT; ++q)
+        if (p0 + q < a.npairs) write_two<float2>(a, m, k, p0 + q, neg, S[q].acc1, S[q].acc2);
 }
 
 // ------------------------------------------------------------------ DF64
@@ -459,7 +462,7 @@ sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
     a.ncomp = p->ncomp;
     a.R = p->R;
     a.npairs = p->npairs;
-    a.ppt = (p->precision == SL_FP64) ? 1 : 2;
+    a.ppt = (p->precision == SL_FP64) ? 1 : (p->precision == SL_DF64 ? 2 : kF32Pairs);
     a.nchunk = (p->npairs + a.ppt * kHalf - 1) / (a.ppt * kHalf);
     a.nalm = p->nalm;
     a.sky = (const double2 *)sky;
@@ -490,7 +493,7 @@ sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
         k_to_f32<<<(unsigned)std::min<int64_t>((nb + 255) / 256, 4096), 256, 0, p->stream>>>(
             (const double2 *)beam, p->d_beam32, nb);
         slot = timing_begin(p, "lcontract_f32");
-        k_lcontract_f32<<<(unsigned)nblk, kNT, 0, p->stream>>>(a);
+        k_lcontract_f32<kF32Pairs><<<(unsigned)nblk, kNT, 0, p->stream>>>(a);
     }
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_lcontract launch");
