@@ -15,6 +15,11 @@ Multi-GPU (torchrun): each rank builds the (replicated) cube and evaluates its
 own consecutive shard of the scan; no data-path collective (weak scaling).
 The reference arm (--impl reference) times the CPU FP64 oracle on the host
 cores on a bounded sample of the same workload.
+
+Other workloads (--workload): highres (lmax 2048, kmax 32, precision variant),
+detectors (22 detectors in one CUDA graph), multisky (many skies, tensor cores),
+orbital (orbital dipole through the 4pi beam), psigrid (step 2 through a psi
+grid), sweep (cube-build runtime against lmax).  Each prints the same JSON line.
 """
 from __future__ import annotations
 
@@ -589,7 +594,7 @@ TRAFFIC = {
 }
 
 
-# ----------------------------------------------------------------------------- CPU oracle timing
+# ----------------------------------------------------------------------------- psi-grid variant
 def psigrid_arm(args):
     """Step 2 as the paper states it: the transform over k to a psi grid and
     Lagrange interpolation in theta, phi and psi, against the exact phase sum
@@ -710,6 +715,7 @@ def psigrid_arm(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- runtime sweep
 SWEEP = [(256, 0), (256, 10), (512, 0), (512, 10), (1024, 0), (1024, 10), (2048, 0), (2048, 10), (4096, 0),
          (4096, 10), (8192, 0), (8192, 10), (512, 100)]
 
@@ -796,6 +802,7 @@ def sweep_arm(args):
             f.write(line + "\n")
 
 
+# ----------------------------------------------------------------------------- orbital dipole
 ORB_SUBSAMPLE = 20
 # FP64 flops k_orb_nodes executes per node (DADD + DMUL + 2 DFMA from an ncu op
 # count of one launch, divided by the nodes): the three library sincos and the
@@ -1018,6 +1025,7 @@ def orbital_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------------------- CPU oracle timing
 def oracle_sample(cfg, th, ph, ps, n, ring_sample, samp_n):
     """Time the CPU FP64 oracle on a bounded sample of one step and extrapolate:
     spin Legendre step + DFT for `ring_sample` of the rings, interpolation of
