@@ -18,6 +18,10 @@
 //   the stores are coalesced).  Output layout [R][nphi][npsi].
 // k_interp_psi: one thread per sample in cell-sorted order (the plan's sort),
 //   p^3 reads of the real cube per sample instead of p^2 (K + 1) complex ones.
+// k_interp_psi_tiled (FP32 plans): one CTA per work item of a sort tile; the
+//   tile's stencil nodes (all npsi values, ghost rows already shifted by pi in
+//   phi and psi) are staged in shared memory with coalesced loads, then each
+//   sample reads its p^3 values from there.
 #include <algorithm>
 
 #include "sl_internal.cuh"
@@ -111,6 +115,141 @@ __global__ void __launch_bounds__(256) k_interp_psi(const InterpGeom g, int npsi
         }
         tod[s] = (double)acc;
     }
+}
+
+struct PsiTiledArgs {
+    InterpGeom g;
+    int npsi;
+    const float *cube;
+    const StencilRec32 *rec;
+    const unsigned *perm, *start, *chunk_off;
+    int ntiles, ncell;
+    double *tod;
+};
+
+template <int TC, int P>
+__global__ void __launch_bounds__(256) k_interp_psi_tiled(const PsiTiledArgs A) {
+    constexpr int TW = TC + P - 1, NR = kTileRows + P - 1, NN = NR * TW;
+    const InterpGeom &g = A.g;
+    const int npsi = A.npsi;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *node = reinterpret_cast<float *>(smem_raw);   // [NN][npsi]
+    const float vscale = (float)npsi / 6.28318530717958647692f;
+    const unsigned nchunks = A.chunk_off[A.ntiles];
+    int staged_tile = -1;
+    for (unsigned v = blockIdx.x; v < nchunks; v += gridDim.x) {
+        const int tile = find_tile(A.chunk_off, A.ntiles, v);
+        const unsigned c = v - A.chunk_off[tile];
+        const unsigned s_beg = A.start[(int64_t)tile * A.ncell] + c * kWorkChunk;
+        const unsigned s_end = min(A.start[(int64_t)(tile + 1) * A.ncell], s_beg + kWorkChunk);
+        const int tr = tile / g.ntc, tcol = tile - tr * g.ntc;
+        const int rowlo = tr * kTileRows - P / 2, collo = tcol * TC - P / 2 + 1;
+        if (tile != staged_tile) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < NN * npsi; e += blockDim.x) {
+                const int nd = e / npsi, n = e - nd * npsi;
+                const int r = nd / TW, cc = nd - r * TW;
+                const int row = rowlo + r;
+                float val = 0.f;
+                if (row >= -P / 2 && row <= g.R - 1 + P / 2) {
+                    int ring = row, col = collo + cc, q = n;
+                    if (row < 0 || row >= g.R) {   // ghost row: ring at phi + pi, psi + pi
+                        ring = (row < 0) ? -1 - row : 2 * g.R - 1 - row;
+                        col += g.nphi >> 1;
+                        q += npsi >> 1;
+                        if (q >= npsi) q -= npsi;
+                    }
+                    if (col < 0) col += g.nphi;
+                    if (col >= g.nphi) col -= g.nphi;
+                    if (col >= g.nphi) col -= g.nphi;
+                    val = __ldg(A.cube + ((int64_t)ring * g.nphi + col) * npsi + q);
+                }
+                node[e] = val;
+            }
+            __syncthreads();
+            staged_tile = tile;
+        }
+        for (unsigned t = s_beg + threadIdx.x; t < s_end; t += blockDim.x) {
+            const unsigned s = A.perm[t];
+            const StencilRec32 r = A.rec[s];
+            const int i = (int)(r.cell >> 16) - 1, j = (int)(r.cell & 0xffffu);
+            float o[P], wd[P], wt[P], wp[P], wq[P];
+#pragma unroll
+            for (int a = 0; a < P; ++a) {
+                o[a] = __ldg(g.rowtab32 + (size_t)(i + 1) * 2 * P + a);
+                wd[a] = __ldg(g.rowtab32 + (size_t)(i + 1) * 2 * P + P + a);
+            }
+            lagrange_theta<P>(r.dth, o, wd, wt);
+            lagrange_phi<P>(r.fph, wp);
+            // psi (reduced to [-pi, pi) by the binning) on the periodic grid
+            float vq = r.psr * vscale;
+            if (vq < 0.f) vq += (float)npsi;
+            int n0 = (int)floorf(vq);
+            if (n0 >= npsi) n0 = npsi - 1;
+            if (n0 < 0) n0 = 0;
+            lagrange_phi<P>(vq - (float)n0, wq);
+            int q[P];
+#pragma unroll
+            for (int cq = 0; cq < P; ++cq) {
+                int a = n0 - P / 2 + 1 + cq;
+                q[cq] = a < 0 ? a + npsi : (a >= npsi ? a - npsi : a);
+            }
+            const float *nb = node + ((i - P / 2 + 1 - rowlo) * TW + (j - P / 2 + 1 - collo)) * npsi;
+            float acc = 0.f;
+#pragma unroll
+            for (int a = 0; a < P; ++a) {
+                float ra = 0.f;
+#pragma unroll
+                for (int b = 0; b < P; ++b) {
+                    const float *nd = nb + (a * TW + b) * npsi;
+                    float rb = 0.f;
+#pragma unroll
+                    for (int cq = 0; cq < P; ++cq) rb = fmaf(wq[cq], nd[q[cq]], rb);
+                    ra = fmaf(wp[b], rb, ra);
+                }
+                acc = fmaf(wt[a], ra, acc);
+            }
+            A.tod[s] = (double)acc;
+        }
+    }
+}
+
+size_t interp_psi_tiled_smem(const sl_plan *p, int npsi) {
+    return (size_t)(kTileRows + p->p - 1) * (p->geom.tile_cols + p->p - 1) * npsi * sizeof(float);
+}
+
+sl_status launch_interp_psi_tiled(sl_plan *p, const SortBufs &b, const void *cube, int npsi, int64_t n, double *tod) {
+    (void)n;
+    PsiTiledArgs a;
+    a.g = p->geom;
+    a.npsi = npsi;
+    a.cube = (const float *)cube;
+    a.rec = (const StencilRec32 *)b.rec;
+    a.perm = b.perm;
+    a.start = b.hist;
+    a.chunk_off = b.chunk_off;
+    a.ntiles = p->ntiles;
+    a.ncell = kTileRows * p->geom.tile_cols;
+    a.tod = tod;
+    const size_t sm = interp_psi_tiled_smem(p, npsi);
+    void (*kern)(const PsiTiledArgs) = nullptr;
+#define SL_PT(TCV, PV) \
+    if (p->geom.tile_cols == TCV && p->p == PV) kern = k_interp_psi_tiled<TCV, PV>;
+    SL_PT(32, 4) SL_PT(16, 4) SL_PT(8, 4)
+    SL_PT(32, 2) SL_PT(16, 2) SL_PT(8, 2)
+    SL_PT(32, 6) SL_PT(16, 6) SL_PT(8, 6)
+#undef SL_PT
+    if (!kern) return set_error(SL_ERR_UNSUPPORTED, "tile width %d, interp_order %d", p->geom.tile_cols, p->p);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return cuda_check(e, "k_interp_psi_tiled smem attribute");
+    int per_sm = 1, nsm = 152;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
+    if (per_sm < 1) per_sm = 1;
+    const int slot = timing_begin(p, "interp_psi_f32");
+    kern<<<(unsigned)(nsm * per_sm), 256, sm, p->stream>>>(a);
+    timing_end(p, slot);
+    return cuda_check(cudaGetLastError(), "k_interp_psi_tiled launch");
 }
 
 template <typename T>

@@ -903,6 +903,11 @@ sl_status interp_tod_psi(sl_plan *p, const void *cube_psi, int npsi, const doubl
     if (n == 0) return SL_OK;
     if ((st = ensure_sort_capacity(p, n)) != SL_OK) return st;
     SortBufs b = p->sort;
+    // FP32 plans: tile-staged from shared memory when the tile's npsi values fit
+    if (plan_fp32(p->precision) && interp_psi_tiled_smem(p, npsi) <= kSmemOptin) {
+        if ((st = launch_sort_into(p, b, theta, phi, psi, n, 1, 0, 1)) != SL_OK) return st;
+        return launch_interp_psi_tiled(p, b, cube_psi, npsi, n, tod);
+    }
     b.chunk_off = nullptr;
     if ((st = launch_sort_into(p, b, theta, phi, psi, n, 1, 1, 0)) != SL_OK) return st;
     return launch_interp_psi(p, b, cube_psi, npsi, psi, n, tod);

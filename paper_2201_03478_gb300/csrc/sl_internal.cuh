@@ -317,6 +317,8 @@ size_t psi_cube_smem_bytes(const sl_plan *p, int npsi);
 sl_status launch_psi_cube(sl_plan *p, const void *maps, int npsi, const void *tab, void *out);
 sl_status launch_interp_psi(sl_plan *p, const SortBufs &b, const void *cube, int npsi, const double *psi, int64_t n,
                             double *tod);
+size_t interp_psi_tiled_smem(const sl_plan *p, int npsi);
+sl_status launch_interp_psi_tiled(sl_plan *p, const SortBufs &b, const void *cube, int npsi, int64_t n, double *tod);
 sl_status launch_orbital(sl_plan *p, const OrbLaunch &o);
 
 // launchers (one per translation unit)
