@@ -587,8 +587,8 @@ def multisky_arm(args):
 TRAFFIC = {
     ("lcontract_f64", "fp64"): 674.1e6 + 516.7e6,
     ("interp_f64", "fp64"): 14801.7e6 + 1813.7e6,
-    ("lcontract_f32", "fp32"): 370.5e6 + 231.6e6,
-    ("interp_f32", "fp32"): 7297.4e6 + 2036.5e6,
+    ("lcontract_f32", "fp32"): 370.9e6 + 231.1e6,
+    ("interp_f32", "fp32"): 7258.7e6 + 2029.7e6,
     ("lcontract_df", "df64"): 672.8e6 + 511.4e6,
     ("interp_df", "df64"): 22844.9e6 + 2732.1e6,
 }
