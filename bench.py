@@ -828,7 +828,7 @@ def orbital_bytes(starts, n, s):
 
 
 def orbital_arm(args):
-    """Orbital dipole and quadrupole through the 4pi beam (Sect. 4): the rotation at
+    """Orbital dipole and quadrupole through the 4pi beam (Sect. 3.3): the rotation at
     every 20th sample of each pointing period, a natural cubic spline in between,
     the remainder exact; the exact per-sample GPU evaluation and the CPU oracle
     are timed beside it."""

@@ -219,7 +219,7 @@ sl_status interp_tod_psi(sl_plan *plan, const void *cube_psi, int npsi, const do
                          const double *psi, int64_t n, double *tod);
 
 /* ---------------------------------------------------------------------------
- * Orbital dipole and quadrupole through the full 4pi beam (Sect. 4, Eqs.
+ * Orbital dipole and quadrupole through the full 4pi beam (Sect. 3.3, Eqs.
  * dipole_simple, dipole and dipole_fast).  The satellite velocity beta = v/c
  * (one 3-vector per pointing period, in the frame of the pointings) gives the
  * sky signal D(n) = T0 [beta.n + q (beta.n)^2]; seen through the beam it is

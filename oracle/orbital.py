@@ -1,5 +1,5 @@
 """Plain FP64 CPU oracle for the orbital dipole and quadrupole seen through the
-full 4pi beam (Galloway et al., BeyondPlanck VIII, Sect. 4: Eqs. dipole_simple,
+full 4pi beam (Galloway et al., BeyondPlanck VIII, Sect. 3.3: Eqs. dipole_simple,
 dipole and dipole_fast, and the subsampled-rotation scheme described after them).
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the

@@ -232,7 +232,7 @@ def orbital_moments(plan: Plan, beam):
 
 def orbital_dipole_tod(plan: Plan, beam, T0, q, theta, phi, psi, period_start, beta, subsample=20, tod=None,
                        accumulate=False):
-    """Orbital dipole and quadrupole through the 4pi beam (Sect. 4, Eq. dipole_fast).
+    """Orbital dipole and quadrupole through the 4pi beam (Sect. 3.3, Eq. dipole_fast).
 
     period_start: nper + 1 sample offsets (host, 0 ... n); beta: [nper, 3] velocity / c
     per pointing period (host); subsample: rotation at every s-th sample of a period,

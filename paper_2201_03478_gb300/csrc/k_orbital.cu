@@ -1,5 +1,5 @@
 // k_orbital.cu -- the orbital dipole and quadrupole seen through the full 4pi
-// beam (Sect. 4, Eqs. dipole and dipole_fast), with the paper's acceleration:
+// beam (Sect. 3.3, Eqs. dipole and dipole_fast), with the paper's acceleration:
 // the rotation into the beam frame at every s-th sample of a pointing period,
 // a cubic spline in between, and the remainder of each period exact.
 //

@@ -1,5 +1,5 @@
 """Orbital dipole through the 4pi beam on the GPU (k_orbital.cu through the C ABI)
-against the oracle (Sect. 4, Eq. dipole_fast and the subsampled rotation with a
+against the oracle (Sect. 3.3, Eq. dipole_fast and the subsampled rotation with a
 natural cubic spline): the moments, every sample of small scans with edge-case
 pointing periods (empty, one sample, shorter than and equal to the node
 spacing, with and without a remainder), s = 1 (exact), accumulate, and whole

@@ -1,4 +1,4 @@
-"""Pins of the orbital-dipole oracle (Sect. 4: Eqs. dipole, dipole_fast and the
+"""Pins of the orbital-dipole oracle (Sect. 3.3: Eqs. dipole, dipole_fast and the
 subsampled rotation with a spline in between) against things other than itself:
 quadrature with scipy's spherical harmonics, the Sect. 2.1 convolution oracle on
 the dipole sky, scipy's natural cubic spline, and closed-form special cases."""
