@@ -287,6 +287,21 @@ def gpu_arm(args):
     if lc_name in roofs:
         roofs[lc_name]["flops_dense_triangle"] = fl_dense
         roofs[lc_name]["dense_equivalent_tflops"] = round(fl_dense / (roofs[lc_name]["avg_ms"] / 1e3) / 1e12, 4)
+    # HBM side of both kernels against the measured copy bandwidth: algorithmic bytes and
+    # the ncu-measured DRAM traffic per launch over the live launch time (the ALU roof binds)
+    hbm_peak = measured_peaks().get("hbm_gbs", 6800.0)
+    elem = 16 if prec in ("fp64", "df64") else 8
+    cube_bytes = float(R) * nphi * (K + 1) * elem
+    alg_bytes = {lc_name: float(ncomp) * plan.nalm * 16 * 2 + (K + 1) * R * (2 * L + 1) * elem,
+                 "interp_" + suffix: n * (8.0 + 8.0 + (24.0 if elem == 16 else 16.0) + 4.0) + cube_bytes}
+    for name, r in roofs.items():
+        if name in alg_bytes:
+            sec = r["avg_ms"] / 1e3
+            r["hbm"] = {"algorithmic_bytes": alg_bytes[name], "achieved_gbs": round(alg_bytes[name] / sec / 1e9, 1),
+                        "traffic_gbs": round(r["traffic"] / sec / 1e9, 1) if r.get("traffic") else None,
+                        "peak_gbs": hbm_peak, "frac": round(alg_bytes[name] / sec / 1e9 / hbm_peak, 4),
+                        "note": "interpolation bytes per sample: psi 8, TOD 8, stencil record 24 (FP32 plans "
+                                "16), permutation 4; plus the cube once; contraction: sky read once, G written once"}
     dominant = max(stats.items(), key=lambda kv: kv[1][1])[0] if stats else None
     shares = {k: round(v[1] / max(1e-9, sum(x[1] for x in stats.values())), 4) for k, v in stats.items()}
     launches = sum(v[0] for v in stats.values())
