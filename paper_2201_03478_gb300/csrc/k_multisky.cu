@@ -72,22 +72,33 @@ __device__ __forceinline__ uint32_t ms_idesc(int m, int n) {
 // float index of element (row, k) of a [rows][32] tile in that layout
 __device__ __forceinline__ int ms_sw(int row, int k) { return row * 32 + ((((k >> 2) ^ (row & 7))) << 2) + (k & 3); }
 
+constexpr unsigned kMsSuspendNs = 20000;   // suspend-time hint of one mbarrier test
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
 
+// One test of the phase; a thread whose phase is not complete is suspended in
+// hardware until it completes or kMsSuspendNs pass (no spinning on the issue slots
+// the producer warps need).
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, %3;\n\t"
+                 "selp.u32 %0, 1, 0, q;\n\t}"
+                 : "=r"(done) : "r"(bar), "r"(parity), "n"(kMsSuspendNs) : "memory");
+    return done != 0;
+}
+
 // Waits for the completion of the mbarrier phase of the given parity, for at
-// most limit_ns of wall time; false when the limit expired.
+// most limit_ns of wall time; false when the limit expired.  The wall clock is
+// read only once the first test has failed (reading it is slow).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns = kMsWaitNs) {
+    if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     for (;;) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, q;\n\t}"
-                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-        if (done) return true;
+        if (mbar_try(bar, parity)) return true;
         if (globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
