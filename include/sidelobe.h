@@ -369,6 +369,14 @@ sl_status sl_batch_run(sl_batch *batch);
 sl_status sl_batch_get_info(const sl_batch *batch, sl_batch_info *info);
 void sl_batch_destroy(sl_batch *batch);
 
+/* Bounds-checked builds (the library compiled with -DSL_CHECKED): every data-
+ * dependent gather and scatter index of the binning, scatter, interpolation
+ * (forward and adjoint, all precisions), psi-grid and orbital kernels is tested
+ * before the access; a failed test skips the access and records a site code.
+ * Returns the code of a recorded failure since the last call (0: none) and
+ * clears the record; synchronises the device.  Ordinary builds: always 0. */
+unsigned sl_debug_check_status(void);
+
 /* Thread-local message describing the last non-OK status of this thread. */
 const char *sl_last_error(void);
 

@@ -23,7 +23,7 @@ EXPORTS = ["sidelobe_plan_create", "synth_spin_maps", "interp_tod", "adjoint_tod
            "sl_plan_enable_timing", "sl_plan_kernel_stats", "sl_plan_reserve", "sl_plan_set_tile_cols",
            "sl_batch_create", "sl_batch_run", "sl_batch_get_info", "sl_batch_destroy", "synth_spin_maps_multi",
            "sl_plan_selftest_timeout", "sl_orbital_moments", "orbital_dipole_tod", "synth_psi_cube", "interp_tod_psi",
-           "sl_last_error"]
+           "sl_debug_check_status", "sl_last_error"]
 SL_BATCH_AUTOTUNE = 1
 
 
@@ -62,6 +62,16 @@ class SidelobeError(RuntimeError):
 
 
 _lib = None
+_checked = False
+
+
+def use_checked_build() -> None:
+    """Select the bounds-checked library variant (libsidelobe_checked.so, built on
+    demand) for this process; must come before the first call into the library."""
+    global _checked
+    if _lib is not None:
+        raise RuntimeError("the library is already loaded")
+    _checked = True
 
 
 def load(build: bool = True) -> ctypes.CDLL:
@@ -69,7 +79,10 @@ def load(build: bool = True) -> ctypes.CDLL:
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build() if build else _build.LIB
+    if _checked:
+        path = _build.build(checked=True) if build else _build.LIB_CHECKED
+    else:
+        path = _build.build() if build else _build.LIB
     if not os.path.exists(path):
         raise OSError("libsidelobe.so not found at %s (run paper_2201_03478_gb300._build.build())" % path)
     lib = ctypes.CDLL(path)
@@ -100,6 +113,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "synth_psi_cube": (I, [P, P, I, P]),
         "interp_tod_psi": (I, [P, P, I, P, P, P, I64, P]),
         "orbital_dipole_tod": (I, [P, P, ctypes.c_double, ctypes.c_double, P, P, P, I64, P, P, I64, I, P, I]),
+        "sl_debug_check_status": (ctypes.c_uint, []),
         "sl_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():

@@ -50,6 +50,10 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const do
             for (int b = 0; b < P; ++b) {
                 off[a * P + b] = roff[a] + (((ghost >> a) & 1u) ? coffg[b] : coff[b]);
                 w[a * P + b] = wt[a] * wp[b];
+                if (!SL_GUARD(off[a * P + b] >= 0 &&
+                                  (int64_t)off[a * P + b] + g.K < (int64_t)g.R * g.nphi * (g.K + 1),
+                              0x201u))
+                    off[a * P + b] = 0;
             }
         double sp, cp;
         sincos(psi[s], &sp, &cp);
@@ -144,6 +148,7 @@ __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
                     if (col >= g.nphi) col -= g.nphi;
                     if (col >= g.nphi) col -= g.nphi;
                     flip = ring != row;
+                    if (!SL_GUARD(ring >= 0 && ring < g.R && col >= 0 && col < g.nphi, 0x202u)) ring = col = 0;
                     const float2 *src = A.maps + ((int64_t)ring * g.nphi + col) * K1 + k;
                     const float2 v0 = __ldg(src);
                     const float2 v1 = (k + 1 < K1) ? __ldg(src + 1) : make_float2(0.f, 0.f);
@@ -173,7 +178,9 @@ __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
             float w[P * P];
 #pragma unroll
             for (int q = 0; q < P * P; ++q) w[q] = wt[q / P] * wp[q % P];
-            const float4 *nb = node + (i - P / 2 + 1 - rowlo) * TW + (j - P / 2 + 1 - collo);
+            int nb0 = (i - P / 2 + 1 - rowlo) * TW + (j - P / 2 + 1 - collo);
+            if (!SL_GUARD(nb0 >= 0 && nb0 + (P - 1) * TW + (P - 1) < NN, 0x203u)) nb0 = 0;
+            const float4 *nb = node + nb0;
             float sz, cz;
             sincosf(r.psr, &sz, &cz);
             // z^k for the pair (k, k+1), starting at (1, z)
@@ -201,6 +208,8 @@ __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
         }
     }
 }
+
+SL_CHECK_READER(chk_interp)
 
 size_t interp_f32_tiled_smem_tc(const sl_plan *p, int tc) {
     const int KH = (p->K + 2) / 2;
@@ -273,7 +282,9 @@ __global__ void k_interp_adjoint(const AdjArgs A) {
                 for (int ra = 0; ra < P; ++ra)
 #pragma unroll
                     for (int cb = 0; cb < P; ++cb) ws[ra * P + cb] = wt[ra] * wp[cb];
-                LOC[threadIdx.x] = (i - P / 2 + 1 - rowlo) * tw + (j - P / 2 + 1 - collo);
+                int loc = (i - P / 2 + 1 - rowlo) * tw + (j - P / 2 + 1 - collo);
+                if (!SL_GUARD(loc >= 0 && loc + (P - 1) * tw + (P - 1) < nnode, 0x204u)) loc = 0;
+                LOC[threadIdx.x] = loc;
                 double sp, cp;
                 sincos(A.psi[s], &sp, &cp);
                 const double y = A.y[s], c2 = 2.0 * cp;
@@ -356,6 +367,7 @@ __global__ void k_interp_adjoint(const AdjArgs A) {
             }
             col %= g.nphi;
             if (col < 0) col += g.nphi;
+            if (!SL_GUARD(ring >= 0 && ring < g.R, 0x205u)) continue;
             double2 *o = A.fbar + ((int64_t)ring * g.nphi + col) * K1 + kk;
             atomicAdd(&o->x, sg * val.x);
             atomicAdd(&o->y, sg * val.y);

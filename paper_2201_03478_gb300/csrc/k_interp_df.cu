@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(256) k_interp_df_tiled(const DfArgs A) {
                     if (col < 0) col += g.nphi;
                     if (col >= g.nphi) col -= g.nphi;
                     if (col >= g.nphi) col -= g.nphi;
+                    if (!SL_GUARD(ring >= 0 && ring < g.R && col >= 0 && col < g.nphi, 0x301u)) ring = col = 0;
                     double2 d = __ldg(A.maps + ((int64_t)ring * g.nphi + col) * K1 + k);
                     if (ring != row && (k & 1)) { d.x = -d.x; d.y = -d.y; }
                     const dfl re = df_from_d(d.x), im = df_from_d(d.y);
@@ -122,7 +123,9 @@ __global__ void __launch_bounds__(256) k_interp_df_tiled(const DfArgs A) {
             dfl w[P * P];
 #pragma unroll
             for (int q = 0; q < P * P; ++q) w[q] = df_mul(wt[q / P], wp[q % P]);
-            const float4 *nb = node + (i - P / 2 + 1 - rowlo) * TW + (j - P / 2 + 1 - collo);
+            int nb0 = (i - P / 2 + 1 - rowlo) * TW + (j - P / 2 + 1 - collo);
+            if (!SL_GUARD(nb0 >= 0 && nb0 + (P - 1) * TW + (P - 1) < NN, 0x302u)) nb0 = 0;
+            const float4 *nb = node + nb0;
             const dfl two = df_make(2.f, 0.f);
             // C_k = 2 cos(k psi), S_k = 2 sin(k psi): X_{k+1} = (2 cos psi) X_k - X_{k-1}
             const dfl c1 = df_from_d(2.0 * cp);
@@ -213,7 +216,9 @@ __global__ void k_interp_adjoint_df(const DfArgs A) {
                         const dfl w = df_mul(wt[ra], wp[cb]);
                         ws[ra * P + cb] = make_float2(w.h, w.l);
                     }
-                LOC[threadIdx.x] = (i - P / 2 + 1 - rowlo) * tw + (j - P / 2 + 1 - collo);
+                int loc = (i - P / 2 + 1 - rowlo) * tw + (j - P / 2 + 1 - collo);
+                if (!SL_GUARD(loc >= 0 && loc + (P - 1) * tw + (P - 1) < nnode, 0x303u)) loc = 0;
+                LOC[threadIdx.x] = loc;
                 double sp, cp;
                 sincos(__ldg(A.psi + s), &sp, &cp);
                 const double yv = A.tod[s];
@@ -300,6 +305,7 @@ __global__ void k_interp_adjoint_df(const DfArgs A) {
             }
             col %= g.nphi;
             if (col < 0) col += g.nphi;
+            if (!SL_GUARD(ring >= 0 && ring < g.R, 0x304u)) continue;
             double2 *o = A.fbar + ((int64_t)ring * g.nphi + col) * K1 + kk;
             atomicAdd(&o->x, sg * ((double)val.x + (double)val.y));
             atomicAdd(&o->y, sg * ((double)val.z + (double)val.w));
@@ -393,5 +399,7 @@ sl_status launch_interp_df(sl_plan *p, const SortBufs &b, int fine, const void *
     (void)n;
     return cuda_check(cudaGetLastError(), "k_interp_df launch");
 }
+
+SL_CHECK_READER(chk_interp_df)
 
 }  // namespace sl

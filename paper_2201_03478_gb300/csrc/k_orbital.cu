@@ -240,9 +240,13 @@ __global__ void __launch_bounds__(256) k_orb_eval(const OrbArgs a) {
                 val = a.y[g0];
             } else {
                 const unsigned j = jt < M - 1 ? jt : M - 2;
-                const double4_32a w = a.w[t - j * su];             // r = t - j s (s at the last node)
-                const double *yy = a.y + g0 + j, *mm = a.M2 + g0 + j;
-                val = w.x * yy[0] + w.y * yy[1] + w.z * mm[0] + w.w * mm[1];
+                if (SL_GUARD(g0 + j + 1 < a.nnodes && t - j * su <= su, 0x501u)) {
+                    const double4_32a w = a.w[t - j * su];         // r = t - j s (s at the last node)
+                    const double *yy = a.y + g0 + j, *mm = a.M2 + g0 + j;
+                    val = w.x * yy[0] + w.y * yy[1] + w.z * mm[0] + w.w * mm[1];
+                } else {
+                    val = 0.0;
+                }
             }
         }
         if (exact) val = orb_value(a.S, a.T0, a.q, a.theta[i], a.phi[i], a.psi[i], a.beta + 3 * p);
@@ -297,5 +301,7 @@ sl_status launch_orbital(sl_plan *p, const OrbLaunch &o) {
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_orb_eval launch");
 }
+
+SL_CHECK_READER(chk_orbital)
 
 }  // namespace sl

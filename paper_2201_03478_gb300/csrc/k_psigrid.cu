@@ -105,7 +105,9 @@ __global__ void __launch_bounds__(256) k_interp_psi(const InterpGeom g, int npsi
             T ra = T(0);
 #pragma unroll
             for (int b = 0; b < P; ++b) {
-                const T *node = cube + roff[a] + (gh ? coffg[b] : coff[b]);
+                int no = roff[a] + (gh ? coffg[b] : coff[b]);
+                if (!SL_GUARD(no >= 0 && (int64_t)no + npsi <= (int64_t)g.R * g.nphi * npsi, 0x401u)) no = 0;
+                const T *node = cube + no;
                 T rb = T(0);
 #pragma unroll
                 for (int c = 0; c < P; ++c) rb = fma((T)wq[c], __ldg(node + (gh ? qg[c] : q[c])), rb);
@@ -194,7 +196,9 @@ __global__ void __launch_bounds__(256) k_interp_psi_tiled(const PsiTiledArgs A) 
                 int a = n0 - P / 2 + 1 + cq;
                 q[cq] = a < 0 ? a + npsi : (a >= npsi ? a - npsi : a);
             }
-            const float *nb = node + ((i - P / 2 + 1 - rowlo) * TW + (j - P / 2 + 1 - collo)) * npsi;
+            int nb0 = (i - P / 2 + 1 - rowlo) * TW + (j - P / 2 + 1 - collo);
+            if (!SL_GUARD(nb0 >= 0 && nb0 + (P - 1) * TW + (P - 1) < NN, 0x402u)) nb0 = 0;
+            const float *nb = node + nb0 * npsi;
             float acc = 0.f;
 #pragma unroll
             for (int a = 0; a < P; ++a) {
@@ -304,5 +308,7 @@ sl_status launch_interp_psi(sl_plan *p, const SortBufs &b, const void *cube, int
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_interp_psi launch");
 }
+
+SL_CHECK_READER(chk_psigrid)
 
 }  // namespace sl

@@ -41,6 +41,8 @@ __global__ void __launch_bounds__(256) k_bin(const InterpGeom g, int fine, const
             const int tc = j / g.tile_cols, lj = j - tc * g.tile_cols;
             const unsigned tile = (unsigned)tr * (unsigned)g.ntc + (unsigned)tc;
             key = fine ? tile * (unsigned)(kTileRows * g.tile_cols) + (unsigned)(li * g.tile_cols + lj) : tile;
+            const unsigned nkeys = (unsigned)(g.ntr * g.ntc) * (fine ? (unsigned)(kTileRows * g.tile_cols) : 1u);
+            if (!SL_GUARD(i >= -1 && i < g.R && j >= 0 && j < g.nphi && key < nkeys, 0x101u)) key = 0;
             keys[s] = key;
             // theta - theta(i0), i0 = i - p/2 + 1 the first stencil row (index i0 + half = i + 1),
             // in 2^-60 fixed point (exact for theta >= 2^-8)
@@ -151,13 +153,15 @@ __global__ void k_scan_add(int64_t n, unsigned *__restrict__ data, const unsigne
     if (blockIdx.x == 0 && threadIdx.x == 0) data[n] = bsum[total_slot_from_bsum];
 }
 
-__global__ void __launch_bounds__(256) k_scatter(int64_t n, const unsigned *__restrict__ keys,
+__global__ void __launch_bounds__(256) k_scatter(int64_t n, int64_t nkeys, const unsigned *__restrict__ keys,
                                                  unsigned *__restrict__ cursor, unsigned *__restrict__ perm) {
+    (void)nkeys;
     const unsigned lane = threadIdx.x & 31;
     for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x; s0 < n; s0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = s0 + threadIdx.x;
         const bool ok = s < n;
-        const unsigned key = ok ? keys[s] : 0xffffffffu;
+        unsigned key = ok ? keys[s] : 0xffffffffu;
+        if (ok && !SL_GUARD(key < nkeys, 0x102u)) key = 0;
         const unsigned act = __ballot_sync(0xffffffffu, ok);
         if (ok) {
             const unsigned peers = __match_any_sync(act, key);
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(256) k_scatter(int64_t n, const unsigned *__re
             unsigned base = 0;
             if ((int)lane == leader) base = atomicAdd(cursor + key, (unsigned)__popc(peers));
             base = __shfl_sync(peers, base, leader);
-            perm[base + rank] = (unsigned)s;
+            if (SL_GUARD(base + rank < n, 0x103u)) perm[base + rank] = (unsigned)s;
         }
     }
 }
@@ -179,6 +183,8 @@ __global__ void k_tile_chunks(int ntiles, int ncell, const unsigned *__restrict_
     const unsigned c = start[(int64_t)(t + 1) * ncell] - start[(int64_t)t * ncell];
     chunk_off[t] = (c + kChunk - 1) / kChunk;
 }
+
+SL_CHECK_READER(chk_sort)
 
 static unsigned grid_for(int64_t n, int bs) {
     int64_t b = (n + bs - 1) / bs;
@@ -213,7 +219,7 @@ sl_status launch_sort_into(sl_plan *p, const SortBufs &b, const double *theta, c
     timing_end(p, slot);
     if ((st = cuda_check(cudaGetLastError(), "k_scan launch")) != SL_OK) return st;
     slot = timing_begin(p, "scatter");
-    k_scatter<<<grid_for(n, 256), 256, 0, p->stream>>>(n, b.keys, b.cursor, b.perm);
+    k_scatter<<<grid_for(n, 256), 256, 0, p->stream>>>(n, nkeys, b.keys, b.cursor, b.perm);
     timing_end(p, slot);
     if ((st = cuda_check(cudaGetLastError(), "k_scatter launch")) != SL_OK) return st;
     if (with_chunks) {

@@ -913,6 +913,14 @@ sl_status interp_tod_psi(sl_plan *p, const void *cube_psi, int npsi, const doubl
     return launch_interp_psi(p, b, cube_psi, npsi, psi, n, tod);
 }
 
+unsigned sl_debug_check_status(void) {
+    // every unit's word is read (and cleared); the first nonzero one is reported
+    const unsigned w[5] = {chk_sort(), chk_interp(), chk_interp_df(), chk_psigrid(), chk_orbital()};
+    for (unsigned v : w)
+        if (v) return v;
+    return 0u;
+}
+
 sl_status sl_plan_enable_timing(sl_plan *p, int enable) {
     sl_status st = enter(p);
     if (st != SL_OK) return st;

@@ -62,6 +62,38 @@ struct InterpGeom {
     const float2 *rowtab_df;      // [(R+1) * 2p]: the same, as double-float (hi, lo)
 };
 
+// Bounds-checked builds (-DSL_CHECKED, the variant _build.build(checked=True) makes):
+// SL_GUARD(cond, site) is true in ordinary builds (no code); in checked builds it
+// evaluates cond and, when it fails, records the site in this translation unit's
+// status word and skips the access it guards.  The status words of all units are
+// read by sl_debug_check_status.
+#ifdef SL_CHECKED
+static __device__ unsigned sl_chk_word;
+__device__ __forceinline__ bool sl_guard(bool ok, unsigned site) {
+    if (!ok) atomicCAS(&sl_chk_word, 0u, site);
+    return ok;
+}
+#define SL_GUARD(cond, site) (::sl::sl_guard((cond), (site)))
+#define SL_CHECK_READER(name)                                                  \
+    unsigned name() {                                                          \
+        unsigned v = 0;                                                        \
+        cudaMemcpyFromSymbol(&v, sl_chk_word, sizeof(v));                      \
+        const unsigned z = 0;                                                  \
+        cudaMemcpyToSymbol(sl_chk_word, &z, sizeof(z));                        \
+        return v;                                                              \
+    }
+#else
+#define SL_GUARD(cond, site) (true)
+#define SL_CHECK_READER(name) \
+    unsigned name() { return 0u; }
+#endif
+// per-unit readers (each translation unit with guards defines its own)
+unsigned chk_sort();
+unsigned chk_interp();
+unsigned chk_interp_df();
+unsigned chk_psigrid();
+unsigned chk_orbital();
+
 // p-point Lagrange weights (separable interpolation, any even p).  theta:
 // nodes at offsets o[a] from the first stencil row (o[0] = 0), 1/prod(o_a - o_b)
 // in wd; d0 = theta - theta(first row).  phi: uniform nodes x_b = b - p/2 + 1
