@@ -276,6 +276,8 @@ typedef struct {
                               (the evanescent part below the significance
                               threshold is skipped) */
     int64_t tile_cols;     /* phi columns per sort tile (the tile is 4 rows high) */
+    int64_t fft_rings;     /* rings x k orders one CTA of the ring FFT transforms */
+    int64_t fft_korders;   /* (both 0 when the rings need the cluster form) */
 } sl_plan_sizes;
 sl_status sl_plan_get_sizes(const sl_plan *plan, sl_plan_sizes *out);
 
@@ -296,6 +298,16 @@ sl_status sl_plan_reserve(sl_plan *plan, int64_t n);
  * holds the plan; SL_ERR_UNSUPPORTED when the staged tile would not fit in
  * shared memory. */
 sl_status sl_plan_set_tile_cols(sl_plan *plan, int tile_cols);
+
+/* Sets how many rings (1, 2 or 4) and beam orders k (1 or 2) one CTA of the
+ * ring FFT of synth_spin_maps transforms together (Sect. 2.1, step 1: the
+ * transform along each ring of every F_k): its G reads then cover that many
+ * adjacent rings and its cube writes that many adjacent k.  0, 0 restores the
+ * default.  Results do not depend on it (every transform runs the same
+ * arithmetic); speed does.  SL_ERR_ARG for other values; SL_ERR_UNSUPPORTED
+ * when rings x korders transforms of nphi values do not fit in one CTA's shared
+ * memory, or when the rings are long enough to need the cluster form. */
+sl_status sl_plan_set_fft_tile(sl_plan *plan, int rings, int korders);
 
 /* Synchronises the plan's stream; reports device faults as SL_ERR_CUDA and an
  * expired bounded wait inside a kernel (synth_spin_maps_multi) as

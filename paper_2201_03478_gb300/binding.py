@@ -78,6 +78,11 @@ class Plan:
         """Sort-tile width in phi columns: 8, 16 or 32 (sl_plan_set_tile_cols)."""
         check(_lib.load().sl_plan_set_tile_cols(self.ptr, int(tile_cols)))
 
+    def set_fft_tile(self, rings, korders):
+        """Rings (1, 2, 4) x beam orders (1, 2) per CTA of the ring FFT; 0, 0 for the
+        default (sl_plan_set_fft_tile)."""
+        check(_lib.load().sl_plan_set_fft_tile(self.ptr, int(rings), int(korders)))
+
     def __del__(self):
         try:
             plan_destroy(self)

@@ -1,7 +1,7 @@
 // k_fft.cu -- the phi direction of the cube (Sect. 2.1, step 1 of the
 // two-step algorithm: the synthesis along each ring) and its transpose.
 //
-// Synthesis (one CTA per (ring r, k)):
+// Synthesis (one CTA per group of up to 4 rings x 2 orders k, in place):
 //   H(q)  = sum_{m = q mod nphi, |m| <= L} G_k(r, m)     (exact alias folding,
 //           G stored [k][m + L][r])
 //   F_k(r, phi_j) = sum_q H(q) e^{+2 pi i q j / nphi}    (inverse DFT)
@@ -16,9 +16,11 @@
 // cluster synchronises after each pass, and each CTA gathers and writes its
 // own slice of the ring.
 //
-// The DFT is a self-sorting (Stockham) mixed-radix FFT with radices 4, 2, 3, 5
-// entirely in shared memory, twiddles from a table e^{+2 pi i j/nphi} built in
-// long double on the host.  Each pass computes, for butterfly t in [0, N/R):
+// The synthesis DFT is a decimation-in-time mixed-radix FFT (radices 4, 2, 3,
+// 5) in place in shared memory on digit-reversed input; the transpose and the
+// cluster form use a self-sorting (Stockham) FFT with two buffers.  Twiddles
+// come from a table e^{+2 pi i j/nphi} built in long double on the host.  Each
+// Stockham pass computes, for butterfly t in [0, N/R):
 //   kk = t mod Ns,  v_q = x[t + q N/R] w^{s q kk N/(Ns R)},  v = DFT_R(v),
 //   y[(t div Ns) Ns R + kk + q Ns] = v_q,  Ns <- Ns R.
 #include <cooperative_groups.h>
@@ -158,57 +160,146 @@ __device__ C *fft_smem(C *buf0, C *buf1, int N, const Radices &rad, const C *__r
     return src;
 }
 
-constexpr int kRingGroup = 4;   // rings per sector of an FP32 G row
+constexpr int kRingGroup = 4;   // rings per sector of an FP32 G row (cluster form)
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_ringfft_synth(int L, int K, int R, int N, Radices rad,
-                                                       const typename CplxOf<T>::type *__restrict__ G,
-                                                       const typename CplxOf<T>::type *__restrict__ tw,
-                                                       typename CplxOf<T>::type *__restrict__ maps) {
+// ------------------------------------------------------------------ in-place multi-ring form
+// One CTA transforms RG consecutive rings x KG consecutive k (TT = RG KG
+// transforms).  Shared memory holds units of TT values, unit e = element e of
+// every transform (t = ring-slot KG + k-slot), so each butterfly loads and
+// stores whole units and reads its twiddles once for all TT transforms.  The
+// G reads of a CTA cover RG adjacent rings of one (k, m) row (G is ring-fastest)
+// and its cube writes KG adjacent k of one (ring, j) (the cube is k-fastest).
+// The transform runs in place (decimation in time): slot s receives the input
+// q = slotq[s] (and q sits in slot qslot[q]), the digit reversal of s in the radix sequence (the last pass's
+// radix least significant), and pass p (radix R, span Ns = product of the
+// earlier radices) combines, for each block of Ns R slots and kk < Ns, the slots
+// kk + q Ns (q < R) after the twiddles e^{+2 pi i kk q/(Ns R)} -- each butterfly
+// reads and writes the same R slots, so one buffer suffices.  Units are placed
+// with an XOR swizzle, unit e at e ^ ((e / U) mod U), U units per 128-byte bank
+// row, so that the strided butterflies of the first passes do not collide on
+// the same banks.
+template <typename C, int TT>
+struct alignas(TT * sizeof(C) >= 16 ? 16 : TT * sizeof(C)) FftUnit {
+    C v[TT];
+};
+
+template <int UB>
+struct Swz {   // UB bytes per unit
+    static constexpr int U = UB >= 128 ? 1 : 128 / UB;
+    static constexpr int lg = U >= 16 ? 4 : U >= 8 ? 3 : U >= 4 ? 2 : U >= 2 ? 1 : 0;
+    static __device__ __forceinline__ int at(int e) { return e ^ ((e >> lg) & (U - 1)); }
+    static int units(int n) { return (n + U - 1) / U * U; }   // slots allocated for n units
+};
+
+template <typename C, int R, int TT>
+__device__ __forceinline__ void dit_pass(C *x, int N, int Ns, const C *__restrict__ ptw) {
+    using Ut = FftUnit<C, TT>;
+    using S = Swz<TT * (int)sizeof(C)>;
+    Ut *xu = reinterpret_cast<Ut *>(x);
+    const bool p2 = (Ns & (Ns - 1)) == 0;
+    const int lg = __ffs(Ns) - 1;
+    for (int b = threadIdx.x; b < N / R; b += blockDim.x) {
+        const int kk = p2 ? (b & (Ns - 1)) : b % Ns;
+        const int g = p2 ? (b >> lg) : b / Ns;
+        const int e0 = g * Ns * R + kk;
+        Ut u[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) u[q] = xu[S::at(e0 + q * Ns)];
+        C w[R];
+#pragma unroll
+        for (int q = 1; q < R; ++q) w[q] = Ns > 1 ? __ldg(ptw + (q - 1) * Ns + kk) : mk<C>(1.0, 0.0);
+#pragma unroll
+        for (int t = 0; t < TT; ++t) {
+            C v[R];
+            v[0] = u[0].v[t];
+#pragma unroll
+            for (int q = 1; q < R; ++q) v[q] = Ns > 1 ? mulc(u[q].v[t], w[q]) : u[q].v[t];
+            dft_small<C, true>(R, v);
+#pragma unroll
+            for (int q = 0; q < R; ++q) u[q].v[t] = v[q];
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) xu[S::at(e0 + q * Ns)] = u[q];
+    }
+}
+
+template <typename T, int RG, int KG>
+__global__ void __launch_bounds__(256) k_ringfft_synth_ip(int L, int K, int R, int N, Radices rad,
+                                                          const typename CplxOf<T>::type *__restrict__ G,
+                                                          const typename CplxOf<T>::type *__restrict__ ptw,
+                                                          const int *__restrict__ slotq,
+                                                          const int *__restrict__ qslot,
+                                                          typename CplxOf<T>::type *__restrict__ maps) {
     using C = typename CplxOf<T>::type;
+    constexpr int TT = RG * KG;
+    using S = Swz<TT * (int)sizeof(C)>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf0 = reinterpret_cast<C *>(smem_raw);
-    C *buf1 = buf0 + N;
-    // CTA order: kRingGroup consecutive rings fastest, then k, then the ring
-    // group, so that the rings sharing a sector of G (ring index fastest) and the
-    // k values sharing a sector of the cube ([r][j][k]) run close together
-    int b = blockIdx.x;
-    const int rlo = b % kRingGroup;
-    b /= kRingGroup;
-    const int k = b % (K + 1);
-    const int r = (b / (K + 1)) * kRingGroup + rlo;
-    if (r >= R) return;
+    C *x = reinterpret_cast<C *>(smem_raw);   // units [slot][TT]
+    // CTA order: the k groups of one ring group adjacent (they share the cube's sectors)
+    const int nkg = (K + KG) / KG;
+    const int kg = (int)blockIdx.x % nkg;
+    const int r0 = ((int)blockIdx.x / nkg) * RG, k0 = kg * KG;
     // blockIdx.y: sky of a multi-sky build (consecutive G and cube blocks)
     G += (int64_t)blockIdx.y * (K + 1) * R * (2 * L + 1);
     maps += (int64_t)blockIdx.y * R * N * (K + 1);
-    const C *g = G + (int64_t)k * (2 * L + 1) * R + r;
-    // the first alias of kGather values of q per thread is loaded before any is used
-    constexpr int kGather = 8;
     const bool p2n = (N & (N - 1)) == 0;
     const int lgn = __ffs(N) - 1;
-    for (int q0 = threadIdx.x; q0 < N; q0 += kGather * blockDim.x) {
-        C v[kGather];
-#pragma unroll
-        for (int i = 0; i < kGather; ++i) {
-            const int q = q0 + i * (int)blockDim.x;
-            const int m = q - N * (p2n ? (q + L) >> lgn : (q + L) / N);   // smallest m >= -L, m = q (mod N)
-            v[i] = (q < N && m <= L) ? g[(int64_t)(m + L) * R] : mk<C>(0.0, 0.0);
-        }
-#pragma unroll
-        for (int i = 0; i < kGather; ++i) {
-            const int q = q0 + i * (int)blockDim.x;
-            if (q < N) {
-                C acc = v[i];
-                for (int m = q - N * (p2n ? (q + L) >> lgn : (q + L) / N) + N; m <= L; m += N)
-                    acc = add(acc, g[(int64_t)(m + L) * R]);
-                buf0[q] = acc;
-            }
-        }
+    // gather, slot by slot: lanes run over the ring slot, then the k slot, then
+    // the slot s; slot s receives the first alias m >= -L of its input q =
+    // slotq[s] by an asynchronous copy (zero when there is none), so that every
+    // copy of the CTA is in flight at once
+    const int total = N * TT;
+    for (int u = threadIdx.x; u < total; u += blockDim.x) {
+        const int ri = u % RG, ki = (u / RG) % KG, sl = u / TT;
+        const int k = k0 + ki, r = r0 + ri;
+        const int q = __ldg(slotq + sl);
+        const int m = q - N * (p2n ? (q + L) >> lgn : (q + L) / N);   // smallest m >= -L, m = q (mod N)
+        const bool ok = k <= K && r < R && m <= L;
+        const C *src = ok ? G + ((int64_t)k * (2 * L + 1) + (m + L)) * R + r : G;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(x + S::at(sl) * TT + ri * KG + ki);
+        if (sizeof(C) == 8)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src),
+                         "r"(ok ? 8 : 0) : "memory");
+        else
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                         "r"(ok ? 16 : 0) : "memory");
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    // the further aliases (2L + 1 > N): m = N - L + i, i < min(N, 2L + 1 - N), are
+    // the aliases after the first of distinct q, each with its own multiples of N
+    const int next = min(N, 2 * L + 1 - N);
+    for (int u = threadIdx.x; u < next * TT; u += blockDim.x) {
+        const int ri = u % RG, ki = (u / RG) % KG, i = u / TT;
+        const int k = k0 + ki, r = r0 + ri;
+        if (k > K || r >= R) continue;
+        const int m0 = N - L + i;
+        C acc = mk<C>(0.0, 0.0);
+        for (int m = m0; m <= L; m += N) acc = add(acc, G[((int64_t)k * (2 * L + 1) + (m + L)) * R + r]);
+        const int q = ((m0 % N) + N) % N;   // m0 < 0 when L > N
+        C *d = x + S::at(__ldg(qslot + q)) * TT + ri * KG + ki;
+        *d = add(*d, acc);
     }
     __syncthreads();
-    const C *res = fft_smem<C, true>(buf0, buf1, N, rad, tw);
-    C *out = maps + (int64_t)r * N * (K + 1) + k;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) out[(int64_t)j * (K + 1)] = res[j];
+    int Ns = 1, off = 0;
+    for (int pass = 0; pass < rad.n; ++pass) {
+        const int Rp = (int)((rad.code >> (3 * pass)) & 7);
+        switch (Rp) {
+            case 4: dit_pass<C, 4, TT>(x, N, Ns, ptw + off); break;
+            case 2: dit_pass<C, 2, TT>(x, N, Ns, ptw + off); break;
+            case 3: dit_pass<C, 3, TT>(x, N, Ns, ptw + off); break;
+            default: dit_pass<C, 5, TT>(x, N, Ns, ptw + off); break;
+        }
+        __syncthreads();
+        off += Ns * (Rp - 1);
+        Ns *= Rp;
+    }
+    // write: lanes run over the k slot, then the ring slot, then j
+    for (int u = threadIdx.x; u < total; u += blockDim.x) {
+        const int ki = u % KG, ri = (u / KG) % RG, j = u / TT;
+        const int k = k0 + ki, r = r0 + ri;
+        if (k <= K && r < R) maps[((int64_t)r * N + j) * (K + 1) + k] = x[S::at(j) * TT + ri * KG + ki];
+    }
 }
 
 __global__ void __launch_bounds__(256) k_ringdft_adjoint(int L, int K, int R, int N, Radices rad,
@@ -371,8 +462,75 @@ static int fft_cluster_size(int N, size_t elem) {
     return 0;
 }
 
+static Radices radices_of(const sl_plan *p) {
+    Radices r;
+    r.n = p->nradix;
+    r.code = 0;
+    for (int i = 0; i < p->nradix; ++i) r.code |= (unsigned long long)p->radices[i] << (3 * i);
+    return r;
+}
+
+// The synthesis runs in place (one buffer of nphi values per transform): one CTA
+// while a single transform fits, else the two-buffer cluster form.
 int ring_fft_cluster_size(const sl_plan *p) {
-    return fft_cluster_size(p->nphi, plan_wide(p->precision) ? sizeof(double2) : sizeof(float2));
+    const size_t elem = plan_wide(p->precision) ? sizeof(double2) : sizeof(float2);
+    if ((size_t)p->nphi * elem <= (size_t)kFftSmemMax) return 1;
+    return fft_cluster_size(p->nphi, elem);
+}
+
+size_t ring_fft_ip_smem(const sl_plan *p, int rg, int kg) {
+    const int ub = rg * kg * (plan_wide(p->precision) ? (int)sizeof(double2) : (int)sizeof(float2));
+    const int U = ub >= 128 ? 1 : 128 / ub;
+    return (size_t)((p->nphi + U - 1) / U * U) * ub;   // slots rounded up to whole swizzle groups
+}
+
+// Default tile: 2 rings x 1 order within kFftIpBudget bytes of shared memory,
+// else 1 x 1 (measured at lmax 1024, 1024 x 2048 rings, kmax 16, FP32 and FP64:
+// 2 x 1 fastest, before 1 x 2, 1 x 1, 2 x 2, 4 x 1 and 4 x 2 -- the larger tiles
+// lose more to fewer resident CTAs than they gain from wider requests).
+constexpr size_t kFftIpBudget = 64 * 1024;
+
+void ring_fft_tile(const sl_plan *p, int *rg, int *kg) {
+    *rg = *kg = 0;
+    if (ring_fft_cluster_size(p) != 1) return;
+    if (p->fft_rg > 0) {
+        *rg = p->fft_rg;
+        *kg = p->fft_kg;
+        return;
+    }
+    static const int cand[2][2] = {{2, 1}, {1, 1}};
+    for (const auto &c : cand)
+        if (ring_fft_ip_smem(p, c[0], c[1]) <= kFftIpBudget || (c[0] == 1 && c[1] == 1)) {
+            *rg = c[0];
+            *kg = c[1];
+            return;
+        }
+}
+
+template <typename T, int RG, int KG>
+static cudaError_t launch_ip(sl_plan *p, const void *G, int nsky, void *maps) {
+    using C = typename CplxOf<T>::type;
+    const size_t sm = ring_fft_ip_smem(p, RG, KG);
+    cudaError_t e = cudaFuncSetAttribute(k_ringfft_synth_ip<T, RG, KG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const unsigned nblk = (unsigned)(((p->R + RG - 1) / RG) * ((p->K + KG) / KG));
+    const C *ptw = plan_wide(p->precision) ? (const C *)p->d_ptw64 : (const C *)p->d_ptw32;
+    k_ringfft_synth_ip<T, RG, KG><<<dim3(nblk, (unsigned)nsky), 256, sm, p->stream>>>(
+        p->L, p->K, p->R, p->nphi, radices_of(p), (const C *)G, ptw, p->d_fftperm, p->d_fftpos, (C *)maps);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_ip_tile(sl_plan *p, int rg, int kg, const void *G, int nsky, void *maps) {
+    switch (rg * 4 + kg) {
+        case 4 * 4 + 2: return launch_ip<T, 4, 2>(p, G, nsky, maps);
+        case 2 * 4 + 2: return launch_ip<T, 2, 2>(p, G, nsky, maps);
+        case 4 * 4 + 1: return launch_ip<T, 4, 1>(p, G, nsky, maps);
+        case 2 * 4 + 1: return launch_ip<T, 2, 1>(p, G, nsky, maps);
+        case 1 * 4 + 2: return launch_ip<T, 1, 2>(p, G, nsky, maps);
+        default: return launch_ip<T, 1, 1>(p, G, nsky, maps);
+    }
 }
 
 template <typename K_, typename... Args>
@@ -392,14 +550,6 @@ static cudaError_t launch_cluster(K_ kern, dim3 grid, int csize, size_t sm, cuda
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
-static Radices radices_of(const sl_plan *p) {
-    Radices r;
-    r.n = p->nradix;
-    r.code = 0;
-    for (int i = 0; i < p->nradix; ++i) r.code |= (unsigned long long)p->radices[i] << (3 * i);
-    return r;
 }
 
 sl_status launch_ringfft_synth_from(sl_plan *p, const void *G, int nsky, void *maps) {
@@ -425,21 +575,18 @@ sl_status launch_ringfft_synth_from(sl_plan *p, const void *G, int nsky, void *m
         timing_end(p, slot);
         return cuda_check(e, "k_ringfft_synth_cl launch");
     }
+    int rg, kg;
+    ring_fft_tile(p, &rg, &kg);
+    cudaError_t e;
     if (plan_wide(p->precision)) {
-        const size_t sm = 2 * (size_t)p->nphi * sizeof(double2);
-        cudaFuncSetAttribute(k_ringfft_synth<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         slot = timing_begin(p, "ringfft_f64");
-        k_ringfft_synth<double><<<nblk, 256, sm, p->stream>>>(p->L, p->K, p->R, p->nphi, radices_of(p),
-                                                              (const double2 *)G, p->d_tw64, (double2 *)maps);
+        e = launch_ip_tile<double>(p, rg, kg, G, nsky, maps);
     } else {
-        const size_t sm = 2 * (size_t)p->nphi * sizeof(float2);
-        cudaFuncSetAttribute(k_ringfft_synth<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         slot = timing_begin(p, "ringfft_f32");
-        k_ringfft_synth<float><<<nblk, 256, sm, p->stream>>>(p->L, p->K, p->R, p->nphi, radices_of(p),
-                                                             (const float2 *)G, p->d_tw32, (float2 *)maps);
+        e = launch_ip_tile<float>(p, rg, kg, G, nsky, maps);
     }
     timing_end(p, slot);
-    return cuda_check(cudaGetLastError(), "k_ringfft_synth launch");
+    return cuda_check(e, "k_ringfft_synth_ip launch");
 }
 
 sl_status launch_ringfft_synth(sl_plan *p, void *maps) { return launch_ringfft_synth_from(p, p->d_G, 1, maps); }

@@ -279,6 +279,10 @@ void plan_destroy(sl_plan *p) {
     dfree(p->d_beam32);
     dfree(p->d_tw64);
     dfree(p->d_tw32);
+    dfree(p->d_fftperm);
+    dfree(p->d_fftpos);
+    dfree(p->d_ptw64);
+    dfree(p->d_ptw32);
     if (p->d_Gadj && (void *)p->d_Gadj != p->d_G) dfree(p->d_Gadj);
     dfree(p->d_G);
     dfree(p->d_Fbar);
@@ -434,6 +438,7 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     TRY(dalloc_t(p, &p->d_lut, lut.size(), "ring lut"));
     TRY(dalloc_t(p, &p->d_tw64, tw64.size(), "twiddles"));
     TRY(dalloc_t(p, &p->d_tw32, tw32.size(), "twiddles"));
+    TRY(dalloc_t(p, &p->d_fftperm, (size_t)p->nphi, "fft slot table"));
     TRY(dalloc_t(p, &d_c2, p->npairs, "seed tmp"));
     TRY(dalloc_t(p, &d_s2, p->npairs, "seed tmp"));
     TRY(dalloc_t(p, &d_cs, p->npairs, "seed tmp"));
@@ -452,6 +457,50 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
     TRY(cuda_check(cudaMemcpy(p->d_lut, lut.data(), lut.size() * sizeof(int), cudaMemcpyHostToDevice), "upload"));
     TRY(cuda_check(cudaMemcpy(p->d_tw64, tw64.data(), tw64.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload"));
     TRY(cuda_check(cudaMemcpy(p->d_tw32, tw32.data(), tw32.size() * sizeof(float2), cudaMemcpyHostToDevice), "upload"));
+    {
+        // In-place ring FFT.  Input q sits in slot pos(q): the digits of q in the
+        // radix sequence, the last pass's radix least significant, reversed; the
+        // table holds q for each slot.  Pass twiddles: for pass (span Ns, radix R),
+        // entries (q - 1) Ns + kk = e^{+2 pi i kk q / (Ns R)}, q in [1, R), kk < Ns,
+        // passes one after another (nphi - 1 entries in all).
+        std::vector<int> slotq((size_t)p->nphi), qslot((size_t)p->nphi);
+        for (int q = 0; q < p->nphi; ++q) {
+            int pos = 0, mult = p->nphi, n = q;
+            for (int i = p->nradix - 1; i >= 0; --i) {
+                mult /= p->radices[i];
+                pos += (n % p->radices[i]) * mult;
+                n /= p->radices[i];
+            }
+            slotq[(size_t)pos] = q;
+            qslot[(size_t)q] = pos;
+        }
+        std::vector<double2> ptw64((size_t)p->nphi, make_double2(0.0, 0.0));
+        std::vector<float2> ptw32((size_t)p->nphi, make_float2(0.f, 0.f));
+        size_t o = 0;
+        long long Ns = 1;
+        for (int i = 0; i < p->nradix; ++i) {
+            const int Rp = p->radices[i];
+            for (int q = 1; q < Rp; ++q)
+                for (long long kk = 0; kk < Ns; ++kk, ++o) {
+                    const long double a = 2.0L * 3.14159265358979323846264338327950288L * (long double)(kk * q) /
+                                          (long double)(Ns * Rp);
+                    ptw64[o] = make_double2((double)cosl(a), (double)sinl(a));
+                    ptw32[o] = make_float2((float)cosl(a), (float)sinl(a));
+                }
+            Ns *= Rp;
+        }
+        TRY(dalloc_t(p, &p->d_fftpos, qslot.size(), "fft slot table"));
+        TRY(cuda_check(cudaMemcpy(p->d_fftpos, qslot.data(), qslot.size() * sizeof(int), cudaMemcpyHostToDevice),
+                       "upload"));
+        TRY(dalloc_t(p, &p->d_ptw64, ptw64.size(), "pass twiddles"));
+        TRY(dalloc_t(p, &p->d_ptw32, ptw32.size(), "pass twiddles"));
+        TRY(cuda_check(cudaMemcpy(p->d_fftperm, slotq.data(), slotq.size() * sizeof(int), cudaMemcpyHostToDevice),
+                       "upload"));
+        TRY(cuda_check(cudaMemcpy(p->d_ptw64, ptw64.data(), ptw64.size() * sizeof(double2), cudaMemcpyHostToDevice),
+                       "upload"));
+        TRY(cuda_check(cudaMemcpy(p->d_ptw32, ptw32.data(), ptw32.size() * sizeof(float2), cudaMemcpyHostToDevice),
+                       "upload"));
+    }
     TRY(cuda_check(cudaMemcpy(d_c2, c2.data(), c2.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
     TRY(cuda_check(cudaMemcpy(d_s2, s2.data(), s2.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
     TRY(cuda_check(cudaMemcpy(d_cs, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
@@ -616,6 +665,12 @@ sl_status sl_plan_get_sizes(const sl_plan *p, sl_plan_sizes *o) {
     o->scratch_bytes = p->bytes_held;
     o->lsteps = p->lsteps;
     o->tile_cols = p->geom.tile_cols;
+    {
+        int rg, kg;
+        ring_fft_tile(p, &rg, &kg);
+        o->fft_rings = rg;
+        o->fft_korders = kg;
+    }
     return SL_OK;
 }
 
@@ -643,6 +698,28 @@ sl_status sl_plan_set_tile_cols(sl_plan *p, int tc) {
     free_sort_tables(p);
     set_tile_grid(p, tc);
     return alloc_sort_tables(p);
+}
+
+sl_status sl_plan_set_fft_tile(sl_plan *p, int rings, int korders) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if (rings == 0 && korders == 0) {
+        p->fft_rg = p->fft_kg = 0;
+        return SL_OK;
+    }
+    if ((rings != 1 && rings != 2 && rings != 4) || (korders != 1 && korders != 2))
+        return set_error(SL_ERR_ARG, "fft tile %d x %d: rings must be 1, 2 or 4 and korders 1 or 2", rings, korders);
+    if (ring_fft_cluster_size(p) != 1)
+        return set_error(SL_ERR_UNSUPPORTED, "nphi=%d: the ring FFT runs on clusters", p->nphi);
+    int dev_smem = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    const size_t need = ring_fft_ip_smem(p, rings, korders);
+    if (need > (size_t)kFftSmemMax || (dev_smem > 0 && need > (size_t)dev_smem))
+        return set_error(SL_ERR_UNSUPPORTED, "fft tile %d x %d needs %zu bytes of shared memory", rings, korders,
+                         need);
+    p->fft_rg = rings;
+    p->fft_kg = korders;
+    return SL_OK;
 }
 
 sl_status sl_plan_set_stream(sl_plan *p, void *stream) {

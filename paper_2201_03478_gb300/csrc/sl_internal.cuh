@@ -274,6 +274,11 @@ struct sl_plan {
     // ring FFT
     double2 *d_tw64 = nullptr;        // [nphi] e^{+2 pi i j / nphi}
     float2 *d_tw32 = nullptr;
+    int *d_fftperm = nullptr;         // [nphi] FFT input q held by slot s (in-place ring FFT)
+    int *d_fftpos = nullptr;          // [nphi] slot of FFT input q (its inverse)
+    double2 *d_ptw64 = nullptr;       // [nphi] per-pass twiddles of the in-place ring FFT
+    float2 *d_ptw32 = nullptr;
+    int fft_rg = 0, fft_kg = 0;       // rings x k orders per in-place FFT CTA (0: default)
     int radices[sl::kMaxRadices];
     int nradix = 0;
 
@@ -364,6 +369,10 @@ sl_status launch_ringfft_synth(sl_plan *p, void *maps);
 sl_status launch_ringfft_synth_from(sl_plan *p, const void *G, int nsky, void *maps);
 // CTAs per cluster of the ring FFT (1: one CTA per ring; 0: unsupported nphi)
 int ring_fft_cluster_size(const sl_plan *p);
+// rings x k orders per CTA of the in-place ring FFT the plan uses (0, 0 for the cluster form)
+void ring_fft_tile(const sl_plan *p, int *rg, int *kg);
+// shared memory of the in-place ring FFT for RG rings x KG k orders
+size_t ring_fft_ip_smem(const sl_plan *p, int rg, int kg);
 // Multi-sky spin Legendre step on the tensor cores (k_multisky.cu), FP32 plans.
 sl_status launch_lcontract_mma(sl_plan *p, int nsky, const double *sky, const double *beam, float2 *sky32,
                                float2 *G, int *err);
