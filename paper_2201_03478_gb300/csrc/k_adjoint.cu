@@ -49,7 +49,33 @@ struct AdjSmem {
     double dots[kLCA][8];
     double2 rc[kLCA];              // a', b'
     double cl[kLCA];               // c_l
+    int qlo[2][kLCA];              // [sign][l - c0]: first pair whose y is nonzero at l (or later)
 };
+
+
+// Pairs below qlo[sign][i] have y = 0 at l = c0 + i (their recurrence starts
+// later; the evanescent zone), so the dot products of that l start there: the
+// skipped terms are exact zeros and the sums are unchanged.  Each thread enters
+// its first nonzero l of the chunk; warp 0 turns the entries into prefix minima.
+__device__ __forceinline__ void adj_qlo_mark(int (*qlo)[kLCA], bool active, int ls, int c0, int nc, int neg,
+                                             int lp) {
+    if (active && ls < c0 + nc) atomicMin(&qlo[neg][max(0, ls - c0)], lp);
+}
+__device__ __forceinline__ void adj_qlo_scan(int (*qlo)[kLCA]) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+#pragma unroll
+        for (int sg = 0; sg < 2; ++sg) {
+            int v = qlo[sg][lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v = min(v, t);
+            }
+            qlo[sg][lane] = v;
+        }
+    }
+}
 
 __global__ void __launch_bounds__(kNTA) k_lcontract_adj(const LcAdjArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -130,7 +156,9 @@ __global__ void __launch_bounds__(kNTA) k_lcontract_adj(const LcAdjArgs a) {
             rc[threadIdx.x] = make_double2(t.a, t.b);
             cl[threadIdx.x] = t.c;
         }
+        if (threadIdx.x < 2 * kLCA) S.qlo[threadIdx.x / kLCA][threadIdx.x % kLCA] = kPA;
         __syncthreads();
+        adj_qlo_mark(S.qlo, active, ls, c0, nc, neg, lp);
         // phase 1: recurrence values of this (pair, sign) for the chunk
         for (int i = 0; i < nc; ++i) {
             const int l = c0 + i;
@@ -146,13 +174,15 @@ __global__ void __launch_bounds__(kNTA) k_lcontract_adj(const LcAdjArgs a) {
         }
         for (int i = nc; i < kLCA; ++i) W[i][neg][lp] = 0.0;
         __syncthreads();
-        // phase 2: dot product (dl, dq) over the CTA's pairs
+        adj_qlo_scan(S.qlo);
+        __syncthreads();
+        // phase 2: dot product (dl, dq) over the CTA's pairs with a nonzero y
         {
             const double *wr = W[dl][wsg];
             const double *gr = Gv[dq];
             double s0 = 0.0, s1 = 0.0;
 #pragma unroll 8
-            for (int q = 0; q < kPA; q += 2) {
+            for (int q = S.qlo[wsg][dl] & ~1; q < kPA; q += 2) {
                 s0 = fma(wr[q], gr[q], s0);
                 s1 = fma(wr[q + 1], gr[q + 1], s1);
             }
@@ -186,6 +216,7 @@ struct AdjSmemDF {
     double dots[kLCA][8];
     float4 rc[kLCA];               // a', b' as double-float
     double cl[kLCA];
+    int qlo[2][kLCA];
 };
 
 __global__ void __launch_bounds__(kNTA) k_lcontract_adj_df(const LcAdjArgs a) {
@@ -261,7 +292,9 @@ __global__ void __launch_bounds__(kNTA) k_lcontract_adj_df(const LcAdjArgs a) {
             S.rc[threadIdx.x] = make_float4(ra.h, ra.l, rb.h, rb.l);
             S.cl[threadIdx.x] = t.c;
         }
+        if (threadIdx.x < 2 * kLCA) S.qlo[threadIdx.x / kLCA][threadIdx.x % kLCA] = kPA;
         __syncthreads();
+        adj_qlo_mark(S.qlo, active, ls, c0, nc, neg, lp);
         for (int i = 0; i < nc; ++i) {
             const int l = c0 + i;
             float2 v = make_float2(0.f, 0.f);
@@ -277,6 +310,8 @@ __global__ void __launch_bounds__(kNTA) k_lcontract_adj_df(const LcAdjArgs a) {
         }
         for (int i = nc; i < kLCA; ++i) S.W[i][neg][lp] = make_float2(0.f, 0.f);
         __syncthreads();
+        adj_qlo_scan(S.qlo);
+        __syncthreads();
         {
             const float2 *wr = S.W[dl][wsg];
             const float2 *gr = S.Gv[dq];
@@ -284,7 +319,7 @@ __global__ void __launch_bounds__(kNTA) k_lcontract_adj_df(const LcAdjArgs a) {
             dacc_zero(s0);
             dacc_zero(s1);
 #pragma unroll 4
-            for (int q = 0; q < kPA; q += 2) {
+            for (int q = S.qlo[wsg][dl] & ~1; q < kPA; q += 2) {
                 const float2 w0 = wr[q], g0 = gr[q], w1 = wr[q + 1], g1 = gr[q + 1];
                 dacc_mac(s0, dfl{w0.x, w0.y}, dfl{g0.x, g0.y});
                 dacc_mac(s1, dfl{w1.x, w1.y}, dfl{g1.x, g1.y});
