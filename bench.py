@@ -452,10 +452,13 @@ def detectors_arm(args):
             sl.synth_spin_maps(it["plan"], it["sky"], it["beam"], it["maps"])
             sl.interp_tod(it["plan"], it["maps"], it["theta"], it["phi"], it["psi"], it["tod"])
 
-    def timed(fn):
+    def timed(fn, stats_on=False):
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
+        if stats_on:   # the plan's kernel timers cover the timed calls only
+            plan.enable_timing(True)
+            plan.kernel_stats(reset=True)
         e0.record(stream)
         for _ in range(args.steps):
             fn()
@@ -534,10 +537,13 @@ def multisky_arm(args):
     stream = torch.cuda.current_stream(device)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def timed(fn):
+    def timed(fn, stats_on=False):
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
+        if stats_on:   # the plan's kernel timers cover the timed calls only
+            plan.enable_timing(True)
+            plan.kernel_stats(reset=True)
         e0.record(stream)
         for _ in range(args.steps):
             fn()
@@ -550,12 +556,10 @@ def multisky_arm(args):
             sl.synth_spin_maps(plan, skies[s], beam, one)
 
     ms_single = timed(singles)
-    plan.enable_timing(True)
-    plan.kernel_stats(reset=True)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    ms_multi = timed(lambda: sl.synth_spin_maps_multi(plan, skies, beam, maps))
+    ms_multi = timed(lambda: sl.synth_spin_maps_multi(plan, skies, beam, maps), stats_on=True)
     clk = clocks.stop()
     stats = plan.kernel_stats(reset=True)
     plan.enable_timing(False)
@@ -593,6 +597,17 @@ def multisky_arm(args):
         "gpu_launches": int(sum(v[0] for v in stats.values()) / args.steps),
         "clocks": clk,
     }
+    if mma_ms > 0:
+        # dominant kernel against the TF32 tensor peak: the executed TF32 work (three
+        # products per FP32 product) and, beside it, the FP32-equivalent algorithmic rate
+        ach = mma_flops / (mma_ms / 1e3) / 1e12
+        out["roofline"] = {"bound": "tensor", "kernel": "lcontract_mma", "achieved": round(ach, 3),
+                           "peak": round(PEAK_TF32_TFLOPS, 1), "unit": "TFLOP/s",
+                           "frac": round(ach / PEAK_TF32_TFLOPS, 4), "traffic": None, "avg_ms": round(mma_ms, 4),
+                           "algorithmic_fp32_tflops": round(ach / 3, 3),
+                           "peak_note": "measured bf16 burst x nominal TF32/BF16 ratio (of measured); achieved "
+                                        "counts 3 TF32 products x 2 flops per visited (ring pair, m, k, sign, l) "
+                                        "step and column"}
     sl.plan_destroy(plan)
     print(json.dumps(out), flush=True)
 

@@ -169,6 +169,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 //              12 MMAs of the chunk, commits them to empty[b];
 // the producers wait on empty[b] before refilling buffer b.  After the last
 // chunk the W warps wait for its commit and read the accumulator.
+// NC = T/E/B components per sky (1 or 3), a compile-time count so that the V
+// producers' component loops unroll and the four skies of a unit interleave.
+template <int NC>
 __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
                                                                   const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ unsigned char ms_raw[];
@@ -176,6 +179,7 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
     __shared__ __align__(8) uint64_t stg_bar[4][kMsNS];    // TMA arrivals of each V warp's staging slots
     __shared__ uint32_t tmem_base;
     __shared__ int s_lmin, s_fail;
+    __shared__ float2 wcoef[4][kMsLC];                      // per W warp: (a, c+ or c-) of the chunk's l
     volatile int *fail = &s_fail;   // set by any role whose bounded wait ran out
 
     int b = blockIdx.x;
@@ -250,32 +254,51 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
 
     if (warp < 4) {
         // ---------------------------------------------------------------- W producers
-        // this warp's lane i holds the coefficients of l = c0 + i (prefetched one chunk ahead)
-        RTab32 tcur = {0.f, 0.f, 0.f, 0.f}, tnext = {0.f, 0.f, 0.f, 0.f};
+        // this warp's lane i holds the coefficients of l = c0 + i (prefetched two chunks ahead)
+        RTab32 tcur = {0.f, 0.f, 0.f, 0.f}, tnext = {0.f, 0.f, 0.f, 0.f}, tnext2 = {0.f, 0.f, 0.f, 0.f};
         if (lstart + lane <= a.L) tcur = tab[lstart + lane];
+        if (lstart + kMsLC + lane <= a.L) tnext = tab[lstart + kMsLC + lane];
         for (int c = 0; c < nchunks; ++c) {
             const int bi = c % kMsNB;
             const int c0 = lstart + c * kMsLC;
-            if (c + 1 < nchunks && c0 + kMsLC + lane <= a.L) tnext = tab[c0 + kMsLC + lane];
+            if (c + 2 < nchunks && c0 + 2 * kMsLC + lane <= a.L) tnext2 = tab[c0 + 2 * kMsLC + lane];
             if (c >= kMsNB && !mbar_wait(smem_u32(&empty[bi]), ((c - kMsNB) / kMsNB) & 1)) *fail = 1;
             if (*fail) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // the chunk's coefficients, broadcast through shared memory (one load per step)
+            __syncwarp();
+            wcoef[warp][lane] = make_float2(tcur.a, neg ? tcur.cm : tcur.cp);
+            __syncwarp();
             uint32_t hv[kMsLC], lv[kMsLC];
+            if (__all_sync(0xffffffffu, c0 >= ls && c0 + kMsLC - 1 <= a.L)) {
+                // every lane's recurrence runs through the whole chunk: no range tests
 #pragma unroll
-            for (int i = 0; i < kMsLC; ++i) {
-                const int l = c0 + i;
-                const float ta = __shfl_sync(0xffffffffu, tcur.a, i);
-                const float tc = __shfl_sync(0xffffffffu, neg ? tcur.cm : tcur.cp, i);
-                float v = 0.f;
-                if (l >= ls && l <= a.L) {
-                    v = y;
-                    D = fmaf(fmaf(-ta, yc, tc), y, D);
+                for (int i = 0; i < kMsLC; ++i) {
+                    const float2 t = wcoef[warp][i];
+                    const float v = y;
+                    D = fmaf(fmaf(-t.x, yc, t.y), y, D);
                     y += D;
+                    float h, lo;
+                    tf32_split(v, h, lo);
+                    hv[i] = __float_as_uint(h);
+                    lv[i] = __float_as_uint(lo);
                 }
-                float h, lo;
-                tf32_split(v, h, lo);
-                hv[i] = __float_as_uint(h);
-                lv[i] = __float_as_uint(lo);
+            } else {
+#pragma unroll
+                for (int i = 0; i < kMsLC; ++i) {
+                    const int l = c0 + i;
+                    const float2 t = wcoef[warp][i];
+                    float v = 0.f;
+                    if (l >= ls && l <= a.L) {
+                        v = y;
+                        D = fmaf(fmaf(-t.x, yc, t.y), y, D);
+                        y += D;
+                    }
+                    float h, lo;
+                    tf32_split(v, h, lo);
+                    hv[i] = __float_as_uint(h);
+                    lv[i] = __float_as_uint(lo);
+                }
             }
             const uint32_t arow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kMsAcol + bi * 64);
             asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
@@ -300,6 +323,7 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(smem_u32(&full_a[bi]));
             tcur = tnext;
+            tnext = tnext2;
         }
     } else if (warp < 8) {
         // ---------------------------------------------------------------- V producers
@@ -311,12 +335,20 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
         const float2 *beam_k = a.beam + (int64_t)k * (a.L + 1);
         const int lmin = max(m, k);
         const int i = lane, ch = i >> 2, lo4 = i & 3;
+        // this lane's float offset in row q of the 4 rows of one sky, for an even (h = 0) or
+        // odd (h = 1) sky of a multiple-of-4 group: the 16-byte chunk ch of a 128-byte row
+        // sits at chunk ch ^ (row & 7), and row & 7 = 4 h + q
+        int swz_off[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) swz_off[h][q] = q * 32 + ((ch ^ (4 * h + q)) << 2) + lo4;
         const int npass = (a.nsg + 15) >> 4, nunits = nchunks * npass;
         // this warp's passes j < na hold skies (4 vw + 16 j < nsg); its staged units are
         // numbered ui = c na + j, slot ui mod 3, and issued two units ahead
         const int na = min(npass, max(0, (a.nsg - 4 * vw + 15) >> 4)), nact = nchunks * na;
         float *stage = base + 2 * kMsNB * bfl + vw * kMsNS * kMsStageF;
-        const uint32_t tx_bytes = (uint32_t)(kMsBoxX * a.ncomp * 4 * sizeof(float));
+        const uint32_t tx_bytes = (uint32_t)(kMsBoxX * NC * 4 * sizeof(float));
         auto issue = [&](int ui) {
             if (lane != 0 || ui >= nact) return;
             const int c = ui / na, j = ui - c * na, s0 = 4 * vw + 16 * j;
@@ -334,24 +366,25 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
         };
         issue(0);
         issue(1);
-        // beam and c_l of the next chunk are prefetched into registers
-        float2 bn[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        float cn = 0.f;
-        auto beam_of = [&](int c) {
+        // beam and c_l of the next two chunks are prefetched into registers
+        float2 bn[3], bn2[3];
+        float cn, cn2;
+        auto beam_of = [&](int c, float2 *bo, float &co) {
             const int l = lstart + c * kMsLC + i;
-            bn[0] = bn[1] = bn[2] = make_float2(0.f, 0.f);
-            cn = 0.f;
+            bo[0] = bo[1] = bo[2] = make_float2(0.f, 0.f);
+            co = 0.f;
             if (c < nchunks && l <= a.L && l >= lmin) {
 #pragma unroll
                 for (int X = 0; X < 3; ++X)
-                    if (X < a.ncomp) {
-                        bn[X] = __ldg(beam_k + (int64_t)X * (a.K + 1) * (a.L + 1) + l);
-                        if (k == 0) bn[X].y = 0.f;
+                    if (X < NC) {
+                        bo[X] = __ldg(beam_k + (int64_t)X * (a.K + 1) * (a.L + 1) + l);
+                        if (k == 0) bo[X].y = 0.f;
                     }
-                cn = __ldg(&tab[l].c);
+                co = __ldg(&tab[l].c);
             }
         };
-        beam_of(0);
+        beam_of(0, bn, cn);
+        beam_of(1, bn2, cn2);
         float2 bv[3];
         float cl = 0.f, sc = 0.f;
         int ui_done = 0;                  // staged units consumed
@@ -360,10 +393,14 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
             if (j == 0) {
                 const int l = lstart + c * kMsLC + i;
 #pragma unroll
-                for (int X = 0; X < 3; ++X) bv[X] = bn[X];
+                for (int X = 0; X < 3; ++X) {
+                    bv[X] = bn[X];
+                    bn[X] = bn2[X];
+                }
                 cl = cn;
+                cn = cn2;
                 sc = (l & 1) ? -cl : cl;
-                beam_of(c + 1);
+                beam_of(c + 2, bn2, cn2);
                 if (c >= kMsNB && !mbar_wait(smem_u32(&empty[bi]), ((c - kMsNB) / kMsNB) & 1)) *fail = 1;
             }
             if (*fail) break;
@@ -373,7 +410,7 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
                 issue(ui + 2);
                 if (!mbar_wait(smem_u32(&stg_bar[vw][ui % kMsNS]), (ui / kMsNS) & 1)) *fail = 1;
                 if (*fail) break;
-                float *Bh = base + bi * 2 * bfl, *Bl = Bh + bfl;
+                float *Bh = base + bi * 2 * bfl + 128 * s0, *Bl = Bh + bfl;
                 // this lane's l sits at float2 (x0 & 1) + lane of each staged row
                 const int64_t x0 = moff + lstart + (int64_t)c * kMsLC;
                 const float *src = stage + (ui % kMsNS) * kMsStageF + 2 * ((int)(x0 & 1) + i);
@@ -383,8 +420,8 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
                     float2 ap = {0.f, 0.f}, am = {0.f, 0.f};
 #pragma unroll
                     for (int X = 0; X < 3; ++X) {
-                        if (X >= a.ncomp) break;
-                        float2 s2 = *reinterpret_cast<const float2 *>(src + (t * a.ncomp + X) * kMsBoxX);
+                        if (X >= NC) break;
+                        float2 s2 = *reinterpret_cast<const float2 *>(src + (t * NC + X) * kMsBoxX);
                         if (m == 0) s2.y = 0.f;
                         const float2 b2 = bv[X];
                         ap.x += s2.x * b2.x + s2.y * b2.y;      // s conj(b)
@@ -396,7 +433,8 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
                     const float vv[4] = {cl * p1.x, cl * p1.y, sc * p2.x, sc * p2.y};
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int row = 4 * s + q, off = row * 32 + ((ch ^ (row & 7)) << 2) + lo4;
+                        // row 4 s + q; s0 is a multiple of 4, so (row & 7) = 4 (t & 1) + q
+                        const int off = 128 * t + swz_off[t & 1][q];
                         float h, lo;
                         tf32_split(vv[q], h, lo);
                         Bh[off] = h;
@@ -588,10 +626,11 @@ sl_status launch_lcontract_mma(sl_plan *p, int nsky, const double *sky, const do
     const int64_t nblk = (int64_t)(p->L + 1) * (p->K + 1) * 2 * a.nrc * a.ngroups;
     if (nblk > 0x7fffffff) return set_error(SL_ERR_UNSUPPORTED, "grid too large");
     const size_t sm = lcontract_mma_smem(a.nsg, a.ncomp);
-    cudaError_t e = cudaFuncSetAttribute(k_lcontract_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    void (*kern)(const MsArgs, const CUtensorMap) = a.ncomp == 1 ? k_lcontract_mma<1> : k_lcontract_mma<3>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return cuda_check(e, "k_lcontract_mma smem attribute");
     const int slot = timing_begin(p, "lcontract_mma");
-    k_lcontract_mma<<<(unsigned)nblk, kMsThreads, sm, p->stream>>>(a, tmap);
+    kern<<<(unsigned)nblk, kMsThreads, sm, p->stream>>>(a, tmap);
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_lcontract_mma launch");
 }
