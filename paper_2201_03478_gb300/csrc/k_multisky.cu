@@ -385,21 +385,25 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
         };
         beam_of(0, bn, cn);
         beam_of(1, bn2, cn2);
-        float2 bv[3];
-        float cl = 0.f, sc = 0.f;
+        float bxc[3], byc[3], bxs[3], bys[3], par = 1.f;
         int ui_done = 0;                  // staged units consumed
         for (int u = 0; u < nunits; ++u) {
             const int c = u / npass, j = u - c * npass, bi = c % kMsNB, s0 = 4 * vw + 16 * j;
             if (j == 0) {
                 const int l = lstart + c * kMsLC + i;
+                // this lane's beam factors for the chunk (c_l folded in; sigma = sign of k
+                // and the m = 0 rule -- Im s ignored -- folded into the factors of Im s)
+                const float cl = cn, sg = neg ? -cl : cl, sy = (m == 0) ? 0.f : sg;
 #pragma unroll
                 for (int X = 0; X < 3; ++X) {
-                    bv[X] = bn[X];
+                    bxc[X] = cl * bn[X].x;
+                    byc[X] = cl * bn[X].y;
+                    bxs[X] = sy * bn[X].x;
+                    bys[X] = sy * bn[X].y;
                     bn[X] = bn2[X];
                 }
-                cl = cn;
+                par = (l & 1) ? -1.f : 1.f;
                 cn = cn2;
-                sc = (l & 1) ? -cl : cl;
                 beam_of(c + 2, bn2, cn2);
                 if (c >= kMsNB && !mbar_wait(smem_u32(&empty[bi]), ((c - kMsNB) / kMsNB) & 1)) *fail = 1;
             }
@@ -416,21 +420,22 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
                 const float *src = stage + (ui % kMsNS) * kMsStageF + 2 * ((int)(x0 & 1) + i);
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const int s = s0 + t;
-                    float2 ap = {0.f, 0.f}, am = {0.f, 0.f};
+                    // with A+ = sum_X s conj(b) and A- = sum_X conj(s) conj(b), the four
+                    // columns are c (p1.x, p1.y), (-1)^l c (p2.x, p2.y), (p1, p2) = (A+, A-)
+                    // for +k and (A-, A+) for -k:
+                    //   c p1 = (xa + ys, yx - xb),  c p2 = (xa - ys, -(yx + xb))
+                    // xa = sum s.x c b.x, xb = sum s.x c b.y, ys = sum s.y sigma c b.y,
+                    // yx = sum s.y sigma c b.x
+                    float xa = 0.f, xb = 0.f, ys = 0.f, yx = 0.f;
 #pragma unroll
-                    for (int X = 0; X < 3; ++X) {
-                        if (X >= NC) break;
-                        float2 s2 = *reinterpret_cast<const float2 *>(src + (t * NC + X) * kMsBoxX);
-                        if (m == 0) s2.y = 0.f;
-                        const float2 b2 = bv[X];
-                        ap.x += s2.x * b2.x + s2.y * b2.y;      // s conj(b)
-                        ap.y += s2.y * b2.x - s2.x * b2.y;
-                        am.x += s2.x * b2.x - s2.y * b2.y;      // conj(s) conj(b)
-                        am.y -= s2.y * b2.x + s2.x * b2.y;
+                    for (int X = 0; X < NC; ++X) {
+                        const float2 s2 = *reinterpret_cast<const float2 *>(src + (t * NC + X) * kMsBoxX);
+                        xa = fmaf(s2.x, bxc[X], xa);
+                        xb = fmaf(s2.x, byc[X], xb);
+                        ys = fmaf(s2.y, bys[X], ys);
+                        yx = fmaf(s2.y, bxs[X], yx);
                     }
-                    const float2 p1 = neg ? am : ap, p2 = neg ? ap : am;
-                    const float vv[4] = {cl * p1.x, cl * p1.y, sc * p2.x, sc * p2.y};
+                    const float vv[4] = {xa + ys, yx - xb, par * (xa - ys), -par * (yx + xb)};
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         // row 4 s + q; s0 is a multiple of 4, so (row & 7) = 4 (t & 1) + q
