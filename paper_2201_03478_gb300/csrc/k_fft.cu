@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(256) k_ringfft_synth_cl(int L, int K, int R, i
     const int S = N / nc;
     DistBuf<C> b0{reinterpret_cast<C *>(smem_raw), S, (S & (S - 1)) == 0 ? __ffs(S) - 1 : -1};
     DistBuf<C> b1{b0.local + S, S, b0.lgS};
-    // cluster index -> (ring, k), rings of a sector together as in k_ringfft_synth
+    // cluster index -> (ring, k): kRingGroup consecutive rings fastest (they share the sectors of G)
     int b = blockIdx.x / nc;
     const int rlo = b % kRingGroup;
     b /= kRingGroup;
