@@ -343,14 +343,15 @@ def gpu_arm(args):
         gs = torch.zeros_like(sky)
         gb = torch.zeros_like(beam)
         y = tod.clone()
-        sl.adjoint_tod(plan, theta, phi, psi, y, sky, beam, gs, gb)          # warm (allocates scratch)
+        sl.adjoint_tod_sharded(plan, theta, phi, psi, y, sky, beam, gs, gb)  # warm (allocates scratch)
         torch.cuda.synchronize()
         plan.enable_timing(True)
         plan.kernel_stats(reset=True)
         barrier(device)
         e0.record(stream)
         for _ in range(args.adjoint_steps):
-            sl.adjoint_tod(plan, theta, phi, psi, y, sky, beam, gs, gb)
+            # each rank's stretch of the scan; the gradients summed over ranks (one all-reduce)
+            sl.adjoint_tod_sharded(plan, theta, phi, psi, y, sky, beam, gs, gb)
         e1.record(stream)
         torch.cuda.synchronize()
         ms_adj = reduce_max(e0.elapsed_time(e1), device) / args.adjoint_steps

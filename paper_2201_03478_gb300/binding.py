@@ -281,6 +281,21 @@ def adjoint_tod(plan: Plan, theta, phi, psi, tod, sky, beam, sky_grad=None, beam
     return sky_grad, beam_grad
 
 
+def adjoint_tod_sharded(plan: Plan, theta, phi, psi, tod, sky, beam, sky_grad=None, beam_grad=None,
+                        group=None):
+    """Adjoint of a TOD whose samples are split over the ranks of a process group
+    (every rank holds the whole cube and its own stretch of pointings; the TOD is
+    linear in the cube, Sect. 2.1): the local adjoint_tod, then one sum all-reduce
+    of each gradient, so that every rank holds the gradients of the whole TOD.
+    Without an initialised process group, or with one rank, it is adjoint_tod."""
+    import torch.distributed as dist
+    gs, gb = adjoint_tod(plan, theta, phi, psi, tod, sky, beam, sky_grad, beam_grad)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
+        for g in (gs, gb):
+            dist.all_reduce(torch.view_as_real(g), op=dist.ReduceOp.SUM, group=group)
+    return gs, gb
+
+
 def adjoint_interp(plan: Plan, theta, phi, psi, tod, maps_bar=None):
     """Transpose of interp_tod: the adjoint cube [R, nphi, K+1] complex128."""
     n = _ptg(plan, theta, phi, psi)
