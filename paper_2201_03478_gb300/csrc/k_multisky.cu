@@ -17,16 +17,20 @@
 //   * W and V are split into TF32 high and low parts and multiplied as
 //     hi x hi + hi x lo + lo x hi (three MMAs, FP32 accumulation in tensor
 //     memory): ~2^-21 relative per product, the accuracy of the FP32 path;
-//   * W lives in tensor memory: the thread that owns ring pair r runs its
-//     recurrence and writes its row (TMEM lane r) with tcgen05.st; V lives in
-//     shared memory, K-major with the 128-byte swizzle, built by all warps
-//     from coalesced sky and beam loads; both double buffered, so that while
-//     the MMAs of one chunk run the CTA builds the next chunk; the chunk's
-//     recurrence coefficients are staged by cp.async one chunk ahead;
-//   * 256 TMEM columns and 33 KB of shared memory per CTA: two CTAs per SM;
+//   * W lives in tensor memory: four producer warps, the thread that owns ring
+//     pair r runs its recurrence and writes its row (TMEM lane r) with
+//     tcgen05.st, the chunk's coefficients broadcast through shared memory;
+//     V lives in shared memory, K-major with the 128-byte swizzle, built by
+//     four other producer warps from sky rows brought in by TMA tensor loads
+//     and per-chunk beam factors; both double buffered, so that while the MMAs
+//     of one chunk run the producers build the next chunk;
+//   * 256 TMEM columns and 105 KB of shared memory per CTA at 32 skies (B
+//     buffers 64 KB, staging 39 KB): two CTAs per SM;
 //   * one thread issues the MMAs and commits them to an mbarrier per buffer;
 //     every wait is bounded and sets an error flag (the CTA then stops,
 //     waits for its MMAs with a bound and frees its tensor memory).
+// The V producers bind the kernel (the MMA thread waits on them, the W warps
+// wait on the MMAs); their work per sky and l is four FMAs per component.
 #include <algorithm>
 
 #include <cuda.h>
