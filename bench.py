@@ -616,12 +616,12 @@ def multisky_arm(args):
 # ncu-measured DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
 # at full size for the current kernels (profiles/launches_lfi_*.txt).
 TRAFFIC = {
-    ("lcontract_f64", "fp64"): 674.3e6 + 516.6e6,
-    ("interp_f64", "fp64"): 14801.9e6 + 1807.3e6,
-    ("lcontract_f32", "fp32"): 370.5e6 + 231.3e6,
-    ("interp_f32", "fp32"): 7332.9e6 + 2042.3e6,
-    ("lcontract_df", "df64"): 672.8e6 + 511.4e6,
-    ("interp_df", "df64"): 22844.9e6 + 2732.1e6,
+    ("lcontract_f64", "fp64"): 674.3e6 + 516.7e6,
+    ("interp_f64", "fp64"): 14807.3e6 + 1833.3e6,
+    ("lcontract_f32", "fp32"): 370.8e6 + 231.1e6,
+    ("interp_f32", "fp32"): 7309.0e6 + 2037.7e6,
+    ("lcontract_df", "df64"): 672.3e6 + 511.4e6,
+    ("interp_df", "df64"): 22960.7e6 + 2737.6e6,
 }
 
 
