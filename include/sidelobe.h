@@ -383,7 +383,8 @@ void sl_batch_destroy(sl_batch *batch);
 
 /* Bounds-checked builds (the library compiled with -DSL_CHECKED): every data-
  * dependent gather and scatter index of the binning, scatter, interpolation
- * (forward and adjoint, all precisions), psi-grid and orbital kernels is tested
+ * (forward and adjoint, all precisions), psi-grid, orbital and ring-FFT
+ * (its digit-reversal tables) kernels is tested
  * before the access; a failed test skips the access and records a site code.
  * Returns the code of a recorded failure since the last call (0: none) and
  * clears the record; synchronises the device.  Ordinary builds: always 0. */

@@ -252,7 +252,8 @@ __global__ void __launch_bounds__(256) k_ringfft_synth_ip(int L, int K, int R, i
     for (int u = threadIdx.x; u < total; u += blockDim.x) {
         const int ri = u % RG, ki = (u / RG) % KG, sl = u / TT;
         const int k = k0 + ki, r = r0 + ri;
-        const int q = __ldg(slotq + sl);
+        int q = __ldg(slotq + sl);
+        if (!SL_GUARD(q >= 0 && q < N, 0x601u)) q = 0;
         const int m = q - N * (p2n ? (q + L) >> lgn : (q + L) / N);   // smallest m >= -L, m = q (mod N)
         const bool ok = k <= K && r < R && m <= L;
         const C *src = ok ? G + ((int64_t)k * (2 * L + 1) + (m + L)) * R + r : G;
@@ -277,7 +278,9 @@ __global__ void __launch_bounds__(256) k_ringfft_synth_ip(int L, int K, int R, i
         C acc = mk<C>(0.0, 0.0);
         for (int m = m0; m <= L; m += N) acc = add(acc, G[((int64_t)k * (2 * L + 1) + (m + L)) * R + r]);
         const int q = ((m0 % N) + N) % N;   // m0 < 0 when L > N
-        C *d = x + S::at(__ldg(qslot + q)) * TT + ri * KG + ki;
+        int sq = __ldg(qslot + q);
+        if (!SL_GUARD(sq >= 0 && sq < N, 0x602u)) continue;
+        C *d = x + S::at(sq) * TT + ri * KG + ki;
         *d = add(*d, acc);
     }
     __syncthreads();
@@ -469,6 +472,8 @@ static Radices radices_of(const sl_plan *p) {
     for (int i = 0; i < p->nradix; ++i) r.code |= (unsigned long long)p->radices[i] << (3 * i);
     return r;
 }
+
+SL_CHECK_READER(chk_fft)
 
 // The synthesis runs in place (one buffer of nphi values per transform): one CTA
 // while a single transform fits, else the two-buffer cluster form.

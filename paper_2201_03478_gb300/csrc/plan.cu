@@ -992,7 +992,7 @@ sl_status interp_tod_psi(sl_plan *p, const void *cube_psi, int npsi, const doubl
 
 unsigned sl_debug_check_status(void) {
     // every unit's word is read (and cleared); the first nonzero one is reported
-    const unsigned w[5] = {chk_sort(), chk_interp(), chk_interp_df(), chk_psigrid(), chk_orbital()};
+    const unsigned w[6] = {chk_sort(), chk_interp(), chk_interp_df(), chk_psigrid(), chk_orbital(), chk_fft()};
     for (unsigned v : w)
         if (v) return v;
     return 0u;

@@ -93,6 +93,7 @@ unsigned chk_interp();
 unsigned chk_interp_df();
 unsigned chk_psigrid();
 unsigned chk_orbital();
+unsigned chk_fft();
 
 // p-point Lagrange weights (separable interpolation, any even p).  theta:
 // nodes at offsets o[a] from the first stencil row (o[0] = 0), 1/prod(o_a - o_b)
