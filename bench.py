@@ -213,6 +213,8 @@ def gpu_arm(args):
     plan = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=ncomp, precision=args.precision, device=local)
     if args.tile_cols:
         plan.set_tile_cols(args.tile_cols)
+    if args.fft_tile:
+        plan.set_fft_tile(*(int(v) for v in args.fft_tile.split(",")))
     maps = torch.empty(plan.maps_shape(), dtype=plan.maps_dtype, device=device)
     tod = torch.empty(n, dtype=torch.float64, device=device)
 
@@ -325,6 +327,7 @@ def gpu_arm(args):
         "config": {"workload": workload,
                    "lmax": L, "kmax": K, "ncomp": ncomp, "nrings": R, "nphi": nphi, "interp_order": 4,
                    "tile_cols": plan.sizes()["tile_cols"],
+                   "fft_tile": [plan.sizes()["fft_rings"], plan.sizes()["fft_korders"]],
                    "samples_per_gpu": n, "precision": prec, "parallelism": "replicated cube, sharded TOD",
                    "l2": "inputs larger than L2 (pointings %.1f GB, cube %.2f GB)" % (24 * n / 1e9,
                                                                                        plan.sizes()["maps_bytes"] / 1e9)},
@@ -1153,6 +1156,7 @@ def main(argv=None):
     ap.add_argument("--sweep-max", type=int, default=8192, help="largest lmax of the sweep workload")
     ap.add_argument("--sweep-precisions", default="fp64,fp32,df64", help="plans of the sweep workload")
     ap.add_argument("--tile-cols", type=int, default=0, help="sort-tile width (8, 16, 32; 0: the plan's default)")
+    ap.add_argument("--fft-tile", default="", help="rings,korders per CTA of the ring FFT (e.g. 2,1; default: the plan's)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--n", type=float, default=0, help="pointings per GPU (default 1e8; 2e8 for highres)")
     ap.add_argument("--e2e-steps", type=int, default=3)
