@@ -131,7 +131,8 @@ sl_status synth_spin_maps(sl_plan *plan, const double *sky, const double *beam, 
  * l-contraction of all skies runs per (m, k) as one tensor-core tile product
  * (tcgen05; the rescaled Wigner values and the sky x beam columns are split
  * into TF32 high and low parts, three products, FP32 accumulation in tensor
- * memory), with the accuracy of the FP32 path.
+ * memory), with the accuracy of the FP32 path.  nsky in [1, 65535] (larger:
+ * SL_ERR_UNSUPPORTED; call once per group of skies).
  *   sky  : device double [nsky][ncomp][nalm][2], the packing above per sky;
  *   beam : device, the packing above (shared by every sky);
  *   maps : device float2 [nsky][nrings][nphi][kmax+1], fully overwritten.

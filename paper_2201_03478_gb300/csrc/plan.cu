@@ -762,6 +762,8 @@ sl_status synth_spin_maps_multi(sl_plan *p, int nsky, const double *sky, const d
     if (!plan_fp32(p->precision))
         return set_error(SL_ERR_UNSUPPORTED, "synth_spin_maps_multi: FP32 plans only (the tensor-core path)");
     if (nsky < 1) return set_error(SL_ERR_ARG, "synth_spin_maps_multi: nsky=%d < 1", nsky);
+    if (nsky > 65535)   // the ring FFT runs one grid row per sky
+        return set_error(SL_ERR_UNSUPPORTED, "synth_spin_maps_multi: nsky=%d > 65535", nsky);
     if (!sky || !beam || !maps) return set_error(SL_ERR_ARG, "synth_spin_maps_multi: NULL buffer");
     if (nsky > p->msky_cap) {
         if (p->batch_refs > 0) return set_error(SL_ERR_ARG, "synth_spin_maps_multi: the plan is held by a batch graph");

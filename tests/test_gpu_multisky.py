@@ -63,6 +63,14 @@ def test_multisky_rejects_fp64_plans():
     from paper_2201_03478_gb300 import _lib
     st = _lib.load().synth_spin_maps_multi(plan.ptr, 2, sky.data_ptr(), beam.data_ptr(), sky.data_ptr())
     assert st == -2
+    sl.plan_destroy(plan)
+    # more skies than the ring FFT's grid rows: refused before any buffer is touched
+    plan = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=1, precision="fp32")
+    st = _lib.load().synth_spin_maps_multi(plan.ptr, 65536, sky.data_ptr(), beam.data_ptr(), sky.data_ptr())
+    assert st == -2
+    st = _lib.load().synth_spin_maps_multi(plan.ptr, 0, sky.data_ptr(), beam.data_ptr(), sky.data_ptr())
+    assert st == -1
+    sl.plan_destroy(plan)
 
 
 def test_bounded_wait_expires_and_is_reported():
