@@ -173,6 +173,54 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 //              12 MMAs of the chunk, commits them to empty[b];
 // the producers wait on empty[b] before refilling buffer b.  After the last
 // chunk the W warps wait for its commit and read the accumulator.
+// One work unit of the sky x beam columns: 4 skies (staged rows at src, this lane's l)
+// into rows 4 s + q of the K-major swizzled B buffer (Bh, Bl: TF32 high and low parts).
+// With A+ = sum_X s conj(b) and A- = sum_X conj(s) conj(b), the four columns are
+// c (p1.x, p1.y), (-1)^l c (p2.x, p2.y), (p1, p2) = (A+, A-) for +k and (A-, A+) for -k:
+//   c p1 = (xa + ys, yx - xb),  c p2 = (xa - ys, -(yx + xb)),
+// xa = sum s.x c b.x, xb = sum s.x c b.y, ys = sum s.y sigma c b.y, yx = sum s.y sigma c b.x
+// (the factors b* carry c_l, sigma = sign of k and the m = 0 rule).
+template <int NC>
+__device__ __forceinline__ void ms_build_unit(const float *src, float *Bh, float *Bl, const float *bxc,
+                                              const float *byc, const float *bxs, const float *bys, float par,
+                                              const int (&swz_off)[2][4]) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        float xa = 0.f, xb = 0.f, ys = 0.f, yx = 0.f;
+#pragma unroll
+        for (int X = 0; X < NC; ++X) {
+            const float2 s2 = *reinterpret_cast<const float2 *>(src + (t * NC + X) * kMsBoxX);
+            xa = fmaf(s2.x, bxc[X], xa);
+            xb = fmaf(s2.x, byc[X], xb);
+            ys = fmaf(s2.y, bys[X], ys);
+            yx = fmaf(s2.y, bxs[X], yx);
+        }
+        const float vv[4] = {xa + ys, yx - xb, par * (xa - ys), -par * (yx + xb)};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // row 4 s + q; the group's first sky is a multiple of 4, so (row & 7) = 4 (t & 1) + q
+            const int off = 128 * t + swz_off[t & 1][q];
+            float h, lo;
+            tf32_split(vv[q], h, lo);
+            Bh[off] = h;
+            Bl[off] = lo;
+        }
+    }
+}
+
+// this lane's float offset in row q of the 4 rows of one sky, for an even (h = 0) or odd
+// (h = 1) sky of a multiple-of-4 group: the 16-byte chunk (lane / 4) of a 128-byte row
+// sits at chunk (lane / 4) ^ (row & 7), and row & 7 = 4 h + q
+__device__ __forceinline__ void ms_swz_offsets(int lane, int (&swz_off)[2][4]) {
+    const int ch = lane >> 2, lo4 = lane & 3;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) swz_off[h][q] = q * 32 + ((ch ^ (4 * h + q)) << 2) + lo4;
+}
+
+// 288 threads, two CTAs per SM: the 18 warps spread 5, 5, 4, 4 over the SM's four
+// 16,384-register partitions, so at most 96 registers a thread.
 // NC = T/E/B components per sky (1 or 3), a compile-time count so that the V
 // producers' component loops unroll and the four skies of a unit interleave.
 template <int NC>
@@ -181,6 +229,7 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
     extern __shared__ unsigned char ms_raw[];
     __shared__ __align__(8) uint64_t full_a[kMsNB], full_b[kMsNB], empty[kMsNB];
     __shared__ __align__(8) uint64_t stg_bar[4][kMsNS];    // TMA arrivals of each V warp's staging slots
+    __shared__ __align__(8) uint64_t slot_free[4][kMsNS];  // consumer of a helped V warp's slot has finished
     __shared__ uint32_t tmem_base;
     __shared__ int s_lmin, s_fail;
     __shared__ float2 wcoef[4][kMsLC];                      // per W warp: (a, c+ or c-) of the chunk's l
@@ -235,6 +284,14 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
         return;
     }
     const int nchunks = (a.L - lstart + kMsLC) / kMsLC;
+    // With more than 16 skies a V warp has two units per chunk (skies 4 vw.. and 16 + 4 vw..);
+    // when both hold skies, W warp vw builds the second one after its recurrence (the W
+    // warps would otherwise idle on the MMAs while the V warps bind the kernel).
+    const int npass = (a.nsg + 15) >> 4;
+    auto passes_of = [&](int vw) { return min(npass, max(0, (a.nsg - 4 * vw + 15) >> 4)); };
+    int nhelp = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) nhelp += (npass == 2 && passes_of(w) == 2) ? 1 : 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(&tmem_base)), "r"(kMsTmemCols) : "memory");
@@ -244,9 +301,13 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
         for (int q = 0; q < 4 * kMsNS; ++q)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&stg_bar[q / kMsNS][q % kMsNS]))
                          : "memory");
+        for (int q = 0; q < 4 * kMsNS; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&slot_free[q / kMsNS][q % kMsNS]))
+                         : "memory");
         for (int q = 0; q < kMsNB; ++q) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&full_a[q])), "r"(kMsRows) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&full_b[q])), "r"(kMsRows) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&full_b[q])), "r"(kMsRows + 32 * nhelp)
+                         : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[q])) : "memory");
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -258,14 +319,26 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
 
     if (warp < 4) {
         // ---------------------------------------------------------------- W producers
-        // this warp's lane i holds the coefficients of l = c0 + i (prefetched two chunks ahead)
-        RTab32 tcur = {0.f, 0.f, 0.f, 0.f}, tnext = {0.f, 0.f, 0.f, 0.f}, tnext2 = {0.f, 0.f, 0.f, 0.f};
+        // this warp's lane i holds the coefficients of l = c0 + i (prefetched one chunk ahead)
+        RTab32 tcur = {0.f, 0.f, 0.f, 0.f}, tnext = {0.f, 0.f, 0.f, 0.f};
+        // helper duty: the second unit of V warp `warp` (skies 16 + 4 warp ..), see the V producers
+        const bool whelp = npass == 2 && passes_of(warp) == 2;
+        const int lmin = max(m, k);
+        const float2 *beam_k = a.beam + (int64_t)k * (a.L + 1);
+        int swz_off[2][4];
+        ms_swz_offsets(lane, swz_off);
         if (lstart + lane <= a.L) tcur = tab[lstart + lane];
-        if (lstart + kMsLC + lane <= a.L) tnext = tab[lstart + kMsLC + lane];
         for (int c = 0; c < nchunks; ++c) {
             const int bi = c % kMsNB;
             const int c0 = lstart + c * kMsLC;
-            if (c + 2 < nchunks && c0 + 2 * kMsLC + lane <= a.L) tnext2 = tab[c0 + 2 * kMsLC + lane];
+            if (c + 1 < nchunks && c0 + kMsLC + lane <= a.L) tnext = tab[c0 + kMsLC + lane];
+            // the beam values of this lane's l for the helper unit (in flight during the recurrence)
+            float2 wb[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            const bool lok = c0 + lane <= a.L && c0 + lane >= lmin;
+            if (whelp && lok) {
+#pragma unroll
+                for (int X = 0; X < NC; ++X) wb[X] = __ldg(beam_k + (int64_t)X * (a.K + 1) * (a.L + 1) + c0 + lane);
+            }
             if (c >= kMsNB && !mbar_wait(smem_u32(&empty[bi]), ((c - kMsNB) / kMsNB) & 1)) *fail = 1;
             if (*fail) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -326,8 +399,35 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(smem_u32(&full_a[bi]));
+            if (whelp) {
+                const int ui = 2 * c + 1, sl = ui % kMsNS;
+                // V warp `warp` has read unit ui - 3 of this slot and issued unit ui into it
+                if (c >= 1 && !mbar_wait(smem_u32(&slot_free[warp][sl]), ((ui - 3) / kMsNS) & 1)) *fail = 1;
+                if (!*fail && !mbar_wait(smem_u32(&stg_bar[warp][sl]), (ui / kMsNS) & 1)) *fail = 1;
+                if (*fail) break;
+                // this lane's beam factors (l = c0 + lane), as the V producers form them
+                const float cl = lok ? tcur.c : 0.f, sg = neg ? -cl : cl, sy = (m == 0) ? 0.f : sg;
+                float bxc[3], byc[3], bxs[3], bys[3];
+#pragma unroll
+                for (int X = 0; X < 3; ++X) {
+                    if (k == 0) wb[X].y = 0.f;
+                    bxc[X] = cl * wb[X].x;
+                    byc[X] = cl * wb[X].y;
+                    bxs[X] = sy * wb[X].x;
+                    bys[X] = sy * wb[X].y;
+                }
+                const float par = ((c0 + lane) & 1) ? -1.f : 1.f;
+                float *Bh = base + bi * 2 * bfl + 128 * (16 + 4 * warp), *Bl = Bh + bfl;
+                const int64_t x0 = moff + lstart + (int64_t)c * kMsLC;
+                const float *wstage = base + 2 * kMsNB * bfl + warp * kMsNS * kMsStageF;
+                ms_build_unit<NC>(wstage + sl * kMsStageF + 2 * ((int)(x0 & 1) + lane), Bh, Bl, bxc, byc, bxs,
+                                  bys, par, swz_off);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&slot_free[warp][sl]));
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(smem_u32(&full_b[bi]));
+            }
             tcur = tnext;
-            tnext = tnext2;
         }
     } else if (warp < 8) {
         // ---------------------------------------------------------------- V producers
@@ -338,19 +438,14 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
         const int vw = warp - 4;
         const float2 *beam_k = a.beam + (int64_t)k * (a.L + 1);
         const int lmin = max(m, k);
-        const int i = lane, ch = i >> 2, lo4 = i & 3;
-        // this lane's float offset in row q of the 4 rows of one sky, for an even (h = 0) or
-        // odd (h = 1) sky of a multiple-of-4 group: the 16-byte chunk ch of a 128-byte row
-        // sits at chunk ch ^ (row & 7), and row & 7 = 4 h + q
+        const int i = lane;
         int swz_off[2][4];
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) swz_off[h][q] = q * 32 + ((ch ^ (4 * h + q)) << 2) + lo4;
-        const int npass = (a.nsg + 15) >> 4, nunits = nchunks * npass;
+        ms_swz_offsets(lane, swz_off);
+        const int nunits = nchunks * npass;
         // this warp's passes j < na hold skies (4 vw + 16 j < nsg); its staged units are
         // numbered ui = c na + j, slot ui mod 3, and issued two units ahead
-        const int na = min(npass, max(0, (a.nsg - 4 * vw + 15) >> 4)), nact = nchunks * na;
+        const int na = passes_of(vw), nact = nchunks * na;
+        const bool helped = npass == 2 && na == 2;
         float *stage = base + 2 * kMsNB * bfl + vw * kMsNS * kMsStageF;
         const uint32_t tx_bytes = (uint32_t)(kMsBoxX * NC * 4 * sizeof(float));
         auto issue = [&](int ui) {
@@ -390,25 +485,72 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
         beam_of(0, bn, cn);
         beam_of(1, bn2, cn2);
         float bxc[3], byc[3], bxs[3], bys[3], par = 1.f;
+        auto chunk_factors = [&](int c) {
+            const int l = lstart + c * kMsLC + i;
+            // this lane's beam factors for the chunk (c_l folded in; sigma = sign of k
+            // and the m = 0 rule -- Im s ignored -- folded into the factors of Im s)
+            const float cl = cn, sg = neg ? -cl : cl, sy = (m == 0) ? 0.f : sg;
+#pragma unroll
+            for (int X = 0; X < 3; ++X) {
+                bxc[X] = cl * bn[X].x;
+                byc[X] = cl * bn[X].y;
+                bxs[X] = sy * bn[X].x;
+                bys[X] = sy * bn[X].y;
+                bn[X] = bn2[X];
+            }
+            par = (l & 1) ? -1.f : 1.f;
+            cn = cn2;
+            beam_of(c + 2, bn2, cn2);
+        };
         int ui_done = 0;                  // staged units consumed
+        int issued = min(2, nact);        // units issued (the helped schedule)
+        if (helped) {
+            // Units 2c (this warp) and 2c + 1 (W warp vw) per chunk; unit u sits in slot u mod 3.
+            // A copy lands in a slot only once the slot's previous unit has been read: unit
+            // 2c + 3 goes into the slot of 2c, which this warp has just read; unit 2c + 2 into
+            // the slot of 2c - 1, which W warp vw releases through slot_free.  This warp arrives
+            // on the slot_free of 2c once 2c is read and 2c + 3 issued; W warp vw waits for that
+            // before it tests the staging barrier of 2c + 3 (so no parity test runs two phases
+            // away from its barrier).
+            for (int c = 0; c < nchunks; ++c) {
+                const int bi = c % kMsNB;
+                chunk_factors(c);
+                if (c >= kMsNB && !mbar_wait(smem_u32(&empty[bi]), ((c - kMsNB) / kMsNB) & 1)) *fail = 1;
+                if (*fail) break;
+                const int nx = 2 * c + 2;
+                if (nx < nact) {
+                    if (c >= 1 && !mbar_wait(smem_u32(&slot_free[vw][nx % kMsNS]), ((2 * c - 1) / kMsNS) & 1))
+                        *fail = 1;
+                    if (*fail) break;
+                    issue(nx);
+                    issued = nx + 1;
+                }
+                const int ui = 2 * c;
+                if (!mbar_wait(smem_u32(&stg_bar[vw][ui % kMsNS]), (ui / kMsNS) & 1)) *fail = 1;
+                if (*fail) break;
+                float *Bh = base + bi * 2 * bfl + 128 * (4 * vw), *Bl = Bh + bfl;
+                const int64_t x0 = moff + lstart + (int64_t)c * kMsLC;
+                ms_build_unit<NC>(stage + (ui % kMsNS) * kMsStageF + 2 * ((int)(x0 & 1) + i), Bh, Bl, bxc, byc,
+                                  bxs, bys, par, swz_off);
+                __syncwarp();
+                if (ui + 3 < nact) {
+                    issue(ui + 3);
+                    issued = ui + 4;
+                }
+                if (lane == 0) mbar_arrive(smem_u32(&slot_free[vw][ui % kMsNS]));
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(smem_u32(&full_b[bi]));
+            }
+            // after a failed wait: the last copy issued into each slot lands (bounded) before
+            // the CTA's shared memory is released
+            if (*fail && lane == 0)
+                for (int u = max(0, issued - kMsNS); u < issued; ++u)
+                    mbar_wait(smem_u32(&stg_bar[vw][u % kMsNS]), (u / kMsNS) & 1, 1000000ull);
+        } else
         for (int u = 0; u < nunits; ++u) {
             const int c = u / npass, j = u - c * npass, bi = c % kMsNB, s0 = 4 * vw + 16 * j;
             if (j == 0) {
-                const int l = lstart + c * kMsLC + i;
-                // this lane's beam factors for the chunk (c_l folded in; sigma = sign of k
-                // and the m = 0 rule -- Im s ignored -- folded into the factors of Im s)
-                const float cl = cn, sg = neg ? -cl : cl, sy = (m == 0) ? 0.f : sg;
-#pragma unroll
-                for (int X = 0; X < 3; ++X) {
-                    bxc[X] = cl * bn[X].x;
-                    byc[X] = cl * bn[X].y;
-                    bxs[X] = sy * bn[X].x;
-                    bys[X] = sy * bn[X].y;
-                    bn[X] = bn2[X];
-                }
-                par = (l & 1) ? -1.f : 1.f;
-                cn = cn2;
-                beam_of(c + 2, bn2, cn2);
+                chunk_factors(c);
                 if (c >= kMsNB && !mbar_wait(smem_u32(&empty[bi]), ((c - kMsNB) / kMsNB) & 1)) *fail = 1;
             }
             if (*fail) break;
@@ -421,35 +563,8 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
                 float *Bh = base + bi * 2 * bfl + 128 * s0, *Bl = Bh + bfl;
                 // this lane's l sits at float2 (x0 & 1) + lane of each staged row
                 const int64_t x0 = moff + lstart + (int64_t)c * kMsLC;
-                const float *src = stage + (ui % kMsNS) * kMsStageF + 2 * ((int)(x0 & 1) + i);
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    // with A+ = sum_X s conj(b) and A- = sum_X conj(s) conj(b), the four
-                    // columns are c (p1.x, p1.y), (-1)^l c (p2.x, p2.y), (p1, p2) = (A+, A-)
-                    // for +k and (A-, A+) for -k:
-                    //   c p1 = (xa + ys, yx - xb),  c p2 = (xa - ys, -(yx + xb))
-                    // xa = sum s.x c b.x, xb = sum s.x c b.y, ys = sum s.y sigma c b.y,
-                    // yx = sum s.y sigma c b.x
-                    float xa = 0.f, xb = 0.f, ys = 0.f, yx = 0.f;
-#pragma unroll
-                    for (int X = 0; X < NC; ++X) {
-                        const float2 s2 = *reinterpret_cast<const float2 *>(src + (t * NC + X) * kMsBoxX);
-                        xa = fmaf(s2.x, bxc[X], xa);
-                        xb = fmaf(s2.x, byc[X], xb);
-                        ys = fmaf(s2.y, bys[X], ys);
-                        yx = fmaf(s2.y, bxs[X], yx);
-                    }
-                    const float vv[4] = {xa + ys, yx - xb, par * (xa - ys), -par * (yx + xb)};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        // row 4 s + q; s0 is a multiple of 4, so (row & 7) = 4 (t & 1) + q
-                        const int off = 128 * t + swz_off[t & 1][q];
-                        float h, lo;
-                        tf32_split(vv[q], h, lo);
-                        Bh[off] = h;
-                        Bl[off] = lo;
-                    }
-                }
+                ms_build_unit<NC>(stage + (ui % kMsNS) * kMsStageF + 2 * ((int)(x0 & 1) + i), Bh, Bl, bxc, byc,
+                                  bxs, bys, par, swz_off);
                 ui_done = ui + 1;
             }
             if (j == npass - 1) {
@@ -459,7 +574,7 @@ __global__ void __launch_bounds__(kMsThreads, 2) k_lcontract_mma(const MsArgs a,
         }
         // after a failed wait: the TMA loads still in flight land (bounded) before the
         // CTA's shared memory is released
-        if (*fail && lane == 0)
+        if (!helped && *fail && lane == 0)
             for (int ui = ui_done; ui < min(ui_done + kMsNS, nact); ++ui)
                 mbar_wait(smem_u32(&stg_bar[vw][ui % kMsNS]), (ui / kMsNS) & 1, 1000000ull);
     } else if (lane == 0) {
