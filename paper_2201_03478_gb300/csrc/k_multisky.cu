@@ -29,8 +29,9 @@
 //   * one thread issues the MMAs and commits them to an mbarrier per buffer;
 //     every wait is bounded and sets an error flag (the CTA then stops,
 //     waits for its MMAs with a bound and frees its tensor memory).
-// The V producers bind the kernel (the MMA thread waits on them, the W warps
-// wait on the MMAs); their work per sky and l is four FMAs per component.
+// The V producers bind the kernel (the MMA thread waits on them); with more
+// than 16 skies each W warp, otherwise idle on the MMAs, also builds the second
+// 4-sky unit of its V partner.  Their work per sky and l is four FMAs per component.
 #include <algorithm>
 
 #include <cuda.h>
@@ -166,7 +167,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // Roles (warp-specialized; no CTA-wide barrier inside the chunk loop):
 //   warps 0-3  W producers: thread = ring pair = TMEM lane; per chunk the 32
 //              recurrence steps, TF32 split, tcgen05.st into A buffer b;
-//              arrive on full_a[b];
+//              arrive on full_a[b]; with more than 16 skies W warp w then builds
+//              the unit of skies 16 + 4w .. + 3 into B buffer b (staged by V
+//              warp 4 + w, handed over through slot_free) and arrives on full_b[b];
 //   warps 4-7  V producers: lane = l - c0, warp over skies; sky x beam
 //              columns into the swizzled B buffer b; arrive on full_b[b];
 //   warp 8     MMA issuer (lane 0): waits full_a[b] and full_b[b], issues the
