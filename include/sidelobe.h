@@ -89,7 +89,9 @@ typedef enum {
                      tables, FFT and coordinates of SL_FP64 (maps are double2),
                      with the l-contraction and the interpolation sums run in
                      double-float arithmetic (pairs of floats, ~48-bit
-                     significands).  The adjoint runs in FP64. */
+                     significands), and so do the transposes of both in
+                     adjoint_tod.  (SL_FP32 and SL_TF32X3 plans run adjoint_tod
+                     in FP64.) */
 } sl_precision;
 
 typedef struct {
