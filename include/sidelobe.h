@@ -39,7 +39,8 @@
  *   beam : double [ncomp][kmax+1][lmax+1][2]; entries with l < k are
  *          ignored; Im of k = 0 entries is ignored; b_{l,-k} = (-1)^k conj(b_lk).
  *   maps : the cube, [nrings][nphi][kmax+1] complex, k fastest;
- *          double2 in SL_FP64 plans, float2 in SL_FP32 plans.
+ *          double2 in SL_FP64 and SL_DF64 plans, float2 in SL_FP32 and
+ *          SL_TF32X3 plans.
  *          phi_j = 2 pi j / nphi on every ring.
  *   theta, phi, psi : double [n], radians; theta in [0, pi].
  *   tod  : double [n].
