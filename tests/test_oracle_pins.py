@@ -313,11 +313,12 @@ def test_polarised_is_sum_of_scalar_convolutions(oracle_lib):
 
 
 # --------------------------------------------------------------------------- cube
-@pytest.mark.parametrize("nphi", [24, 16])
+@pytest.mark.parametrize("nphi", [24, 16, 8])
 def test_cube_nodes_are_psi_fourier_coefficients(oracle_lib, nphi):
     """Step 1 of the two-step algorithm: the cube at a node equals the k-th Fourier
     coefficient in psi of the exact convolution there (nphi = 16 < 2L+1 also checks
-    that folding m mod nphi is exact at the nodes)."""
+    that folding m mod nphi is exact at the nodes; nphi = 8 <= L, that several
+    aliases of one bin add up)."""
     rng = np.random.default_rng(8)
     L, K, R = 10, 3, 8
     sky, beam = _rand_sky(rng, L, 2), _rand_beam(rng, L, K, 2)
