@@ -106,3 +106,28 @@ def test_batch_arguments_are_checked_before_any_device_call(lib):
 def test_oracle_builds():
     import oracle
     assert os.path.exists(oracle.build())
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/sidelobe.h compiles as C99 (no C++ in the boundary) and a C program
+    that takes the address of every declared function links against the library
+    (nothing is called: no GPU here)."""
+    import shutil
+    import subprocess
+    from paper_2201_03478_gb300 import _build
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = _declared_functions()
+    src = tmp_path / "use_abi.c"
+    src.write_text("#include \"sidelobe.h\"\n#include <stdio.h>\n"
+                   "typedef void (*fn)(void);\n"
+                   "int main(void) {\n    const fn f[] = {\n"
+                   + "".join("        (fn)&%s,\n" % n for n in names)
+                   + "    };\n    printf(\"%d\\n\", (int)(sizeof f / sizeof f[0]));\n    return 0;\n}\n")
+    libdir = os.path.dirname(_build.LIB)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-o", str(tmp_path / "use_abi"), "-L", libdir,
+                        "-lsidelobe", "-Wl,-rpath," + libdir, "-Wl,--allow-shlib-undefined"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
