@@ -14,8 +14,9 @@
 // until the process exits:
 //   kNoAllocMaxSamples (262,144) samples and kNoAllocMaxTiles (65,536) grid
 //   tiles, 8.75 MiB per device.
-// Longer TODs are processed in chunks of at most kNoAllocMaxSamples.  The sort
-// here keys samples by tile (not by cell), which keeps the histogram small.
+// A call with n above kNoAllocMaxSamples is rejected with SL_ERR_ARG; the
+// caller splits a longer TOD into chunks of at most that many samples.  The
+// sort here keys samples by tile (not by cell), which keeps the histogram small.
 #include <mutex>
 
 #include "sl_internal.cuh"
@@ -83,7 +84,10 @@ extern "C" sl_status interp_tod_noalloc(sl_plan *p, const void *maps, const doub
     b.cursor = b.hist + (kNoAllocMaxTiles + 1);
     b.bsum = b.cursor + kNoAllocMaxTiles;
     const int rec64 = plan_wide(p->precision);
-    b.chunk_off = p->precision == SL_FP64 ? nullptr : b.bsum + kBsumWords;  // tile-staged kernels: work items
-    if ((st = launch_sort_into(p, b, theta, phi, psi, n, 0, rec64, !rec64)) != SL_OK) return st;
+    // FP32, TF32X3 and DF64 plans interpolate tile by tile from shared memory and need
+    // the per-tile work list; FP64 plans gather per sample and do not.
+    const int chunks = p->precision != SL_FP64;
+    b.chunk_off = chunks ? b.bsum + kBsumWords : nullptr;
+    if ((st = launch_sort_into(p, b, theta, phi, psi, n, 0, rec64, chunks)) != SL_OK) return st;
     return launch_interp(p, b, 0, maps, psi, n, tod);
 }

@@ -1,7 +1,7 @@
 """The bounds-checked library variant (compiled with -DSL_CHECKED: every data-
 dependent gather and scatter index of the binning, scatter, interpolation in all
 precisions and directions, psi-grid and orbital kernels is tested before the
-access) on the parity workloads, including pointings at and near both poles and
+access; the forward also runs through interp_tod_noalloc) on the parity workloads, including pointings at and near both poles and
 at phi = 0 and 2 pi: no guard may fire, and the results must still match the
 oracle.  This stands in for a memory checker, which is not available here; it
 runs in a child process because a process loads one library variant."""
@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 SCRIPT = r'''
+import ctypes
 import sys
 import numpy as np
 import torch
@@ -47,10 +48,16 @@ for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5), ("df64", 1e-10)):
     gs, gb = sl.adjoint_tod(plan, dev(th), dev(ph), dev(ps), dev(y), dev(cfg["sky"]), dev(cfg["beam"]))
     npsi = 2 * K + 2
     tp = sl.interp_tod_psi(plan, sl.synth_psi_cube(plan, maps, npsi), dev(th), dev(ph), dev(ps)).cpu().numpy()
+    tna = torch.full((th.size,), float("nan"), dtype=torch.float64, device="cuda")
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    dth, dph, dps = dev(th), dev(ph), dev(ps)
+    _lib.check(lib.interp_tod_noalloc(plan.ptr, P(maps), P(dth), P(dph), P(dps), th.size, P(tna)))
     plan.sync()
+    tna = tna.cpu().numpy()
     st = lib.sl_debug_check_status()
     assert st == 0, (prec, hex(st))
     assert rel(tod, ref_tod) < tol, (prec, rel(tod, ref_tod))
+    assert rel(tna, ref_tod) < tol, (prec, "noalloc", rel(tna, ref_tod))
     assert rel(gs.cpu().numpy(), rs) < 1e-10 and rel(gb.cpu().numpy(), rb) < 1e-10, prec   # adjoint: FP64
     ref_tp = pg.interp_psi(pg.psi_cube(ref_cube, npsi), rt, th, ph, ps)
     assert rel(tp, ref_tp) < tol, (prec, rel(tp, ref_tp))
