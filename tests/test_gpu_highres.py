@@ -11,7 +11,7 @@ import pytest
 import torch
 
 import workloads as W
-from tests.conftest import rel_l2
+from tests.conftest import MAX32, MAX64, MAXTC, check_close, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -70,12 +70,10 @@ def test_highres_precision_modes_vs_oracle(highres, oracle_lib):
         for prec in got:
             got[prec].append(highres[prec][idx])
     ref = np.concatenate(refs)
-    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5), ("df64", 1e-10), ("tf32x3", 1e-5)):
+    for prec, tol, mx in (("fp64", 1e-10, MAX64), ("fp32", 1e-5, MAX32), ("df64", 1e-10, MAX64),
+                          ("tf32x3", 1e-5, MAXTC)):
         g = np.concatenate(got[prec])
-        err = rel_l2(g, ref)
-        print("lmax=2048 kmax=32: %s TOD on %d-sample subset, rel L2 vs oracle %.2e, max|err|/rms %.2e"
-              % (prec, ref.size, err, np.max(np.abs(g - ref)) / np.sqrt(np.mean(ref ** 2))))
-        assert err < tol
+        check_close(g, ref, tol, mx, "lmax=2048 kmax=32: %s TOD on %d-sample subset vs oracle" % (prec, ref.size))
 
 
 def test_highres_fp32_vs_fp64_whole_tod(highres):

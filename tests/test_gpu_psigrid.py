@@ -9,7 +9,7 @@ import torch
 
 import workloads as W
 from oracle import psi_grid as pg
-from tests.conftest import rel_l2
+from tests.conftest import MAX32, MAX64, check_close
 
 pytestmark = pytest.mark.gpu
 
@@ -47,11 +47,10 @@ def test_psi_cube_and_tod_match_oracle(small, prec, tol, mult):
     finally:
         sl.plan_destroy(plan)
     ref_cube = pg.psi_cube(cube, npsi)
-    e_cube = rel_l2(cp_h, ref_cube)
     ref_tod = pg.interp_psi(ref_cube, cfg["ring_theta"], th, ph, ps)
-    e_tod = rel_l2(tod_h, ref_tod)
-    print("psi-grid %s npsi=%d: cube %.2e, tod %.2e" % (prec, npsi, e_cube, e_tod))
-    assert e_cube < tol and e_tod < tol
+    mx = MAX64 if tol <= 1e-10 else MAX32
+    check_close(cp_h, ref_cube, tol, mx, "psi-grid %s npsi=%d cube" % (prec, npsi))
+    check_close(tod_h, ref_tod, tol, mx, "psi-grid %s npsi=%d tod" % (prec, npsi))
 
 
 @pytest.mark.parametrize("order", [2, 6])
@@ -69,7 +68,7 @@ def test_interpolation_orders(small, order):
     finally:
         sl.plan_destroy(plan)
     ref = pg.interp_psi(pg.psi_cube(cube, npsi), cfg["ring_theta"], th, ph, ps, p=order)
-    assert rel_l2(tod_h, ref) < 1e-10
+    check_close(tod_h, ref, 1e-10, MAX64, "psi-grid order %d tod" % order)
 
 
 def test_bad_npsi_is_rejected(small):
@@ -116,7 +115,6 @@ def test_fullsize_psi_cube_rings_and_grid_angles(oracle_lib):
         torch.cuda.empty_cache()
     G = oracle_lib.cube_G(cfg["sky"], cfg["beam"], cfg["ring_theta"][RINGS])
     ref = pg.psi_cube(oracle_lib.cube_from_G(G, cfg["nphi"]), npsi)
-    e_rows = rel_l2(rows, ref)
-    print("full-size psi cube rings %.2e; psi-grid vs exact TOD at grid angles %.2e" % (e_rows, e_grid))
-    assert e_rows < 1e-10
+    print("full-size psi-grid vs exact TOD at grid angles %.2e" % e_grid)
+    check_close(rows, ref, 1e-10, MAX64, "full-size psi cube rings")
     assert e_grid < 1e-12
