@@ -323,6 +323,16 @@ sl_status sl_plan_sync(sl_plan *plan);
  * so that the next sl_plan_sync returns SL_ERR_TIMEOUT. */
 sl_status sl_plan_selftest_timeout(sl_plan *plan);
 
+/* Measured arithmetic peak of `device` (no counterpart in the paper: the
+ * denominator of the roofline fractions reported for the ALU-bound kernels).
+ * kind 0: FP64 fused multiply-add; 1: FP32 fused multiply-add; 2: packed FP32
+ * (two lanes per instruction).  Runs 8 independent chains per thread on 8
+ * CTAs of 256 threads per SM for about 16 ms, best of three timed launches
+ * after a warm-up, and stores flops per second (2 per lane multiply-add) in
+ * *flops_per_s.  Touches no memory; synchronises its own stream.
+ * SL_ERR_ARG for a NULL output or another kind. */
+sl_status sl_measure_alu_peak(int device, int kind, double *flops_per_s);
+
 /* Per-kernel timing.  While enabled, every launch is bracketed by CUDA events
  * on the plan's stream.  sl_plan_kernel_stats fills, for up to max entries,
  * the kernel name, the number of launches and the summed device milliseconds

@@ -6,7 +6,7 @@ from .binding import (Batch, Plan, adjoint_interp, adjoint_synth, adjoint_tod, a
                       orbital_dipole_tod,
                       orbital_moments, plan_destroy, quad_factor, sidelobe_plan_create, sl_batch_create, sl_batch_destroy,
                       sl_batch_run, synth_spin_maps, synth_spin_maps_multi, tod_from_host, synth_psi_cube,
-                      interp_tod_psi)
+                      interp_tod_psi, measure_alu_peak)
 from ._lib import SL_DF64, SL_FP32, SL_FP64, SL_TF32X3, SidelobeError
 from .autograd import SidelobeConvolution, sidelobe_tod
 
@@ -14,4 +14,5 @@ __all__ = ["Plan", "sidelobe_plan_create", "synth_spin_maps", "interp_tod", "adj
            "adjoint_interp",
            "adjoint_synth", "plan_destroy", "tod_from_host", "SidelobeError", "SL_FP64", "SL_FP32", "SL_DF64", "SL_TF32X3",
            "SidelobeConvolution", "sidelobe_tod", "Batch", "sl_batch_create", "sl_batch_run", "sl_batch_destroy",
-           "synth_spin_maps_multi", "orbital_moments", "orbital_dipole_tod", "quad_factor", "synth_psi_cube", "interp_tod_psi"]
+           "synth_spin_maps_multi", "orbital_moments", "orbital_dipole_tod", "quad_factor", "synth_psi_cube", "interp_tod_psi",
+           "measure_alu_peak"]

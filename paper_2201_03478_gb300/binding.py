@@ -432,3 +432,12 @@ def sl_batch_destroy(batch: Batch) -> None:
     if batch is not None and batch.ptr:
         _lib.load().sl_batch_destroy(batch.ptr)
         batch.ptr = None
+
+
+def measure_alu_peak(kind: str = "fp64", device: int = 0) -> float:
+    """Measured arithmetic peak of ``device`` in flops/s (sl_measure_alu_peak):
+    kind "fp64", "fp32" or "fp32x2" (packed two-lane FP32 multiply-add)."""
+    code = {"fp64": 0, "fp32": 1, "fp32x2": 2}[kind]
+    out = ctypes.c_double(0.0)
+    check(_lib.load().sl_measure_alu_peak(int(device), code, ctypes.byref(out)))
+    return float(out.value)

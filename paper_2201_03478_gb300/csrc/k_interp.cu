@@ -19,7 +19,9 @@
 // owning a disjoint set of k so that no two threads update the same word, and
 // the tile is flushed to the global adjoint cube with atomic adds.
 #include <algorithm>
+#include <climits>
 
+#include "mbar.cuh"
 #include "sl_internal.cuh"
 
 namespace sl {
@@ -109,6 +111,8 @@ struct TiledArgs {
     const unsigned *perm, *start, *chunk_off;
     int ntiles, ncell;
     double *tod;
+    int *err;                 // device error flag (bounded waits of k_interp_f32_cells)
+    unsigned *work;           // work counter of k_interp_f32_cells (zeroed before each launch)
 };
 
 template <int TC, int P>
@@ -207,6 +211,420 @@ __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
             A.tod[s] = (double)acc0 + 2.0 * (double)acc1;
         }
     }
+}
+
+// ------------------------------------------------------------------ forward FP32, cell groups
+// The path interp_tod takes for FP32 plans.  The fine sort orders each tile's
+// samples by cell, so a thread evaluates S samples of ONE cell together (S = 2
+// for p <= 4; 1 for p = 6, where two samples' weights would not fit in
+// registers): every node value it loads from shared memory feeds S sums, which
+// halves the shared-memory traffic per multiply-add -- the bound of the
+// one-sample form (k_interp_f32_tiled, kept for the tile-keyed sort of
+// interp_tod_noalloc).  The (re, im) sums run as packed two-lane FP32
+// multiply-adds (__ffma2_rn), half the issue slots of scalar ones.  The k sum
+// is a Horner scheme in z = e^{i psi}, from k = K down to 1:
+//   h <- h z + S_k,   c = Re S_0 + 2 Re(z h)   (the last step in FP64).
+//
+// Warp-specialized, no CTA-wide barrier after the set-up.  Warp 0 stages;
+// warps 1-7 evaluate.  The staging warp takes chunks of kCellIPC consecutive
+// work items (<= kChunkA sorted samples of one tile) from a global counter and
+// cuts them into sub-items of <= kCellSub samples.  All its global -> shared
+// traffic is asynchronous (cp.async and one bulk copy), so one latency covers
+// a whole tile or sub-item.
+//   node buffers (2):   node0[NR][TW] = Re F_0 (k = 0 enters the TOD through
+//                       its real part only), node[KP][NR][TW] = float4
+//                       (F_{2j+1}, F_{2j+2}), KP = ceil(K/2) (an odd K's unused
+//                       slot holds zeros), the tile's four base rows of the row
+//                       table and its cells' first sorted positions.  Same tile,
+//                       halo and ghost-row rule as the tiled kernel (ghost rows
+//                       get their (-1)^k sign in a pass after the copies land);
+//                       refilled when the tile changes.
+//   record buffers (2): a sub-item's sample indices (one bulk copy), its stencil
+//                       records (cp.async gathers through those indices), its
+//                       group table (per cell ceil(count / S) groups, prefix
+//                       offsets) and a header.
+// Handoff by mbarriers: nfull and rfull (32 staging lanes' arrivals plus 32
+// arrivals on completion of their cp.async copies), nempty and rempty (7
+// evaluating warps); a private barrier paces the bulk copy.  Every wait is
+// bounded (mbar.cuh); an expired wait raises the plan's error flag and the warp
+// stops (SL_ERR_TIMEOUT at the next sl_plan_sync).
+constexpr int kCellSub = 1024;        // samples per record buffer
+constexpr int kCellSidx = kCellSub + 8;   // sample-index slots: a 16-byte aligned superset of the sub-item
+constexpr int kCellConsumers = 7;     // evaluating warps per CTA (plus one staging warp)
+constexpr int kCellIPC = 8;           // work items per chunk taken from the counter
+
+struct CellMeta {
+    int nbuf, rowlo, collo, tr;
+    unsigned ngroups;                 // 0xffffffff: no more work for this CTA
+    unsigned poff;                    // first sample index of the sub-item within its slots
+};
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+}
+// 4-byte copy; with ok == false nothing is read and the destination is zero-filled
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" :: "r"(smem_u32(dst)), "l"(src), "r"(ok ? 4 : 0)
+                 : "memory");
+}
+
+// Exact float -> double by integer operations only (normal, subnormal, zero,
+// infinity, NaN): the FP64 pipe runs at 1/64 of the FP32 rate, and the
+// hardware conversion runs on it.
+__device__ __forceinline__ double f2d_exact(float x) {
+    const unsigned u = __float_as_uint(x), e = (u >> 23) & 0xffu;
+    unsigned m = u & 0x7fffffu;
+    unsigned de;
+    if (e == 0xffu) {
+        de = 0x7ffu;
+    } else if (e != 0u) {
+        de = e + 896u;
+    } else if (m == 0u) {
+        de = 0u;
+    } else {   // subnormal m 2^-149: the leading one at bit b moves to the implicit bit
+        const unsigned b = 31u - (unsigned)__clz(m);
+        m = (m << (23u - b)) & 0x7fffffu;
+        de = b + 874u;
+    }
+    return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                            ((unsigned long long)de << 52) | ((unsigned long long)m << 29)));
+}
+
+template <int TC, int P>
+__global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const TiledArgs A) {
+    constexpr int TW = TC + P - 1, NR = kTileRows + P - 1, NN = NR * TW;
+    constexpr int NCELL = kTileRows * TC, NQ = P * P, CPL = NCELL / 32, ROWT = kTileRows * 2 * P;
+    constexpr int S = (P <= 4) ? 2 : 1;
+    constexpr unsigned kEnd = 0xffffffffu;
+    const InterpGeom &g = A.g;
+    const int K = g.K, K1 = K + 1, KP = (K + 1) >> 1, KE = KP + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *nodeb = reinterpret_cast<float4 *>(smem_raw);                             // [2][KP * NN]
+    StencilRec32 *srecb = reinterpret_cast<StencilRec32 *>(nodeb + 2 * (size_t)KP * NN);   // [2][kCellSub]
+    unsigned *ssidb = reinterpret_cast<unsigned *>(srecb + 2 * kCellSub);            // [2][kCellSidx]
+    unsigned *cstb = ssidb + 2 * kCellSidx;                                          // [2][NCELL + 1]
+    float *node0b = reinterpret_cast<float *>(cstb + 2 * (NCELL + 1));               // [2][NN]
+    float *srowb = node0b + 2 * NN;                                                  // [2][ROWT]
+    unsigned *goffb = reinterpret_cast<unsigned *>(srowb + 2 * ROWT);                // [2][NCELL + 1]
+    unsigned *cbegb = goffb + 2 * (NCELL + 1);                                       // [2][NCELL]
+    unsigned *cendb = cbegb + 2 * NCELL;                                             // [2][NCELL]
+    __shared__ CellMeta meta[2];
+    __shared__ __align__(8) unsigned long long bars[9];
+    const uint32_t rfull = smem_u32(&bars[0]), rempty = smem_u32(&bars[2]);
+    const uint32_t nfull = smem_u32(&bars[4]), nempty = smem_u32(&bars[6]), pbar = smem_u32(&bars[8]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(rfull + 8 * b, 64);
+            mbar_init(rempty + 8 * b, kCellConsumers);
+            mbar_init(nfull + 8 * b, 64);
+            mbar_init(nempty + 8 * b, kCellConsumers);
+        }
+        mbar_init(pbar, 1);
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+        // ------------------------------------------------ staging warp
+        const unsigned nchunks = A.chunk_off[A.ntiles];
+        bool ok = true;
+        int tile = -1;
+        unsigned nfill = 0, u = 0, pphase = 0;
+        int nb = 0, rowlo = 0, collo = 0, tr = 0;
+        for (;;) {
+            unsigned v0 = 0;
+            if (lane == 0) v0 = atomicAdd(A.work, 1u) * kCellIPC;
+            v0 = __shfl_sync(0xffffffffu, v0, 0);
+            if (v0 >= nchunks || !ok) break;
+            const unsigned v_end = min(nchunks, v0 + kCellIPC);
+            int tcur = find_tile(A.chunk_off, A.ntiles, v0);
+            for (unsigned v = v0; v < v_end && ok; ++v) {
+                while (tcur + 1 < A.ntiles && A.chunk_off[tcur + 1] <= v) ++tcur;
+                const unsigned c = v - A.chunk_off[tcur];
+                if (tcur != tile) {
+                    nb = nfill & 1;
+                    if (nfill >= 2) ok = __all_sync(0xffffffffu, mbar_wait(nempty + 8 * nb, ((nfill - 2) >> 1) & 1));
+                    if (!ok) break;
+                    tr = tcur / g.ntc;
+                    const int tcol = tcur - tr * g.ntc;
+                    rowlo = tr * kTileRows - P / 2;
+                    collo = tcol * TC - P / 2 + 1;
+                    float4 *node = nodeb + (size_t)nb * KP * NN;
+                    float *node0 = node0b + nb * NN;
+                    bool polar = false;
+                    for (int r = 0; r < NR; ++r) {
+                        const int row = rowlo + r;
+                        const bool inr = row >= -P / 2 && row <= g.R - 1 + P / 2;
+                        const bool ghost = row < 0 || row >= g.R;
+                        polar |= inr && ghost;
+                        const int ring = !inr ? 0 : (row < 0 ? -1 - row : (row >= g.R ? 2 * g.R - 1 - row : row));
+                        const int cshift = ghost ? (g.nphi >> 1) : 0;
+                        const float2 *rsrc = A.maps + (int64_t)ring * g.nphi * K1;
+                        for (int idx = lane; idx < TW * KE; idx += 32) {
+                            const int cc = idx / KE, w = idx - cc * KE;
+                            int col = collo + cc + cshift;
+                            if (col < 0) col += g.nphi;
+                            if (col >= g.nphi) col -= g.nphi;
+                            if (col >= g.nphi) col -= g.nphi;
+                            if (!SL_GUARD(col >= 0 && col < g.nphi, 0x205u)) col = 0;
+                            const float2 *src = rsrc + (int64_t)col * K1;
+                            const int nd = r * TW + cc;
+                            if (w == 0) {
+                                cp_async4(node0 + nd, src, inr);
+                            } else {
+                                const int k = 2 * w - 1;
+                                float2 *d2 = reinterpret_cast<float2 *>(node + (w - 1) * NN + nd);
+                                cp_async8(d2, src + k, inr);
+                                cp_async8(d2 + 1, src + (k + 1 <= K ? k + 1 : k), inr && k + 1 <= K);
+                            }
+                        }
+                    }
+                    // the row table of the tile's base rows (i + 1 = tr * 4 .. tr * 4 + 3, at most R)
+                    for (int t = lane; t < ROWT; t += 32) {
+                        const int ri = tr * kTileRows + t / (2 * P);
+                        cp_async4(srowb + nb * ROWT + t, g.rowtab32 + (size_t)(ri <= g.R ? ri : 0) * 2 * P + t % (2 * P),
+                                  ri <= g.R);
+                    }
+                    // first sorted position of each cell of the tile (and the tile's end)
+                    const int64_t cb = (int64_t)tcur * NCELL;
+                    for (int t = lane; t <= NCELL; t += 32) cp_async4(cstb + nb * (NCELL + 1) + t, A.start + cb + t, true);
+                    // the group tables below read the cell starts: wait for this lane's copies, then the warp's
+                    cp_async_wait_all();
+                    __syncwarp();
+                    if (__any_sync(0xffffffffu, polar)) {
+                        // ghost rows: (-1)^k, i.e. the odd member (k = 2j + 1) of every pair flips
+                        for (int r = 0; r < NR; ++r) {
+                            const int row = rowlo + r;
+                            if (!(row < 0 || row >= g.R)) continue;
+                            for (int idx = lane; idx < TW * KP; idx += 32) {
+                                const int jj = idx / TW, cc = idx - jj * TW;
+                                float4 &e = node[jj * NN + r * TW + cc];
+                                e.x = -e.x;
+                                e.y = -e.y;
+                            }
+                        }
+                        __syncwarp();
+                    }
+                    mbar_arrive_cp_async(nfull + 8 * nb);
+                    mbar_arrive(nfull + 8 * nb);
+                    tile = tcur;
+                    ++nfill;
+                }
+                const unsigned *cst = cstb + nb * (NCELL + 1);
+                const unsigned s_beg = cst[0] + c * kChunkA;
+                const unsigned s_end = min(cst[NCELL], s_beg + kChunkA);
+                for (unsigned sb = s_beg; sb < s_end && ok; sb += kCellSub, ++u) {
+                    const unsigned se = min(s_end, sb + kCellSub);
+                    const int rb = u & 1;
+                    if (u >= 2) ok = __all_sync(0xffffffffu, mbar_wait(rempty + 8 * rb, ((u - 2) >> 1) & 1));
+                    if (!ok) break;
+                    // sample indices: one bulk copy of a 16-byte aligned superset
+                    const unsigned sb4 = sb & ~3u, se4 = (se + 3u) & ~3u, poff = sb - sb4;
+                    unsigned *ssid = ssidb + rb * kCellSidx;
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(pbar, (se4 - sb4) * 4u);
+                        bulk_copy_g2s(ssid, A.perm + sb4, (se4 - sb4) * 4u, pbar);
+                    }
+                    // group table: per cell ceil(count / S) groups, exclusive prefix over the cells
+                    unsigned cnt[CPL], gbv[CPL], gev[CPL], lsum = 0;
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) {
+                        const int cc = lane * CPL + q;
+                        unsigned gb = max(cst[cc], sb), ge = min(cst[cc + 1], se);
+                        if (ge < gb) ge = gb;
+                        gbv[q] = gb - sb;
+                        gev[q] = ge - sb;
+                        cnt[q] = (ge - gb + S - 1) / S;
+                        lsum += cnt[q];
+                    }
+                    unsigned x = lsum;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    unsigned pre = x - lsum;
+                    unsigned *goff = goffb + rb * (NCELL + 1);
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) {
+                        const int cc = lane * CPL + q;
+                        goff[cc] = pre;
+                        cbegb[rb * NCELL + cc] = gbv[q];
+                        cendb[rb * NCELL + cc] = gev[q];
+                        pre += cnt[q];
+                    }
+                    if (lane == 31) goff[NCELL] = x;
+                    const unsigned total = __shfl_sync(0xffffffffu, x, 31);
+                    if (lane == 0) meta[rb] = CellMeta{nb, rowlo, collo, tr, total, poff};
+                    // the records, gathered through the indices
+                    ok = __all_sync(0xffffffffu, mbar_wait(pbar, pphase));
+                    pphase ^= 1u;
+                    if (!ok) break;
+                    StencilRec32 *srec = srecb + rb * kCellSub;
+                    for (unsigned t = lane; t < se - sb; t += 32) cp_async16(srec + t, A.rec + ssid[poff + t]);
+                    mbar_arrive_cp_async(rfull + 8 * rb);
+                    mbar_arrive(rfull + 8 * rb);
+                }
+            }
+        }
+        if (ok) {   // end marker
+            const int rb = u & 1;
+            if (u >= 2) ok = __all_sync(0xffffffffu, mbar_wait(rempty + 8 * rb, ((u - 2) >> 1) & 1));
+            if (ok) {
+                if (lane == 0) meta[rb].ngroups = kEnd;
+                mbar_arrive_cp_async(rfull + 8 * rb);
+                mbar_arrive(rfull + 8 * rb);
+            }
+        }
+        if (!ok) {
+            cp_async_wait_all();
+            mbar_wait(pbar, pphase, 10000000ull);   // a bulk copy that may still be in flight
+            if (lane == 0) atomicExch(A.err, 1);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------- evaluating warps
+    constexpr unsigned NCT = 32 * kCellConsumers;
+    const unsigned ct = threadIdx.x - 32;
+    unsigned rot = 0;   // groups dealt so far, mod NCT: each sub-item starts where the last one stopped
+    int cur_nb = -1;
+    unsigned nfill = 0;
+    bool ok = true;
+    for (unsigned u = 0;; ++u) {
+        const int rb = u & 1;
+        ok = __all_sync(0xffffffffu, mbar_wait(rfull + 8 * rb, (u >> 1) & 1));
+        if (!ok) break;
+        const unsigned ngroups = meta[rb].ngroups;
+        if (ngroups == kEnd) break;
+        const int mnb = meta[rb].nbuf;
+        if (mnb != cur_nb) {   // the next node fill (fills alternate between the two buffers)
+            __syncwarp();
+            if (cur_nb >= 0 && lane == 0) mbar_arrive(nempty + 8 * cur_nb);
+            ok = __all_sync(0xffffffffu, mbar_wait(nfull + 8 * mnb, (nfill >> 1) & 1));
+            if (!ok) break;
+            cur_nb = mnb;
+            ++nfill;
+        }
+        const int m_rowlo = meta[rb].rowlo, m_collo = meta[rb].collo, m_tr = meta[rb].tr;
+        const float4 *node = nodeb + (size_t)cur_nb * KP * NN;
+        const float *node0 = node0b + cur_nb * NN;
+        const float *srow = srowb + cur_nb * ROWT;
+        const StencilRec32 *srec = srecb + rb * kCellSub;
+        const unsigned *ssid = ssidb + rb * kCellSidx + meta[rb].poff;
+        const unsigned *goff = goffb + rb * (NCELL + 1);
+        const unsigned *cbeg = cbegb + rb * NCELL, *cend = cendb + rb * NCELL;
+        const unsigned g_first = (ct + NCT - rot) % NCT;
+        rot = (rot + ngroups) % NCT;
+        for (unsigned gi = g_first; gi < ngroups; gi += NCT) {
+            // the group's cell: the last cell whose first group is <= gi (never an empty one)
+            int lo = 0, hi = NCELL - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (goff[mid] <= gi) lo = mid; else hi = mid - 1;
+            }
+            const unsigned t0 = cbeg[lo] + S * (gi - goff[lo]);   // sub-item-local sorted position
+            const unsigned tl = cend[lo];
+            unsigned sidx[S], rcell[S];
+            float rdth[S], rfph[S], rpsr[S];
+#pragma unroll
+            for (int q = 0; q < S; ++q) {
+                const unsigned t = (t0 + q < tl) ? t0 + q : t0;
+                sidx[q] = ssid[t];
+                const StencilRec32 rr = srec[t];
+                rdth[q] = rr.dth;
+                rfph[q] = rr.fph;
+                rpsr[q] = rr.psr;
+                rcell[q] = rr.cell;
+            }
+            const int i = (int)(rcell[0] >> 16) - 1, j = (int)(rcell[0] & 0xffffu);
+            int li = i + 1 - m_tr * kTileRows;
+            if (!SL_GUARD(li >= 0 && li < kTileRows, 0x207u)) li = 0;
+            float o[P], wd[P];
+#pragma unroll
+            for (int a = 0; a < P; ++a) {
+                o[a] = srow[li * 2 * P + a];
+                wd[a] = srow[li * 2 * P + P + a];
+            }
+            float2 W[S][NQ];
+            float zc[S], zs[S];
+#pragma unroll
+            for (int q = 0; q < S; ++q) {
+                float wt[P], wp[P];
+                lagrange_theta<P>(rdth[q], o, wd, wt);
+                lagrange_phi<P>(rfph[q], wp);
+#pragma unroll
+                for (int e = 0; e < NQ; ++e) {
+                    const float w = wt[e / P] * wp[e % P];
+                    W[q][e] = make_float2(w, w);
+                }
+                sincosf(rpsr[q], &zs[q], &zc[q]);
+            }
+            int nb0 = (i - P / 2 + 1 - m_rowlo) * TW + (j - P / 2 + 1 - m_collo);
+            if (!SL_GUARD(nb0 >= 0 && nb0 + (P - 1) * TW + (P - 1) < NN && (S == 1 || rcell[S - 1] == rcell[0]),
+                          0x206u))
+                nb0 = 0;
+            // k = 0: Re S_0
+            float a0[S];
+#pragma unroll
+            for (int q = 0; q < S; ++q) a0[q] = 0.f;
+#pragma unroll
+            for (int e = 0; e < NQ; ++e) {
+                const float f = node0[nb0 + (e / P) * TW + (e % P)];
+#pragma unroll
+                for (int q = 0; q < S; ++q) a0[q] = fmaf(W[q][e].x, f, a0[q]);
+            }
+            // k = K .. 1, two at a time, Horner in z
+            float hr[S], hi_[S];
+#pragma unroll
+            for (int q = 0; q < S; ++q) hr[q] = hi_[q] = 0.f;
+            const float4 *nbp = node + (size_t)(KP - 1) * NN + nb0;
+            for (int jj = KP - 1; jj >= 0; --jj, nbp -= NN) {
+                float2 sa[S], sb2[S];
+#pragma unroll
+                for (int q = 0; q < S; ++q) sa[q] = sb2[q] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int e = 0; e < NQ; ++e) {
+                    const float4 vv = nbp[(e / P) * TW + (e % P)];
+                    const float2 lo2 = make_float2(vv.x, vv.y), hi2 = make_float2(vv.z, vv.w);
+#pragma unroll
+                    for (int q = 0; q < S; ++q) {
+                        sa[q] = __ffma2_rn(W[q][e], lo2, sa[q]);
+                        sb2[q] = __ffma2_rn(W[q][e], hi2, sb2[q]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < S; ++q) {
+                    // h <- (h z + S_{2jj+2}) z + S_{2jj+1}
+                    const float nr = fmaf(hr[q], zc[q], fmaf(-hi_[q], zs[q], sb2[q].x));
+                    const float ni = fmaf(hr[q], zs[q], fmaf(hi_[q], zc[q], sb2[q].y));
+                    hr[q] = fmaf(nr, zc[q], fmaf(-ni, zs[q], sa[q].x));
+                    hi_[q] = fmaf(nr, zs[q], fmaf(ni, zc[q], sa[q].y));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < S; ++q)
+                if (q == 0 || t0 + q < tl) {
+                    const float pz = fmaf(zc[q], hr[q], -zs[q] * hi_[q]);   // Re(z h)
+                    A.tod[sidx[q]] = fma(2.0, f2d_exact(pz), f2d_exact(a0[q]));
+                }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(rempty + 8 * rb);
+    }
+    if (!ok && lane == 0) atomicExch(A.err, 1);
+}
+
+size_t interp_f32_cells_smem_tc(const sl_plan *p, int tc) {
+    const int KP = (p->K + 1) / 2, NN = (kTileRows + p->p - 1) * (tc + p->p - 1), ncell = kTileRows * tc;
+    return 2 * ((size_t)KP * NN * sizeof(float4) + (size_t)kCellSub * sizeof(StencilRec32) +
+                (size_t)kCellSidx * sizeof(unsigned) + (size_t)(ncell + 1) * sizeof(unsigned) +
+                (size_t)NN * sizeof(float) + (size_t)kTileRows * 2 * p->p * sizeof(float)) +
+           (size_t)(2 * (ncell + 1) + 4 * ncell) * sizeof(unsigned);
 }
 
 SL_CHECK_READER(chk_interp)
@@ -409,10 +827,19 @@ sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *map
         a.ntiles = p->ntiles;
         a.ncell = fine ? kTileRows * p->geom.tile_cols : 1;
         a.tod = tod;
-        const size_t sm = interp_f32_tiled_smem(p);
+        a.err = p->d_err;
+        a.work = p->d_err ? reinterpret_cast<unsigned *>(p->d_err + 1) : nullptr;
+        if (fine) {
+            if (!a.err) return set_error(SL_ERR_ARG, "FP32 interpolation needs the plan's error flag");
+            cudaError_t me = cudaMemsetAsync(a.work, 0, sizeof(unsigned), p->stream);
+            if (me != cudaSuccess) return cuda_check(me, "work counter");
+        }
+        // cell-sorted samples (fine sort): S samples of a cell per thread; tile-keyed
+        // sort (interp_tod_noalloc): one sample per thread
+        const size_t sm = fine ? interp_f32_cells_smem_tc(p, p->geom.tile_cols) : interp_f32_tiled_smem(p);
         void (*kern)(const TiledArgs) = nullptr;
 #define SL_TILED(TCV, PV) \
-    if (p->geom.tile_cols == TCV && p->p == PV) kern = k_interp_f32_tiled<TCV, PV>;
+    if (p->geom.tile_cols == TCV && p->p == PV) kern = fine ? k_interp_f32_cells<TCV, PV> : k_interp_f32_tiled<TCV, PV>;
         SL_TILED(32, 4) SL_TILED(16, 4) SL_TILED(8, 4)
         SL_TILED(32, 2) SL_TILED(16, 2) SL_TILED(8, 2)
         SL_TILED(32, 6) SL_TILED(16, 6) SL_TILED(8, 6)

@@ -37,6 +37,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include "mbar.cuh"
 #include "sl_internal.cuh"
 
 namespace sl {
@@ -44,7 +45,6 @@ namespace sl {
 constexpr int kMsRows = 128;      // ring pairs per CTA (MMA M)
 constexpr int kMsLC = 32;         // l per chunk
 constexpr int kMsThreads = 288;   // 4 W-producer warps, 4 V-producer warps, 1 MMA warp
-constexpr unsigned long long kMsWaitNs = 1000000000ull;   // bound of every mbarrier wait: 1 s
 
 struct MsArgs {
     int L, K, ncomp, R, npairs, nrc;     // nrc: ring chunks of 128 pairs
@@ -62,8 +62,6 @@ struct MsArgs {
     int *err;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
 // Shared-memory operand descriptor: K-major, 128-byte swizzle (rows of 128 B,
 // 16-byte chunk c of row r stored at chunk c ^ (r & 7), 8-row groups 1024 B apart).
 __device__ __forceinline__ uint64_t ms_sdesc(uint32_t addr) {
@@ -76,49 +74,6 @@ __device__ __forceinline__ uint32_t ms_idesc(int m, int n) {
 }
 // float index of element (row, k) of a [rows][32] tile in that layout
 __device__ __forceinline__ int ms_sw(int row, int k) { return row * 32 + ((((k >> 2) ^ (row & 7))) << 2) + (k & 3); }
-
-constexpr unsigned kMsSuspendNs = 20000;   // suspend-time hint of one mbarrier test
-
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// One test of the phase; a thread whose phase is not complete is suspended in
-// hardware until it completes or kMsSuspendNs pass (no spinning on the issue slots
-// the producer warps need).
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, %3;\n\t"
-                 "selp.u32 %0, 1, 0, q;\n\t}"
-                 : "=r"(done) : "r"(bar), "r"(parity), "n"(kMsSuspendNs) : "memory");
-    return done != 0;
-}
-
-// Waits for the completion of the mbarrier phase of the given parity, for at
-// most limit_ns of wall time; false when the limit expired.  The wall clock is
-// read only once the first test has failed (reading it is slow).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns = kMsWaitNs) {
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer_ns();
-    for (;;) {
-        if (mbar_try(bar, parity)) return true;
-        if (globaltimer_ns() - t0 > limit_ns) return false;
-    }
-}
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(dst)), "l"(src) : "memory");
-}
-// 8-byte copy; with ok == false nothing is read and the destination is zero-filled
-__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool ok) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" :: "r"(smem_u32(dst)), "l"(src), "r"(ok ? 8 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int NPEND>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(NPEND) : "memory"); }
 
 // TF32 split: hi keeps the 19 bits the tensor core reads, lo = x - hi (exact)
 __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
@@ -159,10 +114,6 @@ constexpr int kMsNB = 2;            // operand buffers (chunks in flight)
 constexpr int kMsNS = 3;            // staging slots of the sky values per V warp (work units in flight)
 constexpr int kMsBoxX = 68;         // floats per TMA row: 34 float2 = 32 l plus the alignment slack
 constexpr int kMsStageF = 832;      // floats per staging slot: [4 skies][<= 3 components][68], 128-byte multiple
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
-}
 
 // Roles (warp-specialized; no CTA-wide barrier inside the chunk loop):
 //   warps 0-3  W producers: thread = ring pair = TMEM lane; per chunk the 32

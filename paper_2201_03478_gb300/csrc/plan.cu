@@ -111,13 +111,14 @@ static sl_status ensure_sort_capacity(sl_plan *p, int64_t n) {
     dfree(p->sort.keys);
     dfree(p->sort.perm);
     dfree(p->sort.rec);
-    p->bytes_held -= p->sort_cap * (int64_t)(2 * sizeof(unsigned) + sizeof(StencilRec64));
+    if (p->sort_cap > 0)
+        p->bytes_held -= p->sort_cap * (int64_t)(2 * sizeof(unsigned) + sizeof(StencilRec64)) + 4 * (int64_t)sizeof(unsigned);
     p->sort.keys = p->sort.perm = nullptr;
     p->sort.rec = nullptr;
     p->sort_cap = 0;
     sl_status st = dalloc_t(p, &p->sort.keys, (size_t)n, "sort keys");
     if (st != SL_OK) return st;
-    st = dalloc_t(p, &p->sort.perm, (size_t)n, "sort permutation");
+    st = dalloc_t(p, &p->sort.perm, (size_t)n + 4, "sort permutation");
     if (st != SL_OK) return st;
     st = dalloc(p, &p->sort.rec, (size_t)n * sizeof(StencilRec64), "stencil records");
     if (st != SL_OK) return st;
@@ -148,7 +149,8 @@ static void free_sort_tables(sl_plan *p) {
 // Shared memory the tile-staged kernels need at tile width tc.
 static size_t tile_smem_need(const sl_plan *p, int tc) {
     size_t need = interp_adjoint_smem_tc(p, tc);
-    if (plan_fp32(p->precision)) need = std::max(need, interp_f32_tiled_smem_tc(p, tc));
+    if (plan_fp32(p->precision))
+        need = std::max(need, std::max(interp_f32_tiled_smem_tc(p, tc), interp_f32_cells_smem_tc(p, tc)));
     if (p->precision == SL_DF64)
         need = std::max(need, std::max(interp_df_tiled_smem_tc(p, tc), interp_adjoint_df_smem_tc(p, tc)));
     return need;
@@ -554,9 +556,11 @@ sl_status sidelobe_plan_create(sl_plan **out, const sl_plan_desc *d) {
         TRY(dalloc(p, &p->d_G, p->G_bytes, "spin-Legendre scratch G"));
     }
     TRY(alloc_sort_tables(p));
-    if (p->precision == SL_TF32X3) {   // device flag of the tensor-core kernel's bounded waits
-        TRY(dalloc_t(p, &p->d_err, 1, "error flag"));
-        TRY(cuda_check(cudaMemset(p->d_err, 0, sizeof(int)), "error flag"));
+    if (plan_fp32(p->precision)) {
+        // [0]: device flag of the bounded waits (FP32 interpolation, tensor-core contraction);
+        // [1]: work counter of the FP32 interpolation
+        TRY(dalloc_t(p, &p->d_err, 2, "error flag"));
+        TRY(cuda_check(cudaMemset(p->d_err, 0, 2 * sizeof(int)), "error flag"));
     }
     TRY(cuda_check(cudaStreamSynchronize(p->stream), "plan seeds"));
     dfree(d_c2);
@@ -740,7 +744,8 @@ sl_status sl_plan_sync(sl_plan *p) {
             return st;
         if (flag) {
             cudaMemset(p->d_err, 0, sizeof(int));
-            return set_error(SL_ERR_TIMEOUT, "a bounded wait of the tensor-core contraction expired");
+            return set_error(SL_ERR_TIMEOUT, "a bounded wait inside a kernel expired (FP32 interpolation or "
+                                             "tensor-core contraction)");
         }
     }
     return SL_OK;

@@ -207,8 +207,8 @@ struct __align__(16) StencilRec32 {
 // Device buffers of one pointing sort.
 struct SortBufs {
     unsigned *keys;       // [n]
-    unsigned *perm;       // [n]
-    void *rec;            // [n] StencilRec64 or StencilRec32
+    unsigned *perm;       // [n + 4]: sorted position -> sample (the tail pads 16-byte bulk copies)
+    void *rec;            // [n] StencilRec64 or StencilRec32, by sample
     unsigned *hist;       // [nkeys + 1]: key counts, then first position of each key
     unsigned *cursor;     // [nkeys]
     unsigned *bsum;       // [nkeys / 4096 + 2]
@@ -392,6 +392,7 @@ sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *map
 size_t interp_f32_tiled_smem(const sl_plan *p);
 // Dynamic shared memory of the two tile-staged kernels for tile width tc.
 size_t interp_f32_tiled_smem_tc(const sl_plan *p, int tc);
+size_t interp_f32_cells_smem_tc(const sl_plan *p, int tc);
 size_t interp_adjoint_smem_tc(const sl_plan *p, int tc);
 // Double-float interpolation (SL_DF64 plans; k_interp_df.cu), over a sort made
 // with rec64 = 1 and with_chunks = 1.
