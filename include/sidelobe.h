@@ -258,6 +258,11 @@ sl_status interp_tod_psi(sl_plan *plan, const void *cube_psi, int npsi, const do
  *   beta, or period_start not running from 0 to n; SL_ERR_NOMEM if the
  *   scratch cannot grow. */
 sl_status sl_orbital_moments(sl_plan *plan, const double *beam, double *S);
+
+/* The quadrupole factor q of Eq. dipole_simple (Sect. 3.3): q = (a/2)(e^a + 1)/(e^a - 1),
+ * a = h nu / (k_B T0), with the exact SI values of h and k_B; nu in Hz, T0 in K.
+ * Written to *q (HOST).  SL_ERR_ARG for a NULL output or nu, T0 not finite and > 0. */
+sl_status sl_quad_factor(double nu_hz, double T0, double *q);
 sl_status orbital_dipole_tod(sl_plan *plan, const double *beam, double T0, double q, const double *theta,
                              const double *phi, const double *psi, int64_t n, const int64_t *period_start,
                              const double *beta, int64_t nper, int subsample, double *tod, int accumulate);

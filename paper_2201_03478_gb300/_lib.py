@@ -23,7 +23,7 @@ EXPORTS = ["sidelobe_plan_create", "synth_spin_maps", "interp_tod", "adjoint_tod
            "sl_plan_enable_timing", "sl_plan_kernel_stats", "sl_plan_reserve", "sl_plan_set_tile_cols", "sl_plan_set_fft_tile",
            "sl_batch_create", "sl_batch_run", "sl_batch_get_info", "sl_batch_destroy", "synth_spin_maps_multi",
            "sl_plan_selftest_timeout", "sl_orbital_moments", "orbital_dipole_tod", "synth_psi_cube", "interp_tod_psi",
-           "sl_debug_check_status", "sl_measure_alu_peak", "sl_last_error"]
+           "sl_debug_check_status", "sl_measure_alu_peak", "sl_quad_factor", "sl_last_error"]
 SL_BATCH_AUTOTUNE = 1
 
 
@@ -116,6 +116,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "orbital_dipole_tod": (I, [P, P, ctypes.c_double, ctypes.c_double, P, P, P, I64, P, P, I64, I, P, I]),
         "sl_debug_check_status": (ctypes.c_uint, []),
         "sl_measure_alu_peak": (I, [I, I, ctypes.POINTER(ctypes.c_double)]),
+        "sl_quad_factor": (I, [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
         "sl_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():

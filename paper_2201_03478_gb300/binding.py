@@ -16,7 +16,6 @@ come back in the same layouts, as d/dRe + i d/dIm of sum_i tod_i c_i.
 from __future__ import annotations
 
 import ctypes
-import math
 
 import numpy as np
 import torch
@@ -219,10 +218,10 @@ def interp_tod_psi(plan: Plan, cube_psi, theta, phi, psi, tod=None):
 
 
 def quad_factor(nu_hz: float, T0: float) -> float:
-    """The quadrupole factor of the orbital dipole: (a/2)(e^a + 1)/(e^a - 1) with
-    a = h nu / (k_B T0) (h, k_B exact SI values)."""
-    a = 6.62607015e-34 * nu_hz / (1.380649e-23 * T0)
-    return 0.5 * a * (math.exp(a) + 1.0) / math.expm1(a)
+    """The quadrupole factor of the orbital dipole (sl_quad_factor)."""
+    out = ctypes.c_double(0.0)
+    check(_lib.load().sl_quad_factor(float(nu_hz), float(T0), ctypes.byref(out)))
+    return float(out.value)
 
 
 def orbital_moments(plan: Plan, beam):

@@ -33,6 +33,8 @@
 // Between nodes the spline is w0 y_j + w1 y_{j+1} + w2 M_j + w3 M_{j+1} with
 // weights of r = t - j s only (B = r/s, A = 1 - B, w2 = (A^3 - A) s^2/6,
 // w3 = (B^3 - B) s^2/6), tabulated on the host: four FP64 operations a sample.
+#include <cmath>
+
 #include "sl_internal.cuh"
 
 namespace sl {
@@ -305,3 +307,13 @@ sl_status launch_orbital(sl_plan *p, const OrbLaunch &o) {
 SL_CHECK_READER(chk_orbital)
 
 }  // namespace sl
+
+extern "C" sl_status sl_quad_factor(double nu_hz, double T0, double *q) {
+    if (!q) return sl::set_error(SL_ERR_ARG, "sl_quad_factor: NULL output");
+    if (!(nu_hz > 0.0 && nu_hz < HUGE_VAL && T0 > 0.0 && T0 < HUGE_VAL))
+        return sl::set_error(SL_ERR_ARG, "sl_quad_factor: nu=%g and T0=%g must be finite and > 0", nu_hz, T0);
+    const double h = 6.62607015e-34, kb = 1.380649e-23;   // exact SI values
+    const double a = h * nu_hz / (kb * T0);
+    *q = 0.5 * a * (std::exp(a) + 1.0) / std::expm1(a);
+    return SL_OK;
+}
