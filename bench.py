@@ -174,6 +174,196 @@ def algorithmic_flops(L, K, R, n, p=4):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def workload_config(cfg, n, prec, highres):
+    """The `config` object of the headline workload (the same keys in both arms)."""
+    L, K = cfg["lmax"], cfg["kmax"]
+    R, nphi = cfg["ring_theta"].size, cfg["nphi"]
+    if highres:
+        workload = ("precision variant: unpolarised, lmax=%d, kmax=%d, %d rings x %d phi, %d uniform pointings "
+                    "per GPU" % (L, K, R, nphi, n))
+    else:
+        workload = ("LFI-like: polarised T/E/B, lmax=%d, kmax=%d, %d rings x %d phi, "
+                    "%d scan pointings per GPU (32.5 Hz, 1 rpm, 85 deg)" % (L, K, R, nphi, n))
+    return {"workload": workload, "lmax": L, "kmax": K, "ncomp": int(cfg["sky"].shape[0]), "nrings": R, "nphi": nphi,
+            "interp_order": 4, "samples_per_gpu": n, "precision": prec,
+            "parallelism": "replicated cube, sharded TOD",
+            "l2": "inputs larger than L2 (pointings %.1f GB, cube %.2f GB)"
+                  % (24 * n / 1e9, R * nphi * (K + 1) * (16 if prec in ("fp64", "df64") else 8) / 1e9)}
+
+
+def headline_metric(cfg, highres):
+    if highres:
+        return ("TOD samples/s (cube build+interp) at lmax=%d,kmax=%d; %%roofline; vs GPU FP64" % (cfg["lmax"], cfg["kmax"]),
+                "synthetic (seeded Gaussian sky, Gaussian-taper beam, uniform pointings)")
+    return ("TOD samples/s (cube build+interp) at lmax=1024,kmax=16; %roofline; vs GPU FP64",
+            "synthetic (seeded T/E/B sky, far-sidelobe beam, satellite scan)")
+
+
+def measure_alu(sl, device_index):
+    """Measured multiply-add peaks of this GPU (sl_measure_alu_peak), TFLOP/s."""
+    out = {}
+    for kind in ("fp64", "fp32", "fp32x2"):
+        try:
+            out[kind] = round(sl.measure_alu_peak(kind, device_index) / 1e12, 4)
+        except Exception as e:   # reported, not fatal
+            out[kind] = None
+            out["error"] = str(e)
+    out["note"] = ("8 independent multiply-add chains per thread, 8 CTAs x 256 threads per SM, best of 3 (~16 ms "
+                   "each); fp32x2 = packed two-lane FP32 multiply-add")
+    return out
+
+
+def kernel_roofs(stats, plan, prec, L, K, R, nphi, ncomp, n, alu, traffic_ok=True):
+    """Rooflines of the contraction and the interpolation from one instrumented pass
+    (the plan's per-kernel CUDA-event timers): algorithmic work per launch over the
+    average launch time, against the peak of the unit that binds it."""
+    fl_dense, fl_in = algorithmic_flops(L, K, R, n)
+    lsteps = float(plan.sizes()["lsteps"])
+    # the contraction skips the evanescent zone: count the work it executes,
+    # 11 flops (3 recurrence + 2 complex x real MACs) per visited (ring, m, k, sign, l)
+    fl_lc = 11.0 * lsteps
+    suffix = {"fp64": "f64", "fp32": "f32", "df64": "df", "tf32x3": "f32"}[prec]
+    lc_name = "lcontract_mma" if prec == "tf32x3" else "lcontract_" + suffix
+    meas = {"fp64": alu.get("fp64"), "fp32": alu.get("fp32")}
+    kernels = [
+        (lc_name,
+         {"fp64": fl_lc, "fp32": fl_lc, "df64": DF_LC_INST_PER_STEP * lsteps,
+          # tensor work executed: 3 TF32 products x 2 flops x 16 columns (4 used, one sky)
+          "tf32x3": 3 * 2.0 * 16 * lsteps}[prec],
+         {"fp64": "fp64", "fp32": "fp32", "df64": "fp32inst", "tf32x3": "tf32"}[prec]),
+        ("interp_" + suffix, float(n) * df_interp_inst(K) if prec == "df64" else fl_in,
+         {"fp64": "fp64", "fp32": "fp32", "df64": "fp32inst", "tf32x3": "fp32"}[prec]),
+    ]
+    peaks = {"fp64": (PEAK_FP64_TFLOPS, "TFLOP/s", "alu", "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz"),
+             "fp32": (PEAK_FP32_TFLOPS, "TFLOP/s", "alu", "derived: 152 SMs x 128 FFMA/clk x 2 flops x 2.07 GHz"),
+             "fp32inst": (PEAK_FP32_TINST, "Tinst/s", "alu",
+                          "derived: 152 SMs x 128 FP32 instructions/clk x 2.07 GHz (double-float arithmetic)"),
+             "tf32": (PEAK_TF32_TFLOPS, "TFLOP/s", "tensor",
+                      "measured bf16 burst (MEASURED_PEAKS.json) x nominal TF32/BF16 ratio 1.1/2.25 (of measured)")}
+    roofs = {}
+    for name, work, unit_kind in kernels:
+        if name not in stats or stats[name][0] <= 0:
+            continue
+        peak, unit, bound, note = peaks[unit_kind]
+        avg_ms = stats[name][1] / stats[name][0]
+        ach = work / (avg_ms / 1e3) / 1e12
+        r = {"bound": bound, "achieved": round(ach, 4), "peak": round(peak, 4), "unit": unit,
+             "frac": round(ach / peak, 4), "traffic": TRAFFIC.get((name, prec)) if traffic_ok else None,
+             "avg_ms": round(avg_ms, 4),
+             ("flops_per_launch" if unit == "TFLOP/s" else "fp32_inst_per_launch"): work, "peak_note": note}
+        mp = meas.get(unit_kind)
+        if mp:
+            r["frac_of_measured_alu_peak"] = round(ach / mp, 4)
+        roofs[name] = r
+    if lc_name in roofs:
+        roofs[lc_name]["flops_dense_triangle"] = fl_dense
+        roofs[lc_name]["dense_equivalent_tflops"] = round(fl_dense / (roofs[lc_name]["avg_ms"] / 1e3) / 1e12, 4)
+    # HBM side against the measured copy bandwidth: algorithmic bytes and (when taken
+    # at this size) the ncu-measured DRAM traffic per launch over the live launch time
+    hbm_peak = measured_peaks().get("hbm_gbs", 6800.0)
+    elem = 16 if prec in ("fp64", "df64") else 8
+    cube_bytes = float(R) * nphi * (K + 1) * elem
+    alg_bytes = {lc_name: float(ncomp) * plan.nalm * 16 * 2 + (K + 1) * R * (2 * L + 1) * elem,
+                 "interp_" + suffix: n * (8.0 + 8.0 + (24.0 if elem == 16 else 16.0) + 4.0) + cube_bytes}
+    for name, r in roofs.items():
+        if name in alg_bytes:
+            sec = r["avg_ms"] / 1e3
+            r["hbm"] = {"algorithmic_bytes": alg_bytes[name], "achieved_gbs": round(alg_bytes[name] / sec / 1e9, 1),
+                        "traffic_gbs": round(r["traffic"] / sec / 1e9, 1) if r.get("traffic") else None,
+                        "peak_gbs": hbm_peak, "frac": round(alg_bytes[name] / sec / 1e9 / hbm_peak, 4),
+                        "note": "interpolation bytes per sample: psi 8, TOD 8, stencil record 24 (FP32 plans "
+                                "16), permutation 4; plus the cube once; contraction: sky read once, G written once"}
+    return roofs
+
+
+def adjoint_roofs(stats, plan, K, n, alu):
+    """FP64 adjoint kernels: the interpolation transpose does the forward's
+    multiply-adds per sample (4 p^2 (K+1) + 10 flops), the contraction transpose
+    11 flops per (ring, m, k, sign, l) step of the forward's volume."""
+    lsteps = float(plan.sizes()["lsteps"])
+    out = {}
+    for name, work in (("interp_adj", float(n) * (4.0 * 16 * (K + 1) + 10.0)), ("lcontract_adj", 11.0 * lsteps)):
+        if name in stats and stats[name][0] > 0:
+            avg_ms = stats[name][1] / stats[name][0]
+            ach = work / (avg_ms / 1e3) / 1e12
+            out[name] = {"bound": "alu", "achieved": round(ach, 4), "peak": round(PEAK_FP64_TFLOPS, 4),
+                         "unit": "TFLOP/s", "frac": round(ach / PEAK_FP64_TFLOPS, 4), "avg_ms": round(avg_ms, 4),
+                         "flops_per_launch": work, "traffic": None,
+                         "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz"}
+            if alu.get("fp64"):
+                out[name]["frac_of_measured_alu_peak"] = round(ach / alu["fp64"], 4)
+    return out
+
+
+def timed_steps(step, steps, stream, device, e0, e1):
+    """Device time of `steps` calls of step() (CUDA events on the launching stream),
+    max over ranks."""
+    import torch
+    barrier(device)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return reduce_max(e0.elapsed_time(e1), device)
+
+
+def split_pass(plan, step, steps):
+    """Per-kernel times from an instrumented pass (each launch bracketed by CUDA
+    events on the plan's stream), separate from any timed region."""
+    import torch
+    torch.cuda.synchronize()
+    plan.enable_timing(True)
+    plan.kernel_stats(reset=True)
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    stats = plan.kernel_stats(reset=True)
+    plan.enable_timing(False)
+    return stats
+
+
+def multisky_leg(sl, cfg, nsky, steps, warmup, device, local):
+    """Cube builds of nsky T/E/B skies sharing the beam on the tensor cores
+    (synth_spin_maps_multi, FP32 plan), with the contraction's tensor roofline."""
+    import torch
+    import workloads as W
+    L, K, rt, nphi = cfg["lmax"], cfg["kmax"], cfg["ring_theta"], cfg["nphi"]
+    skies = torch.from_numpy(np.stack([W.sky_polarised(L, seed=s) for s in range(nsky)])).to(device)
+    beam = torch.from_numpy(cfg["beam"]).to(device)
+    plan = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=3, precision="fp32", device=local)
+    maps = torch.empty((nsky,) + plan.maps_shape(), dtype=torch.complex64, device=device)
+    stream = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step = lambda: sl.synth_spin_maps_multi(plan, skies, beam, maps)
+    for _ in range(warmup):
+        step()
+    ms = timed_steps(step, steps, stream, device, e0, e1) / steps
+    stats = split_pass(plan, step, 2)
+    plan.sync()
+    mma = stats.get("lcontract_mma", (1, 0.0))
+    mma_ms = mma[1] / max(1, mma[0])
+    nsg = (min(32, nsky) + 3) // 4 * 4
+    n_cols = 4 * nsg * ((nsky + nsg - 1) // nsg)
+    mma_flops = 3 * 2.0 * float(plan.sizes()["lsteps"]) * n_cols
+    out = {"value": nsky / (ms / 1e3), "unit": "cubes/s", "nsky": nsky, "ms_per_step": ms, "steps": steps,
+           "kernel_ms_per_step": {k: round(v[1] / 2, 4) for k, v in stats.items()}}
+    if mma_ms > 0:
+        ach = mma_flops / (mma_ms / 1e3) / 1e12
+        out["roofline"] = {"bound": "tensor", "kernel": "lcontract_mma", "achieved": round(ach, 3),
+                           "peak": round(PEAK_TF32_TFLOPS, 1), "unit": "TFLOP/s",
+                           "frac": round(ach / PEAK_TF32_TFLOPS, 4), "traffic": None, "avg_ms": round(mma_ms, 4),
+                           "tf32_flops_per_launch": mma_flops, "algorithmic_fp32_tflops": round(ach / 3, 3),
+                           "peak_note": "measured bf16 burst x nominal TF32/BF16 ratio 1.1/2.25 (of measured); "
+                                        "achieved counts 3 TF32 products x 2 flops per visited (ring pair, m, k, "
+                                        "sign, l) step and column"}
+    sl.plan_destroy(plan)
+    del skies, maps
+    torch.cuda.empty_cache()
+    return out
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -190,7 +380,8 @@ def gpu_arm(args):
     n = int(args.n)
     highres = args.workload == "highres"
     cfg = W.config_highres(with_pointings=False) if highres else W.config_lfi(with_pointings=False)
-    if args.lmax or args.nrings or args.nphi:   # smaller variants of the same workload (profiling)
+    small = bool(args.lmax or args.nrings or args.nphi)
+    if small:   # smaller variants of the same workload (profiling)
         Ls = args.lmax or cfg["lmax"]
         cfg = dict(cfg, lmax=Ls, sky=W.sky_polarised(Ls, seed=0), beam=W.beam_far_sidelobe(Ls, cfg["kmax"], seed=1),
                    ring_theta=W.equiangular_ring_theta(args.nrings or cfg["ring_theta"].size),
@@ -209,6 +400,7 @@ def gpu_arm(args):
     sky = sky_h.to(device)
     beam = beam_h.to(device)
     theta, phi, psi = (t.to(device) for t in ptg_h)
+    alu = measure_alu(sl, local) if (rank == 0 and args.alu_peaks) else {}
 
     plan = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=ncomp, precision=args.precision, device=local)
     if args.tile_cols:
@@ -217,6 +409,9 @@ def gpu_arm(args):
         plan.set_fft_tile(*(int(v) for v in args.fft_tile.split(",")))
     maps = torch.empty(plan.maps_shape(), dtype=plan.maps_dtype, device=device)
     tod = torch.empty(n, dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
 
     def step():
         sl.synth_spin_maps(plan, sky, beam, maps)
@@ -228,111 +423,40 @@ def gpu_arm(args):
     if not bool(torch.isfinite(tod).all()):
         raise RuntimeError("non-finite TOD")
 
-    stream = torch.cuda.current_stream(device)
-    plan.enable_timing(True)
-    plan.kernel_stats(reset=True)
+    # ---- the timed region: K steps, no per-launch instrumentation
     clocks = ClockSampler(local)
     if rank == 0:
         clocks.start()
         time.sleep(0.3)
-    barrier(device)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(device)
-    ms_total = e0.elapsed_time(e1)
+    ms_total = timed_steps(step, args.steps, stream, device, e0, e1)
     clk = clocks.stop() if rank == 0 else None
-    stats = plan.kernel_stats(reset=True)
-    plan.enable_timing(False)
-    ms_total = reduce_max(ms_total, device)
     ms_step = ms_total / args.steps
     value = world * n * args.steps / (ms_total / 1e3)
 
-    # ---- roofline of the two big kernels (CUDA events around each launch, same stream)
-    fl_dense, fl_in = algorithmic_flops(L, K, R, n)
-    # the contraction skips the evanescent zone: count the work it executes,
-    # 11 flops (3 recurrence + 2 complex x real MACs) per visited (ring, m, k, sign, l)
-    fl_lc = 11.0 * plan.sizes()["lsteps"]
+    # ---- per-kernel split and rooflines from a separate instrumented pass
     prec = args.precision
-    suffix = {"fp64": "f64", "fp32": "f32", "df64": "df", "tf32x3": "f32"}[prec]
-    roofs = {}
-    lc_name = "lcontract_mma" if prec == "tf32x3" else "lcontract_" + suffix
-    lsteps = float(plan.sizes()["lsteps"])
-    lc_work = {"fp64": fl_lc, "fp32": fl_lc, "df64": DF_LC_INST_PER_STEP * lsteps,
-               # tensor work executed: 3 TF32 products x 2 flops x 16 columns (4 used, one sky)
-               "tf32x3": 3 * 2.0 * 16 * lsteps}[prec]
-    kernels = [(lc_name, lc_work,
-                {"fp64": PEAK_FP64_TFLOPS, "fp32": PEAK_FP32_TFLOPS, "df64": PEAK_FP32_TINST,
-                 "tf32x3": PEAK_TF32_TFLOPS}[prec],
-                "Tinst/s" if prec == "df64" else "TFLOP/s"),
-               ("interp_" + suffix, fl_in if prec != "df64" else float(n) * df_interp_inst(K),
-                PEAK_FP32_TINST if prec == "df64" else (PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS),
-                "Tinst/s" if prec == "df64" else "TFLOP/s")]
-    for name, fl, peak, unit in kernels:
-        if name in stats and stats[name][0] > 0:
-            avg_ms = stats[name][1] / stats[name][0]
-            ach = fl / (avg_ms / 1e3) / 1e12
-            roofs[name] = {"bound": "tensor" if name == "lcontract_mma" else "alu", "achieved": round(ach, 4),
-                           "peak": round(peak, 4),
-                           "unit": unit, "frac": round(ach / peak, 4),
-                           "traffic": None if highres else TRAFFIC.get((name, prec)),
-                           "avg_ms": round(avg_ms, 4),
-                           ("flops_per_launch" if unit == "TFLOP/s" else "fp32_inst_per_launch"): fl,
-                           "peak_note": ("measured bf16 burst x nominal TF32/BF16 ratio (of measured)"
-                                         if name == "lcontract_mma" else
-                                         "derived from unit counts x 2.07 GHz max SM clock")}
-    if lc_name in roofs:
-        roofs[lc_name]["flops_dense_triangle"] = fl_dense
-        roofs[lc_name]["dense_equivalent_tflops"] = round(fl_dense / (roofs[lc_name]["avg_ms"] / 1e3) / 1e12, 4)
-    # HBM side of both kernels against the measured copy bandwidth: algorithmic bytes and
-    # the ncu-measured DRAM traffic per launch over the live launch time (the ALU roof binds)
-    hbm_peak = measured_peaks().get("hbm_gbs", 6800.0)
-    elem = 16 if prec in ("fp64", "df64") else 8
-    cube_bytes = float(R) * nphi * (K + 1) * elem
-    alg_bytes = {lc_name: float(ncomp) * plan.nalm * 16 * 2 + (K + 1) * R * (2 * L + 1) * elem,
-                 "interp_" + suffix: n * (8.0 + 8.0 + (24.0 if elem == 16 else 16.0) + 4.0) + cube_bytes}
-    for name, r in roofs.items():
-        if name in alg_bytes:
-            sec = r["avg_ms"] / 1e3
-            r["hbm"] = {"algorithmic_bytes": alg_bytes[name], "achieved_gbs": round(alg_bytes[name] / sec / 1e9, 1),
-                        "traffic_gbs": round(r["traffic"] / sec / 1e9, 1) if r.get("traffic") else None,
-                        "peak_gbs": hbm_peak, "frac": round(alg_bytes[name] / sec / 1e9 / hbm_peak, 4),
-                        "note": "interpolation bytes per sample: psi 8, TOD 8, stencil record 24 (FP32 plans "
-                                "16), permutation 4; plus the cube once; contraction: sky read once, G written once"}
+    stats = split_pass(plan, step, args.split_steps)
+    roofs = kernel_roofs(stats, plan, prec, L, K, R, nphi, ncomp, n, alu, traffic_ok=not (highres or small))
     dominant = max(stats.items(), key=lambda kv: kv[1][1])[0] if stats else None
     shares = {k: round(v[1] / max(1e-9, sum(x[1] for x in stats.values())), 4) for k, v in stats.items()}
-    launches = sum(v[0] for v in stats.values())
+    launches_per_step = sum(v[0] for v in stats.values()) / max(1, args.split_steps)
 
-    if highres:
-        metric = "TOD samples/s (cube build+interp) at lmax=%d,kmax=%d; %%roofline; vs GPU FP64" % (L, K)
-        data = "synthetic (seeded Gaussian sky, Gaussian-taper beam, uniform pointings)"
-        workload = ("precision variant: unpolarised, lmax=%d, kmax=%d, %d rings x %d phi, %d uniform pointings "
-                    "per GPU" % (L, K, R, nphi, n))
-    else:
-        metric = "TOD samples/s (cube build+interp) at lmax=1024,kmax=16; %roofline; vs GPU FP64"
-        data = "synthetic (seeded T/E/B sky, far-sidelobe beam, satellite scan)"
-        workload = ("LFI-like: polarised T/E/B, lmax=%d, kmax=%d, %d rings x %d phi, "
-                    "%d scan pointings per GPU (32.5 Hz, 1 rpm, 85 deg)" % (L, K, R, nphi, n))
+    metric, data = headline_metric(cfg, highres)
+    config = workload_config(cfg, n, prec, highres)
     out = {
         "metric": metric,
         "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE[prec],
         "data": data,
-        "config": {"workload": workload,
-                   "lmax": L, "kmax": K, "ncomp": ncomp, "nrings": R, "nphi": nphi, "interp_order": 4,
-                   "tile_cols": plan.sizes()["tile_cols"],
-                   "fft_tile": [plan.sizes()["fft_rings"], plan.sizes()["fft_korders"]],
-                   "samples_per_gpu": n, "precision": prec, "parallelism": "replicated cube, sharded TOD",
-                   "l2": "inputs larger than L2 (pointings %.1f GB, cube %.2f GB)" % (24 * n / 1e9,
-                                                                                       plan.sizes()["maps_bytes"] / 1e9)},
-        "gpu_launches": int(launches),
-        "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in stats.items()},
+        "config": config,
+        "tuning": {"tile_cols": plan.sizes()["tile_cols"],
+                   "fft_tile": [plan.sizes()["fft_rings"], plan.sizes()["fft_korders"]]},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "kernel_split": {"steps": args.split_steps,
+                         "note": "per-kernel times from a separate pass with each launch bracketed by CUDA events; "
+                                 "the timed region runs without them"},
+        "kernel_ms_per_step": {k: round(v[1] / args.split_steps, 4) for k, v in stats.items()},
         "kernel_share": shares,
         "dominant_kernel": dominant,
         "roofline": roofs.get(dominant) if dominant in roofs else (next(iter(roofs.values())) if roofs else None),
@@ -340,29 +464,24 @@ def gpu_arm(args):
     }
     if rank == 0:
         out["clocks"] = clk
+        out["alu_peaks_measured"] = alu
 
     # ---- adjoint (gradients of sum_i y_i c_i w.r.t. sky and beam) on the same pointings
     if args.adjoint_steps > 0:
         gs = torch.zeros_like(sky)
         gb = torch.zeros_like(beam)
         y = tod.clone()
-        sl.adjoint_tod_sharded(plan, theta, phi, psi, y, sky, beam, gs, gb)  # warm (allocates scratch)
+        adj = lambda: sl.adjoint_tod_sharded(plan, theta, phi, psi, y, sky, beam, gs, gb)
+        adj()   # warm (allocates scratch)
         torch.cuda.synchronize()
-        plan.enable_timing(True)
-        plan.kernel_stats(reset=True)
-        barrier(device)
-        e0.record(stream)
-        for _ in range(args.adjoint_steps):
-            # each rank's stretch of the scan; the gradients summed over ranks (one all-reduce)
-            sl.adjoint_tod_sharded(plan, theta, phi, psi, y, sky, beam, gs, gb)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_adj = reduce_max(e0.elapsed_time(e1), device) / args.adjoint_steps
-        st_adj = plan.kernel_stats(reset=True)
-        plan.enable_timing(False)
+        # each rank's stretch of the scan; the gradients summed over ranks (one all-reduce)
+        ms_adj = timed_steps(adj, args.adjoint_steps, stream, device, e0, e1) / args.adjoint_steps
+        st_adj = split_pass(plan, adj, 1)
         out["adjoint"] = {"value": world * n / (ms_adj / 1e3), "unit": "samples/s", "ms_per_step": ms_adj,
                           "steps": args.adjoint_steps, "precision": "df64" if prec == "df64" else "fp64",
-                          "kernel_ms_per_step": {k: round(v[1] / args.adjoint_steps, 4) for k, v in st_adj.items()}}
+                          "kernel_ms_per_step": {k: round(v[1], 4) for k, v in st_adj.items()}}
+        if prec != "df64":
+            out["adjoint"]["roofline_kernels"] = adjoint_roofs(st_adj, plan, K, n, alu)
         del gs, gb, y
 
     # ---- the other precisions on the same box, compared with this run's TOD
@@ -378,18 +497,22 @@ def gpu_arm(args):
             sl.interp_tod(p2, maps2, theta, phi, psi, tod2)
         for _ in range(args.warmup):
             step2()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            step2()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms2 = e0.elapsed_time(e1) / args.steps
+        ms2 = timed_steps(step2, args.steps, stream, device, e0, e1) / args.steps
+        st2 = split_pass(p2, step2, args.split_steps)
         err = float(torch.linalg.vector_norm(tod2 - tod) / torch.linalg.vector_norm(tod))
-        out["other_precisions"].append({"precision": other, "dtype": DTYPE[other], "value": n / (ms2 / 1e3),
-                                        "unit": "samples/s", "ms_per_step": ms2,
-                                        "rate_vs_%s" % prec: ms_step / ms2, "tod_rel_l2_vs_%s" % prec: err})
+        out["other_precisions"].append({
+            "precision": other, "dtype": DTYPE[other], "value": n / (ms2 / 1e3), "unit": "samples/s",
+            "ms_per_step": ms2, "rate_vs_%s" % prec: ms_step / ms2, "tod_rel_l2_vs_%s" % prec: err,
+            "kernel_ms_per_step": {k: round(v[1] / args.split_steps, 4) for k, v in st2.items()},
+            "roofline_kernels": kernel_roofs(st2, p2, other, L, K, R, nphi, ncomp, n, alu,
+                                             traffic_ok=not (highres or small))})
+        sl.plan_destroy(p2)
         del maps2, tod2, p2
+        torch.cuda.empty_cache()
+
+    # ---- many skies with one beam on the tensor cores (the posterior-sample workload)
+    if args.multisky_leg > 0 and rank == 0 and world == 1 and not highres:
+        out["multisky"] = multisky_leg(sl, cfg, args.multisky_leg, max(3, args.steps // 2), args.warmup, device, local)
 
     # ---- end to end through the public API from pinned host buffers
     if args.e2e_steps > 0:
@@ -1090,6 +1213,12 @@ def cpu_baseline(cfg, th, ph, ps, n, args):
 
 
 def reference_arm(args):
+    """The oracle timed on the host cores, each step a bounded sample of the
+    workload (the spin Legendre step + DFT on a subset of rings, the
+    interpolation of a subset of samples).  `ms_per_step` is the time one such
+    step took; `value` is the metric for the full workload, extrapolated from
+    the sample (the per-ring and per-sample costs are uniform), with the
+    extrapolated full-step time beside it."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -1101,36 +1230,28 @@ def reference_arm(args):
     th, ph, ps = W.pointings_uniform(sn, seed=2) if highres else W.pointings_scan(sn)
     for _ in range(args.warmup):
         oracle_sample(cfg, th, ph, ps, n, 4, min(sn, 100000))
-    per = []
-    t_meas = 0.0
+    per, meas = [], []
     for _ in range(args.steps):
         full, det = oracle_sample(cfg, th, ph, ps, n, args.ref_rings, sn)
         per.append(full)
-        t_meas += det["cube_s"] + det["interp_s"]
+        meas.append(det["cube_s"] + det["interp_s"])
     full = float(np.mean(per))
     value = world * n / full
-    L, K, R = cfg["lmax"], cfg["kmax"], cfg["ring_theta"].size
-    if highres:
-        metric = "TOD samples/s (cube build+interp) at lmax=%d,kmax=%d; %%roofline; vs GPU FP64" % (L, K)
-        data = "synthetic (seeded Gaussian sky, Gaussian-taper beam, uniform pointings)"
-        workload = ("precision variant: unpolarised, lmax=%d, kmax=%d, %d rings x %d phi, %d uniform pointings "
-                    "per GPU" % (L, K, R, cfg["nphi"], n))
-    else:
-        metric = "TOD samples/s (cube build+interp) at lmax=1024,kmax=16; %roofline; vs GPU FP64"
-        data = "synthetic (seeded T/E/B sky, far-sidelobe beam, satellite scan)"
-        workload = ("LFI-like: polarised T/E/B, lmax=%d, kmax=%d, %d rings x %d phi, "
-                    "%d scan pointings per GPU (32.5 Hz, 1 rpm, 85 deg)" % (L, K, R, cfg["nphi"], n))
+    R = cfg["ring_theta"].size
+    metric, data = headline_metric(cfg, highres)
     out = {"impl": "reference", "metric": metric,
            "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": full * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64", "data": data,
-           "config": {"workload": workload, "precision": "fp64"},
+           "ms_per_step": float(np.mean(meas)) * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": data,
+           "config": workload_config(cfg, n, "fp64", highres),
+           "extrapolated_ms_per_full_step": full * 1e3,
+           "sample_per_step": {"rings": args.ref_rings, "of_rings": R, "samples": sn, "of_samples": n},
            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
                             "sample": "each step: oracle spin Legendre step + DFT on %d of %d rings and "
-                                      "interpolation of %d samples, extrapolated to a full step"
-                                      % (args.ref_rings, R, sn)},
+                                      "interpolation of %d of %d samples (%.2f s measured per step); value "
+                                      "extrapolated to the full step" % (args.ref_rings, R, sn, n, float(np.mean(meas)))},
            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-           "measured_seconds": t_meas}
+           "measured_seconds": float(np.sum(meas))}
     print(json.dumps(out), flush=True)
 
 
@@ -1159,7 +1280,13 @@ def main(argv=None):
     ap.add_argument("--fft-tile", default="", help="rings,korders per CTA of the ring FFT (e.g. 2,1; default: the plan's)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--n", type=float, default=0, help="pointings per GPU (default 1e8; 2e8 for highres)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--split-steps", type=int, default=3,
+                    help="steps of the separate instrumented pass that gives the per-kernel split")
+    ap.add_argument("--multisky-leg", type=int, default=32,
+                    help="skies of the tensor-core multi-sky leg of the headline line (0: skip)")
+    ap.add_argument("--no-alu-peaks", dest="alu_peaks", action="store_false",
+                    help="skip the measured ALU peaks (sl_measure_alu_peak)")
     ap.add_argument("--adjoint-steps", type=int, default=3, help="timed adjoint_tod calls (0: skip)")
     ap.add_argument("--no-compare", dest="compare", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -1,7 +1,9 @@
 """The benchmark's reference arm (the CPU oracle timed on the host's cores) on a
 tiny sample: it runs without a GPU and prints one JSON line with the contract's
 keys -- impl, the headline metric and unit, the step count, a cpu_baseline that
-says what was timed, and an e2e object with no host/device copies."""
+says what was timed, and an e2e object with no host/device copies.  Its config
+is the GPU arm's (same keys and values), and ms_per_step is the time a step
+actually took (the extrapolation to the full workload has its own key)."""
 import json
 import os
 import subprocess
@@ -28,3 +30,9 @@ def test_reference_arm_prints_the_contract_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    assert abs(d["ms_per_step"] * d["steps"] / 1e3 - d["measured_seconds"]) < 1e-6 * max(1.0, d["measured_seconds"])
+    assert d["extrapolated_ms_per_full_step"] >= d["ms_per_step"]
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    assert d["config"] == bench.workload_config(W.config_lfi(with_pointings=False), int(1e8), "fp64", False)
