@@ -28,8 +28,9 @@
 // 28% of the (ring, m, l) volume at lmax = 1024) is not run at all.
 //
 // FP64 plans: one thread per (north ring, sign of k): per l, 2 FP64 operations
-// for the recurrence and 4 for the two complex x real sums.  FP32 plans: one
-// thread per (two adjacent north rings, sign); the recurrence in the
+// for the recurrence and 4 for the two complex x real sums.  FP32 plans: eight
+// ring pairs per thread of one sign, two at a time in the lanes of packed FP32x2
+// instructions (k_lcontract_f32); the recurrence in the
 // difference form  D_{l+1} = (c'_l - a'_l y) y_l + D_l,  y_{l+1} = y_l + D_{l+1}
 // with y = 1 - cos(theta) and c' = a' -+ b' - 2 formed in double (keeps the
 // FP32 recurrence accurate near the pole, where cos theta alone carries too
@@ -38,8 +39,10 @@
 // and the sums in double-float arithmetic (df.cuh): per l, two double-float
 // products and two sums for the recurrence and four double-float
 // multiply-accumulates, all on the FP32 pipes.
-// The CTA stages the coefficients of a chunk of l in shared memory (double
-// buffered in FP32); a thread steps only from its own start l.
+// FP64 and DF64: the CTA stages the coefficients of a chunk of l in shared
+// memory and a thread steps only from its own start l.  FP32: each warp stages
+// its own coefficients, 32 l at a time, and steps from its earliest start
+// (recurrences not yet started hold an exact zero state).
 #include <algorithm>
 
 #include "df.cuh"
@@ -49,7 +52,9 @@ namespace sl {
 
 constexpr int kNT = 256;          // threads per CTA
 constexpr int kHalf = kNT / 2;    // threads per sign
-constexpr int kF32Pairs = 4;      // ring pairs per thread of the FP32 contraction
+constexpr int kF32Pairs = 8;      // ring pairs per thread of the FP32 contraction (4 packed pairs)
+constexpr int kNT32 = 128;        // threads per CTA of the FP32 contraction (64 per sign of k):
+constexpr int kHalf32 = kNT32 / 2;   // 512 ring pairs per CTA, the LFI-like grid's northern rings
 constexpr int kLC64 = 64;         // l values staged per chunk (FP64)
 
 struct __align__(16) Coef64 {
@@ -216,11 +221,16 @@ __device__ __forceinline__ void stage_load(const LcArgs &a, const RTab32 *tab, i
     }
 }
 
-struct __align__(16) Acc32 {
-    float2 ap, sam, am, sap;
+// Per staged l and sign of k, what a step needs: (-a', c') with c' = c'+ for
+// +k and c'- for -k, and the two sums' coefficients (ap, sam) for +k, (am, sap)
+// for -k.  Threads of a warp read the same l: three 8-byte broadcasts per l
+// (16-byte broadcasts of pre-duplicated values cost more shared-memory
+// wavefronts than the register moves they save).
+struct __align__(8) Stage32x2 {
+    float2 r, c1, c2;
 };
 
-__device__ __forceinline__ void stage_store(const Stage32 &st, int l, float4 *rc, Acc32 *ac) {
+__device__ __forceinline__ void stage_store(const Stage32 &st, int l, Stage32x2 *plus, Stage32x2 *minus) {
     float2 ap = {0.f, 0.f}, am = {0.f, 0.f};
 #pragma unroll
     for (int X = 0; X < 3; ++X) {
@@ -231,100 +241,169 @@ __device__ __forceinline__ void stage_store(const Stage32 &st, int l, float4 *rc
         am.y -= s.y * b.x + s.x * b.y;
     }
     const float c = st.t.c, sc = (l & 1) ? -c : c;
-    *rc = make_float4(st.t.a, st.t.cp, st.t.cm, 0.f);
-    *ac = Acc32{make_float2(c * ap.x, c * ap.y), make_float2(sc * am.x, sc * am.y),
-                make_float2(c * am.x, c * am.y), make_float2(sc * ap.x, sc * ap.y)};
+    const float na = -st.t.a;
+    *plus = Stage32x2{make_float2(na, st.t.cp), make_float2(c * ap.x, c * ap.y), make_float2(sc * am.x, sc * am.y)};
+    *minus = Stage32x2{make_float2(na, st.t.cm), make_float2(c * am.x, c * am.y), make_float2(sc * ap.x, sc * ap.y)};
 }
 
-struct Rec32 {
-    float yc, y, D;
-    int ls;
-    float2 acc1, acc2;
+// Two recurrences (two ring pairs of one sign) in the two lanes of packed FP32
+// pairs: every operation below is one two-lane instruction (__ffma2_rn,
+// __fadd2_rn) doing what the scalar form does per lane, with the same rounding.
+struct Rec32x2 {
+    float2 yc, y, D;                  // 1 - cos theta, value, difference
+    float2 a1r, a1i, a2r, a2i;        // the two complex sums, split into re and im pairs
+    float2 ys, Ds;                    // start states, injected at the start l
+    int ls0, ls1;                     // start l of each lane (L + 1: never)
 };
 
-__device__ __forceinline__ void rec32_step(Rec32 &s, float ra, float rc_, float2 c1, float2 c2) {
-    s.acc1.x = fmaf(c1.x, s.y, s.acc1.x);
-    s.acc1.y = fmaf(c1.y, s.y, s.acc1.y);
-    s.acc2.x = fmaf(c2.x, s.y, s.acc2.x);
-    s.acc2.y = fmaf(c2.y, s.y, s.acc2.y);
-    s.D = fmaf(fmaf(-ra, s.yc, rc_), s.y, s.D);
-    s.y += s.D;
+// One l step; the per-l values come duplicated into both lanes.
+struct Coef32x2 {
+    float2 na, cr, c1r, c1i, c2r, c2i;
+};
+
+__device__ __forceinline__ Coef32x2 coef32x2(const Stage32x2 &v) {
+    return Coef32x2{make_float2(v.r.x, v.r.x), make_float2(v.r.y, v.r.y), make_float2(v.c1.x, v.c1.x),
+                    make_float2(v.c1.y, v.c1.y), make_float2(v.c2.x, v.c2.x), make_float2(v.c2.y, v.c2.y)};
 }
 
-// PPT ring pairs per thread (consecutive pairs): each staged coefficient load
-// feeds PPT recurrence steps.
+__device__ __forceinline__ void rec32x2_step(Rec32x2 &s, const Coef32x2 &c) {
+    // sums with y_l: re/im of c1 y, c2 y
+    s.a1r = __ffma2_rn(c.c1r, s.y, s.a1r);
+    s.a1i = __ffma2_rn(c.c1i, s.y, s.a1i);
+    s.a2r = __ffma2_rn(c.c2r, s.y, s.a2r);
+    s.a2i = __ffma2_rn(c.c2i, s.y, s.a2i);
+    // D_{l+1} = (c' - a' y_c) y_l + D_l,  y_{l+1} = y_l + D_{l+1}
+    const float2 t = __ffma2_rn(c.na, s.yc, c.cr);
+    s.D = __ffma2_rn(t, s.y, s.D);
+    s.y = __fadd2_rn(s.y, s.D);
+}
+
+// PPT ring pairs per thread, two per packed recurrence.  A warp owns 32 * PPT
+// consecutive ring pairs of one sign of k; packed pair q of lane j holds pairs
+// base + 64 q + j (low lane) and base + 64 q + 32 + j (high lane), so that the
+// 32 lanes of one packed pair cover 64 neighbouring rings, whose recurrences
+// start at similar l (the start moves with the ring's distance from the pole).
+// Until its start l a recurrence holds an exact zero state (it then adds exact
+// zeros to its sums), and at the start l its start state is injected; packed
+// pair q is not stepped at all before the earliest start among its lanes (a
+// warp-uniform test), and the loop bounds are the warp's earliest and latest
+// starts, so the lanes never diverge.  Each warp stages its own coefficients,
+// 32 l at a time (one l per lane, double-buffered, the next batch loaded while
+// the current one is used): no CTA-wide barrier, every warp runs from its own
+// first start.  Each coefficient load from shared memory feeds PPT recurrence
+// steps.
 template <int PPT>
-__global__ void __launch_bounds__(kNT) k_lcontract_f32(const LcArgs a) {
-    __shared__ float4 rc[2][kNT];   // a', c'+, c'-, unused
-    __shared__ Acc32 ac[2][kNT];
+__global__ void __launch_bounds__(kNT32, 4) k_lcontract_f32(const LcArgs a) {
+    constexpr int NP = PPT / 2;
+    __shared__ Stage32x2 stg[kNT32 / 32][2][32];   // [warp][buffer][l in batch]
     int m, k, pc;
     block_mk(a, m, k, pc);
-    const int neg = threadIdx.x >= kHalf;
-    const int p0 = pc * (PPT * kHalf) + PPT * (threadIdx.x & (kHalf - 1));
+    const int neg = threadIdx.x >= kHalf32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wsign = (threadIdx.x & (kHalf32 - 1)) >> 5;
+    const int base = pc * (PPT * kHalf32) + wsign * (32 * PPT);
     const int64_t moff = (int64_t)m * (2 * a.L + 1 - m) / 2;
     const RTab32 *tab = a.tab32 + (int64_t)k * a.nalm + moff;
 
-    Rec32 S[PPT];
+    Rec32x2 S[NP];
+    int qmin[NP];   // earliest start among the lanes of packed pair q (warp-uniform)
     int lme = a.L + 1, lmx = 0;
 #pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-        S[q].ls = a.L + 1;
-        S[q].acc1 = S[q].acc2 = make_float2(0.f, 0.f);
-        S[q].y = S[q].D = S[q].yc = 0.f;
-        if (p0 + q < a.npairs) {
-            const int64_t si = start_index(a, k, m, neg, p0 + q);
-            S[q].ls = a.ls[si];
-            const float2 st2 = a.st32[si];
-            S[q].y = st2.x;
-            S[q].D = st2.y;
-            S[q].yc = a.y32[p0 + q];
+    for (int q = 0; q < NP; ++q) {
+        float st[2][3];
+        int ls[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int pair = base + 64 * q + 32 * h + lane;
+            ls[h] = a.L + 1;
+            st[h][0] = st[h][1] = st[h][2] = 0.f;
+            if (pair < a.npairs) {
+                const int64_t si = start_index(a, k, m, neg, pair);
+                ls[h] = a.ls[si];
+                const float2 st2 = a.st32[si];
+                st[h][0] = st2.x;
+                st[h][1] = st2.y;
+                st[h][2] = a.y32[pair];
+            }
         }
-        lme = min(lme, S[q].ls);
-        lmx = max(lmx, S[q].ls);
+        S[q].ls0 = ls[0];
+        S[q].ls1 = ls[1];
+        S[q].ys = make_float2(st[0][0], st[1][0]);
+        S[q].Ds = make_float2(st[0][1], st[1][1]);
+        S[q].yc = make_float2(st[0][2], st[1][2]);
+        S[q].y = S[q].D = make_float2(0.f, 0.f);
+        S[q].a1r = S[q].a1i = S[q].a2r = S[q].a2i = make_float2(0.f, 0.f);
+        qmin[q] = __reduce_min_sync(0xffffffffu, min(ls[0], ls[1]));
+        lme = min(lme, qmin[q]);
+        lmx = max(lmx, max(ls[0], ls[1]));
     }
-    const int lstart = block_min(lme);
-    const int cofs = neg ? 2 : 0;
+    lmx = __reduce_max_sync(0xffffffffu, lmx);
     Stage32 st;
-    {
-        const int l = lstart + (int)threadIdx.x;
-        if (l <= a.L) {
-            stage_load(a, tab, moff, m, k, l, st);
-            stage_store(st, l, &rc[0][threadIdx.x], &ac[0][threadIdx.x]);
-        }
+    Stage32x2 dummy;
+    auto stage_mine = [&](int l, Stage32x2 *dst) {   // this warp's sign only
+        if (neg) stage_store(st, l, &dummy, dst);
+        else stage_store(st, l, dst, &dummy);
+    };
+    if (lme + lane <= a.L) {
+        stage_load(a, tab, moff, m, k, lme + lane, st);
+        stage_mine(lme + lane, &stg[warp][0][lane]);
     }
     int buf = 0;
-    for (int c0 = lstart; c0 <= a.L; c0 += kNT, buf ^= 1) {
-        const int nc = min(kNT, a.L - c0 + 1);
-        const int ln = c0 + kNT + (int)threadIdx.x;   // this thread's l in the next chunk
+    for (int c0 = lme; c0 <= a.L; c0 += 32, buf ^= 1) {
+        const int nc = min(32, a.L - c0 + 1);
+        const int ln = c0 + 32 + lane;   // this lane's l in the next batch
         const bool next = ln <= a.L;
         if (next) stage_load(a, tab, moff, m, k, ln, st);
-        __syncthreads();
-        const float4 *rcv = rc[buf];
-        // (c1, c2) = (ap, sam) for +k, (am, sap) for -k: one 16-byte load each step
-        const float4 *acv = reinterpret_cast<const float4 *>(ac[buf]) + (cofs >> 1);
-        int i = max(0, lme - c0);
-        // until every ring of the thread has started
-        for (; i < nc && c0 + i < lmx; ++i) {
-            const float4 r = rcv[i], cc = acv[2 * i];
-            const float ra = r.x, rcc = neg ? r.z : r.y;    // c'- for -k, c'+ for +k
-            const float2 c1 = make_float2(cc.x, cc.y), c2 = make_float2(cc.z, cc.w);
+        __syncwarp();
+        const Stage32x2 *sv = stg[warp][buf];
+        int i = 0;
+        // until every recurrence of the warp has started (up to and including the
+        // last start l): inject start states; skip packed pairs none of whose lanes started
+        for (; i < nc && c0 + i <= lmx; ++i) {
+            const int l = c0 + i;
+            const Coef32x2 c = coef32x2(sv[i]);
 #pragma unroll
-            for (int q = 0; q < PPT; ++q)
-                if (c0 + i >= S[q].ls) rec32_step(S[q], ra, rcc, c1, c2);
+            for (int q = 0; q < NP; ++q) {
+                if (l < qmin[q]) continue;
+                if (l == S[q].ls0) { S[q].y.x = S[q].ys.x; S[q].D.x = S[q].Ds.x; }
+                if (l == S[q].ls1) { S[q].y.y = S[q].ys.y; S[q].D.y = S[q].Ds.y; }
+                rec32x2_step(S[q], c);
+            }
         }
 #pragma unroll 2
         for (; i < nc; ++i) {
-            const float4 r = rcv[i], cc = acv[2 * i];
-            const float ra = r.x, rcc = neg ? r.z : r.y;    // c'- for -k, c'+ for +k
-            const float2 c1 = make_float2(cc.x, cc.y), c2 = make_float2(cc.z, cc.w);
+            const Coef32x2 c = coef32x2(sv[i]);
+            // the step of rec32x2_step, stage by stage across the packed pairs (independent
+            // instructions between each producer and its consumer)
+            float2 t[NP];
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) rec32_step(S[q], ra, rcc, c1, c2);
+            for (int q = 0; q < NP; ++q) t[q] = __ffma2_rn(c.na, S[q].yc, c.cr);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                S[q].a1r = __ffma2_rn(c.c1r, S[q].y, S[q].a1r);
+                S[q].a1i = __ffma2_rn(c.c1i, S[q].y, S[q].a1i);
+            }
+#pragma unroll
+            for (int q = 0; q < NP; ++q) S[q].D = __ffma2_rn(t[q], S[q].y, S[q].D);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                S[q].a2r = __ffma2_rn(c.c2r, S[q].y, S[q].a2r);
+                S[q].a2i = __ffma2_rn(c.c2i, S[q].y, S[q].a2i);
+            }
+#pragma unroll
+            for (int q = 0; q < NP; ++q) S[q].y = __fadd2_rn(S[q].y, S[q].D);
         }
-        if (next) stage_store(st, ln, &rc[buf ^ 1][threadIdx.x], &ac[buf ^ 1][threadIdx.x]);
+        __syncwarp();   // the batch is read before the other buffer is overwritten next time round
+        if (next) stage_mine(ln, &stg[warp][buf ^ 1][lane]);
     }
 #pragma unroll
-    for (int q = 0; q < PPT; ++q)
-        if (p0 + q < a.npairs) write_two<float2>(a, m, k, p0 + q, neg, S[q].acc1, S[q].acc2);
+    for (int q = 0; q < NP; ++q) {
+        const int pair = base + 64 * q + lane;
+        if (pair < a.npairs)
+            write_two<float2>(a, m, k, pair, neg, make_float2(S[q].a1r.x, S[q].a1i.x), make_float2(S[q].a2r.x, S[q].a2i.x));
+        if (pair + 32 < a.npairs)
+            write_two<float2>(a, m, k, pair + 32, neg, make_float2(S[q].a1r.y, S[q].a1i.y),
+                              make_float2(S[q].a2r.y, S[q].a2i.y));
+    }
 }
 
 // ------------------------------------------------------------------ DF64
@@ -463,7 +542,8 @@ sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
     a.R = p->R;
     a.npairs = p->npairs;
     a.ppt = (p->precision == SL_FP64) ? 1 : (p->precision == SL_DF64 ? 2 : kF32Pairs);
-    a.nchunk = (p->npairs + a.ppt * kHalf - 1) / (a.ppt * kHalf);
+    const int half = plan_fp32(p->precision) ? kHalf32 : kHalf;   // ring pairs per sign of a CTA / ppt
+    a.nchunk = (p->npairs + a.ppt * half - 1) / (a.ppt * half);
     a.nalm = p->nalm;
     a.sky = (const double2 *)sky;
     a.beam = (const double2 *)beam;
@@ -493,7 +573,7 @@ sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
         k_to_f32<<<(unsigned)std::min<int64_t>((nb + 255) / 256, 4096), 256, 0, p->stream>>>(
             (const double2 *)beam, p->d_beam32, nb);
         slot = timing_begin(p, "lcontract_f32");
-        k_lcontract_f32<kF32Pairs><<<(unsigned)nblk, kNT, 0, p->stream>>>(a);
+        k_lcontract_f32<kF32Pairs><<<(unsigned)nblk, kNT32, 0, p->stream>>>(a);
     }
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_lcontract launch");
