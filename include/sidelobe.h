@@ -287,6 +287,7 @@ typedef struct {
     int64_t tile_cols;     /* phi columns per sort tile (the tile is 4 rows high) */
     int64_t fft_rings;     /* rings x k orders one CTA of the ring FFT transforms */
     int64_t fft_korders;   /* (both 0 when the rings need the cluster form) */
+    int64_t contraction_pairs;   /* SL_FP32 plans: ring pairs per thread of the contraction (else 0) */
 } sl_plan_sizes;
 sl_status sl_plan_get_sizes(const sl_plan *plan, sl_plan_sizes *out);
 
@@ -317,6 +318,15 @@ sl_status sl_plan_set_tile_cols(sl_plan *plan, int tile_cols);
  * when rings x korders transforms of nphi values do not fit in one CTA's shared
  * memory, or when the rings are long enough to need the cluster form. */
 sl_status sl_plan_set_fft_tile(sl_plan *plan, int rings, int korders);
+
+/* SL_FP32 plans: how many ring pairs (2, 4 or 8) each thread of the
+ * l-contraction of synth_spin_maps steps together, i.e. 128, 256 or 512 ring
+ * pairs per CTA (Sect. 2.1, Eqs. c_m and S: the spin "Legendre" step); 0
+ * restores the automatic choice (the variant that leaves the fewest threads
+ * idle for the plan's rings).  Results do not depend on it (the same
+ * arithmetic per recurrence); speed does.  SL_ERR_ARG for other values;
+ * SL_ERR_UNSUPPORTED for a nonzero value on plans of other precisions. */
+sl_status sl_plan_set_contraction_pairs(sl_plan *plan, int pairs);
 
 /* Synchronises the plan's stream; reports device faults as SL_ERR_CUDA and an
  * expired bounded wait inside a kernel (synth_spin_maps_multi) as
@@ -383,7 +393,16 @@ typedef struct {
     double *tod;                          /* device [n] (written) */
 } sl_batch_item;
 
-enum { SL_BATCH_AUTOTUNE = 1 };
+/* SL_BATCH_PERSISTENT: the persistent form -- persistent launches for every
+ * detector's l-contraction (one per number of ring pairs per thread among the
+ * detectors, side by side) and one for every detector's interpolation, the
+ * ring FFTs and pointing sorts between them, all in the graph.  Needs SL_FP32
+ * plans with one interp_order, at most 32 items; the plans are given one
+ * sort-tile width (the autotuner's choice, else the smallest default).  With
+ * SL_BATCH_AUTOTUNE the tuner picks per detector the contraction's ring pairs
+ * per thread and the ring FFT tile (timing its cube build), then the common
+ * tile width (timing graph replays). */
+enum { SL_BATCH_AUTOTUNE = 1, SL_BATCH_PERSISTENT = 2 };
 
 typedef struct {
     int nitems;
@@ -393,10 +412,15 @@ typedef struct {
                                  (measured while autotuning; 0 otherwise) */
     int kernel_nodes;         /* kernel launches one run of the graph makes */
     int graph_nodes;          /* all nodes of the graph (kernels, memsets, events) */
+    int persistent;           /* 1 for the persistent form (SL_BATCH_PERSISTENT) */
 } sl_batch_info;
 
 sl_status sl_batch_create(sl_batch **out, const sl_batch_item *items, int nitems, void *stream, int flags);
 sl_status sl_batch_run(sl_batch *batch);
+/* Synchronises the batch's stream; reports device faults as SL_ERR_CUDA and an
+ * expired bounded wait of the persistent interpolation as SL_ERR_TIMEOUT (the
+ * flag is then cleared). */
+sl_status sl_batch_sync(sl_batch *batch);
 sl_status sl_batch_get_info(const sl_batch *batch, sl_batch_info *info);
 void sl_batch_destroy(sl_batch *batch);
 

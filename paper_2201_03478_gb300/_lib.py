@@ -20,11 +20,12 @@ STATUS_NAMES = {0: "SL_OK", -1: "SL_ERR_ARG", -2: "SL_ERR_UNSUPPORTED", -3: "SL_
 # Symbols include/sidelobe.h declares (checked by the host tests).
 EXPORTS = ["sidelobe_plan_create", "synth_spin_maps", "interp_tod", "adjoint_tod", "adjoint_interp",
            "adjoint_synth", "interp_tod_noalloc", "plan_destroy", "sl_plan_get_sizes", "sl_plan_set_stream", "sl_plan_sync",
-           "sl_plan_enable_timing", "sl_plan_kernel_stats", "sl_plan_reserve", "sl_plan_set_tile_cols", "sl_plan_set_fft_tile",
-           "sl_batch_create", "sl_batch_run", "sl_batch_get_info", "sl_batch_destroy", "synth_spin_maps_multi",
+           "sl_plan_enable_timing", "sl_plan_kernel_stats", "sl_plan_reserve", "sl_plan_set_tile_cols", "sl_plan_set_fft_tile", "sl_plan_set_contraction_pairs",
+           "sl_batch_create", "sl_batch_run", "sl_batch_sync", "sl_batch_get_info", "sl_batch_destroy", "synth_spin_maps_multi",
            "sl_plan_selftest_timeout", "sl_orbital_moments", "orbital_dipole_tod", "synth_psi_cube", "interp_tod_psi",
            "sl_debug_check_status", "sl_measure_alu_peak", "sl_quad_factor", "sl_last_error"]
 SL_BATCH_AUTOTUNE = 1
+SL_BATCH_PERSISTENT = 2
 
 
 class PlanDesc(ctypes.Structure):
@@ -37,7 +38,8 @@ class PlanDesc(ctypes.Structure):
 class PlanSizes(ctypes.Structure):
     _fields_ = [("nalm", ctypes.c_int64), ("sky_doubles", ctypes.c_int64), ("beam_doubles", ctypes.c_int64),
                 ("maps_bytes", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64), ("lsteps", ctypes.c_int64),
-                ("tile_cols", ctypes.c_int64), ("fft_rings", ctypes.c_int64), ("fft_korders", ctypes.c_int64)]
+                ("tile_cols", ctypes.c_int64), ("fft_rings", ctypes.c_int64), ("fft_korders", ctypes.c_int64),
+                ("contraction_pairs", ctypes.c_int64)]
 
 
 class BatchItem(ctypes.Structure):
@@ -48,7 +50,8 @@ class BatchItem(ctypes.Structure):
 
 class BatchInfo(ctypes.Structure):
     _fields_ = [("nitems", ctypes.c_int), ("nstreams", ctypes.c_int), ("tuned_ms", ctypes.c_double),
-                ("serial_ms", ctypes.c_double), ("kernel_nodes", ctypes.c_int), ("graph_nodes", ctypes.c_int)]
+                ("serial_ms", ctypes.c_double), ("kernel_nodes", ctypes.c_int), ("graph_nodes", ctypes.c_int),
+                ("persistent", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -106,8 +109,10 @@ def load(build: bool = True) -> ctypes.CDLL:
         "sl_plan_reserve": (I, [P, I64]),
         "sl_plan_set_tile_cols": (I, [P, I]),
         "sl_plan_set_fft_tile": (I, [P, I, I]),
+        "sl_plan_set_contraction_pairs": (I, [P, I]),
         "sl_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(BatchItem), I, P, I]),
         "sl_batch_run": (I, [P]),
+        "sl_batch_sync": (I, [P]),
         "sl_batch_get_info": (I, [P, ctypes.POINTER(BatchInfo)]),
         "sl_batch_destroy": (None, [P]),
         "sl_orbital_moments": (I, [P, P, P]),

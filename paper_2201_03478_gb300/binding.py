@@ -82,6 +82,11 @@ class Plan:
         default (sl_plan_set_fft_tile)."""
         check(_lib.load().sl_plan_set_fft_tile(self.ptr, int(rings), int(korders)))
 
+    def set_contraction_pairs(self, pairs):
+        """Ring pairs (2, 4, 8) per thread of the FP32 contraction; 0 for the automatic
+        choice (sl_plan_set_contraction_pairs)."""
+        check(_lib.load().sl_plan_set_contraction_pairs(self.ptr, int(pairs)))
+
     def __del__(self):
         try:
             plan_destroy(self)
@@ -385,6 +390,11 @@ class Batch:
     def run(self):
         check(_lib.load().sl_batch_run(self.ptr))
 
+    def sync(self):
+        """Waits for the batch's stream; raises on a device fault or an expired
+        bounded wait (sl_batch_sync)."""
+        check(_lib.load().sl_batch_sync(self.ptr))
+
     def info(self):
         out = _lib.BatchInfo()
         check(_lib.load().sl_batch_get_info(self.ptr, ctypes.byref(out)))
@@ -397,10 +407,11 @@ class Batch:
             pass
 
 
-def sl_batch_create(items, autotune: bool = False) -> Batch:
+def sl_batch_create(items, autotune: bool = False, persistent: bool = False) -> Batch:
     """items: sequence of dicts with keys plan, sky, beam, maps, theta, phi, psi, tod
     (device tensors in the layouts of synth_spin_maps and interp_tod, one plan per
-    item).  Captured on the current torch stream of the first plan's device."""
+    item).  Captured on the current torch stream of the first plan's device.
+    persistent: the persistent form (SL_BATCH_PERSISTENT; SL_FP32 plans)."""
     lib = _lib.load()
     items = [dict(it) for it in items]
     if not items:
@@ -418,8 +429,8 @@ def sl_batch_create(items, autotune: bool = False) -> Batch:
                                 tod=_ptr(it["tod"]))
     stream = torch.cuda.current_stream(device).cuda_stream
     out = ctypes.c_void_p()
-    check(lib.sl_batch_create(ctypes.byref(out), arr, len(items), ctypes.c_void_p(stream),
-                              _lib.SL_BATCH_AUTOTUNE if autotune else 0))
+    flags = (_lib.SL_BATCH_AUTOTUNE if autotune else 0) | (_lib.SL_BATCH_PERSISTENT if persistent else 0)
+    check(lib.sl_batch_create(ctypes.byref(out), arr, len(items), ctypes.c_void_p(stream), flags))
     return Batch(out, items, device)
 
 

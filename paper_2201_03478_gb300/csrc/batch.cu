@@ -9,6 +9,17 @@
 // tile width (8, 16 or 32 columns) by timing its own interpolation, then the
 // number of branches (1, 2, 4, 8) by timing replays.
 //
+// Persistent mode (SL_BATCH_PERSISTENT; SL_FP32 plans, one interpolation
+// order): the graph holds persistent contraction launches over every
+// detector's blocks (k_lcontract_f32_batch, one launch per number of ring
+// pairs per thread among the detectors, side by side: warps take work items
+// from a device counter, largest first), each detector's ring FFT and pointing
+// sort, and one persistent interpolation launch over every detector's work
+// items (k_interp_f32_cells with per-detector arguments).  Its autotuner picks,
+// per detector, the contraction's ring pairs per thread and the ring FFT's
+// tile by timing the detector's cube build, then one sort-tile width (8, 16,
+// 32) for all detectors by timing graph replays.
+//
 // This layer is host code on top of the plan API; it only adds the plans'
 // batch_refs lock, which stops a plan from reallocating scratch that a graph
 // still points into.
@@ -24,13 +35,21 @@ struct sl_batch {
     std::vector<sl_batch_item> items;
     std::vector<double> cost;            // per item: measured ms (autotune) or a flop estimate
     std::vector<cudaStream_t> branches;  // capture-only streams
-    cudaEvent_t fork = nullptr;
+    cudaEvent_t fork = nullptr, mid = nullptr;
     std::vector<cudaEvent_t> joins;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int nstreams = 0;
     double tuned_ms = 0.0, serial_ms = 0.0;
     bool locked = false;
+    // persistent mode
+    bool persistent = false;
+    sl::LcBatchItem *d_items = nullptr;  // contraction work items (device), grouped by ring pairs per thread
+    int group_items[sl::kLcBatchGroups] = {};
+    unsigned *d_ctr = nullptr;           // work counters: the contraction groups', then the interpolation's
+    cudaStream_t lc_side[sl::kLcBatchGroups - 1] = {};   // capture-only streams of the contraction groups
+    cudaEvent_t lc_ready = nullptr, lc_done[sl::kLcBatchGroups - 1] = {};
+    int *d_err = nullptr;                // flag of the interpolation's bounded waits
 };
 
 namespace sl {
@@ -126,6 +145,86 @@ static sl_status capture(sl_batch *b, int nbr, cudaGraph_t *graph, cudaGraphExec
     return st != SL_OK ? st : rst;
 }
 
+// Captures the persistent form (every plan moved to the batch stream meanwhile).
+static sl_status capture_persistent(sl_batch *b, cudaGraph_t *graph, cudaGraphExec_t *exec) {
+    *graph = nullptr;
+    *exec = nullptr;
+    const int n = (int)b->items.size();
+    std::vector<cudaStream_t> saved(n), here(n, b->stream);
+    std::vector<bool> timing(n);
+    std::vector<sl_plan *> plans(n);
+    std::vector<const double *> sky(n), beam(n);
+    int kmax = 0;
+    for (int i = 0; i < n; ++i) {
+        saved[i] = b->items[i].plan->stream;
+        timing[i] = b->items[i].plan->timing;
+        plans[i] = b->items[i].plan;
+        sky[i] = b->items[i].sky;
+        beam[i] = b->items[i].beam;
+        kmax = std::max(kmax, plans[i]->K);
+    }
+    sl_status st = move_plans(b, &here, nullptr);
+    if (st != SL_OK) {
+        move_plans(b, nullptr, &saved);
+        return st;
+    }
+    for (int i = 0; i < n; ++i) plans[i]->timing = false;   // no event records inside the graph
+    st = cuda_check(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (st == SL_OK) {
+        // The pointing sorts depend on the pointings only: they run on side branches
+        // while the persistent contraction runs on the batch stream; each ring FFT
+        // follows the contraction on a branch; the persistent interpolation waits
+        // for every branch.
+        const int nbr = (int)b->branches.size();
+        sl_status cst = cuda_check(cudaEventRecord(b->fork, b->stream), "fork");
+        for (int s = 0; s < nbr && cst == SL_OK; ++s)
+            cst = cuda_check(cudaStreamWaitEvent(b->branches[s], b->fork, 0), "fork wait");
+        std::vector<TiledArgs> args;
+        for (int i = 0; i < n && cst == SL_OK; ++i) {
+            const sl_batch_item &it = b->items[i];
+            if (it.n == 0) continue;
+            plans[i]->stream = b->branches[i % nbr];   // inside the capture: no stream switch that synchronises
+            cst = launch_sort_into(plans[i], plans[i]->sort, it.theta, it.phi, it.psi, it.n, 1, 0, 1);
+            args.push_back(fine_tiled_args(plans[i], plans[i]->sort, it.maps, it.tod));
+        }
+        if (cst == SL_OK)
+            cst = launch_lcontract_f32_batch(b->stream, b->lc_side, b->lc_done, b->lc_ready, plans.data(), sky.data(),
+                                             beam.data(), n, b->d_items, b->group_items, b->d_ctr);
+        if (cst == SL_OK) cst = cuda_check(cudaEventRecord(b->mid, b->stream), "contraction done");
+        for (int s = 0; s < nbr && cst == SL_OK; ++s)
+            cst = cuda_check(cudaStreamWaitEvent(b->branches[s], b->mid, 0), "contraction wait");
+        for (int i = 0; i < n && cst == SL_OK; ++i) {
+            plans[i]->stream = b->branches[i % nbr];
+            cst = launch_ringfft_synth(plans[i], b->items[i].maps);
+        }
+        for (int s = 0; s < nbr && cst == SL_OK; ++s) {
+            cst = cuda_check(cudaEventRecord(b->joins[s], b->branches[s]), "join");
+            if (cst == SL_OK) cst = cuda_check(cudaStreamWaitEvent(b->stream, b->joins[s], 0), "join wait");
+        }
+        for (int i = 0; i < n; ++i) plans[i]->stream = b->stream;
+        if (cst == SL_OK && !args.empty())
+            cst = launch_interp_f32_cells(b->stream, b->device, args.data(), (int)args.size(),
+                                          plans[0]->geom.tile_cols, plans[0]->p, kmax, b->d_ctr + kLcBatchGroups,
+                                          b->d_err);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (cst == SL_OK) cst = cuda_check(e, "end capture");
+        if (cst == SL_OK) cst = cuda_check(cudaGraphInstantiate(exec, g, 0), "graph instantiate");
+        if (cst != SL_OK) {
+            if (*exec) cudaGraphExecDestroy(*exec);
+            if (g) cudaGraphDestroy(g);
+            *exec = nullptr;
+            g = nullptr;
+            cudaGetLastError();
+        }
+        *graph = g;
+        st = cst;
+    }
+    for (int i = 0; i < n; ++i) plans[i]->timing = timing[i];
+    const sl_status rst = move_plans(b, nullptr, &saved);
+    return st != SL_OK ? st : rst;
+}
+
 // Milliseconds of `reps` replays of exec on the batch stream (after one warm replay).
 static sl_status time_replays(sl_batch *b, cudaGraphExec_t exec, int reps, double *ms) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -196,6 +295,43 @@ static sl_status autotune_items(sl_batch *b) {
     }, &b->serial_ms);
 }
 
+// Persistent mode, per detector: the contraction's ring pairs per thread and
+// the ring FFT tile by timing its cube build (plans moved to the batch stream
+// by the caller).
+static sl_status autotune_synth(sl_batch *b) {
+    for (const sl_batch_item &it : b->items) {
+        sl_plan *p = it.plan;
+        auto synth = [&] { return synth_spin_maps(p, it.sky, it.beam, it.maps); };
+        double t = 0.0, best = -1.0;
+        sl_status st;
+        int best_ppt = 0;
+        for (int ppt : {8, 4, 2}) {
+            if (sl_plan_set_contraction_pairs(p, ppt) != SL_OK) continue;
+            if ((st = time_on_stream(b, synth, &t)) != SL_OK) return st;   // warm
+            if ((st = time_on_stream(b, synth, &t)) != SL_OK) return st;
+            if (best < 0.0 || t < best) {
+                best = t;
+                best_ppt = ppt;
+            }
+        }
+        if ((st = sl_plan_set_contraction_pairs(p, best_ppt)) != SL_OK) return st;
+        best = -1.0;
+        int brg = 0, bkg = 0;
+        for (int rg : {1, 2, 4})
+            for (int kg : {1, 2}) {
+                if (sl_plan_set_fft_tile(p, rg, kg) != SL_OK) continue;   // not valid for this grid
+                if ((st = time_on_stream(b, synth, &t)) != SL_OK) return st;
+                if (best < 0.0 || t < best) {
+                    best = t;
+                    brg = rg;
+                    bkg = kg;
+                }
+            }
+        if ((st = sl_plan_set_fft_tile(p, brg, bkg)) != SL_OK) return st;
+    }
+    return SL_OK;
+}
+
 static void release(sl_batch *b) {
     if (b->locked)
         for (const sl_batch_item &it : b->items) --it.plan->batch_refs;
@@ -203,10 +339,68 @@ static void release(sl_batch *b) {
     destroy_graph(b->graph, b->exec);
     for (cudaStream_t s : b->branches) cudaStreamDestroy(s);
     b->branches.clear();
+    for (cudaStream_t s : b->lc_side)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->lc_done)
+        if (e) cudaEventDestroy(e);
+    if (b->lc_ready) cudaEventDestroy(b->lc_ready);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->mid) cudaEventDestroy(b->mid);
     for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
     b->joins.clear();
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_ctr) cudaFree(b->d_ctr);
+    if (b->d_err) cudaFree(b->d_err);
+    b->d_items = nullptr;
+    b->d_ctr = nullptr;
+    b->d_err = nullptr;
+}
+
+// Persistent mode: validation, a common tile width, the batch's device
+// counters and the contraction groups' streams.
+static sl_status prepare_persistent(sl_batch *b) {
+    const int n = (int)b->items.size();
+    if (n > kMaxBatchDets)
+        return set_error(SL_ERR_UNSUPPORTED, "persistent batch: %d detectors, at most %d", n, kMaxBatchDets);
+    int tc = 32;
+    for (int i = 0; i < n; ++i) {
+        const sl_plan *p = b->items[i].plan;
+        if (p->precision != SL_FP32)
+            return set_error(SL_ERR_UNSUPPORTED, "persistent batch: item %d is not an SL_FP32 plan", i);
+        if (p->p != b->items[0].plan->p)
+            return set_error(SL_ERR_UNSUPPORTED, "persistent batch: items 0 and %d differ in interp_order", i);
+        tc = std::min(tc, p->geom.tile_cols);
+    }
+    for (int i = 0; i < n; ++i) {   // one tile width for the shared interpolation launch
+        sl_status st = sl_plan_set_tile_cols(b->items[i].plan, tc);
+        if (st != SL_OK) return st;
+    }
+    sl_status st = cuda_check(cudaMalloc(&b->d_ctr, (kLcBatchGroups + 1) * sizeof(unsigned)), "batch counters");
+    for (int j = 0; j < kLcBatchGroups - 1 && st == SL_OK; ++j) {
+        st = cuda_check(cudaStreamCreateWithFlags(&b->lc_side[j], cudaStreamNonBlocking), "contraction stream");
+        if (st == SL_OK) st = cuda_check(cudaEventCreateWithFlags(&b->lc_done[j], cudaEventDisableTiming), "event");
+    }
+    if (st == SL_OK) st = cuda_check(cudaEventCreateWithFlags(&b->lc_ready, cudaEventDisableTiming), "event");
+    if (st == SL_OK) st = cuda_check(cudaMalloc(&b->d_err, sizeof(int)), "batch error flag");
+    if (st == SL_OK) st = cuda_check(cudaMemset(b->d_err, 0, sizeof(int)), "batch error flag");
+    return st;
+}
+
+// (Re)builds the contraction's work items from the plans' current settings.
+static sl_status upload_items(sl_batch *b) {
+    std::vector<sl_plan *> plans;
+    for (const sl_batch_item &it : b->items) plans.push_back(it.plan);
+    std::vector<LcBatchItem> items;
+    sl_status st = lcontract_f32_batch_items(plans.data(), (int)plans.size(), items, b->group_items);
+    if (st != SL_OK) return st;
+    if (b->d_items) cudaFree(b->d_items);
+    b->d_items = nullptr;
+    st = cuda_check(cudaMalloc(&b->d_items, items.size() * sizeof(LcBatchItem)), "batch work items");
+    if (st == SL_OK)
+        st = cuda_check(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(LcBatchItem), cudaMemcpyHostToDevice),
+                        "batch work items");
+    return st;
 }
 
 }  // namespace sl
@@ -256,13 +450,61 @@ sl_status sl_batch_create(sl_batch **out, const sl_batch_item *items, int nitems
         if (st == SL_OK) b->joins.push_back(ev);
     }
     if (st == SL_OK) st = cuda_check(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "fork event");
+    if (st == SL_OK) st = cuda_check(cudaEventCreateWithFlags(&b->mid, cudaEventDisableTiming), "mid event");
     for (int i = 0; i < nitems && st == SL_OK; ++i) st = sl_plan_reserve(b->items[i].plan, b->items[i].n);
     for (int i = 0; i < nitems && st == SL_OK; ++i) {   // flop estimate (FP64 at 1/64 of the FP32 rate)
         const sl_plan *p = b->items[i].plan;
         const double w = p->precision == SL_FP64 ? 64.0 : (p->precision == SL_DF64 ? 12.0 : 1.0);
         b->cost[i] = w * (11.0 * (double)p->lsteps + 4.0 * 16.0 * (p->K + 1) * (double)b->items[i].n);
     }
-    if (st == SL_OK && (flags & SL_BATCH_AUTOTUNE)) {
+    if (st == SL_OK && (flags & SL_BATCH_PERSISTENT)) {
+        b->persistent = true;
+        st = prepare_persistent(b);
+        if (st == SL_OK && (flags & SL_BATCH_AUTOTUNE)) {
+            std::vector<cudaStream_t> saved(nitems), here(nitems, b->stream);
+            for (int i = 0; i < nitems; ++i) saved[i] = b->items[i].plan->stream;
+            st = move_plans(b, &here, nullptr);
+            if (st == SL_OK) st = autotune_synth(b);
+            if (st == SL_OK)   // the detectors one after another (their own kernels), for reference
+                st = time_on_stream(b, [&] {
+                    for (const sl_batch_item &it : b->items) {
+                        sl_status s2 = run_item(it);
+                        if (s2 != SL_OK) return s2;
+                    }
+                    return SL_OK;
+                }, &b->serial_ms);
+            const sl_status rst = move_plans(b, nullptr, &saved);
+            if (st == SL_OK) st = rst;
+            // one tile width for all detectors, by timing graph replays
+            int best_tc = 0;
+            if (st == SL_OK) st = upload_items(b);
+            for (int tc : {32, 16, 8}) {
+                if (st != SL_OK) break;
+                bool ok = true;
+                for (const sl_batch_item &it : b->items) ok = ok && sl_plan_set_tile_cols(it.plan, tc) == SL_OK;
+                if (!ok) continue;
+                cudaGraph_t g = nullptr;
+                cudaGraphExec_t e = nullptr;
+                double ms = 0.0;
+                st = capture_persistent(b, &g, &e);
+                if (st == SL_OK) st = time_replays(b, e, 2, &ms);
+                if (st == SL_OK && (best_tc == 0 || ms < b->tuned_ms)) {
+                    best_tc = tc;
+                    b->tuned_ms = ms;
+                }
+                destroy_graph(g, e);
+            }
+            if (st == SL_OK && best_tc == 0) st = set_error(SL_ERR_UNSUPPORTED, "persistent batch: no common tile width");
+            for (const sl_batch_item &it : b->items)   // settle on it (re-tiles) and capture once more
+                if (st == SL_OK) st = sl_plan_set_tile_cols(it.plan, best_tc);
+            b->nstreams = 1;
+            if (st == SL_OK) st = capture_persistent(b, &b->graph, &b->exec);
+        } else if (st == SL_OK) {
+            b->nstreams = 1;
+            st = upload_items(b);
+            if (st == SL_OK) st = capture_persistent(b, &b->graph, &b->exec);
+        }
+    } else if (st == SL_OK && (flags & SL_BATCH_AUTOTUNE)) {
         std::vector<cudaStream_t> saved(nitems), here(nitems, b->stream);
         for (int i = 0; i < nitems; ++i) saved[i] = b->items[i].plan->stream;
         st = move_plans(b, &here, nullptr);
@@ -307,10 +549,26 @@ sl_status sl_batch_run(sl_batch *b) {
     return cuda_check(cudaGraphLaunch(b->exec, b->stream), "sl_batch_run: graph launch");
 }
 
+sl_status sl_batch_sync(sl_batch *b) {
+    if (!b) return set_error(SL_ERR_ARG, "sl_batch_sync: no batch");
+    sl_status st = cuda_check(cudaSetDevice(b->device), "cudaSetDevice");
+    if (st == SL_OK) st = cuda_check(cudaStreamSynchronize(b->stream), "sl_batch_sync");
+    if (st != SL_OK || !b->d_err) return st;
+    int flag = 0;
+    if ((st = cuda_check(cudaMemcpy(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost), "batch error flag")) != SL_OK)
+        return st;
+    if (flag) {
+        cudaMemset(b->d_err, 0, sizeof(int));
+        return set_error(SL_ERR_TIMEOUT, "a bounded wait of the batch's interpolation expired");
+    }
+    return SL_OK;
+}
+
 sl_status sl_batch_get_info(const sl_batch *b, sl_batch_info *info) {
     if (!b || !info) return set_error(SL_ERR_ARG, "sl_batch_get_info: NULL argument");
     info->nitems = (int)b->items.size();
     info->nstreams = b->nstreams;
+    info->persistent = b->persistent ? 1 : 0;
     info->tuned_ms = b->tuned_ms;
     info->serial_ms = b->serial_ms;
     info->kernel_nodes = info->graph_nodes = 0;

@@ -367,7 +367,7 @@ sl_status launch_lcontract_adjoint(sl_plan *p) {
     const bool df = p->precision == SL_DF64;
     const size_t sm = df ? sizeof(AdjSmemDF) : sizeof(AdjSmem);
     void (*kern)(const LcAdjArgs) = df ? k_lcontract_adj_df : k_lcontract_adj;
-    if ((st = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+    if ((st = cuda_check(allow_dyn_smem(kern, sm),
                          "k_lcontract_adj smem attribute")) != SL_OK)
         return st;
     int slot = timing_begin(p, df ? "lcontract_adj_df" : "lcontract_adj");

@@ -516,8 +516,7 @@ template <typename T, int RG, int KG>
 static cudaError_t launch_ip(sl_plan *p, const void *G, int nsky, void *maps) {
     using C = typename CplxOf<T>::type;
     const size_t sm = ring_fft_ip_smem(p, RG, KG);
-    cudaError_t e = cudaFuncSetAttribute(k_ringfft_synth_ip<T, RG, KG>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = allow_dyn_smem(k_ringfft_synth_ip<T, RG, KG>, sm);
     if (e != cudaSuccess) return e;
     const unsigned nblk = (unsigned)(((p->R + RG - 1) / RG) * ((p->K + KG) / KG));
     const C *ptw = plan_wide(p->precision) ? (const C *)p->d_ptw64 : (const C *)p->d_ptw32;
@@ -540,7 +539,7 @@ static cudaError_t launch_ip_tile(sl_plan *p, int rg, int kg, const void *G, int
 
 template <typename K_, typename... Args>
 static cudaError_t launch_cluster(K_ kern, dim3 grid, int csize, size_t sm, cudaStream_t st, Args... args) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = allow_dyn_smem(kern, sm);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
@@ -610,7 +609,8 @@ sl_status launch_ringdft_adjoint(sl_plan *p, const double2 *fbar) {
         return cuda_check(e, "k_ringdft_adjoint_cl launch");
     }
     const size_t sm = 2 * (size_t)p->nphi * sizeof(double2);
-    cudaFuncSetAttribute(k_ringdft_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = allow_dyn_smem(k_ringdft_adjoint, sm);
+    if (e != cudaSuccess) return cuda_check(e, "k_ringdft_adjoint smem attribute");
     int slot = timing_begin(p, "ringdft_adj");
     k_ringdft_adjoint<<<nblk, 256, sm, p->stream>>>(p->L, p->K, p->R, p->nphi, radices_of(p), fbar, p->d_tw64,
                                                     p->d_Gadj);

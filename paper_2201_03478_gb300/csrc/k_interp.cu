@@ -104,16 +104,6 @@ __global__ void __launch_bounds__(256) k_interp_f64(const InterpGeom g, const do
 // sample sit at compile-time offsets from its first node, and one k pair is
 // one 128-bit load.  Samples are then evaluated from shared memory; the lanes
 // of a warp mostly share one cell (broadcast reads).
-struct TiledArgs {
-    InterpGeom g;
-    const float2 *maps;
-    const StencilRec32 *rec;
-    const unsigned *perm, *start, *chunk_off;
-    int ntiles, ncell;
-    double *tod;
-    int *err;                 // device error flag (bounded waits of k_interp_f32_cells)
-    unsigned *work;           // work counter of k_interp_f32_cells (zeroed before each launch)
-};
 
 template <int TC, int P>
 __global__ void __launch_bounds__(256) k_interp_f32_tiled(const TiledArgs A) {
@@ -257,6 +247,15 @@ struct CellMeta {
     int nbuf, rowlo, collo, tr;
     unsigned ngroups;                 // 0xffffffff: no more work for this CTA
     unsigned poff;                    // first sample index of the sub-item within its slots
+    int det;                          // detector (plan) of the sub-item
+};
+
+// Parameters of one launch: one detector (interp_tod) or many (a batch).
+struct CellArgs {
+    int ndet, kpmax;                  // detectors; node pairs ceil(kmax/2) of the largest kmax
+    unsigned *work;                   // work counter (zeroed before the launch)
+    int *err;                         // device error flag of the bounded waits
+    TiledArgs d[kMaxBatchDets];
 };
 
 __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, uint32_t bar) {
@@ -295,16 +294,15 @@ __device__ __forceinline__ double f2d_exact(float x) {
 }
 
 template <int TC, int P>
-__global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const TiledArgs A) {
+__global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const __grid_constant__ CellArgs C) {
     constexpr int TW = TC + P - 1, NR = kTileRows + P - 1, NN = NR * TW;
     constexpr int NCELL = kTileRows * TC, NQ = P * P, CPL = NCELL / 32, ROWT = kTileRows * 2 * P;
     constexpr int S = (P <= 4) ? 2 : 1;
     constexpr unsigned kEnd = 0xffffffffu;
-    const InterpGeom &g = A.g;
-    const int K = g.K, K1 = K + 1, KP = (K + 1) >> 1, KE = KP + 1;
+    const int KPM = C.kpmax;   // node pairs of the largest kmax: the node buffers' stride
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4 *nodeb = reinterpret_cast<float4 *>(smem_raw);                             // [2][KP * NN]
-    StencilRec32 *srecb = reinterpret_cast<StencilRec32 *>(nodeb + 2 * (size_t)KP * NN);   // [2][kCellSub]
+    float4 *nodeb = reinterpret_cast<float4 *>(smem_raw);                             // [2][KPM * NN]
+    StencilRec32 *srecb = reinterpret_cast<StencilRec32 *>(nodeb + 2 * (size_t)KPM * NN);   // [2][kCellSub]
     unsigned *ssidb = reinterpret_cast<unsigned *>(srecb + 2 * kCellSub);            // [2][kCellSidx]
     unsigned *cstb = ssidb + 2 * kCellSidx;                                          // [2][NCELL + 1]
     float *node0b = reinterpret_cast<float *>(cstb + 2 * (NCELL + 1));               // [2][NN]
@@ -313,6 +311,7 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const TiledArgs A) 
     unsigned *cbegb = goffb + 2 * (NCELL + 1);                                       // [2][NCELL]
     unsigned *cendb = cbegb + 2 * NCELL;                                             // [2][NCELL]
     __shared__ CellMeta meta[2];
+    __shared__ unsigned dcum[kMaxBatchDets + 1];   // first global work item of each detector
     __shared__ __align__(8) unsigned long long bars[9];
     const uint32_t rfull = smem_u32(&bars[0]), rempty = smem_u32(&bars[2]);
     const uint32_t nfull = smem_u32(&bars[4]), nempty = smem_u32(&bars[6]), pbar = smem_u32(&bars[8]);
@@ -330,22 +329,44 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const TiledArgs A) 
 
     if (warp == 0) {
         // ------------------------------------------------ staging warp
-        const unsigned nchunks = A.chunk_off[A.ntiles];
+        {   // work items of the detectors, one after another
+            const unsigned nd = lane < C.ndet ? C.d[lane].chunk_off[C.d[lane].ntiles] : 0u;
+            unsigned x = nd;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane < C.ndet) dcum[lane + 1] = x;
+            if (lane == 0) dcum[0] = 0u;
+            __syncwarp();
+        }
+        const unsigned nchunks = dcum[C.ndet];
         bool ok = true;
-        int tile = -1;
+        int tile = -1, tile_det = -1, det = -1, tcur = 0;
         unsigned nfill = 0, u = 0, pphase = 0;
         int nb = 0, rowlo = 0, collo = 0, tr = 0;
         for (;;) {
             unsigned v0 = 0;
-            if (lane == 0) v0 = atomicAdd(A.work, 1u) * kCellIPC;
+            if (lane == 0) v0 = atomicAdd(C.work, 1u) * kCellIPC;
             v0 = __shfl_sync(0xffffffffu, v0, 0);
             if (v0 >= nchunks || !ok) break;
             const unsigned v_end = min(nchunks, v0 + kCellIPC);
-            int tcur = find_tile(A.chunk_off, A.ntiles, v0);
+            det = -1;
             for (unsigned v = v0; v < v_end && ok; ++v) {
-                while (tcur + 1 < A.ntiles && A.chunk_off[tcur + 1] <= v) ++tcur;
-                const unsigned c = v - A.chunk_off[tcur];
-                if (tcur != tile) {
+                int dv = 0;
+                while (dv + 1 < C.ndet && dcum[dv + 1] <= v) ++dv;
+                const TiledArgs &A = C.d[dv];
+                const InterpGeom &g = A.g;
+                const int K = g.K, K1 = K + 1, KP = (K + 1) >> 1, KE = KP + 1;
+                const unsigned vl = v - dcum[dv];
+                if (dv != det) {
+                    det = dv;
+                    tcur = find_tile(A.chunk_off, A.ntiles, vl);
+                }
+                while (tcur + 1 < A.ntiles && A.chunk_off[tcur + 1] <= vl) ++tcur;
+                const unsigned c = vl - A.chunk_off[tcur];
+                if (tcur != tile || det != tile_det) {
                     nb = nfill & 1;
                     if (nfill >= 2) ok = __all_sync(0xffffffffu, mbar_wait(nempty + 8 * nb, ((nfill - 2) >> 1) & 1));
                     if (!ok) break;
@@ -353,7 +374,7 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const TiledArgs A) 
                     const int tcol = tcur - tr * g.ntc;
                     rowlo = tr * kTileRows - P / 2;
                     collo = tcol * TC - P / 2 + 1;
-                    float4 *node = nodeb + (size_t)nb * KP * NN;
+                    float4 *node = nodeb + (size_t)nb * KPM * NN;
                     float *node0 = node0b + nb * NN;
                     bool polar = false;
                     for (int r = 0; r < NR; ++r) {
@@ -412,6 +433,7 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const TiledArgs A) 
                     mbar_arrive_cp_async(nfull + 8 * nb);
                     mbar_arrive(nfull + 8 * nb);
                     tile = tcur;
+                    tile_det = det;
                     ++nfill;
                 }
                 const unsigned *cst = cstb + nb * (NCELL + 1);
@@ -459,7 +481,7 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const TiledArgs A) 
                     }
                     if (lane == 31) goff[NCELL] = x;
                     const unsigned total = __shfl_sync(0xffffffffu, x, 31);
-                    if (lane == 0) meta[rb] = CellMeta{nb, rowlo, collo, tr, total, poff};
+                    if (lane == 0) meta[rb] = CellMeta{nb, rowlo, collo, tr, total, poff, det};
                     // the records, gathered through the indices
                     ok = __all_sync(0xffffffffu, mbar_wait(pbar, pphase));
                     pphase ^= 1u;
@@ -483,7 +505,7 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const TiledArgs A) 
         if (!ok) {
             cp_async_wait_all();
             mbar_wait(pbar, pphase, 10000000ull);   // a bulk copy that may still be in flight
-            if (lane == 0) atomicExch(A.err, 1);
+            if (lane == 0) atomicExch(C.err, 1);
         }
         return;
     }
@@ -511,7 +533,9 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const TiledArgs A) 
             ++nfill;
         }
         const int m_rowlo = meta[rb].rowlo, m_collo = meta[rb].collo, m_tr = meta[rb].tr;
-        const float4 *node = nodeb + (size_t)cur_nb * KP * NN;
+        const TiledArgs &A = C.d[meta[rb].det];
+        const int KP = (A.g.K + 1) >> 1;
+        const float4 *node = nodeb + (size_t)cur_nb * KPM * NN;
         const float *node0 = node0b + cur_nb * NN;
         const float *srow = srowb + cur_nb * ROWT;
         const StencilRec32 *srec = srecb + rb * kCellSub;
@@ -616,16 +640,18 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const TiledArgs A) 
         __syncwarp();
         if (lane == 0) mbar_arrive(rempty + 8 * rb);
     }
-    if (!ok && lane == 0) atomicExch(A.err, 1);
+    if (!ok && lane == 0) atomicExch(C.err, 1);
 }
 
-size_t interp_f32_cells_smem_tc(const sl_plan *p, int tc) {
-    const int KP = (p->K + 1) / 2, NN = (kTileRows + p->p - 1) * (tc + p->p - 1), ncell = kTileRows * tc;
+size_t interp_f32_cells_smem(int K, int P, int tc) {
+    const int KP = (K + 1) / 2, NN = (kTileRows + P - 1) * (tc + P - 1), ncell = kTileRows * tc;
     return 2 * ((size_t)KP * NN * sizeof(float4) + (size_t)kCellSub * sizeof(StencilRec32) +
                 (size_t)kCellSidx * sizeof(unsigned) + (size_t)(ncell + 1) * sizeof(unsigned) +
-                (size_t)NN * sizeof(float) + (size_t)kTileRows * 2 * p->p * sizeof(float)) +
+                (size_t)NN * sizeof(float) + (size_t)kTileRows * 2 * P * sizeof(float)) +
            (size_t)(2 * (ncell + 1) + 4 * ncell) * sizeof(unsigned);
 }
+
+size_t interp_f32_cells_smem_tc(const sl_plan *p, int tc) { return interp_f32_cells_smem(p->K, p->p, tc); }
 
 SL_CHECK_READER(chk_interp)
 
@@ -799,6 +825,52 @@ static unsigned grid_for(int64_t n, int bs) {
     return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
+TiledArgs fine_tiled_args(const sl_plan *p, const SortBufs &b, const void *maps, double *tod) {
+    TiledArgs a;
+    a.g = p->geom;
+    a.maps = (const float2 *)maps;
+    a.rec = (const StencilRec32 *)b.rec;
+    a.perm = b.perm;
+    a.start = b.hist;
+    a.chunk_off = b.chunk_off;
+    a.ntiles = p->ntiles;
+    a.ncell = kTileRows * p->geom.tile_cols;
+    a.tod = tod;
+    return a;
+}
+
+// One persistent launch of k_interp_f32_cells over nd detectors' work items
+// (their sorts done; all with tile width tc and interpolation order P; kmax
+// at most kmax_max).  work and err: a counter (zeroed here) and the error flag.
+sl_status launch_interp_f32_cells(cudaStream_t stream, int device, const TiledArgs *dets, int nd, int tc, int P,
+                                  int kmax_max, unsigned *work, int *err) {
+    if (nd < 1 || nd > kMaxBatchDets) return set_error(SL_ERR_ARG, "FP32 interpolation: %d detectors (1..%d)", nd, kMaxBatchDets);
+    CellArgs C;
+    C.ndet = nd;
+    C.kpmax = (kmax_max + 1) / 2;
+    C.work = work;
+    C.err = err;
+    for (int d = 0; d < nd; ++d) C.d[d] = dets[d];
+    const size_t sm = interp_f32_cells_smem(kmax_max, P, tc);
+    void (*kern)(const CellArgs) = nullptr;
+#define SL_CELLS(TCV, PV) \
+    if (tc == TCV && P == PV) kern = k_interp_f32_cells<TCV, PV>;
+    SL_CELLS(32, 4) SL_CELLS(16, 4) SL_CELLS(8, 4)
+    SL_CELLS(32, 2) SL_CELLS(16, 2) SL_CELLS(8, 2)
+    SL_CELLS(32, 6) SL_CELLS(16, 6) SL_CELLS(8, 6)
+#undef SL_CELLS
+    if (!kern) return set_error(SL_ERR_UNSUPPORTED, "tile width %d, interp_order %d", tc, P);
+    cudaError_t e = allow_dyn_smem(kern, sm);
+    if (e != cudaSuccess) return cuda_check(e, "k_interp_f32_cells smem attribute");
+    if ((e = cudaMemsetAsync(work, 0, sizeof(unsigned), stream)) != cudaSuccess) return cuda_check(e, "work counter");
+    int per_sm = 1, nsm = 152;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    if (per_sm < 1) per_sm = 1;
+    kern<<<(unsigned)(nsm * per_sm), 256, sm, stream>>>(C);
+    return cuda_check(cudaGetLastError(), "k_interp_f32_cells launch");
+}
+
 sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *maps, const double *psi, int64_t n,
                         double *tod) {
     int slot;
@@ -827,25 +899,25 @@ sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *map
         a.ntiles = p->ntiles;
         a.ncell = fine ? kTileRows * p->geom.tile_cols : 1;
         a.tod = tod;
-        a.err = p->d_err;
-        a.work = p->d_err ? reinterpret_cast<unsigned *>(p->d_err + 1) : nullptr;
-        if (fine) {
-            if (!a.err) return set_error(SL_ERR_ARG, "FP32 interpolation needs the plan's error flag");
-            cudaError_t me = cudaMemsetAsync(a.work, 0, sizeof(unsigned), p->stream);
-            if (me != cudaSuccess) return cuda_check(me, "work counter");
+        if (fine) {   // cell-sorted samples: S samples of a cell per thread
+            if (!p->d_err) return set_error(SL_ERR_ARG, "FP32 interpolation needs the plan's error flag");
+            slot = timing_begin(p, "interp_f32");
+            sl_status st = launch_interp_f32_cells(p->stream, p->device, &a, 1, p->geom.tile_cols, p->p, p->K,
+                                                   reinterpret_cast<unsigned *>(p->d_err + 1), p->d_err);
+            timing_end(p, slot);
+            return st;
         }
-        // cell-sorted samples (fine sort): S samples of a cell per thread; tile-keyed
-        // sort (interp_tod_noalloc): one sample per thread
-        const size_t sm = fine ? interp_f32_cells_smem_tc(p, p->geom.tile_cols) : interp_f32_tiled_smem(p);
+        // tile-keyed sort (interp_tod_noalloc): one sample per thread
+        const size_t sm = interp_f32_tiled_smem(p);
         void (*kern)(const TiledArgs) = nullptr;
 #define SL_TILED(TCV, PV) \
-    if (p->geom.tile_cols == TCV && p->p == PV) kern = fine ? k_interp_f32_cells<TCV, PV> : k_interp_f32_tiled<TCV, PV>;
+    if (p->geom.tile_cols == TCV && p->p == PV) kern = k_interp_f32_tiled<TCV, PV>;
         SL_TILED(32, 4) SL_TILED(16, 4) SL_TILED(8, 4)
         SL_TILED(32, 2) SL_TILED(16, 2) SL_TILED(8, 2)
         SL_TILED(32, 6) SL_TILED(16, 6) SL_TILED(8, 6)
 #undef SL_TILED
         if (!kern) return set_error(SL_ERR_UNSUPPORTED, "tile width %d, interp_order %d", p->geom.tile_cols, p->p);
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = allow_dyn_smem(kern, sm);
         if (e != cudaSuccess) return cuda_check(e, "k_interp_f32_tiled smem attribute");
         int per_sm = 1, nsm = 152;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
@@ -891,7 +963,7 @@ sl_status launch_interp_adjoint(sl_plan *p, const SortBufs &b, int fine, const d
         case 6: kern = k_interp_adjoint<6>; break;
         default: return set_error(SL_ERR_UNSUPPORTED, "interp_order %d", p->p);
     }
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = allow_dyn_smem(kern, sm);
     if (e != cudaSuccess) return cuda_check(e, "k_interp_adjoint smem attribute");
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * nwarps, sm);

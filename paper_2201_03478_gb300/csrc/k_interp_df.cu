@@ -347,7 +347,7 @@ sl_status launch_interp_adjoint_df(sl_plan *p, const SortBufs &b, int fine, cons
         case 6: kern = k_interp_adjoint_df<6>; break;
         default: return set_error(SL_ERR_UNSUPPORTED, "interp_order %d", p->p);
     }
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = allow_dyn_smem(kern, sm);
     if (e != cudaSuccess) return cuda_check(e, "k_interp_adjoint_df smem attribute");
     int per_sm = 1, nsm = 152;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * nwarps, sm);
@@ -387,7 +387,7 @@ sl_status launch_interp_df(sl_plan *p, const SortBufs &b, int fine, const void *
     SL_TILED(32, 6) SL_TILED(16, 6) SL_TILED(8, 6)
 #undef SL_TILED
     if (!kern) return set_error(SL_ERR_UNSUPPORTED, "tile width %d, interp_order %d", p->geom.tile_cols, p->p);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = allow_dyn_smem(kern, sm);
     if (e != cudaSuccess) return cuda_check(e, "k_interp_df_tiled smem attribute");
     int per_sm = 1, nsm = 152;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);

@@ -44,6 +44,7 @@
 // its own coefficients, 32 l at a time, and steps from its earliest start
 // (recurrences not yet started hold an exact zero state).
 #include <algorithm>
+#include <vector>
 
 #include "df.cuh"
 #include "sl_internal.cuh"
@@ -52,9 +53,8 @@ namespace sl {
 
 constexpr int kNT = 256;          // threads per CTA
 constexpr int kHalf = kNT / 2;    // threads per sign
-constexpr int kF32Pairs = 8;      // ring pairs per thread of the FP32 contraction (4 packed pairs)
-constexpr int kNT32 = 128;        // threads per CTA of the FP32 contraction (64 per sign of k):
-constexpr int kHalf32 = kNT32 / 2;   // 512 ring pairs per CTA, the LFI-like grid's northern rings
+constexpr int kNT32 = 128;        // threads per CTA of the FP32 contraction: 64 per sign of k,
+constexpr int kHalf32 = kNT32 / 2;   // 2, 4 or 8 ring pairs each (lcontract_f32_ppt)
 constexpr int kLC64 = 64;         // l values staged per chunk (FP64)
 
 struct __align__(16) Coef64 {
@@ -79,13 +79,14 @@ struct LcArgs {
     void *G;
 };
 
-__device__ __forceinline__ void block_mk(const LcArgs &a, int &m, int &k, int &pc) {
-    int b = blockIdx.x;
+// Block b -> (m, k, ring chunk pc).
+__device__ __forceinline__ void block_mk_of(const LcArgs &a, int b, int &m, int &k, int &pc) {
     pc = b % a.nchunk;
     b /= a.nchunk;
     k = b % (a.K + 1);
     m = b / (a.K + 1);
 }
+__device__ __forceinline__ void block_mk(const LcArgs &a, int &m, int &k, int &pc) { block_mk_of(a, blockIdx.x, m, k, pc); }
 
 __device__ __forceinline__ int64_t start_index(const LcArgs &a, int k, int m, int neg, int pair) {
     return (((int64_t)k * (a.L + 1) + m) * 2 + neg) * a.npairs + pair;
@@ -292,14 +293,18 @@ __device__ __forceinline__ void rec32x2_step(Rec32x2 &s, const Coef32x2 &c) {
 // the current one is used): no CTA-wide barrier, every warp runs from its own
 // first start.  Each coefficient load from shared memory feeds PPT recurrence
 // steps.
+//
+// lcontract_f32_warp runs one warp's share of one CTA block (the block index
+// as in k_lcontract_f32; wpart = the warp's index in the block: 0-1 for +k,
+// 2-3 for -k) with its staging buffers stw; the warps of a block are
+// independent of each other.
 template <int PPT>
-__global__ void __launch_bounds__(kNT32, 4) k_lcontract_f32(const LcArgs a) {
+__device__ __forceinline__ void lcontract_f32_warp(const LcArgs &a, int block, int wpart, Stage32x2 (*stw)[32]) {
     constexpr int NP = PPT / 2;
-    __shared__ Stage32x2 stg[kNT32 / 32][2][32];   // [warp][buffer][l in batch]
     int m, k, pc;
-    block_mk(a, m, k, pc);
-    const int neg = threadIdx.x >= kHalf32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wsign = (threadIdx.x & (kHalf32 - 1)) >> 5;
+    block_mk_of(a, block, m, k, pc);
+    const int neg = wpart >= 2;
+    const int lane = threadIdx.x & 31, wsign = wpart & 1;
     const int base = pc * (PPT * kHalf32) + wsign * (32 * PPT);
     const int64_t moff = (int64_t)m * (2 * a.L + 1 - m) / 2;
     const RTab32 *tab = a.tab32 + (int64_t)k * a.nalm + moff;
@@ -345,7 +350,7 @@ __global__ void __launch_bounds__(kNT32, 4) k_lcontract_f32(const LcArgs a) {
     };
     if (lme + lane <= a.L) {
         stage_load(a, tab, moff, m, k, lme + lane, st);
-        stage_mine(lme + lane, &stg[warp][0][lane]);
+        stage_mine(lme + lane, &stw[0][lane]);
     }
     int buf = 0;
     for (int c0 = lme; c0 <= a.L; c0 += 32, buf ^= 1) {
@@ -354,7 +359,7 @@ __global__ void __launch_bounds__(kNT32, 4) k_lcontract_f32(const LcArgs a) {
         const bool next = ln <= a.L;
         if (next) stage_load(a, tab, moff, m, k, ln, st);
         __syncwarp();
-        const Stage32x2 *sv = stg[warp][buf];
+        const Stage32x2 *sv = stw[buf];
         int i = 0;
         // until every recurrence of the warp has started (up to and including the
         // last start l): inject start states; skip packed pairs none of whose lanes started
@@ -393,7 +398,7 @@ __global__ void __launch_bounds__(kNT32, 4) k_lcontract_f32(const LcArgs a) {
             for (int q = 0; q < NP; ++q) S[q].y = __fadd2_rn(S[q].y, S[q].D);
         }
         __syncwarp();   // the batch is read before the other buffer is overwritten next time round
-        if (next) stage_mine(ln, &stg[warp][buf ^ 1][lane]);
+        if (next) stage_mine(ln, &stw[buf ^ 1][lane]);
     }
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
@@ -404,6 +409,32 @@ __global__ void __launch_bounds__(kNT32, 4) k_lcontract_f32(const LcArgs a) {
             write_two<float2>(a, m, k, pair + 32, neg, make_float2(S[q].a1r.y, S[q].a1i.y),
                               make_float2(S[q].a2r.y, S[q].a2i.y));
     }
+}
+
+// One block per (m, k, ring chunk); warp w takes part w.
+template <int PPT>
+__global__ void __launch_bounds__(kNT32, 4) k_lcontract_f32(const LcArgs a) {
+    __shared__ Stage32x2 stg[kNT32 / 32][2][32];   // [warp][buffer][l in batch]
+    const int warp = threadIdx.x >> 5;
+    lcontract_f32_warp<PPT>(a, blockIdx.x, warp, stg[warp]);
+}
+
+// Ring pairs per thread of the FP32 contraction for a grid of npairs northern
+// rings: the variant (2, 4 or 8, i.e. 128, 256 or 512 ring pairs per block)
+// that leaves the fewest threads idle, the larger on a tie.
+int lcontract_f32_ppt(int npairs) {
+    int best = 8;
+    double best_idle = 2.0;
+    for (int ppt : {8, 4, 2}) {
+        const int per = ppt * kHalf32;
+        const int nb = (npairs + per - 1) / per;
+        const double idle = 1.0 - (double)npairs / ((double)nb * per);
+        if (idle < best_idle - 1e-9) {
+            best_idle = idle;
+            best = ppt;
+        }
+    }
+    return best;
 }
 
 // ------------------------------------------------------------------ DF64
@@ -532,16 +563,15 @@ __global__ void k_to_f32(const double2 *__restrict__ in, float2 *__restrict__ ou
         out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
 
-sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
-    if (p->precision == SL_TF32X3)   // one sky on the tensor cores
-        return launch_lcontract_mma(p, 1, sky, beam, p->d_sky32, (float2 *)p->d_G, p->d_err);
-    LcArgs a;
+// The contraction's arguments for plan p (ppt and nchunk as its kernels use them).
+static void make_lcargs(const sl_plan *p, const double *sky, const double *beam, LcArgs &a) {
     a.L = p->L;
     a.K = p->K;
     a.ncomp = p->ncomp;
     a.R = p->R;
     a.npairs = p->npairs;
-    a.ppt = (p->precision == SL_FP64) ? 1 : (p->precision == SL_DF64 ? 2 : kF32Pairs);
+    a.ppt = (p->precision == SL_FP64) ? 1
+          : (p->precision == SL_DF64 ? 2 : (p->lc_ppt ? p->lc_ppt : lcontract_f32_ppt(p->npairs)));
     const int half = plan_fp32(p->precision) ? kHalf32 : kHalf;   // ring pairs per sign of a CTA / ppt
     a.nchunk = (p->npairs + a.ppt * half - 1) / (a.ppt * half);
     a.nalm = p->nalm;
@@ -557,6 +587,21 @@ sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
     a.tab64 = p->d_tab64;
     a.tab32 = p->d_tab32;
     a.G = p->d_G;
+}
+
+// FP32 copies of a plan's sky and beam (the FP32 contraction reads them).
+static sl_status launch_to_f32(sl_plan *p, cudaStream_t s, const double *sky, const double *beam) {
+    const int64_t ns = (int64_t)p->ncomp * p->nalm, nb = (int64_t)p->ncomp * (p->K + 1) * (p->L + 1);
+    k_to_f32<<<(unsigned)std::min<int64_t>((ns + 255) / 256, 4096), 256, 0, s>>>((const double2 *)sky, p->d_sky32, ns);
+    k_to_f32<<<(unsigned)std::min<int64_t>((nb + 255) / 256, 4096), 256, 0, s>>>((const double2 *)beam, p->d_beam32, nb);
+    return cuda_check(cudaGetLastError(), "k_to_f32 launch");
+}
+
+sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
+    if (p->precision == SL_TF32X3)   // one sky on the tensor cores
+        return launch_lcontract_mma(p, 1, sky, beam, p->d_sky32, (float2 *)p->d_G, p->d_err);
+    LcArgs a;
+    make_lcargs(p, sky, beam, a);
     const int64_t nblk = (int64_t)(p->L + 1) * (p->K + 1) * a.nchunk;
     if (nblk > 0x7fffffff) return set_error(SL_ERR_UNSUPPORTED, "grid too large");
     int slot;
@@ -567,16 +612,126 @@ sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
         slot = timing_begin(p, "lcontract_f64");
         k_lcontract_f64<<<(unsigned)nblk, kNT, 0, p->stream>>>(a);
     } else {
-        const int64_t ns = (int64_t)p->ncomp * p->nalm, nb = (int64_t)p->ncomp * (p->K + 1) * (p->L + 1);
-        k_to_f32<<<(unsigned)std::min<int64_t>((ns + 255) / 256, 4096), 256, 0, p->stream>>>(
-            (const double2 *)sky, p->d_sky32, ns);
-        k_to_f32<<<(unsigned)std::min<int64_t>((nb + 255) / 256, 4096), 256, 0, p->stream>>>(
-            (const double2 *)beam, p->d_beam32, nb);
+        sl_status st = launch_to_f32(p, p->stream, sky, beam);
+        if (st != SL_OK) return st;
         slot = timing_begin(p, "lcontract_f32");
-        k_lcontract_f32<kF32Pairs><<<(unsigned)nblk, kNT32, 0, p->stream>>>(a);
+        if (a.ppt == 8) k_lcontract_f32<8><<<(unsigned)nblk, kNT32, 0, p->stream>>>(a);
+        else if (a.ppt == 4) k_lcontract_f32<4><<<(unsigned)nblk, kNT32, 0, p->stream>>>(a);
+        else k_lcontract_f32<2><<<(unsigned)nblk, kNT32, 0, p->stream>>>(a);
     }
     timing_end(p, slot);
     return cuda_check(cudaGetLastError(), "k_lcontract launch");
+}
+
+// ------------------------------------------------------------------ many detectors
+// Persistent launches for the FP32 contractions of up to kMaxBatchDets plans
+// (detectors with their own lmax, kmax, grids, skies and beams): one launch
+// per number of ring pairs per thread among them (one kernel variant each, at
+// its full occupancy), the launches side by side on their own streams.  Every
+// warp takes (block, part) units -- the part of a k_lcontract_f32 block one
+// warp runs -- from its launch's counter over the launch's items, ordered by
+// decreasing cost, and runs it with its detector's arguments (kernel
+// parameters).  A block's four parts are independent and the launches share
+// nothing, so no warp ever waits for another; the order balances the tail
+// (largest blocks first), and a launch's CTAs take the SMs that another's
+// finished CTAs leave.
+struct LcBatchArgs {
+    int ndet, nitems;
+    const LcBatchItem *items;
+    unsigned *counter;                // zeroed before the launch
+    LcArgs d[kMaxBatchDets];
+};
+
+template <int PPT>
+__global__ void __launch_bounds__(kNT32, 4) k_lcontract_f32_batch(const __grid_constant__ LcBatchArgs B) {
+    __shared__ Stage32x2 stg[kNT32 / 32][2][32];   // [warp][buffer][l in batch]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned u = 0;
+        if (lane == 0) u = atomicAdd(B.counter, 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= 4u * (unsigned)B.nitems) break;
+        const LcBatchItem it = B.items[u >> 2];
+        const LcArgs &a = B.d[it.det];
+        const int part = (int)(u & 3u);
+        lcontract_f32_warp<PPT>(a, it.block, part, stg[warp]);
+        __syncwarp();
+    }
+}
+
+// Work items: every block of every detector, grouped by the detector's ring
+// pairs per thread (8, 4, 2), each group by decreasing cost; counts[g] items in
+// group g.
+sl_status lcontract_f32_batch_items(sl_plan *const *plans, int n, std::vector<LcBatchItem> &items,
+                                    int counts[kLcBatchGroups]) {
+    items.clear();
+    for (int g = 0; g < kLcBatchGroups; ++g) counts[g] = 0;
+    for (int d = 0; d < n; ++d) {
+        const sl_plan *p = plans[d];
+        if (!plan_fp32(p->precision) || p->precision == SL_TF32X3)
+            return set_error(SL_ERR_UNSUPPORTED, "batched contraction: plan %d is not an SL_FP32 plan", d);
+        LcArgs a;
+        make_lcargs(p, nullptr, nullptr, a);
+        const int per = a.ppt * kHalf32;
+        for (int m = 0; m <= p->L; ++m)
+            for (int k = 0; k <= p->K; ++k)
+                for (int c = 0; c < a.nchunk; ++c) {
+                    // recurrence steps of the block (the evanescent zone ignored): l from max(m, k) to L
+                    const int pairs = std::min(per, p->npairs - c * per);
+                    const float cost = (float)(p->L + 1 - std::max(m, k)) * (float)pairs;
+                    items.push_back(LcBatchItem{d, (m * (p->K + 1) + k) * a.nchunk + c, a.ppt, cost});
+                }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const LcBatchItem &x, const LcBatchItem &y) {
+        return x.ppt != y.ppt ? x.ppt > y.ppt : x.cost > y.cost;
+    });
+    for (const LcBatchItem &it : items) ++counts[it.ppt == 8 ? 0 : (it.ppt == 4 ? 1 : 2)];
+    return SL_OK;
+}
+
+sl_status launch_lcontract_f32_batch(cudaStream_t stream, const cudaStream_t *side, const cudaEvent_t *side_done,
+                                     cudaEvent_t ready, sl_plan *const *plans, const double *const *sky,
+                                     const double *const *beam, int n, const LcBatchItem *items,
+                                     const int counts[kLcBatchGroups], unsigned *counters) {
+    if (n < 1 || n > kMaxBatchDets) return set_error(SL_ERR_ARG, "batched contraction: %d plans (1..%d)", n, kMaxBatchDets);
+    LcBatchArgs B;
+    B.ndet = n;
+    for (int d = 0; d < n; ++d) {
+        sl_status st = launch_to_f32(plans[d], stream, sky[d], beam[d]);
+        if (st != SL_OK) return st;
+        make_lcargs(plans[d], sky[d], beam[d], B.d[d]);
+    }
+    sl_status st = cuda_check(cudaMemsetAsync(counters, 0, kLcBatchGroups * sizeof(unsigned), stream), "batch counters");
+    if (st == SL_OK) st = cuda_check(cudaEventRecord(ready, stream), "batch counters ready");
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, plans[0]->device);
+    int first = 0, nside = 0;
+    bool main_used = false;
+    for (int g = 0; g < kLcBatchGroups && st == SL_OK; first += counts[g], ++g) {
+        if (counts[g] == 0) continue;
+        void (*kern)(const LcBatchArgs) = g == 0 ? k_lcontract_f32_batch<8>
+                                        : (g == 1 ? k_lcontract_f32_batch<4> : k_lcontract_f32_batch<2>);
+        int per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT32, 0);
+        if (per_sm < 1) per_sm = 1;
+        B.items = items + first;
+        B.nitems = counts[g];
+        B.counter = counters + g;
+        // the first group on the batch stream, the others on side streams beside it
+        const cudaStream_t s = main_used ? side[nside] : stream;
+        main_used = true;
+        if (s != stream) st = cuda_check(cudaStreamWaitEvent(s, ready, 0), "batch side stream");
+        if (st != SL_OK) break;
+        kern<<<(unsigned)(nsm * per_sm), kNT32, 0, s>>>(B);
+        st = cuda_check(cudaGetLastError(), "k_lcontract_f32_batch launch");
+        if (st == SL_OK && s != stream) {
+            st = cuda_check(cudaEventRecord(side_done[nside], s), "batch side stream done");
+            ++nside;
+        }
+    }
+    for (int j = 0; j < nside && st == SL_OK; ++j)
+        st = cuda_check(cudaStreamWaitEvent(stream, side_done[j], 0), "batch side stream join");
+    return st;
 }
 
 }  // namespace sl

@@ -705,7 +705,7 @@ sl_status launch_lcontract_mma(sl_plan *p, int nsky, const double *sky, const do
     if (nblk > 0x7fffffff) return set_error(SL_ERR_UNSUPPORTED, "grid too large");
     const size_t sm = lcontract_mma_smem(a.nsg, a.ncomp);
     void (*kern)(const MsArgs, const CUtensorMap) = a.ncomp == 1 ? k_lcontract_mma<1> : k_lcontract_mma<3>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = allow_dyn_smem(kern, sm);
     if (e != cudaSuccess) return cuda_check(e, "k_lcontract_mma smem attribute");
     const int slot = timing_begin(p, "lcontract_mma");
     kern<<<(unsigned)nblk, kMsThreads, sm, p->stream>>>(a, tmap);

@@ -244,7 +244,7 @@ sl_status launch_interp_psi_tiled(sl_plan *p, const SortBufs &b, const void *cub
     SL_PT(32, 6) SL_PT(16, 6) SL_PT(8, 6)
 #undef SL_PT
     if (!kern) return set_error(SL_ERR_UNSUPPORTED, "tile width %d, interp_order %d", p->geom.tile_cols, p->p);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = allow_dyn_smem(kern, sm);
     if (e != cudaSuccess) return cuda_check(e, "k_interp_psi_tiled smem attribute");
     int per_sm = 1, nsm = 152;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
@@ -272,14 +272,14 @@ sl_status launch_psi_cube(sl_plan *p, const void *maps, int npsi, const void *ta
     int slot;
     if (plan_wide(p->precision)) {
         const size_t sm = psi_cube_smem<double>(K1, npsi);
-        cudaError_t e = cudaFuncSetAttribute(k_psi_cube<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = allow_dyn_smem(k_psi_cube<double>, sm);
         if (e != cudaSuccess) return cuda_check(e, "k_psi_cube smem attribute");
         slot = timing_begin(p, "psi_cube_f64");
         k_psi_cube<double><<<nb, 256, sm, p->stream>>>((const double2 *)maps, (const double2 *)tab, K1, npsi, nnode,
                                                        (double *)out);
     } else {
         const size_t sm = psi_cube_smem<float>(K1, npsi);
-        cudaError_t e = cudaFuncSetAttribute(k_psi_cube<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = allow_dyn_smem(k_psi_cube<float>, sm);
         if (e != cudaSuccess) return cuda_check(e, "k_psi_cube smem attribute");
         slot = timing_begin(p, "psi_cube_f32");
         k_psi_cube<float><<<nb, 256, sm, p->stream>>>((const float2 *)maps, (const float2 *)tab, K1, npsi, nnode,

@@ -7,6 +7,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <cmath>
 #include <vector>
 #include <new>
@@ -23,6 +26,26 @@ sl_status set_error(sl_status st, const char *fmt, ...) {
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
     return st;
+}
+
+cudaError_t allow_dyn_smem_fn(const void *kern, size_t sm) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> caps;   // (kernel, device) -> cap set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = caps.find({kern, dev});
+    if (it == caps.end()) {
+        int optin = 0;
+        cudaFuncAttributes fa;
+        if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+        const int cap = optin - (int)fa.sharedSizeBytes;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess) return e;
+        it = caps.emplace(std::make_pair(kern, dev), cap).first;
+    }
+    return sm <= (size_t)it->second ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 sl_status cuda_check(cudaError_t e, const char *what) {
@@ -675,6 +698,7 @@ sl_status sl_plan_get_sizes(const sl_plan *p, sl_plan_sizes *o) {
         o->fft_rings = rg;
         o->fft_korders = kg;
     }
+    o->contraction_pairs = p->precision == SL_FP32 ? (p->lc_ppt ? p->lc_ppt : lcontract_f32_ppt(p->npairs)) : 0;
     return SL_OK;
 }
 
@@ -723,6 +747,17 @@ sl_status sl_plan_set_fft_tile(sl_plan *p, int rings, int korders) {
                          need);
     p->fft_rg = rings;
     p->fft_kg = korders;
+    return SL_OK;
+}
+
+sl_status sl_plan_set_contraction_pairs(sl_plan *p, int pairs) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if (pairs != 0 && pairs != 2 && pairs != 4 && pairs != 8)
+        return set_error(SL_ERR_ARG, "contraction pairs %d: 0 (automatic), 2, 4 or 8", pairs);
+    if (p->precision != SL_FP32 && pairs != 0)
+        return set_error(SL_ERR_UNSUPPORTED, "contraction pairs: only SL_FP32 plans have the choice");
+    p->lc_ppt = pairs;
     return SL_OK;
 }
 

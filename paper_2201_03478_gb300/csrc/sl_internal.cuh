@@ -204,6 +204,16 @@ struct __align__(16) StencilRec32 {
     unsigned cell;
 };
 
+// Arguments of the tile-staged FP32 interpolation of one plan's sorted pointings.
+struct TiledArgs {
+    InterpGeom g;
+    const float2 *maps;
+    const StencilRec32 *rec;
+    const unsigned *perm, *start, *chunk_off;
+    int ntiles, ncell;
+    double *tod;
+};
+
 // Device buffers of one pointing sort.
 struct SortBufs {
     unsigned *keys;       // [n]
@@ -280,6 +290,7 @@ struct sl_plan {
     double2 *d_ptw64 = nullptr;       // [nphi] per-pass twiddles of the in-place ring FFT
     float2 *d_ptw32 = nullptr;
     int fft_rg = 0, fft_kg = 0;       // rings x k orders per in-place FFT CTA (0: default)
+    int lc_ppt = 0;                   // ring pairs per thread of the FP32 contraction (0: automatic)
     int radices[sl::kMaxRadices];
     int nradix = 0;
 
@@ -328,6 +339,19 @@ namespace sl {
 sl_status set_error(sl_status st, const char *fmt, ...);
 sl_status cuda_check(cudaError_t e, const char *what);
 
+// Dynamic shared-memory cap of a kernel (plan.cu).  Raises the function's
+// cap, once per device, to the device's opt-in maximum less the kernel's
+// static shared memory, and checks that `sm` bytes fit under it.  The cap is
+// never lowered to one plan's size: a CUDA graph captured earlier keeps its
+// nodes' own (possibly larger) sizes, and a node launched again on its own
+// (a profiler replaying graph nodes one by one) is checked against the
+// function's current cap.
+cudaError_t allow_dyn_smem_fn(const void *kern, size_t sm);
+template <typename F>
+inline cudaError_t allow_dyn_smem(F *kern, size_t sm) {
+    return allow_dyn_smem_fn(reinterpret_cast<const void *>(kern), sm);
+}
+
 // timing (plan.cu): returns an index; call timing_end after the launch
 int timing_begin(sl_plan *p, const char *name);
 void timing_end(sl_plan *p, int idx);
@@ -365,6 +389,24 @@ sl_status launch_rtab(sl_plan *p);
 sl_status launch_advance(sl_plan *p, double thr, int *ls, double2 *st64, float2 *st32);
 sl_status count_lsteps(sl_plan *p, int64_t *out);
 sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam);
+// Many detectors (batch.cu): work items of the persistent FP32 contraction.
+constexpr int kMaxBatchDets = 32;
+struct LcBatchItem {
+    int det, block, ppt;
+    float cost;
+};
+int lcontract_f32_ppt(int npairs);
+// items grouped by ring pairs per thread (8, 4, 2), counts[g] per group
+constexpr int kLcBatchGroups = 3;
+sl_status lcontract_f32_batch_items(sl_plan *const *plans, int n, std::vector<LcBatchItem> &items,
+                                    int counts[kLcBatchGroups]);
+// one launch per nonempty group: the first on `stream`, the others on side[j]
+// (after `ready`, recorded on `stream`), joined back through side_done[j];
+// counters[kLcBatchGroups] are zeroed on `stream` first
+sl_status launch_lcontract_f32_batch(cudaStream_t stream, const cudaStream_t *side, const cudaEvent_t *side_done,
+                                     cudaEvent_t ready, sl_plan *const *plans, const double *const *sky,
+                                     const double *const *beam, int n, const LcBatchItem *items,
+                                     const int counts[kLcBatchGroups], unsigned *counters);
 sl_status launch_ringfft_synth(sl_plan *p, void *maps);
 // nsky cubes from nsky consecutive G blocks (gridDim.y = nsky)
 sl_status launch_ringfft_synth_from(sl_plan *p, const void *G, int nsky, void *maps);
@@ -387,6 +429,9 @@ sl_status launch_sort_into(sl_plan *p, const SortBufs &b, const double *theta, c
                            const double *psi, int64_t n, int fine, int rec64, int with_chunks);
 // Forward interpolation over a sort (records in the plan's precision).  FP32
 // plans use the tile-staged kernel when the sort built work items (chunk_off).
+TiledArgs fine_tiled_args(const sl_plan *p, const SortBufs &b, const void *maps, double *tod);
+sl_status launch_interp_f32_cells(cudaStream_t stream, int device, const TiledArgs *dets, int nd, int tc, int P,
+                                  int kmax_max, unsigned *work, int *err);
 sl_status launch_interp(sl_plan *p, const SortBufs &b, int fine, const void *maps, const double *psi, int64_t n,
                         double *tod);
 size_t interp_f32_tiled_smem(const sl_plan *p);

@@ -104,3 +104,68 @@ def test_batch_rejects_shared_plans():
     items[1]["sky"], items[1]["beam"] = items[0]["sky"], items[0]["beam"]
     with pytest.raises(sl.SidelobeError):
         sl.sl_batch_create(items)
+
+
+# FP32 detectors of uneven lmax, kmax, grids and sample counts (one of them empty)
+PERSISTENT_DETECTORS = [
+    (32, 2, W.equiangular_ring_theta(32), 64, 20_000),
+    (48, 5, W.healpix_ring_theta(16), 96, 50_000),
+    (64, 8, W.equiangular_ring_theta(64), 128, 0),
+    (24, 24, W.equiangular_ring_theta(30), 60, 3_000),
+    (100, 4, W.equiangular_ring_theta(100), 200, 100_000),
+    (40, 17, W.equiangular_ring_theta(40), 80, 30_000),
+    (300, 3, W.equiangular_ring_theta(300), 600, 200_000),
+]
+
+
+def _make_fp32(sl, seed):
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    items = []
+    for d, (L, K, rt, nphi, n) in enumerate(PERSISTENT_DETECTORS):
+        ell = np.arange(L + 1, dtype=np.float64)
+        plan = sl.sidelobe_plan_create(L, K, rt, nphi, ncomp=1, precision="fp32")
+        th, ph, ps = W.pointings_uniform(n, seed=seed + d)
+        items.append(dict(plan=plan, sky=dev(W.sky_gaussian(L, [(ell + 1.0) ** -2], seed=seed + d)),
+                          beam=dev(W.beam_gaussian_taper(L, K, 20.0, seed=100 + d)),
+                          maps=torch.empty(plan.maps_shape(), dtype=plan.maps_dtype, device="cuda"),
+                          theta=dev(th), phi=dev(ph), psi=dev(ps),
+                          tod=torch.zeros(n, dtype=torch.float64, device="cuda")))
+    return items
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_persistent_batch_matches_individual_calls(autotune):
+    """The persistent form (one contraction launch and one interpolation launch
+    for all detectors) gives every detector's TOD bit for bit: the same
+    arithmetic per recurrence and per sample, whatever the tuning (ring pairs
+    per thread, FFT tile, tile width) decides."""
+    import paper_2201_03478_gb300 as sl
+    items = _make_fp32(sl, 11)
+    ref = _individual(sl, items)
+    batch = sl.sl_batch_create(items, autotune=autotune, persistent=True)
+    info = batch.info()
+    assert info["persistent"] == 1 and info["nitems"] == len(PERSISTENT_DETECTORS)
+    widths = {it["plan"].sizes()["tile_cols"] for it in items}
+    assert len(widths) == 1 and widths <= {8, 16, 32}
+    for it in items:
+        assert it["plan"].sizes()["contraction_pairs"] in (2, 4, 8)
+    for it in items:
+        it["tod"].zero_()
+    batch.run()
+    batch.sync()
+    for it, r in zip(items, ref):
+        assert np.array_equal(it["tod"].cpu().numpy(), r)
+    for it in items:                                   # replays read the current inputs
+        it["sky"].mul_(2.0)
+    batch.run()
+    batch.sync()
+    for it, r in zip(items, ref):
+        assert np.array_equal(it["tod"].cpu().numpy(), 2.0 * r)
+    sl.sl_batch_destroy(batch)
+
+
+def test_persistent_batch_rejects_other_precisions():
+    import paper_2201_03478_gb300 as sl
+    items = _make(sl, 13)[:2]                          # an FP64 and an FP32 plan
+    with pytest.raises(sl.SidelobeError, match="SL_ERR_UNSUPPORTED"):
+        sl.sl_batch_create(items, persistent=True)
