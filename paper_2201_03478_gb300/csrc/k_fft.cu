@@ -51,11 +51,12 @@ template <typename C, bool INV> __device__ __forceinline__ C rot(C a) {
     if (INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
     return r;
 }
-template <typename C> __device__ __forceinline__ C scal(C a, double s) {
-    C r;
-    r.x = a.x * s;
-    r.y = a.y * s;
-    return r;
+// scale by a constant, in the transform's own precision (an FP32 value times a
+// double would run on the FP64 pipe)
+__device__ __forceinline__ double2 scal(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 scal(float2 a, double s) {
+    const float f = (float)s;
+    return make_float2(a.x * f, a.y * f);
 }
 
 // cos/sin of 2 pi/3, 2 pi/5, 4 pi/5 (from their closed forms)

@@ -21,15 +21,48 @@ namespace sl {
 constexpr int kChunk = kWorkChunk;
 constexpr int kScanBlock = 4096;    // keys per CTA of k_scan_local (1024 threads x 4)
 
+// Samples [*beg, *end) of this CTA in k_bin and k_scatter: one contiguous slice
+// of the TOD per CTA (a multiple of blockDim.x long), walked blockDim.x at a
+// time.  A scan repeats the same circle on the sky every few thousand samples,
+// so a grid-stride walk -- every resident CTA on one contiguous stretch of the
+// TOD -- sends hundreds of warps to the same cells' counters at once, and
+// their atomics serialise; slices put the CTAs on different stretches.
+// Runs of equal keys among the warp's lanes (the active lanes are a prefix of
+// the warp: lanes 0 .. nact - 1): the run of this lane starts at lane *head and
+// holds *cnt lanes.  One atomic per run replaces one per lane; lanes of a scan
+// that share a cell are almost always adjacent, and a key that recurs after
+// another key just starts another run.  (Grouping all equal keys with
+// __match_any_sync costs a multi-pass instruction per lane group that binds
+// both sort kernels.)
+__device__ __forceinline__ void key_run(unsigned key, bool ok, unsigned lane, int *head, unsigned *cnt) {
+    const unsigned prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const unsigned act = __ballot_sync(0xffffffffu, ok);
+    const unsigned heads = __ballot_sync(0xffffffffu, ok && (lane == 0 || key != prev));
+    const unsigned upto = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);   // lanes 0 .. lane
+    *head = 31 - __clz(heads & upto);
+    const unsigned after = heads & ~upto;
+    const int next = after ? __ffs(after) - 1 : 32;
+    const int nact = __popc(act);
+    *cnt = (unsigned)(min(next, nact) - *head);
+}
+
+__device__ __forceinline__ void cta_slice(int64_t n, int64_t *beg, int64_t *end) {
+    const int64_t per = ((n + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
+    *beg = min(n, (int64_t)blockIdx.x * per);
+    *end = min(n, *beg + per);
+}
+
 template <bool REC64>
 __global__ void __launch_bounds__(256) k_bin(const InterpGeom g, int fine, const double *__restrict__ theta,
                                              const double *__restrict__ phi, const double *__restrict__ psi,
                                              int64_t n, unsigned *__restrict__ keys, void *__restrict__ rec,
                                              unsigned *__restrict__ hist) {
     const unsigned lane = threadIdx.x & 31;
-    for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x; s0 < n; s0 += (int64_t)gridDim.x * blockDim.x) {
+    int64_t sbeg, send;
+    cta_slice(n, &sbeg, &send);
+    for (int64_t s0 = sbeg; s0 < send; s0 += blockDim.x) {
         const int64_t s = s0 + threadIdx.x;
-        const bool ok = s < n;
+        const bool ok = s < send;
         unsigned key = 0xffffffffu;
         if (ok) {
             const double th = theta[s];
@@ -70,12 +103,10 @@ __global__ void __launch_bounds__(256) k_bin(const InterpGeom g, int fine, const
                 reinterpret_cast<StencilRec32 *>(rec)[s] = StencilRec32{dth, frac_bits_f(fr, sh), psr, cell};
             }
         }
-        const unsigned act = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            const unsigned peers = __match_any_sync(act, key);
-            const int leader = __ffs(peers) - 1;
-            if ((int)lane == leader) atomicAdd(hist + key, (unsigned)__popc(peers));
-        }
+        int head;
+        unsigned cnt;
+        key_run(key, ok, lane, &head, &cnt);
+        if (ok && (int)lane == head) atomicAdd(hist + key, cnt);
     }
 }
 
@@ -157,21 +188,21 @@ __global__ void __launch_bounds__(256) k_scatter(int64_t n, int64_t nkeys, const
                                                  unsigned *__restrict__ cursor, unsigned *__restrict__ perm) {
     (void)nkeys;
     const unsigned lane = threadIdx.x & 31;
-    for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x; s0 < n; s0 += (int64_t)gridDim.x * blockDim.x) {
+    int64_t sbeg, send;
+    cta_slice(n, &sbeg, &send);
+    for (int64_t s0 = sbeg; s0 < send; s0 += blockDim.x) {
         const int64_t s = s0 + threadIdx.x;
-        const bool ok = s < n;
+        const bool ok = s < send;
         unsigned key = ok ? keys[s] : 0xffffffffu;
         if (ok && !SL_GUARD(key < nkeys, 0x102u)) key = 0;
-        const unsigned act = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            const unsigned peers = __match_any_sync(act, key);
-            const int leader = __ffs(peers) - 1;
-            const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-            unsigned base = 0;
-            if ((int)lane == leader) base = atomicAdd(cursor + key, (unsigned)__popc(peers));
-            base = __shfl_sync(peers, base, leader);
-            if (SL_GUARD(base + rank < n, 0x103u)) perm[base + rank] = (unsigned)s;
-        }
+        int head;
+        unsigned cnt;
+        key_run(key, ok, lane, &head, &cnt);
+        unsigned base = 0;
+        if (ok && (int)lane == head) base = atomicAdd(cursor + key, cnt);
+        base = __shfl_sync(0xffffffffu, base, head < 0 ? 0 : head);
+        const unsigned rank = lane - (unsigned)head;
+        if (ok && SL_GUARD(base + rank < n, 0x103u)) perm[base + rank] = (unsigned)s;
     }
 }
 
