@@ -35,7 +35,7 @@ struct sl_batch {
     std::vector<sl_batch_item> items;
     std::vector<double> cost;            // per item: measured ms (autotune) or a flop estimate
     std::vector<cudaStream_t> branches;  // capture-only streams
-    cudaEvent_t fork = nullptr, mid = nullptr;
+    cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> joins;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -47,8 +47,11 @@ struct sl_batch {
     sl::LcBatchItem *d_items = nullptr;  // contraction work items (device), grouped by ring pairs per thread
     int group_items[sl::kLcBatchGroups] = {};
     unsigned *d_ctr = nullptr;           // work counters: the contraction groups', then the interpolation's
-    cudaStream_t lc_side[sl::kLcBatchGroups - 1] = {};   // capture-only streams of the contraction groups
-    cudaEvent_t lc_ready = nullptr, lc_done[sl::kLcBatchGroups - 1] = {};
+    cudaStream_t lc_side[sl::kLcBatchGroups] = {};   // capture-only streams of the contraction groups
+    cudaEvent_t lc_ready = nullptr, lc_done[sl::kLcBatchGroups] = {};
+    cudaEvent_t idone[sl::kLcBatchGroups] = {};      // a group's interpolation done
+    std::vector<cudaEvent_t> fft_done;               // [group][branch]: a group's FFTs dealt so far
+    double group_cost[sl::kLcBatchGroups] = {};       // recurrence steps x ring pairs per group
     int *d_err = nullptr;                // flag of the interpolation's bounded waits
 };
 
@@ -179,33 +182,60 @@ static sl_status capture_persistent(sl_batch *b, cudaGraph_t *graph, cudaGraphEx
         sl_status cst = cuda_check(cudaEventRecord(b->fork, b->stream), "fork");
         for (int s = 0; s < nbr && cst == SL_OK; ++s)
             cst = cuda_check(cudaStreamWaitEvent(b->branches[s], b->fork, 0), "fork wait");
-        std::vector<TiledArgs> args;
+        std::vector<TiledArgs> args[kLcBatchGroups];   // interpolation arguments per contraction group
+        int gkmax[kLcBatchGroups] = {0, 0, 0};
         for (int i = 0; i < n && cst == SL_OK; ++i) {
             const sl_batch_item &it = b->items[i];
             if (it.n == 0) continue;
             plans[i]->stream = b->branches[i % nbr];   // inside the capture: no stream switch that synchronises
             cst = launch_sort_into(plans[i], plans[i]->sort, it.theta, it.phi, it.psi, it.n, 1, 0, 1);
-            args.push_back(fine_tiled_args(plans[i], plans[i]->sort, it.maps, it.tod));
+            const int g = lcontract_f32_group(plans[i]);
+            args[g].push_back(fine_tiled_args(plans[i], plans[i]->sort, it.maps, it.tod));
+            gkmax[g] = std::max(gkmax[g], plans[i]->K);
         }
         if (cst == SL_OK)
             cst = launch_lcontract_f32_batch(b->stream, b->lc_side, b->lc_done, b->lc_ready, plans.data(), sky.data(),
                                              beam.data(), n, b->d_items, b->group_items, b->d_ctr);
-        if (cst == SL_OK) cst = cuda_check(cudaEventRecord(b->mid, b->stream), "contraction done");
-        for (int s = 0; s < nbr && cst == SL_OK; ++s)
-            cst = cuda_check(cudaStreamWaitEvent(b->branches[s], b->mid, 0), "contraction wait");
-        for (int i = 0; i < n && cst == SL_OK; ++i) {
-            plans[i]->stream = b->branches[i % nbr];
-            cst = launch_ringfft_synth(plans[i], b->items[i].maps);
+        // Per contraction group, in the order the groups are expected to end (least
+        // work first): each detector's ring FFT waits for its own group's contraction
+        // launch only (the FFTs run on the SMs that the group's CTAs leave while the
+        // other groups still run), dealt round-robin over the branches; then one
+        // persistent interpolation launch over the group's detectors on the group's
+        // stream, after the branches' work so far (their sorts and the group's FFTs).
+        int gorder[kLcBatchGroups] = {0, 1, 2};
+        std::sort(gorder, gorder + kLcBatchGroups, [&](int x, int y) { return b->group_cost[x] < b->group_cost[y]; });
+        int dealt = 0;
+        for (int gi = 0; gi < kLcBatchGroups && cst == SL_OK; ++gi) {
+            const int g = gorder[gi];
+            if (b->group_items[g] == 0) continue;
+            for (int i = 0; i < n && cst == SL_OK; ++i) {
+                if (lcontract_f32_group(plans[i]) != g) continue;
+                const cudaStream_t br = b->branches[dealt++ % nbr];
+                cst = cuda_check(cudaStreamWaitEvent(br, b->lc_done[g], 0), "contraction group wait");
+                plans[i]->stream = br;
+                if (cst == SL_OK) cst = launch_ringfft_synth(plans[i], b->items[i].maps);
+            }
+            if (args[g].empty()) continue;
+            for (int s2 = 0; s2 < nbr && cst == SL_OK; ++s2) {
+                cudaEvent_t ev = b->fft_done[g * nbr + s2];
+                cst = cuda_check(cudaEventRecord(ev, b->branches[s2]), "ffts of a group");
+                if (cst == SL_OK) cst = cuda_check(cudaStreamWaitEvent(b->lc_side[g], ev, 0), "ffts of a group wait");
+            }
+            if (cst == SL_OK)
+                cst = launch_interp_f32_cells(b->lc_side[g], b->device, args[g].data(), (int)args[g].size(),
+                                              plans[0]->geom.tile_cols, plans[0]->p, gkmax[g],
+                                              b->d_ctr + kLcBatchGroups + g, b->d_err);
+            if (cst == SL_OK) cst = cuda_check(cudaEventRecord(b->idone[g], b->lc_side[g]), "interpolation of a group");
         }
-        for (int s = 0; s < nbr && cst == SL_OK; ++s) {
-            cst = cuda_check(cudaEventRecord(b->joins[s], b->branches[s]), "join");
-            if (cst == SL_OK) cst = cuda_check(cudaStreamWaitEvent(b->stream, b->joins[s], 0), "join wait");
+        for (int s2 = 0; s2 < nbr && cst == SL_OK; ++s2) {
+            cst = cuda_check(cudaEventRecord(b->joins[s2], b->branches[s2]), "join");
+            if (cst == SL_OK) cst = cuda_check(cudaStreamWaitEvent(b->stream, b->joins[s2], 0), "join wait");
         }
+        for (int g = 0; g < kLcBatchGroups && cst == SL_OK; ++g)   // every group stream joins the batch stream
+            if (b->group_items[g] > 0)
+                cst = cuda_check(cudaStreamWaitEvent(b->stream, args[g].empty() ? b->lc_done[g] : b->idone[g], 0),
+                                 "group join");
         for (int i = 0; i < n; ++i) plans[i]->stream = b->stream;
-        if (cst == SL_OK && !args.empty())
-            cst = launch_interp_f32_cells(b->stream, b->device, args.data(), (int)args.size(),
-                                          plans[0]->geom.tile_cols, plans[0]->p, kmax, b->d_ctr + kLcBatchGroups,
-                                          b->d_err);
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
         if (cst == SL_OK) cst = cuda_check(e, "end capture");
@@ -343,9 +373,13 @@ static void release(sl_batch *b) {
         if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->lc_done)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->idone)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->fft_done)
+        if (e) cudaEventDestroy(e);
+    b->fft_done.clear();
     if (b->lc_ready) cudaEventDestroy(b->lc_ready);
     if (b->fork) cudaEventDestroy(b->fork);
-    if (b->mid) cudaEventDestroy(b->mid);
     for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
     b->joins.clear();
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -376,11 +410,15 @@ static sl_status prepare_persistent(sl_batch *b) {
         sl_status st = sl_plan_set_tile_cols(b->items[i].plan, tc);
         if (st != SL_OK) return st;
     }
-    sl_status st = cuda_check(cudaMalloc(&b->d_ctr, (kLcBatchGroups + 1) * sizeof(unsigned)), "batch counters");
-    for (int j = 0; j < kLcBatchGroups - 1 && st == SL_OK; ++j) {
+    sl_status st = cuda_check(cudaMalloc(&b->d_ctr, 2 * kLcBatchGroups * sizeof(unsigned)), "batch counters");
+    for (int j = 0; j < kLcBatchGroups && st == SL_OK; ++j) {
         st = cuda_check(cudaStreamCreateWithFlags(&b->lc_side[j], cudaStreamNonBlocking), "contraction stream");
         if (st == SL_OK) st = cuda_check(cudaEventCreateWithFlags(&b->lc_done[j], cudaEventDisableTiming), "event");
+        if (st == SL_OK) st = cuda_check(cudaEventCreateWithFlags(&b->idone[j], cudaEventDisableTiming), "event");
     }
+    b->fft_done.assign(kLcBatchGroups * b->branches.size(), nullptr);
+    for (size_t j = 0; j < b->fft_done.size() && st == SL_OK; ++j)
+        st = cuda_check(cudaEventCreateWithFlags(&b->fft_done[j], cudaEventDisableTiming), "event");
     if (st == SL_OK) st = cuda_check(cudaEventCreateWithFlags(&b->lc_ready, cudaEventDisableTiming), "event");
     if (st == SL_OK) st = cuda_check(cudaMalloc(&b->d_err, sizeof(int)), "batch error flag");
     if (st == SL_OK) st = cuda_check(cudaMemset(b->d_err, 0, sizeof(int)), "batch error flag");
@@ -394,6 +432,8 @@ static sl_status upload_items(sl_batch *b) {
     std::vector<LcBatchItem> items;
     sl_status st = lcontract_f32_batch_items(plans.data(), (int)plans.size(), items, b->group_items);
     if (st != SL_OK) return st;
+    for (int g = 0; g < kLcBatchGroups; ++g) b->group_cost[g] = 0.0;
+    for (const LcBatchItem &it : items) b->group_cost[it.ppt == 8 ? 0 : (it.ppt == 4 ? 1 : 2)] += it.cost;
     if (b->d_items) cudaFree(b->d_items);
     b->d_items = nullptr;
     st = cuda_check(cudaMalloc(&b->d_items, items.size() * sizeof(LcBatchItem)), "batch work items");
@@ -450,7 +490,6 @@ sl_status sl_batch_create(sl_batch **out, const sl_batch_item *items, int nitems
         if (st == SL_OK) b->joins.push_back(ev);
     }
     if (st == SL_OK) st = cuda_check(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "fork event");
-    if (st == SL_OK) st = cuda_check(cudaEventCreateWithFlags(&b->mid, cudaEventDisableTiming), "mid event");
     for (int i = 0; i < nitems && st == SL_OK; ++i) st = sl_plan_reserve(b->items[i].plan, b->items[i].n);
     for (int i = 0; i < nitems && st == SL_OK; ++i) {   // flop estimate (FP64 at 1/64 of the FP32 rate)
         const sl_plan *p = b->items[i].plan;

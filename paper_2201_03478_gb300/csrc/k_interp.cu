@@ -311,6 +311,7 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const __grid_consta
     unsigned *cbegb = goffb + 2 * (NCELL + 1);                                       // [2][NCELL]
     unsigned *cendb = cbegb + 2 * NCELL;                                             // [2][NCELL]
     __shared__ CellMeta meta[2];
+    __shared__ unsigned gctr[2];                   // groups of each record buffer claimed so far
     __shared__ unsigned dcum[kMaxBatchDets + 1];   // first global work item of each detector
     __shared__ __align__(8) unsigned long long bars[9];
     const uint32_t rfull = smem_u32(&bars[0]), rempty = smem_u32(&bars[2]);
@@ -481,7 +482,10 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const __grid_consta
                     }
                     if (lane == 31) goff[NCELL] = x;
                     const unsigned total = __shfl_sync(0xffffffffu, x, 31);
-                    if (lane == 0) meta[rb] = CellMeta{nb, rowlo, collo, tr, total, poff, det};
+                    if (lane == 0) {
+                        meta[rb] = CellMeta{nb, rowlo, collo, tr, total, poff, det};
+                        gctr[rb] = 0u;
+                    }
                     // the records, gathered through the indices
                     ok = __all_sync(0xffffffffu, mbar_wait(pbar, pphase));
                     pphase ^= 1u;
@@ -511,9 +515,6 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const __grid_consta
     }
 
     // ---------------------------------------------------- evaluating warps
-    constexpr unsigned NCT = 32 * kCellConsumers;
-    const unsigned ct = threadIdx.x - 32;
-    unsigned rot = 0;   // groups dealt so far, mod NCT: each sub-item starts where the last one stopped
     int cur_nb = -1;
     unsigned nfill = 0;
     bool ok = true;
@@ -542,9 +543,15 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const __grid_consta
         const unsigned *ssid = ssidb + rb * kCellSidx + meta[rb].poff;
         const unsigned *goff = goffb + rb * (NCELL + 1);
         const unsigned *cbeg = cbegb + rb * NCELL, *cend = cendb + rb * NCELL;
-        const unsigned g_first = (ct + NCT - rot) % NCT;
-        rot = (rot + ngroups) % NCT;
-        for (unsigned gi = g_first; gi < ngroups; gi += NCT) {
+        // groups are claimed 32 at a time (one per lane) from the buffer's counter, so
+        // the warps finish a sub-item together and its buffer is released early
+        for (;;) {
+            unsigned gclaim = 0;
+            if (lane == 0) gclaim = atomicAdd(&gctr[rb], 32u);
+            gclaim = __shfl_sync(0xffffffffu, gclaim, 0);
+            if (gclaim >= ngroups) break;
+            const unsigned gi = gclaim + lane;
+            if (gi >= ngroups) continue;
             // the group's cell: the last cell whose first group is <= gi (never an empty one)
             int lo = 0, hi = NCELL - 1;
             while (lo < hi) {

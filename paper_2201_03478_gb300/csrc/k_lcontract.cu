@@ -634,7 +634,8 @@ sl_status launch_lcontract(sl_plan *p, const double *sky, const double *beam) {
 // parameters).  A block's four parts are independent and the launches share
 // nothing, so no warp ever waits for another; the order balances the tail
 // (largest blocks first), and a launch's CTAs take the SMs that another's
-// finished CTAs leave.
+// finished CTAs leave.  (Claiming whole blocks per CTA, so that a block's four
+// warps share L1, measured slower: the CTA then waits for its slowest warp.)
 struct LcBatchArgs {
     int ndet, nitems;
     const LcBatchItem *items;
@@ -646,16 +647,19 @@ template <int PPT>
 __global__ void __launch_bounds__(kNT32, 4) k_lcontract_f32_batch(const __grid_constant__ LcBatchArgs B) {
     __shared__ Stage32x2 stg[kNT32 / 32][2][32];   // [warp][buffer][l in batch]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (;;) {
-        unsigned u = 0;
-        if (lane == 0) u = atomicAdd(B.counter, 1u);
-        u = __shfl_sync(0xffffffffu, u, 0);
-        if (u >= 4u * (unsigned)B.nitems) break;
+    const unsigned nunits = 4u * (unsigned)B.nitems;
+    unsigned u = 0;
+    if (lane == 0) u = atomicAdd(B.counter, 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    while (u < nunits) {
+        // the next unit is claimed before this one runs: the atomic's round trip
+        // overlaps the work instead of preceding it
+        unsigned un = 0;
+        if (lane == 0) un = atomicAdd(B.counter, 1u);
         const LcBatchItem it = B.items[u >> 2];
-        const LcArgs &a = B.d[it.det];
-        const int part = (int)(u & 3u);
-        lcontract_f32_warp<PPT>(a, it.block, part, stg[warp]);
+        lcontract_f32_warp<PPT>(B.d[it.det], it.block, (int)(u & 3u), stg[warp]);
         __syncwarp();
+        u = __shfl_sync(0xffffffffu, un, 0);
     }
 }
 
@@ -682,14 +686,27 @@ sl_status lcontract_f32_batch_items(sl_plan *const *plans, int n, std::vector<Lc
                     items.push_back(LcBatchItem{d, (m * (p->K + 1) + k) * a.nchunk + c, a.ppt, cost});
                 }
     }
-    std::stable_sort(items.begin(), items.end(), [](const LcBatchItem &x, const LcBatchItem &y) {
-        return x.ppt != y.ppt ? x.ppt > y.ppt : x.cost > y.cost;
+    // within a group: detector by detector (the largest first), each in block order
+    // as a k_lcontract_f32 grid runs it -- the (m, k) blocks of one detector that
+    // run together share its sky rows in L2 -- except that the detector's last
+    // blocks wait for the end of the group
+    std::vector<double> dcost(n, 0.0);
+    for (const LcBatchItem &it : items) dcost[it.det] += it.cost;
+    std::stable_sort(items.begin(), items.end(), [&](const LcBatchItem &x, const LcBatchItem &y) {
+        if (x.ppt != y.ppt) return x.ppt > y.ppt;
+        if (x.det != y.det) return dcost[x.det] != dcost[y.det] ? dcost[x.det] > dcost[y.det] : x.det < y.det;
+        return false;
     });
     for (const LcBatchItem &it : items) ++counts[it.ppt == 8 ? 0 : (it.ppt == 4 ? 1 : 2)];
     return SL_OK;
 }
 
-sl_status launch_lcontract_f32_batch(cudaStream_t stream, const cudaStream_t *side, const cudaEvent_t *side_done,
+int lcontract_f32_group(const sl_plan *p) {
+    const int ppt = p->lc_ppt ? p->lc_ppt : lcontract_f32_ppt(p->npairs);
+    return ppt == 8 ? 0 : (ppt == 4 ? 1 : 2);
+}
+
+sl_status launch_lcontract_f32_batch(cudaStream_t stream, const cudaStream_t *gstream, const cudaEvent_t *gdone,
                                      cudaEvent_t ready, sl_plan *const *plans, const double *const *sky,
                                      const double *const *beam, int n, const LcBatchItem *items,
                                      const int counts[kLcBatchGroups], unsigned *counters) {
@@ -705,8 +722,7 @@ sl_status launch_lcontract_f32_batch(cudaStream_t stream, const cudaStream_t *si
     if (st == SL_OK) st = cuda_check(cudaEventRecord(ready, stream), "batch counters ready");
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, plans[0]->device);
-    int first = 0, nside = 0;
-    bool main_used = false;
+    int first = 0;
     for (int g = 0; g < kLcBatchGroups && st == SL_OK; first += counts[g], ++g) {
         if (counts[g] == 0) continue;
         void (*kern)(const LcBatchArgs) = g == 0 ? k_lcontract_f32_batch<8>
@@ -717,20 +733,13 @@ sl_status launch_lcontract_f32_batch(cudaStream_t stream, const cudaStream_t *si
         B.items = items + first;
         B.nitems = counts[g];
         B.counter = counters + g;
-        // the first group on the batch stream, the others on side streams beside it
-        const cudaStream_t s = main_used ? side[nside] : stream;
-        main_used = true;
-        if (s != stream) st = cuda_check(cudaStreamWaitEvent(s, ready, 0), "batch side stream");
+        const cudaStream_t s = gstream[g];
+        st = cuda_check(cudaStreamWaitEvent(s, ready, 0), "batch group stream");
         if (st != SL_OK) break;
         kern<<<(unsigned)(nsm * per_sm), kNT32, 0, s>>>(B);
         st = cuda_check(cudaGetLastError(), "k_lcontract_f32_batch launch");
-        if (st == SL_OK && s != stream) {
-            st = cuda_check(cudaEventRecord(side_done[nside], s), "batch side stream done");
-            ++nside;
-        }
+        if (st == SL_OK) st = cuda_check(cudaEventRecord(gdone[g], s), "batch group done");
     }
-    for (int j = 0; j < nside && st == SL_OK; ++j)
-        st = cuda_check(cudaStreamWaitEvent(stream, side_done[j], 0), "batch side stream join");
     return st;
 }
 

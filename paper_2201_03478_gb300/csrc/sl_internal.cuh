@@ -400,10 +400,12 @@ int lcontract_f32_ppt(int npairs);
 constexpr int kLcBatchGroups = 3;
 sl_status lcontract_f32_batch_items(sl_plan *const *plans, int n, std::vector<LcBatchItem> &items,
                                     int counts[kLcBatchGroups]);
-// one launch per nonempty group: the first on `stream`, the others on side[j]
-// (after `ready`, recorded on `stream`), joined back through side_done[j];
-// counters[kLcBatchGroups] are zeroed on `stream` first
-sl_status launch_lcontract_f32_batch(cudaStream_t stream, const cudaStream_t *side, const cudaEvent_t *side_done,
+// the group of a plan's blocks (by its ring pairs per thread: 8, 4, 2)
+int lcontract_f32_group(const sl_plan *p);
+// one launch per nonempty group g on gstream[g], after `ready` (recorded on
+// `stream` once the FP32 copies are made and counters[kLcBatchGroups] zeroed
+// there), its end recorded in gdone[g]; the caller joins the group streams
+sl_status launch_lcontract_f32_batch(cudaStream_t stream, const cudaStream_t *gstream, const cudaEvent_t *gdone,
                                      cudaEvent_t ready, sl_plan *const *plans, const double *const *sky,
                                      const double *const *beam, int n, const LcBatchItem *items,
                                      const int counts[kLcBatchGroups], unsigned *counters);
