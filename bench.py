@@ -276,7 +276,7 @@ def kernel_roofs(stats, plan, prec, L, K, R, nphi, ncomp, n, alu, traffic_ok=Tru
     return roofs
 
 
-def adjoint_roofs(stats, plan, K, n, alu):
+def adjoint_roofs(stats, plan, K, n, alu, traffic_ok=True):
     """FP64 adjoint kernels: the interpolation transpose does the forward's
     multiply-adds per sample (4 p^2 (K+1) + 10 flops), the contraction transpose
     11 flops per (ring, m, k, sign, l) step of the forward's volume."""
@@ -288,7 +288,7 @@ def adjoint_roofs(stats, plan, K, n, alu):
             ach = work / (avg_ms / 1e3) / 1e12
             out[name] = {"bound": "alu", "achieved": round(ach, 4), "peak": round(PEAK_FP64_TFLOPS, 4),
                          "unit": "TFLOP/s", "frac": round(ach / PEAK_FP64_TFLOPS, 4), "avg_ms": round(avg_ms, 4),
-                         "flops_per_launch": work, "traffic": None,
+                         "flops_per_launch": work, "traffic": TRAFFIC.get((name, "fp64")) if traffic_ok else None,
                          "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz"}
             if alu.get("fp64"):
                 out[name]["frac_of_measured_alu_peak"] = round(ach / alu["fp64"], 4)
@@ -381,6 +381,8 @@ def gpu_arm(args):
     highres = args.workload == "highres"
     cfg = W.config_highres(with_pointings=False) if highres else W.config_lfi(with_pointings=False)
     small = bool(args.lmax or args.nrings or args.nphi)
+    # the stored DRAM traffic per launch holds for the LFI-like workload at 1e8 pointings only
+    traffic_sized = not (highres or small) and n == int(1e8)
     if small:   # smaller variants of the same workload (profiling)
         Ls = args.lmax or cfg["lmax"]
         cfg = dict(cfg, lmax=Ls, sky=W.sky_polarised(Ls, seed=0), beam=W.beam_far_sidelobe(Ls, cfg["kmax"], seed=1),
@@ -436,7 +438,7 @@ def gpu_arm(args):
     # ---- per-kernel split and rooflines from a separate instrumented pass
     prec = args.precision
     stats = split_pass(plan, step, args.split_steps)
-    roofs = kernel_roofs(stats, plan, prec, L, K, R, nphi, ncomp, n, alu, traffic_ok=not (highres or small))
+    roofs = kernel_roofs(stats, plan, prec, L, K, R, nphi, ncomp, n, alu, traffic_ok=traffic_sized)
     dominant = max(stats.items(), key=lambda kv: kv[1][1])[0] if stats else None
     shares = {k: round(v[1] / max(1e-9, sum(x[1] for x in stats.values())), 4) for k, v in stats.items()}
     launches_per_step = sum(v[0] for v in stats.values()) / max(1, args.split_steps)
@@ -481,7 +483,8 @@ def gpu_arm(args):
                           "steps": args.adjoint_steps, "precision": "df64" if prec == "df64" else "fp64",
                           "kernel_ms_per_step": {k: round(v[1], 4) for k, v in st_adj.items()}}
         if prec != "df64":
-            out["adjoint"]["roofline_kernels"] = adjoint_roofs(st_adj, plan, K, n, alu)
+            out["adjoint"]["roofline_kernels"] = adjoint_roofs(st_adj, plan, K, n, alu,
+                                                               traffic_ok=traffic_sized)
         del gs, gb, y
 
     # ---- the other precisions on the same box, compared with this run's TOD
@@ -505,7 +508,7 @@ def gpu_arm(args):
             "ms_per_step": ms2, "rate_vs_%s" % prec: ms_step / ms2, "tod_rel_l2_vs_%s" % prec: err,
             "kernel_ms_per_step": {k: round(v[1] / args.split_steps, 4) for k, v in st2.items()},
             "roofline_kernels": kernel_roofs(st2, p2, other, L, K, R, nphi, ncomp, n, alu,
-                                             traffic_ok=not (highres or small))})
+                                             traffic_ok=traffic_sized)})
         sl.plan_destroy(p2)
         del maps2, tod2, p2
         torch.cuda.empty_cache()
@@ -772,12 +775,16 @@ def multisky_arm(args):
 # ncu-measured DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
 # at full size for the current kernels (profiles/launches_lfi_*.txt).
 TRAFFIC = {
-    ("lcontract_f64", "fp64"): 674.3e6 + 516.7e6,
-    ("interp_f64", "fp64"): 14807.3e6 + 1833.3e6,
-    ("lcontract_f32", "fp32"): 370.8e6 + 231.1e6,
-    ("interp_f32", "fp32"): 7309.0e6 + 2037.7e6,
-    ("lcontract_df", "df64"): 672.3e6 + 511.4e6,
-    ("interp_df", "df64"): 22960.7e6 + 2737.6e6,
+    # dram__bytes_read.sum + dram__bytes_write.sum per launch, LFI-like workload, 1e8 pointings
+    # (profiles/launches_lfi_{fp64,fp32,df64}.txt; single-pass ncu metrics of the current kernels)
+    ("lcontract_f64", "fp64"): 673.9e6 + 516.6e6,
+    ("interp_f64", "fp64"): 14806.2e6 + 1834.7e6,
+    ("lcontract_f32", "fp32"): 370.3e6 + 233.7e6,
+    ("interp_f32", "fp32"): 7135.0e6 + 2123.1e6,
+    ("lcontract_df", "df64"): 672.7e6 + 511.4e6,
+    ("interp_df", "df64"): 22956.7e6 + 2739.6e6,
+    ("interp_adj", "fp64"): 18364.5e6 + 385.3e6,
+    ("lcontract_adj", "fp64"): 1506.6e6 + 285.3e6,
 }
 
 
