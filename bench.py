@@ -415,7 +415,10 @@ def gpu_arm(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
 
-    def step():
+    def step():   # the whole forward in one call: the pointing sort runs beside the cube build
+        sl.convolve_tod(plan, sky, beam, theta, phi, psi, maps=maps, tod=tod)
+
+    def step_two_calls():   # the same work as two calls on one stream (per-kernel split, reference time)
         sl.synth_spin_maps(plan, sky, beam, maps)
         sl.interp_tod(plan, maps, theta, phi, psi, tod)
 
@@ -435,9 +438,11 @@ def gpu_arm(args):
     ms_step = ms_total / args.steps
     value = world * n * args.steps / (ms_total / 1e3)
 
-    # ---- per-kernel split and rooflines from a separate instrumented pass
+    # ---- the two calls one after another, and the per-kernel split and rooflines
+    # from a separate instrumented pass of them (kernels timed alone, not beside the sort)
+    ms_two = timed_steps(step_two_calls, max(3, args.steps // 4), stream, device, e0, e1) / max(3, args.steps // 4)
     prec = args.precision
-    stats = split_pass(plan, step, args.split_steps)
+    stats = split_pass(plan, step_two_calls, args.split_steps)
     roofs = kernel_roofs(stats, plan, prec, L, K, R, nphi, ncomp, n, alu, traffic_ok=traffic_sized)
     dominant = max(stats.items(), key=lambda kv: kv[1][1])[0] if stats else None
     shares = {k: round(v[1] / max(1e-9, sum(x[1] for x in stats.values())), 4) for k, v in stats.items()}
@@ -455,9 +460,13 @@ def gpu_arm(args):
         "tuning": {"tile_cols": plan.sizes()["tile_cols"],
                    "fft_tile": [plan.sizes()["fft_rings"], plan.sizes()["fft_korders"]]},
         "gpu_launches": int(round(launches_per_step * args.steps)),
+        "step": "convolve_tod (cube build and interpolation in one call; the pointing sort on a second "
+                "stream beside the cube build)",
+        "two_calls": {"ms_per_step": ms_two, "steps": max(3, args.steps // 4),
+                      "note": "synth_spin_maps then interp_tod on one stream: the same work without the overlap"},
         "kernel_split": {"steps": args.split_steps,
-                         "note": "per-kernel times from a separate pass with each launch bracketed by CUDA events; "
-                                 "the timed region runs without them"},
+                         "note": "per-kernel times from a separate pass of the two calls with each launch bracketed "
+                                 "by CUDA events; the timed region runs without them"},
         "kernel_ms_per_step": {k: round(v[1] / args.split_steps, 4) for k, v in stats.items()},
         "kernel_share": shares,
         "dominant_kernel": dominant,
@@ -496,12 +505,15 @@ def gpu_arm(args):
         tod2 = torch.empty(n, dtype=torch.float64, device=device)
 
         def step2():
+            sl.convolve_tod(p2, sky, beam, theta, phi, psi, maps=maps2, tod=tod2)
+
+        def step2_two_calls():
             sl.synth_spin_maps(p2, sky, beam, maps2)
             sl.interp_tod(p2, maps2, theta, phi, psi, tod2)
         for _ in range(args.warmup):
             step2()
         ms2 = timed_steps(step2, args.steps, stream, device, e0, e1) / args.steps
-        st2 = split_pass(p2, step2, args.split_steps)
+        st2 = split_pass(p2, step2_two_calls, args.split_steps)
         err = float(torch.linalg.vector_norm(tod2 - tod) / torch.linalg.vector_norm(tod))
         out["other_precisions"].append({
             "precision": other, "dtype": DTYPE[other], "value": n / (ms2 / 1e3), "unit": "samples/s",

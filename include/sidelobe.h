@@ -166,6 +166,19 @@ sl_status adjoint_tod(sl_plan *plan, const double *theta, const double *phi, con
                       const double *tod, int64_t n, const double *sky, const double *beam,
                       double *sky_grad, double *beam_grad, int accumulate);
 
+/* The whole forward operator in one call (Sect. 2.1: the cube of step 1, then
+ * the TOD of step 2): the result of synth_spin_maps(plan, sky, beam, maps)
+ * followed by interp_tod(plan, maps, theta, phi, psi, n, tod) -- maps and tod
+ * are both written, bit for bit as by those two calls.  The pointing sort
+ * needs the pointings only, so it runs on a second stream that the plan owns,
+ * forked from the plan's stream when the call is made (after all work queued
+ * there before), concurrently with the l-contraction and the ring FFT on the
+ * plan's stream; the interpolation waits for both.  Arguments, layouts and
+ * errors as the two calls (n may be 0: then only maps is written).  The call
+ * may be captured into a CUDA graph from the plan's stream like the others. */
+sl_status convolve_tod(sl_plan *plan, const double *sky, const double *beam, void *maps, const double *theta,
+                       const double *phi, const double *psi, int64_t n, double *tod);
+
 /* The two halves of adjoint_tod, for callers that keep the adjoint cube.
  * adjoint_interp: maps_bar (maps layout, always double2) = transpose of the
  * interpolation and phase sum applied to tod; overwritten.

@@ -190,6 +190,24 @@ def interp_tod(plan: Plan, maps, theta, phi, psi, tod=None):
     return tod
 
 
+def convolve_tod(plan: Plan, sky, beam, theta, phi, psi, maps=None, tod=None):
+    """The whole forward operator in one call (Sect. 2.1, steps 1 and 2): the cube
+    and the TOD, as synth_spin_maps followed by interp_tod, with the pointing sort
+    running beside the cube build.  Returns (maps, tod)."""
+    sky, beam = _sky_beam(plan, sky, beam)
+    if maps is None:
+        maps = torch.empty(plan.maps_shape(), dtype=plan.maps_dtype, device=sky.device)
+    _dev_tensor(maps, plan.maps_dtype, plan.device, "maps", plan.maps_shape())
+    n = _ptg(plan, theta, phi, psi)
+    if tod is None:
+        tod = torch.empty(n, dtype=torch.float64, device=theta.device)
+    _dev_tensor(tod, torch.float64, plan.device, "tod", (n,))
+    plan._sync_stream()
+    check(_lib.load().convolve_tod(plan.ptr, _ptr(sky), _ptr(beam), _ptr(maps), _ptr(theta), _ptr(phi), _ptr(psi),
+                                   n, _ptr(tod)))
+    return maps, tod
+
+
 def synth_psi_cube(plan: Plan, maps, npsi: int, cube_psi=None):
     """psi-grid cube c(theta_r, phi_j, psi_n), psi_n = 2 pi n / npsi, from the spin
     cube (Sect. 2.1, step 2): float64 [R, nphi, npsi] for FP64/DF64 plans, float32

@@ -377,6 +377,18 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const __grid_consta
                     collo = tcol * TC - P / 2 + 1;
                     float4 *node = nodeb + (size_t)nb * KPM * NN;
                     float *node0 = node0b + nb * NN;
+                    // first sorted position of each cell of the tile (and the tile's end): a
+                    // cp.async group of its own, issued first, so that the group tables below
+                    // wait for these copies only and not for the node copies behind them
+                    // (earlier record gathers still pending join this group)
+                    cp_async_commit();
+                    const int64_t cb = (int64_t)tcur * NCELL;
+                    for (int t = lane; t <= NCELL; t += 32) cp_async4(cstb + nb * (NCELL + 1) + t, A.start + cb + t, true);
+                    cp_async_commit();
+                    // node (column cc, k slot w) of row r for idx = cc * KE + w, stepped by 32
+                    // lanes with counters instead of a division per element
+                    const int q32 = 32 / KE, r32 = 32 - q32 * KE;
+                    const int cc0 = lane / KE, w0 = lane - cc0 * KE;
                     bool polar = false;
                     for (int r = 0; r < NR; ++r) {
                         const int row = rowlo + r;
@@ -386,8 +398,8 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const __grid_consta
                         const int ring = !inr ? 0 : (row < 0 ? -1 - row : (row >= g.R ? 2 * g.R - 1 - row : row));
                         const int cshift = ghost ? (g.nphi >> 1) : 0;
                         const float2 *rsrc = A.maps + (int64_t)ring * g.nphi * K1;
+                        int cc = cc0, w = w0;
                         for (int idx = lane; idx < TW * KE; idx += 32) {
-                            const int cc = idx / KE, w = idx - cc * KE;
                             int col = collo + cc + cshift;
                             if (col < 0) col += g.nphi;
                             if (col >= g.nphi) col -= g.nphi;
@@ -403,6 +415,12 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const __grid_consta
                                 cp_async8(d2, src + k, inr);
                                 cp_async8(d2 + 1, src + (k + 1 <= K ? k + 1 : k), inr && k + 1 <= K);
                             }
+                            w += r32;
+                            cc += q32;
+                            if (w >= KE) {
+                                w -= KE;
+                                ++cc;
+                            }
                         }
                     }
                     // the row table of the tile's base rows (i + 1 = tr * 4 .. tr * 4 + 3, at most R)
@@ -411,13 +429,10 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const __grid_consta
                         cp_async4(srowb + nb * ROWT + t, g.rowtab32 + (size_t)(ri <= g.R ? ri : 0) * 2 * P + t % (2 * P),
                                   ri <= g.R);
                     }
-                    // first sorted position of each cell of the tile (and the tile's end)
-                    const int64_t cb = (int64_t)tcur * NCELL;
-                    for (int t = lane; t <= NCELL; t += 32) cp_async4(cstb + nb * (NCELL + 1) + t, A.start + cb + t, true);
-                    // the group tables below read the cell starts: wait for this lane's copies, then the warp's
-                    cp_async_wait_all();
-                    __syncwarp();
+                    cp_async_commit();
                     if (__any_sync(0xffffffffu, polar)) {
+                        cp_async_wait_all();   // the ghost rows are fixed up in place once they land
+                        __syncwarp();
                         // ghost rows: (-1)^k, i.e. the odd member (k = 2j + 1) of every pair flips
                         for (int r = 0; r < NR; ++r) {
                             const int row = rowlo + r;
@@ -429,6 +444,12 @@ __global__ void __launch_bounds__(256, 2) k_interp_f32_cells(const __grid_consta
                                 e.y = -e.y;
                             }
                         }
+                        __syncwarp();
+                    } else {
+                        // the group tables below read the cell starts: this lane's copies of them
+                        // (all but the most recent group), then the warp's; the node copies land on
+                        // their own and are tracked by nfull
+                        cp_async_wait<1>();
                         __syncwarp();
                     }
                     mbar_arrive_cp_async(nfull + 8 * nb);

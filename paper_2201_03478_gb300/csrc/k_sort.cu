@@ -12,7 +12,8 @@
 //                 phi fraction, [reduced psi], cell}; key histogram
 //   k_scan_local / k_scan1 / k_scan_add:  exclusive prefix sum of the histogram
 //                 -> first position of every key (and a cursor copy)
-//   k_scatter:    perm[cursor[key]++] = s   (order within a key unspecified)
+//   k_scatter_agg: perm[cursor[key]++] = s, the cursor atomics aggregated per
+//                 chunk of samples in shared memory (order within a key unspecified)
 //   k_tile_chunks: work items of at most kChunk samples per tile (adjoint)
 #include "sl_internal.cuh"
 
@@ -21,19 +22,13 @@ namespace sl {
 constexpr int kChunk = kWorkChunk;
 constexpr int kScanBlock = 4096;    // keys per CTA of k_scan_local (1024 threads x 4)
 
-// Samples [*beg, *end) of this CTA in k_bin and k_scatter: one contiguous slice
-// of the TOD per CTA (a multiple of blockDim.x long), walked blockDim.x at a
-// time.  A scan repeats the same circle on the sky every few thousand samples,
-// so a grid-stride walk -- every resident CTA on one contiguous stretch of the
-// TOD -- sends hundreds of warps to the same cells' counters at once, and
-// their atomics serialise; slices put the CTAs on different stretches.
 // Runs of equal keys among the warp's lanes (the active lanes are a prefix of
 // the warp: lanes 0 .. nact - 1): the run of this lane starts at lane *head and
 // holds *cnt lanes.  One atomic per run replaces one per lane; lanes of a scan
 // that share a cell are almost always adjacent, and a key that recurs after
 // another key just starts another run.  (Grouping all equal keys with
-// __match_any_sync costs a multi-pass instruction per lane group that binds
-// both sort kernels.)
+// __match_any_sync costs a multi-pass instruction per lane group, which bound
+// the binning and the scatter.)
 __device__ __forceinline__ void key_run(unsigned key, bool ok, unsigned lane, int *head, unsigned *cnt) {
     const unsigned prev = __shfl_up_sync(0xffffffffu, key, 1);
     const unsigned act = __ballot_sync(0xffffffffu, ok);
@@ -46,6 +41,12 @@ __device__ __forceinline__ void key_run(unsigned key, bool ok, unsigned lane, in
     *cnt = (unsigned)(min(next, nact) - *head);
 }
 
+// Samples [*beg, *end) of this CTA in k_bin: one contiguous slice
+// of the TOD per CTA (a multiple of blockDim.x long), walked blockDim.x at a
+// time.  A scan repeats the same circle on the sky every few thousand samples,
+// so a grid-stride walk -- every resident CTA on one contiguous stretch of the
+// TOD -- sends hundreds of warps to the same cells' counters at once, and
+// their atomics serialise; slices put the CTAs on different stretches.
 __device__ __forceinline__ void cta_slice(int64_t n, int64_t *beg, int64_t *end) {
     const int64_t per = ((n + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
     *beg = min(n, (int64_t)blockIdx.x * per);
@@ -70,8 +71,10 @@ __global__ void __launch_bounds__(256) k_bin(const InterpGeom g, int fine, const
             unsigned long long fr;
             int sh;
             const int j = locate_col_fix(g, phi[s], fr, sh);
-            const int tr = (i + 1) / kTileRows, li = (i + 1) - tr * kTileRows;
-            const int tc = j / g.tile_cols, lj = j - tc * g.tile_cols;
+            // tile_cols is 8, 16 or 32 and i + 1 >= 0: shifts and masks instead of divisions
+            const int tlg = __ffs(g.tile_cols) - 1;
+            const int tr = (int)((unsigned)(i + 1) / kTileRows), li = (i + 1) - tr * kTileRows;
+            const int tc = j >> tlg, lj = j & (g.tile_cols - 1);
             const unsigned tile = (unsigned)tr * (unsigned)g.ntc + (unsigned)tc;
             key = fine ? tile * (unsigned)(kTileRows * g.tile_cols) + (unsigned)(li * g.tile_cols + lj) : tile;
             const unsigned nkeys = (unsigned)(g.ntr * g.ntc) * (fine ? (unsigned)(kTileRows * g.tile_cols) : 1u);
@@ -184,25 +187,78 @@ __global__ void k_scan_add(int64_t n, unsigned *__restrict__ data, const unsigne
     if (blockIdx.x == 0 && threadIdx.x == 0) data[n] = bsum[total_slot_from_bsum];
 }
 
-__global__ void __launch_bounds__(256) k_scatter(int64_t n, int64_t nkeys, const unsigned *__restrict__ keys,
-                                                 unsigned *__restrict__ cursor, unsigned *__restrict__ perm) {
-    (void)nkeys;
-    const unsigned lane = threadIdx.x & 31;
-    int64_t sbeg, send;
-    cta_slice(n, &sbeg, &send);
-    for (int64_t s0 = sbeg; s0 < send; s0 += blockDim.x) {
-        const int64_t s = s0 + threadIdx.x;
-        const bool ok = s < send;
-        unsigned key = ok ? keys[s] : 0xffffffffu;
-        if (ok && !SL_GUARD(key < nkeys, 0x102u)) key = 0;
-        int head;
-        unsigned cnt;
-        key_run(key, ok, lane, &head, &cnt);
-        unsigned base = 0;
-        if (ok && (int)lane == head) base = atomicAdd(cursor + key, cnt);
-        base = __shfl_sync(0xffffffffu, base, head < 0 ? 0 : head);
-        const unsigned rank = lane - (unsigned)head;
-        if (ok && SL_GUARD(base + rank < n, 0x103u)) perm[base + rank] = (unsigned)s;
+// The scatter with its atomics aggregated per chunk of kAggChunk samples: a
+// shared-memory hash table gives every sample of the chunk its rank among the
+// chunk's samples of the same key (a shared atomic); then one global atomic per
+// distinct key reserves the key's range, these atomics issued eight at a time
+// and independent of each other, so their round trips overlap; last, each
+// sample goes to its range start plus its rank.  Along a scan a 4096-sample
+// chunk holds about two visits of every cell of a circle; a per-lane scatter
+// (one returning atomic per run of equal keys in a warp) waited for one
+// round trip per warp and 32 samples.
+constexpr int kAggThreads = 256, kAggPer = 16, kAggChunk = kAggThreads * kAggPer;
+constexpr int kAggLog = 13, kAggSlots = 1 << kAggLog;   // > 2 x the distinct keys of a chunk
+static_assert(kAggSlots >= kAggChunk, "the hash table must hold every distinct key of a chunk");
+constexpr unsigned kNoKey = 0xffffffffu;
+
+__global__ void __launch_bounds__(kAggThreads) k_scatter_agg(int64_t n, int64_t nkeys, const unsigned *__restrict__ keys,
+                                                             unsigned *__restrict__ cursor,
+                                                             unsigned *__restrict__ perm) {
+    extern __shared__ __align__(16) unsigned agg_smem[];
+    unsigned *hkey = agg_smem, *hval = agg_smem + kAggSlots;   // key per slot; count, then range start
+    const int64_t per = (n + (int64_t)gridDim.x * kAggChunk - 1) / ((int64_t)gridDim.x * kAggChunk) * kAggChunk;
+    const int64_t sbeg = min(n, (int64_t)blockIdx.x * per), send = min(n, sbeg + per);
+    for (int64_t c0 = sbeg; c0 < send; c0 += kAggChunk) {
+        for (int i = threadIdx.x; i < kAggSlots / 4; i += kAggThreads) {
+            reinterpret_cast<uint4 *>(hkey)[i] = make_uint4(kNoKey, kNoKey, kNoKey, kNoKey);
+            reinterpret_cast<uint4 *>(hval)[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncthreads();
+        unsigned slot[kAggPer], rank[kAggPer];
+#pragma unroll
+        for (int j = 0; j < kAggPer; ++j) {
+            const int64_t s = c0 + (int64_t)j * kAggThreads + threadIdx.x;
+            slot[j] = kAggSlots;
+            rank[j] = 0u;
+            if (s < send) {
+                unsigned key = keys[s];
+                if (!SL_GUARD(key < nkeys, 0x102u)) key = 0;
+                unsigned h = (key * 2654435761u) >> (32 - kAggLog);
+                // linear probing; the table holds more slots than the chunk has samples,
+                // so a free or matching slot is always found within kAggSlots probes
+                for (int probe = 0; probe < kAggSlots; ++probe) {
+                    const unsigned prev = atomicCAS(&hkey[h], kNoKey, key);
+                    if (prev == kNoKey || prev == key) break;
+                    h = (h + 1u) & (kAggSlots - 1);
+                }
+                slot[j] = h;
+                rank[j] = atomicAdd(&hval[h], 1u);
+            }
+        }
+        __syncthreads();
+        for (int i0 = threadIdx.x; i0 < kAggSlots; i0 += 8 * kAggThreads) {
+            unsigned got[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = i0 + q * kAggThreads;
+                const unsigned k = hkey[i];
+                got[q] = (k != kNoKey) ? atomicAdd(cursor + k, hval[i]) : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = i0 + q * kAggThreads;
+                if (hkey[i] != kNoKey) hval[i] = got[q];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kAggPer; ++j) {
+            if (slot[j] >= kAggSlots) continue;
+            const int64_t s = c0 + (int64_t)j * kAggThreads + threadIdx.x;
+            const unsigned pos = hval[slot[j]] + rank[j];
+            if (SL_GUARD(pos < n, 0x103u)) perm[pos] = (unsigned)s;
+        }
+        __syncthreads();   // the table is cleared for the next chunk
     }
 }
 
@@ -250,9 +306,15 @@ sl_status launch_sort_into(sl_plan *p, const SortBufs &b, const double *theta, c
     timing_end(p, slot);
     if ((st = cuda_check(cudaGetLastError(), "k_scan launch")) != SL_OK) return st;
     slot = timing_begin(p, "scatter");
-    k_scatter<<<grid_for(n, 256), 256, 0, p->stream>>>(n, nkeys, b.keys, b.cursor, b.perm);
+    {
+        const size_t sm = 2 * (size_t)kAggSlots * sizeof(unsigned);
+        if ((st = cuda_check(allow_dyn_smem(k_scatter_agg, sm), "k_scatter_agg smem attribute")) != SL_OK) return st;
+        const int64_t nchunk = (n + kAggChunk - 1) / kAggChunk;
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nchunk, 152 * 3 * 4));
+        k_scatter_agg<<<grid, kAggThreads, sm, p->stream>>>(n, nkeys, b.keys, b.cursor, b.perm);
+    }
     timing_end(p, slot);
-    if ((st = cuda_check(cudaGetLastError(), "k_scatter launch")) != SL_OK) return st;
+    if ((st = cuda_check(cudaGetLastError(), "k_scatter_agg launch")) != SL_OK) return st;
     if (with_chunks) {
         k_tile_chunks<<<(p->ntiles + 255) / 256, 256, 0, p->stream>>>(p->ntiles, ncell, b.hist, b.chunk_off);
         k_scan1<<<1, 1024, 0, p->stream>>>(p->ntiles, b.chunk_off);

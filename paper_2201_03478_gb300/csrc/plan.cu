@@ -329,6 +329,9 @@ void plan_destroy(sl_plan *p) {
     dfree(p->sort.keys);
     dfree(p->sort.perm);
     dfree(p->sort.rec);
+    if (p->side_fork) cudaEventDestroy(p->side_fork);
+    if (p->side_join) cudaEventDestroy(p->side_join);
+    if (p->side) cudaStreamDestroy(p->side);
     delete p;
     cudaSetDevice(prev);
 }
@@ -621,6 +624,14 @@ sl_status synth_spin_maps(sl_plan *p, const double *sky, const double *beam, voi
     return launch_ringfft_synth(p, maps);
 }
 
+static sl_status ensure_side_stream(sl_plan *p) {
+    if (p->side) return SL_OK;
+    sl_status st = cuda_check(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking), "side stream");
+    if (st == SL_OK) st = cuda_check(cudaEventCreateWithFlags(&p->side_fork, cudaEventDisableTiming), "side event");
+    if (st == SL_OK) st = cuda_check(cudaEventCreateWithFlags(&p->side_join, cudaEventDisableTiming), "side event");
+    return st;
+}
+
 static sl_status check_ptg(const double *theta, const double *phi, const double *psi, int64_t n,
                            const void *io, const char *who) {
     if (n < 0 || n >= ((int64_t)1 << 31)) return set_error(SL_ERR_ARG, "%s: n=%lld outside [0, 2^31)", who, (long long)n);
@@ -642,6 +653,34 @@ sl_status interp_tod(sl_plan *p, const void *maps, const double *theta, const do
     const int chunks = p->precision != SL_FP64;
     if (!chunks) b.chunk_off = nullptr;
     if ((st = launch_sort_into(p, b, theta, phi, psi, n, 1, rec64, chunks)) != SL_OK) return st;
+    return launch_interp(p, b, 1, maps, psi, n, tod);
+}
+
+sl_status convolve_tod(sl_plan *p, const double *sky, const double *beam, void *maps, const double *theta,
+                       const double *phi, const double *psi, int64_t n, double *tod) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if (!sky || !beam || !maps) return set_error(SL_ERR_ARG, "convolve_tod: NULL sky, beam or maps");
+    if ((st = check_ptg(theta, phi, psi, n, tod, "convolve_tod")) != SL_OK) return st;
+    if (n == 0) return synth_spin_maps(p, sky, beam, maps);
+    // scratch first (it may synchronise the plan's stream), then the fork
+    if ((st = ensure_sort_capacity(p, n)) != SL_OK) return st;
+    if ((st = ensure_side_stream(p)) != SL_OK) return st;
+    const int rec64 = plan_wide(p->precision);
+    SortBufs b = p->sort;
+    const int chunks = p->precision != SL_FP64;
+    if (!chunks) b.chunk_off = nullptr;
+    if ((st = cuda_check(cudaEventRecord(p->side_fork, p->stream), "fork")) != SL_OK) return st;
+    if ((st = cuda_check(cudaStreamWaitEvent(p->side, p->side_fork, 0), "fork wait")) != SL_OK) return st;
+    const cudaStream_t main_stream = p->stream;
+    p->stream = p->side;   // the sort's launches (and their timers) go to the side stream
+    st = launch_sort_into(p, b, theta, phi, psi, n, 1, rec64, chunks);
+    if (st == SL_OK) st = cuda_check(cudaEventRecord(p->side_join, p->side), "sort done");
+    p->stream = main_stream;
+    if (st != SL_OK) return st;
+    if ((st = launch_lcontract(p, sky, beam)) != SL_OK) return st;
+    if ((st = launch_ringfft_synth(p, maps)) != SL_OK) return st;
+    if ((st = cuda_check(cudaStreamWaitEvent(p->stream, p->side_join, 0), "join")) != SL_OK) return st;
     return launch_interp(p, b, 1, maps, psi, n, tod);
 }
 

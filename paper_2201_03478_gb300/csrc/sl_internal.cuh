@@ -322,6 +322,8 @@ struct sl_plan {
     void *h_orb = nullptr;              // pinned staging of the period tables
     size_t h_orb_bytes = 0;
     cudaEvent_t orb_ev = nullptr;       // recorded after the last table upload
+    cudaStream_t side = nullptr;        // convolve_tod: the pointing sort's stream (created on first use)
+    cudaEvent_t side_fork = nullptr, side_join = nullptr;
     // number of captured batch graphs that hold pointers into this plan's
     // scratch: while > 0 nothing may be reallocated (the graphs would dangle)
     int batch_refs = 0;
