@@ -16,7 +16,7 @@
 // cluster synchronises after each pass, and each CTA gathers and writes its
 // own slice of the ring.
 //
-// The synthesis DFT is a decimation-in-time mixed-radix FFT (radices 4, 2, 3,
+// The synthesis DFT is a decimation-in-time mixed-radix FFT (radices 8, 4, 2, 3,
 // 5) in place in shared memory on digit-reversed input; the transpose and the
 // cluster form use a self-sorting (Stockham) FFT with two buffers.  Twiddles
 // come from a table e^{+2 pi i j/nphi} built in long double on the host.  Each
@@ -59,8 +59,9 @@ __device__ __forceinline__ float2 scal(float2 a, double s) {
     return make_float2(a.x * f, a.y * f);
 }
 
-// cos/sin of 2 pi/3, 2 pi/5, 4 pi/5 (from their closed forms)
+// cos/sin of 2 pi/3, 2 pi/5, 4 pi/5 and cos pi/4 (from their closed forms)
 constexpr double kS3 = 0.86602540378443864676;   // sqrt(3)/2
+constexpr double kS2 = 0.70710678118654752440;   // sqrt(2)/2
 constexpr double kC51 = 0.30901699437494742410;  // (sqrt(5)-1)/4
 constexpr double kS51 = 0.95105651629515357212;
 constexpr double kC52 = -0.80901699437494742410;
@@ -86,6 +87,27 @@ __device__ __forceinline__ void dft_small(int R, C *v) {
         v[0] = add(v[0], t1);
         v[1] = add(a, t2);
         v[2] = sub(a, t2);
+    } else if (R == 8) {
+        // 4-point transforms of the even and the odd inputs (J = rot: +-i), then
+        // X_k = E_k + W^k O_k, X_{k+4} = E_k - W^k O_k with W = e^{+-2 pi i/8}:
+        // W O = (O + J O)/sqrt2, W^2 O = J O, W^3 O = (J O - O)/sqrt2
+        const C e0 = add(v[0], v[4]), e1 = sub(v[0], v[4]);
+        const C e2 = add(v[2], v[6]), e3 = rot<C, INV>(sub(v[2], v[6]));
+        const C o0 = add(v[1], v[5]), o1 = sub(v[1], v[5]);
+        const C o2 = add(v[3], v[7]), o3 = rot<C, INV>(sub(v[3], v[7]));
+        const C E0 = add(e0, e2), E2 = sub(e0, e2), E1 = add(e1, e3), E3 = sub(e1, e3);
+        const C O0 = add(o0, o2), O2 = sub(o0, o2), O1 = add(o1, o3), O3 = sub(o1, o3);
+        const C t1 = scal(add(O1, rot<C, INV>(O1)), kS2);
+        const C t2 = rot<C, INV>(O2);
+        const C t3 = scal(sub(rot<C, INV>(O3), O3), kS2);
+        v[0] = add(E0, O0);
+        v[4] = sub(E0, O0);
+        v[1] = add(E1, t1);
+        v[5] = sub(E1, t1);
+        v[2] = add(E2, t2);
+        v[6] = sub(E2, t2);
+        v[3] = add(E3, t3);
+        v[7] = sub(E3, t3);
     } else {  // 5
         C t1 = add(v[1], v[4]), t2 = add(v[2], v[3]);
         C t3 = sub(v[1], v[4]), t4 = sub(v[2], v[3]);
@@ -103,7 +125,7 @@ __device__ __forceinline__ void dft_small(int R, C *v) {
 
 struct Radices {
     int n;
-    unsigned long long code;   // radix of pass i in bits [3i, 3i + 3)
+    unsigned long long code;   // radix of pass i in bits [4i, 4i + 4)
 };
 
 template <typename C, bool INV, int R>
@@ -145,8 +167,9 @@ __device__ C *fft_smem(C *buf0, C *buf1, int N, const Radices &rad, const C *__r
     C *src = buf0, *dst = buf1;
     int Ns = 1;
     for (int pass = 0; pass < rad.n; ++pass) {
-        const int R = (int)((rad.code >> (3 * pass)) & 7);
+        const int R = (int)((rad.code >> (4 * pass)) & 15);
         switch (R) {
+            case 8: fft_pass<C, INV, 8>(src, dst, N, Ns, tw); break;
             case 4: fft_pass<C, INV, 4>(src, dst, N, Ns, tw); break;
             case 2: fft_pass<C, INV, 2>(src, dst, N, Ns, tw); break;
             case 3: fft_pass<C, INV, 3>(src, dst, N, Ns, tw); break;
@@ -287,8 +310,9 @@ __global__ void __launch_bounds__(256) k_ringfft_synth_ip(int L, int K, int R, i
     __syncthreads();
     int Ns = 1, off = 0;
     for (int pass = 0; pass < rad.n; ++pass) {
-        const int Rp = (int)((rad.code >> (3 * pass)) & 7);
+        const int Rp = (int)((rad.code >> (4 * pass)) & 15);
         switch (Rp) {
+            case 8: dit_pass<C, 8, TT>(x, N, Ns, ptw + off); break;
             case 4: dit_pass<C, 4, TT>(x, N, Ns, ptw + off); break;
             case 2: dit_pass<C, 2, TT>(x, N, Ns, ptw + off); break;
             case 3: dit_pass<C, 3, TT>(x, N, Ns, ptw + off); break;
@@ -377,9 +401,10 @@ __device__ int fft_cluster(cooperative_groups::cluster_group &cl, const DistBuf<
     const int g0 = (int)cl.block_rank() * blockDim.x + threadIdx.x, gstride = (int)cl.num_blocks() * blockDim.x;
     int cur = 0, Ns = 1;
     for (int pass = 0; pass < rad.n; ++pass) {
-        const int R = (int)((rad.code >> (3 * pass)) & 7);
+        const int R = (int)((rad.code >> (4 * pass)) & 15);
         const DistBuf<C> &src = cur ? b1 : b0, &dst = cur ? b0 : b1;
         switch (R) {
+            case 8: fft_pass_cl<C, INV, 8>(cl, src, dst, N, Ns, tw, g0, gstride); break;
             case 4: fft_pass_cl<C, INV, 4>(cl, src, dst, N, Ns, tw, g0, gstride); break;
             case 2: fft_pass_cl<C, INV, 2>(cl, src, dst, N, Ns, tw, g0, gstride); break;
             case 3: fft_pass_cl<C, INV, 3>(cl, src, dst, N, Ns, tw, g0, gstride); break;
@@ -470,7 +495,7 @@ static Radices radices_of(const sl_plan *p) {
     Radices r;
     r.n = p->nradix;
     r.code = 0;
-    for (int i = 0; i < p->nradix; ++i) r.code |= (unsigned long long)p->radices[i] << (3 * i);
+    for (int i = 0; i < p->nradix; ++i) r.code |= (unsigned long long)p->radices[i] << (4 * i);
     return r;
 }
 
