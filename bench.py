@@ -792,7 +792,7 @@ TRAFFIC = {
     ("lcontract_f64", "fp64"): 673.9e6 + 516.6e6,
     ("interp_f64", "fp64"): 14806.2e6 + 1834.7e6,
     ("lcontract_f32", "fp32"): 370.3e6 + 233.7e6,
-    ("interp_f32", "fp32"): 7135.0e6 + 2123.1e6,
+    ("interp_f32", "fp32"): 7086.2e6 + 2115.9e6,
     ("lcontract_df", "df64"): 672.7e6 + 511.4e6,
     ("interp_df", "df64"): 22956.7e6 + 2739.6e6,
     ("interp_adj", "fp64"): 18364.5e6 + 385.3e6,

@@ -312,7 +312,10 @@ __global__ void __launch_bounds__(256) k_ringfft_synth_ip(int L, int K, int R, i
     for (int pass = 0; pass < rad.n; ++pass) {
         const int Rp = (int)((rad.code >> (4 * pass)) & 15);
         switch (Rp) {
-            case 8: dit_pass<C, 8, TT>(x, N, Ns, ptw + off); break;
+            case 8:   // FP64-class plans only: compiled for double2 alone, since a radix-8
+                      // pass in the FP32 kernel raises its registers for every radix
+                if constexpr (sizeof(C) == sizeof(double2)) dit_pass<C, 8, TT>(x, N, Ns, ptw + off);
+                break;
             case 4: dit_pass<C, 4, TT>(x, N, Ns, ptw + off); break;
             case 2: dit_pass<C, 2, TT>(x, N, Ns, ptw + off); break;
             case 3: dit_pass<C, 3, TT>(x, N, Ns, ptw + off); break;
@@ -404,7 +407,9 @@ __device__ int fft_cluster(cooperative_groups::cluster_group &cl, const DistBuf<
         const int R = (int)((rad.code >> (4 * pass)) & 15);
         const DistBuf<C> &src = cur ? b1 : b0, &dst = cur ? b0 : b1;
         switch (R) {
-            case 8: fft_pass_cl<C, INV, 8>(cl, src, dst, N, Ns, tw, g0, gstride); break;
+            case 8:   // FP64-class plans only (as in the in-place form)
+                if constexpr (sizeof(C) == sizeof(double2)) fft_pass_cl<C, INV, 8>(cl, src, dst, N, Ns, tw, g0, gstride);
+                break;
             case 4: fft_pass_cl<C, INV, 4>(cl, src, dst, N, Ns, tw, g0, gstride); break;
             case 2: fft_pass_cl<C, INV, 2>(cl, src, dst, N, Ns, tw, g0, gstride); break;
             case 3: fft_pass_cl<C, INV, 3>(cl, src, dst, N, Ns, tw, g0, gstride); break;
