@@ -267,6 +267,50 @@ __device__ __forceinline__ Coef32x2 coef32x2(const Stage32x2 &v) {
                     make_float2(v.c1.y, v.c1.y), make_float2(v.c2.x, v.c2.x), make_float2(v.c2.y, v.c2.y)};
 }
 
+// One l step of packed pairs Q0 .. NP-1, stage by stage across them (independent
+// instructions between each producer and its consumer); with INJ, first the
+// start states of the lanes whose start l is l (selects: before its start a
+// recurrence holds exact zeros).
+template <int NP, int Q0, bool INJ>
+__device__ __forceinline__ void rec32x2_steps(Rec32x2 (&S)[NP], const Coef32x2 &c, int l) {
+    if (INJ) {
+#pragma unroll
+        for (int q = Q0; q < NP; ++q) {
+            const bool j0 = l == S[q].ls0, j1 = l == S[q].ls1;
+            S[q].y.x = j0 ? S[q].ys.x : S[q].y.x;
+            S[q].D.x = j0 ? S[q].Ds.x : S[q].D.x;
+            S[q].y.y = j1 ? S[q].ys.y : S[q].y.y;
+            S[q].D.y = j1 ? S[q].Ds.y : S[q].D.y;
+        }
+    }
+    float2 t[NP];
+#pragma unroll
+    for (int q = Q0; q < NP; ++q) t[q] = __ffma2_rn(c.na, S[q].yc, c.cr);
+#pragma unroll
+    for (int q = Q0; q < NP; ++q) {
+        S[q].a1r = __ffma2_rn(c.c1r, S[q].y, S[q].a1r);
+        S[q].a1i = __ffma2_rn(c.c1i, S[q].y, S[q].a1i);
+    }
+#pragma unroll
+    for (int q = Q0; q < NP; ++q) S[q].D = __ffma2_rn(t[q], S[q].y, S[q].D);
+#pragma unroll
+    for (int q = Q0; q < NP; ++q) {
+        S[q].a2r = __ffma2_rn(c.c2r, S[q].y, S[q].a2r);
+        S[q].a2i = __ffma2_rn(c.c2i, S[q].y, S[q].a2i);
+    }
+#pragma unroll
+    for (int q = Q0; q < NP; ++q) S[q].y = __fadd2_rn(S[q].y, S[q].D);
+}
+
+// The ramp step with the last na packed pairs begun (na a constant after unrolling).
+template <int NP>
+__device__ __forceinline__ void rec32x2_ramp(int na, Rec32x2 (&S)[NP], const Coef32x2 &c, int l) {
+    if (na == NP) rec32x2_steps<NP, 0, true>(S, c, l);
+    if constexpr (NP >= 2) if (na == NP - 1) rec32x2_steps<NP, 1, true>(S, c, l);
+    if constexpr (NP >= 3) if (na == NP - 2) rec32x2_steps<NP, (NP >= 3 ? 2 : 0), true>(S, c, l);
+    if constexpr (NP >= 4) if (na == NP - 3) rec32x2_steps<NP, (NP >= 4 ? 3 : 0), true>(S, c, l);
+}
+
 __device__ __forceinline__ void rec32x2_step(Rec32x2 &s, const Coef32x2 &c) {
     // sums with y_l: re/im of c1 y, c2 y
     s.a1r = __ffma2_rn(c.c1r, s.y, s.a1r);
@@ -342,6 +386,11 @@ __device__ __forceinline__ void lcontract_f32_warp(const LcArgs &a, int block, i
         lmx = max(lmx, max(ls[0], ls[1]));
     }
     lmx = __reduce_max_sync(0xffffffffu, lmx);
+    // the packed pairs' earliest starts usually descend with q (ring pairs nearer the
+    // equator start earlier): then they begin in the order NP-1, NP-2, .. 0 (warp-uniform)
+    bool qdesc = true;
+#pragma unroll
+    for (int q = 1; q < NP; ++q) qdesc = qdesc && qmin[q] <= qmin[q - 1];
     Stage32 st;
     Stage32x2 dummy;
     auto stage_mine = [&](int l, Stage32x2 *dst) {   // this warp's sign only
@@ -362,41 +411,30 @@ __device__ __forceinline__ void lcontract_f32_warp(const LcArgs &a, int block, i
         const Stage32x2 *sv = stw[buf];
         int i = 0;
         // until every recurrence of the warp has started (up to and including the
-        // last start l): inject start states; skip packed pairs none of whose lanes started
-        for (; i < nc && c0 + i <= lmx; ++i) {
-            const int l = c0 + i;
-            const Coef32x2 c = coef32x2(sv[i]);
+        // last start l): inject start states; packed pairs none of whose lanes has
+        // started are not stepped
+        if (qdesc) {
+            // in segments: with na pairs begun, those na step together, interleaved
 #pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                if (l < qmin[q]) continue;
-                if (l == S[q].ls0) { S[q].y.x = S[q].ys.x; S[q].D.x = S[q].Ds.x; }
-                if (l == S[q].ls1) { S[q].y.y = S[q].ys.y; S[q].D.y = S[q].Ds.y; }
-                rec32x2_step(S[q], c);
+            for (int na = 1; na <= NP; ++na) {
+                const int lend = (na < NP) ? min(qmin[NP - 1 - na], lmx + 1) : lmx + 1;
+                for (; i < nc && c0 + i < lend; ++i) rec32x2_ramp<NP>(na, S, coef32x2(sv[i]), c0 + i);
+            }
+        } else {
+            for (; i < nc && c0 + i <= lmx; ++i) {
+                const int l = c0 + i;
+                const Coef32x2 c = coef32x2(sv[i]);
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    if (l < qmin[q]) continue;
+                    if (l == S[q].ls0) { S[q].y.x = S[q].ys.x; S[q].D.x = S[q].Ds.x; }
+                    if (l == S[q].ls1) { S[q].y.y = S[q].ys.y; S[q].D.y = S[q].Ds.y; }
+                    rec32x2_step(S[q], c);
+                }
             }
         }
 #pragma unroll 2
-        for (; i < nc; ++i) {
-            const Coef32x2 c = coef32x2(sv[i]);
-            // the step of rec32x2_step, stage by stage across the packed pairs (independent
-            // instructions between each producer and its consumer)
-            float2 t[NP];
-#pragma unroll
-            for (int q = 0; q < NP; ++q) t[q] = __ffma2_rn(c.na, S[q].yc, c.cr);
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                S[q].a1r = __ffma2_rn(c.c1r, S[q].y, S[q].a1r);
-                S[q].a1i = __ffma2_rn(c.c1i, S[q].y, S[q].a1i);
-            }
-#pragma unroll
-            for (int q = 0; q < NP; ++q) S[q].D = __ffma2_rn(t[q], S[q].y, S[q].D);
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                S[q].a2r = __ffma2_rn(c.c2r, S[q].y, S[q].a2r);
-                S[q].a2i = __ffma2_rn(c.c2i, S[q].y, S[q].a2i);
-            }
-#pragma unroll
-            for (int q = 0; q < NP; ++q) S[q].y = __fadd2_rn(S[q].y, S[q].D);
-        }
+        for (; i < nc; ++i) rec32x2_steps<NP, 0, false>(S, coef32x2(sv[i]), c0 + i);
         __syncwarp();   // the batch is read before the other buffer is overwritten next time round
         if (next) stage_mine(ln, &stw[buf ^ 1][lane]);
     }
