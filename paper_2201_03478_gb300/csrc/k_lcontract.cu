@@ -268,20 +268,18 @@ __device__ __forceinline__ Coef32x2 coef32x2(const Stage32x2 &v) {
 }
 
 // One l step of packed pairs Q0 .. NP-1, stage by stage across them (independent
-// instructions between each producer and its consumer); with INJ, first the
-// start states of the lanes whose start l is l (selects: before its start a
-// recurrence holds exact zeros).
-template <int NP, int Q0, bool INJ>
+// instructions between each producer and its consumer); first, for pairs Q0 ..
+// Q1-1, the start states of the lanes whose start l is l (selects: before its
+// start a recurrence holds exact zeros, and stepping zeros adds exact zeros).
+template <int NP, int Q0, int Q1>
 __device__ __forceinline__ void rec32x2_steps(Rec32x2 (&S)[NP], const Coef32x2 &c, int l) {
-    if (INJ) {
 #pragma unroll
-        for (int q = Q0; q < NP; ++q) {
-            const bool j0 = l == S[q].ls0, j1 = l == S[q].ls1;
-            S[q].y.x = j0 ? S[q].ys.x : S[q].y.x;
-            S[q].D.x = j0 ? S[q].Ds.x : S[q].D.x;
-            S[q].y.y = j1 ? S[q].ys.y : S[q].y.y;
-            S[q].D.y = j1 ? S[q].Ds.y : S[q].D.y;
-        }
+    for (int q = Q0; q < Q1; ++q) {
+        const bool j0 = l == S[q].ls0, j1 = l == S[q].ls1;
+        S[q].y.x = j0 ? S[q].ys.x : S[q].y.x;
+        S[q].D.x = j0 ? S[q].Ds.x : S[q].D.x;
+        S[q].y.y = j1 ? S[q].ys.y : S[q].y.y;
+        S[q].D.y = j1 ? S[q].Ds.y : S[q].D.y;
     }
     float2 t[NP];
 #pragma unroll
@@ -302,13 +300,25 @@ __device__ __forceinline__ void rec32x2_steps(Rec32x2 (&S)[NP], const Coef32x2 &
     for (int q = Q0; q < NP; ++q) S[q].y = __fadd2_rn(S[q].y, S[q].D);
 }
 
-// The ramp step with the last na packed pairs begun (na a constant after unrolling).
+// Ramp steps i .. iend-1 of a batch with the last NA packed pairs begun, the last
+// NB of them with every lane started (no injection left for those).
+template <int NP, int NA, int NB>
+__device__ __forceinline__ void rec32x2_ramp_loop(int &i, int iend, Rec32x2 (&S)[NP], const Stage32x2 *sv, int c0) {
+    for (; i < iend; ++i) rec32x2_steps<NP, NP - NA, NP - NB>(S, coef32x2(sv[i]), c0 + i);
+}
 template <int NP>
-__device__ __forceinline__ void rec32x2_ramp(int na, Rec32x2 (&S)[NP], const Coef32x2 &c, int l) {
-    if (na == NP) rec32x2_steps<NP, 0, true>(S, c, l);
-    if constexpr (NP >= 2) if (na == NP - 1) rec32x2_steps<NP, 1, true>(S, c, l);
-    if constexpr (NP >= 3) if (na == NP - 2) rec32x2_steps<NP, (NP >= 3 ? 2 : 0), true>(S, c, l);
-    if constexpr (NP >= 4) if (na == NP - 3) rec32x2_steps<NP, (NP >= 4 ? 3 : 0), true>(S, c, l);
+__device__ __forceinline__ void rec32x2_ramp(int na, int nb, int &i, int iend, Rec32x2 (&S)[NP],
+                                             const Stage32x2 *sv, int c0) {
+#define SL_RAMP(A, B)                                                                                  \
+    if constexpr (A <= NP && B <= A)                                                                   \
+        if (na == A && nb == B) {                                                                      \
+            rec32x2_ramp_loop<NP, (A <= NP ? A : 1), (A <= NP && B <= A ? B : 0)>(i, iend, S, sv, c0); \
+            return;                                                                                    \
+        }
+    SL_RAMP(1, 0) SL_RAMP(1, 1) SL_RAMP(2, 0) SL_RAMP(2, 1) SL_RAMP(2, 2) SL_RAMP(3, 0) SL_RAMP(3, 1)
+    SL_RAMP(3, 2) SL_RAMP(3, 3) SL_RAMP(4, 0) SL_RAMP(4, 1) SL_RAMP(4, 2) SL_RAMP(4, 3) SL_RAMP(4, 4)
+#undef SL_RAMP
+    i = iend;   // not reached: 1 <= na <= NP, 0 <= nb <= na
 }
 
 __device__ __forceinline__ void rec32x2_step(Rec32x2 &s, const Coef32x2 &c) {
@@ -386,6 +396,12 @@ __device__ __forceinline__ void lcontract_f32_warp(const LcArgs &a, int block, i
         lmx = max(lmx, max(ls[0], ls[1]));
     }
     lmx = __reduce_max_sync(0xffffffffu, lmx);
+    int qmax[NP];   // latest start among the lanes of packed pair q that start at all (warp-uniform)
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int s0 = S[q].ls0 <= a.L ? S[q].ls0 : -1, s1 = S[q].ls1 <= a.L ? S[q].ls1 : -1;
+        qmax[q] = __reduce_max_sync(0xffffffffu, max(s0, s1));
+    }
     // the packed pairs' earliest starts usually descend with q (ring pairs nearer the
     // equator start earlier): then they begin in the order NP-1, NP-2, .. 0 (warp-uniform)
     bool qdesc = true;
@@ -414,11 +430,27 @@ __device__ __forceinline__ void lcontract_f32_warp(const LcArgs &a, int block, i
         // last start l): inject start states; packed pairs none of whose lanes has
         // started are not stepped
         if (qdesc) {
-            // in segments: with na pairs begun, those na step together, interleaved
+            // in segments: the last na pairs begun, the last nb of them with every lane
+            // started; those na step together, interleaved, and only the na - nb still
+            // starting pay for the injection selects
+            while (i < nc && c0 + i <= lmx) {
+                const int l = c0 + i;
+                int na = 0, nb = 0, lnext = lmx + 1;
+                bool run = true;
 #pragma unroll
-            for (int na = 1; na <= NP; ++na) {
-                const int lend = (na < NP) ? min(qmin[NP - 1 - na], lmx + 1) : lmx + 1;
-                for (; i < nc && c0 + i < lend; ++i) rec32x2_ramp<NP>(na, S, coef32x2(sv[i]), c0 + i);
+                for (int q = NP - 1; q >= 0; --q)
+                    if (run) {
+                        if (qmin[q] <= l) ++na;
+                        else { lnext = min(lnext, qmin[q]); run = false; }
+                    }
+                run = true;
+#pragma unroll
+                for (int q = NP - 1; q >= 0; --q)
+                    if (run && q >= NP - na) {
+                        if (qmax[q] < l) ++nb;
+                        else { lnext = min(lnext, qmax[q] + 1); run = false; }
+                    }
+                rec32x2_ramp<NP>(na, nb, i, min(nc, lnext - c0), S, sv, c0);
             }
         } else {
             for (; i < nc && c0 + i <= lmx; ++i) {
@@ -434,7 +466,7 @@ __device__ __forceinline__ void lcontract_f32_warp(const LcArgs &a, int block, i
             }
         }
 #pragma unroll 2
-        for (; i < nc; ++i) rec32x2_steps<NP, 0, false>(S, coef32x2(sv[i]), c0 + i);
+        for (; i < nc; ++i) rec32x2_steps<NP, 0, 0>(S, coef32x2(sv[i]), c0 + i);
         __syncwarp();   // the batch is read before the other buffer is overwritten next time round
         if (next) stage_mine(ln, &stw[buf ^ 1][lane]);
     }
