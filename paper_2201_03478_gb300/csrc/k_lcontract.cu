@@ -716,6 +716,17 @@ struct LcBatchArgs {
 template <int PPT>
 __global__ void __launch_bounds__(kNT32, 4) k_lcontract_f32_batch(const __grid_constant__ LcBatchArgs B) {
     __shared__ Stage32x2 stg[kNT32 / 32][2][32];   // [warp][buffer][l in batch]
+    // the detectors' arguments, copied once from the kernel parameters: read at a
+    // run-time index, they are shared-memory loads instead of constant-cache misses
+    __shared__ __align__(16) LcArgs s_args[kMaxBatchDets];
+    static_assert(sizeof(LcArgs) % sizeof(int) == 0, "LcArgs copied as ints");
+    {
+        const int *src = reinterpret_cast<const int *>(B.d);
+        int *dst = reinterpret_cast<int *>(s_args);
+        const int nw = B.ndet * (int)(sizeof(LcArgs) / sizeof(int));
+        for (int w = threadIdx.x; w < nw; w += blockDim.x) dst[w] = src[w];
+        __syncthreads();
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned nunits = 4u * (unsigned)B.nitems;
     unsigned u = 0;
@@ -727,7 +738,7 @@ __global__ void __launch_bounds__(kNT32, 4) k_lcontract_f32_batch(const __grid_c
         unsigned un = 0;
         if (lane == 0) un = atomicAdd(B.counter, 1u);
         const LcBatchItem it = B.items[u >> 2];
-        lcontract_f32_warp<PPT>(B.d[it.det], it.block, (int)(u & 3u), stg[warp]);
+        lcontract_f32_warp<PPT>(s_args[it.det], it.block, (int)(u & 3u), stg[warp]);
         __syncwarp();
         u = __shfl_sync(0xffffffffu, un, 0);
     }
