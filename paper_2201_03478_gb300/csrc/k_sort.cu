@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) k_bin(const InterpGeom g, int fine, const
             const int tc = j >> tlg, lj = j & (g.tile_cols - 1);
             const unsigned tile = (unsigned)tr * (unsigned)g.ntc + (unsigned)tc;
             key = fine ? tile * (unsigned)(kTileRows * g.tile_cols) + (unsigned)(li * g.tile_cols + lj) : tile;
-            const unsigned nkeys = (unsigned)(g.ntr * g.ntc) * (fine ? (unsigned)(kTileRows * g.tile_cols) : 1u);
+            [[maybe_unused]] const unsigned nkeys = (unsigned)(g.ntr * g.ntc) * (fine ? (unsigned)(kTileRows * g.tile_cols) : 1u);
             if (!SL_GUARD(i >= -1 && i < g.R && j >= 0 && j < g.nphi && key < nkeys, 0x101u)) key = 0;
             keys[s] = key;
             // theta - theta(i0), i0 = i - p/2 + 1 the first stencil row (index i0 + half = i + 1),
