@@ -789,14 +789,14 @@ def multisky_arm(args):
 TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum per launch, LFI-like workload, 1e8 pointings
     # (profiles/launches_lfi_{fp64,fp32,df64}.txt; single-pass ncu metrics of the current kernels)
-    ("lcontract_f64", "fp64"): 673.9e6 + 516.6e6,
-    ("interp_f64", "fp64"): 14806.2e6 + 1834.7e6,
+    ("lcontract_f64", "fp64"): 673.9e6 + 516.4e6,
+    ("interp_f64", "fp64"): 15153.3e6 + 1911.1e6,
     ("lcontract_f32", "fp32"): 370.3e6 + 233.7e6,
     ("interp_f32", "fp32"): 7086.2e6 + 2115.9e6,
-    ("lcontract_df", "df64"): 672.7e6 + 511.4e6,
-    ("interp_df", "df64"): 22956.7e6 + 2739.6e6,
-    ("interp_adj", "fp64"): 18364.5e6 + 385.3e6,
-    ("lcontract_adj", "fp64"): 1506.6e6 + 285.3e6,
+    ("lcontract_df", "df64"): 672.3e6 + 511.3e6,
+    ("interp_df", "df64"): 22934.1e6 + 2736.6e6,
+    ("interp_adj", "fp64"): 18463.7e6 + 385.5e6,
+    ("lcontract_adj", "fp64"): 1507.2e6 + 285.3e6,
 }
 
 
