@@ -496,7 +496,7 @@ def gpu_arm(args):
                                                                traffic_ok=traffic_sized)
         del gs, gb, y
 
-    # ---- the other precisions on the same box, compared with this run's TOD
+    # ---- the other precisions on the same GPU, compared with this run's TOD
     others = [q for q in ("fp64", "df64", "fp32", "tf32x3") if q != prec] if (args.compare and rank == 0 and world == 1) else []
     out["other_precisions"] = []
     for other in others:

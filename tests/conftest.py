@@ -19,7 +19,7 @@ def rel_l2(a, b):
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
 
 
-# Parity tolerances.  Relative L2 over the whole output is the benchmark spec's target
+# Parity tolerances.  Relative L2 over the whole output is the accuracy target
 # (FP64-class plans 1e-10, FP32-class plans 1e-5).  The element-wise bound is
 # max |got - ref| / rms(ref): it catches an error confined to a few samples
 # (a pole, a ghost row, a tile edge) that the global norm would average away.

@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle,
 element by element on seeded inputs.
 
-Tolerances (relative L2 over the whole output, spec targets):
+Tolerances (relative L2 over the whole output, the accuracy targets):
   FP64 plans: 1e-10 (oracle and kernels take different but equally exact
               routes: recurrence arrangement, FFT vs explicit DFT, sum order);
   DF64 plans (double-float contraction and interpolation): the FP64 target, 1e-10;
