@@ -73,3 +73,47 @@ def test_convolve_tod_without_samples():
     plan.sync()
     assert tod_b.numel() == 0 and torch.equal(maps_a, maps_b)
     sl.plan_destroy(plan)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "df64", "tf32x3"])
+def test_convolve_tod_in_a_cuda_graph(prec):
+    """convolve_tod captured into a CUDA graph on the plan's stream (thread-local
+    capture, after a warm call on that stream has created the plan's second stream
+    and sized its scratch).  Every replay gives the eager results bit for bit and
+    reads the buffers' current contents: pointings rewritten between replays, then
+    a doubled sky (every TOD value exactly doubled)."""
+    n = 50_000
+    sl, plan, host, (sky, beam, th, ph, ps) = _setup(prec, n, seed=5)
+    th2, ph2, ps2 = (torch.from_numpy(a).cuda() for a in W.pointings_uniform(n, seed=11))
+    cur = [t.clone() for t in (th, ph, ps)]
+    maps = torch.empty(plan.maps_shape(), dtype=plan.maps_dtype, device="cuda")
+    tod = torch.empty(n, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        ref_maps, ref1 = (t.clone() for t in sl.convolve_tod(plan, sky, beam, th, ph, ps))
+        ref2 = sl.interp_tod(plan, ref_maps, th2, ph2, ps2).clone()
+        sl.convolve_tod(plan, sky, beam, cur[0], cur[1], cur[2], maps=maps, tod=tod)   # warm, on s
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+        sl.convolve_tod(plan, sky, beam, cur[0], cur[1], cur[2], maps=maps, tod=tod)
+    torch.cuda.synchronize()
+    for it in range(4):
+        for c, x in zip(cur, (th2, ph2, ps2) if it % 2 else (th, ph, ps)):
+            c.copy_(x)
+        maps.zero_()
+        tod.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(maps, ref_maps), it
+        assert torch.equal(tod, ref2 if it % 2 else ref1), it
+    for c, x in zip(cur, (th, ph, ps)):
+        c.copy_(x)
+    sky.mul_(2.0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(tod, 2.0 * ref1)
+    del g
+    plan.sync()
+    sl.plan_destroy(plan)
