@@ -355,7 +355,7 @@ sl_status sl_plan_selftest_timeout(sl_plan *plan);
  * denominator of the roofline fractions reported for the ALU-bound kernels).
  * kind 0: FP64 fused multiply-add; 1: FP32 fused multiply-add; 2: packed FP32
  * (two lanes per instruction).  Runs 8 independent chains per thread on 8
- * CTAs of 256 threads per SM for about 16 ms, best of three timed launches
+ * CTAs of 256 threads per SM for about 17-20 ms, best of three timed launches
  * after a warm-up, and stores flops per second (2 per lane multiply-add) in
  * *flops_per_s.  Touches no memory; synchronises its own stream.
  * SL_ERR_ARG for a NULL output or another kind. */

@@ -82,7 +82,7 @@ extern "C" sl_status sl_measure_alu_peak(int device, int kind, double *flops_per
     if ((st = cuda_check(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device), "SM count")) != SL_OK)
         return st;
     const int blocks = nsm * 8, threads = 256;
-    // about 40 ms per launch at the nominal GB300 rates
+    // about 17-20 ms per launch on GB300 (1.06 / 77.8 / 79.2 TFLOP/s measured)
     const int iters = kind == 0 ? 4096 : (kind == 1 ? 262144 : 131072);
     const double flops_per_fma = kind == 2 ? 4.0 : 2.0;
     const double flops = (double)blocks * threads * kChains * (double)iters * flops_per_fma;
