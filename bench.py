@@ -529,7 +529,8 @@ def gpu_arm(args):
     if args.multisky_leg > 0 and rank == 0 and world == 1 and not highres:
         out["multisky"] = multisky_leg(sl, cfg, args.multisky_leg, max(3, args.steps // 2), args.warmup, device, local)
 
-    # ---- end to end through the public API from pinned host buffers
+    # ---- end to end from pinned host buffers through the C-ABI call convolve_tod_host
+    # (binding tod_from_host): copies, cube build, interpolation and download inside
     if args.e2e_steps > 0:
         pin = [t.pin_memory() for t in (sky_h, beam_h, *ptg_h)]
         res = torch.empty(n, dtype=torch.float64, pin_memory=True)   # reused TOD buffer
@@ -543,7 +544,7 @@ def gpu_arm(args):
         h2d = sum(t.numel() * t.element_size() for t in pin)
         out["e2e"] = {"value": world * n * args.e2e_steps / dt, "unit": "samples/s",
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(res.numel() * 8),
-                      "steps": args.e2e_steps}
+                      "steps": args.e2e_steps, "call": "convolve_tod_host (host buffers, 8 pieces)"}
         del pin, res
 
     if rank == 0 and world == 1 and args.cpu_baseline:

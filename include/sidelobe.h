@@ -179,6 +179,25 @@ sl_status adjoint_tod(sl_plan *plan, const double *theta, const double *phi, con
 sl_status convolve_tod(sl_plan *plan, const double *sky, const double *beam, void *maps, const double *theta,
                        const double *phi, const double *psi, int64_t n, double *tod);
 
+/* convolve_tod from HOST buffers, for callers that keep their data on the host
+ * (no counterpart in the paper): sky, beam, theta, phi, psi and tod are host
+ * pointers with the layouts of convolve_tod.  The call copies sky and beam to
+ * device buffers that the plan owns and builds the cube there (synth_spin_maps);
+ * meanwhile it uploads the pointings in `pieces` consecutive pieces on a stream of
+ * its own, interpolates each piece on the plan's stream as soon as it has arrived
+ * (interp_tod) and copies its TOD back on a third stream.  Unlike the device
+ * calls it is synchronous: it returns when the whole TOD is in tod and nothing of
+ * the call is in flight, with SL_ERR_TIMEOUT if a bounded wait inside a kernel
+ * expired.  The copies start after the work queued on the plan's stream before
+ * the call.  pieces in [1, 64] (fewer when n is smaller); SL_ERR_ARG otherwise.
+ * For the copies to overlap the computation the host buffers must be page-locked
+ * (cudaHostAlloc, pinned tensors); pageable buffers work, with serialised copies.
+ * The plan's device buffers of this call (inputs, cube, TOD: about 32 bytes per
+ * sample plus the cube) are allocated on first use and grown when n exceeds
+ * every earlier call; each piece's sort uses the plan's sort scratch. */
+sl_status convolve_tod_host(sl_plan *plan, const double *sky, const double *beam, const double *theta,
+                            const double *phi, const double *psi, int64_t n, int pieces, double *tod);
+
 /* The two halves of adjoint_tod, for callers that keep the adjoint cube.
  * adjoint_interp: maps_bar (maps layout, always double2) = transpose of the
  * interpolation and phase sum applied to tod; overwritten.

@@ -18,7 +18,8 @@ STATUS_NAMES = {0: "SL_OK", -1: "SL_ERR_ARG", -2: "SL_ERR_UNSUPPORTED", -3: "SL_
                 -4: "SL_ERR_CUDA", -5: "SL_ERR_TIMEOUT"}
 
 # Symbols include/sidelobe.h declares (checked by the host tests).
-EXPORTS = ["sidelobe_plan_create", "synth_spin_maps", "interp_tod", "convolve_tod", "adjoint_tod", "adjoint_interp",
+EXPORTS = ["sidelobe_plan_create", "synth_spin_maps", "interp_tod", "convolve_tod", "convolve_tod_host", "adjoint_tod",
+           "adjoint_interp",
            "adjoint_synth", "interp_tod_noalloc", "plan_destroy", "sl_plan_get_sizes", "sl_plan_set_stream", "sl_plan_sync",
            "sl_plan_enable_timing", "sl_plan_kernel_stats", "sl_plan_reserve", "sl_plan_set_tile_cols", "sl_plan_set_fft_tile", "sl_plan_set_contraction_pairs",
            "sl_batch_create", "sl_batch_run", "sl_batch_sync", "sl_batch_get_info", "sl_batch_destroy", "synth_spin_maps_multi",
@@ -96,6 +97,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "synth_spin_maps_multi": (I, [P, I, P, P, P]),
         "interp_tod": (I, [P, P, P, P, P, I64, P]),
         "convolve_tod": (I, [P, P, P, P, P, P, P, I64, P]),
+        "convolve_tod_host": (I, [P, P, P, P, P, P, I64, I, P]),
         "adjoint_tod": (I, [P, P, P, P, P, I64, P, P, P, P, I]),
         "adjoint_interp": (I, [P, P, P, P, P, I64, P]),
         "adjoint_synth": (I, [P, P, P, P, P, P, I]),

@@ -345,53 +345,28 @@ def adjoint_synth(plan: Plan, maps_bar, sky, beam, sky_grad=None, beam_grad=None
 
 
 def tod_from_host(plan: Plan, sky, beam, theta, phi, psi, chunks: int = 8, out=None):
-    """End-to-end call from host arrays: copies the inputs to the device, builds
-    the cube, interpolates and copies the TOD back into `out` (a pinned host
-    float64 tensor; allocated when None) and returns it.  The pointings are
-    uploaded in `chunks` pieces on a copy stream while the cube is built; each
-    piece is interpolated as soon as it has arrived and its TOD is copied back
-    on a third stream (host tensors should be pinned for the copies to
-    overlap).  Reusing `out` across calls avoids a pinned allocation per call."""
-    dev = torch.device("cuda", plan.device)
-
-    def host(x, dtype):
+    """End-to-end call from host arrays (convolve_tod_host): the library copies
+    the inputs to the device, builds the cube, uploads the pointings in `chunks`
+    pieces while the cube is built, interpolates each piece as soon as it has
+    arrived and copies its TOD back into `out` (a host float64 tensor; a pinned
+    one is allocated when None), and returns `out` when all of it is there.
+    Pinned host tensors let the copies overlap the computation; reusing `out`
+    across calls avoids a pinned allocation per call."""
+    def host(x, dtype, name, shape):
         t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x))
-        return t if t.dtype == dtype else t.to(dtype)
-    th_h, ph_h, ps_h = host(theta, torch.float64), host(phi, torch.float64), host(psi, torch.float64)
-    n = th_h.numel()
-    main = torch.cuda.current_stream(dev)
-    up_s, down_s = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    sky_d = host(sky, torch.complex128).to(dev, non_blocking=True)
-    beam_d = host(beam, torch.complex128).to(dev, non_blocking=True)
-    th, ph, ps = (torch.empty(n, dtype=torch.float64, device=dev) for _ in range(3))
-    tod = torch.empty(n, dtype=torch.float64, device=dev)
+        if t.device.type != "cpu" or t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous host %s array of shape %s" % (name, dtype, tuple(shape)))
+        return t
+    n = int(theta.numel() if isinstance(theta, torch.Tensor) else np.size(theta))
+    sky = host(sky, torch.complex128, "sky", (plan.ncomp, plan.nalm))
+    beam = host(beam, torch.complex128, "beam", (plan.ncomp, plan.kmax + 1, plan.lmax + 1))
+    th, ph, ps = (host(x, torch.float64, nm, (n,)) for x, nm in ((theta, "theta"), (phi, "phi"), (psi, "psi")))
     if out is None:
         out = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    elif out.dtype != torch.float64 or out.numel() != n or out.device.type != "cpu" or not out.is_contiguous():
-        raise ValueError("out must be a contiguous host float64 tensor of %d elements" % n)
-    chunks = max(1, min(int(chunks), n)) if n else 1
-    bounds = [n * c // chunks for c in range(chunks + 1)]
-    arrived = []
-    with torch.cuda.stream(up_s):
-        for c in range(chunks):
-            a, b = bounds[c], bounds[c + 1]
-            for d_, h_ in ((th, th_h), (ph, ph_h), (ps, ps_h)):
-                d_[a:b].copy_(h_[a:b], non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(up_s)
-            arrived.append(ev)
-    maps = synth_spin_maps(plan, sky_d, beam_d)
-    for c in range(chunks):
-        a, b = bounds[c], bounds[c + 1]
-        main.wait_event(arrived[c])
-        if b > a:
-            interp_tod(plan, maps, th[a:b], ph[a:b], ps[a:b], tod[a:b])
-        done = torch.cuda.Event()
-        done.record(main)
-        down_s.wait_event(done)
-        with torch.cuda.stream(down_s):
-            out[a:b].copy_(tod[a:b], non_blocking=True)
-    down_s.synchronize()      # every piece of the TOD is on the host
+    host(out, torch.float64, "out", (n,))
+    plan._sync_stream()
+    check(_lib.load().convolve_tod_host(plan.ptr, _ptr(sky), _ptr(beam), _ptr(th), _ptr(ph), _ptr(ps), n,
+                                        int(max(1, min(int(chunks), 64))), _ptr(out)))
     return out
 
 

@@ -337,6 +337,17 @@ void plan_destroy(sl_plan *p) {
     if (p->side_fork) cudaEventDestroy(p->side_fork);
     if (p->side_join) cudaEventDestroy(p->side_join);
     if (p->side) cudaStreamDestroy(p->side);
+    if (p->up) cudaStreamSynchronize(p->up);
+    if (p->down) cudaStreamSynchronize(p->down);
+    dfree(p->d_hin);
+    dfree(p->d_htod);
+    dfree(p->d_hmaps);
+    for (int c = 0; c < 64; ++c) {
+        if (p->h_arrived[c]) cudaEventDestroy(p->h_arrived[c]);
+        if (p->h_done[c]) cudaEventDestroy(p->h_done[c]);
+    }
+    if (p->up) cudaStreamDestroy(p->up);
+    if (p->down) cudaStreamDestroy(p->down);
     delete p;
     cudaSetDevice(prev);
 }
@@ -688,6 +699,106 @@ sl_status convolve_tod(sl_plan *p, const double *sky, const double *beam, void *
     if ((st = launch_ringfft_synth(p, maps)) != SL_OK) return st;
     if ((st = cuda_check(cudaStreamWaitEvent(p->stream, p->side_join, 0), "join")) != SL_OK) return st;
     return launch_interp(p, b, 1, maps, psi, n, tod);
+}
+
+// ---- end to end from host buffers
+constexpr int kMaxHostPieces = 64;   // the size of sl_plan's h_arrived / h_done
+
+// Doubles of sky and beam at the front of d_hin (the pointings follow them).
+static size_t host_harmonic_doubles(const sl_plan *p) {
+    return (size_t)2 * p->ncomp * p->nalm + (size_t)2 * p->ncomp * (p->K + 1) * (p->L + 1);
+}
+
+// Streams, events and device buffers of convolve_tod_host for n samples.
+static sl_status ensure_host_path(sl_plan *p, int64_t n) {
+    sl_status st = SL_OK;
+    if (!p->up) {
+        if ((st = cuda_check(cudaStreamCreateWithFlags(&p->up, cudaStreamNonBlocking), "upload stream")) != SL_OK)
+            return st;
+        if ((st = cuda_check(cudaStreamCreateWithFlags(&p->down, cudaStreamNonBlocking), "download stream")) != SL_OK)
+            return st;
+        for (int c = 0; c < kMaxHostPieces && st == SL_OK; ++c) {
+            st = cuda_check(cudaEventCreateWithFlags(&p->h_arrived[c], cudaEventDisableTiming), "piece event");
+            if (st == SL_OK) st = cuda_check(cudaEventCreateWithFlags(&p->h_done[c], cudaEventDisableTiming), "piece event");
+        }
+        if (st != SL_OK) return st;
+    }
+    if (!p->d_hmaps) {
+        const size_t mb = (size_t)p->R * p->nphi * (p->K + 1) * (plan_wide(p->precision) ? 16 : 8);
+        if ((st = dalloc(p, &p->d_hmaps, mb, "host-path cube")) != SL_OK) return st;
+    }
+    if (n > p->host_cap) {
+        cudaStreamSynchronize(p->stream);
+        const size_t fixed = host_harmonic_doubles(p);
+        if (p->host_cap >= 0)
+            p->bytes_held -= (int64_t)((fixed + 3 * (size_t)p->host_cap + (size_t)p->host_cap) * sizeof(double));
+        dfree(p->d_hin);
+        dfree(p->d_htod);
+        p->d_hin = p->d_htod = nullptr;
+        p->host_cap = -1;
+        if ((st = dalloc_t(p, &p->d_hin, fixed + 3 * (size_t)n, "host-path inputs")) != SL_OK) return st;
+        if ((st = dalloc_t(p, &p->d_htod, (size_t)n, "host-path TOD")) != SL_OK) return st;
+        p->host_cap = n;
+    }
+    return SL_OK;
+}
+
+static sl_status host_pipeline(sl_plan *p, const double *sky, const double *beam, const double *theta,
+                               const double *phi, const double *psi, int64_t n, int np, double *tod) {
+    const size_t nsky = (size_t)2 * p->ncomp * p->nalm;
+    double *d_sky = p->d_hin, *d_beam = d_sky + nsky;
+    double *d_th = d_sky + host_harmonic_doubles(p), *d_ph = d_th + p->host_cap, *d_ps = d_ph + p->host_cap;
+    sl_status st = cuda_check(cudaMemcpyAsync(d_sky, sky, nsky * sizeof(double), cudaMemcpyDefault, p->stream), "sky");
+    if (st == SL_OK)
+        st = cuda_check(cudaMemcpyAsync(d_beam, beam, (host_harmonic_doubles(p) - nsky) * sizeof(double),
+                                        cudaMemcpyDefault, p->stream), "beam");
+    // the pointings piece by piece on the upload stream, after the work queued so far
+    if (st == SL_OK) st = cuda_check(cudaEventRecord(p->side_fork, p->stream), "fork");
+    if (st == SL_OK) st = cuda_check(cudaStreamWaitEvent(p->up, p->side_fork, 0), "fork wait");
+    for (int c = 0; c < np && st == SL_OK; ++c) {
+        const int64_t a = n * c / np, b = n * (c + 1) / np;
+        const size_t bytes = (size_t)(b - a) * sizeof(double);
+        if (b > a) {
+            st = cuda_check(cudaMemcpyAsync(d_th + a, theta + a, bytes, cudaMemcpyDefault, p->up), "theta");
+            if (st == SL_OK) st = cuda_check(cudaMemcpyAsync(d_ph + a, phi + a, bytes, cudaMemcpyDefault, p->up), "phi");
+            if (st == SL_OK) st = cuda_check(cudaMemcpyAsync(d_ps + a, psi + a, bytes, cudaMemcpyDefault, p->up), "psi");
+        }
+        if (st == SL_OK) st = cuda_check(cudaEventRecord(p->h_arrived[c], p->up), "piece arrived");
+    }
+    // the cube while they arrive; then each piece's TOD, copied back on the download stream
+    if (st == SL_OK) st = synth_spin_maps(p, d_sky, d_beam, p->d_hmaps);
+    for (int c = 0; c < np && st == SL_OK; ++c) {
+        const int64_t a = n * c / np, b = n * (c + 1) / np;
+        st = cuda_check(cudaStreamWaitEvent(p->stream, p->h_arrived[c], 0), "piece wait");
+        if (st == SL_OK && b > a) st = interp_tod(p, p->d_hmaps, d_th + a, d_ph + a, d_ps + a, b - a, p->d_htod + a);
+        if (st == SL_OK) st = cuda_check(cudaEventRecord(p->h_done[c], p->stream), "piece done");
+        if (st == SL_OK) st = cuda_check(cudaStreamWaitEvent(p->down, p->h_done[c], 0), "download wait");
+        if (st == SL_OK && b > a)
+            st = cuda_check(cudaMemcpyAsync(tod + a, p->d_htod + a, (size_t)(b - a) * sizeof(double),
+                                            cudaMemcpyDefault, p->down), "tod");
+    }
+    return st;
+}
+
+sl_status convolve_tod_host(sl_plan *p, const double *sky, const double *beam, const double *theta,
+                            const double *phi, const double *psi, int64_t n, int pieces, double *tod) {
+    sl_status st = enter(p);
+    if (st != SL_OK) return st;
+    if (!sky || !beam) return set_error(SL_ERR_ARG, "convolve_tod_host: NULL sky or beam");
+    if ((st = check_ptg(theta, phi, psi, n, tod, "convolve_tod_host")) != SL_OK) return st;
+    if (pieces < 1 || pieces > kMaxHostPieces)
+        return set_error(SL_ERR_ARG, "convolve_tod_host: pieces=%d outside [1, %d]", pieces, kMaxHostPieces);
+    const int np = (int)std::min<int64_t>(pieces, std::max<int64_t>(n, 1));
+    if ((st = ensure_host_path(p, n)) != SL_OK) return st;
+    if (n > 0 && (st = ensure_sort_capacity(p, (n + np - 1) / np)) != SL_OK) return st;
+    if ((st = ensure_side_stream(p)) != SL_OK) return st;
+    st = host_pipeline(p, sky, beam, theta, phi, psi, n, np, tod);
+    // returns only when nothing of the call is in flight, also after an error
+    const sl_status su = cuda_check(cudaStreamSynchronize(p->up), "upload stream synchronize");
+    const sl_status sd = cuda_check(cudaStreamSynchronize(p->down), "download stream synchronize");
+    const sl_status ss = sl_plan_sync(p);   // the plan's stream, and the error flag of the bounded waits
+    if (st != SL_OK) return st;
+    return su != SL_OK ? su : (sd != SL_OK ? sd : ss);
 }
 
 sl_status adjoint_interp(sl_plan *p, const double *theta, const double *phi, const double *psi,

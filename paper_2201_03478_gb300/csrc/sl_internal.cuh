@@ -324,6 +324,15 @@ struct sl_plan {
     cudaEvent_t orb_ev = nullptr;       // recorded after the last table upload
     cudaStream_t side = nullptr;        // convolve_tod: the pointing sort's stream (created on first use)
     cudaEvent_t side_fork = nullptr, side_join = nullptr;
+    // convolve_tod_host (created and grown on first use): device copies of the host
+    // inputs (sky, beam, then the three pointing arrays of host_cap samples each),
+    // the cube, the TOD, the upload and download streams and the per-piece events
+    double *d_hin = nullptr;
+    double *d_htod = nullptr;
+    void *d_hmaps = nullptr;
+    int64_t host_cap = -1;
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t h_arrived[64] = {}, h_done[64] = {};
     // number of captured batch graphs that hold pointers into this plan's
     // scratch: while > 0 nothing may be reallocated (the graphs would dangle)
     int batch_refs = 0;

@@ -295,18 +295,38 @@ def test_adjoint_interp_order_2_and_6(sl, oracle_lib, order_case, p, prec):
     check_close(got, ref, 1e-12, MAX64, "p=%d %s adjoint interp" % (p, prec))
 
 
-def test_tod_from_host_pipeline(sl):
-    """The host-buffer end-to-end call (chunked upload / interpolation / download)
-    gives the device path's TOD, for several chunk counts including ragged ones."""
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tod_from_host_pipeline(sl, prec):
+    """The host-buffer end-to-end call (convolve_tod_host: upload in pieces beside
+    the cube build, interpolation per piece, download) gives the device path's TOD
+    bit for bit (every sample's arithmetic is the same whatever piece it falls in),
+    for several piece counts including ragged ones and more pieces than samples,
+    from pinned and from pageable host memory."""
+    import ctypes
+    from paper_2201_03478_gb300 import _lib
     c = CASES["small_healpix"]()
-    plan = _plan(sl, c)
+    plan = _plan(sl, c, prec)
     ref = sl.interp_tod(plan, sl.synth_spin_maps(plan, _dev(c["sky"]), _dev(c["beam"])), _dev(c["th"]),
                         _dev(c["ph"]), _dev(c["ps"])).cpu().numpy()
-    pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (c["sky"], c["beam"], c["th"], c["ph"],
-                                                                            c["ps"])]
-    for chunks in (1, 3, 8):
+    host = [torch.from_numpy(np.ascontiguousarray(a)) for a in (c["sky"], c["beam"], c["th"], c["ph"], c["ps"])]
+    pin = [t.pin_memory() for t in host]
+    for chunks in (1, 3, 8, 64):
         got = sl.tod_from_host(plan, *pin, chunks=chunks).numpy()
-        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+        assert np.array_equal(got, ref), chunks
+    assert np.array_equal(sl.tod_from_host(plan, *host, chunks=5).numpy(), ref)   # pageable
+    few = [t[:5] for t in host[2:]]
+    got = sl.tod_from_host(plan, host[0], host[1], *few, chunks=64).numpy()           # pieces > n
+    assert np.array_equal(got, ref[:5])
+    empty = [t[:0] for t in host[2:]]
+    assert sl.tod_from_host(plan, host[0], host[1], *empty).numel() == 0
+    lib = _lib.load()
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    out = torch.empty(ref.size, dtype=torch.float64)
+    for bad in (0, 65):
+        st = lib.convolve_tod_host(plan.ptr, P(host[0]), P(host[1]), P(host[2]), P(host[3]), P(host[4]),
+                                   ref.size, bad, P(out))
+        assert st == _lib.SL_ERR_ARG
+    sl.plan_destroy(plan)
 
 
 def test_errors_are_reported(sl):
